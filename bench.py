@@ -1,0 +1,342 @@
+"""Benchmark of the acoustic path-tracing hot path on one GB300 (or N, as independent poses).
+
+Workload (default): the procedural clutter scene -- ground plane + ~200k triangles of icospheres
+and cylinders in a 20 x 20 x 5 m volume, 4 materials with 16-band curves, 1M Fibonacci rays,
+5 bounces, curvature-based Monte Carlo diffraction (64 samples per high-curvature vertex, 4M
+budget), a 32-microphone 12 cm disc array and 512 bins over 20-80 kHz (synthetic, seeded).
+
+One step = one full simulate of one sensor pose through the C ABI: tracing (Algorithm 1),
+diffraction sampling and filters, direct path, accumulation of all three spectra.  With
+--include-precompute the step also rebuilds the scene (weld, curvature, CDFs, LBVH).
+
+Metric: Mrays/s = (closest-hit + any-hit ray segments traced) / device time, with mic-spectra/s
+and the accelerator kernel roofline reported beside it.  Under torchrun every rank simulates its
+own pose of the same scene (weak scaling, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Mrays/s (closest-hit + any-hit segments per second, spectra at <=1e-4 rel-L2 vs oracle)"
+UNIT = "Mrays/s"
+FLOPS_PER_TERM = 12  # complex rotation (6) + complex scale-accumulate (4) + lobe exponent (2)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name: str, rank: int):
+    if name == "clutter":
+        wl = synth.clutter(seed=202)
+    elif name == "shoebox":
+        wl = synth.shoebox(seed=101)
+    elif name == "vegetation":
+        wl = synth.vegetation(seed=303)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return wl
+
+
+def workload_config(wl, args):
+    return {"workload": f"{wl.name}: {wl.n_tris} triangles, {len(wl.dirs)} rays x {wl.bounces} bounces, "
+                        f"{len(wl.mics)} mics, {wl.n_bins} bins {wl.f_lo/1e3:.0f}-{wl.f_hi/1e3:.0f} kHz, "
+                        f"diffraction {'on' if wl.diffraction else 'off'}",
+            "triangles": wl.n_tris, "rays": len(wl.dirs), "bounces": wl.bounces, "mics": len(wl.mics),
+            "bins": wl.n_bins, "diffraction": bool(wl.diffraction),
+            "step": "scene precompute + simulate" if args.include_precompute else "simulate (scene prebuilt)",
+            "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"{args.gpus} independent poses (one per GPU)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled every 200 ms while running."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def oracle_sample(wl, n_sample_rays: int, nthreads: int = 0):
+    """The oracle as it stands on a bounded sample of the workload: every n-th ray (all mics, all
+    bins) and the same fraction of the diffraction candidates.  Returns (segments, seconds, desc)."""
+    import oracle
+    N = len(wl.dirs)
+    stride = max(1, N // n_sample_rays)
+    sub = np.arange(0, N, stride)[:n_sample_rays]
+    t0 = time.perf_counter()
+    scene = oracle.Scene(wl.verts, wl.tris)
+    ct_all = cp_all = None
+    if wl.diffraction:  # per-scene pre-processing, like the BVH: not part of the timed sample
+        G = oracle.curvature(wl.verts, wl.tris)
+        Cm = oracle.tri_metric(wl.verts, wl.tris, G)
+        cd = oracle.diffraction_cdf(wl.verts, wl.tris, Cm, wl.tri_obj)
+        ct_all, cp_all = oracle.diffraction_samples(wl.verts, wl.tris, cd)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    R = oracle.mic_centroid(wl.mics)
+    rec = oracle.trace(scene, wl.emitter, wl.emitter_quat, wl.dirs[sub], wl.bounces, r_max=wl.max_distance, R=R,
+                       nthreads=nthreads)
+    n_rec = int((rec["tri"] >= 0).sum())
+    ended_by_miss = int(((rec["tri"] >= 0).sum(1) < wl.bounces).sum())
+    segs = n_rec + ended_by_miss + n_rec  # closest queries (hits + final misses) + one visibility ray per hit
+    ct = cp = keep = None
+    frac = len(sub) / N
+    if wl.diffraction:
+        ks = np.arange(0, len(ct_all), max(1, int(round(1 / frac))))
+        ct, cp = ct_all[ks], cp_all[ks]
+        keep = oracle.diffraction_filter(scene, wl.emitter, wl.emitter_quat, ct, cp, fov_half=wl.fov_half,
+                                         nthreads=nthreads)
+        segs += len(ct)
+    dvis = oracle.direct_visibility(scene, wl.emitter, wl.mics)
+    segs += len(wl.mics)
+    params = oracle.spec_params(wl)
+    oracle.spectra(params, rec, wl.dirs[sub], wl.tri_mat, ct, cp, keep, dvis, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    desc = (f"every {stride}-th ray ({len(sub)} of {N}) traced with the oracle's BVH (BVH, curvature and CDFs "
+            f"{t_build:.1f} s, not timed), 1/{int(round(1 / frac))} of the diffraction candidates, all {len(wl.mics)} mics x "
+            f"{wl.n_bins} bins")
+    return segs, dt, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args.workload, 0)
+    cores = os.cpu_count()
+    times, segs_all = [], []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        segs, dt, desc = oracle_sample(wl, args.ref_rays)
+        if i >= args.warmup:
+            times.append(dt)
+            segs_all.append(segs)
+    value = sum(segs_all) / sum(times) / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry, f64 spectra", "data": "synthetic",
+            "impl": "reference", "config": workload_config(wl, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clutter")
+    ap.add_argument("--include-precompute", action="store_true")
+    ap.add_argument("--cpu-rays", type=int, default=16384, help="rays in the oracle's CPU-baseline sample")
+    ap.add_argument("--ref-rays", type=int, default=2048, help="rays per step of the reference (oracle) arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2602_19652_gb300 as st
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = workload(args.workload, rank)
+    ctx = st.Context(local)
+    sc = st.from_workload(ctx, wl)
+    params = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance, pose_index=rank)
+    out = torch.empty((3, len(wl.mics), wl.n_bins), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(stats=True):
+        if args.include_precompute:
+            sc.precompute()
+        return ctx.simulate(sc, params, out=out, stats=stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    st_list = []
+    peaks, peak_src = load_peaks()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 255)                       # evict L2 between steps (outside the timed events)
+            ev[i][0].record(stream)
+            _, s = step()
+            ev[i][1].record(stream)
+            st_list.append(s)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    segs = sum(s.closest_queries + s.shadow_queries for s in st_list)
+    # max over ranks of the time, sum of the work
+    t = torch.tensor([total_ms, float(segs), float(len(wl.mics) * args.steps)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_all = float(tmax[0])
+    else:
+        total_ms_all = total_ms
+    segs_all, spectra_all = float(t[1]), float(t[2])
+    value = segs_all / (total_ms_all / 1e3) / 1e6
+
+    # ---- dominant kernel: the accumulator (FP32/XU-pipe arithmetic)
+    acc_ms = sum(s.ms_accum_kernel for s in st_list)
+    acc_launches = sum(s.accum_launches for s in st_list)
+    terms = sum(s.terms for s in st_list)
+    clocks = clk.summary()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_TERM * terms / (acc_ms / 1e3) / 1e12 if acc_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_accum (spectrum accumulator)", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {peak_src})",
+                "work": f"{FLOPS_PER_TERM} FP32 flops per (path, mic, bin) term, {terms / max(acc_launches, 1):.3e} "
+                        f"terms per launch", "ms_per_launch": acc_ms / max(acc_launches, 1),
+                "traffic": None}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if rank == 0 or world > 1:
+        dirs_h = torch.from_numpy(np.ascontiguousarray(wl.dirs)).pin_memory()
+        mics_h = np.ascontiguousarray(wl.mics, np.float32)
+        spec_h = np.empty((3, len(wl.mics), wl.n_bins), np.complex64)
+        import ctypes as C
+        L = st.load()
+        pos = np.ascontiguousarray(wl.emitter, np.float32)
+        quat = np.ascontiguousarray(wl.emitter_quat, np.float32)
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+
+        def e2e_step():
+            st.check(L.st_set_emitter(ctx.h, cp(pos), cp(quat), len(wl.dirs), C.c_void_p(dirs_h.data_ptr()),
+                                      None, 0, float(np.float32(wl.fov_half)), st.ST_MEM_HOST), ctx.h)
+            st.check(L.st_set_receivers(ctx.h, len(mics_h), cp(mics_h), None, None, 0, 0, 0, st.ST_MEM_HOST), ctx.h)
+            if args.include_precompute:
+                sc.precompute()
+            st.check(L.st_simulate_host(ctx.h, sc.h, C.byref(params), cp(spec_h), None), ctx.h)
+
+        for _ in range(2):
+            e2e_step()
+        e2e_t = []
+        for i in range(max(3, args.steps // 2)):
+            flush.fill_(i & 255)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            e2e_t.append(time.perf_counter() - t0)
+        segs_per_step = segs / len(st_list)
+        h2d = wl.dirs.nbytes + mics_h.nbytes + pos.nbytes + quat.nbytes
+        e2e = {"value": segs_per_step / float(np.mean(e2e_t)) / 1e6 * world, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(spec_h.nbytes),
+               "ms_per_step": 1e3 * float(np.mean(e2e_t))}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        segs_c, dt_c, desc = oracle_sample(wl, args.cpu_rays)
+        cpu = {"value": segs_c / dt_c / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
+               "seconds": dt_c}
+
+    s0 = st_list[-1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (float-float path lengths and phases)",
+            "data": "synthetic", "config": workload_config(wl, args),
+            "mic_spectra_per_s": spectra_all / (total_ms_all / 1e3),
+            "per_step": {"closest_segments": s0.closest_queries, "anyhit_segments": s0.shadow_queries,
+                         "visible_records": s0.visible_records, "diffraction_candidates": s0.candidates,
+                         "diffraction_kept": s0.candidates_kept, "terms": s0.terms,
+                         "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
+                         "ms_accumulate": s0.ms_accumulate},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * sonotrace.h -- C ABI of the GB300 acoustic path-tracing library.
+ *
+ * The library computes, on one GPU, the specular, diffraction and direct spectra of an
+ * in-air ultrasonic scene as described for SonoTraceUE (Jansen & Steckel, arXiv 2602.19652):
+ *   - Sec. III-B  geometric pre-processing: Meyer mean curvature G_v, triangle metric C_i (Eq. 1)
+ *   - Sec. III-C  Algorithm 1: multi-bounce specular tracing of emitter rays with a visibility ray
+ *                 per hit; magnitudes with 1/r^2 spreading, atmospheric decay and the BRDF lobe
+ *                 (Eq. 2, 3) synthesised into complex spectra H(f) (Eq. 4), summed over paths
+ *   - Sec. III-D  curvature-importance-sampled diffraction candidates, field-of-view, incidence
+ *                 and visibility filters, magnitudes M_d (Eq. 7), spectra G(f) (Eq. 8)
+ *   - Sec. III-E  the direct emitter-to-receiver path, M_p (Eq. 11), P(f) (Eq. 12)
+ * The inverse transforms (Eq. 5-6, 9-10, 13) are linear and act on the summed spectra.
+ *
+ * Conventions
+ *   - Every call returns st_status (0 = ST_OK, < 0 = error) and never throws.  The message of
+ *     the last error of a context is available from st_last_error().
+ *   - All arrays are row-major, little-endian; float = IEEE binary32, double = binary64.
+ *     Complex spectra are interleaved (re, im) float32 pairs.
+ *   - A `mem` argument says where a pointer lives: ST_MEM_HOST (pageable or pinned host memory)
+ *     or ST_MEM_DEVICE (device memory of the context's GPU).  Inputs are copied; the caller
+ *     keeps ownership of everything it passes.
+ *   - Work is issued on the context's CUDA stream and is stream-ordered: device outputs are
+ *     complete when that stream reaches the point after the call.  Calls that return host
+ *     data or statistics synchronise the stream.
+ *   - Not thread-safe per context; different contexts may be used from different threads.
+ */
+#ifndef SONOTRACE_H
+#define SONOTRACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t st_status;
+#define ST_OK 0
+#define ST_ERR_ARG (-1)      /* invalid argument (null pointer, size out of range, ...) */
+#define ST_ERR_CUDA (-2)     /* a CUDA call failed; see st_last_error() */
+#define ST_ERR_OOM (-3)      /* device allocation failed */
+#define ST_ERR_MESH (-4)     /* index out of range or non-finite vertex in the mesh */
+#define ST_ERR_TIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define ST_ERR_STATE (-6)    /* call out of order (e.g. simulate before set_receivers) */
+#define ST_ERR_OVERFLOW (-7) /* a fixed-size device structure overflowed (traversal stack) */
+
+#define ST_MEM_HOST 0
+#define ST_MEM_DEVICE 1
+
+/* bits of st_sim_params.components and indices of the spectra's first dimension */
+#define ST_COMP_SPECULAR 1   /* index 0: H(f), Eq. 4 */
+#define ST_COMP_DIFFRACTION 2 /* index 1: G(f), Eq. 8 */
+#define ST_COMP_DIRECT 4     /* index 2: P(f), Eq. 12 */
+
+typedef struct st_ctx st_ctx;
+typedef struct st_scene st_scene;
+
+/* Pre-processing parameters (Sec. III-B and III-D). */
+typedef struct st_curv_params {
+    float eta;                  /* global scale of Eq. 1 (default 1) */
+    float area_ref;             /* w(A) = clamp(A / area_ref, 0, 1), m^2 (default 1e-4) */
+    double dither;              /* CDF dither amplitude relative to the mesh-mean weight (default 1e-3) */
+    float hc_frac;              /* a triangle is high-curvature if C_i >= hc_frac * max_mesh C (default 0.25) */
+    int32_t samples_per_vertex; /* diffraction samples per high-curvature vertex (default 64) */
+    int64_t sample_budget;      /* cap on the total sample count, < 0 = none (default 4,000,000) */
+    uint64_t seed;              /* Philox key of the CDF dither (default 0) */
+} st_curv_params;
+
+/* Simulation parameters (Algorithm 1, Eq. 2-4, 7-8, 11-12). */
+typedef struct st_sim_params {
+    int32_t max_bounces;        /* B: hit points per ray (default 3), 1..8 */
+    double max_distance;        /* a ray ends after the hit whose path length reaches this, m (default 1e9) */
+    double c;                   /* speed of sound, m/s (default 343) */
+    double alpha0_db_m;         /* air absorption alpha(f) = alpha0 + alpha1 * f[kHz], dB/m (amplitude) */
+    double alpha1_db_m_khz;     /* (defaults 0 and 0.033) */
+    float t_min;                /* minimum hit distance along a ray, m (default 1e-5) */
+    float los_eps;              /* visibility rays stop this short of their target, m (default 1e-4) */
+    int32_t reflection_mode;    /* 0: product of k over all hits so far; 1: k of the last hit only */
+    int32_t components;         /* ST_COMP_* mask (default all) */
+    float theta_inc_rad;        /* diffraction incidence constraint, |n . v_s| >= cos(theta) (default 80 deg) */
+    float direct_gain;          /* I_p of Eq. 11 (default 1) */
+    uint64_t seed;              /* Philox key of the diffraction samples (default 0) */
+    uint32_t pose_index;        /* Philox counter word distinguishing poses (default 0) */
+} st_sim_params;
+
+/* Optional statistics of one simulate call (filled after the stream is synchronised). */
+typedef struct st_stats {
+    int64_t rays;               /* emitter rays */
+    int64_t closest_queries;    /* closest-hit ray segments traced */
+    int64_t shadow_queries;     /* any-hit visibility segments traced */
+    int64_t records;            /* specular hit records */
+    int64_t visible_records;    /* records whose receiver point is visible */
+    int64_t candidates;         /* diffraction samples drawn */
+    int64_t candidates_kept;    /* diffraction samples passing the filters */
+    int64_t terms;              /* (path, microphone, bin) terms accumulated */
+    float ms_trace;             /* device time of ray generation + bounces, ms */
+    float ms_diffraction;       /* device time of sampling + filters, ms */
+    float ms_accumulate;        /* device time of spectrum accumulation, ms */
+    float ms_total;             /* device time of the whole call, ms */
+    float ms_accum_kernel;      /* device time of the accumulator kernel launches alone, ms */
+    int32_t accum_launches;     /* number of accumulator kernel launches */
+    int64_t kernel_launches;    /* kernels launched by this call */
+} st_stats;
+
+void st_curv_params_default(st_curv_params* p);
+void st_sim_params_default(st_sim_params* p);
+const char* st_status_string(st_status s);
+/* Message of the last failing call on ctx (owned by ctx, valid until the next call). */
+const char* st_last_error(const st_ctx* ctx);
+
+/* Create a context on `device` issuing work on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  The library allocates its working memory lazily and owns it until destroy. */
+st_status st_create(st_ctx** out, int32_t device, void* cuda_stream);
+st_status st_destroy(st_ctx* ctx);
+st_status st_set_stream(st_ctx* ctx, void* cuda_stream);
+
+/* Scene (Sec. III-B: the registered objects' meshes).  verts [n_verts][3], tris [n_tris][3]
+ * (indices into verts), tri_material [n_tris] (index into the material table), tri_object
+ * [n_tris] (mesh id >= 0; diffraction CDFs are built per mesh).  Indices out of range or
+ * non-finite vertices give ST_ERR_MESH.  The scene belongs to ctx and must be destroyed before it. */
+st_status st_scene_load(st_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                        const int32_t* tri_material, const int32_t* tri_object, int32_t mem, st_scene** out);
+/* Materials (Sec. III-B): per-band reflection magnitude k [n_mat][n_bands], lobe opening angle
+ * beta [n_mat][n_bands] (rad, > 0) and diffraction coefficient I_d [n_mat][n_bands] at band
+ * centres band_hz [n_bands] (ascending).  Host pointers.  Values are linear in frequency between
+ * centres (beta through the lobe exponent 1/(2 beta^2)) and constant beyond the end bands. */
+st_status st_scene_set_materials(st_scene* scene, int32_t n_mat, int32_t n_bands, const float* band_hz,
+                                 const float* k, const float* beta, const float* diffr);
+/* Build the device LBVH, triangle normals, curvature (G_v, C_i) and diffraction CDFs.
+ * params may be NULL (defaults).  Synchronises the stream once (to size the sample buffers). */
+st_status st_scene_precompute(st_scene* scene, const st_curv_params* params);
+/* Copy per-vertex G [n_verts], per-triangle C [n_tris] and the diffraction sample count per
+ * mesh out (any may be NULL).  n_samples has one entry per mesh id up to max(tri_object). */
+st_status st_scene_get_curvature(st_scene* scene, float* G, float* C, int64_t* n_samples, int32_t mem);
+st_status st_scene_destroy(st_scene* scene);
+
+/* Emitter (Algorithm 1 inputs): position, orientation quaternion (w, x, y, z; forward is +x
+ * rotated by it), n_rays local unit directions dirs [n_rays][3], an optional directivity table
+ * [n_theta][n_bins] over the angle to forward in [0, pi] (NULL = omni; n_bins must equal the
+ * frequency grid at simulate time) and the diffraction field of view half-angle (>= pi: off). */
+st_status st_set_emitter(st_ctx* ctx, const float pos[3], const float quat[4], int64_t n_rays, const float* dirs,
+                         const float* dir_table, int32_t n_theta, float fov_half_rad, int32_t mem);
+/* Receivers: positions [n_mics][3]; optional orientations [n_mics][4] and directivity tables
+ * [n_mics][n_el][n_az][n_bands] on the (az, el) grid az = -pi + 2 pi i / n_az, el = -pi/2 +
+ * pi j / (n_el - 1) of the arrival direction in the microphone frame, bands = the materials'
+ * band centres (NULL = omni). */
+st_status st_set_receivers(st_ctx* ctx, int32_t n_mics, const float* pos, const float* quats,
+                           const float* tables, int32_t n_el, int32_t n_az, int32_t n_bands, int32_t mem);
+/* Uniform frequency grid f_k = f_lo + k (f_hi - f_lo) / (n_bins - 1), k = 0..n_bins-1, Hz. */
+st_status st_set_frequencies(st_ctx* ctx, int32_t n_bins, double f_lo, double f_hi);
+
+/* One simulation: tracing, diffraction, direct path, accumulation.  spectra_out is caller-owned
+ * device memory of 3 * n_mics * n_bins complex64 values laid out [component][mic][bin]; every
+ * element is written (components not requested are zero).  params NULL = defaults.  The path
+ * records are kept in ctx for st_get_paths / st_backward until the next simulate. */
+st_status st_simulate(st_ctx* ctx, st_scene* scene, const st_sim_params* params, void* spectra_out,
+                      st_stats* stats);
+/* Same, with host input/output: spectra_out is host memory (3 * n_mics * n_bins complex64). */
+st_status st_simulate_host(st_ctx* ctx, st_scene* scene, const st_sim_params* params, void* spectra_out,
+                           st_stats* stats);
+
+/* Path records of the last simulate, [n_rays][B] each (any pointer may be NULL): hit triangle
+ * (-1 = none), hit point [3], reflected direction [3], path length (float64), receiver-point
+ * visibility.  Synchronises. */
+st_status st_get_paths(st_ctx* ctx, int32_t* tri, float* point, float* dir, double* r, uint8_t* los, int32_t mem);
+/* Diffraction samples of the last simulate: *n_out = count; triangle, point [3], kept flag
+ * (arrays of at least `capacity` entries; any may be NULL).  Synchronises. */
+st_status st_get_diffraction(st_ctx* ctx, int64_t* n_out, int32_t* tri, float* point, uint8_t* keep,
+                             int64_t capacity, int32_t mem);
+/* Direct-path visibility per microphone of the last simulate. */
+st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SONOTRACE_H */

@@ -205,9 +205,11 @@ def diffraction_filter(scene: Scene, s, q, cand_tri, cand_p, fov_half=math.pi, c
                        t_min=1e-5, los_eps=1e-4, nthreads=0):
     s, q = _c(s, np.float32), _c(q, np.float32)
     ct, cp = _c(cand_tri, np.int32), _c(cand_p, np.float32)
-    cos_fov = np.float32(-2.0) if fov_half >= math.pi else np.float32(math.cos(fov_half))
+    # the angles are float32 parameters of the interface: cos is taken of the float32 value
+    f32 = lambda x: float(np.float32(x))
+    cos_fov = np.float32(-2.0) if f32(fov_half) >= f32(math.pi) else np.float32(math.cos(f32(fov_half)))
     if cos_inc is None:
-        cos_inc = np.float32(math.cos(math.radians(theta_inc_deg)))
+        cos_inc = np.float32(math.cos(f32(math.radians(theta_inc_deg))))
     keep = np.zeros(len(ct), dtype=np.uint8)
     lib().ora_diffraction_filter(scene.h, _p(scene.nrm), _p(s), _p(q), len(ct), _p(ct), _p(cp), float(cos_fov),
                                  float(cos_inc), t_min, los_eps, _p(keep), nthreads)

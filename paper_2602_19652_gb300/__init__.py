@@ -1,0 +1,198 @@
+"""GB300 acoustic path tracing (SonoTraceUE hot path, arXiv 2602.19652) -- Python binding.
+
+Thin wrapper over the C ABI of libsonotrace (include/sonotrace.h).  PyTorch provides device
+memory and the current CUDA stream; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: without the built library or a GPU the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
+                   SimParams, SonotraceError, Stats, check, load)
+
+__all__ = ["Context", "Scene", "CurvParams", "SimParams", "Stats", "SonotraceError", "sim_params", "curv_params",
+           "ST_COMP_SPECULAR", "ST_COMP_DIFFRACTION", "ST_COMP_DIRECT"]
+
+
+def curv_params(**kw) -> CurvParams:
+    p = CurvParams()
+    load().st_curv_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def sim_params(**kw) -> SimParams:
+    p = SimParams()
+    load().st_sim_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _dev(t, dtype):
+    t = torch.as_tensor(t, dtype=dtype, device="cuda").contiguous()
+    return t
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One library context on one GPU, issuing work on a CUDA stream (default: torch's current)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.L = load()
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        check(self.L.st_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+        self._keep = []
+        self.M = self.F = 0
+        self.N = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.st_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status):
+        check(status, self.h)
+
+    # -------------------------------------------------------------- inputs
+    def set_frequencies(self, n_bins: int, f_lo: float, f_hi: float):
+        self._check(self.L.st_set_frequencies(self.h, int(n_bins), float(f_lo), float(f_hi)))
+        self.F = int(n_bins)
+
+    def set_emitter(self, pos, quat, dirs, table=None, fov_half: float = math.pi):
+        pos = np.ascontiguousarray(pos, np.float32)
+        quat = np.ascontiguousarray(quat, np.float32)
+        d = _dev(dirs, torch.float32)
+        tab = None if table is None else _dev(table, torch.float32)
+        self._check(self.L.st_set_emitter(self.h, pos.ctypes.data_as(C.c_void_p), quat.ctypes.data_as(C.c_void_p),
+                                          int(d.shape[0]), _ptr(d), None if tab is None else _ptr(tab),
+                                          0 if tab is None else int(tab.shape[0]), float(np.float32(fov_half)),
+                                          ST_MEM_DEVICE))
+        self.N = int(d.shape[0])
+
+    def set_receivers(self, mics):
+        m = _dev(mics, torch.float32)
+        self._check(self.L.st_set_receivers(self.h, int(m.shape[0]), _ptr(m), None, None, 0, 0, 0, ST_MEM_DEVICE))
+        self.M = int(m.shape[0])
+
+    # -------------------------------------------------------------- simulate
+    def simulate(self, scene: "Scene", params: SimParams | None = None, out: torch.Tensor | None = None,
+                 stats: bool = False):
+        """Returns complex64 [3][M][F] spectra on the device (specular, diffraction, direct)."""
+        if out is None:
+            out = torch.empty((3, self.M, self.F), dtype=torch.complex64, device=f"cuda:{self.device}")
+        st = Stats() if stats else None
+        self._check(self.L.st_simulate(self.h, scene.h, None if params is None else C.byref(params), _ptr(out),
+                                       None if st is None else C.byref(st)))
+        return (out, st) if stats else out
+
+    def simulate_host(self, scene: "Scene", params: SimParams | None = None, out: np.ndarray | None = None):
+        if out is None:
+            out = np.empty((3, self.M, self.F), dtype=np.complex64)
+        self._check(self.L.st_simulate_host(self.h, scene.h, None if params is None else C.byref(params),
+                                            out.ctypes.data_as(C.c_void_p), None))
+        return out
+
+    def paths(self, B: int):
+        N = self.N
+        tri = np.empty((N, B), np.int32)
+        p = np.empty((N, B, 3), np.float32)
+        d = np.empty((N, B, 3), np.float32)
+        r = np.empty((N, B), np.float64)
+        los = np.empty((N, B), np.uint8)
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(self.L.st_get_paths(self.h, cp(tri), cp(p), cp(d), cp(r), cp(los), ST_MEM_HOST))
+        return dict(tri=tri, p=p, d=d, r=r, los=los)
+
+    def diffraction(self):
+        n = C.c_int64(0)
+        self._check(self.L.st_get_diffraction(self.h, C.byref(n), None, None, None, 0, ST_MEM_HOST))
+        K = n.value
+        tri = np.empty(max(K, 1), np.int32)
+        p = np.empty((max(K, 1), 3), np.float32)
+        keep = np.empty(max(K, 1), np.uint8)
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(self.L.st_get_diffraction(self.h, C.byref(n), cp(tri), cp(p), cp(keep), K, ST_MEM_HOST))
+        return tri[:K], p[:K], keep[:K]
+
+    def direct_visibility(self):
+        v = np.empty(self.M, np.uint8)
+        self._check(self.L.st_get_direct_visibility(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST))
+        return v
+
+
+class Scene:
+    """A triangle scene owned by a Context: load, set materials, precompute (BVH, curvature, CDFs)."""
+
+    def __init__(self, ctx: Context, verts, tris, tri_mat, tri_obj):
+        self.ctx = ctx
+        v = np.ascontiguousarray(verts, np.float32)
+        t = np.ascontiguousarray(tris, np.int32)
+        m = np.ascontiguousarray(tri_mat, np.int32)
+        o = np.ascontiguousarray(tri_obj, np.int32)
+        h = C.c_void_p()
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+        ctx._check(ctx.L.st_scene_load(ctx.h, cp(v), len(v), cp(t), len(t), cp(m), cp(o), ST_MEM_HOST, C.byref(h)))
+        self.h = h
+        self.n_verts, self.n_tris = len(v), len(t)
+        self.n_obj = int(o.max()) + 1
+
+    def set_materials(self, band_hz, k, beta, diffr):
+        b = np.ascontiguousarray(band_hz, np.float32)
+        k = np.ascontiguousarray(k, np.float32)
+        be = np.ascontiguousarray(beta, np.float32)
+        d = np.ascontiguousarray(diffr, np.float32)
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self.ctx._check(self.ctx.L.st_scene_set_materials(self.h, k.shape[0], k.shape[1], cp(b), cp(k), cp(be), cp(d)))
+
+    def precompute(self, params: CurvParams | None = None):
+        self.ctx._check(self.ctx.L.st_scene_precompute(self.h, None if params is None else C.byref(params)))
+
+    def curvature(self):
+        G = np.empty(self.n_verts, np.float32)
+        Cm = np.empty(self.n_tris, np.float32)
+        ns = np.empty(self.n_obj, np.int64)
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self.ctx._check(self.ctx.L.st_scene_get_curvature(self.h, cp(G), cp(Cm), cp(ns), ST_MEM_HOST))
+        return G, Cm, ns
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.L.st_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_workload(ctx: Context, wl, curv: CurvParams | None = None) -> Scene:
+    """Load a synthetic workload's scene and sensor into ctx (scene precomputed)."""
+    sc = Scene(ctx, wl.verts, wl.tris, wl.tri_mat, wl.tri_obj)
+    sc.set_materials(wl.band_hz, wl.k_band, wl.beta_band, wl.diff_band)
+    sc.precompute(curv)
+    ctx.set_frequencies(wl.n_bins, wl.f_lo, wl.f_hi)
+    ctx.set_emitter(wl.emitter, wl.emitter_quat, wl.dirs, wl.emitter_table, wl.fov_half)
+    ctx.set_receivers(wl.mics)
+    return sc

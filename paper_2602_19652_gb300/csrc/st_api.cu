@@ -1,0 +1,825 @@
+// C ABI of libsonotrace: contexts, scenes, inputs and the simulate pipeline.
+//
+// One simulate call issues, on the context's stream:
+//   receiver reference point -> B bounce launches (Algorithm 1) -> visible-record compaction and
+//   gathering -> diffraction sampling + filters + compaction (Sec. III-D) -> direct visibility and
+//   spectrum (Sec. III-E) -> specular / diffraction accumulation and fixed-order chunk reduction.
+// No host synchronisation happens inside unless statistics are requested.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "st_internal.cuh"
+
+using namespace st;
+
+namespace st {
+
+cudaError_t grow(DevBuf& b, size_t bytes) {
+    if (bytes <= b.cap && b.p) return cudaSuccess;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.cap = want;
+    return cudaSuccess;
+}
+
+namespace {
+int64_t g_launches = 0;  // host-side count of kernel launches issued by this library (not thread-safe)
+}
+void note_launch() { ++g_launches; }
+int64_t launch_count() { return g_launches; }
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+}  // namespace st
+
+struct st_ctx {
+    int32_t device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // emitter
+    bool has_emitter = false;
+    float s[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0};
+    int64_t N = 0;
+    DevBuf dirs, etab;
+    int32_t n_theta = 0;
+    float fov_half = 4.0f;
+    // receivers
+    bool has_rx = false;
+    int32_t M = 0;
+    DevBuf mics;
+    // frequencies
+    bool has_freq = false;
+    int32_t F = 0;
+    double f_lo = 0, f_hi = 0;
+    // tables cache
+    AccumTables tables;
+    const void* tables_scene = nullptr;
+    uint64_t tables_version = 0;
+    double tables_key[5] = {0, 0, 0, 0, 0};
+    // work buffers
+    DevBuf st_o[3], st_d[3], st_r, st_prev, q0, q1, counts, queries, flags, R, rec_tri, rec_p, rec_d, rec_r, rec_los;
+    DevBuf sflags, sscan, sidx, scratch;
+    PathList paths;
+    DevBuf cand_tri, cand_p, keep, dvis, partial;
+    DevBuf host_out;
+    int64_t last_N = 0, last_K = 0;
+    int32_t last_B = 0, last_M = 0, last_F = 0;
+    bool has_last = false;
+    // last simulate parameters (for the adjoint)
+    st_sim_params last_params;
+    int32_t last_chunks_spec = 0, last_chunks_diff = 0;
+    cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+struct st_scene {
+    st_ctx* ctx = nullptr;
+    SceneDev S;
+    bool has_materials = false;
+    uint64_t version = 0;
+};
+
+namespace {
+
+st_status fail(st_ctx* c, st_status code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+st_status cuda_fail(st_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA, m);
+}
+
+#define CKC(ctx, x, where)                                   \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+cudaMemcpyKind kind_in(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+uint64_t g_scene_version = 1;
+
+}  // namespace
+
+extern "C" {
+
+void st_curv_params_default(st_curv_params* p) {
+    if (!p) return;
+    p->eta = 1.0f;
+    p->area_ref = 1e-4f;
+    p->dither = 1e-3;
+    p->hc_frac = 0.25f;
+    p->samples_per_vertex = 64;
+    p->sample_budget = 4000000;
+    p->seed = 0;
+}
+
+void st_sim_params_default(st_sim_params* p) {
+    if (!p) return;
+    p->max_bounces = 3;
+    p->max_distance = 1e9;
+    p->c = 343.0;
+    p->alpha0_db_m = 0.0;
+    p->alpha1_db_m_khz = 0.033;
+    p->t_min = 1e-5f;
+    p->los_eps = 1e-4f;
+    p->reflection_mode = 0;
+    p->components = ST_COMP_SPECULAR | ST_COMP_DIFFRACTION | ST_COMP_DIRECT;
+    p->theta_inc_rad = (float)(80.0 * M_PI / 180.0);
+    p->direct_gain = 1.0f;
+    p->seed = 0;
+    p->pose_index = 0;
+}
+
+const char* st_status_string(st_status s) {
+    switch (s) {
+        case ST_OK: return "ok";
+        case ST_ERR_ARG: return "invalid argument";
+        case ST_ERR_CUDA: return "CUDA error";
+        case ST_ERR_OOM: return "out of device memory";
+        case ST_ERR_MESH: return "invalid mesh";
+        case ST_ERR_TIMEOUT: return "device wait timed out";
+        case ST_ERR_STATE: return "call out of order";
+        case ST_ERR_OVERFLOW: return "device structure overflow";
+        default: return "unknown status";
+    }
+}
+
+const char* st_last_error(const st_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+st_status st_create(st_ctx** out, int32_t device, void* cuda_stream) {
+    if (!out) return ST_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return ST_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return ST_ERR_CUDA;
+    st_ctx* c = new st_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    for (auto& e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            delete c;
+            return ST_ERR_CUDA;
+        }
+    *out = c;
+    return ST_OK;
+}
+
+st_status st_destroy(st_ctx* c) {
+    if (!c) return ST_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (DevBuf* b : {&c->dirs, &c->etab, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
+                      &c->st_d[2], &c->st_r, &c->st_prev, &c->q0, &c->q1, &c->counts, &c->queries, &c->flags, &c->R, &c->rec_tri,
+                      &c->rec_p, &c->rec_d, &c->rec_r, &c->rec_los, &c->sflags, &c->sscan, &c->sidx, &c->scratch,
+                      &c->cand_tri, &c->cand_p, &c->keep, &c->dvis, &c->partial, &c->host_out, &c->tables.lk,
+                      &c->tables.g2, &c->tables.lid, &c->tables.qhi, &c->tables.qlo})
+        release(*b);
+    PathList& P = c->paths;
+    for (DevBuf* b : {&P.px, &P.py, &P.pz, &P.dx, &P.dy, &P.dz, &P.rhi, &P.rlo, &P.chain_lo, &P.chain_hi, &P.meta, &P.dep})
+        release(*b);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+    return ST_OK;
+}
+
+st_status st_set_stream(st_ctx* c, void* stream) {
+    if (!c) return ST_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return ST_OK;
+}
+
+// ------------------------------------------------------------------ scene
+st_status st_scene_load(st_ctx* c, const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                        const int32_t* tri_material, const int32_t* tri_object, int32_t mem, st_scene** out) {
+    if (!c || !out) return ST_ERR_ARG;
+    *out = nullptr;
+    if (!verts || !tris || !tri_material || !tri_object || n_verts <= 0 || n_tris <= 0 ||
+        n_tris >= (1ll << 28) || n_verts >= (1ll << 31) || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
+        return fail(c, ST_ERR_ARG, "scene_load: null pointer or size out of range (1..2^28 triangles)");
+    cudaSetDevice(c->device);
+    st_scene* sc = new st_scene();
+    sc->ctx = c;
+    SceneDev& S = sc->S;
+    S.n_verts = n_verts;
+    S.n_tris = n_tris;
+    cudaError_t e;
+    if ((e = grow(S.verts, (size_t)n_verts * 12)) != cudaSuccess || (e = grow(S.tris, (size_t)n_tris * 12)) != cudaSuccess ||
+        (e = grow(S.tri_mat, (size_t)n_tris * 4)) != cudaSuccess || (e = grow(S.tri_obj, (size_t)n_tris * 4)) != cudaSuccess) {
+        delete sc;
+        return cuda_fail(c, e, "scene_load alloc");
+    }
+    cudaMemcpyAsync(S.verts.p, verts, (size_t)n_verts * 12, kind_in(mem), c->stream);
+    cudaMemcpyAsync(S.tris.p, tris, (size_t)n_tris * 12, kind_in(mem), c->stream);
+    cudaMemcpyAsync(S.tri_mat.p, tri_material, (size_t)n_tris * 4, kind_in(mem), c->stream);
+    cudaMemcpyAsync(S.tri_obj.p, tri_object, (size_t)n_tris * 4, kind_in(mem), c->stream);
+    // mesh count: max object id + 1 (host side needs it to size per-mesh arrays)
+    std::vector<int32_t> obj(n_tris);
+    e = cudaMemcpyAsync(obj.data(), S.tri_obj.p, (size_t)n_tris * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        delete sc;
+        return cuda_fail(c, e, "scene_load copy");
+    }
+    int32_t mx = -1;
+    for (int32_t o : obj) {
+        if (o < 0) {
+            delete sc;
+            return fail(c, ST_ERR_MESH, "scene_load: negative object id");
+        }
+        mx = std::max(mx, o);
+    }
+    if (mx >= (1 << 24)) {
+        delete sc;
+        return fail(c, ST_ERR_MESH, "scene_load: object ids must be < 2^24");
+    }
+    S.n_obj = mx + 1;
+    sc->version = g_scene_version++;
+    *out = sc;
+    return ST_OK;
+}
+
+st_status st_scene_set_materials(st_scene* sc, int32_t n_mat, int32_t n_bands, const float* band_hz, const float* k,
+                                 const float* beta, const float* diffr) {
+    if (!sc) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (n_mat <= 0 || n_mat > 255 || n_bands <= 0 || n_bands > 64 || !band_hz || !k || !beta || !diffr)
+        return fail(c, ST_ERR_ARG, "set_materials: 1..255 materials, 1..64 bands, non-null tables");
+    for (int b = 1; b < n_bands; ++b)
+        if (!(band_hz[b] > band_hz[b - 1])) return fail(c, ST_ERR_ARG, "set_materials: band centres must ascend");
+    for (int i = 0; i < n_mat * n_bands; ++i)
+        if (!(beta[i] > 0.0f) || !(k[i] >= 0.0f) || !(diffr[i] >= 0.0f) || !isfinite(k[i]) || !isfinite(beta[i]))
+            return fail(c, ST_ERR_ARG, "set_materials: need beta > 0, k >= 0, I_d >= 0, finite");
+    SceneDev& S = sc->S;
+    S.n_mat = n_mat;
+    S.n_bands = n_bands;
+    S.band_hz.assign(band_hz, band_hz + n_bands);
+    S.k_band.assign(k, k + (size_t)n_mat * n_bands);
+    S.beta_band.assign(beta, beta + (size_t)n_mat * n_bands);
+    S.diff_band.assign(diffr, diffr + (size_t)n_mat * n_bands);
+    sc->has_materials = true;
+    sc->version = g_scene_version++;
+    return ST_OK;
+}
+
+st_status st_scene_precompute(st_scene* sc, const st_curv_params* params) {
+    if (!sc) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (!sc->has_materials) return fail(c, ST_ERR_STATE, "scene_precompute: set materials first");
+    st_curv_params p;
+    st_curv_params_default(&p);
+    if (params) p = *params;
+    if (!(p.area_ref > 0.0f) || p.samples_per_vertex < 0 || !(p.dither >= 0.0))
+        return fail(c, ST_ERR_ARG, "scene_precompute: area_ref > 0, samples_per_vertex >= 0, dither >= 0");
+    cudaSetDevice(c->device);
+    CurvParamsDev cp{p.eta, p.area_ref, p.hc_frac, p.dither, p.samples_per_vertex, p.sample_budget, p.seed};
+    bool mesh_err = false;
+    std::string msg;
+    cudaError_t e = scene_build(sc->S, cp, c->stream, &mesh_err, &msg);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scene_precompute");
+    if (mesh_err) return fail(c, ST_ERR_MESH, "scene_precompute: " + msg);
+    sc->version = g_scene_version++;
+    return ST_OK;
+}
+
+st_status st_scene_get_curvature(st_scene* sc, float* G, float* C, int64_t* n_samples, int32_t mem) {
+    if (!sc) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (!sc->S.built) return fail(c, ST_ERR_STATE, "scene_get_curvature: precompute first");
+    cudaSetDevice(c->device);
+    if (G) CKC(c, cudaMemcpyAsync(G, sc->S.G.p, (size_t)sc->S.n_verts * 4, kind_out(mem), c->stream), "get G");
+    if (C) CKC(c, cudaMemcpyAsync(C, sc->S.C.p, (size_t)sc->S.n_tris * 4, kind_out(mem), c->stream), "get C");
+    if (n_samples)
+        CKC(c, cudaMemcpyAsync(n_samples, sc->S.n_samples.p, (size_t)sc->S.n_obj * 8, kind_out(mem), c->stream),
+            "get n_samples");
+    CKC(c, cudaStreamSynchronize(c->stream), "get curvature sync");
+    return ST_OK;
+}
+
+st_status st_scene_destroy(st_scene* sc) {
+    if (!sc) return ST_ERR_ARG;
+    cudaSetDevice(sc->ctx->device);
+    cudaStreamSynchronize(sc->ctx->stream);
+    SceneDev& S = sc->S;
+    for (DevBuf* b : {&S.verts, &S.tris, &S.tri_mat, &S.tri_obj, &S.nrm, &S.nodes, &S.tri_v, &S.G, &S.C, &S.mesh_tris,
+                      &S.mesh_off, &S.cdf, &S.n_samples, &S.sample_off})
+        release(*b);
+    if (sc->ctx->tables_scene == sc) sc->ctx->tables_scene = nullptr;
+    delete sc;
+    return ST_OK;
+}
+
+// ------------------------------------------------------------------ sensor inputs
+st_status st_set_emitter(st_ctx* c, const float pos[3], const float quat[4], int64_t n_rays, const float* dirs,
+                         const float* dir_table, int32_t n_theta, float fov_half_rad, int32_t mem) {
+    if (!c) return ST_ERR_ARG;
+    if (!pos || !quat || n_rays < 0 || n_rays > (1ll << 31) - 1 || (n_rays > 0 && !dirs) ||
+        (dir_table && n_theta < 2) || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
+        return fail(c, ST_ERR_ARG, "set_emitter: bad argument");
+    cudaSetDevice(c->device);
+    float hp[3], hq[4];
+    if (mem == ST_MEM_DEVICE) {
+        CKC(c, cudaMemcpyAsync(hp, pos, 12, cudaMemcpyDeviceToHost, c->stream), "set_emitter pos");
+        CKC(c, cudaMemcpyAsync(hq, quat, 16, cudaMemcpyDeviceToHost, c->stream), "set_emitter quat");
+        CKC(c, cudaStreamSynchronize(c->stream), "set_emitter sync");
+    } else {
+        memcpy(hp, pos, 12);
+        memcpy(hq, quat, 16);
+    }
+    memcpy(c->s, hp, 12);
+    memcpy(c->q, hq, 16);
+    c->N = n_rays;
+    if (n_rays > 0) {
+        CKC(c, grow(c->dirs, (size_t)n_rays * 12), "set_emitter alloc");
+        CKC(c, cudaMemcpyAsync(c->dirs.p, dirs, (size_t)n_rays * 12, kind_in(mem), c->stream), "set_emitter dirs");
+    }
+    c->n_theta = dir_table ? n_theta : 0;
+    c->fov_half = fov_half_rad;
+    c->has_emitter = true;
+    if (dir_table) {
+        // the bin count is known at simulate time; keep the raw table and check its size there
+        if (!c->has_freq) return fail(c, ST_ERR_STATE, "set_emitter: set the frequency grid before a directivity table");
+        const size_t bytes = (size_t)n_theta * c->F * 4;
+        CKC(c, grow(c->etab, bytes), "set_emitter table alloc");
+        CKC(c, cudaMemcpyAsync(c->etab.p, dir_table, bytes, kind_in(mem), c->stream), "set_emitter table");
+    }
+    return ST_OK;
+}
+
+st_status st_set_receivers(st_ctx* c, int32_t n_mics, const float* pos, const float* quats, const float* tables,
+                           int32_t n_el, int32_t n_az, int32_t n_bands, int32_t mem) {
+    if (!c) return ST_ERR_ARG;
+    if (n_mics <= 0 || n_mics > kMaxMics || !pos || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
+        return fail(c, ST_ERR_ARG, "set_receivers: 1..4096 microphones, non-null positions");
+    if (tables) return fail(c, ST_ERR_ARG, "set_receivers: receiver directivity tables are not supported yet");
+    (void)quats;
+    (void)n_el;
+    (void)n_az;
+    (void)n_bands;
+    cudaSetDevice(c->device);
+    CKC(c, grow(c->mics, (size_t)n_mics * 12), "set_receivers alloc");
+    CKC(c, cudaMemcpyAsync(c->mics.p, pos, (size_t)n_mics * 12, kind_in(mem), c->stream), "set_receivers copy");
+    c->M = n_mics;
+    c->has_rx = true;
+    return ST_OK;
+}
+
+st_status st_set_frequencies(st_ctx* c, int32_t n_bins, double f_lo, double f_hi) {
+    if (!c) return ST_ERR_ARG;
+    if (n_bins <= 0 || n_bins > (1 << 20) || !(f_lo > 0.0) || !(f_hi >= f_lo) || (n_bins > 1 && !(f_hi > f_lo)))
+        return fail(c, ST_ERR_ARG, "set_frequencies: 1..2^20 bins, 0 < f_lo < f_hi");
+    c->F = n_bins;
+    c->f_lo = f_lo;
+    c->f_hi = f_hi;
+    c->has_freq = true;
+    return ST_OK;
+}
+
+// ------------------------------------------------------------------ simulate
+static st_status ensure_paths(st_ctx* c, int64_t n) {
+    PathList& P = c->paths;
+    if (P.n_max >= n) return ST_OK;
+    for (DevBuf* b : {&P.px, &P.py, &P.pz, &P.dx, &P.dy, &P.dz, &P.rhi, &P.rlo, &P.chain_lo, &P.chain_hi, &P.meta, &P.dep})
+        CKC(c, grow(*b, (size_t)std::max<int64_t>(n, 1) * 4), "path list alloc");
+    P.n_max = n;
+    return ST_OK;
+}
+
+st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void* spectra_out, st_stats* stats) {
+    if (!c || !sc || !spectra_out) return fail(c, ST_ERR_ARG, "simulate: null argument");
+    if (!c->has_emitter || !c->has_rx || !c->has_freq)
+        return fail(c, ST_ERR_STATE, "simulate: set emitter, receivers and frequencies first");
+    if (!sc->S.built || !sc->has_materials) return fail(c, ST_ERR_STATE, "simulate: scene not precomputed");
+    st_sim_params p;
+    st_sim_params_default(&p);
+    if (params) p = *params;
+    if (p.max_bounces < 1 || p.max_bounces > kMaxBounces || !(p.c > 0.0) || !(p.t_min >= 0.0f) ||
+        !(p.los_eps >= 0.0f) || p.reflection_mode < 0 || p.reflection_mode > 1)
+        return fail(c, ST_ERR_ARG, "simulate: 1..8 bounces, c > 0, t_min >= 0, los_eps >= 0");
+    if (c->n_theta > 0 && c->etab.cap < (size_t)c->n_theta * c->F * 4)
+        return fail(c, ST_ERR_ARG, "simulate: emitter table was set for a different bin count");
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    SceneDev& S = sc->S;
+    const int64_t N = c->N;
+    const int32_t B = p.max_bounces, M = c->M, F = c->F;
+    const int64_t NB = N * B;
+    if (stats) CKC(c, cudaEventRecord(c->ev[0], s), "event");
+    const int64_t launches0 = launch_count();
+
+    // ---- per-bin tables (cached per scene materials, grid and constants)
+    const double key[5] = {(double)F, c->f_lo, c->f_hi, p.c, 0.0};
+    if (c->tables_scene != sc || c->tables_version != sc->version || memcmp(key, c->tables_key, sizeof(key)) != 0) {
+        CKC(c, build_accum_tables(c->tables, S, F, c->f_lo, c->f_hi, p.c, p.alpha0_db_m, p.alpha1_db_m_khz, s),
+            "tables");
+        c->tables_scene = sc;
+        c->tables_version = sc->version;
+        memcpy(c->tables_key, key, sizeof(key));
+    }
+    AccumTables& T = c->tables;
+
+    // ---- buffers
+    const int64_t K = (p.components & ST_COMP_DIFFRACTION) ? S.total_samples : 0;
+    const int64_t nflag = std::max<int64_t>(std::max<int64_t>(NB, K), 1);
+    for (int k = 0; k < 3; ++k) {
+        CKC(c, grow(c->st_o[k], (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+        CKC(c, grow(c->st_d[k], (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    }
+    CKC(c, grow(c->st_r, (size_t)std::max<int64_t>(N, 1) * 8), "alloc");
+    CKC(c, grow(c->st_prev, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    CKC(c, grow(c->q0, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    CKC(c, grow(c->q1, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    CKC(c, grow(c->counts, 64), "alloc");
+    CKC(c, grow(c->queries, 16), "alloc");
+    CKC(c, grow(c->flags, 16), "alloc");
+    CKC(c, grow(c->R, 16), "alloc");
+    CKC(c, grow(c->rec_tri, (size_t)std::max<int64_t>(NB, 1) * 4), "alloc");
+    CKC(c, grow(c->rec_p, (size_t)std::max<int64_t>(NB, 1) * 12), "alloc");
+    CKC(c, grow(c->rec_d, (size_t)std::max<int64_t>(NB, 1) * 12), "alloc");
+    CKC(c, grow(c->rec_r, (size_t)std::max<int64_t>(NB, 1) * 8), "alloc");
+    CKC(c, grow(c->rec_los, (size_t)std::max<int64_t>(NB, 1)), "alloc");
+    CKC(c, grow(c->sflags, (size_t)nflag * 4), "alloc");
+    CKC(c, grow(c->sscan, (size_t)nflag * 4), "alloc");
+    CKC(c, grow(c->sidx, (size_t)nflag * 4), "alloc");
+    CKC(c, grow(c->scratch, scan_scratch_bytes(nflag)), "alloc");
+    CKC(c, grow(c->dvis, (size_t)M), "alloc");
+    st_status ps = ensure_paths(c, std::max<int64_t>(NB, K));
+    if (ps != ST_OK) return ps;
+    if (K > 0) {
+        CKC(c, grow(c->cand_tri, (size_t)K * 4), "alloc");
+        CKC(c, grow(c->cand_p, (size_t)K * 12), "alloc");
+        CKC(c, grow(c->keep, (size_t)K), "alloc");
+    }
+    const int32_t chunks_spec = accum_chunks(NB, M, F);
+    const int32_t chunks_diff = accum_chunks(K, M, F);
+    const int32_t chunks = std::max(chunks_spec, chunks_diff);
+    CKC(c, grow(c->partial, (size_t)chunks * M * F * 8), "alloc");
+
+    float2* out = static_cast<float2*>(spectra_out);
+    const int64_t MF = (int64_t)M * F;
+    CKC(c, cudaMemsetAsync(out, 0, (size_t)3 * MF * 8, s), "memset out");
+    CKC(c, cudaMemsetAsync(c->flags.p, 0, 16, s), "memset");
+    CKC(c, cudaMemsetAsync(c->counts.p, 0, 64, s), "memset");
+    CKC(c, cudaMemsetAsync(c->queries.p, 0, 16, s), "memset");
+    unsigned long long* qctr = ptr<unsigned long long>(c->queries);
+    CKC(c, cudaMemsetAsync(c->rec_tri.p, 0xff, (size_t)std::max<int64_t>(NB, 1) * 4, s), "memset");
+    CKC(c, cudaMemsetAsync(c->rec_los.p, 0, (size_t)std::max<int64_t>(NB, 1), s), "memset");
+    CKC(c, cudaMemsetAsync(c->rec_r.p, 0, (size_t)std::max<int64_t>(NB, 1) * 8, s), "memset");
+    CKC(c, cudaMemsetAsync(c->rec_p.p, 0, (size_t)std::max<int64_t>(NB, 1) * 12, s), "memset");
+    CKC(c, cudaMemsetAsync(c->rec_d.p, 0, (size_t)std::max<int64_t>(NB, 1) * 12, s), "memset");
+    uint32_t* cnt = ptr<uint32_t>(c->counts);  // [0],[1] queue counts, [2] visible records, [3] kept candidates
+    mic_centroid_host_order(ptr<float>(c->mics), M, ptr<float>(c->R), s);
+    CKC(c, cudaGetLastError(), "centroid");
+
+    float fwd[3];
+    {
+        // forward axis = q applied to +x (host float32, the same steps as the device rotation)
+        const float* q = c->q;
+        const float vx = 1.0f, vy = 0.0f, vz = 0.0f;
+        const float cx = q[2] * vz - q[3] * vy, cy = q[3] * vx - q[1] * vz, cz = q[1] * vy - q[2] * vx;
+        const float tx = 2.0f * cx, ty = 2.0f * cy, tz = 2.0f * cz;
+        const float c2x = q[2] * tz - q[3] * ty, c2y = q[3] * tx - q[1] * tz, c2z = q[1] * ty - q[2] * tx;
+        fwd[0] = (vx + q[0] * tx) + c2x;
+        fwd[1] = (vy + q[0] * ty) + c2y;
+        fwd[2] = (vz + q[0] * tz) + c2z;
+    }
+
+    // ---- Algorithm 1
+    if (p.components & ST_COMP_SPECULAR && N > 0) {
+        TraceArgs ta{};
+        ta.nodes = ptr<float4>(S.nodes);
+        ta.tri_v = ptr<float4>(S.tri_v);
+        ta.root = S.root;
+        ta.nrm = ptr<float>(S.nrm);
+        memcpy(ta.s, c->s, 12);
+        memcpy(ta.q, c->q, 16);
+        ta.R = ptr<float>(c->R);
+        ta.dirs = ptr<float>(c->dirs);
+        ta.N = N;
+        ta.B = B;
+        ta.r_max = p.max_distance;
+        ta.t_min = p.t_min;
+        ta.los_eps = p.los_eps;
+        ta.ox = ptr<float>(c->st_o[0]);
+        ta.oy = ptr<float>(c->st_o[1]);
+        ta.oz = ptr<float>(c->st_o[2]);
+        ta.dx = ptr<float>(c->st_d[0]);
+        ta.dy = ptr<float>(c->st_d[1]);
+        ta.dz = ptr<float>(c->st_d[2]);
+        ta.racc = ptr<double>(c->st_r);
+        ta.prev = ptr<int32_t>(c->st_prev);
+        ta.q_in = ptr<uint32_t>(c->q0);
+        ta.q_out = ptr<uint32_t>(c->q1);
+        ta.n_in = cnt + 0;
+        ta.n_out = cnt + 1;
+        ta.rec_tri = ptr<int32_t>(c->rec_tri);
+        ta.rec_p = ptr<float>(c->rec_p);
+        ta.rec_d = ptr<float>(c->rec_d);
+        ta.rec_r = ptr<double>(c->rec_r);
+        ta.rec_los = ptr<uint8_t>(c->rec_los);
+        ta.flags = ptr<uint32_t>(c->flags);
+        ta.queries = qctr;
+        CKC(c, trace_rays(ta, s, 128), "trace");
+    }
+    if (stats) CKC(c, cudaEventRecord(c->ev[1], s), "event");
+
+    // ---- diffraction (Sec. III-D)
+    if (K > 0) {
+        DiffArgs da{};
+        da.nodes = ptr<float4>(S.nodes);
+        da.tri_v = ptr<float4>(S.tri_v);
+        da.root = S.root;
+        da.nrm = ptr<float>(S.nrm);
+        da.verts = ptr<float>(S.verts);
+        da.tris = ptr<int32_t>(S.tris);
+        da.n_obj = S.n_obj;
+        da.mesh_tris = ptr<int32_t>(S.mesh_tris);
+        da.mesh_off = ptr<int64_t>(S.mesh_off);
+        da.cdf = ptr<uint64_t>(S.cdf);
+        da.sample_off = ptr<int64_t>(S.sample_off);
+        da.K = K;
+        da.seed = p.seed;
+        da.pose = p.pose_index;
+        memcpy(da.s, c->s, 12);
+        memcpy(da.fwd, fwd, 12);
+        da.cos_fov = c->fov_half >= (float)M_PI ? -2.0f : (float)cos((double)c->fov_half);
+        da.cos_inc = (float)cos((double)p.theta_inc_rad);
+        da.t_min = p.t_min;
+        da.los_eps = p.los_eps;
+        da.cand_tri = ptr<int32_t>(c->cand_tri);
+        da.cand_p = ptr<float>(c->cand_p);
+        da.keep = ptr<uint8_t>(c->keep);
+        da.flags = ptr<uint32_t>(c->flags);
+        da.queries = qctr;
+        CKC(c, diffraction_sample(da, s), "diffraction");
+    }
+    if (stats) CKC(c, cudaEventRecord(c->ev[2], s), "event");
+
+    const float inv_dtheta = c->n_theta > 1 ? (float)((c->n_theta - 1) / M_PI) : 0.0f;
+    const double l2_10_over_20 = log2(10.0) / 20.0;
+    AccumArgs aa{};
+    aa.mics = ptr<float>(c->mics);
+    aa.M = M;
+    aa.F = F;
+    aa.lk = ptr<float>(T.lk);
+    aa.g2 = ptr<float>(T.g2);
+    aa.lid = ptr<float>(T.lid);
+    aa.qhi = ptr<float>(T.qhi);
+    aa.qlo = ptr<float>(T.qlo);
+    {
+        const double dq = T.df / p.c;
+        aa.dq_hi = (float)dq;
+        aa.dq_lo = (float)(dq - (double)aa.dq_hi);
+        aa.atm2_0 = (float)(-(p.alpha0_db_m + p.alpha1_db_m_khz * c->f_lo / 1000.0) * l2_10_over_20);
+        aa.atm2_step = (float)(-(p.alpha1_db_m_khz * T.df / 1000.0) * l2_10_over_20);
+    }
+    aa.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
+    aa.n_theta = c->n_theta;
+    aa.reflection_mode = p.reflection_mode;
+    aa.partial = ptr<float2>(c->partial);
+
+    GatherArgs ga{};
+    ga.N = N;
+    ga.B = B;
+    ga.rec_tri = ptr<int32_t>(c->rec_tri);
+    ga.rec_p = ptr<float>(c->rec_p);
+    ga.rec_d = ptr<float>(c->rec_d);
+    ga.rec_r = ptr<double>(c->rec_r);
+    ga.rec_los = ptr<uint8_t>(c->rec_los);
+    ga.tri_mat = ptr<int32_t>(S.tri_mat);
+    ga.dirs = ptr<float>(c->dirs);
+    memcpy(ga.q, c->q, 16);
+    memcpy(ga.fwd, fwd, 12);
+    ga.inv_dtheta = inv_dtheta;
+    ga.has_etab = c->n_theta > 0;
+    ga.K = K;
+    ga.cand_tri = ptr<int32_t>(c->cand_tri);
+    ga.cand_p = ptr<float>(c->cand_p);
+    ga.keep = ptr<uint8_t>(c->keep);
+    memcpy(ga.s, c->s, 12);
+    ga.idx = ptr<uint32_t>(c->sidx);
+    ga.out = &c->paths;
+    PathList& PL = c->paths;
+    auto set_paths = [&](AccumArgs& x) {
+        x.px = ptr<float>(PL.px);
+        x.py = ptr<float>(PL.py);
+        x.pz = ptr<float>(PL.pz);
+        x.dx = ptr<float>(PL.dx);
+        x.dy = ptr<float>(PL.dy);
+        x.dz = ptr<float>(PL.dz);
+        x.rhi = ptr<float>(PL.rhi);
+        x.rlo = ptr<float>(PL.rlo);
+        x.chain_lo = ptr<uint32_t>(PL.chain_lo);
+        x.chain_hi = ptr<uint32_t>(PL.chain_hi);
+        x.meta = ptr<uint32_t>(PL.meta);
+        x.dep = ptr<float>(PL.dep);
+    };
+
+    int n_accum = 0;  // bit 0: specular launch issued, bit 1: diffraction launch issued
+    // ---- specular accumulation (Eq. 2-4)
+    if (p.components & ST_COMP_SPECULAR && NB > 0) {
+        CKC(c, flags_visible_records(ptr<int32_t>(c->rec_tri), ptr<uint8_t>(c->rec_los), NB, ptr<uint32_t>(c->sflags), s),
+            "flags");
+        CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, cnt + 2, c->scratch.p, s),
+            "scan");
+        CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, ptr<uint32_t>(c->sidx), s),
+            "compact");
+        ga.count = cnt + 2;
+        CKC(c, gather_specular(ga, s), "gather");
+        AccumArgs x = aa;
+        x.kind = 0;
+        x.n_paths = NB;
+        x.d_count = cnt + 2;
+        set_paths(x);
+        x.n_chunks = chunks_spec;
+        if (stats) CKC(c, cudaEventRecord(c->ev[4], s), "event");
+        CKC(c, accumulate(x, s), "accumulate specular");
+        if (stats) CKC(c, cudaEventRecord(c->ev[5], s), "event");
+        n_accum++;
+        CKC(c, reduce_partials(ptr<float2>(c->partial), chunks_spec, MF, out, s), "reduce");
+    }
+    // ---- diffraction accumulation (Eq. 7-8)
+    if (K > 0) {
+        CKC(c, flags_from_u8(ptr<uint8_t>(c->keep), K, ptr<uint32_t>(c->sflags), s), "flags");
+        CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), K, cnt + 3, c->scratch.p, s),
+            "scan");
+        CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), K, ptr<uint32_t>(c->sidx), s),
+            "compact");
+        ga.count = cnt + 3;
+        CKC(c, gather_diffraction(ga, s), "gather");
+        AccumArgs x = aa;
+        x.kind = 1;
+        x.n_paths = K;
+        x.d_count = cnt + 3;
+        set_paths(x);
+        x.n_chunks = chunks_diff;
+        if (stats) CKC(c, cudaEventRecord(c->ev[6], s), "event");
+        CKC(c, accumulate(x, s), "accumulate diffraction");
+        if (stats) CKC(c, cudaEventRecord(c->ev[7], s), "event");
+        n_accum += 2;
+        CKC(c, reduce_partials(ptr<float2>(c->partial), chunks_diff, MF, out + MF, s), "reduce");
+    }
+    // ---- direct path (Eq. 11-12)
+    if (p.components & ST_COMP_DIRECT) {
+        DirectArgs dv{};
+        dv.nodes = ptr<float4>(S.nodes);
+        dv.tri_v = ptr<float4>(S.tri_v);
+        dv.root = S.root;
+        memcpy(dv.s, c->s, 12);
+        dv.mics = ptr<float>(c->mics);
+        dv.M = M;
+        dv.t_min = p.t_min;
+        dv.los_eps = p.los_eps;
+        dv.vis = ptr<uint8_t>(c->dvis);
+        dv.flags = ptr<uint32_t>(c->flags);
+        dv.queries = qctr;
+        CKC(c, direct_visibility(dv, s), "direct visibility");
+        DirectAccumArgs da{};
+        memcpy(da.s, c->s, 12);
+        da.mics = ptr<float>(c->mics);
+        da.M = M;
+        da.F = F;
+        da.vis = ptr<uint8_t>(c->dvis);
+        da.f_lo = c->f_lo;
+        da.df = T.df;
+        da.c = p.c;
+        da.a0 = p.alpha0_db_m;
+        da.a1 = p.alpha1_db_m_khz;
+        da.gain = p.direct_gain;
+        da.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
+        da.n_theta = c->n_theta;
+        memcpy(da.fwd, fwd, 12);
+        da.out = out + 2 * MF;
+        CKC(c, accumulate_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), s), "direct");
+    } else {
+        CKC(c, cudaMemsetAsync(c->dvis.p, 0, (size_t)M, s), "memset");
+    }
+    if (stats) CKC(c, cudaEventRecord(c->ev[3], s), "event");
+
+    c->last_N = N;
+    c->last_B = B;
+    c->last_K = K;
+    c->last_M = M;
+    c->last_F = F;
+    c->last_params = p;
+    c->last_chunks_spec = chunks_spec;
+    c->last_chunks_diff = chunks_diff;
+    c->has_last = true;
+
+    // device-side error flags are checked whenever the caller synchronises through stats
+    if (stats) {
+        uint32_t h[4] = {0, 0, 0, 0}, fl = 0;
+        unsigned long long hq[2] = {0, 0};
+        CKC(c, cudaMemcpyAsync(h, cnt, 16, cudaMemcpyDeviceToHost, s), "stats");
+        CKC(c, cudaMemcpyAsync(hq, qctr, 16, cudaMemcpyDeviceToHost, s), "stats");
+        CKC(c, cudaMemcpyAsync(&fl, c->flags.p, 4, cudaMemcpyDeviceToHost, s), "stats");
+        CKC(c, cudaStreamSynchronize(s), "stats sync");
+        memset(stats, 0, sizeof(*stats));
+        stats->rays = N;
+        stats->closest_queries = (int64_t)hq[0];
+        stats->shadow_queries = (int64_t)hq[1];
+        stats->records = 0;
+        stats->visible_records = h[2];
+        stats->candidates = K;
+        stats->candidates_kept = h[3];
+        float ms;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+        stats->ms_trace = ms;
+        cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
+        stats->ms_diffraction = ms;
+        cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+        stats->ms_accumulate = ms;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);
+        stats->ms_total = ms;
+        stats->kernel_launches = launch_count() - launches0;
+        stats->ms_accum_kernel = 0.0f;
+        stats->accum_launches = 0;
+        if (n_accum & 1) {
+            cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+            stats->ms_accum_kernel += ms;
+            stats->accum_launches++;
+        }
+        if (n_accum & 2) {
+            cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]);
+            stats->ms_accum_kernel += ms;
+            stats->accum_launches++;
+        }
+        stats->terms = ((int64_t)((n_accum & 1) ? h[2] : 0) + (int64_t)((n_accum & 2) ? h[3] : 0)) * M * F;
+        if (fl & kFlagStackOverflow) return fail(c, ST_ERR_OVERFLOW, "traversal stack overflow");
+    }
+    return ST_OK;
+}
+
+st_status st_simulate_host(st_ctx* c, st_scene* sc, const st_sim_params* params, void* spectra_out, st_stats* stats) {
+    if (!c || !spectra_out) return fail(c, ST_ERR_ARG, "simulate_host: null argument");
+    cudaSetDevice(c->device);
+    const size_t bytes = (size_t)3 * c->M * c->F * 8;
+    CKC(c, grow(c->host_out, bytes), "alloc");
+    st_status r = st_simulate(c, sc, params, c->host_out.p, stats);
+    if (r != ST_OK) return r;
+    CKC(c, cudaMemcpyAsync(spectra_out, c->host_out.p, bytes, cudaMemcpyDeviceToHost, c->stream), "copy out");
+    CKC(c, cudaStreamSynchronize(c->stream), "sync");
+    return ST_OK;
+}
+
+st_status st_get_paths(st_ctx* c, int32_t* tri, float* point, float* dir, double* r, uint8_t* los, int32_t mem) {
+    if (!c) return ST_ERR_ARG;
+    if (!c->has_last) return fail(c, ST_ERR_STATE, "get_paths: no simulate yet");
+    cudaSetDevice(c->device);
+    const size_t nb = (size_t)c->last_N * c->last_B;
+    if (tri) CKC(c, cudaMemcpyAsync(tri, c->rec_tri.p, nb * 4, kind_out(mem), c->stream), "get_paths");
+    if (point) CKC(c, cudaMemcpyAsync(point, c->rec_p.p, nb * 12, kind_out(mem), c->stream), "get_paths");
+    if (dir) CKC(c, cudaMemcpyAsync(dir, c->rec_d.p, nb * 12, kind_out(mem), c->stream), "get_paths");
+    if (r) CKC(c, cudaMemcpyAsync(r, c->rec_r.p, nb * 8, kind_out(mem), c->stream), "get_paths");
+    if (los) CKC(c, cudaMemcpyAsync(los, c->rec_los.p, nb, kind_out(mem), c->stream), "get_paths");
+    CKC(c, cudaStreamSynchronize(c->stream), "get_paths sync");
+    return ST_OK;
+}
+
+st_status st_get_diffraction(st_ctx* c, int64_t* n_out, int32_t* tri, float* point, uint8_t* keep, int64_t capacity,
+                             int32_t mem) {
+    if (!c || !n_out) return ST_ERR_ARG;
+    if (!c->has_last) return fail(c, ST_ERR_STATE, "get_diffraction: no simulate yet");
+    *n_out = c->last_K;
+    const int64_t n = std::min(capacity, c->last_K);
+    cudaSetDevice(c->device);
+    if (n > 0) {
+        if (tri) CKC(c, cudaMemcpyAsync(tri, c->cand_tri.p, (size_t)n * 4, kind_out(mem), c->stream), "get_diffraction");
+        if (point) CKC(c, cudaMemcpyAsync(point, c->cand_p.p, (size_t)n * 12, kind_out(mem), c->stream), "get_diffraction");
+        if (keep) CKC(c, cudaMemcpyAsync(keep, c->keep.p, (size_t)n, kind_out(mem), c->stream), "get_diffraction");
+    }
+    CKC(c, cudaStreamSynchronize(c->stream), "get_diffraction sync");
+    return ST_OK;
+}
+
+st_status st_get_direct_visibility(st_ctx* c, uint8_t* vis, int32_t mem) {
+    if (!c || !vis) return ST_ERR_ARG;
+    if (!c->has_last) return fail(c, ST_ERR_STATE, "get_direct_visibility: no simulate yet");
+    cudaSetDevice(c->device);
+    CKC(c, cudaMemcpyAsync(vis, c->dvis.p, (size_t)c->last_M, kind_out(mem), c->stream), "get_direct_visibility");
+    CKC(c, cudaStreamSynchronize(c->stream), "sync");
+    return ST_OK;
+}
+
+}  // extern "C"

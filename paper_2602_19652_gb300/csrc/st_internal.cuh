@@ -1,0 +1,260 @@
+// Internal declarations shared by the translation units of libsonotrace (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sonotrace.h"
+
+namespace st {
+
+// ------------------------------------------------------------------ constants
+constexpr int kLeafMax = 4;        // triangles per BVH leaf after collapsing small subtrees
+constexpr int kStack = 96;         // traversal stack entries per thread
+constexpr int kMaxBounces = 8;     // B limit (material chain packed in 8 bytes)
+constexpr int kMaxMics = 4096;
+
+// error flag bits written by kernels into Ctx::d_flags
+constexpr uint32_t kFlagStackOverflow = 1u;
+constexpr uint32_t kFlagBadIndex = 2u;
+constexpr uint32_t kFlagBadVertex = 4u;
+
+// ------------------------------------------------------------------ device buffers
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+cudaError_t grow(DevBuf& b, size_t bytes);
+void release(DevBuf& b);
+template <class T>
+T* ptr(const DevBuf& b) {
+    return static_cast<T*>(b.p);
+}
+
+// ------------------------------------------------------------------ scene on the device
+struct SceneDev {
+    int64_t n_verts = 0, n_tris = 0;
+    DevBuf verts;      // [V][3] f32
+    DevBuf tris;       // [T][3] i32
+    DevBuf tri_mat;    // [T] i32
+    DevBuf tri_obj;    // [T] i32
+    DevBuf nrm;        // [T][3] f32 geometric normals (input triangle order)
+    // LBVH
+    DevBuf nodes;      // [max(T-1,1)][4] float4: child boxes + child refs
+    DevBuf tri_v;      // [T][3] float4 in leaf order; tri_v[3i].w = triangle index bits
+    int32_t root = 0;  // child-ref encoding of the root
+    float bounds_lo[3] = {0, 0, 0}, bounds_hi[3] = {0, 0, 0};
+    // curvature and diffraction CDFs
+    DevBuf G;          // [V] f32
+    DevBuf C;          // [T] f32
+    int32_t n_obj = 0;
+    DevBuf mesh_tris;  // [T] i32, triangles grouped by mesh, ascending within a mesh
+    DevBuf mesh_off;   // [n_obj+1] i64
+    DevBuf cdf;        // [T] u64 per-mesh inclusive prefix, in mesh_tris order
+    DevBuf n_samples;  // [n_obj] i64
+    DevBuf sample_off; // [n_obj+1] i64
+    int64_t total_samples = 0;
+    // materials (host copies; device band tables are built per frequency grid)
+    int32_t n_mat = 0, n_bands = 0;
+    std::vector<float> band_hz, k_band, beta_band, diff_band;
+    bool built = false;
+};
+
+struct st_scene_impl;
+
+// ------------------------------------------------------------------ helpers for launches
+// Every kernel launch of the library calls note_launch() first; the count is reported in st_stats.
+void note_launch();
+int64_t launch_count();
+
+inline unsigned grid_for(int64_t n, int block, int64_t cap = 152 * 32) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// ------------------------------------------------------------------ primitives (st_sort.cu)
+// Stable LSD radix sort of (u64 key, u32 value) pairs over the low `bits` bits of the key.
+// Scratch must hold sort_scratch_bytes(n) bytes.
+size_t sort_scratch_bytes(int64_t n);
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, void* scratch, cudaStream_t s);
+// Exclusive scan of n u32 flags/counts into out (u32), total written to *total (device, may be null).
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* scratch,
+                               cudaStream_t s);
+cudaError_t inclusive_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, void* scratch, cudaStream_t s);
+
+// ------------------------------------------------------------------ scene build (st_scene.cu)
+struct CurvParamsDev {
+    float eta, area_ref, hc_frac;
+    double dither;
+    int32_t samples_per_vertex;
+    int64_t budget;
+    uint64_t seed;
+};
+// Validates indices and vertices (flags), computes normals, welds, curvature, C, CDFs, sample
+// counts and the LBVH.  Synchronises once.  Returns a CUDA error or sets *mesh_error.
+cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bool* mesh_error,
+                        std::string* msg);
+
+// ------------------------------------------------------------------ tracing (st_trace.cu)
+struct TraceArgs {
+    // scene
+    const float4* nodes;
+    const float4* tri_v;
+    int32_t root;
+    const float* nrm;
+    // rays
+    float s[3];
+    float q[4];
+    const float* R;       // device [3]: receiver reference point for the per-hit visibility ray
+    const float* dirs;    // [N][3] local directions
+    int64_t N;
+    int32_t B;
+    double r_max;
+    float t_min, los_eps;
+    // state (SoA, indexed by ray id)
+    float* ox; float* oy; float* oz;
+    float* dx; float* dy; float* dz;
+    double* racc;
+    int32_t* prev;
+    // queues
+    uint32_t* q_in; uint32_t* q_out;
+    uint32_t* n_in; uint32_t* n_out;
+    // records [N][B]
+    int32_t* rec_tri;
+    float* rec_p;    // [N][B][3]
+    float* rec_d;    // [N][B][3]
+    double* rec_r;
+    uint8_t* rec_los;
+    uint32_t* flags;
+    unsigned long long* queries;  // [0] closest-hit segments, [1] any-hit segments
+};
+cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block);
+
+struct DiffArgs {
+    const float4* nodes;
+    const float4* tri_v;
+    int32_t root;
+    const float* nrm;
+    const float* verts;
+    const int32_t* tris;
+    int32_t n_obj;
+    const int32_t* mesh_tris;
+    const int64_t* mesh_off;
+    const uint64_t* cdf;
+    const int64_t* sample_off;
+    int64_t K;
+    uint64_t seed;
+    uint32_t pose;
+    float s[3];
+    float fwd[3];
+    float cos_fov;        // <= -1: off
+    float cos_inc;
+    float t_min, los_eps;
+    int32_t* cand_tri;
+    float* cand_p;        // [K][3]
+    uint8_t* keep;
+    uint32_t* flags;
+    unsigned long long* queries;
+};
+cudaError_t diffraction_sample(DiffArgs& a, cudaStream_t s);
+
+struct DirectArgs {
+    const float4* nodes;
+    const float4* tri_v;
+    int32_t root;
+    float s[3];
+    const float* mics;
+    int32_t M;
+    float t_min, los_eps;
+    uint8_t* vis;
+    uint32_t* flags;
+    unsigned long long* queries;
+};
+cudaError_t direct_visibility(DirectArgs& a, cudaStream_t s);
+
+void mic_centroid_host_order(const float* mics_dev, int32_t M, float* R_dev, cudaStream_t s);
+
+// ------------------------------------------------------------------ accumulation (st_accum.cu)
+// Unified contributor list ("paths") feeding the accumulator.
+struct PathList {
+    int64_t n_max = 0;
+    DevBuf px, py, pz, dx, dy, dz, rhi, rlo, chain_lo, chain_hi, meta, dep;
+    // meta: bits 0..3 = chain length (specular) or 0 (diffraction), bits 8..15 = material of the
+    // last leg's surface
+};
+
+struct AccumTables {
+    int32_t F = 0, n_mat = 0;
+    DevBuf lk;     // [n_mat][F] log2 k(mat, f)
+    DevBuf g2;     // [n_mat][F] lobe exponent 1/(2 beta^2) * log2(e)
+    DevBuf lid;    // [n_mat][F] log2 I_d(mat, f)
+    DevBuf qhi, qlo;  // [F] f_k / c as float-float
+    double f_lo = 0, df = 0, c = 343, a0 = 0, a1 = 0;
+};
+
+struct AccumArgs {
+    int kind;               // 0 specular, 1 diffraction
+    int64_t n_paths;        // upper bound; actual count in *d_count
+    const uint32_t* d_count;
+    const float* px; const float* py; const float* pz;
+    const float* dx; const float* dy; const float* dz;
+    const float* rhi; const float* rlo;
+    const uint32_t* chain_lo; const uint32_t* chain_hi;
+    const uint32_t* meta;
+    const float* dep;       // per path: emitter directivity coordinate theta / dtheta (or -1 = omni)
+    const float* mics;      // [M][3]
+    int32_t M, F;
+    const float* lk; const float* g2; const float* lid;
+    const float* qhi; const float* qlo;
+    float dq_hi, dq_lo;     // (f_{k+1} - f_k) / c as float-float
+    float atm2_0, atm2_step;  // log2 amplitude decay per metre at bin 0 and per bin step
+    const float* etab;      // emitter table [n_theta][F] or null
+    int32_t n_theta;
+    int32_t reflection_mode;
+    float2* partial;        // [n_chunks][M][F]
+    int32_t n_chunks;
+};
+cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, double f_lo, double f_hi, double c,
+                               double a0, double a1, cudaStream_t s);
+cudaError_t accumulate(const AccumArgs& a, cudaStream_t s);
+cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s);
+int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F);
+
+struct GatherArgs {
+    // specular
+    int64_t N; int32_t B;
+    const int32_t* rec_tri; const float* rec_p; const float* rec_d; const double* rec_r; const uint8_t* rec_los;
+    const int32_t* tri_mat;
+    const float* dirs; float q[4]; float fwd[3]; float inv_dtheta; int has_etab;
+    // diffraction
+    int64_t K; const int32_t* cand_tri; const float* cand_p; const uint8_t* keep; float s[3];
+    // outputs
+    const uint32_t* idx;   // compacted source indices
+    const uint32_t* count;
+    PathList* out;
+};
+cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s);
+cudaError_t gather_diffraction(const GatherArgs& g, cudaStream_t s);
+cudaError_t flags_visible_records(const int32_t* rec_tri, const uint8_t* rec_los, int64_t n, uint32_t* flags,
+                                  cudaStream_t s);
+cudaError_t flags_from_u8(const uint8_t* keep, int64_t n, uint32_t* flags, cudaStream_t s);
+cudaError_t compact_indices(const uint32_t* flags, const uint32_t* scan, int64_t n, uint32_t* idx, cudaStream_t s);
+
+struct DirectAccumArgs {
+    float s[3];
+    const float* mics; int32_t M, F;
+    const uint8_t* vis;
+    double f_lo, df, c, a0, a1;
+    float gain;
+    const float* etab; int32_t n_theta; float fwd[3];
+    float2* out;           // [M][F] (component 2 of the spectra)
+};
+cudaError_t accumulate_direct(const DirectAccumArgs& a, const float* qhi, const float* qlo, cudaStream_t s);
+
+}  // namespace st

@@ -1,0 +1,134 @@
+"""GPU vs oracle parity through the C ABI.
+
+Bars: path sets (hit triangle per bounce, hit points, reflected directions, float64 path lengths,
+visibility flags), curvature, diffraction samples and filters bit-exact; spectra within 1e-4
+relative L2 error per component (the target tolerance of the path; float32 amplitudes with
+float-float range-reduced phases on the GPU against float64 throughout in the oracle)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b.ravel())
+    if nb == 0:
+        return float(np.linalg.norm(a.ravel()))
+    return float(np.linalg.norm((a - b).ravel()) / nb)
+
+
+@pytest.fixture(scope="module")
+def st():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_19652_gb300 as st_
+    return st_
+
+
+def gpu_run(st, wl, curv=None, **kw):
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, curv)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance, **kw)
+    S, stats = ctx.simulate(sc, p, stats=True)
+    return ctx, sc, S.cpu().numpy(), stats
+
+
+def compare_paths(g, o, rows=None):
+    for k in ("tri", "los", "p", "d", "r"):
+        a, b = g[k], o[k]
+        if rows is not None:
+            a = a[rows]
+        mism = np.argwhere(~((a == b) | (np.isnan(a) & np.isnan(b))).reshape(len(a), -1).all(1)) if a.dtype.kind == "f" \
+            else np.argwhere(~(a == b).reshape(len(a), -1).all(1))
+        assert len(mism) == 0, f"{k}: {len(mism)} rays differ, first {mism[:5].ravel()}"
+
+
+def test_shoebox_paths_and_spectra(st):
+    import oracle
+    wl = synth.shoebox(seed=101)
+    ctx, sc, S, stats = gpu_run(st, wl)
+    g = ctx.paths(wl.bounces)
+    o = oracle.simulate(wl)
+    compare_paths(g, o["rec"])
+    assert stats.visible_records == (o["rec"]["los"] == 1).sum()
+    for c in (0, 2):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, c
+    assert np.all(S[1] == 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gradient_workload_forward(st, mode):
+    import oracle
+    wl = synth.gradient_problem(n_rays=3000)
+    ctx, sc, S, _ = gpu_run(st, wl, reflection_mode=mode)
+    o = oracle.simulate(wl, reflection_mode=mode)
+    compare_paths(ctx.paths(wl.bounces), o["rec"])
+    for c in (0, 2):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, c
+
+
+def small_clutter(**kw):
+    args = dict(seed=202, target_tris=20_000, n_rays=20_000, bounces=5, n_mics=8, n_bins=96)
+    args.update(kw)
+    return synth.clutter(**args)
+
+
+def test_clutter_small_full_parity(st):
+    import oracle
+    wl = small_clutter()
+    curv = dict(budget=200_000)
+    ctx, sc, S, stats = gpu_run(st, wl, curv=st.curv_params(sample_budget=200_000))
+    o = oracle.simulate(wl, curv=curv)
+    compare_paths(ctx.paths(wl.bounces), o["rec"])
+    G, C, ns = sc.curvature()
+    assert np.array_equal(G, o["G"])
+    assert np.array_equal(C, o["C"])
+    assert np.array_equal(ns, o["cdf"]["n_samples"])
+    ct, cp, keep = ctx.diffraction()
+    assert np.array_equal(ct, o["cand_tri"])
+    assert np.array_equal(cp, o["cand_p"])
+    assert np.array_equal(keep, o["cand_keep"])
+    assert np.array_equal(ctx.direct_visibility(), o["direct_vis"])
+    assert keep.sum() > 100 and stats.visible_records > 1000
+    for c in range(3):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
+
+
+def test_ragged_sizes_and_single_mic_bin(st):
+    """M = 1, F = 1 and sizes that are not multiples of any tile."""
+    import oracle
+    for M, F in [(1, 1), (3, 17), (33, 35)]:
+        wl = small_clutter(target_tris=3000, n_rays=1537, n_mics=M, n_bins=F, bounces=3, diffraction=False)
+        ctx, sc, S, _ = gpu_run(st, wl)
+        o = oracle.simulate(wl)
+        compare_paths(ctx.paths(wl.bounces), o["rec"])
+        for c in (0, 2):
+            assert rel_l2(S[c], o["spectra"][c]) <= TOL, (M, F, c)
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 5, 7, 8, 9, 31, 32, 33, 1000])
+def test_bvh_small_triangle_counts(st, T):
+    """Leaf-size and warp boundaries of the LBVH: GPU closest hits equal brute force."""
+    import oracle
+    rng = np.random.default_rng(T)
+    c = rng.uniform(-1, 1, size=(T, 1, 3))
+    v = (c + 0.3 * rng.normal(size=(T, 3, 3))).reshape(-1, 3).astype(np.float32)
+    tris = np.arange(3 * T, dtype=np.int32).reshape(T, 3)
+    n_bands = 2
+    wl = synth.Workload(name="soup", verts=v, tris=tris, tri_mat=np.zeros(T, np.int32),
+                        tri_obj=np.zeros(T, np.int32), band_hz=np.array([20e3, 80e3], np.float32),
+                        k_band=np.full((1, n_bands), 0.9, np.float32), beta_band=np.full((1, n_bands), 0.3, np.float32),
+                        diff_band=np.full((1, n_bands), 0.05, np.float32), emitter=np.zeros(3, np.float32),
+                        emitter_quat=np.array([1, 0, 0, 0], np.float32), dirs=synth.fibonacci_directions(4096),
+                        mics=np.array([[0.1, 0.2, 0.05]], np.float32), n_bins=4, f_lo=20e3, f_hi=80e3, bounces=4)
+    ctx, sc, S, _ = gpu_run(st, wl)
+    o = oracle.simulate(wl, use_bvh=False)
+    compare_paths(ctx.paths(wl.bounces), o["rec"])
+    assert rel_l2(S[0], o["spectra"][0]) <= TOL
