@@ -100,6 +100,8 @@ typedef struct st_stats {
     float ms_accum_kernel;      /* device time of the accumulator kernel launches alone, ms */
     int32_t accum_launches;     /* number of accumulator kernel launches */
     int64_t kernel_launches;    /* kernels launched by this call */
+    int64_t visits[4];          /* with ST_COUNT_VISITS=1: BVH nodes and triangles visited by closest-hit
+                                   queries, then by any-hit queries (0 otherwise) */
 } st_stats;
 
 void st_curv_params_default(st_curv_params* p);

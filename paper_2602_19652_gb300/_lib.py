@@ -34,7 +34,8 @@ class Stats(C.Structure):
     _fields_ = [("rays", I64), ("closest_queries", I64), ("shadow_queries", I64), ("records", I64),
                 ("visible_records", I64), ("candidates", I64), ("candidates_kept", I64), ("terms", I64),
                 ("ms_trace", F32), ("ms_diffraction", F32), ("ms_accumulate", F32), ("ms_total", F32),
-                ("ms_accum_kernel", F32), ("accum_launches", I32), ("kernel_launches", I64)]
+                ("ms_accum_kernel", F32), ("accum_launches", I32), ("kernel_launches", I64),
+                ("visits", I64 * 4)]
 
 
 class Job(C.Structure):

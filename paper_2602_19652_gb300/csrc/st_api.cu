@@ -7,6 +7,7 @@
 // No host synchronisation happens inside unless statistics are requested.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -58,7 +59,7 @@ struct st_ctx {
     bool has_emitter = false;
     float s[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0};
     int64_t N = 0;
-    DevBuf dirs, etab;
+    DevBuf dirs, etab, perm, ord_keys, ord_scr;
     int32_t n_theta = 0;
     float fov_half = 4.0f;
     // receivers
@@ -86,6 +87,7 @@ struct st_ctx {
     // last simulate parameters (for the adjoint)
     st_sim_params last_params;
     int32_t last_chunks_spec = 0, last_chunks_diff = 0;
+    bool count_visits = false;  // ST_COUNT_VISITS=1 in the environment: node/triangle visit counters
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -176,6 +178,8 @@ st_status st_create(st_ctx** out, int32_t device, void* cuda_stream) {
     st_ctx* c = new st_ctx();
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
+    const char* cv = getenv("ST_COUNT_VISITS");
+    c->count_visits = cv && cv[0] == '1';
     for (auto& e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             delete c;
@@ -189,7 +193,7 @@ st_status st_destroy(st_ctx* c) {
     if (!c) return ST_ERR_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (DevBuf* b : {&c->dirs, &c->etab, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
+    for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
                       &c->st_d[2], &c->st_r, &c->st_prev, &c->q0, &c->q1, &c->counts, &c->queries, &c->flags, &c->R, &c->rec_tri,
                       &c->rec_p, &c->rec_d, &c->rec_r, &c->rec_los, &c->sflags, &c->sscan, &c->sidx, &c->scratch,
                       &c->cand_tri, &c->cand_p, &c->keep, &c->dvis, &c->partial, &c->host_out, &c->tables.lk,
@@ -353,6 +357,13 @@ st_status st_set_emitter(st_ctx* c, const float pos[3], const float quat[4], int
     if (n_rays > 0) {
         CKC(c, grow(c->dirs, (size_t)n_rays * 12), "set_emitter alloc");
         CKC(c, cudaMemcpyAsync(c->dirs.p, dirs, (size_t)n_rays * 12, kind_in(mem), c->stream), "set_emitter dirs");
+        // first-bounce processing order: rays sorted by direction (coherent warps)
+        CKC(c, grow(c->perm, (size_t)n_rays * 4), "set_emitter alloc");
+        CKC(c, grow(c->ord_keys, (size_t)n_rays * 8), "set_emitter alloc");
+        CKC(c, grow(c->ord_scr, sort_scratch_bytes(n_rays)), "set_emitter alloc");
+        CKC(c, direction_order(ptr<float>(c->dirs), n_rays, ptr<uint64_t>(c->ord_keys), ptr<uint32_t>(c->perm),
+                               c->ord_scr.p, c->stream),
+            "set_emitter order");
     }
     c->n_theta = dir_table ? n_theta : 0;
     c->fov_half = fov_half_rad;
@@ -451,7 +462,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, grow(c->q0, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
     CKC(c, grow(c->q1, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
     CKC(c, grow(c->counts, 64), "alloc");
-    CKC(c, grow(c->queries, 16), "alloc");
+    CKC(c, grow(c->queries, 64), "alloc");
     CKC(c, grow(c->flags, 16), "alloc");
     CKC(c, grow(c->R, 16), "alloc");
     CKC(c, grow(c->rec_tri, (size_t)std::max<int64_t>(NB, 1) * 4), "alloc");
@@ -481,7 +492,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, cudaMemsetAsync(out, 0, (size_t)3 * MF * 8, s), "memset out");
     CKC(c, cudaMemsetAsync(c->flags.p, 0, 16, s), "memset");
     CKC(c, cudaMemsetAsync(c->counts.p, 0, 64, s), "memset");
-    CKC(c, cudaMemsetAsync(c->queries.p, 0, 16, s), "memset");
+    CKC(c, cudaMemsetAsync(c->queries.p, 0, 64, s), "memset");
     unsigned long long* qctr = ptr<unsigned long long>(c->queries);
     CKC(c, cudaMemsetAsync(c->rec_tri.p, 0xff, (size_t)std::max<int64_t>(NB, 1) * 4, s), "memset");
     CKC(c, cudaMemsetAsync(c->rec_los.p, 0, (size_t)std::max<int64_t>(NB, 1), s), "memset");
@@ -511,11 +522,14 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         ta.nodes = ptr<float4>(S.nodes);
         ta.tri_v = ptr<float4>(S.tri_v);
         ta.root = S.root;
+        ta.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+        ta.visits = c->count_visits ? qctr + 2 : nullptr;
         ta.nrm = ptr<float>(S.nrm);
         memcpy(ta.s, c->s, 12);
         memcpy(ta.q, c->q, 16);
         ta.R = ptr<float>(c->R);
         ta.dirs = ptr<float>(c->dirs);
+        ta.perm = ptr<uint32_t>(c->perm);
         ta.N = N;
         ta.B = B;
         ta.r_max = p.max_distance;
@@ -550,6 +564,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         da.nodes = ptr<float4>(S.nodes);
         da.tri_v = ptr<float4>(S.tri_v);
         da.root = S.root;
+        da.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+        da.visits = c->count_visits ? qctr + 2 : nullptr;
         da.nrm = ptr<float>(S.nrm);
         da.verts = ptr<float>(S.verts);
         da.tris = ptr<int32_t>(S.tris);
@@ -686,6 +702,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         dv.nodes = ptr<float4>(S.nodes);
         dv.tri_v = ptr<float4>(S.tri_v);
         dv.root = S.root;
+        dv.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+        dv.visits = c->count_visits ? qctr + 2 : nullptr;
         memcpy(dv.s, c->s, 12);
         dv.mics = ptr<float>(c->mics);
         dv.M = M;
@@ -730,15 +748,16 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     // device-side error flags are checked whenever the caller synchronises through stats
     if (stats) {
         uint32_t h[4] = {0, 0, 0, 0}, fl = 0;
-        unsigned long long hq[2] = {0, 0};
+        unsigned long long hq[6] = {0, 0, 0, 0, 0, 0};
         CKC(c, cudaMemcpyAsync(h, cnt, 16, cudaMemcpyDeviceToHost, s), "stats");
-        CKC(c, cudaMemcpyAsync(hq, qctr, 16, cudaMemcpyDeviceToHost, s), "stats");
+        CKC(c, cudaMemcpyAsync(hq, qctr, 48, cudaMemcpyDeviceToHost, s), "stats");
         CKC(c, cudaMemcpyAsync(&fl, c->flags.p, 4, cudaMemcpyDeviceToHost, s), "stats");
         CKC(c, cudaStreamSynchronize(s), "stats sync");
         memset(stats, 0, sizeof(*stats));
         stats->rays = N;
         stats->closest_queries = (int64_t)hq[0];
         stats->shadow_queries = (int64_t)hq[1];
+        for (int k = 0; k < 4; ++k) stats->visits[k] = (int64_t)hq[2 + k];
         stats->records = 0;
         stats->visible_records = h[2];
         stats->candidates = K;
@@ -767,6 +786,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         }
         stats->terms = ((int64_t)((n_accum & 1) ? h[2] : 0) + (int64_t)((n_accum & 2) ? h[3] : 0)) * M * F;
         if (fl & kFlagStackOverflow) return fail(c, ST_ERR_OVERFLOW, "traversal stack overflow");
+        if (fl & kFlagBadTree) return fail(c, ST_ERR_CUDA, "malformed BVH: traversal exceeded the node count");
     }
     return ST_OK;
 }

@@ -21,6 +21,7 @@ constexpr int kMaxMics = 4096;
 constexpr uint32_t kFlagStackOverflow = 1u;
 constexpr uint32_t kFlagBadIndex = 2u;
 constexpr uint32_t kFlagBadVertex = 4u;
+constexpr uint32_t kFlagBadTree = 8u;
 
 // ------------------------------------------------------------------ device buffers
 struct DevBuf {
@@ -107,12 +108,15 @@ struct TraceArgs {
     const float4* nodes;
     const float4* tri_v;
     int32_t root;
+    int32_t max_iter;
+    unsigned long long* visits;
     const float* nrm;
     // rays
     float s[3];
     float q[4];
     const float* R;       // device [3]: receiver reference point for the per-hit visibility ray
     const float* dirs;    // [N][3] local directions
+    const uint32_t* perm; // [N] processing order of the first bounce (rays sorted by direction) or null
     int64_t N;
     int32_t B;
     double r_max;
@@ -135,11 +139,16 @@ struct TraceArgs {
     unsigned long long* queries;  // [0] closest-hit segments, [1] any-hit segments
 };
 cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block);
+// perm = indices 0..n-1 sorted by an octahedral Morton key of dirs (keys: n u64 scratch)
+cudaError_t direction_order(const float* dirs, int64_t n, uint64_t* keys, uint32_t* perm, void* scratch,
+                            cudaStream_t s);
 
 struct DiffArgs {
     const float4* nodes;
     const float4* tri_v;
     int32_t root;
+    int32_t max_iter;
+    unsigned long long* visits;
     const float* nrm;
     const float* verts;
     const int32_t* tris;
@@ -168,6 +177,8 @@ struct DirectArgs {
     const float4* nodes;
     const float4* tri_v;
     int32_t root;
+    int32_t max_iter;
+    unsigned long long* visits;
     float s[3];
     const float* mics;
     int32_t M;

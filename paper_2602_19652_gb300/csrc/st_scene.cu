@@ -502,7 +502,7 @@ struct Box {
 // a node unites both slots and climbs.  box_tmp: [n-1][2] boxes.
 __global__ void k_boxes(const float* V, const int32_t* T, int n, const uint32_t* sorted_tri, const int2* child,
                         const int32_t* parent_int, const int32_t* parent_leaf, float pad, Box* box_tmp,
-                        uint32_t* visits) {
+                        uint32_t* visits, uint32_t* err) {
     int stride = gridDim.x * blockDim.x;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
         int64_t t = sorted_tri[p];
@@ -516,10 +516,18 @@ __global__ void k_boxes(const float* V, const int32_t* T, int n, const uint32_t*
         int node = parent_leaf[p];
         int slot = (child[node].x == ~p) ? 0 : 1;
         box_tmp[2 * node + slot] = b;
-        while (true) {
+        for (int climb = 0;; ++climb) {
+            if (climb > n) {  // deeper than the node count: not a tree
+                atomicOr(err, kFlagBadTree);
+                break;
+            }
             __threadfence();
             uint32_t old = atomicAdd(&visits[node], 1u);
             if (old == 0) break;
+            if (old > 1) {  // a node has two children: a third arrival means a malformed hierarchy
+                atomicOr(err, kFlagBadTree);
+                break;
+            }
             __threadfence();
             const volatile float* b0 = reinterpret_cast<const volatile float*>(&box_tmp[2 * node]);
             const volatile float* b1 = reinterpret_cast<const volatile float*>(&box_tmp[2 * node + 1]);
@@ -790,7 +798,8 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
             CK(cudaGetLastError());
             note_launch();
             k_boxes<<<grid_for(n, kB), kB, 0, s>>>(V, T, n, ptr<uint32_t>(vals), ptr<int2>(child), ptr<int32_t>(par_i),
-                                                   ptr<int32_t>(par_l), pad, ptr<Box>(boxes), ptr<uint32_t>(visits));
+                                                   ptr<int32_t>(par_l), pad, ptr<Box>(boxes), ptr<uint32_t>(visits),
+                                                   ptr<uint32_t>(flags));
             CK(cudaGetLastError());
             note_launch();
             k_pack_nodes<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(child), ptr<int2>(range), ptr<Box>(boxes),
@@ -798,7 +807,13 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
             CK(cudaGetLastError());
         }
     }
+    CK(cudaMemcpyAsync(&hflags, flags.p, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (hflags & kFlagBadTree) {
+        *mesh_error = true;
+        *msg = "LBVH construction produced a malformed hierarchy";
+        return cudaSuccess;
+    }
     S.built = true;
     return cudaSuccess;
 }

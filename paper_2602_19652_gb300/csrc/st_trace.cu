@@ -22,6 +22,8 @@ struct Trav {
     const float4* __restrict__ nodes;
     const float4* __restrict__ tri_v;
     int32_t root;
+    int32_t max_iter;               // 2 * node count + 8: bound on loop iterations of one traversal
+    unsigned long long* visits;     // optional [4]: nodes and triangles visited (closest, any-hit)
 };
 
 __device__ __forceinline__ float safe_inv(float d) {
@@ -31,17 +33,18 @@ __device__ __forceinline__ float safe_inv(float d) {
     return 1.0f / d;
 }
 
-// slab test of one box; returns the entry distance or +inf when missed.  tfar is widened by
-// (1 + 2 gamma_3) (Ize, "Robust BVH ray traversal", JCGT 2013); boxes are padded as well.
-__device__ __forceinline__ float slab(float lx, float ly, float lz, float hx, float hy, float hz, f3 o, f3 inv,
-                                      float tmin, float tmax) {
+// slab test of one box over [tmin, tmax]: true when hit, entry distance in *tn.  tfar is widened
+// by (1 + 2 gamma_3) (Ize, "Robust BVH ray traversal", JCGT 2013); boxes are padded as well.
+__device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, float hy, float hz, f3 o, f3 inv,
+                                     float tmin, float tmax, float* tn_out) {
     float t0x = (lx - o.x) * inv.x, t1x = (hx - o.x) * inv.x;
     float t0y = (ly - o.y) * inv.y, t1y = (hy - o.y) * inv.y;
     float t0z = (lz - o.z) * inv.z, t1z = (hz - o.z) * inv.z;
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), tmin));
     float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
     tf = tf * 1.0000004f;
-    return tn <= tf ? tn : __int_as_float(0x7f800000);
+    *tn_out = tn;
+    return tn <= tf;
 }
 
 template <bool AnyHit>
@@ -54,17 +57,27 @@ __device__ __forceinline__ int32_t traverse(const Trav& T, f3 o, f3 d, int32_t e
     int2 stack[kStack];
     int sp = 0;
     int32_t ref = T.root;
+    // every node of a proper tree is visited at most once: more iterations than nodes means a
+    // malformed hierarchy, reported through the flags instead of looping
+    int guard = T.max_iter;
+    int n_nodes = 0, n_tris = 0;
     // the search interval for boxes: [-inf, tb]; t_min is enforced on triangles only
     while (true) {
+        if (--guard < 0) {
+            atomicOr(flags, kFlagBadTree);
+            break;
+        }
         if (ref >= 0) {
             const float4 a = __ldg(&T.nodes[4 * ref + 0]);
             const float4 b = __ldg(&T.nodes[4 * ref + 1]);
             const float4 c = __ldg(&T.nodes[4 * ref + 2]);
             const float4 e = __ldg(&T.nodes[4 * ref + 3]);
-            const float tl = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, -1e30f, tb);
-            const float tr = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, -1e30f, tb);
+            ++n_nodes;
+            // boxes are padded, so a box holding a hit at t > t_min >= 0 exits at t > 0 after rounding
+            float tl, tr;
+            const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, 0.0f, tb, &tl);
+            const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, 0.0f, tb, &tr);
             const int32_t rl = __float_as_int(e.x), rr = __float_as_int(e.y);
-            const bool hl = tl <= tb, hr = tr <= tb;
             if (hl && hr) {
                 const bool lfirst = tl <= tr;
                 ref = lfirst ? rl : rr;
@@ -90,12 +103,17 @@ __device__ __forceinline__ int32_t traverse(const Trav& T, f3 o, f3 d, int32_t e
                 if (id == exclude) continue;
                 const float4 v1 = __ldg(&T.tri_v[3 * i + 1]);
                 const float4 v2 = __ldg(&T.tri_v[3 * i + 2]);
+                ++n_tris;
                 float th;
                 if (!wt_hit(wr, f3{v0.x, v0.y, v0.z}, f3{v1.x, v1.y, v1.z}, f3{v2.x, v2.y, v2.z}, &th)) continue;
                 if (!(th > t_min)) continue;
                 if (AnyHit) {
                     if (th < t_max) {
                         *t_out = th;
+                        if (T.visits) {
+                            atomicAdd(&T.visits[2], (unsigned long long)n_nodes);
+                            atomicAdd(&T.visits[3], (unsigned long long)n_tris);
+                        }
                         return id;
                     }
                 } else if (th < tb || (th == tb && id < best)) {
@@ -115,6 +133,10 @@ __device__ __forceinline__ int32_t traverse(const Trav& T, f3 o, f3 d, int32_t e
             }
         }
         if (!found) break;
+    }
+    if (T.visits) {
+        atomicAdd(&T.visits[AnyHit ? 2 : 0], (unsigned long long)n_nodes);
+        atomicAdd(&T.visits[AnyHit ? 3 : 1], (unsigned long long)n_tris);
     }
     *t_out = tb;
     return best;
@@ -139,12 +161,12 @@ __device__ __forceinline__ void warp_count(unsigned long long* ctr) {
 
 // One bounce of Algorithm 1 over the live-ray queue.
 __global__ void __launch_bounds__(128) k_bounce(const TraceArgs a, int j, int64_t n_first) {
-    const Trav T{a.nodes, a.tri_v, a.root};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     const int64_t n_live = (j == 0) ? n_first : (int64_t)*a.n_in;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const f3 R{a.R[0], a.R[1], a.R[2]};  // device copy written by k_centroid
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_live; idx += stride) {
-        const int64_t ray = (j == 0) ? idx : (int64_t)a.q_in[idx];
+        const int64_t ray = (j == 0) ? (a.perm ? (int64_t)a.perm[idx] : idx) : (int64_t)a.q_in[idx];
         f3 o, d;
         double r;
         int32_t prev;
@@ -231,7 +253,7 @@ __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, 
 // Sec. III-D: sample g of the global list -> mesh m, local index s; Philox(s, m, pose, 0) selects a
 // triangle through the mesh's integer CDF and a barycentric point; then the filters.
 __global__ void __launch_bounds__(128) k_diffraction(const DiffArgs a) {
-    const Trav T{a.nodes, a.tri_v, a.root};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const f3 s{a.s[0], a.s[1], a.s[2]};
     const f3 fwd{a.fwd[0], a.fwd[1], a.fwd[2]};
@@ -301,7 +323,7 @@ __global__ void __launch_bounds__(128) k_diffraction(const DiffArgs a) {
 }
 
 __global__ void k_direct(const DirectArgs a) {
-    const Trav T{a.nodes, a.tri_v, a.root};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= a.M) return;
     const f3 s{a.s[0], a.s[1], a.s[2]};
@@ -319,7 +341,47 @@ __global__ void k_centroid(const float* mics, int32_t M, float* R) {
     for (int k = 0; k < 3; ++k) R[k] = (float)(acc[k] / (double)M);
 }
 
+// Octahedral map of a direction to [0,1]^2, 16 bits per axis, Morton-interleaved: nearby directions
+// get nearby keys, so sorting by the key groups rays that traverse the same part of the scene.
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+__global__ void k_dir_keys(const float* dirs, int64_t n, uint64_t* keys, uint32_t* vals) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float x = dirs[3 * i], y = dirs[3 * i + 1], z = dirs[3 * i + 2];
+        const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
+        float px = l1 > 0.0f ? x / l1 : 0.0f, py = l1 > 0.0f ? y / l1 : 0.0f;
+        if (z < 0.0f) {
+            const float qx = (1.0f - fabsf(py)) * (px >= 0.0f ? 1.0f : -1.0f);
+            const float qy = (1.0f - fabsf(px)) * (py >= 0.0f ? 1.0f : -1.0f);
+            px = qx;
+            py = qy;
+        }
+        const uint32_t u = (uint32_t)fminf(fmaxf((px + 1.0f) * 32767.5f, 0.0f), 65535.0f);
+        const uint32_t v = (uint32_t)fminf(fmaxf((py + 1.0f) * 32767.5f, 0.0f), 65535.0f);
+        keys[i] = (uint64_t)((spread16(u) << 1) | spread16(v));
+        vals[i] = (uint32_t)i;
+    }
+}
+
 }  // namespace
+
+cudaError_t direction_order(const float* dirs, int64_t n, uint64_t* keys, uint32_t* perm, void* scratch,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    note_launch();
+    k_dir_keys<<<grid_for(n, 256), 256, 0, s>>>(dirs, n, keys, perm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return radix_sort_u64(keys, perm, n, 32, scratch, s);
+}
 
 cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
     const unsigned grid = grid_for(a.N, block, 152 * 16);
