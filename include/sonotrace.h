@@ -172,6 +172,33 @@ st_status st_get_diffraction(st_ctx* ctx, int64_t* n_out, int32_t* tri, float* p
 /* Direct-path visibility per microphone of the last simulate. */
 st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
 
+/* Allocation-free specular accumulation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory where they need spectra -- code running inside another
+ * allocator's fixed memory budget or arena, real-time loops where cudaMalloc would stall or
+ * synchronise the device, or callbacks in which allocation is not allowed.
+ *
+ * Computes the specular component (index 0 of st_simulate's spectra, Eq. 2-4) from path records
+ * laid out as st_get_paths returns them: rec_tri [n_rays][max_bounces] (-1 = no hit), rec_point and
+ * rec_dir [n_rays][max_bounces][3], rec_r [n_rays][max_bounces] (float64), rec_los [n_rays]
+ * [max_bounces]; tri_material [n_tris]; mics [n_mics][3]; all device pointers.  The material band
+ * tables (band_hz [n_bands], k and beta [n_mat][n_bands]) are host pointers.  Omni emitter and
+ * receivers.  Uses params->c, alpha0/alpha1 and reflection_mode (NULL = defaults).  Writes
+ * spectra_out, device complex64 [n_mics][n_bins], on cuda_stream.
+ *
+ * It calls no allocator.  Its scratch is one array of ST_NOALLOC_SCRATCH_BYTES compiled into the
+ * library; every GPU that loads the library holds it until the process exits.  Sizes whose tables
+ * plus one chunk of partial spectra (about 8 * n_mics * n_bins + 8 * n_mat * n_bins bytes) exceed
+ * it return ST_ERR_ARG.  The first call on a device looks up the array's device address; make that
+ * call before any stream capture.  All calls share the array: calls that overlap on the GPU race
+ * and give wrong results, so order them on one stream.  No state carries over between calls. */
+#define ST_NOALLOC_SCRATCH_BYTES (8u << 20)
+st_status st_accumulate_specular_noalloc(const int32_t* rec_tri, const float* rec_point, const float* rec_dir,
+                                         const double* rec_r, const uint8_t* rec_los, int64_t n_rays,
+                                         int32_t max_bounces, const int32_t* tri_material, const float* mics,
+                                         int32_t n_mics, int32_t n_bins, double f_lo, double f_hi, int32_t n_mat,
+                                         int32_t n_bands, const float* band_hz, const float* k, const float* beta,
+                                         const st_sim_params* params, void* spectra_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
