@@ -33,7 +33,7 @@ import synth  # noqa: E402
 
 METRIC = "Mrays/s (closest-hit + any-hit segments per second, spectra at <=1e-4 rel-L2 vs oracle)"
 UNIT = "Mrays/s"
-FLOPS_PER_TERM = 12  # complex rotation (6) + complex scale-accumulate (4) + lobe exponent (2)
+FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by-complex multiply-accumulate (4)
 
 
 def load_peaks():

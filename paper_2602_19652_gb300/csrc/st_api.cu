@@ -482,8 +482,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         CKC(c, grow(c->cand_p, (size_t)K * 12), "alloc");
         CKC(c, grow(c->keep, (size_t)K), "alloc");
     }
-    const int32_t chunks_spec = accum_chunks(NB, M, F);
-    const int32_t chunks_diff = accum_chunks(K, M, F);
+    const int32_t chunks_spec = accum_chunks(NB, M, F, S.n_mat);
+    const int32_t chunks_diff = accum_chunks(K, M, F, S.n_mat);
     const int32_t chunks = std::max(chunks_spec, chunks_diff);
     CKC(c, grow(c->partial, (size_t)chunks * M * F * 8), "alloc");
 
@@ -601,6 +601,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     aa.lk = ptr<float>(T.lk);
     aa.g2 = ptr<float>(T.g2);
     aa.lid = ptr<float>(T.lid);
+    aa.n_mat_tab = T.n_mat;
     aa.qhi = ptr<float>(T.qhi);
     aa.qlo = ptr<float>(T.qlo);
     {

@@ -222,6 +222,7 @@ struct AccumArgs {
     const float* mics;      // [M][3]
     int32_t M, F;
     const float* lk; const float* g2; const float* lid;
+    int32_t n_mat_tab;      // materials in the per-bin tables
     const float* qhi; const float* qlo;
     float dq_hi, dq_lo;     // (f_{k+1} - f_k) / c as float-float
     float atm2_0, atm2_step;  // log2 amplitude decay per metre at bin 0 and per bin step
@@ -235,7 +236,7 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
                                double a0, double a1, cudaStream_t s);
 cudaError_t accumulate(const AccumArgs& a, cudaStream_t s);
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s);
-int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F);
+int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat);
 
 struct GatherArgs {
     // specular
