@@ -158,6 +158,34 @@ def oracle_sample(wl, n_sample_rays: int, nthreads: int = 0):
     return segs, dt, desc
 
 
+def measure_adjoint(st, torch, wl, steps: int = 5):
+    """Device time of one forward simulate and of one st_backward (all gradients) on a workload."""
+    ctx = st.Context(torch.cuda.current_device())
+    sc = st.from_workload(ctx, wl)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    S = ctx.simulate(sc, p)
+    G = torch.randn_like(S.real) + 1j * torch.randn_like(S.real)
+    G = G.to(torch.complex64)
+    n_mat, n_bands = wl.k_band.shape
+    for _ in range(2):
+        ctx.simulate(sc, p, out=S)
+        ctx.backward(sc, G, n_mat, n_bands)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd, bwd = [], []
+    for _ in range(steps):
+        ev[0].record(stream)
+        ctx.simulate(sc, p, out=S)
+        ev[1].record(stream)
+        ctx.backward(sc, G, n_mat, n_bands)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        bwd.append(ev[1].elapsed_time(ev[2]))
+    f, b = float(np.median(fwd)), float(np.median(bwd))
+    return {"fwd_ms": f, "bwd_ms": b, "bwd_over_fwd": b / f}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -192,6 +220,7 @@ def main():
     ap.add_argument("--cpu-rays", type=int, default=16384, help="rays in the oracle's CPU-baseline sample")
     ap.add_argument("--ref-rays", type=int, default=2048, help="rays per step of the reference (oracle) arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -309,6 +338,12 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(spec_h.nbytes),
                "ms_per_step": 1e3 * float(np.mean(e2e_t))}
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = {"gradient workload (shoebox, 4 materials x 16 bands, 32 mics, 128 bins, 10k rays x 3)":
+                   measure_adjoint(st, torch, synth.gradient_problem(seed=404)),
+                   f"{wl.name} workload": measure_adjoint(st, torch, wl)}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -331,7 +366,7 @@ def main():
                          "diffraction_kept": s0.candidates_kept, "terms": s0.terms,
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
                          "ms_accumulate": s0.ms_accumulate},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
     print(json.dumps(line))
     if world > 1:

@@ -172,6 +172,18 @@ st_status st_get_diffraction(st_ctx* ctx, int64_t* n_out, int32_t* tri, float* p
 /* Direct-path visibility per microphone of the last simulate. */
 st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
 
+/* Adjoint of the last simulate with its path set frozen (the paper has no gradients; this is the
+ * reverse pass of Eq. 2-4, 7-8 and 11-12).  grad_spectra = dL/dRe S + j dL/dIm S, device complex64
+ * [3][n_mics][n_bins] laid out like the spectra.  Writes, as device float32 (any may be NULL):
+ *   grad_k [n_mat][n_bands]: reflection band values (specular paths; assumes k > 0 at every bin),
+ *   grad_mic [n_mics][3]:    microphone positions (specular, diffraction and direct paths),
+ *   grad_emitter [3]:        emitter position through the diffraction and direct paths only.
+ * Position gradients need an omni emitter (ST_ERR_ARG otherwise).  scene must be the one of the
+ * last simulate, unchanged since (ST_ERR_STATE otherwise).  Deterministic: every sum runs in a fixed
+ * order.  Stream-ordered; allocates reduction buffers on first use. */
+st_status st_backward(st_ctx* ctx, st_scene* scene, const void* grad_spectra, float* grad_k, float* grad_mic,
+                      float* grad_emitter);
+
 /* Allocation-free specular accumulation.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory where they need spectra -- code running inside another
  * allocator's fixed memory budget or arena, real-time loops where cudaMalloc would stall or

@@ -13,10 +13,11 @@ import numpy as np
 import torch
 
 from . import _lib
+from .autograd import SpectraFn  # noqa: E402
 from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
                    SimParams, SonotraceError, Stats, check, load)
 
-__all__ = ["Context", "Scene", "CurvParams", "SimParams", "Stats", "SonotraceError", "sim_params", "curv_params",
+__all__ = ["Context", "Scene", "SpectraFn", "CurvParams", "SimParams", "Stats", "SonotraceError", "sim_params", "curv_params",
            "ST_COMP_SPECULAR", "ST_COMP_DIFFRACTION", "ST_COMP_DIRECT"]
 
 
@@ -79,6 +80,7 @@ class Context:
         self.F = int(n_bins)
 
     def set_emitter(self, pos, quat, dirs, table=None, fov_half: float = math.pi):
+        self.quat, self.dirs, self.fov_half = quat, dirs, fov_half
         pos = np.ascontiguousarray(pos, np.float32)
         quat = np.ascontiguousarray(quat, np.float32)
         d = _dev(dirs, torch.float32)
@@ -134,6 +136,17 @@ class Context:
         self._check(self.L.st_get_diffraction(self.h, C.byref(n), cp(tri), cp(p), cp(keep), K, ST_MEM_HOST))
         return tri[:K], p[:K], keep[:K]
 
+    def backward(self, scene: "Scene", grad_spectra: torch.Tensor, n_mat: int, n_bands: int):
+        """(dL/dk [n_mat][n_bands], dL/dmic [M][3], dL/demitter [3]) for grad_spectra = dL/dRe S + j dL/dIm S."""
+        dev = grad_spectra.device
+        g = grad_spectra.contiguous().to(torch.complex64)
+        gk = torch.zeros((n_mat, n_bands), dtype=torch.float32, device=dev)
+        gm = torch.zeros((self.M, 3), dtype=torch.float32, device=dev)
+        ge = torch.zeros(3, dtype=torch.float32, device=dev)
+        vp = lambda t: C.c_void_p(t.data_ptr())
+        self._check(self.L.st_backward(self.h, scene.h, vp(g), vp(gk), vp(gm), vp(ge)))
+        return gk, gm, ge
+
     def direct_visibility(self):
         v = np.empty(self.M, np.uint8)
         self._check(self.L.st_get_direct_visibility(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST))
@@ -157,6 +170,7 @@ class Scene:
         self.n_obj = int(o.max()) + 1
 
     def set_materials(self, band_hz, k, beta, diffr):
+        self.band_hz, self.k_band, self.beta_band, self.diff_band = band_hz, k, beta, diffr
         b = np.ascontiguousarray(band_hz, np.float32)
         k = np.ascontiguousarray(k, np.float32)
         be = np.ascontiguousarray(beta, np.float32)

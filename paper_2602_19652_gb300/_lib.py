@@ -70,6 +70,7 @@ SIGNATURES = {
     "st_get_paths": (I32, [P, P, P, P, P, P, I32]),
     "st_get_diffraction": (I32, [P, P, P, P, P, I64, I32]),
     "st_get_direct_visibility": (I32, [P, P, I32]),
+    "st_backward": (I32, [P, P, P, P, P, P]),
     "st_accumulate_specular_noalloc": (I32, [P, P, P, P, P, I64, I32, P, P, I32, I32, F64, F64, I32, I32, P, P, P,
                                              P, P, P]),
 }

@@ -26,6 +26,7 @@ UNITS = {
     "st_scene.cu": ["-fmad=false"],
     "st_trace.cu": ["-fmad=false"],
     "st_accum.cu": [],
+    "st_adjoint.cu": [],
     "st_noalloc.cu": [],
 }
 

@@ -1,0 +1,364 @@
+// Device code shared by the spectrum accumulator and its adjoint: float-float arithmetic, packed
+// FP32 pairs, the CTA tile geometry and the producer of per-tile tables and anchors.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "st_internal.cuh"
+
+namespace st {
+namespace acc {
+
+// ---------------------------------------------------------------- float-float arithmetic
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return ff{s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    float s = a + b;
+    float e = b - (s - a);
+    return ff{s, e};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    float p = a * b;
+    float e = fmaf(a, b, -p);
+    return ff{p, e};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    float e = s.lo + (x.lo + y.lo);
+    return fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    ff p = two_prod(x.hi, y.hi);
+    float e = p.lo + fmaf(x.hi, y.lo, x.lo * y.hi);
+    return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+    if (!(x.hi > 0.0f)) return ff{0.0f, 0.0f};
+    float s = sqrtf(x.hi);
+    ff p = two_prod(s, s);
+    float d = (((x.hi - p.hi) - p.lo) + x.lo) / (2.0f * s);
+    return fast_two_sum(s, d);
+}
+// |a - b| for float32 points, ~2^-44 relative
+__device__ __forceinline__ ff dist_ff(float ax, float ay, float az, float bx, float by, float bz) {
+    ff dx = two_sum(ax, -bx), dy = two_sum(ay, -by), dz = two_sum(az, -bz);
+    ff sx = two_prod(dx.hi, dx.hi);
+    sx.lo = fmaf(2.0f * dx.hi, dx.lo, sx.lo);
+    ff sy = two_prod(dy.hi, dy.hi);
+    sy.lo = fmaf(2.0f * dy.hi, dy.lo, sy.lo);
+    ff sz = two_prod(dz.hi, dz.hi);
+    sz.lo = fmaf(2.0f * dz.hi, dz.lo, sz.lo);
+    return ff_sqrt(ff_add(ff_add(sx, sy), sz));
+}
+// fractional part in [-0.5, 0.5] of a non-negative float-float
+__device__ __forceinline__ float ff_frac(ff x) {
+    float n = rintf(x.hi);
+    return (x.hi - n) + x.lo;
+}
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float log2_ff(ff r) { return log2f(r.hi) + r.lo / (r.hi * 0.69314718055994531f); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+constexpr float kNegInf = -__builtin_huge_valf();
+
+// ---------------------------------------------------------------- accumulator
+// Packed FP32 pairs (fma/mul .f32x2, sm_100 and later): one 64-bit register holds the same
+// quantity for two microphones, so every inner-loop instruction advances two terms.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up2(u64 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// (zr, zi) *= (wr, wi) for two microphones at once; nwi = -wi
+__device__ __forceinline__ void cmul2(u64& zr, u64& zi, u64 wr, u64 wi, u64 nwi) {
+    const u64 t1 = fmul2(zr, wr), t2 = fmul2(zi, wr);
+    const u64 r = ffma2(zi, nwi, t1);
+    zi = ffma2(zr, wi, t2);
+    zr = r;
+}
+
+struct Geom {
+    int TP, NS, MP, KB, PT;  // mic pairs per CTA (threads along x), subtiles, mics per CTA, bins per CTA, paths/tile
+    int n_mb, n_bb;
+    int mat_cached;          // material tables held in shared memory (n_mat small enough)
+    size_t mat_bytes;        // their size
+    size_t buf_bytes;        // one pipeline buffer (tables + anchors of PT paths)
+    size_t smem;
+};
+
+// Shared memory: two pipeline buffers, each
+//   tab [PT][KB] float4      per (path, bin): (log2 X, log2 X, g, g) specular, (X, X, -, -) diffraction,
+//                            bin kb + s*KT + kk stored at i = kk*NS + s
+//   za  [PT][NS][TP] ulonglong2  phasor at bin kb + s*KT of the two mics of pair tp (re pair, im pair)
+//   wst [PT][TP][4] u64      one-bin step (re, im) and two-bin step (re, im) of the pair
+//   ngp [PT][TP] u64         -gamma^2 of the pair
+// then two path-data buffers pd [PT][12] + valid [PT], then the per-CTA material tables.
+struct Buf {
+    float4* tab;
+    ulonglong2* za;
+    u64* wst;
+    u64* ngp;
+};
+
+template <int KT>
+__device__ __forceinline__ Buf buf_at(float4* base, const Geom& g, int b) {
+    Buf B;
+    char* p = reinterpret_cast<char*>(base) + (size_t)b * g.buf_bytes;
+    B.tab = reinterpret_cast<float4*>(p);
+    B.za = reinterpret_cast<ulonglong2*>(B.tab + (size_t)g.PT * g.KB);
+    B.wst = reinterpret_cast<u64*>(B.za + (size_t)g.PT * g.NS * g.TP);
+    B.ngp = B.wst + (size_t)g.PT * g.TP * 4;
+    return B;
+}
+
+// path data of one tile into pd / pv
+template <int KIND>
+__device__ __forceinline__ void load_paths(const AccumArgs& a, int PT, int64_t pbase, int64_t count, float* pd, int* pv) {
+    for (int p = threadIdx.x; p < PT; p += blockDim.x) {
+        const int64_t pi = pbase + p;
+        const bool ok = pi < count;
+        pv[p] = ok;
+        float* d = pd + p * 12;
+        if (ok) {
+            d[0] = a.px[pi];
+            d[1] = a.py[pi];
+            d[2] = a.pz[pi];
+            d[6] = a.rhi[pi];
+            d[7] = a.rlo[pi];
+            d[8] = __uint_as_float(a.meta[pi]);
+            d[11] = a.dep ? a.dep[pi] : -1.0f;
+            if (KIND == 0) {
+                d[3] = a.dx[pi];
+                d[4] = a.dy[pi];
+                d[5] = a.dz[pi];
+                d[9] = __uint_as_float(a.chain_lo[pi]);
+                d[10] = __uint_as_float(a.chain_hi[pi]);
+            }
+        }
+    }
+}
+
+// tables and anchors of one tile (reads pd / pv, writes buffer B)
+template <int KT, int KIND>
+__device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const Buf& B, const float* pd, const int* pv,
+                                        const float* mt, int mic0, int kb, float invNS, float invKB) {
+    const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
+    const bool cached = g.mat_cached > 0;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    // 1a: per (path, bin) factors, written in table order.  With NS % 4 == 0 and the material tables in
+    // shared memory, a thread builds four adjacent entries (same path and kk, subtiles s..s+3): one chain
+    // decode, 128-bit loads of the material rows and four conflict-free 128-bit stores.
+    if (cached && (NS & 3) == 0 && !a.etab) {
+        const int KB4 = KB >> 2;
+        const float invKB4 = 1.0f / (float)KB4;
+        for (int e = tid; e < PT * KB4; e += nthr) {
+            const int p = __float2int_rz(((float)e + 0.5f) * invKB4), i = (e - p * KB4) * 4;
+            const int kk = __float2int_rz(((float)i + 0.5f) * invNS), s_ = i - kk * NS;
+            float4 lx4 = make_float4(kNegInf, kNegInf, kNegInf, kNegInf), g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (pv[p]) {
+                const float* d = pd + p * 12;
+                const uint32_t meta = __float_as_uint(d[8]);
+                const int matj = (meta >> 8) & 255;
+                if (KIND == 0) {
+                    if (a.reflection_mode == 1) {
+                        lx4 = *reinterpret_cast<const float4*>(mt + matj * KB + i);
+                    } else {
+                        const int len = meta & 15;
+                        const uint32_t c0 = __float_as_uint(d[9]), c1 = __float_as_uint(d[10]);
+                        lx4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int q = 0; q < len; ++q) {
+                            const int mq = (q < 4 ? (c0 >> (8 * q)) : (c1 >> (8 * (q - 4)))) & 255;
+                            const float4 v = *reinterpret_cast<const float4*>(mt + mq * KB + i);
+                            lx4.x += v.x;
+                            lx4.y += v.y;
+                            lx4.z += v.z;
+                            lx4.w += v.w;
+                        }
+                    }
+                    g4 = *reinterpret_cast<const float4*>(mt + a.n_mat_tab * KB + matj * KB + i);
+                } else {
+                    lx4 = *reinterpret_cast<const float4*>(mt + matj * KB + i);
+                }
+                // bins beyond the grid contribute nothing
+                const int k0 = kb + s_ * KT + kk;
+                if (k0 >= a.F) lx4.x = kNegInf;
+                if (k0 + KT >= a.F) lx4.y = kNegInf;
+                if (k0 + 2 * KT >= a.F) lx4.z = kNegInf;
+                if (k0 + 3 * KT >= a.F) lx4.w = kNegInf;
+            }
+            float4* dst = B.tab + (size_t)p * KB + i;
+            if (KIND == 0) {
+                dst[0] = make_float4(lx4.x, lx4.x, g4.x, g4.x);
+                dst[1] = make_float4(lx4.y, lx4.y, g4.y, g4.y);
+                dst[2] = make_float4(lx4.z, lx4.z, g4.z, g4.z);
+                dst[3] = make_float4(lx4.w, lx4.w, g4.w, g4.w);
+            } else {
+                const float x0 = ex2(lx4.x), x1 = ex2(lx4.y), x2 = ex2(lx4.z), x3 = ex2(lx4.w);
+                dst[0] = make_float4(x0, x0, 0.f, 0.f);
+                dst[1] = make_float4(x1, x1, 0.f, 0.f);
+                dst[2] = make_float4(x2, x2, 0.f, 0.f);
+                dst[3] = make_float4(x3, x3, 0.f, 0.f);
+            }
+        }
+    } else {
+        for (int e = tid; e < PT * KB; e += nthr) {
+            const int p = __float2int_rz(((float)e + 0.5f) * invKB), i = e - p * KB;
+            const int kk = __float2int_rz(((float)i + 0.5f) * invNS), s_ = i - kk * NS;
+            const int k = kb + s_ * KT + kk;
+            float lx = kNegInf, gg = 0.0f;
+            if (pv[p] && k < a.F) {
+                const float* d = pd + p * 12;
+                const uint32_t meta = __float_as_uint(d[8]);
+                const int matj = (meta >> 8) & 255;
+                const int nm = a.n_mat_tab;
+                if (KIND == 0) {
+                    if (a.reflection_mode == 1) {
+                        lx = cached ? mt[matj * KB + i] : a.lk[(int64_t)matj * a.F + k];
+                    } else {
+                        const int len = meta & 15;
+                        const uint32_t c0 = __float_as_uint(d[9]), c1 = __float_as_uint(d[10]);
+                        float acc = 0.0f;
+                        for (int q = 0; q < len; ++q) {
+                            const int mq = (q < 4 ? (c0 >> (8 * q)) : (c1 >> (8 * (q - 4)))) & 255;
+                            acc += cached ? mt[mq * KB + i] : a.lk[(int64_t)mq * a.F + k];
+                        }
+                        lx = acc;
+                    }
+                    gg = cached ? mt[nm * KB + matj * KB + i] : a.g2[(int64_t)matj * a.F + k];
+                } else {
+                    lx = cached ? mt[matj * KB + i] : a.lid[(int64_t)matj * a.F + k];
+                }
+                if (a.etab && d[11] >= 0.0f) {
+                    const float x = d[11];
+                    const int it = min((int)x, a.n_theta - 2);
+                    const float w = x - (float)it;
+                    const float de = (1.0f - w) * a.etab[(int64_t)it * a.F + k] + w * a.etab[(int64_t)(it + 1) * a.F + k];
+                    lx += de > 0.0f ? log2f(de) : kNegInf;
+                }
+            }
+            if (KIND == 0) {
+                B.tab[(size_t)p * KB + i] = make_float4(lx, lx, gg, gg);
+            } else {
+                const float x = ex2(lx);
+                B.tab[(size_t)p * KB + i] = make_float4(x, x, 0.0f, 0.0f);
+            }
+        }
+    }
+    // 1b: per (path, mic) anchors
+    for (int e = tid; e < PT * MP; e += nthr) {
+        const int p = e / MP, ml = e - p * MP;
+        const int pair = ml >> 1, half = ml & 1;
+        const int m = mic0 + ml;
+        float* zf = reinterpret_cast<float*>(B.za + (size_t)p * NS * TP + pair);
+        float* wf = reinterpret_cast<float*>(B.wst + ((size_t)p * TP + pair) * 4);
+        float* nf = reinterpret_cast<float*>(B.ngp + (size_t)p * TP + pair);
+        if (!pv[p] || m >= a.M) {
+            for (int s_ = 0; s_ < NS; ++s_) {
+                zf[(size_t)s_ * TP * 4 + half] = 0.0f;
+                zf[(size_t)s_ * TP * 4 + 2 + half] = 0.0f;
+            }
+            for (int q = 0; q < 4; ++q) wf[2 * q + half] = 0.0f;
+            nf[half] = 0.0f;
+            continue;
+        }
+        const float* d = pd + p * 12;
+        const float mx = a.mics[3 * m], my = a.mics[3 * m + 1], mz = a.mics[3 * m + 2];
+        const ff dist = dist_ff(mx, my, mz, d[0], d[1], d[2]);
+        const ff r = ff_add(ff{d[6], d[7]}, dist);
+        float gam2 = 0.0f;
+        if (KIND == 0) {
+            const float inv = 1.0f / dist.hi;
+            const float ux = (mx - d[0]) * inv, uy = (my - d[1]) * inv, uz = (mz - d[2]) * inv;
+            const float cg = d[3] * ux + d[4] * uy + d[5] * uz;
+            const float cx = d[4] * uz - d[5] * uy, cy = d[5] * ux - d[3] * uz, cz = d[3] * uy - d[4] * ux;
+            const float gm = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), cg);
+            gam2 = gm * gm;
+        }
+        const float rh = r.hi;
+        const float L0 = -2.0f * log2_ff(r) + rh * (a.atm2_0 + a.atm2_step * (float)kb);
+        const ff x0 = ff_mul(r, ff{a.qhi[min(kb, a.F - 1)], a.qlo[min(kb, a.F - 1)]});
+        float s0, c0;
+        sincospif(2.0f * ff_frac(x0), &s0, &c0);
+        const float A0 = ex2(L0);
+        float2 z = make_float2(A0 * c0, A0 * s0);
+        const ff xs = ff_mul(r, ff{a.dq_hi, a.dq_lo});
+        float s1, c1;
+        sincospif(2.0f * ff_frac(xs), &s1, &c1);
+        const float a1 = ex2(rh * a.atm2_step);
+        const float2 W1 = make_float2(a1 * c1, a1 * s1);
+        const float2 W2 = cmul(W1, W1);  // two bins
+        wf[0 + half] = W1.x;
+        wf[2 + half] = W1.y;
+        wf[4 + half] = W2.x;
+        wf[6 + half] = W2.y;
+        nf[half] = -gam2;
+        float2 WK = W2;  // KT bins by repeated squaring (KT is a power of two)
+        for (int q = 2; q < KT; q *= 2) WK = cmul(WK, WK);
+        for (int s_ = 0; s_ < NS; ++s_) {
+            zf[(size_t)s_ * TP * 4 + half] = z.x;
+            zf[(size_t)s_ * TP * 4 + 2 + half] = z.y;
+            z = cmul(z, WK);
+        }
+    }
+}
+
+
+// tp_max: mic pairs per CTA at most; budget: shared-memory bytes per CTA
+inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t budget = 96 * 1024) {
+    Geom g;
+    const int pairs = (M + 1) / 2;
+    const int ns_need = (F + KT - 1) / KT;
+    g.TP = std::max(1, std::min(pairs, tp_max));
+    g.NS = std::max(1, std::min(ns_need, 256 / g.TP));
+    g.TP = std::max(1, std::min(pairs, 256 / g.NS));
+    g.MP = 2 * g.TP;
+    g.KB = g.NS * KT;
+    g.n_mb = (M + g.MP - 1) / g.MP;
+    g.n_bb = (F + g.KB - 1) / g.KB;
+    const size_t per_path = (size_t)g.KB * 16 + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40;
+    const size_t mat_bytes = (size_t)2 * n_mat * g.KB * 4;
+    g.mat_cached = mat_bytes <= 24 * 1024 ? 1 : 0;
+    g.mat_bytes = mat_bytes;
+    const size_t fixed = g.mat_cached ? mat_bytes : 0;
+    const size_t avail = budget > fixed + 4096 ? budget - fixed : 4096;
+    g.PT = (int)std::min<size_t>(8, std::max<size_t>(1, avail / (2 * per_path + 2 * 52)));
+    g.buf_bytes = (per_path * g.PT + 255) & ~size_t(255);
+    g.smem = 2 * g.buf_bytes + 2 * (size_t)g.PT * 52 + 16 + fixed + 64;  // 16: alignment of the material tables
+    return g;
+}
+
+}  // namespace acc
+}  // namespace st

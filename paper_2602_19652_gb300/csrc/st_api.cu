@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "st_accum_dev.cuh"
 #include "st_internal.cuh"
 
 using namespace st;
@@ -78,15 +79,19 @@ struct st_ctx {
     // work buffers
     DevBuf st_o[3], st_d[3], st_r, st_prev, q0, q1, counts, queries, flags, R, rec_tri, rec_p, rec_d, rec_r, rec_los;
     DevBuf sflags, sscan, sidx, scratch;
-    PathList paths;
+    PathList paths, paths_diff;  // gathered specular / diffraction paths of the last simulate
     DevBuf cand_tri, cand_p, keep, dvis, partial;
     DevBuf host_out;
+    DevBuf adj_v, adj_mic, adj_emit;  // adjoint partial sums
+    const st_scene* last_scene = nullptr;
+    uint64_t last_scene_version = 0;
     int64_t last_N = 0, last_K = 0;
     int32_t last_B = 0, last_M = 0, last_F = 0;
     bool has_last = false;
     // last simulate parameters (for the adjoint)
     st_sim_params last_params;
     int32_t last_chunks_spec = 0, last_chunks_diff = 0;
+    float last_fwd[3] = {1, 0, 0};
     bool count_visits = false;  // ST_COUNT_VISITS=1 in the environment: node/triangle visit counters
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
@@ -199,9 +204,11 @@ st_status st_destroy(st_ctx* c) {
                       &c->cand_tri, &c->cand_p, &c->keep, &c->dvis, &c->partial, &c->host_out, &c->tables.lk,
                       &c->tables.g2, &c->tables.lid, &c->tables.qhi, &c->tables.qlo})
         release(*b);
-    PathList& P = c->paths;
-    for (DevBuf* b : {&P.px, &P.py, &P.pz, &P.dx, &P.dy, &P.dz, &P.rhi, &P.rlo, &P.chain_lo, &P.chain_hi, &P.meta, &P.dep})
-        release(*b);
+    for (PathList* P : {&c->paths, &c->paths_diff})
+        for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
+                          &P->meta, &P->dep})
+            release(*b);
+    for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband}) release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -408,8 +415,7 @@ st_status st_set_frequencies(st_ctx* c, int32_t n_bins, double f_lo, double f_hi
 }
 
 // ------------------------------------------------------------------ simulate
-static st_status ensure_paths(st_ctx* c, int64_t n) {
-    PathList& P = c->paths;
+static st_status ensure_paths(st_ctx* c, PathList& P, int64_t n) {
     if (P.n_max >= n) return ST_OK;
     for (DevBuf* b : {&P.px, &P.py, &P.pz, &P.dx, &P.dy, &P.dz, &P.rhi, &P.rlo, &P.chain_lo, &P.chain_hi, &P.meta, &P.dep})
         CKC(c, grow(*b, (size_t)std::max<int64_t>(n, 1) * 4), "path list alloc");
@@ -475,7 +481,9 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, grow(c->sidx, (size_t)nflag * 4), "alloc");
     CKC(c, grow(c->scratch, scan_scratch_bytes(nflag)), "alloc");
     CKC(c, grow(c->dvis, (size_t)M), "alloc");
-    st_status ps = ensure_paths(c, std::max<int64_t>(NB, K));
+    st_status ps = ensure_paths(c, c->paths, std::max<int64_t>(NB, 1));
+    if (ps != ST_OK) return ps;
+    ps = ensure_paths(c, c->paths_diff, std::max<int64_t>(K, 1));
     if (ps != ST_OK) return ps;
     if (K > 0) {
         CKC(c, grow(c->cand_tri, (size_t)K * 4), "alloc");
@@ -636,9 +644,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     ga.keep = ptr<uint8_t>(c->keep);
     memcpy(ga.s, c->s, 12);
     ga.idx = ptr<uint32_t>(c->sidx);
-    ga.out = &c->paths;
-    PathList& PL = c->paths;
-    auto set_paths = [&](AccumArgs& x) {
+    auto set_paths = [&](AccumArgs& x, PathList& PL) {
         x.px = ptr<float>(PL.px);
         x.py = ptr<float>(PL.py);
         x.pz = ptr<float>(PL.pz);
@@ -663,12 +669,13 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, ptr<uint32_t>(c->sidx), s),
             "compact");
         ga.count = cnt + 2;
+        ga.out = &c->paths;
         CKC(c, gather_specular(ga, s), "gather");
         AccumArgs x = aa;
         x.kind = 0;
         x.n_paths = NB;
         x.d_count = cnt + 2;
-        set_paths(x);
+        set_paths(x, c->paths);
         x.n_chunks = chunks_spec;
         if (stats) CKC(c, cudaEventRecord(c->ev[4], s), "event");
         CKC(c, accumulate(x, s), "accumulate specular");
@@ -684,12 +691,13 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), K, ptr<uint32_t>(c->sidx), s),
             "compact");
         ga.count = cnt + 3;
+        ga.out = &c->paths_diff;
         CKC(c, gather_diffraction(ga, s), "gather");
         AccumArgs x = aa;
         x.kind = 1;
         x.n_paths = K;
         x.d_count = cnt + 3;
-        set_paths(x);
+        set_paths(x, c->paths_diff);
         x.n_chunks = chunks_diff;
         if (stats) CKC(c, cudaEventRecord(c->ev[6], s), "event");
         CKC(c, accumulate(x, s), "accumulate diffraction");
@@ -742,7 +750,12 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     c->last_M = M;
     c->last_F = F;
     c->last_params = p;
+    c->last_scene = sc;
+    c->last_scene_version = sc->version;
     c->last_chunks_spec = chunks_spec;
+    c->last_fwd[0] = fwd[0];
+    c->last_fwd[1] = fwd[1];
+    c->last_fwd[2] = fwd[2];
     c->last_chunks_diff = chunks_diff;
     c->has_last = true;
 
@@ -840,6 +853,153 @@ st_status st_get_direct_visibility(st_ctx* c, uint8_t* vis, int32_t mem) {
     cudaSetDevice(c->device);
     CKC(c, cudaMemcpyAsync(vis, c->dvis.p, (size_t)c->last_M, kind_out(mem), c->stream), "get_direct_visibility");
     CKC(c, cudaStreamSynchronize(c->stream), "sync");
+    return ST_OK;
+}
+
+st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* grad_k, float* grad_mic,
+                      float* grad_emitter) {
+    if (!c || !sc || !grad_spectra) return fail(c, ST_ERR_ARG, "backward: null argument");
+    if (!c->has_last || c->last_scene != sc || c->last_scene_version != sc->version)
+        return fail(c, ST_ERR_STATE, "backward: needs the last simulate of this scene, unchanged since");
+    if ((grad_mic || grad_emitter) && c->n_theta > 0)
+        return fail(c, ST_ERR_ARG, "backward: position gradients need an omni emitter");
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const st_sim_params& p = c->last_params;
+    SceneDev& S = sc->S;
+    AccumTables& T = c->tables;
+    const int32_t M = c->last_M, F = c->last_F;
+    const int64_t MF = (int64_t)M * F;
+    const float2* G = static_cast<const float2*>(grad_spectra);
+    const bool want_pos = grad_mic || grad_emitter;
+    uint32_t* cnt = ptr<uint32_t>(c->counts);
+
+    const double l10 = log(10.0) / 20.0;
+    AccumArgs aa{};
+    aa.mics = ptr<float>(c->mics);
+    aa.M = M;
+    aa.F = F;
+    aa.lk = ptr<float>(T.lk);
+    aa.g2 = ptr<float>(T.g2);
+    aa.lid = ptr<float>(T.lid);
+    aa.n_mat_tab = T.n_mat;
+    aa.qhi = ptr<float>(T.qhi);
+    aa.qlo = ptr<float>(T.qlo);
+    {
+        const double dq = T.df / p.c;
+        aa.dq_hi = (float)dq;
+        aa.dq_lo = (float)(dq - (double)aa.dq_hi);
+        const double l2 = log2(10.0) / 20.0;
+        aa.atm2_0 = (float)(-(p.alpha0_db_m + p.alpha1_db_m_khz * c->f_lo / 1000.0) * l2);
+        aa.atm2_step = (float)(-(p.alpha1_db_m_khz * T.df / 1000.0) * l2);
+    }
+    aa.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
+    aa.n_theta = c->n_theta;
+    aa.reflection_mode = p.reflection_mode;
+    AdjointArgs ja{};
+    memcpy(ja.s, c->s, 12);
+    ja.a_0 = (float)((p.alpha0_db_m + p.alpha1_db_m_khz * c->f_lo / 1000.0) * l10);
+    ja.a_step = (float)(p.alpha1_db_m_khz * T.df / 1000.0 * l10);
+    ja.w_0 = (float)(2.0 * M_PI * c->f_lo / p.c);
+    ja.w_step = (float)(2.0 * M_PI * T.df / p.c);
+
+    const acc::Geom g = adjoint_geom(M, F, T.n_mat);
+    const int ctas = g.n_mb * g.n_bb;
+    // path counts of the last simulate size the chunking (one small read-back)
+    uint32_t hc[4] = {0, 0, 0, 0};
+    CKC(c, cudaMemcpyAsync(hc, cnt, 16, cudaMemcpyDeviceToHost, s), "backward counts");
+    CKC(c, cudaStreamSynchronize(s), "backward counts");
+    const int64_t n_paths = std::max<int64_t>(hc[2], hc[3]);
+    const int64_t tiles = std::max<int64_t>(1, (n_paths + g.PT - 1) / g.PT);
+    const int32_t chunks = (int32_t)std::max<int64_t>(
+        1, std::min<int64_t>(152 / std::max(ctas, 1) * 2, (tiles + 7) / 8));
+    const int spec_mic_slices = chunks * g.n_bb, spec_emit_slices = chunks * ctas;
+    const int mic_slices = 2 * spec_mic_slices + 1;                 // specular, diffraction, direct
+    const int emit_slices = 2 * spec_emit_slices + M;               // direct: one slice per microphone
+    CKC(c, grow(c->adj_v, (size_t)chunks * g.n_mb * 4 * F * 4), "alloc");
+    CKC(c, grow(c->adj_mic, (size_t)mic_slices * M * 3 * 4), "alloc");
+    CKC(c, grow(c->adj_emit, (size_t)emit_slices * 3 * 4), "alloc");
+    CKC(c, cudaMemsetAsync(c->adj_mic.p, 0, (size_t)mic_slices * M * 3 * 4, s), "memset");
+    CKC(c, cudaMemsetAsync(c->adj_emit.p, 0, (size_t)emit_slices * 3 * 4, s), "memset");
+    float* micp = ptr<float>(c->adj_mic);
+    float* emitp = ptr<float>(c->adj_emit);
+    if (grad_k) CKC(c, cudaMemsetAsync(grad_k, 0, (size_t)S.n_mat * S.n_bands * 4, s), "memset");
+
+    auto set_paths = [&](AccumArgs& x, PathList& PL) {
+        x.px = ptr<float>(PL.px);
+        x.py = ptr<float>(PL.py);
+        x.pz = ptr<float>(PL.pz);
+        x.dx = ptr<float>(PL.dx);
+        x.dy = ptr<float>(PL.dy);
+        x.dz = ptr<float>(PL.dz);
+        x.rhi = ptr<float>(PL.rhi);
+        x.rlo = ptr<float>(PL.rlo);
+        x.chain_lo = ptr<uint32_t>(PL.chain_lo);
+        x.chain_hi = ptr<uint32_t>(PL.chain_hi);
+        x.meta = ptr<uint32_t>(PL.meta);
+        x.dep = ptr<float>(PL.dep);
+    };
+    // ---- specular: reflection sums in batches of four materials, positions with the first batch
+    if ((p.components & ST_COMP_SPECULAR) && c->last_N > 0 && (grad_k || want_pos)) {
+        AccumArgs x = aa;
+        x.kind = 0;
+        x.d_count = cnt + 2;
+        x.n_chunks = chunks;
+        set_paths(x, c->paths);
+        const int n_batches = grad_k ? (S.n_mat + 3) / 4 : 1;
+        for (int bt = 0; bt < n_batches; ++bt) {
+            AdjointArgs jj = ja;
+            jj.G = G;
+            jj.do_pos = (bt == 0 && want_pos) ? 1 : 0;
+            jj.do_k = grad_k ? 1 : 0;
+            jj.mat_base = 4 * bt;
+            jj.v_part = ptr<float>(c->adj_v);
+            jj.mic_part = micp;
+            jj.emit_part = emitp;
+            CKC(c, adjoint_launch(x, jj, g, s), "adjoint specular");
+            if (grad_k)
+                CKC(c, adjoint_dk(ptr<float>(c->adj_v), chunks * g.n_mb, F, 4 * bt, std::min(4, S.n_mat - 4 * bt),
+                                  S.n_bands, ptr<float>(T.band), ptr<float>(T.kband), c->f_lo, T.df, grad_k, S.n_mat,
+                                  s),
+                    "adjoint dk");
+        }
+    }
+    // ---- diffraction: positions
+    if (want_pos && c->last_K > 0) {
+        AccumArgs x = aa;
+        x.kind = 1;
+        x.d_count = cnt + 3;
+        x.n_chunks = chunks;
+        set_paths(x, c->paths_diff);
+        AdjointArgs jj = ja;
+        jj.G = G + MF;
+        jj.do_pos = 1;
+        jj.do_k = 0;
+        jj.v_part = ptr<float>(c->adj_v);
+        jj.mic_part = micp + (size_t)spec_mic_slices * M * 3;
+        jj.emit_part = emitp + (size_t)spec_emit_slices * 3;
+        CKC(c, adjoint_launch(x, jj, g, s), "adjoint diffraction");
+    }
+    // ---- direct path
+    if (want_pos && (p.components & ST_COMP_DIRECT)) {
+        DirectAccumArgs da{};
+        memcpy(da.s, c->s, 12);
+        da.mics = ptr<float>(c->mics);
+        da.M = M;
+        da.F = F;
+        da.vis = ptr<uint8_t>(c->dvis);
+        da.f_lo = c->f_lo;
+        da.df = T.df;
+        da.c = p.c;
+        da.a0 = p.alpha0_db_m;
+        da.a1 = p.alpha1_db_m_khz;
+        da.gain = p.direct_gain;
+        CKC(c, adjoint_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), G + 2 * MF,
+                              micp + (size_t)2 * spec_mic_slices * M * 3, emitp + (size_t)2 * spec_emit_slices * 3, s),
+            "adjoint direct");
+    }
+    if (want_pos)
+        CKC(c, adjoint_pos(micp, mic_slices, emitp, emit_slices, M, grad_mic, grad_emitter, s), "adjoint reduce");
     return ST_OK;
 }
 

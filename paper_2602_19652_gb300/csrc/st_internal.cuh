@@ -201,7 +201,8 @@ struct PathList {
 };
 
 struct AccumTables {
-    int32_t F = 0, n_mat = 0;
+    int32_t F = 0, n_mat = 0, n_bands = 0;
+    DevBuf band, kband;  // device copies of the band centres and reflection band values (adjoint)
     DevBuf lk;     // [n_mat][F] log2 k(mat, f)
     DevBuf g2;     // [n_mat][F] lobe exponent 1/(2 beta^2) * log2(e)
     DevBuf lid;    // [n_mat][F] log2 I_d(mat, f)
@@ -258,6 +259,20 @@ cudaError_t flags_visible_records(const int32_t* rec_tri, const uint8_t* rec_los
 cudaError_t flags_from_u8(const uint8_t* keep, int64_t n, uint32_t* flags, cudaStream_t s);
 cudaError_t compact_indices(const uint32_t* flags, const uint32_t* scan, int64_t n, uint32_t* idx, cudaStream_t s);
 
+// Adjoint of one accumulation launch (st_adjoint.cu).
+struct AdjointArgs {
+    const float2* G;        // [M][F] dL/dRe S + j dL/dIm S of this component
+    int do_pos;             // accumulate microphone / emitter position gradients
+    int do_k;               // accumulate reflection sums V for materials mat_base .. mat_base + 3
+    int mat_base;
+    float* v_part;          // [n_chunks * n_mb][4][F]
+    float* mic_part;        // [n_chunks * n_bb][M][3]
+    float* emit_part;       // [n_chunks * n_mb * n_bb][3]
+    float s[3];             // emitter
+    float a_0, a_step;      // amplitude decay (nepers per metre) at bin 0 and per bin
+    float w_0, w_step;      // 2 pi f / c at bin 0 and per bin (rad per metre)
+};
+
 struct DirectAccumArgs {
     float s[3];
     const float* mics; int32_t M, F;
@@ -268,5 +283,19 @@ struct DirectAccumArgs {
     float2* out;           // [M][F] (component 2 of the spectra)
 };
 cudaError_t accumulate_direct(const DirectAccumArgs& a, const float* qhi, const float* qlo, cudaStream_t s);
+
+namespace acc {
+struct Geom;
+}
+acc::Geom adjoint_geom(int M, int F, int n_mat);
+size_t adjoint_smem(const acc::Geom& g);
+cudaError_t adjoint_launch(const AccumArgs& a, const AdjointArgs& j, const acc::Geom& g, cudaStream_t s);
+cudaError_t adjoint_direct(const DirectAccumArgs& a, const float* qhi, const float* qlo, const float2* G,
+                           float* mic_out, float* emit_out, cudaStream_t s);
+cudaError_t adjoint_dk(const float* v_part, int n_slices, int F, int mat_base, int n_mat_launch, int n_bands,
+                       const float* band_hz_dev, const float* k_dev, double f_lo, double df, float* dk, int n_mat,
+                       cudaStream_t s);
+cudaError_t adjoint_pos(const float* mic_parts, int n_mic_slices, const float* emit_parts, int n_emit_slices, int M,
+                        float* dmic, float* demit, cudaStream_t s);
 
 }  // namespace st

@@ -1,0 +1,80 @@
+"""GPU adjoint (st_backward) against the oracle's float64 analytic gradient, and the autograd
+wrapper against st_backward, on frozen path sets.  Bar: relative error <= 1e-3 per gradient block
+(the oracle's gradient is itself pinned to float64 central differences in test_oracle_spectra)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-3
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.fixture(scope="module")
+def torch_st():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_19652_gb300 as st
+    return torch, st
+
+
+def grads_vs_oracle(torch, st, wl, curv=None, mode=0):
+    import oracle
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, None if curv is None else st.curv_params(sample_budget=curv))
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance, reflection_mode=mode)
+    S = ctx.simulate(sc, p)
+    rng = np.random.default_rng(7)
+    target = torch.as_tensor(rng.normal(size=S.shape) + 1j * rng.normal(size=S.shape), dtype=torch.complex64,
+                             device=S.device) * S.abs().mean()
+    G = 2.0 * (S - target)
+    gk, gm, ge = ctx.backward(sc, G, wl.k_band.shape[0], wl.k_band.shape[1])
+    o = oracle.simulate(wl, curv=None if curv is None else dict(budget=curv), reflection_mode=mode)
+    dk, dmic, demit = oracle.spectra_grad(o["params"], o["rec"], wl.dirs, wl.tri_mat, G.cpu().numpy().astype(np.complex128),
+                                          o.get("cand_tri"), o.get("cand_p"), o.get("cand_keep"), o["direct_vis"])
+    return gk.cpu().numpy(), gm.cpu().numpy(), ge.cpu().numpy(), dk, dmic, demit
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gradient_workload_matches_oracle(torch_st, mode):
+    torch, st = torch_st
+    wl = synth.gradient_problem(n_rays=2000)
+    wl.n_bins = 64
+    gk, gm, ge, dk, dmic, demit = grads_vs_oracle(torch, st, wl, mode=mode)
+    assert rel(gk, dk) <= TOL, rel(gk, dk)
+    assert rel(gm, dmic) <= TOL, rel(gm, dmic)
+    assert rel(ge, demit) <= TOL, rel(ge, demit)
+
+
+def test_clutter_gradient_with_diffraction(torch_st):
+    torch, st = torch_st
+    wl = synth.clutter(seed=202, target_tris=20_000, n_rays=20_000, bounces=4, n_mics=6, n_bins=40)
+    gk, gm, ge, dk, dmic, demit = grads_vs_oracle(torch, st, wl, curv=100_000)
+    assert rel(gk, dk) <= TOL, rel(gk, dk)
+    assert rel(gm, dmic) <= TOL, rel(gm, dmic)
+    assert rel(ge, demit) <= TOL, rel(ge, demit)
+
+
+def test_autograd_function(torch_st):
+    torch, st = torch_st
+    wl = synth.gradient_problem(n_rays=1000)
+    wl.n_bins = 32
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    k = torch.tensor(wl.k_band, device="cuda", requires_grad=True)
+    m = torch.tensor(wl.mics, device="cuda", requires_grad=True)
+    e = torch.tensor(wl.emitter, device="cuda", requires_grad=True)
+    S = st.SpectraFn.apply(ctx, sc, p, k, m, e)
+    loss = (S.abs() ** 2).sum()
+    loss.backward()
+    gk, gm, ge = ctx.backward(sc, 2.0 * S.detach(), k.shape[0], k.shape[1])
+    # autograd forms dL/dS of |S|^2 through abs(), so it differs from 2 S by rounding only
+    for a, b in ((k.grad, gk), (m.grad, gm), (e.grad, ge)):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()))
