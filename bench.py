@@ -34,6 +34,9 @@ import synth  # noqa: E402
 METRIC = "Mrays/s (closest-hit + any-hit segments per second, spectra at <=1e-4 rel-L2 vs oracle)"
 UNIT = "Mrays/s"
 FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by-complex multiply-accumulate (4)
+# dram__bytes_read.sum + dram__bytes_write.sum per k_accum launch on this workload (profiles/k_accum_clutter.md);
+# set to None when the kernel changes until it is captured again
+ACCUM_DRAM_BYTES_PER_LAUNCH = 34.69e6
 
 
 def load_peaks():
@@ -301,7 +304,7 @@ def main():
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {peak_src})",
                 "work": f"{FLOPS_PER_TERM} FP32 flops per (path, mic, bin) term, {terms / max(acc_launches, 1):.3e} "
                         f"terms per launch", "ms_per_launch": acc_ms / max(acc_launches, 1),
-                "traffic": None}
+                "traffic": ACCUM_DRAM_BYTES_PER_LAUNCH}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
