@@ -34,8 +34,8 @@ import synth  # noqa: E402
 METRIC = "Mrays/s (closest-hit + any-hit segments per second, spectra at <=1e-4 rel-L2 vs oracle)"
 UNIT = "Mrays/s"
 FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by-complex multiply-accumulate (4)
-# dram__bytes_read.sum + dram__bytes_write.sum per k_accum launch on this workload (profiles/k_accum_clutter.md);
-# set to None when the kernel changes until it is captured again
+# dram__bytes_read.sum + dram__bytes_write.sum per k_accum launch on this workload, from an ncu capture of the
+# current kernel; set to None when the kernel changes until it is captured again
 ACCUM_DRAM_BYTES_PER_LAUNCH = 34.69e6
 
 

@@ -178,7 +178,7 @@ st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
  *   grad_k [n_mat][n_bands]: reflection band values (specular paths; assumes k > 0 at every bin),
  *   grad_mic [n_mics][3]:    microphone positions (specular, diffraction and direct paths),
  *   grad_emitter [3]:        emitter position through the diffraction and direct paths only.
- * Position gradients need an omni emitter (ST_ERR_ARG otherwise).  scene must be the one of the
+ * Needs omni receivers; position gradients also need an omni emitter (ST_ERR_ARG otherwise).  scene must be the one of the
  * last simulate, unchanged since (ST_ERR_STATE otherwise).  Deterministic: every sum runs in a fixed
  * order.  Stream-ordered; allocates reduction buffers on first use. */
 st_status st_backward(st_ctx* ctx, st_scene* scene, const void* grad_spectra, float* grad_k, float* grad_mic,

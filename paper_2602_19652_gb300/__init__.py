@@ -91,9 +91,14 @@ class Context:
                                           ST_MEM_DEVICE))
         self.N = int(d.shape[0])
 
-    def set_receivers(self, mics):
+    def set_receivers(self, mics, quats=None, tables=None):
+        """tables: [M][n_el][n_az][n_bands] receiver directivity on the materials' bands (None = omni)."""
         m = _dev(mics, torch.float32)
-        self._check(self.L.st_set_receivers(self.h, int(m.shape[0]), _ptr(m), None, None, 0, 0, 0, ST_MEM_DEVICE))
+        q = None if quats is None else _dev(quats, torch.float32)
+        t = None if tables is None else _dev(tables, torch.float32)
+        n_el, n_az, nb = (0, 0, 0) if t is None else tuple(int(x) for x in t.shape[1:4])
+        self._check(self.L.st_set_receivers(self.h, int(m.shape[0]), _ptr(m), None if q is None else _ptr(q),
+                                            None if t is None else _ptr(t), n_el, n_az, nb, ST_MEM_DEVICE))
         self.M = int(m.shape[0])
 
     # -------------------------------------------------------------- simulate
@@ -208,5 +213,5 @@ def from_workload(ctx: Context, wl, curv: CurvParams | None = None) -> Scene:
     sc.precompute(curv)
     ctx.set_frequencies(wl.n_bins, wl.f_lo, wl.f_hi)
     ctx.set_emitter(wl.emitter, wl.emitter_quat, wl.dirs, wl.emitter_table, wl.fov_half)
-    ctx.set_receivers(wl.mics)
+    ctx.set_receivers(wl.mics, wl.mic_quats, wl.mic_tables)
     return sc

@@ -32,7 +32,7 @@ using namespace acc;
 // ---------------------------------------------------------------- per-bin material tables
 __global__ void k_tables(int32_t F, int32_t n_mat, int32_t n_bands, const float* band_hz, const float* kb,
                          const float* beta, const float* diff, double f_lo, double df, double c, float* lk, float* g2,
-                         float* lid, float* qhi, float* qlo) {
+                         float* lid, float* qhi, float* qlo, float2* bw) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= F * n_mat) return;
     const int mat = idx / F, k = idx % F;
@@ -77,10 +77,11 @@ __global__ void k_tables(int32_t F, int32_t n_mat, int32_t n_bands, const float*
         float h = (float)q;
         qhi[k] = h;
         qlo[k] = (float)(q - (double)h);
+        bw[k] = make_float2((float)b0, (float)w);
     }
 }
 
-template <int KT, int KIND>
+template <int KT, int KIND, int DIR>
 __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) {
     static_assert((KT & (KT - 1)) == 0 && KT >= 2, "KT must be a power of two");
     extern __shared__ float4 smem4[];
@@ -106,6 +107,14 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
     for (int kk = 0; kk < KT; ++kk) Sr[kk] = Si[kk] = 0ull;
 
     const float invNS = 1.0f / (float)NS, invKB = 1.0f / (float)KB;
+    // per-bin band interpolation of the CTA's bins in table order (directional receivers)
+    float2* bwt = reinterpret_cast<float2*>(mt + (g.mat_cached ? 2 * a.n_mat_tab * KB : 0));
+    if (DIR && t0 < t1) {
+        for (int i = tid; i < KB; i += nthr) {
+            const int kk = __float2int_rz(((float)i + 0.5f) * invNS), s_ = i - kk * NS;
+            bwt[i] = a.bw[min(kb + s_ * KT + kk, a.F - 1)];
+        }
+    }
     if (t0 < t1) {
         if (g.mat_cached) {
             const int nm = a.n_mat_tab;
@@ -155,6 +164,18 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
                     E = pk2(ex2(arg.x), ex2(arg.y));
                 } else {
                     E = t.x;
+                }
+                if (DIR) {  // receiver directivity, linear between bands
+                    const float2 bwv = bwt[kk * NS + s];
+                    const int b0 = (int)bwv.x;
+                    const float* d1 = C.dband + ((size_t)p * MP + 2 * tp) * g.NB;
+                    const float* d2 = d1 + g.NB;
+                    float D1 = d1[b0], D2 = d2[b0];
+                    if (g.NB > 1) {
+                        D1 = fmaf(bwv.y, d1[b0 + 1] - D1, D1);
+                        D2 = fmaf(bwv.y, d2[b0 + 1] - D2, D2);
+                    }
+                    E = fmul2(E, pk2(D1, D2));
                 }
                 if ((kk & 1) == 0) {
                     Sr[kk] = ffma2(E, er, Sr[kk]);
@@ -226,7 +247,21 @@ __global__ void k_direct_accum(const DirectAccumArgs a, const float* qhi, const 
         const ff x = ff_mul(r, ff{qhi[k], qlo[k]});
         float sn, cs;
         sincospif(2.0f * ff_frac(x), &sn, &cs);
-        const float A = exp2f(L);
+        float A = exp2f(L);
+        if (a.mic_tab) {  // arrival from the emitter
+            AccumArgs aa{};
+            aa.mic_tab = a.mic_tab;
+            aa.mic_q = a.mic_q;
+            aa.n_el = a.n_el;
+            aa.n_az = a.n_az;
+            float band[64];
+            mic_bands(aa, m, a.s[0] - mx, a.s[1] - my, a.s[2] - mz, band, a.n_bands);
+            const float2 bwv = a.bw[k];
+            const int b0 = (int)bwv.x;
+            float D = band[b0];
+            if (a.n_bands > 1) D = fmaf(bwv.y, band[b0 + 1] - D, D);
+            A *= D;
+        }
         v = make_float2(A * cs, A * sn);
     }
     a.out[idx] = v;
@@ -338,27 +373,28 @@ void read_tile_env() {
     }
 }
 
-template <int KT, int KIND>
+template <int KT, int KIND, int DIR>
 cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
     read_tile_env();
-    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, g_tile_tp, g_tile_budget);
+    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, g_tile_tp, g_tile_budget, DIR ? a.n_bands_tab : 0);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_accum<KT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_accum<KT, KIND, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((unsigned)(g.n_mb * g.n_bb), (unsigned)a.n_chunks);
     note_launch();
-    k_accum<KT, KIND><<<grid, g.TP * g.NS, g.smem, s>>>(a, g);
+    k_accum<KT, KIND, DIR><<<grid, g.TP * g.NS, g.smem, s>>>(a, g);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat) {
+int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb) {
     read_tile_env();
-    const Geom g = make_geom(M, F, g_tile_kt, n_mat, g_tile_tp, g_tile_budget);
+    const Geom g = make_geom(M, F, dir_nb ? 16 : g_tile_kt, n_mat, g_tile_tp, g_tile_budget, dir_nb);
     const int ctas_per_chunk = g.n_mb * g.n_bb;
     const int threads = g.TP * g.NS;
     int resident = std::max(1, std::min(2048 / std::max(threads, 32), (int)((220 * 1024) / std::max<size_t>(g.smem, 1))));
@@ -377,6 +413,7 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
     if ((e = grow(T.lid, (size_t)n_mat * F * 4)) != cudaSuccess) return e;
     if ((e = grow(T.qhi, (size_t)F * 4)) != cudaSuccess) return e;
     if ((e = grow(T.qlo, (size_t)F * 4)) != cudaSuccess) return e;
+    if ((e = grow(T.bw, (size_t)F * 8)) != cudaSuccess) return e;
     DevBuf mt;
     const size_t mb = (size_t)(nb + 3 * n_mat * nb) * 4;
     if ((e = grow(mt, mb)) != cudaSuccess) return e;
@@ -396,7 +433,7 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
     k_tables<<<(F * n_mat + 127) / 128, 128, 0, s>>>(F, n_mat, nb, d, d + nb, d + nb + n_mat * nb,
                                                     d + nb + 2 * n_mat * nb, f_lo, df, c, ptr<float>(T.lk),
                                                     ptr<float>(T.g2), ptr<float>(T.lid), ptr<float>(T.qhi),
-                                                    ptr<float>(T.qlo));
+                                                    ptr<float>(T.qlo), ptr<float2>(T.bw));
     e = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(s);  // the staging buffer is freed below
     release(mt);
@@ -421,8 +458,9 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
 
 cudaError_t accumulate(const AccumArgs& a, cudaStream_t s) {
     read_tile_env();
-    if (g_tile_kt == 8) return a.kind == 0 ? launch_accum<8, 0>(a, s) : launch_accum<8, 1>(a, s);
-    return a.kind == 0 ? launch_accum<16, 0>(a, s) : launch_accum<16, 1>(a, s);
+    if (a.mic_tab) return a.kind == 0 ? launch_accum<16, 0, 1>(a, s) : launch_accum<16, 1, 1>(a, s);
+    if (g_tile_kt == 8) return a.kind == 0 ? launch_accum<8, 0, 0>(a, s) : launch_accum<8, 1, 0>(a, s);
+    return a.kind == 0 ? launch_accum<16, 0, 0>(a, s) : launch_accum<16, 1, 0>(a, s);
 }
 
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s) {

@@ -113,6 +113,7 @@ __device__ __forceinline__ void cmul2(u64& zr, u64& zi, u64 wr, u64 wi, u64 nwi)
 struct Geom {
     int TP, NS, MP, KB, PT;  // mic pairs per CTA (threads along x), subtiles, mics per CTA, bins per CTA, paths/tile
     int n_mb, n_bb;
+    int NB;                  // receiver directivity bands held per (path, mic); 0 = omni receivers
     int mat_cached;          // material tables held in shared memory (n_mat small enough)
     size_t mat_bytes;        // their size
     size_t buf_bytes;        // one pipeline buffer (tables + anchors of PT paths)
@@ -131,6 +132,7 @@ struct Buf {
     ulonglong2* za;
     u64* wst;
     u64* ngp;
+    float* dband;  // [PT][MP][NB] receiver directivity band values (directional receivers only)
 };
 
 template <int KT>
@@ -141,7 +143,48 @@ __device__ __forceinline__ Buf buf_at(float4* base, const Geom& g, int b) {
     B.za = reinterpret_cast<ulonglong2*>(B.tab + (size_t)g.PT * g.KB);
     B.wst = reinterpret_cast<u64*>(B.za + (size_t)g.PT * g.NS * g.TP);
     B.ngp = B.wst + (size_t)g.PT * g.TP * 4;
+    B.dband = reinterpret_cast<float*>(B.ngp + (size_t)g.PT * g.TP);
     return B;
+}
+
+// Receiver directivity: band values of microphone m's table for the arrival direction v (world frame,
+// from the microphone towards the point the sound comes from): rotate into the microphone frame by the
+// conjugate of its orientation, azimuth atan2(y, x) on the periodic grid -pi + 2 pi i / n_az, elevation
+// asin(z) on -pi/2 + pi j / (n_el - 1), bilinear in (az, el).
+__device__ __forceinline__ void mic_bands(const AccumArgs& a, int m, float vx, float vy, float vz, float* out, int NB) {
+    const float l = sqrtf(vx * vx + vy * vy + vz * vz);
+    float x = vx / l, y = vy / l, z = vz / l;
+    if (a.mic_q) {
+        const float* q = a.mic_q + 4 * m;
+        const float qw = q[0], qx = -q[1], qy = -q[2], qz = -q[3];
+        const float tx = 2.0f * (qy * z - qz * y), ty = 2.0f * (qz * x - qx * z), tz = 2.0f * (qx * y - qy * x);
+        const float rx = x + qw * tx + (qy * tz - qz * ty), ry = y + qw * ty + (qz * tx - qx * tz),
+                    rz = z + qw * tz + (qx * ty - qy * tx);
+        x = rx;
+        y = ry;
+        z = rz;
+    }
+    const float az = atan2f(y, x), el = asinf(fminf(1.0f, fmaxf(-1.0f, z)));
+    const float gx = (az + 3.14159265358979f) * (0.15915494309189535f * (float)a.n_az);
+    const float fx = floorf(gx);
+    const float wa = gx - fx;
+    int i0 = (int)fx % a.n_az;
+    if (i0 < 0) i0 += a.n_az;
+    const int i1 = (i0 + 1) % a.n_az;
+    const float gy = (el + 1.5707963267948966f) * (0.3183098861837907f * (float)(a.n_el - 1));
+    int j0 = (int)floorf(gy);
+    j0 = max(0, min(j0, a.n_el - 2));
+    const float wb = gy - (float)j0;
+    const float* T = a.mic_tab + (size_t)m * a.n_el * a.n_az * NB;
+    const float* t00 = T + ((size_t)j0 * a.n_az + i0) * NB;
+    const float* t01 = T + ((size_t)j0 * a.n_az + i1) * NB;
+    const float* t10 = T + ((size_t)(j0 + 1) * a.n_az + i0) * NB;
+    const float* t11 = T + ((size_t)(j0 + 1) * a.n_az + i1) * NB;
+    for (int b = 0; b < NB; ++b) {
+        const float lo = (1.0f - wa) * t00[b] + wa * t01[b];
+        const float hi = (1.0f - wa) * t10[b] + wa * t11[b];
+        out[b] = (1.0f - wb) * lo + wb * hi;
+    }
 }
 
 // path data of one tile into pd / pv
@@ -292,12 +335,14 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
             }
             for (int q = 0; q < 4; ++q) wf[2 * q + half] = 0.0f;
             nf[half] = 0.0f;
+            for (int b = 0; b < g.NB; ++b) B.dband[((size_t)p * MP + ml) * g.NB + b] = 0.0f;
             continue;
         }
         const float* d = pd + p * 12;
         const float mx = a.mics[3 * m], my = a.mics[3 * m + 1], mz = a.mics[3 * m + 2];
         const ff dist = dist_ff(mx, my, mz, d[0], d[1], d[2]);
         const ff r = ff_add(ff{d[6], d[7]}, dist);
+        if (g.NB > 0) mic_bands(a, m, d[0] - mx, d[1] - my, d[2] - mz, B.dband + ((size_t)p * MP + ml) * g.NB, g.NB);
         float gam2 = 0.0f;
         if (KIND == 0) {
             const float inv = 1.0f / dist.hi;
@@ -337,8 +382,9 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
 
 
 // tp_max: mic pairs per CTA at most; budget: shared-memory bytes per CTA
-inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t budget = 96 * 1024) {
+inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t budget = 96 * 1024, int dir_nb = 0) {
     Geom g;
+    g.NB = dir_nb;
     const int pairs = (M + 1) / 2;
     const int ns_need = (F + KT - 1) / KT;
     g.TP = std::max(1, std::min(pairs, tp_max));
@@ -348,11 +394,12 @@ inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t bu
     g.KB = g.NS * KT;
     g.n_mb = (M + g.MP - 1) / g.MP;
     g.n_bb = (F + g.KB - 1) / g.KB;
-    const size_t per_path = (size_t)g.KB * 16 + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40;
+    const size_t per_path = (size_t)g.KB * 16 + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40 + (size_t)g.MP * dir_nb * 4;
     const size_t mat_bytes = (size_t)2 * n_mat * g.KB * 4;
     g.mat_cached = mat_bytes <= 24 * 1024 ? 1 : 0;
-    g.mat_bytes = mat_bytes;
-    const size_t fixed = g.mat_cached ? mat_bytes : 0;
+    // fixed region: cached material tables, then (directional receivers) per-bin band interpolation
+    g.mat_bytes = (g.mat_cached ? mat_bytes : 0) + (dir_nb ? (size_t)g.KB * 8 : 0);
+    const size_t fixed = g.mat_bytes;
     const size_t avail = budget > fixed + 4096 ? budget - fixed : 4096;
     g.PT = (int)std::min<size_t>(8, std::max<size_t>(1, avail / (2 * per_path + 2 * 52)));
     g.buf_bytes = (per_path * g.PT + 255) & ~size_t(255);

@@ -66,7 +66,9 @@ struct st_ctx {
     // receivers
     bool has_rx = false;
     int32_t M = 0;
-    DevBuf mics;
+    DevBuf mics, mic_q, mic_tab;
+    bool has_mic_q = false;
+    int32_t mic_nb = 0, n_el = 0, n_az = 0;  // receiver directivity tables (mic_nb = 0: omni)
     // frequencies
     bool has_freq = false;
     int32_t F = 0;
@@ -198,6 +200,7 @@ st_status st_destroy(st_ctx* c) {
     if (!c) return ST_ERR_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    for (DevBuf* b : {&c->mic_q, &c->mic_tab, &c->tables.bw}) release(*b);
     for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
                       &c->st_d[2], &c->st_r, &c->st_prev, &c->q0, &c->q1, &c->counts, &c->queries, &c->flags, &c->R, &c->rec_tri,
                       &c->rec_p, &c->rec_d, &c->rec_r, &c->rec_los, &c->sflags, &c->sscan, &c->sidx, &c->scratch,
@@ -390,14 +393,25 @@ st_status st_set_receivers(st_ctx* c, int32_t n_mics, const float* pos, const fl
     if (!c) return ST_ERR_ARG;
     if (n_mics <= 0 || n_mics > kMaxMics || !pos || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
         return fail(c, ST_ERR_ARG, "set_receivers: 1..4096 microphones, non-null positions");
-    if (tables) return fail(c, ST_ERR_ARG, "set_receivers: receiver directivity tables are not supported yet");
-    (void)quats;
-    (void)n_el;
-    (void)n_az;
-    (void)n_bands;
+    if (tables && (n_el < 2 || n_az < 1 || n_bands < 1 || n_bands > 64))
+        return fail(c, ST_ERR_ARG, "set_receivers: tables need n_el >= 2, n_az >= 1, 1..64 bands");
     cudaSetDevice(c->device);
     CKC(c, grow(c->mics, (size_t)n_mics * 12), "set_receivers alloc");
     CKC(c, cudaMemcpyAsync(c->mics.p, pos, (size_t)n_mics * 12, kind_in(mem), c->stream), "set_receivers copy");
+    c->has_mic_q = quats != nullptr;
+    if (quats) {
+        CKC(c, grow(c->mic_q, (size_t)n_mics * 16), "set_receivers alloc");
+        CKC(c, cudaMemcpyAsync(c->mic_q.p, quats, (size_t)n_mics * 16, kind_in(mem), c->stream), "set_receivers copy");
+    }
+    c->mic_nb = 0;
+    if (tables) {
+        const size_t bytes = (size_t)n_mics * n_el * n_az * n_bands * 4;
+        CKC(c, grow(c->mic_tab, bytes), "set_receivers alloc");
+        CKC(c, cudaMemcpyAsync(c->mic_tab.p, tables, bytes, kind_in(mem), c->stream), "set_receivers copy");
+        c->mic_nb = n_bands;
+        c->n_el = n_el;
+        c->n_az = n_az;
+    }
     c->M = n_mics;
     c->has_rx = true;
     return ST_OK;
@@ -436,6 +450,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         return fail(c, ST_ERR_ARG, "simulate: 1..8 bounces, c > 0, t_min >= 0, los_eps >= 0");
     if (c->n_theta > 0 && c->etab.cap < (size_t)c->n_theta * c->F * 4)
         return fail(c, ST_ERR_ARG, "simulate: emitter table was set for a different bin count");
+    if (c->mic_nb > 0 && c->mic_nb != sc->S.n_bands)
+        return fail(c, ST_ERR_ARG, "simulate: receiver tables must use the materials' bands");
     cudaSetDevice(c->device);
     cudaStream_t s = c->stream;
     SceneDev& S = sc->S;
@@ -490,8 +506,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         CKC(c, grow(c->cand_p, (size_t)K * 12), "alloc");
         CKC(c, grow(c->keep, (size_t)K), "alloc");
     }
-    const int32_t chunks_spec = accum_chunks(NB, M, F, S.n_mat);
-    const int32_t chunks_diff = accum_chunks(K, M, F, S.n_mat);
+    const int32_t chunks_spec = accum_chunks(NB, M, F, S.n_mat, c->mic_nb);
+    const int32_t chunks_diff = accum_chunks(K, M, F, S.n_mat, c->mic_nb);
     const int32_t chunks = std::max(chunks_spec, chunks_diff);
     CKC(c, grow(c->partial, (size_t)chunks * M * F * 8), "alloc");
 
@@ -610,6 +626,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     aa.g2 = ptr<float>(T.g2);
     aa.lid = ptr<float>(T.lid);
     aa.n_mat_tab = T.n_mat;
+    aa.n_bands_tab = S.n_bands;
+    aa.bw = ptr<float2>(T.bw);
     aa.qhi = ptr<float>(T.qhi);
     aa.qlo = ptr<float>(T.qlo);
     {
@@ -621,6 +639,12 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     }
     aa.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
     aa.n_theta = c->n_theta;
+    aa.n_bands_tab = S.n_bands;
+    aa.mic_tab = c->mic_nb > 0 ? ptr<float>(c->mic_tab) : nullptr;
+    aa.mic_q = (c->mic_nb > 0 && c->has_mic_q) ? ptr<float>(c->mic_q) : nullptr;
+    aa.n_el = c->n_el;
+    aa.n_az = c->n_az;
+    aa.bw = ptr<float2>(T.bw);
     aa.reflection_mode = p.reflection_mode;
     aa.partial = ptr<float2>(c->partial);
 
@@ -737,6 +761,12 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         da.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
         da.n_theta = c->n_theta;
         memcpy(da.fwd, fwd, 12);
+        da.mic_tab = c->mic_nb > 0 ? ptr<float>(c->mic_tab) : nullptr;
+        da.mic_q = (c->mic_nb > 0 && c->has_mic_q) ? ptr<float>(c->mic_q) : nullptr;
+        da.n_el = c->n_el;
+        da.n_az = c->n_az;
+        da.n_bands = S.n_bands;
+        da.bw = ptr<float2>(T.bw);
         da.out = out + 2 * MF;
         CKC(c, accumulate_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), s), "direct");
     } else {
@@ -863,6 +893,7 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
         return fail(c, ST_ERR_STATE, "backward: needs the last simulate of this scene, unchanged since");
     if ((grad_mic || grad_emitter) && c->n_theta > 0)
         return fail(c, ST_ERR_ARG, "backward: position gradients need an omni emitter");
+    if (c->mic_nb > 0) return fail(c, ST_ERR_ARG, "backward: needs omni receivers");
     cudaSetDevice(c->device);
     cudaStream_t s = c->stream;
     const st_sim_params& p = c->last_params;
@@ -883,6 +914,8 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
     aa.g2 = ptr<float>(T.g2);
     aa.lid = ptr<float>(T.lid);
     aa.n_mat_tab = T.n_mat;
+    aa.n_bands_tab = S.n_bands;
+    aa.bw = ptr<float2>(T.bw);
     aa.qhi = ptr<float>(T.qhi);
     aa.qlo = ptr<float>(T.qlo);
     {

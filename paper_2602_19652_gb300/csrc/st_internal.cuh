@@ -207,6 +207,7 @@ struct AccumTables {
     DevBuf g2;     // [n_mat][F] lobe exponent 1/(2 beta^2) * log2(e)
     DevBuf lid;    // [n_mat][F] log2 I_d(mat, f)
     DevBuf qhi, qlo;  // [F] f_k / c as float-float
+    DevBuf bw;        // [F] float2 (lower band index, upper band weight)
     double f_lo = 0, df = 0, c = 343, a0 = 0, a1 = 0;
 };
 
@@ -224,11 +225,16 @@ struct AccumArgs {
     int32_t M, F;
     const float* lk; const float* g2; const float* lid;
     int32_t n_mat_tab;      // materials in the per-bin tables
+    int32_t n_bands_tab;    // bands of the material (and receiver directivity) tables
     const float* qhi; const float* qlo;
     float dq_hi, dq_lo;     // (f_{k+1} - f_k) / c as float-float
     float atm2_0, atm2_step;  // log2 amplitude decay per metre at bin 0 and per bin step
     const float* etab;      // emitter table [n_theta][F] or null
     int32_t n_theta;
+    const float* mic_tab;   // receiver tables [M][n_el][n_az][n_bands] or null (omni)
+    const float* mic_q;     // receiver orientations [M][4] or null (identity)
+    int32_t n_el, n_az;
+    const float2* bw;       // [F] band interpolation per bin: (index of the lower band, weight of the upper)
     int32_t reflection_mode;
     float2* partial;        // [n_chunks][M][F]
     int32_t n_chunks;
@@ -237,7 +243,7 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
                                double a0, double a1, cudaStream_t s);
 cudaError_t accumulate(const AccumArgs& a, cudaStream_t s);
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s);
-int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat);
+int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb);
 
 struct GatherArgs {
     // specular
@@ -280,6 +286,7 @@ struct DirectAccumArgs {
     double f_lo, df, c, a0, a1;
     float gain;
     const float* etab; int32_t n_theta; float fwd[3];
+    const float* mic_tab; const float* mic_q; int32_t n_el, n_az, n_bands; const float2* bw;
     float2* out;           // [M][F] (component 2 of the spectra)
 };
 cudaError_t accumulate_direct(const DirectAccumArgs& a, const float* qhi, const float* qlo, cudaStream_t s);

@@ -132,3 +132,19 @@ def test_bvh_small_triangle_counts(st, T):
     o = oracle.simulate(wl, use_bvh=False)
     compare_paths(ctx.paths(wl.bounces), o["rec"])
     assert rel_l2(S[0], o["spectra"][0]) <= TOL
+
+
+def test_vegetation_directivity_parity(st):
+    """Leaf-disc vegetation with a piston emitter table, two ears with directivity tables (bilinear in
+    azimuth/elevation, linear between bands) and the field-of-view filter (half-angle pi/2)."""
+    import oracle
+    wl = synth.vegetation(seed=303, target_tris=40_000, n_rays=30_000, bounces=4, n_bins=96, leaves_per_mesh=64)
+    ctx, sc, S, stats = gpu_run(st, wl, curv=st.curv_params(sample_budget=200_000))
+    o = oracle.simulate(wl, curv=dict(budget=200_000))
+    compare_paths(ctx.paths(wl.bounces), o["rec"])
+    ct, cp, keep = ctx.diffraction()
+    assert np.array_equal(ct, o["cand_tri"]) and np.array_equal(cp, o["cand_p"])
+    assert np.array_equal(keep, o["cand_keep"])
+    assert 0 < keep.sum() < len(keep)
+    for c in range(3):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
