@@ -113,6 +113,8 @@ const char* st_last_error(const st_ctx* ctx);
 /* Create a context on `device` issuing work on `cuda_stream` (a cudaStream_t; NULL = legacy
  * default stream).  The library allocates its working memory lazily and owns it until destroy. */
 st_status st_create(st_ctx** out, int32_t device, void* cuda_stream);
+/* Frees the context, its working memory and every scene still loaded into it (their handles become
+ * invalid: do not pass them to st_scene_destroy afterwards). */
 st_status st_destroy(st_ctx* ctx);
 st_status st_set_stream(st_ctx* ctx, void* cuda_stream);
 
@@ -183,6 +185,45 @@ st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
  * order.  Stream-ordered; allocates reduction buffers on first use. */
 st_status st_backward(st_ctx* ctx, st_scene* scene, const void* grad_spectra, float* grad_k, float* grad_mic,
                       float* grad_emitter);
+
+/* Batched form: many poses (over one or more precomputed scenes) simulated together.  Every stage
+ * runs over all jobs in one launch (one per bounce level for tracing), and the per-job accumulations
+ * run on parallel branches of a CUDA graph.  The first call with a given batch structure (jobs'
+ * scenes, sizes, pointers, params, tune) runs eagerly and records the graph; later calls with the
+ * same structure replay it, reading the poses (emitter, emitter_quat, dirs, mics) from the job
+ * pointers at run time, so callers update them in place between calls.  Omni emitter and receivers;
+ * params NULL = defaults; tune NULL = defaults.  Writes every job's spectra_out
+ * (complex64 [3][n_mics][n_bins]).  Stream-ordered on the context's stream. */
+typedef struct st_job {
+    st_scene* scene;            /* precomputed scene */
+    const float* emitter;       /* device [3] */
+    const float* emitter_quat;  /* device [4] */
+    const float* dirs;          /* device [n_rays][3] local unit directions */
+    int64_t n_rays;
+    const float* mics;          /* device [n_mics][3] */
+    int32_t n_mics;
+    int32_t n_bins;
+    double f_lo, f_hi;          /* uniform frequency grid */
+    int32_t max_bounces;        /* 1..8 */
+    uint32_t pose_index;        /* Philox counter word of the diffraction samples */
+    float fov_half_rad;         /* diffraction field of view half-angle (>= pi: off) */
+    void* spectra_out;          /* device complex64 [3][n_mics][n_bins] */
+} st_job;
+
+/* Launch shapes picked by st_autotune (0 = default). */
+typedef struct st_tune {
+    int32_t rays_per_block;     /* tracing block size: 64, 128 or 256 */
+    int32_t mic_pairs_per_cta;  /* accumulator: microphone pairs per CTA, 1..16 */
+    int32_t smem_kb;            /* accumulator: shared-memory budget per CTA, 32..160 KB */
+    int32_t reserved;
+} st_tune;
+
+st_status st_simulate_batch(st_ctx* ctx, int32_t n_jobs, const st_job* jobs, const st_sim_params* params,
+                            const st_tune* tune);
+/* Times candidate launch shapes on one sample job through the single-pose path and writes the
+ * fastest to *out (also kept as the context's default for st_simulate).  Replaces the context's
+ * emitter, receivers and frequency grid with the sample job's (omni).  Synchronises. */
+st_status st_autotune(st_ctx* ctx, const st_job* sample, const st_sim_params* params, st_tune* out);
 
 /* Allocation-free specular accumulation.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory where they need spectra -- code running inside another

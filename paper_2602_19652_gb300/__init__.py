@@ -15,10 +15,10 @@ import torch
 from . import _lib
 from .autograd import SpectraFn  # noqa: E402
 from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
-                   SimParams, SonotraceError, Stats, check, load)
+                   Job, SimParams, SonotraceError, Stats, Tune, check, load)
 
-__all__ = ["Context", "Scene", "SpectraFn", "CurvParams", "SimParams", "Stats", "SonotraceError", "sim_params", "curv_params",
-           "ST_COMP_SPECULAR", "ST_COMP_DIFFRACTION", "ST_COMP_DIRECT"]
+__all__ = ["Context", "Scene", "BatchJob", "SpectraFn", "CurvParams", "SimParams", "Stats", "Tune", "SonotraceError",
+           "sim_params", "curv_params", "ST_COMP_SPECULAR", "ST_COMP_DIFFRACTION", "ST_COMP_DIRECT"]
 
 
 def curv_params(**kw) -> CurvParams:
@@ -61,6 +61,7 @@ class Context:
         self.N = 0
 
     def close(self):
+        """Destroys the context and every scene still loaded into it."""
         if getattr(self, "h", None):
             self.L.st_destroy(self.h)
             self.h = None
@@ -157,6 +158,54 @@ class Context:
         self._check(self.L.st_get_direct_visibility(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST))
         return v
 
+    # -------------------------------------------------------------- batched form
+    def simulate_batch(self, jobs: list["BatchJob"], params: SimParams | None = None, tune: Tune | None = None):
+        """All jobs' spectra (each job's .out).  Same job list and sizes on a later call replays the
+        recorded graph; update the jobs' pose tensors in place (BatchJob.set_pose) between calls."""
+        key = tuple(id(j) for j in jobs)
+        if getattr(self, "_batch_key", None) != key:
+            self._batch_arr = (Job * len(jobs))(*[j.job for j in jobs])
+            self._batch_key = key
+            self._batch_jobs = list(jobs)
+        self._check(self.L.st_simulate_batch(self.h, len(jobs), self._batch_arr,
+                                             None if params is None else C.byref(params),
+                                             None if tune is None else C.byref(tune)))
+        return [j.out for j in jobs]
+
+    def autotune(self, job: "BatchJob", params: SimParams | None = None) -> Tune:
+        t = Tune()
+        self._check(self.L.st_autotune(self.h, C.byref(job.job), None if params is None else C.byref(params),
+                                       C.byref(t)))
+        self.M, self.F, self.N = job.M, job.F, job.N
+        return t
+
+
+class BatchJob:
+    """One pose of a batch: device tensors for the pose (updated in place between calls) and the
+    job's output, complex64 [3][M][F]."""
+
+    def __init__(self, scene: "Scene", emitter, emitter_quat, dirs, mics, n_bins: int, f_lo: float, f_hi: float,
+                 max_bounces: int, pose_index: int = 0, fov_half: float = math.pi, device: int = 0):
+        dev = f"cuda:{device}"
+        self.scene = scene
+        self.emitter = torch.as_tensor(np.asarray(emitter, np.float32), device=dev).contiguous()
+        self.emitter_quat = torch.as_tensor(np.asarray(emitter_quat, np.float32), device=dev).contiguous()
+        self.dirs = torch.as_tensor(np.asarray(dirs, np.float32), device=dev).contiguous()
+        self.mics = torch.as_tensor(np.asarray(mics, np.float32), device=dev).contiguous()
+        self.N, self.M, self.F = int(self.dirs.shape[0]), int(self.mics.shape[0]), int(n_bins)
+        self.out = torch.empty((3, self.M, self.F), dtype=torch.complex64, device=dev)
+        vp = lambda t: C.c_void_p(t.data_ptr())
+        self.job = Job(scene=scene.h, emitter=vp(self.emitter), emitter_quat=vp(self.emitter_quat), dirs=vp(self.dirs),
+                       n_rays=self.N, mics=vp(self.mics), n_mics=self.M, n_bins=self.F, f_lo=float(f_lo),
+                       f_hi=float(f_hi), max_bounces=int(max_bounces), pose_index=int(pose_index),
+                       fov_half_rad=float(np.float32(fov_half)), spectra_out=vp(self.out))
+
+    def set_pose(self, emitter=None, emitter_quat=None, mics=None):
+        """Copy a new pose into the job's tensors (same shapes), stream-ordered on torch's current stream."""
+        for dst, src in ((self.emitter, emitter), (self.emitter_quat, emitter_quat), (self.mics, mics)):
+            if src is not None:
+                dst.copy_(torch.as_tensor(np.asarray(src, np.float32)), non_blocking=False)
+
 
 class Scene:
     """A triangle scene owned by a Context: load, set materials, precompute (BVH, curvature, CDFs)."""
@@ -195,9 +244,10 @@ class Scene:
         return G, Cm, ns
 
     def close(self):
-        if getattr(self, "h", None):
+        # a destroyed context has already freed its scenes
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
             self.ctx.L.st_scene_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

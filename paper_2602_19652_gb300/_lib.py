@@ -41,11 +41,11 @@ class Stats(C.Structure):
 class Job(C.Structure):
     _fields_ = [("scene", P), ("emitter", P), ("emitter_quat", P), ("dirs", P), ("n_rays", I64), ("mics", P),
                 ("n_mics", I32), ("n_bins", I32), ("f_lo", F64), ("f_hi", F64), ("max_bounces", I32),
-                ("pose_index", U32), ("spectra_out", P)]
+                ("pose_index", U32), ("fov_half_rad", F32), ("spectra_out", P)]
 
 
 class Tune(C.Structure):
-    _fields_ = [("rays_per_block", I32), ("bins_per_thread", I32), ("mics_per_thread", I32), ("contrib_tile", I32)]
+    _fields_ = [("rays_per_block", I32), ("mic_pairs_per_cta", I32), ("smem_kb", I32), ("reserved", I32)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/sonotrace.h
@@ -71,6 +71,8 @@ SIGNATURES = {
     "st_get_diffraction": (I32, [P, P, P, P, P, I64, I32]),
     "st_get_direct_visibility": (I32, [P, P, I32]),
     "st_backward": (I32, [P, P, P, P, P, P]),
+    "st_simulate_batch": (I32, [P, I32, P, P, P]),
+    "st_autotune": (I32, [P, P, P, P]),
     "st_accumulate_specular_noalloc": (I32, [P, P, P, P, P, I64, I32, P, P, I32, I32, F64, F64, I32, I32, P, P, P,
                                              P, P, P]),
 }

@@ -25,6 +25,7 @@ UNITS = {
     "st_sort.cu": [],
     "st_scene.cu": ["-fmad=false"],
     "st_trace.cu": ["-fmad=false"],
+    "st_batch.cu": ["-fmad=false"],
     "st_accum.cu": [],
     "st_adjoint.cu": [],
     "st_noalloc.cu": [],

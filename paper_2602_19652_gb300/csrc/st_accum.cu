@@ -267,6 +267,30 @@ __global__ void k_direct_accum(const DirectAccumArgs a, const float* qhi, const 
     a.out[idx] = v;
 }
 
+// direct path of every job of a batch: one thread per (job, mic, bin); omni emitter and receivers
+__global__ void k_direct_accum_batch(const BatchArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.MF_total; g += stride) {
+        const JobDev& b = a.jobs[find_job(a.mf_offs, a.n_jobs, g)];
+        const int64_t local = g - b.mf_off;
+        const int m = (int)(local / b.F), k = (int)(local % b.F);
+        float2 v = make_float2(0.0f, 0.0f);
+        if (a.dvis[b.mic_off + m]) {
+            const float mx = b.mics[3 * m], my = b.mics[3 * m + 1], mz = b.mics[3 * m + 2];
+            const ff r = dist_ff(mx, my, mz, b.s[0], b.s[1], b.s[2]);
+            const double f = b.F == 1 ? b.f_lo : b.f_lo + (double)k * b.df;
+            const float alpha = (float)(a.a0 + a.a1 * (f / 1000.0));
+            const float L = log2f(a.direct_gain) - 2.0f * log2_ff(r) - alpha * r.hi * (3.3219280948873623f / 20.0f);
+            const ff x = ff_mul(r, ff{b.qhi[k], b.qlo[k]});
+            float sn, cs;
+            sincospif(2.0f * ff_frac(x), &sn, &cs);
+            const float A = exp2f(L);
+            v = make_float2(A * cs, A * sn);
+        }
+        b.out[(size_t)2 * b.M * b.F + local] = v;
+    }
+}
+
 // ---------------------------------------------------------------- path gathering
 __global__ void k_flags_records(const int32_t* rec_tri, const uint8_t* rec_los, int64_t n, uint32_t* flags) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -376,7 +400,9 @@ void read_tile_env() {
 template <int KT, int KIND, int DIR>
 cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
     read_tile_env();
-    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, g_tile_tp, g_tile_budget, DIR ? a.n_bands_tab : 0);
+    const int tp = a.tile_tp > 0 ? a.tile_tp : g_tile_tp;
+    const size_t budget = a.tile_kb > 0 ? (size_t)a.tile_kb * 1024 : g_tile_budget;
+    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, tp, budget, DIR ? a.n_bands_tab : 0);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
@@ -390,11 +416,71 @@ cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// path list entries of every job (same layout as the single-pose gather; omni emitter)
+__global__ void k_gather_spec_batch(const BatchArgs a, const uint32_t* idx, const uint32_t* count, float* px, float* py,
+                                    float* pz, float* dx, float* dy, float* dz, float* rhi, float* rlo, uint32_t* chl,
+                                    uint32_t* chh, uint32_t* meta, float* dep) {
+    const int64_t n = *count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+        const int64_t id = idx[c];
+        const int job = find_job(a.rec_offs, a.n_jobs, id);
+        const JobDev& b = a.jobs[job];
+        const int64_t local = id - b.rec_off;
+        const int64_t ray = local / b.B;
+        const int j = (int)(local % b.B);
+        px[c] = a.rec_p[3 * id];
+        py[c] = a.rec_p[3 * id + 1];
+        pz[c] = a.rec_p[3 * id + 2];
+        dx[c] = a.rec_d[3 * id];
+        dy[c] = a.rec_d[3 * id + 1];
+        dz[c] = a.rec_d[3 * id + 2];
+        const double r = a.rec_r[id];
+        const float h = (float)r;
+        rhi[c] = h;
+        rlo[c] = (float)(r - (double)h);
+        uint32_t lo = 0, hi = 0;
+        int matj = 0;
+        for (int q = 0; q <= j; ++q) {
+            const uint32_t mq = (uint32_t)b.tri_mat[a.rec_tri[b.rec_off + ray * b.B + q]] & 255u;
+            if (q < 4) lo |= mq << (8 * q); else hi |= mq << (8 * (q - 4));
+            matj = (int)mq;
+        }
+        chl[c] = lo;
+        chh[c] = hi;
+        meta[c] = (uint32_t)(j + 1) | ((uint32_t)matj << 8);
+        dep[c] = -1.0f;
+    }
+}
+
+__global__ void k_gather_diff_batch(const BatchArgs a, const uint32_t* idx, const uint32_t* count, float* px, float* py,
+                                    float* pz, float* rhi, float* rlo, uint32_t* meta, float* dep) {
+    const int64_t n = *count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+        const int64_t i = idx[c];
+        const int job = find_job(a.samp_offs, a.n_jobs, i);
+        const JobDev& b = a.jobs[job];
+        const float ox = a.cand_p[3 * i], oy = a.cand_p[3 * i + 1], oz = a.cand_p[3 * i + 2];
+        px[c] = ox;
+        py[c] = oy;
+        pz[c] = oz;
+        const ff r = dist_ff(ox, oy, oz, b.s[0], b.s[1], b.s[2]);
+        rhi[c] = r.hi;
+        rlo[c] = r.lo;
+        meta[c] = ((uint32_t)b.tri_mat[a.cand_tri[i]] & 255u) << 8;
+        dep[c] = -1.0f;
+    }
+}
+
 }  // namespace
 
-int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb) {
+int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb, int32_t tile_tp,
+                     int32_t tile_kb) {
     read_tile_env();
-    const Geom g = make_geom(M, F, dir_nb ? 16 : g_tile_kt, n_mat, g_tile_tp, g_tile_budget, dir_nb);
+    const int tp = tile_tp > 0 ? tile_tp : g_tile_tp;
+    const size_t budget = tile_kb > 0 ? (size_t)tile_kb * 1024 : g_tile_budget;
+    const Geom g = make_geom(M, F, dir_nb ? 16 : g_tile_kt, n_mat, tp, budget, dir_nb);
     const int ctas_per_chunk = g.n_mb * g.n_bb;
     const int threads = g.TP * g.NS;
     int resident = std::max(1, std::min(2048 / std::max(threads, 32), (int)((220 * 1024) / std::max<size_t>(g.smem, 1))));
@@ -477,6 +563,13 @@ cudaError_t accumulate_direct(const DirectAccumArgs& a, const float* qhi, const 
     return cudaGetLastError();
 }
 
+cudaError_t batch_direct_accum(const BatchArgs& a, cudaStream_t s) {
+    if (a.MF_total <= 0) return cudaSuccess;
+    note_launch();
+    k_direct_accum_batch<<<grid_for(a.MF_total, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t flags_visible_records(const int32_t* rec_tri, const uint8_t* rec_los, int64_t n, uint32_t* flags,
                                   cudaStream_t s) {
     note_launch();
@@ -513,6 +606,27 @@ cudaError_t gather_diffraction(const GatherArgs& g, cudaStream_t s) {
     k_gather_diff<<<grid_for(g.K, 256), 256, 0, s>>>(g, ptr<float>(P.px), ptr<float>(P.py), ptr<float>(P.pz),
                                                      ptr<float>(P.rhi), ptr<float>(P.rlo), ptr<uint32_t>(P.meta),
                                                      ptr<float>(P.dep));
+    return cudaGetLastError();
+}
+
+cudaError_t batch_gather_spec(const BatchArgs& a, const uint32_t* idx, const uint32_t* count, PathList& P,
+                              cudaStream_t s) {
+    note_launch();
+    k_gather_spec_batch<<<grid_for(a.R_total, 256), 256, 0, s>>>(
+        a, idx, count, ptr<float>(P.px), ptr<float>(P.py), ptr<float>(P.pz), ptr<float>(P.dx), ptr<float>(P.dy),
+        ptr<float>(P.dz), ptr<float>(P.rhi), ptr<float>(P.rlo), ptr<uint32_t>(P.chain_lo), ptr<uint32_t>(P.chain_hi),
+        ptr<uint32_t>(P.meta), ptr<float>(P.dep));
+    return cudaGetLastError();
+}
+
+cudaError_t batch_gather_diff(const BatchArgs& a, const uint32_t* idx, const uint32_t* count, PathList& P,
+                              cudaStream_t s) {
+    if (a.K_total <= 0) return cudaSuccess;
+    note_launch();
+    k_gather_diff_batch<<<grid_for(a.K_total, 256), 256, 0, s>>>(a, idx, count, ptr<float>(P.px), ptr<float>(P.py),
+                                                                  ptr<float>(P.pz), ptr<float>(P.rhi),
+                                                                  ptr<float>(P.rlo), ptr<uint32_t>(P.meta),
+                                                                  ptr<float>(P.dep));
     return cudaGetLastError();
 }
 

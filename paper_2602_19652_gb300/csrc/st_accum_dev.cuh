@@ -190,9 +190,11 @@ __device__ __forceinline__ void mic_bands(const AccumArgs& a, int m, float vx, f
 // path data of one tile into pd / pv
 template <int KIND>
 __device__ __forceinline__ void load_paths(const AccumArgs& a, int PT, int64_t pbase, int64_t count, float* pd, int* pv) {
+    const int64_t base = a.d_base ? (int64_t)*a.d_base : 0;  // first path of this launch
     for (int p = threadIdx.x; p < PT; p += blockDim.x) {
-        const int64_t pi = pbase + p;
-        const bool ok = pi < count;
+        const int64_t rel = pbase + p;
+        const bool ok = rel < count;
+        const int64_t pi = base + rel;
         pv[p] = ok;
         float* d = pd + p * 12;
         if (ok) {

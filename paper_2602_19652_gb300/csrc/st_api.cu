@@ -52,6 +52,9 @@ void release(DevBuf& b) {
 
 }  // namespace st
 
+struct BatchState;
+struct st_scene;
+
 struct st_ctx {
     int32_t device = 0;
     cudaStream_t stream = nullptr;
@@ -95,7 +98,33 @@ struct st_ctx {
     int32_t last_chunks_spec = 0, last_chunks_diff = 0;
     float last_fwd[3] = {1, 0, 0};
     bool count_visits = false;  // ST_COUNT_VISITS=1 in the environment: node/triangle visit counters
+    st_tune tune{0, 0, 0, 0};   // launch shapes (st_autotune); 0 = default
+    BatchState* batch = nullptr;
+    std::vector<st_scene*> scenes;  // scenes loaded into this context (freed by st_destroy)
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+// Buffers and the recorded graph of the last batch structure.
+struct BatchState {
+    uint64_t key = 0;
+    bool valid = false;
+    int32_t n_jobs = 0, max_b = 0, n_branches = 0;
+    std::vector<AccumTables> tables;
+    std::vector<JobDev> jobs;
+    std::vector<int32_t> chunks_spec, chunks_diff;
+    DevBuf jobs_dev, offs, derived, perm, ord_keys, ord_scr;
+    DevBuf st_o[3], st_d[3], st_r, st_prev, q0, q1, counts, queries, flags;
+    DevBuf rec_tri, rec_p, rec_d, rec_r, rec_los, cand_tri, cand_p, keep, dvis, ranges;
+    DevBuf sflags, sscan, sidx, scratch;
+    std::vector<DevBuf> partial;  // one per branch
+    PathList spec, diff;
+    int64_t N_total = 0, R_total = 0, K_total = 0, M_total = 0, MF_total = 0;
+    cudaStream_t main = nullptr;     // the batch runs here (capturable even when the context's stream is
+                                     // the legacy default stream), ordered after/before the context's stream
+    std::vector<cudaStream_t> streams;  // accumulation branches
+    std::vector<cudaEvent_t> events;    // [0] fork, [1..n_branches] joins, then context -> main, main -> context
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 struct st_scene {
@@ -104,6 +133,22 @@ struct st_scene {
     bool has_materials = false;
     uint64_t version = 0;
 };
+
+// Entry of every call on a context: select its device and drop a stale, non-sticky error left by
+// earlier unrelated runtime calls, so that the launch checks below see only this call's errors.
+static void enter(const st_ctx* c) {
+    cudaSetDevice(c->device);
+    (void)cudaGetLastError();
+}
+
+static void scene_free(st_scene* sc) {
+    SceneDev& S = sc->S;
+    for (DevBuf* b : {&S.verts, &S.tris, &S.tri_mat, &S.tri_obj, &S.nrm, &S.nodes, &S.tri_v, &S.G, &S.C, &S.mesh_tris,
+                      &S.mesh_off, &S.cdf, &S.n_samples, &S.sample_off})
+        st::release(*b);
+    delete sc;
+}
+
 
 namespace {
 
@@ -127,6 +172,9 @@ cudaMemcpyKind kind_in(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDe
 cudaMemcpyKind kind_out(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
 uint64_t g_scene_version = 1;
+
+void batch_release(BatchState& B);
+void batch_release_public(BatchState& B) { batch_release(B); }
 
 }  // namespace
 
@@ -198,7 +246,7 @@ st_status st_create(st_ctx** out, int32_t device, void* cuda_stream) {
 
 st_status st_destroy(st_ctx* c) {
     if (!c) return ST_ERR_ARG;
-    cudaSetDevice(c->device);
+    enter(c);
     cudaStreamSynchronize(c->stream);
     for (DevBuf* b : {&c->mic_q, &c->mic_tab, &c->tables.bw}) release(*b);
     for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
@@ -214,6 +262,11 @@ st_status st_destroy(st_ctx* c) {
     for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband}) release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->batch) {
+        batch_release_public(*c->batch);
+        delete c->batch;
+    }
+    for (st_scene* sc : c->scenes) scene_free(sc);
     delete c;
     return ST_OK;
 }
@@ -232,7 +285,7 @@ st_status st_scene_load(st_ctx* c, const float* verts, int64_t n_verts, const in
     if (!verts || !tris || !tri_material || !tri_object || n_verts <= 0 || n_tris <= 0 ||
         n_tris >= (1ll << 28) || n_verts >= (1ll << 31) || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
         return fail(c, ST_ERR_ARG, "scene_load: null pointer or size out of range (1..2^28 triangles)");
-    cudaSetDevice(c->device);
+    enter(c);
     st_scene* sc = new st_scene();
     sc->ctx = c;
     SceneDev& S = sc->S;
@@ -241,7 +294,7 @@ st_status st_scene_load(st_ctx* c, const float* verts, int64_t n_verts, const in
     cudaError_t e;
     if ((e = grow(S.verts, (size_t)n_verts * 12)) != cudaSuccess || (e = grow(S.tris, (size_t)n_tris * 12)) != cudaSuccess ||
         (e = grow(S.tri_mat, (size_t)n_tris * 4)) != cudaSuccess || (e = grow(S.tri_obj, (size_t)n_tris * 4)) != cudaSuccess) {
-        delete sc;
+        scene_free(sc);
         return cuda_fail(c, e, "scene_load alloc");
     }
     cudaMemcpyAsync(S.verts.p, verts, (size_t)n_verts * 12, kind_in(mem), c->stream);
@@ -253,23 +306,24 @@ st_status st_scene_load(st_ctx* c, const float* verts, int64_t n_verts, const in
     e = cudaMemcpyAsync(obj.data(), S.tri_obj.p, (size_t)n_tris * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        delete sc;
+        scene_free(sc);
         return cuda_fail(c, e, "scene_load copy");
     }
     int32_t mx = -1;
     for (int32_t o : obj) {
         if (o < 0) {
-            delete sc;
+            scene_free(sc);
             return fail(c, ST_ERR_MESH, "scene_load: negative object id");
         }
         mx = std::max(mx, o);
     }
     if (mx >= (1 << 24)) {
-        delete sc;
+        scene_free(sc);
         return fail(c, ST_ERR_MESH, "scene_load: object ids must be < 2^24");
     }
     S.n_obj = mx + 1;
     sc->version = g_scene_version++;
+    c->scenes.push_back(sc);
     *out = sc;
     return ST_OK;
 }
@@ -306,7 +360,7 @@ st_status st_scene_precompute(st_scene* sc, const st_curv_params* params) {
     if (params) p = *params;
     if (!(p.area_ref > 0.0f) || p.samples_per_vertex < 0 || !(p.dither >= 0.0))
         return fail(c, ST_ERR_ARG, "scene_precompute: area_ref > 0, samples_per_vertex >= 0, dither >= 0");
-    cudaSetDevice(c->device);
+    enter(c);
     CurvParamsDev cp{p.eta, p.area_ref, p.hc_frac, p.dither, p.samples_per_vertex, p.sample_budget, p.seed};
     bool mesh_err = false;
     std::string msg;
@@ -321,7 +375,7 @@ st_status st_scene_get_curvature(st_scene* sc, float* G, float* C, int64_t* n_sa
     if (!sc) return ST_ERR_ARG;
     st_ctx* c = sc->ctx;
     if (!sc->S.built) return fail(c, ST_ERR_STATE, "scene_get_curvature: precompute first");
-    cudaSetDevice(c->device);
+    enter(c);
     if (G) CKC(c, cudaMemcpyAsync(G, sc->S.G.p, (size_t)sc->S.n_verts * 4, kind_out(mem), c->stream), "get G");
     if (C) CKC(c, cudaMemcpyAsync(C, sc->S.C.p, (size_t)sc->S.n_tris * 4, kind_out(mem), c->stream), "get C");
     if (n_samples)
@@ -333,14 +387,13 @@ st_status st_scene_get_curvature(st_scene* sc, float* G, float* C, int64_t* n_sa
 
 st_status st_scene_destroy(st_scene* sc) {
     if (!sc) return ST_ERR_ARG;
-    cudaSetDevice(sc->ctx->device);
-    cudaStreamSynchronize(sc->ctx->stream);
-    SceneDev& S = sc->S;
-    for (DevBuf* b : {&S.verts, &S.tris, &S.tri_mat, &S.tri_obj, &S.nrm, &S.nodes, &S.tri_v, &S.G, &S.C, &S.mesh_tris,
-                      &S.mesh_off, &S.cdf, &S.n_samples, &S.sample_off})
-        release(*b);
-    if (sc->ctx->tables_scene == sc) sc->ctx->tables_scene = nullptr;
-    delete sc;
+    st_ctx* c = sc->ctx;
+    enter(c);
+    cudaStreamSynchronize(c->stream);
+    if (c->batch) c->batch->valid = false;  // a recorded batch may reference the scene
+    if (c->tables_scene == sc) c->tables_scene = nullptr;
+    c->scenes.erase(std::remove(c->scenes.begin(), c->scenes.end(), sc), c->scenes.end());
+    scene_free(sc);
     return ST_OK;
 }
 
@@ -351,7 +404,7 @@ st_status st_set_emitter(st_ctx* c, const float pos[3], const float quat[4], int
     if (!pos || !quat || n_rays < 0 || n_rays > (1ll << 31) - 1 || (n_rays > 0 && !dirs) ||
         (dir_table && n_theta < 2) || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
         return fail(c, ST_ERR_ARG, "set_emitter: bad argument");
-    cudaSetDevice(c->device);
+    enter(c);
     float hp[3], hq[4];
     if (mem == ST_MEM_DEVICE) {
         CKC(c, cudaMemcpyAsync(hp, pos, 12, cudaMemcpyDeviceToHost, c->stream), "set_emitter pos");
@@ -395,7 +448,7 @@ st_status st_set_receivers(st_ctx* c, int32_t n_mics, const float* pos, const fl
         return fail(c, ST_ERR_ARG, "set_receivers: 1..4096 microphones, non-null positions");
     if (tables && (n_el < 2 || n_az < 1 || n_bands < 1 || n_bands > 64))
         return fail(c, ST_ERR_ARG, "set_receivers: tables need n_el >= 2, n_az >= 1, 1..64 bands");
-    cudaSetDevice(c->device);
+    enter(c);
     CKC(c, grow(c->mics, (size_t)n_mics * 12), "set_receivers alloc");
     CKC(c, cudaMemcpyAsync(c->mics.p, pos, (size_t)n_mics * 12, kind_in(mem), c->stream), "set_receivers copy");
     c->has_mic_q = quats != nullptr;
@@ -452,7 +505,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         return fail(c, ST_ERR_ARG, "simulate: emitter table was set for a different bin count");
     if (c->mic_nb > 0 && c->mic_nb != sc->S.n_bands)
         return fail(c, ST_ERR_ARG, "simulate: receiver tables must use the materials' bands");
-    cudaSetDevice(c->device);
+    enter(c);
     cudaStream_t s = c->stream;
     SceneDev& S = sc->S;
     const int64_t N = c->N;
@@ -506,8 +559,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         CKC(c, grow(c->cand_p, (size_t)K * 12), "alloc");
         CKC(c, grow(c->keep, (size_t)K), "alloc");
     }
-    const int32_t chunks_spec = accum_chunks(NB, M, F, S.n_mat, c->mic_nb);
-    const int32_t chunks_diff = accum_chunks(K, M, F, S.n_mat, c->mic_nb);
+    const int32_t chunks_spec = accum_chunks(NB, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb);
+    const int32_t chunks_diff = accum_chunks(K, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb);
     const int32_t chunks = std::max(chunks_spec, chunks_diff);
     CKC(c, grow(c->partial, (size_t)chunks * M * F * 8), "alloc");
 
@@ -578,7 +631,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         ta.rec_los = ptr<uint8_t>(c->rec_los);
         ta.flags = ptr<uint32_t>(c->flags);
         ta.queries = qctr;
-        CKC(c, trace_rays(ta, s, 128), "trace");
+        CKC(c, trace_rays(ta, s, c->tune.rays_per_block > 0 ? c->tune.rays_per_block : 128), "trace");
     }
     if (stats) CKC(c, cudaEventRecord(c->ev[1], s), "event");
 
@@ -647,6 +700,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     aa.bw = ptr<float2>(T.bw);
     aa.reflection_mode = p.reflection_mode;
     aa.partial = ptr<float2>(c->partial);
+    aa.tile_tp = c->tune.mic_pairs_per_cta;
+    aa.tile_kb = c->tune.smem_kb;
 
     GatherArgs ga{};
     ga.N = N;
@@ -837,7 +892,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
 
 st_status st_simulate_host(st_ctx* c, st_scene* sc, const st_sim_params* params, void* spectra_out, st_stats* stats) {
     if (!c || !spectra_out) return fail(c, ST_ERR_ARG, "simulate_host: null argument");
-    cudaSetDevice(c->device);
+    enter(c);
     const size_t bytes = (size_t)3 * c->M * c->F * 8;
     CKC(c, grow(c->host_out, bytes), "alloc");
     st_status r = st_simulate(c, sc, params, c->host_out.p, stats);
@@ -850,7 +905,7 @@ st_status st_simulate_host(st_ctx* c, st_scene* sc, const st_sim_params* params,
 st_status st_get_paths(st_ctx* c, int32_t* tri, float* point, float* dir, double* r, uint8_t* los, int32_t mem) {
     if (!c) return ST_ERR_ARG;
     if (!c->has_last) return fail(c, ST_ERR_STATE, "get_paths: no simulate yet");
-    cudaSetDevice(c->device);
+    enter(c);
     const size_t nb = (size_t)c->last_N * c->last_B;
     if (tri) CKC(c, cudaMemcpyAsync(tri, c->rec_tri.p, nb * 4, kind_out(mem), c->stream), "get_paths");
     if (point) CKC(c, cudaMemcpyAsync(point, c->rec_p.p, nb * 12, kind_out(mem), c->stream), "get_paths");
@@ -867,7 +922,7 @@ st_status st_get_diffraction(st_ctx* c, int64_t* n_out, int32_t* tri, float* poi
     if (!c->has_last) return fail(c, ST_ERR_STATE, "get_diffraction: no simulate yet");
     *n_out = c->last_K;
     const int64_t n = std::min(capacity, c->last_K);
-    cudaSetDevice(c->device);
+    enter(c);
     if (n > 0) {
         if (tri) CKC(c, cudaMemcpyAsync(tri, c->cand_tri.p, (size_t)n * 4, kind_out(mem), c->stream), "get_diffraction");
         if (point) CKC(c, cudaMemcpyAsync(point, c->cand_p.p, (size_t)n * 12, kind_out(mem), c->stream), "get_diffraction");
@@ -880,7 +935,7 @@ st_status st_get_diffraction(st_ctx* c, int64_t* n_out, int32_t* tri, float* poi
 st_status st_get_direct_visibility(st_ctx* c, uint8_t* vis, int32_t mem) {
     if (!c || !vis) return ST_ERR_ARG;
     if (!c->has_last) return fail(c, ST_ERR_STATE, "get_direct_visibility: no simulate yet");
-    cudaSetDevice(c->device);
+    enter(c);
     CKC(c, cudaMemcpyAsync(vis, c->dvis.p, (size_t)c->last_M, kind_out(mem), c->stream), "get_direct_visibility");
     CKC(c, cudaStreamSynchronize(c->stream), "sync");
     return ST_OK;
@@ -894,7 +949,7 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
     if ((grad_mic || grad_emitter) && c->n_theta > 0)
         return fail(c, ST_ERR_ARG, "backward: position gradients need an omni emitter");
     if (c->mic_nb > 0) return fail(c, ST_ERR_ARG, "backward: needs omni receivers");
-    cudaSetDevice(c->device);
+    enter(c);
     cudaStream_t s = c->stream;
     const st_sim_params& p = c->last_params;
     SceneDev& S = sc->S;
@@ -1037,3 +1092,510 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batched form
+namespace {
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+bool tune_ok(const st_tune& t) {
+    return (t.rays_per_block == 0 || t.rays_per_block == 64 || t.rays_per_block == 128 || t.rays_per_block == 256) &&
+           (t.mic_pairs_per_cta == 0 || (t.mic_pairs_per_cta >= 1 && t.mic_pairs_per_cta <= 16)) &&
+           (t.smem_kb == 0 || (t.smem_kb >= 32 && t.smem_kb <= 160));
+}
+
+void batch_free_graph(BatchState& B) {
+    if (B.exec) cudaGraphExecDestroy(B.exec);
+    if (B.graph) cudaGraphDestroy(B.graph);
+    B.exec = nullptr;
+    B.graph = nullptr;
+}
+
+void batch_release(BatchState& B) {
+    batch_free_graph(B);
+    for (DevBuf* b : {&B.jobs_dev, &B.offs, &B.derived, &B.perm, &B.ord_keys, &B.ord_scr, &B.st_o[0], &B.st_o[1],
+                      &B.st_o[2], &B.st_d[0], &B.st_d[1], &B.st_d[2], &B.st_r, &B.st_prev, &B.q0, &B.q1, &B.counts,
+                      &B.queries, &B.flags, &B.rec_tri, &B.rec_p, &B.rec_d, &B.rec_r, &B.rec_los, &B.cand_tri,
+                      &B.cand_p, &B.keep, &B.dvis, &B.ranges, &B.sflags, &B.sscan, &B.sidx, &B.scratch})
+        release(*b);
+    for (auto& d : B.partial) release(d);
+    for (auto& T : B.tables)
+        for (DevBuf* b : {&T.lk, &T.g2, &T.lid, &T.qhi, &T.qlo, &T.bw, &T.band, &T.kband}) release(*b);
+    for (PathList* P : {&B.spec, &B.diff})
+        for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
+                          &P->meta, &P->dep})
+            release(*b);
+    for (auto st : B.streams) cudaStreamDestroy(st);
+    for (auto ev : B.events) cudaEventDestroy(ev);
+    if (B.main) cudaStreamDestroy(B.main);
+    B.main = nullptr;
+    B.streams.clear();
+    B.events.clear();
+}
+
+// All stages of one batch on stream s (branch streams fork from s and join back).
+cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_sim_params& p, const st_tune& tn,
+                        cudaStream_t s) {
+    cudaError_t e;
+#define CB(x)                          \
+    do {                               \
+        if ((e = (x)) != cudaSuccess) return e; \
+    } while (0)
+    const int n = B.n_jobs;
+    const int64_t* offs = ptr<int64_t>(B.offs);
+    BatchArgs a{};
+    a.jobs = ptr<JobDev>(B.jobs_dev);
+    a.n_jobs = n;
+    a.ray_offs = offs;
+    a.rec_offs = offs + (n + 1);
+    a.samp_offs = offs + 2 * (n + 1);
+    a.mic_offs = offs + 3 * (n + 1);
+    a.mf_offs = offs + 4 * (n + 1);
+    a.N_total = B.N_total;
+    a.R_total = B.R_total;
+    a.K_total = B.K_total;
+    a.M_total = B.M_total;
+    a.MF_total = B.MF_total;
+    a.r_max = p.max_distance;
+    a.c = p.c;
+    a.a0 = p.alpha0_db_m;
+    a.a1 = p.alpha1_db_m_khz;
+    a.t_min = p.t_min;
+    a.los_eps = p.los_eps;
+    a.cos_inc = (float)cos((double)p.theta_inc_rad);
+    a.direct_gain = p.direct_gain;
+    a.seed = p.seed;
+    a.ox = ptr<float>(B.st_o[0]);
+    a.oy = ptr<float>(B.st_o[1]);
+    a.oz = ptr<float>(B.st_o[2]);
+    a.dx = ptr<float>(B.st_d[0]);
+    a.dy = ptr<float>(B.st_d[1]);
+    a.dz = ptr<float>(B.st_d[2]);
+    a.racc = ptr<double>(B.st_r);
+    a.prev = ptr<int32_t>(B.st_prev);
+    uint32_t* cnt = ptr<uint32_t>(B.counts);
+    a.q_in = ptr<uint32_t>(B.q0);
+    a.q_out = ptr<uint32_t>(B.q1);
+    a.n_in = cnt + 0;
+    a.n_out = cnt + 1;
+    a.rec_tri = ptr<int32_t>(B.rec_tri);
+    a.rec_p = ptr<float>(B.rec_p);
+    a.rec_d = ptr<float>(B.rec_d);
+    a.rec_r = ptr<double>(B.rec_r);
+    a.rec_los = ptr<uint8_t>(B.rec_los);
+    a.cand_tri = ptr<int32_t>(B.cand_tri);
+    a.cand_p = ptr<float>(B.cand_p);
+    a.keep = ptr<uint8_t>(B.keep);
+    a.dvis = ptr<uint8_t>(B.dvis);
+    a.ranges = ptr<uint32_t>(B.ranges);
+    a.flags = ptr<uint32_t>(B.flags);
+    a.queries = ptr<unsigned long long>(B.queries);
+    const int64_t Rn = std::max<int64_t>(B.R_total, 1);
+    CB(cudaMemsetAsync(B.flags.p, 0, 16, s));
+    CB(cudaMemsetAsync(B.counts.p, 0, 64, s));
+    CB(cudaMemsetAsync(B.queries.p, 0, 64, s));
+    CB(cudaMemsetAsync(B.rec_tri.p, 0xff, (size_t)Rn * 4, s));
+    CB(cudaMemsetAsync(B.rec_los.p, 0, (size_t)Rn, s));
+    for (int j = 0; j < n; ++j) CB(cudaMemsetAsync(jobs[j].spectra_out, 0, (size_t)3 * jobs[j].n_mics * jobs[j].n_bins * 8, s));
+    CB(batch_prep(a.jobs, n, s));
+    const bool spec = (p.components & ST_COMP_SPECULAR) && B.N_total > 0;
+    if (spec) CB(batch_trace(a, B.max_b, B.N_total, tn.rays_per_block > 0 ? tn.rays_per_block : 128, s));
+    if (B.K_total > 0) CB(batch_diffraction(a, s));
+    if (p.components & ST_COMP_DIRECT) CB(batch_direct(a, s));
+    // compaction of visible records and kept candidates over all jobs; per-job ranges
+    if (spec) {
+        CB(flags_visible_records(a.rec_tri, a.rec_los, B.R_total, ptr<uint32_t>(B.sflags), s));
+        CB(exclusive_scan_u32(ptr<uint32_t>(B.sflags), ptr<uint32_t>(B.sscan), B.R_total, cnt + 2, B.scratch.p, s));
+        CB(compact_indices(ptr<uint32_t>(B.sflags), ptr<uint32_t>(B.sscan), B.R_total, ptr<uint32_t>(B.sidx), s));
+        CB(batch_gather_spec(a, ptr<uint32_t>(B.sidx), cnt + 2, B.spec, s));
+    }
+    const int64_t Koff = std::max<int64_t>(B.R_total, 1);  // candidate scan follows the record scan
+    if (B.K_total > 0) {
+        uint32_t* fl = ptr<uint32_t>(B.sflags) + Koff;
+        uint32_t* sc = ptr<uint32_t>(B.sscan) + Koff;
+        uint32_t* ix = ptr<uint32_t>(B.sidx) + Koff;
+        CB(flags_from_u8(a.keep, B.K_total, fl, s));
+        CB(exclusive_scan_u32(fl, sc, B.K_total, cnt + 3, B.scratch.p, s));
+        CB(compact_indices(fl, sc, B.K_total, ix, s));
+        CB(batch_gather_diff(a, ix, cnt + 3, B.diff, s));
+    }
+    if (spec || B.K_total > 0)
+        CB(batch_ranges(a, ptr<uint32_t>(B.sscan), cnt + 2, ptr<uint32_t>(B.sscan) + Koff, cnt + 3, s));
+    if (p.components & ST_COMP_DIRECT) CB(batch_direct_accum(a, s));
+    // per-job accumulation on parallel branches
+    CB(cudaEventRecord(B.events[0], s));
+    for (int b = 0; b < B.n_branches; ++b) CB(cudaStreamWaitEvent(B.streams[b], B.events[0], 0));
+    const double l2 = log2(10.0) / 20.0;
+    for (int j = 0; j < n; ++j) {
+        const int br = j % B.n_branches;
+        cudaStream_t bs = B.streams[br];
+        const JobDev& jd = B.jobs[j];
+        AccumTables& T = B.tables[j];
+        SceneDev& S = jobs[j].scene->S;
+        AccumArgs x{};
+        x.mics = jobs[j].mics;
+        x.M = jd.M;
+        x.F = jd.F;
+        x.lk = ptr<float>(T.lk);
+        x.g2 = ptr<float>(T.g2);
+        x.lid = ptr<float>(T.lid);
+        x.n_mat_tab = T.n_mat;
+        x.n_bands_tab = S.n_bands;
+        x.bw = ptr<float2>(T.bw);
+        x.qhi = ptr<float>(T.qhi);
+        x.qlo = ptr<float>(T.qlo);
+        const double dq = T.df / p.c;
+        x.dq_hi = (float)dq;
+        x.dq_lo = (float)(dq - (double)x.dq_hi);
+        x.atm2_0 = (float)(-(p.alpha0_db_m + p.alpha1_db_m_khz * jobs[j].f_lo / 1000.0) * l2);
+        x.atm2_step = (float)(-(p.alpha1_db_m_khz * T.df / 1000.0) * l2);
+        x.reflection_mode = p.reflection_mode;
+        x.partial = ptr<float2>(B.partial[br]);
+        x.tile_tp = tn.mic_pairs_per_cta;
+        x.tile_kb = tn.smem_kb;
+        const int64_t MF = (int64_t)jd.M * jd.F;
+        float2* out = static_cast<float2*>(jobs[j].spectra_out);
+        uint32_t* rg = ptr<uint32_t>(B.ranges) + 4 * j;
+        if (spec) {
+            AccumArgs y = x;
+            y.kind = 0;
+            y.n_paths = jd.N * jd.B;
+            y.d_base = rg + 0;
+            y.d_count = rg + 1;
+            y.px = ptr<float>(B.spec.px);
+            y.py = ptr<float>(B.spec.py);
+            y.pz = ptr<float>(B.spec.pz);
+            y.dx = ptr<float>(B.spec.dx);
+            y.dy = ptr<float>(B.spec.dy);
+            y.dz = ptr<float>(B.spec.dz);
+            y.rhi = ptr<float>(B.spec.rhi);
+            y.rlo = ptr<float>(B.spec.rlo);
+            y.chain_lo = ptr<uint32_t>(B.spec.chain_lo);
+            y.chain_hi = ptr<uint32_t>(B.spec.chain_hi);
+            y.meta = ptr<uint32_t>(B.spec.meta);
+            y.dep = ptr<float>(B.spec.dep);
+            y.n_chunks = B.chunks_spec[j];
+            CB(accumulate(y, bs));
+            CB(reduce_partials(y.partial, y.n_chunks, MF, out, bs));
+        }
+        if (jd.K > 0) {
+            AccumArgs y = x;
+            y.kind = 1;
+            y.n_paths = jd.K;
+            y.d_base = rg + 2;
+            y.d_count = rg + 3;
+            y.px = ptr<float>(B.diff.px);
+            y.py = ptr<float>(B.diff.py);
+            y.pz = ptr<float>(B.diff.pz);
+            y.dx = ptr<float>(B.diff.dx);
+            y.dy = ptr<float>(B.diff.dy);
+            y.dz = ptr<float>(B.diff.dz);
+            y.chain_lo = ptr<uint32_t>(B.diff.chain_lo);
+            y.chain_hi = ptr<uint32_t>(B.diff.chain_hi);
+            y.rhi = ptr<float>(B.diff.rhi);
+            y.rlo = ptr<float>(B.diff.rlo);
+            y.meta = ptr<uint32_t>(B.diff.meta);
+            y.dep = ptr<float>(B.diff.dep);
+            y.n_chunks = B.chunks_diff[j];
+            CB(accumulate(y, bs));
+            CB(reduce_partials(y.partial, y.n_chunks, MF, out + MF, bs));
+        }
+    }
+    for (int b = 0; b < B.n_branches; ++b) {
+        CB(cudaEventRecord(B.events[1 + b], B.streams[b]));
+        CB(cudaStreamWaitEvent(s, B.events[1 + b], 0));
+    }
+#undef CB
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const st_sim_params* params,
+                            const st_tune* tune) {
+    if (!c || n_jobs <= 0 || !jobs) return fail(c, ST_ERR_ARG, "simulate_batch: need jobs");
+    st_sim_params p;
+    st_sim_params_default(&p);
+    if (params) p = *params;
+    st_tune tn = tune ? *tune : c->tune;
+    if (!tune_ok(tn)) return fail(c, ST_ERR_ARG, "simulate_batch: tune out of range");
+    for (int j = 0; j < n_jobs; ++j) {
+        const st_job& J = jobs[j];
+        if (!J.scene || !J.scene->S.built || !J.scene->has_materials || J.scene->ctx != c)
+            return fail(c, ST_ERR_STATE, "simulate_batch: every job needs a precomputed scene of this context");
+        if (!J.emitter || !J.emitter_quat || !J.mics || !J.spectra_out || (J.n_rays > 0 && !J.dirs) || J.n_rays < 0 ||
+            J.n_mics < 1 || J.n_mics > kMaxMics || J.n_bins < 1 || J.max_bounces < 1 || J.max_bounces > kMaxBounces ||
+            !(J.f_lo > 0.0) || !(J.f_hi >= J.f_lo) || (J.n_bins > 1 && !(J.f_hi > J.f_lo)))
+            return fail(c, ST_ERR_ARG, "simulate_batch: bad job");
+    }
+    enter(c);
+    cudaStream_t s = c->stream;
+    if (!c->batch) c->batch = new BatchState();
+    BatchState& B = *c->batch;
+    // structure key: everything the recorded work depends on except the poses' values
+    uint64_t key = 1469598103934665603ull;
+    key = fnv(key, &n_jobs, sizeof(n_jobs));
+    for (int j = 0; j < n_jobs; ++j) {
+        const st_job& J = jobs[j];
+        const void* ptrs[6] = {J.scene, J.emitter, J.emitter_quat, J.dirs, J.mics, J.spectra_out};
+        key = fnv(key, ptrs, sizeof(ptrs));
+        key = fnv(key, &J.scene->version, sizeof(uint64_t));
+        key = fnv(key, &J.n_rays, sizeof(J.n_rays));
+        const int32_t iv[3] = {J.n_mics, J.n_bins, J.max_bounces};
+        key = fnv(key, iv, sizeof(iv));
+        const double fv[2] = {J.f_lo, J.f_hi};
+        key = fnv(key, fv, sizeof(fv));
+        key = fnv(key, &J.pose_index, sizeof(J.pose_index));
+        key = fnv(key, &J.fov_half_rad, sizeof(J.fov_half_rad));
+    }
+    const double pd[7] = {p.max_distance, p.c, p.alpha0_db_m, p.alpha1_db_m_khz, p.t_min, p.los_eps,
+                          (double)p.theta_inc_rad};
+    key = fnv(key, pd, sizeof(pd));
+    const double pg = p.direct_gain;
+    key = fnv(key, &pg, sizeof(pg));
+    const int64_t pi[3] = {(int64_t)p.components, (int64_t)p.reflection_mode, (int64_t)p.seed};
+    key = fnv(key, pi, sizeof(pi));
+    const int32_t ti[3] = {tn.rays_per_block, tn.mic_pairs_per_cta, tn.smem_kb};
+    key = fnv(key, ti, sizeof(ti));
+    if (B.valid && B.key == key && B.exec) {
+        const int ne = (int)B.events.size();
+        CKC(c, cudaEventRecord(B.events[ne - 2], s), "batch order");
+        CKC(c, cudaStreamWaitEvent(B.main, B.events[ne - 2], 0), "batch order");
+        CKC(c, cudaGraphLaunch(B.exec, B.main), "batch graph launch");
+        CKC(c, cudaEventRecord(B.events[ne - 1], B.main), "batch order");
+        CKC(c, cudaStreamWaitEvent(s, B.events[ne - 1], 0), "batch order");
+        return ST_OK;
+    }
+    // ---- (re)build the batch's buffers, tables and job table
+    batch_release(B);
+    B = BatchState();
+    B.n_jobs = n_jobs;
+    B.tables.resize(n_jobs);
+    B.jobs.resize(n_jobs);
+    B.chunks_spec.resize(n_jobs);
+    B.chunks_diff.resize(n_jobs);
+    B.n_branches = std::min(8, n_jobs);
+    std::vector<int64_t> ho(5 * (size_t)(n_jobs + 1), 0);
+    int64_t* ray_o = ho.data();
+    int64_t* rec_o = ray_o + (n_jobs + 1);
+    int64_t* smp_o = rec_o + (n_jobs + 1);
+    int64_t* mic_o = smp_o + (n_jobs + 1);
+    int64_t* mf_o = mic_o + (n_jobs + 1);
+    for (int j = 0; j < n_jobs; ++j) {
+        const st_job& J = jobs[j];
+        const int64_t K = (p.components & ST_COMP_DIFFRACTION) ? J.scene->S.total_samples : 0;
+        ray_o[j + 1] = ray_o[j] + J.n_rays;
+        rec_o[j + 1] = rec_o[j] + J.n_rays * J.max_bounces;
+        smp_o[j + 1] = smp_o[j] + K;
+        mic_o[j + 1] = mic_o[j] + J.n_mics;
+        mf_o[j + 1] = mf_o[j] + (int64_t)J.n_mics * J.n_bins;
+        B.max_b = std::max(B.max_b, (int)J.max_bounces);
+    }
+    B.N_total = ray_o[n_jobs];
+    B.R_total = rec_o[n_jobs];
+    B.K_total = smp_o[n_jobs];
+    B.M_total = mic_o[n_jobs];
+    B.MF_total = mf_o[n_jobs];
+    const int64_t N1 = std::max<int64_t>(B.N_total, 1), R1 = std::max<int64_t>(B.R_total, 1),
+                  K1 = std::max<int64_t>(B.K_total, 1);
+    CKC(c, grow(B.offs, ho.size() * 8), "batch alloc");
+    CKC(c, cudaMemcpyAsync(B.offs.p, ho.data(), ho.size() * 8, cudaMemcpyHostToDevice, s), "batch copy");
+    CKC(c, grow(B.derived, (size_t)n_jobs * 6 * 4), "batch alloc");
+    CKC(c, grow(B.perm, (size_t)N1 * 4), "batch alloc");
+    int64_t max_n = 1;
+    for (int j = 0; j < n_jobs; ++j) max_n = std::max(max_n, jobs[j].n_rays);
+    CKC(c, grow(B.ord_keys, (size_t)max_n * 8), "batch alloc");
+    CKC(c, grow(B.ord_scr, sort_scratch_bytes(max_n)), "batch alloc");
+    for (int k = 0; k < 3; ++k) {
+        CKC(c, grow(B.st_o[k], (size_t)N1 * 4), "batch alloc");
+        CKC(c, grow(B.st_d[k], (size_t)N1 * 4), "batch alloc");
+    }
+    CKC(c, grow(B.st_r, (size_t)N1 * 8), "batch alloc");
+    CKC(c, grow(B.st_prev, (size_t)N1 * 4), "batch alloc");
+    CKC(c, grow(B.q0, (size_t)N1 * 4), "batch alloc");
+    CKC(c, grow(B.q1, (size_t)N1 * 4), "batch alloc");
+    CKC(c, grow(B.counts, 64), "batch alloc");
+    CKC(c, grow(B.queries, 64), "batch alloc");
+    CKC(c, grow(B.flags, 16), "batch alloc");
+    CKC(c, grow(B.rec_tri, (size_t)R1 * 4), "batch alloc");
+    CKC(c, grow(B.rec_p, (size_t)R1 * 12), "batch alloc");
+    CKC(c, grow(B.rec_d, (size_t)R1 * 12), "batch alloc");
+    CKC(c, grow(B.rec_r, (size_t)R1 * 8), "batch alloc");
+    CKC(c, grow(B.rec_los, (size_t)R1), "batch alloc");
+    CKC(c, grow(B.cand_tri, (size_t)K1 * 4), "batch alloc");
+    CKC(c, grow(B.cand_p, (size_t)K1 * 12), "batch alloc");
+    CKC(c, grow(B.keep, (size_t)K1), "batch alloc");
+    CKC(c, grow(B.dvis, (size_t)std::max<int64_t>(B.M_total, 1)), "batch alloc");
+    CKC(c, grow(B.ranges, (size_t)n_jobs * 16), "batch alloc");
+    CKC(c, grow(B.sflags, (size_t)(R1 + K1) * 4), "batch alloc");
+    CKC(c, grow(B.sscan, (size_t)(R1 + K1) * 4), "batch alloc");
+    CKC(c, grow(B.sidx, (size_t)(R1 + K1) * 4), "batch alloc");
+    CKC(c, grow(B.scratch, scan_scratch_bytes(std::max(R1, K1))), "batch alloc");
+    for (PathList* P : {&B.spec, &B.diff}) {
+        const int64_t nP = P == &B.spec ? R1 : K1;
+        for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
+                          &P->meta, &P->dep})
+            CKC(c, grow(*b, (size_t)nP * 4), "batch alloc");
+        P->n_max = nP;
+    }
+    std::vector<size_t> part_bytes(B.n_branches, 256);
+    float* derived = ptr<float>(B.derived);
+    for (int j = 0; j < n_jobs; ++j) {
+        const st_job& J = jobs[j];
+        SceneDev& S = J.scene->S;
+        CKC(c, build_accum_tables(B.tables[j], S, J.n_bins, J.f_lo, J.f_hi, p.c, p.alpha0_db_m, p.alpha1_db_m_khz, s),
+            "batch tables");
+        if (J.n_rays > 0)
+            CKC(c, direction_order(J.dirs, J.n_rays, ptr<uint64_t>(B.ord_keys), ptr<uint32_t>(B.perm) + ray_o[j],
+                                   B.ord_scr.p, s),
+                "batch order");
+        JobDev& d = B.jobs[j];
+        d = JobDev{};
+        d.nodes = ptr<float4>(S.nodes);
+        d.tri_v = ptr<float4>(S.tri_v);
+        d.nrm = ptr<float>(S.nrm);
+        d.tri_mat = ptr<int32_t>(S.tri_mat);
+        d.verts = ptr<float>(S.verts);
+        d.tris = ptr<int32_t>(S.tris);
+        d.mesh_tris = ptr<int32_t>(S.mesh_tris);
+        d.mesh_off = ptr<int64_t>(S.mesh_off);
+        d.cdf = ptr<uint64_t>(S.cdf);
+        d.sample_off = ptr<int64_t>(S.sample_off);
+        d.root = S.root;
+        d.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+        d.n_obj = S.n_obj;
+        d.cos_fov = J.fov_half_rad >= (float)M_PI ? -2.0f : (float)cos((double)J.fov_half_rad);
+        d.s = J.emitter;
+        d.q = J.emitter_quat;
+        d.dirs = J.dirs;
+        d.mics = J.mics;
+        d.R = derived + 6 * j;
+        d.fwd = derived + 6 * j + 3;
+        d.perm = J.n_rays > 0 ? ptr<uint32_t>(B.perm) + ray_o[j] : nullptr;
+        d.qhi = ptr<float>(B.tables[j].qhi);
+        d.qlo = ptr<float>(B.tables[j].qlo);
+        d.N = J.n_rays;
+        d.K = smp_o[j + 1] - smp_o[j];
+        d.ray_off = ray_o[j];
+        d.rec_off = rec_o[j];
+        d.samp_off = smp_o[j];
+        d.mic_off = mic_o[j];
+        d.mf_off = mf_o[j];
+        d.B = J.max_bounces;
+        d.M = J.n_mics;
+        d.F = J.n_bins;
+        d.pose = J.pose_index;
+        d.f_lo = J.f_lo;
+        d.df = B.tables[j].df;
+        d.out = static_cast<float2*>(J.spectra_out);
+        // chunks: the branches share the GPU, so each job uses about 1/branches of it
+        const int nb = B.n_branches;
+        B.chunks_spec[j] = std::max(1, accum_chunks(d.N * d.B, d.M, d.F, S.n_mat, 0, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
+        B.chunks_diff[j] = std::max(1, accum_chunks(d.K, d.M, d.F, S.n_mat, 0, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
+        const size_t need = (size_t)std::max(B.chunks_spec[j], B.chunks_diff[j]) * d.M * d.F * 8;
+        part_bytes[j % nb] = std::max(part_bytes[j % nb], need);
+    }
+    B.partial.resize(B.n_branches);
+    for (int b = 0; b < B.n_branches; ++b) CKC(c, grow(B.partial[b], part_bytes[b]), "batch alloc");
+    CKC(c, grow(B.jobs_dev, sizeof(JobDev) * (size_t)n_jobs), "batch alloc");
+    CKC(c, cudaMemcpyAsync(B.jobs_dev.p, B.jobs.data(), sizeof(JobDev) * (size_t)n_jobs, cudaMemcpyHostToDevice, s),
+        "batch copy");
+    B.streams.resize(B.n_branches);
+    for (auto& st : B.streams) CKC(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch streams");
+    B.events.resize(3 + B.n_branches);
+    for (auto& ev : B.events) CKC(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch events");
+    CKC(c, cudaStreamCreateWithFlags(&B.main, cudaStreamNonBlocking), "batch streams");
+    CKC(c, cudaStreamSynchronize(s), "batch setup");
+    // ---- eager run (also sets kernel attributes), then record the graph for later calls
+    cudaStream_t ms = B.main;
+    CKC(c, batch_issue(c, B, jobs, p, tn, ms), "batch run");
+    CKC(c, cudaStreamSynchronize(ms), "batch run");
+    uint32_t fl = 0;
+    CKC(c, cudaMemcpy(&fl, B.flags.p, 4, cudaMemcpyDeviceToHost), "batch flags");
+    if (fl & kFlagStackOverflow) return fail(c, ST_ERR_OVERFLOW, "traversal stack overflow");
+    if (fl & kFlagBadTree) return fail(c, ST_ERR_CUDA, "malformed BVH: traversal exceeded the node count");
+    CKC(c, cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal), "batch capture");
+    cudaError_t ie = batch_issue(c, B, jobs, p, tn, ms);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(ms, &g);
+    if (ie != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, ie, "batch capture");
+    }
+    CKC(c, ce, "batch capture end");
+    B.graph = g;
+    CKC(c, cudaGraphInstantiate(&B.exec, g, 0), "batch instantiate");
+    B.key = key;
+    B.valid = true;
+    return ST_OK;
+}
+
+st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, st_tune* out) {
+    if (!c || !J || !out) return fail(c, ST_ERR_ARG, "autotune: null argument");
+    if (!J->scene || !J->scene->S.built) return fail(c, ST_ERR_STATE, "autotune: precomputed scene needed");
+    enter(c);
+    st_status r;
+    if ((r = st_set_frequencies(c, J->n_bins, J->f_lo, J->f_hi)) != ST_OK) return r;
+    if ((r = st_set_emitter(c, J->emitter, J->emitter_quat, J->n_rays, J->dirs, nullptr, 0, J->fov_half_rad,
+                            ST_MEM_DEVICE)) != ST_OK)
+        return r;
+    if ((r = st_set_receivers(c, J->n_mics, J->mics, nullptr, nullptr, 0, 0, 0, ST_MEM_DEVICE)) != ST_OK) return r;
+    st_sim_params p;
+    st_sim_params_default(&p);
+    if (params) p = *params;
+    p.max_bounces = J->max_bounces;
+    p.pose_index = J->pose_index;
+    DevBuf out_buf;
+    CKC(c, grow(out_buf, (size_t)3 * J->n_mics * J->n_bins * 8), "autotune alloc");
+    const st_tune saved = c->tune;
+    const int rpb[3] = {64, 128, 256};
+    const int tiles[5][2] = {{16, 96}, {8, 96}, {16, 64}, {4, 96}, {16, 128}};
+    st_tune best = {128, 16, 96, 0};
+    // tracing block size with the default tile, then the accumulator tile with the best block size
+    for (int phase = 0; phase < 2; ++phase) {
+        const int n_cand = phase == 0 ? 3 : 5;
+        st_tune winner = best;
+        float winner_ms = 1e30f;
+        for (int i = 0; i < n_cand; ++i) {
+            st_tune t = best;
+            if (phase == 0) t.rays_per_block = rpb[i];
+            else {
+                t.mic_pairs_per_cta = tiles[i][0];
+                t.smem_kb = tiles[i][1];
+            }
+            c->tune = t;
+            st_stats st;
+            float acc = 0.0f;
+            for (int rep = 0; rep < 3; ++rep) {
+                r = st_simulate(c, J->scene, &p, out_buf.p, &st);
+                if (r != ST_OK) {
+                    c->tune = saved;
+                    release(out_buf);
+                    return r;
+                }
+                if (rep > 0) acc += phase == 0 ? st.ms_trace : st.ms_accum_kernel;
+            }
+            if (acc < winner_ms) {
+                winner_ms = acc;
+                winner = t;
+            }
+        }
+        best = winner;
+    }
+    release(out_buf);
+    c->tune = best;
+    *out = best;
+    return ST_OK;
+}
+
+}  // extern "C"
+

@@ -215,6 +215,8 @@ struct AccumArgs {
     int kind;               // 0 specular, 1 diffraction
     int64_t n_paths;        // upper bound; actual count in *d_count
     const uint32_t* d_count;
+    const uint32_t* d_base; // optional: first path of this launch in the path arrays (device), null = 0
+    int32_t tile_tp, tile_kb;  // optional tile override: mic pairs per CTA, shared-memory KB (0 = default)
     const float* px; const float* py; const float* pz;
     const float* dx; const float* dy; const float* dz;
     const float* rhi; const float* rlo;
@@ -243,7 +245,8 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
                                double a0, double a1, cudaStream_t s);
 cudaError_t accumulate(const AccumArgs& a, cudaStream_t s);
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s);
-int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb);
+int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb, int32_t tile_tp = 0,
+                     int32_t tile_kb = 0);
 
 struct GatherArgs {
     // specular
@@ -264,6 +267,79 @@ cudaError_t flags_visible_records(const int32_t* rec_tri, const uint8_t* rec_los
                                   cudaStream_t s);
 cudaError_t flags_from_u8(const uint8_t* keep, int64_t n, uint32_t* flags, cudaStream_t s);
 cudaError_t compact_indices(const uint32_t* flags, const uint32_t* scan, int64_t n, uint32_t* idx, cudaStream_t s);
+
+// ------------------------------------------------------------------ batched form (st_batch.cu)
+// One pose of a batch as the device sees it.
+struct JobDev {
+    // scene
+    const float4* nodes;
+    const float4* tri_v;
+    const float* nrm;
+    const int32_t* tri_mat;
+    const float* verts;
+    const int32_t* tris;
+    const int32_t* mesh_tris;
+    const int64_t* mesh_off;
+    const uint64_t* cdf;
+    const int64_t* sample_off;
+    int32_t root, max_iter, n_obj;
+    float cos_fov;          // <= -1: field of view off
+    // sensor inputs (the caller's device memory, read at run time)
+    const float* s;
+    const float* q;
+    const float* dirs;
+    const float* mics;
+    // per-job derived data and tables (batch-owned)
+    float* R;               // [3] receiver reference point
+    float* fwd;             // [3] emitter forward axis
+    const uint32_t* perm;   // [N] first-bounce processing order
+    const float* qhi;
+    const float* qlo;
+    // sizes and offsets into the batch's global arrays
+    int64_t N, K, ray_off, rec_off, samp_off, mic_off, mf_off;
+    int32_t B, M, F;
+    uint32_t pose;
+    double f_lo, df;
+    float2* out;            // spectra [3][M][F]
+};
+
+struct BatchArgs {
+    const JobDev* jobs;
+    int32_t n_jobs;
+    const int64_t* ray_offs;   // [n_jobs+1] each, ascending
+    const int64_t* rec_offs;
+    const int64_t* samp_offs;
+    const int64_t* mic_offs;
+    const int64_t* mf_offs;
+    int64_t N_total, R_total, K_total, M_total, MF_total;
+    double r_max, c, a0, a1;
+    float t_min, los_eps, cos_inc, direct_gain;
+    uint64_t seed;
+    // ray state and queues
+    float* ox; float* oy; float* oz; float* dx; float* dy; float* dz;
+    double* racc;
+    int32_t* prev;
+    uint32_t* q_in; uint32_t* q_out; uint32_t* n_in; uint32_t* n_out;
+    // records [R_total]
+    int32_t* rec_tri; float* rec_p; float* rec_d; double* rec_r; uint8_t* rec_los;
+    // candidates [K_total], direct visibility [M_total]
+    int32_t* cand_tri; float* cand_p; uint8_t* keep; uint8_t* dvis;
+    uint32_t* ranges;          // [n_jobs][4]: specular first path, count, diffraction first path, count
+    uint32_t* flags;
+    unsigned long long* queries;
+};
+
+cudaError_t batch_prep(const JobDev* jobs, int n_jobs, cudaStream_t s);
+cudaError_t batch_trace(BatchArgs& a, int max_b, int64_t n_total, int block, cudaStream_t s);
+cudaError_t batch_diffraction(const BatchArgs& a, cudaStream_t s);
+cudaError_t batch_direct(const BatchArgs& a, cudaStream_t s);
+cudaError_t batch_ranges(const BatchArgs& a, const uint32_t* scan_rec, const uint32_t* total_rec,
+                         const uint32_t* scan_cand, const uint32_t* total_cand, cudaStream_t s);
+cudaError_t batch_gather_spec(const BatchArgs& a, const uint32_t* idx, const uint32_t* count, PathList& P,
+                              cudaStream_t s);
+cudaError_t batch_gather_diff(const BatchArgs& a, const uint32_t* idx, const uint32_t* count, PathList& P,
+                              cudaStream_t s);
+cudaError_t batch_direct_accum(const BatchArgs& a, cudaStream_t s);
 
 // Adjoint of one accumulation launch (st_adjoint.cu).
 struct AdjointArgs {
@@ -304,5 +380,16 @@ cudaError_t adjoint_dk(const float* v_part, int n_slices, int F, int mat_base, i
                        cudaStream_t s);
 cudaError_t adjoint_pos(const float* mic_parts, int n_mic_slices, const float* emit_parts, int n_emit_slices, int M,
                         float* dmic, float* demit, cudaStream_t s);
+
+// last j in [0, n) with off[j] <= g (off ascending, off[0] = 0)
+__device__ __forceinline__ int find_job(const int64_t* off, int n, int64_t g) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 
 }  // namespace st

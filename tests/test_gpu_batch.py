@@ -1,0 +1,161 @@
+"""Batched form (many poses over several scenes in one launch per stage, recorded as a CUDA graph).
+
+Each job's spectra must equal the single-pose path on the same inputs (which the parity tests pin
+to the oracle) up to the order of the float32 chunk sums, and match the oracle directly within the
+spectra tolerance; a graph replay after the poses are updated in place must give the new poses'
+spectra; the autotuner must return launch shapes that give the same results."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4        # against the oracle
+TOL_SINGLE = 2e-5  # against the single-pose path (same path sets; only the chunking of the sums differs)
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b.ravel())
+    if nb == 0:
+        return float(np.linalg.norm(a.ravel()))
+    return float(np.linalg.norm((a - b).ravel()) / nb)
+
+
+@pytest.fixture(scope="module")
+def st():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_19652_gb300 as st_
+    return st_
+
+
+def unit_quat(rng):
+    q = rng.normal(size=4)
+    return (q / np.linalg.norm(q)).astype(np.float32)
+
+
+def make_case(st, ctx, seed=11, n_scenes=3, poses=3, diffraction=True):
+    rng = np.random.default_rng(seed)
+    wls, specs = synth.batched_poses(seed=505 + seed, n_scenes=n_scenes, poses_per_scene=poses, tri_lo=2e3, tri_hi=2e4)
+    scenes = []
+    for wl in wls:
+        sc = st.Scene(ctx, wl.verts, wl.tris, wl.tri_mat, wl.tri_obj)
+        sc.set_materials(wl.band_hz, wl.k_band, wl.beta_band, wl.diff_band)
+        sc.precompute(st.curv_params(sample_budget=50_000))
+        scenes.append(sc)
+    jobs, wl_jobs = [], []
+    for i, sp in enumerate(specs):
+        wl = wls[sp["scene"]]
+        n = int(rng.integers(700, 4000))
+        M = min(sp["n_mics"], 12)
+        F = int(rng.integers(17, 200))
+        fov = float(np.float32(math.pi if i % 2 == 0 else math.pi / 2))
+        wj = dataclasses.replace(wl, emitter=sp["emitter"], emitter_quat=unit_quat(rng),
+                                 dirs=synth.fibonacci_directions(n), mics=sp["mics"][:M].astype(np.float32), n_bins=F,
+                                 bounces=sp["bounces"], max_distance=60.0, diffraction=diffraction, fov_half=fov)
+        jobs.append(st.BatchJob(scenes[sp["scene"]], wj.emitter, wj.emitter_quat, wj.dirs, wj.mics, F, wl.f_lo,
+                                wl.f_hi, wj.bounces, pose_index=sp["pose_index"], fov_half=fov))
+        wl_jobs.append(wj)
+    return scenes, jobs, wl_jobs
+
+
+def single(st, ctx, sc, wj, pose, **kw):
+    ctx.set_frequencies(wj.n_bins, wj.f_lo, wj.f_hi)
+    ctx.set_emitter(wj.emitter, wj.emitter_quat, wj.dirs, None, wj.fov_half)
+    ctx.set_receivers(wj.mics)
+    p = st.sim_params(max_bounces=wj.bounces, max_distance=60.0, pose_index=pose, **kw)
+    return ctx.simulate(sc, p).cpu().numpy()
+
+
+def test_batch_equals_single_pose_and_oracle(st):
+    import oracle
+    ctx = st.Context(0)
+    scenes, jobs, wl_jobs = make_case(st, ctx)
+    p = st.sim_params(max_distance=60.0)
+    outs = [o.cpu().numpy() for o in ctx.simulate_batch(jobs, p)]
+    n_nonzero = 0
+    for j, (job, wj) in enumerate(zip(jobs, wl_jobs)):
+        ref = single(st, ctx, job.scene, wj, job.job.pose_index)
+        for c in range(3):
+            assert rel_l2(outs[j][c], ref[c]) <= TOL_SINGLE, (j, c, rel_l2(outs[j][c], ref[c]))
+        n_nonzero += int(np.abs(outs[j][0]).sum() > 0) + int(np.abs(outs[j][1]).sum() > 0)
+    assert n_nonzero >= len(jobs)
+    # the oracle on two jobs (all three components)
+    for j in (0, len(jobs) - 1):
+        wj = wl_jobs[j]
+        o = oracle.simulate(wj, curv=dict(budget=50_000), pose=jobs[j].job.pose_index)
+        for c in range(3):
+            assert rel_l2(outs[j][c], o["spectra"][c]) <= TOL, (j, c, rel_l2(outs[j][c], o["spectra"][c]))
+
+
+def test_batch_graph_replay_after_pose_update(st):
+    ctx = st.Context(0)
+    scenes, jobs, wl_jobs = make_case(st, ctx, seed=12, n_scenes=2, poses=3)
+    p = st.sim_params(max_distance=60.0)
+    first = [o.cpu().numpy().copy() for o in ctx.simulate_batch(jobs, p)]
+    again = [o.cpu().numpy().copy() for o in ctx.simulate_batch(jobs, p)]  # replay, same poses
+    for a, b in zip(first, again):
+        assert np.array_equal(a, b)  # deterministic reductions
+    rng = np.random.default_rng(99)
+    new_wl = []
+    for job, wj in zip(jobs, wl_jobs):
+        shift = rng.uniform(-0.5, 0.5, size=3).astype(np.float32)
+        shift[2] *= 0.2
+        e = (wj.emitter + shift).astype(np.float32)
+        q = unit_quat(rng)
+        m = (wj.mics + shift).astype(np.float32)
+        job.set_pose(emitter=e, emitter_quat=q, mics=m)
+        new_wl.append(dataclasses.replace(wj, emitter=e, emitter_quat=q, mics=m))
+    outs = [o.cpu().numpy() for o in ctx.simulate_batch(jobs, p)]  # replay with the new poses
+    changed = 0
+    for j, (job, wj) in enumerate(zip(jobs, new_wl)):
+        ref = single(st, ctx, job.scene, wj, job.job.pose_index)
+        for c in range(3):
+            assert rel_l2(outs[j][c], ref[c]) <= TOL_SINGLE, (j, c)
+        changed += int(not np.array_equal(outs[j], first[j]))
+    assert changed == len(jobs)
+
+
+def test_batch_components_and_empty_jobs(st):
+    """Specular only, a job with no rays, and single-mic / single-bin jobs."""
+    ctx = st.Context(0)
+    scenes, jobs, wl_jobs = make_case(st, ctx, seed=13, n_scenes=1, poses=2, diffraction=False)
+    wl0 = wl_jobs[0]
+    sc = jobs[0].scene
+    extra = [
+        (dataclasses.replace(wl0, dirs=np.zeros((0, 3), np.float32), n_bins=5), 0),
+        (dataclasses.replace(wl0, mics=wl0.mics[:1].copy(), n_bins=1, bounces=1), 1),
+    ]
+    for wj, pose in extra:
+        jobs.append(st.BatchJob(sc, wj.emitter, wj.emitter_quat, wj.dirs, wj.mics, wj.n_bins, wj.f_lo, wj.f_hi,
+                                wj.bounces, pose_index=pose, fov_half=wj.fov_half))
+        wl_jobs.append(wj)
+    for comps in (st.ST_COMP_SPECULAR, st.ST_COMP_SPECULAR | st.ST_COMP_DIRECT):
+        p = st.sim_params(max_distance=60.0, components=comps)
+        outs = [o.cpu().numpy() for o in ctx.simulate_batch(jobs, p)]
+        for j, (job, wj) in enumerate(zip(jobs, wl_jobs)):
+            if wj.dirs.shape[0] == 0:
+                assert np.all(outs[j][0] == 0) and np.all(outs[j][1] == 0)
+                continue
+            ref = single(st, ctx, job.scene, wj, job.job.pose_index, components=comps)
+            for c in range(3):
+                assert rel_l2(outs[j][c], ref[c]) <= TOL_SINGLE, (comps, j, c)
+
+
+def test_autotune_shapes_give_same_results(st):
+    ctx = st.Context(0)
+    scenes, jobs, wl_jobs = make_case(st, ctx, seed=14, n_scenes=1, poses=2)
+    p = st.sim_params(max_distance=60.0)
+    base = [o.cpu().numpy().copy() for o in ctx.simulate_batch(jobs, p)]
+    t = ctx.autotune(jobs[0], p)
+    assert t.rays_per_block in (64, 128, 256)
+    assert 1 <= t.mic_pairs_per_cta <= 16 and 32 <= t.smem_kb <= 160
+    tuned = [o.cpu().numpy() for o in ctx.simulate_batch(jobs, p, t)]
+    for a, b in zip(tuned, base):
+        for c in range(3):
+            assert rel_l2(a[c], b[c]) <= TOL_SINGLE
