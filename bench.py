@@ -189,6 +189,90 @@ def measure_adjoint(st, torch, wl, steps: int = 5):
     return {"fwd_ms": f, "bwd_ms": b, "bwd_over_fwd": b / f}
 
 
+def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 65536, reps: int = 3):
+    """Batched form against plain per-pose calls on the pose-sweep workload: 256 sensor poses over 16
+    procedural scenes (triangle counts log-uniform 10k-2M, 1-4 materials), 2-64 mics, 256-2048 bins,
+    1-5 bounces per pose, diffraction on.  Both arms use the autotuned launch shapes; both are timed
+    on the device with L2 flushed before each timed pass."""
+    dev = torch.cuda.current_device()
+    wls, specs = synth.batched_poses(seed=505)
+    ctx = st.Context(dev)
+    scenes = []
+    for wl in wls:
+        sc = st.Scene(ctx, wl.verts, wl.tris, wl.tri_mat, wl.tri_obj)
+        sc.set_materials(wl.band_hz, wl.k_band, wl.beta_band, wl.diff_band)
+        sc.precompute(st.curv_params(sample_budget=sample_budget))
+        scenes.append(sc)
+    dirs = synth.fibonacci_directions(rays_per_pose)
+    rng = np.random.default_rng(606)
+    jobs = []
+    for sp in specs:
+        q = rng.normal(size=4)
+        q = (q / np.linalg.norm(q)).astype(np.float32)
+        wl = wls[sp["scene"]]
+        jobs.append(st.BatchJob(scenes[sp["scene"]], sp["emitter"], q, dirs, sp["mics"], sp["n_bins"], wl.f_lo, wl.f_hi,
+                                sp["bounces"], pose_index=sp["pose_index"], device=dev))
+    p = st.sim_params(max_distance=60.0)
+    order = np.argsort([j.M * j.F * j.job.max_bounces for j in jobs])
+    tune = ctx.autotune(jobs[int(order[len(order) // 2])], p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ms = []
+        for i in range(reps):
+            flush.fill_(i & 255)
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ms))
+
+    # batched: first call runs eagerly and records the graph; the timed calls replay it
+    t0 = time.perf_counter()
+    ctx.simulate_batch(jobs, p, tune)
+    torch.cuda.synchronize()
+    first_call_s = time.perf_counter() - t0
+    ctx.simulate_batch(jobs, p, tune)
+    batched_ms = timed(lambda: ctx.simulate_batch(jobs, p, tune))
+    batched_out = [j.out.clone() for j in jobs]
+
+    # plain: one st_simulate per pose (sensor inputs already on the device)
+    plain_out = [torch.empty_like(j.out) for j in jobs]
+    host_pose = [(j.emitter.cpu().numpy(), j.emitter_quat.cpu().numpy()) for j in jobs]
+    plain_params = [st.sim_params(max_distance=60.0, max_bounces=j.job.max_bounces, pose_index=j.job.pose_index)
+                    for j in jobs]
+
+    def plain():
+        for j, o, (e, q), pp in zip(jobs, plain_out, host_pose, plain_params):
+            ctx.set_frequencies(j.F, j.job.f_lo, j.job.f_hi)
+            ctx.set_emitter(e, q, j.dirs, None, math.pi)
+            ctx.set_receivers(j.mics)
+            ctx.simulate(j.scene, pp, out=o)
+
+    plain()
+    plain_ms = timed(plain)
+    err = 0.0
+    for a, b in zip(batched_out, plain_out):
+        for c in range(3):
+            nb = float(torch.linalg.vector_norm(b[c]))
+            if nb > 0:
+                err = max(err, float(torch.linalg.vector_norm(a[c] - b[c])) / nb)
+    n_rays = sum(j.N for j in jobs)
+    n_spec = sum(j.M for j in jobs)
+    return {"workload": f"{len(jobs)} poses over {len(scenes)} scenes ({min(w.n_tris for w in wls)}-"
+                        f"{max(w.n_tris for w in wls)} triangles), {rays_per_pose} rays per pose, "
+                        f"diffraction budget {sample_budget} per scene",
+            "tune": {"rays_per_block": tune.rays_per_block, "mic_pairs_per_cta": tune.mic_pairs_per_cta,
+                     "smem_kb": tune.smem_kb},
+            "batched_ms": batched_ms, "plain_ms": plain_ms, "speedup": plain_ms / batched_ms,
+            "batched_mrays_per_s": n_rays / batched_ms / 1e3, "plain_mrays_per_s": n_rays / plain_ms / 1e3,
+            "batched_mic_spectra_per_s": n_spec / batched_ms * 1e3, "plain_mic_spectra_per_s": n_spec / plain_ms * 1e3,
+            "max_rel_l2_batched_vs_plain": err, "first_call_s": first_call_s}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -224,6 +308,7 @@ def main():
     ap.add_argument("--ref-rays", type=int, default=2048, help="rays per step of the reference (oracle) arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain pose sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -347,6 +432,10 @@ def main():
                    measure_adjoint(st, torch, synth.gradient_problem(seed=404)),
                    f"{wl.name} workload": measure_adjoint(st, torch, wl)}
 
+    batched = None
+    if not args.no_batched:
+        batched = measure_batched(st, torch)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -370,6 +459,7 @@ def main():
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
                          "ms_accumulate": s0.ms_accumulate},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
+            "batched": batched,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
     print(json.dumps(line))
     if world > 1:
