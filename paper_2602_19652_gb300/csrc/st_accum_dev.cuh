@@ -114,6 +114,7 @@ struct Geom {
     int TP, NS, MP, KB, PT;  // mic pairs per CTA (threads along x), subtiles, mics per CTA, bins per CTA, paths/tile
     int n_mb, n_bb;
     int NB;                  // receiver directivity bands held per (path, mic); 0 = omni receivers
+    int ADJ;                 // adjoint layout: per (path, pair) position-gradient vectors after ngp
     int mat_cached;          // material tables held in shared memory (n_mat small enough)
     size_t mat_bytes;        // their size
     size_t buf_bytes;        // one pipeline buffer (tables + anchors of PT paths)
@@ -126,12 +127,15 @@ struct Geom {
 //   za  [PT][NS][TP] ulonglong2  phasor at bin kb + s*KT of the two mics of pair tp (re pair, im pair)
 //   wst [PT][TP][4] u64      one-bin step (re, im) and two-bin step (re, im) of the pair
 //   ngp [PT][TP] u64         -gamma^2 of the pair
+//   adj [PT][TP][7] u64      (adjoint only) unit(m - P) xyz, lobe-angle vector xyz (specular) or
+//                            -unit(o - s) xyz (diffraction), 1 / r of the pair
 // then two path-data buffers pd [PT][12] + valid [PT], then the per-CTA material tables.
 struct Buf {
     float4* tab;
     ulonglong2* za;
     u64* wst;
     u64* ngp;
+    u64* adj;
     float* dband;  // [PT][MP][NB] receiver directivity band values (directional receivers only)
 };
 
@@ -143,7 +147,8 @@ __device__ __forceinline__ Buf buf_at(float4* base, const Geom& g, int b) {
     B.za = reinterpret_cast<ulonglong2*>(B.tab + (size_t)g.PT * g.KB);
     B.wst = reinterpret_cast<u64*>(B.za + (size_t)g.PT * g.NS * g.TP);
     B.ngp = B.wst + (size_t)g.PT * g.TP * 4;
-    B.dband = reinterpret_cast<float*>(B.ngp + (size_t)g.PT * g.TP);
+    B.adj = B.ngp + (size_t)g.PT * g.TP;
+    B.dband = reinterpret_cast<float*>(B.adj + (g.ADJ ? (size_t)g.PT * g.TP * 7 : 0));
     return B;
 }
 
@@ -216,10 +221,12 @@ __device__ __forceinline__ void load_paths(const AccumArgs& a, int PT, int64_t p
     }
 }
 
-// tables and anchors of one tile (reads pd / pv, writes buffer B)
-template <int KT, int KIND>
+// tables and anchors of one tile (reads pd / pv, writes buffer B); ADJ: also the position-gradient
+// vectors of the adjoint (es = emitter position, diffraction only)
+template <int KT, int KIND, int ADJ = 0>
 __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const Buf& B, const float* pd, const int* pv,
-                                        const float* mt, int mic0, int kb, float invNS, float invKB) {
+                                        const float* mt, int mic0, int kb, float invNS, float invKB,
+                                        const float* es = nullptr) {
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
     const bool cached = g.mat_cached > 0;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -338,6 +345,10 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
             for (int q = 0; q < 4; ++q) wf[2 * q + half] = 0.0f;
             nf[half] = 0.0f;
             for (int b = 0; b < g.NB; ++b) B.dband[((size_t)p * MP + ml) * g.NB + b] = 0.0f;
+            if (ADJ) {
+                float* af = reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7);
+                for (int q = 0; q < 7; ++q) af[2 * q + half] = 0.0f;
+            }
             continue;
         }
         const float* d = pd + p * 12;
@@ -346,15 +357,38 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
         const ff r = ff_add(ff{d[6], d[7]}, dist);
         if (g.NB > 0) mic_bands(a, m, d[0] - mx, d[1] - my, d[2] - mz, B.dband + ((size_t)p * MP + ml) * g.NB, g.NB);
         float gam2 = 0.0f;
-        if (KIND == 0) {
+        if (KIND == 0 || ADJ) {
             const float inv = 1.0f / dist.hi;
             const float ux = (mx - d[0]) * inv, uy = (my - d[1]) * inv, uz = (mz - d[2]) * inv;
-            const float cg = d[3] * ux + d[4] * uy + d[5] * uz;
-            const float cx = d[4] * uz - d[5] * uy, cy = d[5] * ux - d[3] * uz, cz = d[3] * uy - d[4] * ux;
-            const float gm = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), cg);
-            gam2 = gm * gm;
+            float* af = reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7);
+            if (KIND == 0) {
+                const float cg = d[3] * ux + d[4] * uy + d[5] * uz;
+                const float cx = d[4] * uz - d[5] * uy, cy = d[5] * ux - d[3] * uz, cz = d[3] * uy - d[4] * ux;
+                const float sg = sqrtf(cx * cx + cy * cy + cz * cz);
+                const float gm = atan2f(sg, cg);
+                gam2 = gm * gm;
+                if (ADJ) {
+                    // d gamma / d m = -(d' - cos(gamma) u) / (|m - P| sin gamma); with dL/dgamma =
+                    // -2 ln2 gamma sum_k g_k Re w the microphone gradient gains (sum_k g_k Re w) times this vector
+                    const float f = sg > 1e-20f ? 2.0f * 0.69314718055994531f * gm / (dist.hi * sg) : 0.0f;
+                    af[6 + half] = f * (d[3] - cg * ux);
+                    af[8 + half] = f * (d[4] - cg * uy);
+                    af[10 + half] = f * (d[5] - cg * uz);
+                }
+            } else if (ADJ) {
+                const float iv = 1.0f / d[6];  // -unit(o - s): d r / d s of a diffraction path
+                af[6 + half] = -((d[0] - es[0]) * iv);
+                af[8 + half] = -((d[1] - es[1]) * iv);
+                af[10 + half] = -((d[2] - es[2]) * iv);
+            }
+            if (ADJ) {
+                af[0 + half] = ux;
+                af[2 + half] = uy;
+                af[4 + half] = uz;
+            }
         }
         const float rh = r.hi;
+        if (ADJ) reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7)[12 + half] = 1.0f / rh;
         const float L0 = -2.0f * log2_ff(r) + rh * (a.atm2_0 + a.atm2_step * (float)kb);
         const ff x0 = ff_mul(r, ff{a.qhi[min(kb, a.F - 1)], a.qlo[min(kb, a.F - 1)]});
         float s0, c0;
@@ -387,6 +421,7 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
 inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t budget = 96 * 1024, int dir_nb = 0) {
     Geom g;
     g.NB = dir_nb;
+    g.ADJ = 0;
     const int pairs = (M + 1) / 2;
     const int ns_need = (F + KT - 1) / KT;
     g.TP = std::max(1, std::min(pairs, tp_max));

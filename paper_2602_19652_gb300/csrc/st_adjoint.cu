@@ -39,23 +39,71 @@ __device__ __forceinline__ u64 fsub2(u64 a, u64 b) {
 
 constexpr int kNV = 4;  // materials whose reflection gradient one launch accumulates
 
-template <int KT, int KIND>
-__global__ void __launch_bounds__(256) k_adjoint(const AccumArgs a, const AdjointArgs j, const Geom g) {
+// Reduce-scatter of 8 per-bin values over the TP = 2^TPL lanes of a microphone-pair group (TP
+// consecutive lanes share a subtile): after it, v[0 .. VR) of lane tp hold the group's sums for bins
+// rs_first<TPL>(tp) .. + VR.  Fixed order, so the result does not depend on scheduling.
+template <int TPL>
+struct RS {
+    static constexpr int L = TPL < 3 ? TPL : 3;  // halving steps
+    static constexpr int VR = 8 >> L;            // values kept per lane
+};
+template <int TPL>
+__device__ __forceinline__ int rs_first(int tp) {
+    int off = 0, n = 8;
+#pragma unroll
+    for (int i = 0; i < RS<TPL>::L; ++i) {
+        const int h = (1 << TPL) >> (i + 1);
+        n >>= 1;
+        if (tp & h) off += n;
+    }
+    return off;
+}
+template <int TPL>
+__device__ __forceinline__ void rs_reduce(float (&v)[8], int tp, unsigned wm) {
+    int n = 8;
+#pragma unroll
+    for (int i = 0; i < RS<TPL>::L; ++i) {
+        const int h = (1 << TPL) >> (i + 1);
+        n >>= 1;
+        const bool up = (tp & h) != 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (q < n) {
+                const float keep = up ? v[n + q] : v[q];
+                const float send = up ? v[q] : v[n + q];
+                v[q] = keep + __shfl_xor_sync(wm, send, h);
+            }
+        }
+    }
+    if (TPL >= 4) v[0] += __shfl_xor_sync(wm, v[0], 1);  // 16 lanes: tp and tp ^ 1 end with the same sum
+}
+
+// One CTA: MP = 2 TP microphones x KB bins, a chunk of the path list in tiles of PT paths (the
+// forward's software pipeline: the next tile's tables are produced while this tile's terms are
+// reversed; one barrier per tile).  Thread (s, tp) holds G of its two microphones and KT bins and,
+// per path, folds its subtile's share of the position gradients into registers (the derivative of
+// the path length and of the lobe angle are linear in the per-subtile sums C0, C1, Cg), and its
+// share of the reflection sums V into kNV x VR registers after a reduce-scatter over the pair lanes.
+template <int KT, int KIND, int TPL>
+__global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
+    k_adjoint(const AccumArgs a, const AdjointArgs j, const Geom g) {
+    static_assert(KT == 8, "the reduce-scatter of the reflection sums takes 8 bins per thread");
+    constexpr int VR = RS<TPL>::VR;
     extern __shared__ float4 smem4[];
-    const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
+    const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB;
     const Buf B0 = buf_at<KT>(smem4, g, 0), B1 = buf_at<KT>(smem4, g, 1);
-    // after the two pipeline buffers: pd [3][PT][12], pv [3][PT], Cbuf [PT][NS][MP][5], Gbuf [PT][MP][6], mt
+    // after the two pipeline buffers: pd [3][PT][12], pv [3][PT], material tables
     float* pdb = reinterpret_cast<float*>(reinterpret_cast<char*>(smem4) + 2 * g.buf_bytes);
     int* pvb = reinterpret_cast<int*>(pdb + 3 * PT * 12);
-    float* cbuf = reinterpret_cast<float*>(pvb + 3 * PT);
-    float* gbuf = cbuf + (size_t)PT * NS * MP * 5;
-    float* mt = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(gbuf + (size_t)PT * MP * 6) + 15) & ~uintptr_t(15));
+    float* mt = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(pvb + 3 * PT) + 15) & ~uintptr_t(15));
 
     const int mb = blockIdx.x % g.n_mb, bb = blockIdx.x / g.n_mb;
-    const int mic0 = mb * MP, kb = bb * KB;
+    const int mic0 = mb * g.MP, kb = bb * KB;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int tp = tid % TP, s = tid / TP;
+    // lanes of this warp that exist (the last warp of a small CTA is partial; TP divides 32)
+    const int wbase = tid & ~31;
+    const unsigned wm = nthr - wbase >= 32 ? 0xffffffffu : ((1u << (nthr - wbase)) - 1u);
 
     const int64_t count = (int64_t)*a.d_count;
     const int64_t n_tiles = (count + PT - 1) / PT;
@@ -78,12 +126,18 @@ __global__ void __launch_bounds__(256) k_adjoint(const AccumArgs a, const Adjoin
             Gi[kk] = pk2(g1.y, g2.y);
         }
     }
-    float V[kNV][KT];
+    float V[kNV][VR];
 #pragma unroll
     for (int q = 0; q < kNV; ++q)
 #pragma unroll
-        for (int kk = 0; kk < KT; ++kk) V[q][kk] = 0.0f;
-    float dm[3] = {0.f, 0.f, 0.f}, de[3] = {0.f, 0.f, 0.f};  // thread tid < MP: mic mic0 + tid
+        for (int v = 0; v < VR; ++v) V[q][v] = 0.0f;
+    // position gradients of the thread's two microphones (and the emitter, diffraction), packed
+    u64 dmx = 0ull, dmy = 0ull, dmz = 0ull, dex = 0ull, dey = 0ull, dez = 0ull;
+    // d ln T / dr at this subtile's first bin, without the -2/r spreading term: (-a, w); per bin: (-a_step, w_step)
+    const float kbs = (float)(kb + s * KT);
+    const float ars = -(j.a_0 + j.a_step * kbs), nais = -(j.w_0 + j.w_step * kbs);
+    const u64 ArS = pk2(ars, ars), nAiS = pk2(nais, nais);
+    const u64 D1r = pk2(-j.a_step, -j.a_step), nD1i = pk2(-j.w_step, -j.w_step);
 
     const float invNS = 1.0f / (float)NS, invKB = 1.0f / (float)KB;
     if (t0 < t1) {
@@ -104,7 +158,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const AccumArgs a, const Adjoin
         load_paths<KIND>(a, PT, t0 * PT, count, pdb, pvb);
         if (t0 + 1 < t1) load_paths<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
         __syncthreads();
-        produce<KT, KIND>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB);
+        produce<KT, KIND, 1>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, j.s);
         __syncthreads();
     }
     for (int64_t tile = t0; tile < t1; ++tile) {
@@ -112,12 +166,11 @@ __global__ void __launch_bounds__(256) k_adjoint(const AccumArgs a, const Adjoin
         const int pb = (int)((tile - t0) % 3);  // path data of this tile
         const Buf& C = b ? B1 : B0;
         const Buf& Pn = b ? B0 : B1;
-        float* pd = pdb + pb * PT * 12;
+        const float* pd = pdb + pb * PT * 12;
         const int* pv = pvb + pb * PT;
-        // ---- A: tables of the next tile; reverse terms of this tile
         if (tile + 1 < t1) {
             const int nb = (int)((tile + 1 - t0) % 3);
-            produce<KT, KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB);
+            produce<KT, KIND, 1>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, j.s);
         }
         for (int p = 0; p < PT; ++p) {
             const ulonglong2 z0 = C.za[((size_t)p * NS + s) * TP + tp];
@@ -153,22 +206,42 @@ __global__ void __launch_bounds__(256) k_adjoint(const AccumArgs a, const Adjoin
                 y[kk] = wr2.x + wr2.y;
                 if (kk & 1) cmul2(orr, oi, w2r, w2i, nw2i); else cmul2(er, ei, w2r, w2i, nw2i);
             }
-            // per (path, subtile, mic) partial sums for the position gradients
             if (j.do_pos) {
-                const float2 C0r = up2(c0r), C0i = up2(c0i), Qr = up2(qr), Qi = up2(qi), Cg = up2(cg);
-                float* cb = cbuf + (((size_t)p * NS + s) * MP + 2 * tp) * 5;
-                cb[0] = C0r.x; cb[1] = C0i.x; cb[2] = KT * C0r.x - Qr.x; cb[3] = KT * C0i.x - Qi.x; cb[4] = Cg.x;
-                cb[5] = C0r.y; cb[6] = C0i.y; cb[7] = KT * C0r.y - Qr.y; cb[8] = KT * C0i.y - Qi.y; cb[9] = Cg.y;
+                const u64* ad = C.adj + ((size_t)p * TP + tp) * 7;
+                // C1 relative to the subtile's first bin
+                const u64 q1r = fsub2(fmul2(pk2((float)KT, (float)KT), c0r), qr);
+                const u64 q1i = fsub2(fmul2(pk2((float)KT, (float)KT), c0i), qi);
+                const u64 d0r = ffma2(pk2(-2.0f, -2.0f), ad[6], ArS);  // -2/r - a(kb_s)
+                // dL/dr share: Re(D0 C0 + D1 C1), D0 = d0r + j w(kb_s), D1 = -a_step + j w_step
+                u64 dl = fmul2(d0r, c0r);
+                dl = ffma2(nAiS, c0i, dl);
+                dl = ffma2(D1r, q1r, dl);
+                dl = ffma2(nD1i, q1i, dl);
+                dmx = ffma2(dl, ad[0], dmx);
+                dmy = ffma2(dl, ad[1], dmy);
+                dmz = ffma2(dl, ad[2], dmz);
+                if (KIND == 0) {  // lobe angle
+                    dmx = ffma2(cg, ad[3], dmx);
+                    dmy = ffma2(cg, ad[4], dmy);
+                    dmz = ffma2(cg, ad[5], dmz);
+                } else {  // emitter: dr/ds = -unit(o - s)
+                    dex = ffma2(dl, ad[3], dex);
+                    dey = ffma2(dl, ad[4], dey);
+                    dez = ffma2(dl, ad[5], dez);
+                }
             }
             // reflection-coefficient sums for the materials of the path's chain
             if (KIND == 0 && j.do_k && pv[p]) {
+                rs_reduce<TPL>(y, tp, wm);
                 const uint32_t meta = __float_as_uint(pd[p * 12 + 8]);
                 const int len = meta & 15, matj = (meta >> 8) & 255;
                 const uint32_t c0 = __float_as_uint(pd[p * 12 + 9]), c1 = __float_as_uint(pd[p * 12 + 10]);
                 float cnt[kNV] = {0.f, 0.f, 0.f, 0.f};
                 if (a.reflection_mode == 1) {
                     const int q = matj - j.mat_base;
-                    if (q >= 0 && q < kNV) cnt[q] = 1.0f;
+#pragma unroll
+                    for (int u = 0; u < kNV; ++u)
+                        if (q == u) cnt[u] = 1.0f;
                 } else {
                     for (int q = 0; q < len; ++q) {
                         const int mq = ((q < 4 ? (c0 >> (8 * q)) : (c1 >> (8 * (q - 4)))) & 255) - j.mat_base;
@@ -179,67 +252,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const AccumArgs a, const Adjoin
                 }
 #pragma unroll
                 for (int u = 0; u < kNV; ++u)
-                    if (cnt[u] != 0.0f) {
 #pragma unroll
-                        for (int kk = 0; kk < KT; ++kk) V[u][kk] = fmaf(cnt[u], y[kk], V[u][kk]);
-                    }
-            }
-        }
-        __syncthreads();
-        // ---- B: per (path, mic) gradient contributions; path data of tile + 2
-        if (j.do_pos) {
-            for (int e = tid; e < PT * MP; e += nthr) {
-                const int p = e / MP, ml = e - p * MP;
-                const int m = mic0 + ml;
-                float* gb = gbuf + ((size_t)p * MP + ml) * 6;
-                gb[0] = gb[1] = gb[2] = gb[3] = gb[4] = gb[5] = 0.0f;
-                if (!pv[p] || m >= a.M) continue;
-                // sums over the subtiles; C1 relative to kb
-                float c0r = 0.f, c0i = 0.f, c1r = 0.f, c1i = 0.f, cgs = 0.f;
-                for (int s_ = 0; s_ < NS; ++s_) {
-                    const float* cb = cbuf + (((size_t)p * NS + s_) * MP + ml) * 5;
-                    const float off = (float)(s_ * KT);
-                    c0r += cb[0];
-                    c0i += cb[1];
-                    c1r += cb[2] + off * cb[0];
-                    c1i += cb[3] + off * cb[1];
-                    cgs += cb[4];
-                }
-                const float* d = pd + p * 12;
-                const float mx = a.mics[3 * m], my = a.mics[3 * m + 1], mz = a.mics[3 * m + 2];
-                const ff dist = dist_ff(mx, my, mz, d[0], d[1], d[2]);
-                const ff rr = ff_add(ff{d[6], d[7]}, dist);
-                const float r = rr.hi, inv = 1.0f / dist.hi;
-                const float ux = (mx - d[0]) * inv, uy = (my - d[1]) * inv, uz = (mz - d[2]) * inv;
-                // dL/dr = Re(D0 C0 + D1 C1)
-                const float d0r = -2.0f / r - (j.a_0 + j.a_step * (float)kb), d0i = j.w_0 + j.w_step * (float)kb;
-                const float d1r = -j.a_step, d1i = j.w_step;
-                const float dLdr = (d0r * c0r - d0i * c0i) + (d1r * c1r - d1i * c1i);
-                float gx = dLdr * ux, gy = dLdr * uy, gz = dLdr * uz;
-                if (KIND == 0) {
-                    const float dx = d[3], dy = d[4], dz = d[5];
-                    const float cg = dx * ux + dy * uy + dz * uz;
-                    const float cx = dy * uz - dz * uy, cy = dz * ux - dx * uz, cz = dx * uy - dy * ux;
-                    const float sg = sqrtf(cx * cx + cy * cy + cz * cz);
-                    const float gm = atan2f(sg, cg);
-                    const float dLdg = -2.0f * gm * 0.69314718055994531f * cgs;
-                    if (sg > 1e-20f) {
-                        const float f = -dLdg / (dist.hi * sg);
-                        gx += f * (dx - cg * ux);
-                        gy += f * (dy - cg * uy);
-                        gz += f * (dz - cg * uz);
-                    }
-                } else {
-                    // dr/ds = -unit(o - s)
-                    const float vx = d[0] - j.s[0], vy = d[1] - j.s[1], vz = d[2] - j.s[2];
-                    const float iv = 1.0f / d[6];
-                    gb[3] = -dLdr * vx * iv;
-                    gb[4] = -dLdr * vy * iv;
-                    gb[5] = -dLdr * vz * iv;
-                }
-                gb[0] = gx;
-                gb[1] = gy;
-                gb[2] = gz;
+                    for (int v = 0; v < VR; ++v) V[u][v] = fmaf(cnt[u], y[v], V[u][v]);
             }
         }
         if (tile + 2 < t1) {
@@ -247,57 +261,54 @@ __global__ void __launch_bounds__(256) k_adjoint(const AccumArgs a, const Adjoin
             load_paths<KIND>(a, PT, (tile + 2) * PT, count, pdb + nb2 * PT * 12, pvb + nb2 * PT);
         }
         __syncthreads();
-        // ---- C: each microphone's thread accumulates its contributions in path order
-        if (j.do_pos && tid < MP) {
-            for (int p = 0; p < PT; ++p) {
-                const float* gb = gbuf + ((size_t)p * MP + tid) * 6;
-                for (int c = 0; c < 3; ++c) {
-                    dm[c] += gb[c];
-                    de[c] += gb[3 + c];
-                }
-            }
-        }
     }
-    // ---- outputs of this CTA
+    // ---- outputs of this CTA (shared memory reused)
     const int cta = blockIdx.y * gridDim.x + blockIdx.x;
     if (j.do_pos) {
-        if (tid < MP && mic0 + tid < a.M) {
+        float* red = reinterpret_cast<float*>(smem4);  // [NS][TP][2][3] microphones, then [nthr][3] emitter
+        float* rede = red + (size_t)nthr * 6;
+        __syncthreads();
+        {
+            const float2 x = up2(dmx), y2 = up2(dmy), z = up2(dmz);
+            float* o = red + (size_t)tid * 6;
+            o[0] = x.x; o[1] = y2.x; o[2] = z.x;
+            o[3] = x.y; o[4] = y2.y; o[5] = z.y;
+            const float2 ex = up2(dex), ey = up2(dey), ez = up2(dez);
+            rede[tid * 3 + 0] = ex.x + ex.y;
+            rede[tid * 3 + 1] = ey.x + ey.y;
+            rede[tid * 3 + 2] = ez.x + ez.y;
+        }
+        __syncthreads();
+        if (tid < g.MP && mic0 + tid < a.M) {  // microphone mic0 + tid: fixed-order sum over the subtiles
+            const int pair = tid >> 1, half = tid & 1;
+            float acc[3] = {0.f, 0.f, 0.f};
+            for (int s_ = 0; s_ < NS; ++s_) {
+                const float* r = red + ((size_t)s_ * TP + pair) * 6 + 3 * half;
+                acc[0] += r[0];
+                acc[1] += r[1];
+                acc[2] += r[2];
+            }
             float* o = j.mic_part + ((size_t)(blockIdx.y * g.n_bb + bb) * a.M + mic0 + tid) * 3;
-            o[0] = dm[0];
-            o[1] = dm[1];
-            o[2] = dm[2];
+            o[0] = acc[0];
+            o[1] = acc[1];
+            o[2] = acc[2];
         }
-        __syncthreads();
-        // emitter: fixed-order sum over the CTA's microphones
-        float* red = cbuf;
-        if (tid < MP) {
-            red[tid * 3 + 0] = de[0];
-            red[tid * 3 + 1] = de[1];
-            red[tid * 3 + 2] = de[2];
-        }
-        __syncthreads();
         if (tid < 3) {
             float acc = 0.0f;
-            for (int ml = 0; ml < MP; ++ml) acc += red[ml * 3 + tid];
+            for (int t = 0; t < nthr; ++t) acc += rede[t * 3 + tid];
             j.emit_part[(size_t)cta * 3 + tid] = acc;
         }
-        __syncthreads();
     }
     if (KIND == 0 && j.do_k) {
-        // V of the CTA's bins: fixed-order sum over the thread's microphone pairs
-        float* vt = reinterpret_cast<float*>(smem4);  // [kNV][KT][NS][TP]
+        // each bin's sum sits in one lane (two identical lanes with 16 pairs: the even one writes)
+        const bool writer = TPL >= 4 ? (tp & 1) == 0 : true;
+        const int k0 = kb + s * KT + rs_first<TPL>(tp);
+        if (writer) {
 #pragma unroll
-        for (int u = 0; u < kNV; ++u)
+            for (int u = 0; u < kNV; ++u)
 #pragma unroll
-            for (int kk = 0; kk < KT; ++kk) vt[(((size_t)u * KT + kk) * NS + s) * TP + tp] = V[u][kk];
-        __syncthreads();
-        for (int e = tid; e < kNV * KB; e += nthr) {
-            const int u = e / KB, i = e - u * KB;
-            const int kk = i / NS, s_ = i - kk * NS;
-            const int k = kb + s_ * KT + kk;
-            float acc = 0.0f;
-            for (int q = 0; q < TP; ++q) acc += vt[(((size_t)u * KT + kk) * NS + s_) * TP + q];
-            if (k < a.F) j.v_part[((size_t)(blockIdx.y * g.n_mb + mb) * kNV + u) * a.F + k] = acc;
+                for (int v = 0; v < VR; ++v)
+                    if (k0 + v < a.F) j.v_part[((size_t)(blockIdx.y * g.n_mb + mb) * kNV + u) * a.F + k0 + v] = V[u][v];
         }
     }
 }
@@ -349,15 +360,18 @@ __global__ void k_v_reduce(float* v_part, int n_slices, int F) {
     v_part[idx] = acc;
 }
 
-// dk[mat][b] = sum_k V[mat][k] w_b(k) / k(mat, f_k) over the bins whose interpolation uses band b
-__global__ void k_dk_contract(const float* V, int F, int mat_base, int n_mat_launch, int n_bands,
-                              const float* band_hz, const float* kb_tab, double f_lo, double df, float* dk) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_mat_launch * n_bands) return;
-    const int u = idx / n_bands, b = idx % n_bands;
+// dk[mat][b] = sum_k V[mat][k] w_b(k) / k(mat, f_k) over the bins whose interpolation uses band b.
+// One block per (material, band); threads stride over the bins in float64, then a fixed-order tree sum.
+constexpr int kDkThreads = 128;
+__global__ void __launch_bounds__(kDkThreads) k_dk_contract(const float* V, int F, int mat_base, int n_bands,
+                                                           const float* band_hz, const float* kb_tab, double f_lo,
+                                                           double df, float* dk) {
+    __shared__ double red[kDkThreads];
+    const int u = blockIdx.x / n_bands, b = blockIdx.x % n_bands;
     const int mat = mat_base + u;
+    const float* kr = kb_tab + (size_t)mat * n_bands;
     double acc = 0.0;
-    for (int k = 0; k < F; ++k) {
+    for (int k = threadIdx.x; k < F; k += kDkThreads) {
         const double v = (double)V[(size_t)u * F + k];
         if (v == 0.0) continue;
         const double f = F == 1 ? f_lo : f_lo + (double)k * df;
@@ -371,8 +385,12 @@ __global__ void k_dk_contract(const float* V, int F, int mat_base, int n_mat_lau
                 b0 = n_bands - 2;
                 w = 1.0;
             } else {
-                while (b0 + 1 < n_bands && (double)band_hz[b0 + 1] <= f) ++b0;
-                if (b0 >= n_bands - 1) b0 = n_bands - 2;
+                int lo = 0, hi = n_bands - 1;  // last band centre <= f
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((double)band_hz[mid] <= f) lo = mid; else hi = mid;
+                }
+                b0 = lo;
                 w = (f - (double)band_hz[b0]) / ((double)band_hz[b0 + 1] - (double)band_hz[b0]);
             }
         }
@@ -381,12 +399,17 @@ __global__ void k_dk_contract(const float* V, int F, int mat_base, int n_mat_lau
         else if (b == b0) wb = 1.0 - w;
         else if (b == b0 + 1) wb = w;
         if (wb == 0.0) continue;
-        const float* kr = kb_tab + (size_t)mat * n_bands;
         const double kv = n_bands == 1 ? (double)kr[0] : (1.0 - w) * (double)kr[b0] + w * (double)kr[b0 + 1];
         if (!(kv > 0.0)) continue;
         acc += v * wb / kv;
     }
-    dk[(size_t)mat * n_bands + b] = (float)acc;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kDkThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dk[(size_t)mat * n_bands + b] = (float)red[0];
 }
 
 // positions: dmic[m] = sum of all partial slices in order; demit = sum of emitter slices in order
@@ -405,37 +428,52 @@ __global__ void k_pos_reduce(const float* mic_parts, int n_mic_slices, const flo
     }
 }
 
-template <int KT, int KIND>
+template <int KT, int KIND, int TPL>
 cudaError_t launch_adjoint(const AccumArgs& a, const AdjointArgs& j, const Geom& g, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_adjoint<KT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_adjoint<KT, KIND, TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((unsigned)(g.n_mb * g.n_bb), (unsigned)a.n_chunks);
     note_launch();
-    k_adjoint<KT, KIND><<<grid, g.TP * g.NS, adjoint_smem(g), s>>>(a, j, g);
+    k_adjoint<KT, KIND, TPL><<<grid, g.TP * g.NS, g.smem, s>>>(a, j, g);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+namespace {
+
+size_t adjoint_per_path(const acc::Geom& g) {
+    return (size_t)g.KB * 16 + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40 + (size_t)g.TP * 56;
+}
+
+}  // namespace
+
 size_t adjoint_smem(const acc::Geom& g) {
-    const size_t extra = 3 * (size_t)g.PT * 52 + (size_t)g.PT * g.NS * g.MP * 20 + (size_t)g.PT * g.MP * 24 + 16;
-    const size_t vt = (size_t)kNV * g.KB * g.TP * 4;  // end-of-kernel reduction reuses the start of shared memory
-    const size_t total = 2 * g.buf_bytes + extra + (g.mat_cached ? g.mat_bytes : 0) + 64;
-    return std::max(total, vt + 64);
+    const size_t total = 2 * g.buf_bytes + 3 * (size_t)g.PT * 52 + 16 + (g.mat_cached ? g.mat_bytes : 0) + 64;
+    const size_t red = (size_t)g.TP * g.NS * 9 * 4 + 64;  // end-of-kernel reductions reuse the start
+    return std::max(total, red);
 }
 
 acc::Geom adjoint_geom(int M, int F, int n_mat) {
-    // tile shape of the forward (8 bins per thread, 16 microphone pairs per CTA); paths per tile chosen
-    // so the pipeline buffers plus the reduction buffers fit about 96 KB
+    // tile shape of the forward with 8 bins per thread and up to 16 microphone pairs per CTA, the pair
+    // count a power of two (the reflection sums are reduce-scattered across the pair lanes); paths
+    // per tile as many as fit about 100 KB, so that two CTAs share an SM
     acc::Geom g = acc::make_geom(M, F, 8, n_mat, 16, 200 * 1024);
-    const size_t per_path = (size_t)g.KB * 16 + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40;
-    const size_t per_tile = 2 * per_path + 3 * 52 + (size_t)g.NS * g.MP * 20 + (size_t)g.MP * 24;
-    const size_t fixed = (g.mat_cached ? g.mat_bytes : 0) + 16 + 64 + 256;
-    const size_t budget = 96 * 1024;
+    int tp2 = 1;
+    while (tp2 * 2 <= g.TP) tp2 *= 2;
+    g.TP = tp2;
+    g.MP = 2 * tp2;
+    g.n_mb = (M + g.MP - 1) / g.MP;
+    g.ADJ = 1;
+    const size_t per_path = adjoint_per_path(g);
+    const size_t per_tile = 2 * per_path + 3 * 52;
+    const size_t fixed = (g.mat_cached ? g.mat_bytes : 0) + 16 + 64 + 512;
+    const size_t budget = 100 * 1024;
     g.PT = (int)std::max<size_t>(1, std::min<size_t>(8, budget > fixed ? (budget - fixed) / per_tile : 1));
     g.buf_bytes = (per_path * g.PT + 255) & ~size_t(255);
     g.smem = adjoint_smem(g);
@@ -443,7 +481,14 @@ acc::Geom adjoint_geom(int M, int F, int n_mat) {
 }
 
 cudaError_t adjoint_launch(const AccumArgs& a, const AdjointArgs& j, const acc::Geom& g, cudaStream_t s) {
-    return a.kind == 0 ? launch_adjoint<8, 0>(a, j, g, s) : launch_adjoint<8, 1>(a, j, g, s);
+    if (a.kind == 1) return launch_adjoint<8, 1, 0>(a, j, g, s);
+    switch (g.TP) {
+        case 1: return launch_adjoint<8, 0, 0>(a, j, g, s);
+        case 2: return launch_adjoint<8, 0, 1>(a, j, g, s);
+        case 4: return launch_adjoint<8, 0, 2>(a, j, g, s);
+        case 8: return launch_adjoint<8, 0, 3>(a, j, g, s);
+        default: return launch_adjoint<8, 0, 4>(a, j, g, s);
+    }
 }
 
 cudaError_t adjoint_direct(const DirectAccumArgs& a, const float* qhi, const float* qlo, const float2* G,
@@ -466,7 +511,7 @@ cudaError_t adjoint_dk(const float* v_part, int n_slices, int F, int mat_base, i
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     note_launch();
-    k_dk_contract<<<(n + 63) / 64, 64, 0, s>>>(v, F, mat_base, n_mat_launch, n_bands, band_hz_dev, k_dev, f_lo, df, dk);
+    k_dk_contract<<<n, kDkThreads, 0, s>>>(v, F, mat_base, n_bands, band_hz_dev, k_dev, f_lo, df, dk);
     return cudaGetLastError();
 }
 

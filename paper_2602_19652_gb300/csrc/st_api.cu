@@ -993,11 +993,8 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
 
     const acc::Geom g = adjoint_geom(M, F, T.n_mat);
     const int ctas = g.n_mb * g.n_bb;
-    // path counts of the last simulate size the chunking (one small read-back)
-    uint32_t hc[4] = {0, 0, 0, 0};
-    CKC(c, cudaMemcpyAsync(hc, cnt, 16, cudaMemcpyDeviceToHost, s), "backward counts");
-    CKC(c, cudaStreamSynchronize(s), "backward counts");
-    const int64_t n_paths = std::max<int64_t>(hc[2], hc[3]);
+    // chunking from the path lists' capacities (the counts stay on the device: no synchronisation)
+    const int64_t n_paths = std::max<int64_t>(c->last_N * c->last_B, c->last_K);
     const int64_t tiles = std::max<int64_t>(1, (n_paths + g.PT - 1) / g.PT);
     const int32_t chunks = (int32_t)std::max<int64_t>(
         1, std::min<int64_t>(152 / std::max(ctas, 1) * 2, (tiles + 7) / 8));
