@@ -273,6 +273,73 @@ def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 
             "max_rel_l2_batched_vs_plain": err, "first_call_s": first_call_s}
 
 
+def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2):
+    """Device time of one simulate on another workload (scene prebuilt, L2 flushed before each step)."""
+    dev = torch.cuda.current_device()
+    ctx = st.Context(dev)
+    sc = st.from_workload(ctx, wl)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    out = torch.empty((3, len(wl.mics), wl.n_bins), dtype=torch.complex64, device=f"cuda:{dev}")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.simulate(sc, p, out=out)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ms, segs, stats = [], 0, None
+    for i in range(steps):
+        flush.fill_(i & 255)
+        ev[0].record(stream)
+        _, stats = ctx.simulate(sc, p, out=out, stats=True)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+        segs += stats.closest_queries + stats.shadow_queries
+    t = float(sum(ms))
+    res = {"config": f"{wl.name}: {wl.n_tris} triangles, {len(wl.dirs)} rays x {wl.bounces} bounces, "
+                     f"{len(wl.mics)} mics, {wl.n_bins} bins, diffraction {'on' if wl.diffraction else 'off'}",
+           "value": segs / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_step": t / steps,
+           "mic_spectra_per_s": len(wl.mics) * steps / (t / 1e3),
+           "ms_trace": stats.ms_trace, "ms_diffraction": stats.ms_diffraction, "ms_accumulate": stats.ms_accumulate,
+           "visible_records": stats.visible_records, "diffraction_kept": stats.candidates_kept}
+    ctx.close()
+    return res
+
+
+def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm_gbs: float):
+    """BVH fetch bandwidth of the tracing kernels: nodes (64 B) and leaf triangles (48 B) visited,
+    counted in a separate instrumented run (ST_COUNT_VISITS), divided by the uninstrumented kernel
+    times of the headline steps.  The fetches are served mostly by L1/L2 (the node array of the
+    benchmark scene fits in L2), so the ratio to the HBM copy bandwidth can exceed 1."""
+    dev = torch.cuda.current_device()
+    os.environ["ST_COUNT_VISITS"] = "1"
+    try:
+        ctx = st.Context(dev)
+    finally:
+        del os.environ["ST_COUNT_VISITS"]
+    sc = st.from_workload(ctx, wl)
+    p_spec = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance, components=st.ST_COMP_SPECULAR)
+    p_all = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    _, s_spec = ctx.simulate(sc, p_spec, stats=True)
+    _, s_all = ctx.simulate(sc, p_all, stats=True)
+    torch.cuda.synchronize()
+    vs = list(s_spec.visits)
+    va = list(s_all.visits)
+    vd = [a - b for a, b in zip(va, vs)]  # diffraction filters and the direct path (any-hit only)
+    bt = 64 * (vs[0] + vs[2]) + 48 * (vs[1] + vs[3])
+    bd = 64 * (vd[0] + vd[2]) + 48 * (vd[1] + vd[3])
+    ctx.close()
+    q_t = s_spec.closest_queries + s_spec.shadow_queries
+    q_d = (s_all.shadow_queries - s_spec.shadow_queries)
+    return {"bytes_per_node": 64, "bytes_per_triangle": 48, "hbm_peak_gbs": hbm_gbs,
+            "k_bounce": {"queries": int(q_t), "nodes": int(vs[0] + vs[2]), "triangles": int(vs[1] + vs[3]),
+                         "nodes_per_query": (vs[0] + vs[2]) / max(q_t, 1), "ms": ms_trace,
+                         "fetch_gbs": bt / (ms_trace / 1e3) / 1e9, "frac_of_hbm": bt / (ms_trace / 1e3) / 1e9 / hbm_gbs},
+            "k_diffraction": {"queries": int(q_d), "nodes": int(vd[0] + vd[2]), "triangles": int(vd[1] + vd[3]),
+                              "nodes_per_query": (vd[0] + vd[2]) / max(q_d, 1), "ms": ms_diffraction,
+                              "fetch_gbs": bd / (ms_diffraction / 1e3) / 1e9,
+                              "frac_of_hbm": bd / (ms_diffraction / 1e3) / 1e9 / hbm_gbs}}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -309,6 +376,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain pose sweep")
+    ap.add_argument("--no-vegetation", action="store_true", help="skip the full-size vegetation simulate timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -391,6 +459,9 @@ def main():
                         f"terms per launch", "ms_per_launch": acc_ms / max(acc_launches, 1),
                 "traffic": ACCUM_DRAM_BYTES_PER_LAUNCH}
 
+    traversal = measure_traversal(st, torch, wl, float(np.median([s.ms_trace for s in st_list])),
+                                  float(np.median([s.ms_diffraction for s in st_list])), peaks["hbm_gbs"])
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if rank == 0 or world > 1:
@@ -435,6 +506,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = measure_batched(st, torch)
+    vegetation = None
+    if not args.no_vegetation and args.workload != "vegetation":
+        vegetation = measure_workload(st, torch, synth.vegetation(seed=303))
 
     if rank != 0:
         if world > 1:
@@ -459,7 +533,7 @@ def main():
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
                          "ms_accumulate": s0.ms_accumulate},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
-            "batched": batched,
+            "traversal": traversal, "batched": batched, "vegetation": vegetation,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
     print(json.dumps(line))
     if world > 1:

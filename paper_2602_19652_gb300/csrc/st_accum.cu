@@ -477,6 +477,7 @@ __global__ void k_gather_diff_batch(const BatchArgs a, const uint32_t* idx, cons
 
 int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb, int32_t tile_tp,
                      int32_t tile_kb) {
+    if (narrow_accum(M)) return narrow_chunks(n_paths_hint, M, F, n_mat, dir_nb);
     read_tile_env();
     const int tp = tile_tp > 0 ? tile_tp : g_tile_tp;
     const size_t budget = tile_kb > 0 ? (size_t)tile_kb * 1024 : g_tile_budget;
@@ -543,6 +544,7 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
 }
 
 cudaError_t accumulate(const AccumArgs& a, cudaStream_t s) {
+    if (narrow_accum(a.M)) return accumulate_narrow(a, s);
     read_tile_env();
     if (a.mic_tab) return a.kind == 0 ? launch_accum<16, 0, 1>(a, s) : launch_accum<16, 1, 1>(a, s);
     if (g_tile_kt == 8) return a.kind == 0 ? launch_accum<8, 0, 0>(a, s) : launch_accum<8, 1, 0>(a, s);

@@ -247,6 +247,10 @@ cudaError_t accumulate(const AccumArgs& a, cudaStream_t s);
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s);
 int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb, int32_t tile_tp = 0,
                      int32_t tile_kb = 0);
+// narrow receiver arrays (one microphone pair): a separate accumulator kernel
+bool narrow_accum(int32_t M);
+int32_t narrow_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb);
+cudaError_t accumulate_narrow(const AccumArgs& a, cudaStream_t s);
 
 struct GatherArgs {
     // specular

@@ -148,3 +148,15 @@ def test_vegetation_directivity_parity(st):
     assert 0 < keep.sum() < len(keep)
     for c in range(3):
         assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
+
+
+@pytest.mark.parametrize("M,F,mode", [(2, 1, 0), (1, 17, 0), (2, 1000, 0), (2, 1000, 1), (2, 2048, 0), (1, 4100, 0)])
+def test_narrow_arrays(st, M, F, mode):
+    """One microphone pair (the narrow-array accumulator): bin counts from 1 to beyond one CTA's
+    4096 bins, both reflection modes, diffraction on."""
+    import oracle
+    wl = small_clutter(target_tris=5000, n_rays=3000, n_mics=M, n_bins=F, bounces=4)
+    ctx, sc, S, _ = gpu_run(st, wl, curv=st.curv_params(sample_budget=20_000), reflection_mode=mode)
+    o = oracle.simulate(wl, curv=dict(budget=20_000), reflection_mode=mode)
+    for c in range(3):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, (M, F, mode, c, rel_l2(S[c], o["spectra"][c]))
