@@ -234,15 +234,15 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
             for (int kk = 0; kk < kNKT; ++kk) {
                 const int i = s + NS * kk;
                 const int k = kb + i;
-                float lx;
+                float lx, de = 1.0f;
                 if (k < a.F) {
                     lx = lkp[off[0] + i];
 #pragma unroll
                     for (int u = 1; u < kMaxBounces; ++u)
                         if (u < len) lx += lkp[off[u] + i];
-                    if (e0) {
-                        const float de = (1.0f - ew) * e0[k] + ew * e0[a.F + k];
-                        lx += de > 0.0f ? log2f(de) : kNegInf;
+                    if (e0) {  // emitter directivity, a factor of the amplitude (zero where the table is)
+                        de = (1.0f - ew) * __ldg(e0 + k) + ew * __ldg(e0 + a.F + k);
+                        de = fmaxf(de, 0.0f);
                     }
                 } else {
                     lx = kNegInf;
@@ -264,7 +264,9 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
                         D1 = fmaf(bwv.y, d1[b0 + 1] - D1, D1);
                         D2 = fmaf(bwv.y, d2[b0 + 1] - D2, D2);
                     }
-                    E = fmul2(E, pk2(D1, D2));
+                    E = fmul2(E, pk2(D1 * de, D2 * de));
+                } else if (e0) {
+                    E = fmul2(E, pk2(de, de));
                 }
                 if ((kk & 1) == 0) {
                     Sr[kk] = ffma2(E, er, Sr[kk]);
