@@ -35,8 +35,9 @@ METRIC = "Mrays/s (closest-hit + any-hit segments per second, spectra at <=1e-4 
 UNIT = "Mrays/s"
 FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by-complex multiply-accumulate (4)
 # dram__bytes_read.sum + dram__bytes_write.sum per k_accum launch on this workload, from an ncu capture of the
-# current kernel; set to None when the kernel changes until it is captured again
-ACCUM_DRAM_BYTES_PER_LAUNCH = 34.69e6
+# current kernel (the diffraction launch at full size, the specular launch on 200k rays scaled by the visible
+# records: the path list is read once); set to None when the kernel changes until it is captured again
+ACCUM_DRAM_BYTES_PER_LAUNCH = 34.81e6
 
 
 def load_peaks():
@@ -340,6 +341,31 @@ def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm
                               "frac_of_hbm": bd / (ms_diffraction / 1e3) / 1e9 / hbm_gbs}}
 
 
+def run_case(st, torch, case: str, reps: int):
+    """Small cases of single kernels for profiling (ncu captures): no timing output."""
+    dev = torch.cuda.current_device()
+    if case in ("accum", "adjoint", "trace"):
+        wl = synth.clutter(seed=202, n_rays=200_000)
+    elif case == "narrow":
+        wl = synth.vegetation(seed=303, n_rays=500_000)
+    else:
+        raise SystemExit(f"unknown case {case}")
+    ctx = st.Context(dev)
+    sc = st.from_workload(ctx, wl)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    S = ctx.simulate(sc, p)
+    if case == "adjoint":
+        G = (torch.randn_like(S.real) + 1j * torch.randn_like(S.real)).to(torch.complex64)
+        n_mat, n_bands = wl.k_band.shape
+        for _ in range(reps):
+            ctx.backward(sc, G, n_mat, n_bands)
+    else:
+        for _ in range(reps):
+            ctx.simulate(sc, p, out=S)
+    torch.cuda.synchronize()
+    print(f"case {case}: {wl.name}, {len(wl.dirs)} rays, {reps} repetitions")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -377,6 +403,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain pose sweep")
     ap.add_argument("--no-vegetation", action="store_true", help="skip the full-size vegetation simulate timing")
+    ap.add_argument("--case", default=None, choices=["accum", "adjoint", "trace", "narrow"],
+                    help="run a small case of one kernel family a few times and exit (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -385,6 +413,9 @@ def main():
     import torch.distributed as dist
 
     import paper_2602_19652_gb300 as st
+
+    if args.case:
+        return run_case(st, torch, args.case, max(args.steps, 1))
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "st_accum_dev.cuh"
 #include "st_internal.cuh"
@@ -208,15 +209,17 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
             const uint32_t meta = __float_as_uint(d[8]);
             const int len = (KIND == 0 && a.reflection_mode == 0) ? (int)(meta & 15) : 1;
             const int matj = (meta >> 8) & 255;
-            int off[kMaxBounces];
+            // (the first four in registers; hits 5 .. 8 are decoded where they are used)
+            int off[4];
+            uint32_t c1 = 0;
             if (KIND == 0 && a.reflection_mode == 0) {
-                const uint32_t c0 = __float_as_uint(d[9]), c1 = __float_as_uint(d[10]);
+                const uint32_t c0 = __float_as_uint(d[9]);
+                c1 = __float_as_uint(d[10]);
 #pragma unroll
-                for (int u = 0; u < kMaxBounces; ++u)
-                    off[u] = (int)((u < 4 ? (c0 >> (8 * u)) : (c1 >> (8 * (u - 4)))) & 255) * rs;
+                for (int u = 0; u < 4; ++u) off[u] = (int)((c0 >> (8 * u)) & 255) * rs;
             } else {
 #pragma unroll
-                for (int u = 0; u < kMaxBounces; ++u) off[u] = matj * rs;
+                for (int u = 0; u < 4; ++u) off[u] = matj * rs;
             }
             const int goff = matj * rs;
             // emitter directivity: row pair of the path's angle
@@ -230,54 +233,60 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
             }
             const float* d1 = C.dband + (size_t)p * 2 * g.NB;
             const float* d2 = d1 + g.NB;
+            // the term loop, specialised on the emitter table (its loads then carry no condition)
+            auto terms = [&](auto has_e) {
+                constexpr bool HE = decltype(has_e)::value;
 #pragma unroll
-            for (int kk = 0; kk < kNKT; ++kk) {
-                const int i = s + NS * kk;
-                const int k = kb + i;
-                float lx, de = 1.0f;
-                if (k < a.F) {
-                    lx = lkp[off[0] + i];
+                for (int kk = 0; kk < kNKT; ++kk) {
+                    const int i = s + NS * kk;
+                    const int k = kb + i;
+                    float lx, de = 1.0f;
+                    if (HE) {  // emitter directivity, a factor of the amplitude (zero where the table is)
+                        const int kc = min(k, a.F - 1);
+                        de = fmaxf((1.0f - ew) * __ldg(e0 + kc) + ew * __ldg(e0 + a.F + kc), 0.0f);
+                    }
+                    if (k < a.F) {
+                        lx = lkp[off[0] + i];
 #pragma unroll
-                    for (int u = 1; u < kMaxBounces; ++u)
-                        if (u < len) lx += lkp[off[u] + i];
-                    if (e0) {  // emitter directivity, a factor of the amplitude (zero where the table is)
-                        de = (1.0f - ew) * __ldg(e0 + k) + ew * __ldg(e0 + a.F + k);
-                        de = fmaxf(de, 0.0f);
+                        for (int u = 1; u < 4; ++u)
+                            if (u < len) lx += lkp[off[u] + i];
+                        for (int u = 4; u < len; ++u) lx += lkp[(int)((c1 >> (8 * (u - 4))) & 255) * rs + i];
+                    } else {
+                        lx = kNegInf;
                     }
-                } else {
-                    lx = kNegInf;
-                }
-                u64 E;
-                if (KIND == 0) {
-                    const float gg = k < a.F ? g2p[goff + i] : 0.0f;
-                    const float2 arg = up2(ffma2(ng, pk2(gg, gg), pk2(lx, lx)));
-                    E = pk2(ex2(arg.x), ex2(arg.y));
-                } else {
-                    const float x = ex2(lx);
-                    E = pk2(x, x);
-                }
-                if (DIR) {
-                    const float2 bwv = bwt[i];
-                    const int b0 = (int)bwv.x;
-                    float D1 = d1[b0], D2 = d2[b0];
-                    if (g.NB > 1) {
-                        D1 = fmaf(bwv.y, d1[b0 + 1] - D1, D1);
-                        D2 = fmaf(bwv.y, d2[b0 + 1] - D2, D2);
+                    u64 E;
+                    if (KIND == 0) {
+                        const float gg = k < a.F ? g2p[goff + i] : 0.0f;
+                        const float2 arg = up2(ffma2(ng, pk2(gg, gg), pk2(lx, lx)));
+                        E = pk2(ex2(arg.x), ex2(arg.y));
+                    } else {
+                        const float x = ex2(lx);
+                        E = pk2(x, x);
                     }
-                    E = fmul2(E, pk2(D1 * de, D2 * de));
-                } else if (e0) {
-                    E = fmul2(E, pk2(de, de));
+                    if (DIR) {
+                        const float2 bwv = bwt[i];
+                        const int b0 = (int)bwv.x;
+                        float D1 = d1[b0], D2 = d2[b0];
+                        if (g.NB > 1) {
+                            D1 = fmaf(bwv.y, d1[b0 + 1] - D1, D1);
+                            D2 = fmaf(bwv.y, d2[b0 + 1] - D2, D2);
+                        }
+                        E = fmul2(E, pk2(D1 * de, D2 * de));
+                    } else if (HE) {
+                        E = fmul2(E, pk2(de, de));
+                    }
+                    if ((kk & 1) == 0) {
+                        Sr[kk] = ffma2(E, er, Sr[kk]);
+                        Si[kk] = ffma2(E, ei, Si[kk]);
+                        cmul2(er, ei, s2r, s2i, ns2i);
+                    } else {
+                        Sr[kk] = ffma2(E, orr, Sr[kk]);
+                        Si[kk] = ffma2(E, oi, Si[kk]);
+                        cmul2(orr, oi, s2r, s2i, ns2i);
+                    }
                 }
-                if ((kk & 1) == 0) {
-                    Sr[kk] = ffma2(E, er, Sr[kk]);
-                    Si[kk] = ffma2(E, ei, Si[kk]);
-                    cmul2(er, ei, s2r, s2i, ns2i);
-                } else {
-                    Sr[kk] = ffma2(E, orr, Sr[kk]);
-                    Si[kk] = ffma2(E, oi, Si[kk]);
-                    cmul2(orr, oi, s2r, s2i, ns2i);
-                }
-            }
+            };
+            if (e0) terms(std::true_type{}); else terms(std::false_type{});
         }
         if (tile + 2 < t1) {
             const int nb2 = (int)((tile + 2 - t0) % 3);
