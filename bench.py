@@ -307,7 +307,7 @@ def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2):
 
 
 def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm_gbs: float):
-    """BVH fetch bandwidth of the tracing kernels: nodes (64 B) and leaf triangles (48 B) visited,
+    """BVH fetch bandwidth of the tracing kernels: 4-wide nodes (112 B read of 128) and leaf triangles (48 B) visited,
     counted in a separate instrumented run (ST_COUNT_VISITS), divided by the uninstrumented kernel
     times of the headline steps.  The fetches are served mostly by L1/L2 (the node array of the
     benchmark scene fits in L2), so the ratio to the HBM copy bandwidth can exceed 1."""
@@ -326,12 +326,12 @@ def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm
     vs = list(s_spec.visits)
     va = list(s_all.visits)
     vd = [a - b for a, b in zip(va, vs)]  # diffraction filters and the direct path (any-hit only)
-    bt = 64 * (vs[0] + vs[2]) + 48 * (vs[1] + vs[3])
-    bd = 64 * (vd[0] + vd[2]) + 48 * (vd[1] + vd[3])
+    bt = 112 * (vs[0] + vs[2]) + 48 * (vs[1] + vs[3])
+    bd = 112 * (vd[0] + vd[2]) + 48 * (vd[1] + vd[3])
     ctx.close()
     q_t = s_spec.closest_queries + s_spec.shadow_queries
     q_d = (s_all.shadow_queries - s_spec.shadow_queries)
-    return {"bytes_per_node": 64, "bytes_per_triangle": 48, "hbm_peak_gbs": hbm_gbs,
+    return {"bytes_per_node": 112, "bytes_per_triangle": 48, "hbm_peak_gbs": hbm_gbs,
             "k_bounce": {"queries": int(q_t), "nodes": int(vs[0] + vs[2]), "triangles": int(vs[1] + vs[3]),
                          "nodes_per_query": (vs[0] + vs[2]) / max(q_t, 1), "ms": ms_trace,
                          "fetch_gbs": bt / (ms_trace / 1e3) / 1e9, "frac_of_hbm": bt / (ms_trace / 1e3) / 1e9 / hbm_gbs},

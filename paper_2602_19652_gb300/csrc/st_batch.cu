@@ -35,7 +35,7 @@ __global__ void k_batch_prep(const JobDev* J, int n_jobs) {
 }
 
 // one bounce level of Algorithm 1 over the live rays of every job (global ray ids)
-__global__ void __launch_bounds__(256) k_bounce_batch(const BatchArgs a, int j, int64_t n_first) {
+__global__ void __launch_bounds__(256, 4) k_bounce_batch(const BatchArgs a, int j, int64_t n_first) {
     const int64_t n_live = (j == 0) ? n_first : (int64_t)*a.n_in;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_live; idx += stride) {
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_bounce_batch(const BatchArgs a, int j, 
 }
 
 // diffraction samples of every job (global sample index), same steps as the single-pose kernel
-__global__ void __launch_bounds__(128) k_diffraction_batch(const BatchArgs a) {
+__global__ void __launch_bounds__(128, 8) k_diffraction_batch(const BatchArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.K_total; g += stride) {
         const int job = find_job(a.samp_offs, a.n_jobs, g);

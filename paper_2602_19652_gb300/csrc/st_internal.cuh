@@ -13,7 +13,8 @@ namespace st {
 
 // ------------------------------------------------------------------ constants
 constexpr int kLeafMax = 4;        // triangles per BVH leaf after collapsing small subtrees
-constexpr int kStack = 96;         // traversal stack entries per thread
+constexpr int kStack = 128;        // traversal stack entries per thread
+constexpr int32_t kEmptyRef = INT32_MIN;  // unused child slot of a 4-wide BVH node (no valid leaf has this code)
 constexpr int kMaxBounces = 8;     // B limit (material chain packed in 8 bytes)
 constexpr int kMaxMics = 4096;
 
@@ -44,9 +45,10 @@ struct SceneDev {
     DevBuf tri_obj;    // [T] i32
     DevBuf nrm;        // [T][3] f32 geometric normals (input triangle order)
     // LBVH
-    DevBuf nodes;      // [max(T-1,1)][4] float4: child boxes + child refs
+    DevBuf nodes;      // 4-wide BVH: [n4][8] float4: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the 4 children, refs, pad
     DevBuf tri_v;      // [T][3] float4 in leaf order; tri_v[3i].w = triangle index bits
     int32_t root = 0;  // child-ref encoding of the root
+    int64_t n_nodes = 0;  // 4-wide nodes
     float bounds_lo[3] = {0, 0, 0}, bounds_hi[3] = {0, 0, 0};
     // curvature and diffraction CDFs
     DevBuf G;          // [V] f32

@@ -551,26 +551,83 @@ __global__ void k_boxes(const float* V, const int32_t* T, int n, const uint32_t*
 
 __host__ __device__ __forceinline__ int32_t leaf_ref(int first, int count) { return ~((first << 3) | (count - 1)); }
 
-__global__ void k_pack_nodes(int n, const int2* child, const int2* range, const Box* box_tmp, float4* nodes) {
+// child reference of binary node i's side c: a leaf code for single triangles and for subtrees of at
+// most kLeafMax triangles (a contiguous range of the leaf order), else the internal node index
+__device__ __forceinline__ int32_t child_ref(int32_t cc, const int2* range) {
+    if (cc < 0) return leaf_ref(~cc, 1);
+    const int2 r = range[cc];
+    const int cnt = r.y - r.x + 1;
+    return cnt <= kLeafMax ? leaf_ref(r.x, cnt) : cc;
+}
+
+// Binary internal nodes that stay internal (range above kLeafMax, or the root) at even depth become
+// the nodes of the 4-wide BVH: each takes its children, with internal children replaced by theirs.
+__global__ void k_wide_flags(int n, const int2* range, const int32_t* parent_int, uint32_t* flag, uint32_t* err) {
     int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += stride) {
-        int2 c = child[i];
-        int32_t ref[2];
-        int cc[2] = {c.x, c.y};
-        for (int s = 0; s < 2; ++s) {
-            if (cc[s] < 0) {
-                ref[s] = leaf_ref(~cc[s], 1);
+        const int2 r = range[i];
+        const bool internal = i == 0 || r.y - r.x + 1 > kLeafMax;
+        uint32_t f = 0;
+        if (internal) {
+            int d = 0, x = i;
+            while (x != 0) {
+                x = parent_int[x];
+                if (++d > n) {  // deeper than the node count: not a tree
+                    atomicOr(err, kFlagBadTree);
+                    break;
+                }
+            }
+            f = (d & 1) == 0 ? 1u : 0u;
+        }
+        flag[i] = f;
+    }
+}
+
+__global__ void k_pack_wide(int n, const int2* child, const int2* range, const Box* box_tmp, const uint32_t* flag,
+                            const uint32_t* idx, float4* nodes) {
+    int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += stride) {
+        if (!flag[i]) continue;
+        float lo[3][4], hi[3][4];
+        int32_t ref[4];
+        int cnt = 0;
+        auto add = [&](const Box& b, int32_t r) {
+            for (int k = 0; k < 3; ++k) {
+                lo[k][cnt] = b.lo[k];
+                hi[k][cnt] = b.hi[k];
+            }
+            ref[cnt++] = r;
+        };
+        const int2 c = child[i];
+        const int32_t cs[2] = {c.x, c.y};
+        for (int sd = 0; sd < 2; ++sd) {
+            const int32_t r = child_ref(cs[sd], range);
+            if (r < 0) {
+                add(box_tmp[2 * i + sd], r);
             } else {
-                int2 r = range[cc[s]];
-                int cnt = r.y - r.x + 1;
-                ref[s] = cnt <= kLeafMax ? leaf_ref(r.x, cnt) : cc[s];
+                const int2 g = child[r];
+                const int32_t gs[2] = {g.x, g.y};
+                for (int t = 0; t < 2; ++t) {
+                    const int32_t rg = child_ref(gs[t], range);
+                    add(box_tmp[2 * r + t], rg < 0 ? rg : (int32_t)idx[rg]);
+                }
             }
         }
-        Box L = box_tmp[2 * i], R = box_tmp[2 * i + 1];
-        nodes[4 * i + 0] = make_float4(L.lo[0], L.lo[1], L.lo[2], L.hi[0]);
-        nodes[4 * i + 1] = make_float4(L.hi[1], L.hi[2], R.lo[0], R.lo[1]);
-        nodes[4 * i + 2] = make_float4(R.lo[2], R.hi[0], R.hi[1], R.hi[2]);
-        nodes[4 * i + 3] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), 0.0f, 0.0f);
+        for (; cnt < 4; ++cnt) {
+            for (int k = 0; k < 3; ++k) {
+                lo[k][cnt] = 0.0f;
+                hi[k][cnt] = 0.0f;
+            }
+            ref[cnt] = kEmptyRef;
+        }
+        float4* o = nodes + 8 * (size_t)idx[i];
+        for (int k = 0; k < 3; ++k) {
+            o[2 * k] = make_float4(lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
+            o[2 * k + 1] = make_float4(hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
+        }
+        o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
+                           __int_as_float(ref[3]));
+        o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
 
@@ -597,10 +654,10 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
     const int32_t* obj = ptr<int32_t>(S.tri_obj);
     // ---- scratch (freed at the end of the build)
     DevBuf flags, canon, keys, vals, sort_scr, cnt, off, cursor, adj, Gc, cmax, sumQ, Q, S64, nsu, bnd, child, range,
-        par_i, par_l, boxes, visits, moff;
+        par_i, par_l, boxes, visits, moff, range2, wscan_scr, wtotal;
     auto cleanup = [&]() {
         for (DevBuf* b : {&flags, &canon, &keys, &vals, &sort_scr, &cnt, &off, &cursor, &adj, &Gc, &cmax, &sumQ, &Q,
-                          &S64, &nsu, &bnd, &child, &range, &par_i, &par_l, &boxes, &visits, &moff})
+                          &S64, &nsu, &bnd, &child, &range, &par_i, &par_l, &boxes, &visits, &moff, &range2, &wscan_scr, &wtotal})
             release(*b);
     };
     struct Guard {
@@ -780,8 +837,8 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
         note_launch();
         k_reorder<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(vals), ptr<float4>(S.tri_v));
         CK(cudaGetLastError());
-        CK(grow(S.nodes, (size_t)std::max(n - 1, 1) * 4 * sizeof(float4)));
         if (n == 1 || n <= kLeafMax) {
+            CK(grow(S.nodes, 8 * sizeof(float4)));
             S.root = leaf_ref(0, n);
         } else {
             S.root = 0;
@@ -801,10 +858,25 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
                                                    ptr<int32_t>(par_l), pad, ptr<Box>(boxes), ptr<uint32_t>(visits),
                                                    ptr<uint32_t>(flags));
             CK(cudaGetLastError());
+            // 4-wide BVH: flag the binary nodes that become wide nodes, number them, pack
+            uint32_t* wflag = ptr<uint32_t>(visits);  // reuses the climb counters (no longer needed)
+            CK(grow(range2, (size_t)(n - 1) * 4));
+            CK(grow(wscan_scr, scan_scratch_bytes(n - 1)));
+            CK(grow(wtotal, 4));
             note_launch();
-            k_pack_nodes<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(child), ptr<int2>(range), ptr<Box>(boxes),
-                                                            ptr<float4>(S.nodes));
+            k_wide_flags<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(range), ptr<int32_t>(par_i), wflag,
+                                                            ptr<uint32_t>(flags));
             CK(cudaGetLastError());
+            CK(exclusive_scan_u32(wflag, ptr<uint32_t>(range2), n - 1, ptr<uint32_t>(wtotal), wscan_scr.p, s));
+            uint32_t n4 = 0;
+            CK(cudaMemcpyAsync(&n4, wtotal.p, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            CK(grow(S.nodes, (size_t)std::max<uint32_t>(n4, 1) * 8 * sizeof(float4)));
+            note_launch();
+            k_pack_wide<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(child), ptr<int2>(range), ptr<Box>(boxes),
+                                                           wflag, ptr<uint32_t>(range2), ptr<float4>(S.nodes));
+            CK(cudaGetLastError());
+            S.n_nodes = n4;
         }
     }
     CK(cudaMemcpyAsync(&hflags, flags.p, 4, cudaMemcpyDeviceToHost, s));

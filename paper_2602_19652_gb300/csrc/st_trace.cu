@@ -22,7 +22,7 @@ namespace {
 using namespace trv;
 
 // One bounce of Algorithm 1 over the live-ray queue.
-__global__ void __launch_bounds__(256) k_bounce(const TraceArgs a, int j, int64_t n_first) {
+__global__ void __launch_bounds__(256, 4) k_bounce(const TraceArgs a, int j, int64_t n_first) {
     const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     const int64_t n_live = (j == 0) ? n_first : (int64_t)*a.n_in;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_bounce(const TraceArgs a, int j, int64_
 
 // Sec. III-D: sample g of the global list -> mesh m, local index s; Philox(s, m, pose, 0) selects a
 // triangle through the mesh's integer CDF and a barycentric point; then the filters.
-__global__ void __launch_bounds__(128) k_diffraction(const DiffArgs a) {
+__global__ void __launch_bounds__(128, 8) k_diffraction(const DiffArgs a) {
     const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const f3 s{a.s[0], a.s[1], a.s[2]};

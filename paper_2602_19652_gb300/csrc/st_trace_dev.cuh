@@ -59,30 +59,51 @@ __device__ __forceinline__ int32_t traverse(const Trav& T, f3 o, f3 d, int32_t e
             break;
         }
         if (ref >= 0) {
-            const float4 a = __ldg(&T.nodes[4 * ref + 0]);
-            const float4 b = __ldg(&T.nodes[4 * ref + 1]);
-            const float4 c = __ldg(&T.nodes[4 * ref + 2]);
-            const float4 e = __ldg(&T.nodes[4 * ref + 3]);
+            // 4-wide node: children's bounds as lo.x, hi.x, lo.y, hi.y, lo.z, hi.z rows, then the refs
+            const float4* nd = T.nodes + 8 * (size_t)ref;
+            const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+            const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
             ++n_nodes;
             // boxes are padded, so a box holding a hit at t > t_min >= 0 exits at t > 0 after rounding
-            float tl, tr;
-            const bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, 0.0f, tb, &tl);
-            const bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, 0.0f, tb, &tr);
-            const int32_t rl = __float_as_int(e.x), rr = __float_as_int(e.y);
-            if (hl && hr) {
-                const bool lfirst = tl <= tr;
-                ref = lfirst ? rl : rr;
-                if (sp < kStack) {
-                    stack[sp++] = make_int2(lfirst ? rr : rl, __float_as_int(lfirst ? tr : tl));
-                } else {
-                    atomicOr(flags, kFlagStackOverflow);
+            float t0, t1, t2, t3;
+            const int32_t r0 = __float_as_int(rf.x), r1 = __float_as_int(rf.y), r2 = __float_as_int(rf.z),
+                          r3 = __float_as_int(rf.w);
+            const bool h0 = slab(lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, o, inv, 0.0f, tb, &t0);
+            const bool h1 = slab(lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, o, inv, 0.0f, tb, &t1);
+            const bool h2 = r2 != kEmptyRef && slab(lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, o, inv, 0.0f, tb, &t2);
+            const bool h3 = r3 != kEmptyRef && slab(lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, o, inv, 0.0f, tb, &t3);
+            // order the hit children by entry distance (misses last): the nearest is visited next, the
+            // others are pushed farthest first
+            // (hit keys are clamped below +inf, so the hits sort strictly before the misses)
+            const float inf = __int_as_float(0x7f800000), big = 3.0e38f;
+            float k0 = h0 ? fminf(t0, big) : inf, k1 = h1 ? fminf(t1, big) : inf;
+            float k2 = h2 ? fminf(t2, big) : inf, k3 = h3 ? fminf(t3, big) : inf;
+            int32_t c0 = r0, c1 = r1, c2 = r2, c3 = r3;
+            auto cx = [](float& ka, int32_t& ca, float& kb, int32_t& cb) {
+                if (kb < ka) {
+                    const float tk = ka;
+                    ka = kb;
+                    kb = tk;
+                    const int32_t tc = ca;
+                    ca = cb;
+                    cb = tc;
                 }
-                continue;
-            } else if (hl) {
-                ref = rl;
-                continue;
-            } else if (hr) {
-                ref = rr;
+            };
+            cx(k0, c0, k1, c1);
+            cx(k2, c2, k3, c3);
+            cx(k0, c0, k2, c2);
+            cx(k1, c1, k3, c3);
+            cx(k1, c1, k2, c2);
+            const int nh = (int)h0 + (int)h1 + (int)h2 + (int)h3;
+            if (nh > 0) {
+                if (sp + nh - 1 > kStack) {
+                    atomicOr(flags, kFlagStackOverflow);
+                } else {
+                    if (nh > 3) stack[sp++] = make_int2(c3, __float_as_int(k3));
+                    if (nh > 2) stack[sp++] = make_int2(c2, __float_as_int(k2));
+                    if (nh > 1) stack[sp++] = make_int2(c1, __float_as_int(k1));
+                }
+                ref = c0;
                 continue;
             }
         } else {
