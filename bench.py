@@ -162,6 +162,18 @@ def oracle_sample(wl, n_sample_rays: int, nthreads: int = 0):
     return segs, dt, desc
 
 
+def over_ranks(dist, world: int, vals_max, vals_sum, device="cpu"):
+    """Max over ranks of vals_max and sum over ranks of vals_sum (float64 all-reduces); identity at N = 1."""
+    import torch
+    if world <= 1:
+        return [float(v) for v in vals_max], [float(v) for v in vals_sum]
+    a = torch.tensor([float(v) for v in vals_max], dtype=torch.float64, device=device)
+    b = torch.tensor([float(v) for v in vals_sum], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.tolist(), b.tolist()
+
+
 def measure_adjoint(st, torch, wl, steps: int = 5):
     """Device time of one forward simulate and of one st_backward (all gradients) on a workload."""
     ctx = st.Context(torch.cuda.current_device())
@@ -306,6 +318,23 @@ def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2):
     return res
 
 
+def l2_probe_gbs(torch, mb: int = 40, reps: int = 50):
+    """Copy bandwidth with both buffers resident in L2 (2 x 40 MB < 129 MB): read + write bytes over the
+    device time of back-to-back copies.  A torch copy kernel, so a lower bound on the L2 peak."""
+    n = mb * (1 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(reps):
+        b.copy_(a)
+    ev[1].record()
+    torch.cuda.synchronize()
+    return 2.0 * a.numel() * 4 * reps / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e9
+
+
 def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm_gbs: float):
     """BVH fetch bandwidth of the tracing kernels: 4-wide nodes (112 B read of 128) and leaf triangles (48 B) visited,
     counted in a separate instrumented run (ST_COUNT_VISITS), divided by the uninstrumented kernel
@@ -331,7 +360,10 @@ def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm
     ctx.close()
     q_t = s_spec.closest_queries + s_spec.shadow_queries
     q_d = (s_all.shadow_queries - s_spec.shadow_queries)
-    return {"bytes_per_node": 112, "bytes_per_triangle": 48, "hbm_peak_gbs": hbm_gbs,
+    l2 = l2_probe_gbs(torch)
+    ft, fd = bt / (ms_trace / 1e3) / 1e9, bd / (ms_diffraction / 1e3) / 1e9
+    return {"bytes_per_node": 112, "bytes_per_triangle": 48, "hbm_peak_gbs": hbm_gbs, "l2_probe_gbs": l2,
+            "frac_of_l2_probe": {"k_bounce": ft / l2, "k_diffraction": fd / l2},
             "k_bounce": {"queries": int(q_t), "nodes": int(vs[0] + vs[2]), "triangles": int(vs[1] + vs[3]),
                          "nodes_per_query": (vs[0] + vs[2]) / max(q_t, 1), "ms": ms_trace,
                          "fetch_gbs": bt / (ms_trace / 1e3) / 1e9, "frac_of_hbm": bt / (ms_trace / 1e3) / 1e9 / hbm_gbs},
@@ -463,15 +495,8 @@ def main():
     total_ms = float(sum(step_ms))
     segs = sum(s.closest_queries + s.shadow_queries for s in st_list)
     # max over ranks of the time, sum of the work
-    t = torch.tensor([total_ms, float(segs), float(len(wl.mics) * args.steps)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_all = float(tmax[0])
-    else:
-        total_ms_all = total_ms
-    segs_all, spectra_all = float(t[1]), float(t[2])
+    (total_ms_all,), (segs_all, spectra_all) = over_ranks(dist, world, [total_ms],
+                                                          [segs, len(wl.mics) * args.steps], dev)
     value = segs_all / (total_ms_all / 1e3) / 1e6
 
     # ---- dominant kernel: the accumulator (FP32/XU-pipe arithmetic)
@@ -490,12 +515,9 @@ def main():
                         f"terms per launch", "ms_per_launch": acc_ms / max(acc_launches, 1),
                 "traffic": ACCUM_DRAM_BYTES_PER_LAUNCH}
 
-    traversal = measure_traversal(st, torch, wl, float(np.median([s.ms_trace for s in st_list])),
-                                  float(np.median([s.ms_diffraction for s in st_list])), peaks["hbm_gbs"])
-
     # ---- end to end through the C ABI with host buffers
     e2e = None
-    if rank == 0 or world > 1:
+    if True:
         dirs_h = torch.from_numpy(np.ascontiguousarray(wl.dirs)).pin_memory()
         mics_h = np.ascontiguousarray(wl.mics, np.float32)
         spec_h = np.empty((3, len(wl.mics), wl.n_bins), np.complex64)
@@ -515,19 +537,28 @@ def main():
 
         for _ in range(2):
             e2e_step()
-        e2e_t = []
-        for i in range(max(3, args.steps // 2)):
-            flush.fill_(i & 255)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e2e_step()
-            e2e_t.append(time.perf_counter() - t0)
-        segs_per_step = segs / len(st_list)
+        n_e2e = max(3, args.steps // 2)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(n_e2e):
+            e2e_step()  # host buffers in and out: each call returns with its spectra on the host
+        t_e2e = time.perf_counter() - t0
+        (t_e2e_max,), (segs_e2e,) = over_ranks(dist, world, [t_e2e], [segs / len(st_list) * n_e2e], dev)
         h2d = wl.dirs.nbytes + mics_h.nbytes + pos.nbytes + quat.nbytes
-        e2e = {"value": segs_per_step / float(np.mean(e2e_t)) / 1e6 * world, "unit": UNIT,
+        e2e = {"value": segs_e2e / t_e2e_max / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(spec_h.nbytes),
-               "ms_per_step": 1e3 * float(np.mean(e2e_t))}
+               "ms_per_step": 1e3 * t_e2e_max / n_e2e}
 
+    # the remaining measurements run on rank 0 alone
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    traversal = measure_traversal(st, torch, wl, float(np.median([s.ms_trace for s in st_list])),
+                                  float(np.median([s.ms_diffraction for s in st_list])), peaks["hbm_gbs"])
     adjoint = None
     if not args.no_adjoint:
         adjoint = {"gradient workload (shoebox, 4 materials x 16 bands, 32 mics, 128 bins, 10k rays x 3)":
@@ -540,11 +571,6 @@ def main():
     vegetation = None
     if not args.no_vegetation and args.workload != "vegetation":
         vegetation = measure_workload(st, torch, synth.vegetation(seed=303))
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
