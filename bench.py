@@ -72,7 +72,7 @@ def workload_config(wl, args):
 
 
 class ClockSampler:
-    """nvidia-smi clocks sampled every 200 ms while running."""
+    """nvidia-smi clocks sampled every 50 ms while running."""
 
     def __init__(self, gpu: int):
         self.gpu = gpu
@@ -85,7 +85,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
