@@ -373,6 +373,32 @@ def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm
                               "frac_of_hbm": bd / (ms_diffraction / 1e3) / 1e9 / hbm_gbs}}
 
 
+def measure_signal(st, torch, ctx, S, wl, reps: int = 5):
+    """Received signals of the headline spectra: all three components summed, convolved with a 1 ms
+    chirp over the band, sampled at 2.5 x the top frequency over one period 1 / df of the response
+    (a spectrum sampled every df gives a response periodic in 1 / df)."""
+    fs = 2.5 * wl.f_hi
+    period = (wl.n_bins - 1) / (wl.f_hi - wl.f_lo)
+    n = int(math.ceil(min(wl.max_distance / 343.0, period) * fs))
+    t = np.arange(int(1e-3 * fs)) / fs
+    call = np.sin(2 * np.pi * (wl.f_hi * t - 0.5 * (wl.f_hi - wl.f_lo) / 1e-3 * t * t)).astype(np.float32)
+    call_d = torch.from_numpy(call).cuda()
+    for _ in range(2):
+        ctx.impulse_response(S, wl.f_lo, wl.f_hi, fs, n, call=call_d)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    ev[0].record(stream)
+    for _ in range(reps):
+        ctx.impulse_response(S, wl.f_lo, wl.f_hi, fs, n, call=call_d)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    M, F = int(S.shape[1]), int(S.shape[2])
+    flops = 10.0 * M * n * F  # per (mic, sample, bin): rotation 6 + real part of the product 4
+    return {"config": f"{M} mics x {F} bins -> {n} samples at {fs / 1e3:.0f} kHz, {len(call)}-sample chirp",
+            "ms": ms, "msamples_per_s": M * n / ms / 1e3, "tflops": flops / (ms / 1e3) / 1e12}
+
+
 def run_case(st, torch, case: str, reps: int):
     """Small cases of single kernels for profiling (ncu captures): no timing output."""
     dev = torch.cuda.current_device()
@@ -557,6 +583,7 @@ def main():
             dist.destroy_process_group()
         return
 
+    signal = measure_signal(st, torch, ctx, out, wl)
     traversal = measure_traversal(st, torch, wl, float(np.median([s.ms_trace for s in st_list])),
                                   float(np.median([s.ms_diffraction for s in st_list])), peaks["hbm_gbs"])
     adjoint = None
@@ -590,7 +617,7 @@ def main():
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
                          "ms_accumulate": s0.ms_accumulate},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
-            "traversal": traversal, "batched": batched, "vegetation": vegetation,
+            "traversal": traversal, "signal": signal, "batched": batched, "vegetation": vegetation,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
     print(json.dumps(line))
     if world > 1:

@@ -225,6 +225,27 @@ st_status st_simulate_batch(st_ctx* ctx, int32_t n_jobs, const st_job* jobs, con
  * emitter, receivers and frequency grid with the sample job's (omni).  Synchronises. */
 st_status st_autotune(st_ctx* ctx, const st_job* sample, const st_sim_params* params, st_tune* out);
 
+/* Impulse responses and received signals (Eq. 5-6, 9-10, 13 and the signal equation of Sec. III-F).
+ * Every path's transfer function is M(f) e^{+j 2 pi f r / c}; summed over paths, a component's
+ * impulse response is the inverse Fourier transform of its spectrum, the components add, and the
+ * received signal is the impulse response convolved with the emitted call.  On the spectra's uniform
+ * grid f_k = f_lo + k df (df = (f_hi - f_lo) / (n_bins - 1); 1 for a single bin), with the kernel
+ * e^{-j 2 pi f t} (echoes at t = r / c) and the spectra taken as the positive frequencies of a real
+ * signal:
+ *     out[r][n] = 2 df Re sum_k w_k E_k S'[r][k] e^{-j 2 pi f_k n / fs},  n < n_samples,
+ *     E_k = (1 / fs) sum_i call[i] e^{+j 2 pi f_k i / fs}  (1 when call is NULL or call_len is 0),
+ * The response is periodic in t with period 1 / df: an echo at r / c beyond it wraps around.
+ * where S'[m] = sum over the n_comp components of spectra[c][m] (out [n_mics][n_samples]) or, with
+ * ST_IR_PER_COMPONENT in flags, S'[c M + m] = spectra[c][m] (out [n_comp][n_mics][n_samples]).
+ * spectra: device complex64 [n_comp][n_mics][n_bins] (st_simulate's layout); window: device float
+ * [n_bins] or NULL; call: device float [call_len] sampled at fs, or NULL; out: device float32.
+ * Stream-ordered on the context's stream; scratch is owned by the context.  Errors: ST_ERR_ARG for
+ * null pointers, n_comp outside 1..3, n_mics < 1, n_bins < 1, n_samples < 1, fs <= 0, f_hi < f_lo. */
+#define ST_IR_PER_COMPONENT 1
+st_status st_impulse_response(st_ctx* ctx, const void* spectra, int32_t n_comp, int32_t n_mics, int32_t n_bins,
+                              double f_lo, double f_hi, double fs, int32_t n_samples, const float* window,
+                              const float* call, int32_t call_len, int32_t flags, float* out);
+
 /* Allocation-free specular accumulation.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory where they need spectra -- code running inside another
  * allocator's fixed memory budget or arena, real-time loops where cudaMalloc would stall or

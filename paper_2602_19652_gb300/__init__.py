@@ -158,6 +158,26 @@ class Context:
         self._check(self.L.st_get_direct_visibility(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST))
         return v
 
+    # -------------------------------------------------------------- signals
+    def impulse_response(self, spectra: torch.Tensor, f_lo: float, f_hi: float, fs: float, n_samples: int,
+                         window: torch.Tensor | None = None, call: torch.Tensor | None = None,
+                         per_component: bool = False) -> torch.Tensor:
+        """Band-limited impulse responses (or received signals, with the emitted `call` sampled at fs) of
+        spectra [C][M][F]: float32 [M][n_samples] (components summed) or [C][M][n_samples]."""
+        S = spectra.contiguous()
+        if S.dim() == 2:
+            S = S.unsqueeze(0)
+        Cn, M, F = (int(x) for x in S.shape)
+        dev = S.device
+        w = None if window is None else window.to(device=dev, dtype=torch.float32).contiguous()
+        e = None if call is None else call.to(device=dev, dtype=torch.float32).contiguous()
+        out = torch.empty((Cn, M, n_samples) if per_component else (M, n_samples), dtype=torch.float32, device=dev)
+        vp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._check(self.L.st_impulse_response(self.h, vp(S), Cn, M, F, float(f_lo), float(f_hi), float(fs),
+                                               int(n_samples), vp(w), vp(e), 0 if e is None else int(e.numel()),
+                                               _lib.ST_IR_PER_COMPONENT if per_component else 0, vp(out)))
+        return out
+
     # -------------------------------------------------------------- batched form
     def simulate_batch(self, jobs: list["BatchJob"], params: SimParams | None = None, tune: Tune | None = None):
         """All jobs' spectra (each job's .out).  Same job list and sizes on a later call replays the

@@ -30,6 +30,7 @@ UNITS = {
     "st_accum_narrow.cu": [],
     "st_adjoint.cu": [],
     "st_noalloc.cu": [],
+    "st_signal.cu": [],
 }
 
 

@@ -101,6 +101,7 @@ struct st_ctx {
     st_tune tune{0, 0, 0, 0};   // launch shapes (st_autotune); 0 = default
     BatchState* batch = nullptr;
     std::vector<st_scene*> scenes;  // scenes loaded into this context (freed by st_destroy)
+    DevBuf sig_e, sig_g;             // impulse responses: call spectrum [F], combined spectra [rows][F]
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -259,7 +260,8 @@ st_status st_destroy(st_ctx* c) {
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
                           &P->meta, &P->dep})
             release(*b);
-    for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband}) release(*b);
+    for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->sig_e, &c->sig_g})
+        release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->batch) {
@@ -1085,6 +1087,26 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
     }
     if (want_pos)
         CKC(c, adjoint_pos(micp, mic_slices, emitp, emit_slices, M, grad_mic, grad_emitter, s), "adjoint reduce");
+    return ST_OK;
+}
+
+st_status st_impulse_response(st_ctx* c, const void* spectra, int32_t n_comp, int32_t n_mics, int32_t n_bins,
+                              double f_lo, double f_hi, double fs, int32_t n_samples, const float* window,
+                              const float* call, int32_t call_len, int32_t flags, float* out) {
+    if (!c || !spectra || !out) return fail(c, ST_ERR_ARG, "impulse_response: null pointer");
+    if (n_comp < 1 || n_comp > 3 || n_mics < 1 || n_bins < 1 || n_samples < 1 || !(fs > 0.0) || !(f_hi >= f_lo) ||
+        call_len < 0 || (call_len > 0 && !call) || (n_bins > 1 && !(f_hi > f_lo)))
+        return fail(c, ST_ERR_ARG, "impulse_response: bad sizes or grid");
+    enter(c);
+    const int per_comp = (flags & ST_IR_PER_COMPONENT) ? 1 : 0;
+    const int64_t rows = per_comp ? (int64_t)n_comp * n_mics : n_mics;
+    if (rows > 65535) return fail(c, ST_ERR_ARG, "impulse_response: more than 65535 output rows");
+    CKC(c, grow(c->sig_e, (size_t)n_bins * 8), "alloc");
+    CKC(c, grow(c->sig_g, (size_t)rows * n_bins * 8), "alloc");
+    CKC(c, signal_response(static_cast<const float2*>(spectra), n_comp, n_mics, n_bins, f_lo, f_hi, fs, n_samples,
+                           window, call_len > 0 ? call : nullptr, call_len, per_comp, ptr<float2>(c->sig_e),
+                           ptr<float2>(c->sig_g), out, c->stream),
+        "impulse response");
     return ST_OK;
 }
 
