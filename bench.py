@@ -399,6 +399,34 @@ def measure_signal(st, torch, ctx, S, wl, reps: int = 5):
             "ms": ms, "msamples_per_s": M * n / ms / 1e3, "tflops": flops / (ms / 1e3) / 1e12}
 
 
+def measure_scene_update(st, torch, ctx, sc, wl, reps: int = 3):
+    """Device time of a full precompute (weld, curvature, CDFs, LBVH, wide nodes) against a refit of new
+    vertex positions (same topology), with and without recomputing the curvature and CDFs."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    v = wl.verts.astype(np.float64)
+    moved = (v + 0.01 * np.sin(v[:, [1, 2, 0]])).astype(np.float32)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ms))
+
+    res = {"precompute_ms": timed(lambda: sc.precompute()),
+           "refit_ms": timed(lambda: sc.update_vertices(moved)),
+           "refit_keep_curvature_ms": timed(lambda: sc.update_vertices(moved, keep_curvature=True))}
+    sc.update_vertices(wl.verts)
+    sc.precompute()
+    return res
+
+
 def run_case(st, torch, case: str, reps: int):
     """Small cases of single kernels for profiling (ncu captures): no timing output."""
     dev = torch.cuda.current_device()
@@ -584,6 +612,7 @@ def main():
         return
 
     signal = measure_signal(st, torch, ctx, out, wl)
+    scene_update = measure_scene_update(st, torch, ctx, sc, wl)
     traversal = measure_traversal(st, torch, wl, float(np.median([s.ms_trace for s in st_list])),
                                   float(np.median([s.ms_diffraction for s in st_list])), peaks["hbm_gbs"])
     adjoint = None
@@ -617,7 +646,8 @@ def main():
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
                          "ms_accumulate": s0.ms_accumulate},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
-            "traversal": traversal, "signal": signal, "batched": batched, "vegetation": vegetation,
+            "traversal": traversal, "signal": signal, "scene_update": scene_update, "batched": batched,
+            "vegetation": vegetation,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
     print(json.dumps(line))
     if world > 1:

@@ -133,6 +133,16 @@ st_status st_scene_set_materials(st_scene* scene, int32_t n_mat, int32_t n_bands
 /* Build the device LBVH, triangle normals, curvature (G_v, C_i) and diffraction CDFs.
  * params may be NULL (defaults).  Synchronises the stream once (to size the sample buffers). */
 st_status st_scene_precompute(st_scene* scene, const st_curv_params* params);
+/* Dynamic scenes: new positions for the same vertices (n_verts [3] floats, host or device per mem)
+ * of a precomputed scene, then a refit: the LBVH topology and leaf order of the last precompute are
+ * kept and the boxes, wide nodes, leaf triangles and normals recomputed (results stay exact: the
+ * boxes are conservative for any positions, only the traversal cost can grow with large motions).
+ * Welding, curvature, metric, CDFs and sample counts are recomputed too, unless flags holds
+ * ST_REFIT_KEEP_CURVATURE (valid when whole meshes move rigidly, which leaves them unchanged up to
+ * rounding).  The scene's version changes: simulate again before st_backward; recorded batches
+ * re-record.  A non-finite vertex returns ST_ERR_MESH and leaves the scene needing a precompute. */
+#define ST_REFIT_KEEP_CURVATURE 1
+st_status st_scene_update_vertices(st_scene* scene, const float* verts, int32_t mem, int32_t flags);
 /* Copy per-vertex G [n_verts], per-triangle C [n_tris] and the diffraction sample count per
  * mesh out (any may be NULL).  n_samples has one entry per mesh id up to max(tri_object). */
 st_status st_scene_get_curvature(st_scene* scene, float* G, float* C, int64_t* n_samples, int32_t mem);

@@ -255,6 +255,13 @@ class Scene:
     def precompute(self, params: CurvParams | None = None):
         self.ctx._check(self.ctx.L.st_scene_precompute(self.h, None if params is None else C.byref(params)))
 
+    def update_vertices(self, verts, keep_curvature: bool = False):
+        """New positions for the same vertices, then a refit of the precomputed scene (see the C header)."""
+        v = np.ascontiguousarray(verts, np.float32)
+        assert v.shape == (self.n_verts, 3)
+        self.ctx._check(self.ctx.L.st_scene_update_vertices(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST,
+                                                            _lib.ST_REFIT_KEEP_CURVATURE if keep_curvature else 0))
+
     def curvature(self):
         G = np.empty(self.n_verts, np.float32)
         Cm = np.empty(self.n_tris, np.float32)

@@ -133,6 +133,7 @@ struct st_scene {
     SceneDev S;
     bool has_materials = false;
     uint64_t version = 0;
+    st::CurvParamsDev cp{};  // parameters of the last precompute (reused by refits)
 };
 
 // Entry of every call on a context: select its device and drop a stale, non-sticky error left by
@@ -145,7 +146,8 @@ static void enter(const st_ctx* c) {
 static void scene_free(st_scene* sc) {
     SceneDev& S = sc->S;
     for (DevBuf* b : {&S.verts, &S.tris, &S.tri_mat, &S.tri_obj, &S.nrm, &S.nodes, &S.tri_v, &S.G, &S.C, &S.mesh_tris,
-                      &S.mesh_off, &S.cdf, &S.n_samples, &S.sample_off})
+                      &S.mesh_off, &S.cdf, &S.n_samples, &S.sample_off, &S.bvh_child, &S.bvh_range, &S.bvh_par_i,
+                      &S.bvh_par_l, &S.bvh_perm, &S.bvh_wflag, &S.bvh_widx})
         st::release(*b);
     delete sc;
 }
@@ -369,7 +371,28 @@ st_status st_scene_precompute(st_scene* sc, const st_curv_params* params) {
     cudaError_t e = scene_build(sc->S, cp, c->stream, &mesh_err, &msg);
     if (e != cudaSuccess) return cuda_fail(c, e, "scene_precompute");
     if (mesh_err) return fail(c, ST_ERR_MESH, "scene_precompute: " + msg);
+    sc->cp = cp;
     sc->version = g_scene_version++;
+    return ST_OK;
+}
+
+st_status st_scene_update_vertices(st_scene* sc, const float* verts, int32_t mem, int32_t flags) {
+    if (!sc) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (!verts || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
+        return fail(c, ST_ERR_ARG, "scene_update_vertices: null pointer or bad memory kind");
+    if (!sc->S.built) return fail(c, ST_ERR_STATE, "scene_update_vertices: precompute first");
+    enter(c);
+    CKC(c, cudaMemcpyAsync(sc->S.verts.p, verts, (size_t)sc->S.n_verts * 12, kind_in(mem), c->stream),
+        "scene_update_vertices copy");
+    bool mesh_err = false;
+    std::string msg;
+    cudaError_t e = scene_build(sc->S, sc->cp, c->stream, &mesh_err, &msg, true,
+                                (flags & ST_REFIT_KEEP_CURVATURE) != 0);
+    sc->version = g_scene_version++;
+    if (e != cudaSuccess || mesh_err) sc->S.built = false;  // precompute again before the next simulate
+    if (e != cudaSuccess) return cuda_fail(c, e, "scene_update_vertices");
+    if (mesh_err) return fail(c, ST_ERR_MESH, "scene_update_vertices: " + msg);
     return ST_OK;
 }
 

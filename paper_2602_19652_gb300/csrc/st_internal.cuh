@@ -49,6 +49,10 @@ struct SceneDev {
     DevBuf tri_v;      // [T][3] float4 in leaf order; tri_v[3i].w = triangle index bits
     int32_t root = 0;  // child-ref encoding of the root
     int64_t n_nodes = 0;  // 4-wide nodes
+    // LBVH topology kept for refits: binary children, leaf ranges, parents, leaf order, wide-node flags
+    // and numbering
+    DevBuf bvh_child, bvh_range, bvh_par_i, bvh_par_l, bvh_perm, bvh_wflag, bvh_widx;
+    bool bvh_ready = false;
     float bounds_lo[3] = {0, 0, 0}, bounds_hi[3] = {0, 0, 0};
     // curvature and diffraction CDFs
     DevBuf G;          // [V] f32
@@ -101,8 +105,11 @@ struct CurvParamsDev {
 };
 // Validates indices and vertices (flags), computes normals, welds, curvature, C, CDFs, sample
 // counts and the LBVH.  Synchronises once.  Returns a CUDA error or sets *mesh_error.
-cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bool* mesh_error,
-                        std::string* msg);
+// refit: keep the LBVH topology of an earlier build (new vertex positions, same triangles): boxes,
+// wide nodes and leaf triangles are recomputed; keep_curvature: also keep curvature, metric, CDFs and
+// sample counts (valid for rigid motions of whole meshes)
+cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bool* mesh_error, std::string* msg,
+                        bool refit = false, bool keep_curvature = false);
 
 // ------------------------------------------------------------------ tracing (st_trace.cu)
 struct TraceArgs {

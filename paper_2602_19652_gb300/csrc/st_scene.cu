@@ -646,18 +646,21 @@ __global__ void k_reorder(const float* V, const int32_t* T, int64_t nt, const ui
 
 }  // namespace
 
-cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bool* mesh_error, std::string* msg) {
+cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bool* mesh_error, std::string* msg,
+                        bool refit, bool keep_curvature) {
     *mesh_error = false;
+    refit = refit && S.bvh_ready;
+    keep_curvature = keep_curvature && refit;
     const int64_t nv = S.n_verts, nt = S.n_tris;
     const float* V = ptr<float>(S.verts);
     const int32_t* T = ptr<int32_t>(S.tris);
     const int32_t* obj = ptr<int32_t>(S.tri_obj);
     // ---- scratch (freed at the end of the build)
-    DevBuf flags, canon, keys, vals, sort_scr, cnt, off, cursor, adj, Gc, cmax, sumQ, Q, S64, nsu, bnd, child, range,
-        par_i, par_l, boxes, visits, moff, range2, wscan_scr, wtotal;
+    DevBuf flags, canon, keys, vals, sort_scr, cnt, off, cursor, adj, Gc, cmax, sumQ, Q, S64, nsu, bnd, boxes, visits,
+        moff, wscan_scr, wtotal;
     auto cleanup = [&]() {
         for (DevBuf* b : {&flags, &canon, &keys, &vals, &sort_scr, &cnt, &off, &cursor, &adj, &Gc, &cmax, &sumQ, &Q,
-                          &S64, &nsu, &bnd, &child, &range, &par_i, &par_l, &boxes, &visits, &moff, &range2, &wscan_scr, &wtotal})
+                          &S64, &nsu, &bnd, &boxes, &visits, &moff, &wscan_scr, &wtotal})
             release(*b);
     };
     struct Guard {
@@ -688,118 +691,124 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
     k_normals<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<float>(S.nrm));
     CK(cudaGetLastError());
 
-    // ---- weld
-    CK(grow(canon, (size_t)nv * 4));
     CK(grow(keys, (size_t)nmax * 8));
     CK(grow(vals, (size_t)nmax * 4));
     CK(grow(sort_scr, sort_scratch_bytes(nmax) + scan_scratch_bytes(nmax + n_obj + 1)));
-    note_launch();
-    k_pos_keys<<<grid_for(nv, kB), kB, 0, s>>>(V, nv, ptr<uint64_t>(keys), ptr<uint32_t>(vals));
-    CK(cudaGetLastError());
-    CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), nv, 64, sort_scr.p, s));
-    note_launch();
-    k_weld_runs<<<grid_for(nv, kB), kB, 0, s>>>(V, nv, ptr<uint64_t>(keys), ptr<uint32_t>(vals), ptr<int32_t>(canon));
-    CK(cudaGetLastError());
-
-    // ---- adjacency CSR over canonical vertices
-    CK(grow(cnt, (size_t)(nv + 1) * 4));
-    CK(grow(off, (size_t)(nv + 1) * 4));
-    CK(grow(cursor, (size_t)(nv + 1) * 4));
-    CK(grow(adj, (size_t)std::max<int64_t>(3 * nt, 1) * 4));
-    CK(cudaMemsetAsync(cnt.p, 0, (size_t)(nv + 1) * 4, s));
-    CK(cudaMemsetAsync(cursor.p, 0, (size_t)(nv + 1) * 4, s));
-    note_launch();
-    k_adj_count<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(canon), T, nt, ptr<uint32_t>(cnt));
-    CK(cudaGetLastError());
-    CK(exclusive_scan_u32(ptr<uint32_t>(cnt), ptr<uint32_t>(off), nv + 1, nullptr, sort_scr.p, s));
-    note_launch();
-    k_adj_fill<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(canon), T, nt, ptr<uint32_t>(off), ptr<uint32_t>(cursor),
-                                              ptr<int32_t>(adj));
-    CK(cudaGetLastError());
-    note_launch();
-    k_adj_sort<<<grid_for(nv, kB), kB, 0, s>>>(nv, ptr<uint32_t>(off), ptr<int32_t>(adj));
-    CK(cudaGetLastError());
-
-    // ---- curvature and metric
-    CK(grow(Gc, (size_t)nv * 4));
-    CK(grow(S.G, (size_t)nv * 4));
-    CK(grow(S.C, (size_t)nt * 4));
-    note_launch();
-    k_curvature<<<grid_for(nv, kB), kB, 0, s>>>(V, nv, T, ptr<int32_t>(canon), ptr<uint32_t>(off), ptr<int32_t>(adj),
-                                               ptr<float>(Gc));
-    CK(cudaGetLastError());
-    note_launch();
-    k_expand_G<<<grid_for(nv, kB), kB, 0, s>>>(ptr<int32_t>(canon), nv, ptr<float>(Gc), ptr<float>(S.G));
-    CK(cudaGetLastError());
-    CK(grow(cmax, (size_t)(n_obj + 1) * 4));
-    CK(cudaMemsetAsync(cmax.p, 0, (size_t)(n_obj + 1) * 4, s));
-    note_launch();
-    k_metric<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<int32_t>(canon), ptr<float>(S.G), cp.eta, cp.area_ref,
-                                            ptr<float>(S.C), ptr<uint32_t>(cmax), obj);
-    CK(cudaGetLastError());
-
-    // ---- per-mesh triangle lists (ascending), integer weights, CDFs
-    CK(grow(moff, (size_t)(n_obj + 2) * 4));
-    CK(cudaMemsetAsync(cnt.p, 0, (size_t)(n_obj + 1) * 4, s));
-    CK(cudaMemsetAsync(cursor.p, 0, (size_t)(n_obj + 1) * 4, s));
-    note_launch();
-    k_mesh_count<<<grid_for(nt, kB), kB, 0, s>>>(obj, nt, ptr<uint32_t>(cnt));
-    CK(cudaGetLastError());
-    CK(exclusive_scan_u32(ptr<uint32_t>(cnt), ptr<uint32_t>(moff), n_obj + 1, nullptr, sort_scr.p, s));
-    CK(grow(S.mesh_tris, (size_t)nt * 4));
-    {
-        // (mesh, triangle) keys sorted: triangles grouped by mesh, ascending inside a mesh
-        int mesh_bits = 1;
-        while ((1ll << mesh_bits) <= (int64_t)n_obj) ++mesh_bits;
+    if (!keep_curvature) {
+        // ---- weld
+        CK(grow(canon, (size_t)nv * 4));
+        CK(grow(keys, (size_t)nmax * 8));
+        CK(grow(vals, (size_t)nmax * 4));
+        CK(grow(sort_scr, sort_scratch_bytes(nmax) + scan_scratch_bytes(nmax + n_obj + 1)));
         note_launch();
-        k_mesh_keys<<<grid_for(nt, kB), kB, 0, s>>>(obj, nt, ptr<uint64_t>(keys), ptr<uint32_t>(vals));
+        k_pos_keys<<<grid_for(nv, kB), kB, 0, s>>>(V, nv, ptr<uint64_t>(keys), ptr<uint32_t>(vals));
         CK(cudaGetLastError());
-        CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), nt, 32 + mesh_bits, sort_scr.p, s));
-        CK(cudaMemcpyAsync(S.mesh_tris.p, vals.p, (size_t)nt * 4, cudaMemcpyDeviceToDevice, s));
-    }
-    CK(grow(sumQ, (size_t)(n_obj + 1) * 8));
-    CK(cudaMemsetAsync(sumQ.p, 0, (size_t)(n_obj + 1) * 8, s));
-    CK(grow(Q, (size_t)nmax * 8));
-    CK(grow(S64, (size_t)nmax * 8));
-    note_launch();
-    k_quantize<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(S.mesh_tris), nt, obj, ptr<float>(S.C), ptr<uint32_t>(cmax),
-                                              ptr<uint64_t>(Q), ptr<unsigned long long>(sumQ));
-    CK(cudaGetLastError());
-    note_launch();
-    k_dither<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(S.mesh_tris), nt, obj, ptr<uint32_t>(moff),
-                                            ptr<unsigned long long>(sumQ), cp.dither, cp.seed, ptr<uint64_t>(Q));
-    CK(cudaGetLastError());
-    CK(inclusive_scan_u64(ptr<uint64_t>(Q), ptr<uint64_t>(S64), nt, sort_scr.p, s));
-    CK(grow(S.cdf, (size_t)nt * 8));
-    note_launch();
-    k_cdf_fix<<<grid_for(nt, kB), kB, 0, s>>>(ptr<uint64_t>(S64), nt, ptr<int32_t>(S.mesh_tris), obj,
-                                             ptr<uint32_t>(moff), ptr<uint64_t>(S.cdf));
-    CK(cudaGetLastError());
-    // mesh offsets as int64 for the sampling kernels
-    CK(grow(S.mesh_off, (size_t)(n_obj + 1) * 8));
-    {
-        std::vector<uint32_t> h32(n_obj + 1);
-        CK(cudaMemcpyAsync(h32.data(), moff.p, (size_t)(n_obj + 1) * 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        std::vector<int64_t> h64(h32.begin(), h32.end());
-        CK(cudaMemcpyAsync(S.mesh_off.p, h64.data(), (size_t)(n_obj + 1) * 8, cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-    }
-    // sample counts
-    CK(grow(nsu, (size_t)(n_obj + 1) * 8));
-    CK(cudaMemsetAsync(nsu.p, 0, (size_t)(n_obj + 1) * 8, s));
-    note_launch();
-    k_hc_vertices<<<grid_for(nv, kB), kB, 0, s>>>(nv, ptr<int32_t>(canon), ptr<uint32_t>(off), ptr<int32_t>(adj), obj,
-                                                 ptr<float>(S.C), ptr<uint32_t>(cmax), cp.hc_frac,
-                                                 cp.samples_per_vertex, ptr<unsigned long long>(nsu));
-    CK(cudaGetLastError());
-    CK(grow(S.n_samples, (size_t)(n_obj + 1) * 8));
-    CK(grow(S.sample_off, (size_t)(n_obj + 1) * 8));
-    note_launch();
-    k_sample_counts<<<1, 1, 0, s>>>(n_obj, ptr<uint32_t>(moff), ptr<uint64_t>(S.cdf), ptr<unsigned long long>(nsu),
-                                    cp.budget, ptr<int64_t>(S.n_samples), ptr<int64_t>(S.sample_off));
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(&S.total_samples, ptr<int64_t>(S.sample_off) + n_obj, 8, cudaMemcpyDeviceToHost, s));
+        CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), nv, 64, sort_scr.p, s));
+        note_launch();
+        k_weld_runs<<<grid_for(nv, kB), kB, 0, s>>>(V, nv, ptr<uint64_t>(keys), ptr<uint32_t>(vals), ptr<int32_t>(canon));
+        CK(cudaGetLastError());
+
+        // ---- adjacency CSR over canonical vertices
+        CK(grow(cnt, (size_t)(nv + 1) * 4));
+        CK(grow(off, (size_t)(nv + 1) * 4));
+        CK(grow(cursor, (size_t)(nv + 1) * 4));
+        CK(grow(adj, (size_t)std::max<int64_t>(3 * nt, 1) * 4));
+        CK(cudaMemsetAsync(cnt.p, 0, (size_t)(nv + 1) * 4, s));
+        CK(cudaMemsetAsync(cursor.p, 0, (size_t)(nv + 1) * 4, s));
+        note_launch();
+        k_adj_count<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(canon), T, nt, ptr<uint32_t>(cnt));
+        CK(cudaGetLastError());
+        CK(exclusive_scan_u32(ptr<uint32_t>(cnt), ptr<uint32_t>(off), nv + 1, nullptr, sort_scr.p, s));
+        note_launch();
+        k_adj_fill<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(canon), T, nt, ptr<uint32_t>(off), ptr<uint32_t>(cursor),
+                                                  ptr<int32_t>(adj));
+        CK(cudaGetLastError());
+        note_launch();
+        k_adj_sort<<<grid_for(nv, kB), kB, 0, s>>>(nv, ptr<uint32_t>(off), ptr<int32_t>(adj));
+        CK(cudaGetLastError());
+
+        // ---- curvature and metric
+        CK(grow(Gc, (size_t)nv * 4));
+        CK(grow(S.G, (size_t)nv * 4));
+        CK(grow(S.C, (size_t)nt * 4));
+        note_launch();
+        k_curvature<<<grid_for(nv, kB), kB, 0, s>>>(V, nv, T, ptr<int32_t>(canon), ptr<uint32_t>(off), ptr<int32_t>(adj),
+                                                   ptr<float>(Gc));
+        CK(cudaGetLastError());
+        note_launch();
+        k_expand_G<<<grid_for(nv, kB), kB, 0, s>>>(ptr<int32_t>(canon), nv, ptr<float>(Gc), ptr<float>(S.G));
+        CK(cudaGetLastError());
+        CK(grow(cmax, (size_t)(n_obj + 1) * 4));
+        CK(cudaMemsetAsync(cmax.p, 0, (size_t)(n_obj + 1) * 4, s));
+        note_launch();
+        k_metric<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<int32_t>(canon), ptr<float>(S.G), cp.eta, cp.area_ref,
+                                                ptr<float>(S.C), ptr<uint32_t>(cmax), obj);
+        CK(cudaGetLastError());
+
+        // ---- per-mesh triangle lists (ascending), integer weights, CDFs
+        CK(grow(moff, (size_t)(n_obj + 2) * 4));
+        CK(cudaMemsetAsync(cnt.p, 0, (size_t)(n_obj + 1) * 4, s));
+        CK(cudaMemsetAsync(cursor.p, 0, (size_t)(n_obj + 1) * 4, s));
+        note_launch();
+        k_mesh_count<<<grid_for(nt, kB), kB, 0, s>>>(obj, nt, ptr<uint32_t>(cnt));
+        CK(cudaGetLastError());
+        CK(exclusive_scan_u32(ptr<uint32_t>(cnt), ptr<uint32_t>(moff), n_obj + 1, nullptr, sort_scr.p, s));
+        CK(grow(S.mesh_tris, (size_t)nt * 4));
+        {
+            // (mesh, triangle) keys sorted: triangles grouped by mesh, ascending inside a mesh
+            int mesh_bits = 1;
+            while ((1ll << mesh_bits) <= (int64_t)n_obj) ++mesh_bits;
+            note_launch();
+            k_mesh_keys<<<grid_for(nt, kB), kB, 0, s>>>(obj, nt, ptr<uint64_t>(keys), ptr<uint32_t>(vals));
+            CK(cudaGetLastError());
+            CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), nt, 32 + mesh_bits, sort_scr.p, s));
+            CK(cudaMemcpyAsync(S.mesh_tris.p, vals.p, (size_t)nt * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        CK(grow(sumQ, (size_t)(n_obj + 1) * 8));
+        CK(cudaMemsetAsync(sumQ.p, 0, (size_t)(n_obj + 1) * 8, s));
+        CK(grow(Q, (size_t)nmax * 8));
+        CK(grow(S64, (size_t)nmax * 8));
+        note_launch();
+        k_quantize<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(S.mesh_tris), nt, obj, ptr<float>(S.C), ptr<uint32_t>(cmax),
+                                                  ptr<uint64_t>(Q), ptr<unsigned long long>(sumQ));
+        CK(cudaGetLastError());
+        note_launch();
+        k_dither<<<grid_for(nt, kB), kB, 0, s>>>(ptr<int32_t>(S.mesh_tris), nt, obj, ptr<uint32_t>(moff),
+                                                ptr<unsigned long long>(sumQ), cp.dither, cp.seed, ptr<uint64_t>(Q));
+        CK(cudaGetLastError());
+        CK(inclusive_scan_u64(ptr<uint64_t>(Q), ptr<uint64_t>(S64), nt, sort_scr.p, s));
+        CK(grow(S.cdf, (size_t)nt * 8));
+        note_launch();
+        k_cdf_fix<<<grid_for(nt, kB), kB, 0, s>>>(ptr<uint64_t>(S64), nt, ptr<int32_t>(S.mesh_tris), obj,
+                                                 ptr<uint32_t>(moff), ptr<uint64_t>(S.cdf));
+        CK(cudaGetLastError());
+        // mesh offsets as int64 for the sampling kernels
+        CK(grow(S.mesh_off, (size_t)(n_obj + 1) * 8));
+        {
+            std::vector<uint32_t> h32(n_obj + 1);
+            CK(cudaMemcpyAsync(h32.data(), moff.p, (size_t)(n_obj + 1) * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            std::vector<int64_t> h64(h32.begin(), h32.end());
+            CK(cudaMemcpyAsync(S.mesh_off.p, h64.data(), (size_t)(n_obj + 1) * 8, cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        // sample counts
+        CK(grow(nsu, (size_t)(n_obj + 1) * 8));
+        CK(cudaMemsetAsync(nsu.p, 0, (size_t)(n_obj + 1) * 8, s));
+        note_launch();
+        k_hc_vertices<<<grid_for(nv, kB), kB, 0, s>>>(nv, ptr<int32_t>(canon), ptr<uint32_t>(off), ptr<int32_t>(adj), obj,
+                                                     ptr<float>(S.C), ptr<uint32_t>(cmax), cp.hc_frac,
+                                                     cp.samples_per_vertex, ptr<unsigned long long>(nsu));
+        CK(cudaGetLastError());
+        CK(grow(S.n_samples, (size_t)(n_obj + 1) * 8));
+        CK(grow(S.sample_off, (size_t)(n_obj + 1) * 8));
+        note_launch();
+        k_sample_counts<<<1, 1, 0, s>>>(n_obj, ptr<uint32_t>(moff), ptr<uint64_t>(S.cdf), ptr<unsigned long long>(nsu),
+                                        cp.budget, ptr<int64_t>(S.n_samples), ptr<int64_t>(S.sample_off));
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&S.total_samples, ptr<int64_t>(S.sample_off) + n_obj, 8, cudaMemcpyDeviceToHost, s));
+
+    }  // !keep_curvature
 
     // ---- LBVH
     CK(grow(bnd, 64));
@@ -810,10 +819,14 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
     note_launch();
     k_bounds<<<grid_for(nv, kB, 152 * 4), kB, 0, s>>>(V, nv, ptr<uint32_t>(bnd));
     CK(cudaGetLastError());
-    note_launch();
-    k_morton<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(bnd), ptr<uint64_t>(keys), ptr<uint32_t>(vals));
-    CK(cudaGetLastError());
-    CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), nt, 63, sort_scr.p, s));
+    if (!refit) {
+        note_launch();
+        k_morton<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(bnd), ptr<uint64_t>(keys), ptr<uint32_t>(vals));
+        CK(cudaGetLastError());
+        CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), nt, 63, sort_scr.p, s));
+        CK(grow(S.bvh_perm, (size_t)nt * 4));
+        CK(cudaMemcpyAsync(S.bvh_perm.p, vals.p, (size_t)nt * 4, cudaMemcpyDeviceToDevice, s));
+    }
     uint32_t hb[6];
     CK(cudaMemcpyAsync(hb, bnd.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -835,48 +848,58 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
         const int n = (int)nt;
         CK(grow(S.tri_v, (size_t)nt * 3 * sizeof(float4)));
         note_launch();
-        k_reorder<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(vals), ptr<float4>(S.tri_v));
+        k_reorder<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(S.bvh_perm), ptr<float4>(S.tri_v));
         CK(cudaGetLastError());
         if (n == 1 || n <= kLeafMax) {
             CK(grow(S.nodes, 8 * sizeof(float4)));
             S.root = leaf_ref(0, n);
         } else {
             S.root = 0;
-            CK(grow(child, (size_t)(n - 1) * sizeof(int2)));
-            CK(grow(range, (size_t)(n - 1) * sizeof(int2)));
-            CK(grow(par_i, (size_t)n * 4));
-            CK(grow(par_l, (size_t)n * 4));
+            int2* child_p = ptr<int2>(S.bvh_child);
+            int2* range_p = ptr<int2>(S.bvh_range);
+            if (!refit) {
+                CK(grow(S.bvh_child, (size_t)(n - 1) * sizeof(int2)));
+                CK(grow(S.bvh_range, (size_t)(n - 1) * sizeof(int2)));
+                CK(grow(S.bvh_par_i, (size_t)n * 4));
+                CK(grow(S.bvh_par_l, (size_t)n * 4));
+                child_p = ptr<int2>(S.bvh_child);
+                range_p = ptr<int2>(S.bvh_range);
+                note_launch();
+                k_karras<<<grid_for(n - 1, kB), kB, 0, s>>>(ptr<uint64_t>(keys), n, child_p, range_p,
+                                                            ptr<int32_t>(S.bvh_par_i), ptr<int32_t>(S.bvh_par_l));
+                CK(cudaGetLastError());
+            }
             CK(grow(boxes, (size_t)(n - 1) * 2 * sizeof(Box)));
             CK(grow(visits, (size_t)(n - 1) * 4));
             CK(cudaMemsetAsync(visits.p, 0, (size_t)(n - 1) * 4, s));
             note_launch();
-            k_karras<<<grid_for(n - 1, kB), kB, 0, s>>>(ptr<uint64_t>(keys), n, ptr<int2>(child), ptr<int2>(range),
-                                                        ptr<int32_t>(par_i), ptr<int32_t>(par_l));
+            k_boxes<<<grid_for(n, kB), kB, 0, s>>>(V, T, n, ptr<uint32_t>(S.bvh_perm), child_p,
+                                                   ptr<int32_t>(S.bvh_par_i), ptr<int32_t>(S.bvh_par_l), pad,
+                                                   ptr<Box>(boxes), ptr<uint32_t>(visits), ptr<uint32_t>(flags));
             CK(cudaGetLastError());
+            if (!refit) {
+                // 4-wide BVH: flag the binary nodes that become wide nodes, number them
+                CK(grow(S.bvh_wflag, (size_t)(n - 1) * 4));
+                CK(grow(S.bvh_widx, (size_t)(n - 1) * 4));
+                CK(grow(wscan_scr, scan_scratch_bytes(n - 1)));
+                CK(grow(wtotal, 4));
+                note_launch();
+                k_wide_flags<<<grid_for(n - 1, kB), kB, 0, s>>>(n, range_p, ptr<int32_t>(S.bvh_par_i),
+                                                                ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(flags));
+                CK(cudaGetLastError());
+                CK(exclusive_scan_u32(ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(S.bvh_widx), n - 1,
+                                      ptr<uint32_t>(wtotal), wscan_scr.p, s));
+                uint32_t n4 = 0;
+                CK(cudaMemcpyAsync(&n4, wtotal.p, 4, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                CK(grow(S.nodes, (size_t)std::max<uint32_t>(n4, 1) * 8 * sizeof(float4)));
+                S.n_nodes = n4;
+            }
             note_launch();
-            k_boxes<<<grid_for(n, kB), kB, 0, s>>>(V, T, n, ptr<uint32_t>(vals), ptr<int2>(child), ptr<int32_t>(par_i),
-                                                   ptr<int32_t>(par_l), pad, ptr<Box>(boxes), ptr<uint32_t>(visits),
-                                                   ptr<uint32_t>(flags));
+            k_pack_wide<<<grid_for(n - 1, kB), kB, 0, s>>>(n, child_p, range_p, ptr<Box>(boxes),
+                                                           ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(S.bvh_widx),
+                                                           ptr<float4>(S.nodes));
             CK(cudaGetLastError());
-            // 4-wide BVH: flag the binary nodes that become wide nodes, number them, pack
-            uint32_t* wflag = ptr<uint32_t>(visits);  // reuses the climb counters (no longer needed)
-            CK(grow(range2, (size_t)(n - 1) * 4));
-            CK(grow(wscan_scr, scan_scratch_bytes(n - 1)));
-            CK(grow(wtotal, 4));
-            note_launch();
-            k_wide_flags<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(range), ptr<int32_t>(par_i), wflag,
-                                                            ptr<uint32_t>(flags));
-            CK(cudaGetLastError());
-            CK(exclusive_scan_u32(wflag, ptr<uint32_t>(range2), n - 1, ptr<uint32_t>(wtotal), wscan_scr.p, s));
-            uint32_t n4 = 0;
-            CK(cudaMemcpyAsync(&n4, wtotal.p, 4, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            CK(grow(S.nodes, (size_t)std::max<uint32_t>(n4, 1) * 8 * sizeof(float4)));
-            note_launch();
-            k_pack_wide<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(child), ptr<int2>(range), ptr<Box>(boxes),
-                                                           wflag, ptr<uint32_t>(range2), ptr<float4>(S.nodes));
-            CK(cudaGetLastError());
-            S.n_nodes = n4;
         }
     }
     CK(cudaMemcpyAsync(&hflags, flags.p, 4, cudaMemcpyDeviceToHost, s));
@@ -887,6 +910,7 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
         return cudaSuccess;
     }
     S.built = true;
+    S.bvh_ready = true;
     return cudaSuccess;
 }
 
