@@ -235,6 +235,18 @@ st_status st_simulate_batch(st_ctx* ctx, int32_t n_jobs, const st_job* jobs, con
  * emitter, receivers and frequency grid with the sample job's (omni).  Synchronises. */
 st_status st_autotune(st_ctx* ctx, const st_job* sample, const st_sim_params* params, st_tune* out);
 
+/* Emitter ray sets written on the device, float32 [n][3] unit directions in the emitter frame, for
+ * st_set_emitter (ST_MEM_DEVICE).  ST_RAYS_FIBONACCI: the spherical Fibonacci lattice, z_i = 1 -
+ * (2i + 1) / n, phi_i = i pi (3 - sqrt 5).  ST_RAYS_ZONAL: the centre points of the recursive zonal
+ * equal-area partition of the sphere into n regions (Leopardi 2006), the paper's ray set (Sec.
+ * III-C): two polar caps, collars of equal-area regions, each region's centre at the midpoint of its
+ * colatitude and longitude ranges, collar i+1 rotated by half a region against collar i.  Directions
+ * are evaluated in float64 and rounded once.  Synchronises (the zone table is uploaded).  Errors:
+ * ST_ERR_ARG for a null pointer, n < 1 or an unknown kind. */
+#define ST_RAYS_FIBONACCI 0
+#define ST_RAYS_ZONAL 1
+st_status st_ray_directions(st_ctx* ctx, int32_t kind, int64_t n, float* out);
+
 /* Impulse responses and received signals (Eq. 5-6, 9-10, 13 and the signal equation of Sec. III-F).
  * Every path's transfer function is M(f) e^{+j 2 pi f r / c}; summed over paths, a component's
  * impulse response is the inverse Fourier transform of its spectrum, the components add, and the

@@ -158,6 +158,15 @@ class Context:
         self._check(self.L.st_get_direct_visibility(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST))
         return v
 
+    # -------------------------------------------------------------- ray sets
+    def ray_directions(self, n: int, kind: str = "zonal") -> torch.Tensor:
+        """float32 [n][3] emitter-frame directions on the device: "zonal" (the paper's equal-area set)
+        or "fibonacci"."""
+        k = {"fibonacci": _lib.ST_RAYS_FIBONACCI, "zonal": _lib.ST_RAYS_ZONAL}[kind]
+        out = torch.empty((int(n), 3), dtype=torch.float32, device=f"cuda:{self.device}")
+        self._check(self.L.st_ray_directions(self.h, k, int(n), C.c_void_p(out.data_ptr())))
+        return out
+
     # -------------------------------------------------------------- signals
     def impulse_response(self, spectra: torch.Tensor, f_lo: float, f_hi: float, fs: float, n_samples: int,
                          window: torch.Tensor | None = None, call: torch.Tensor | None = None,

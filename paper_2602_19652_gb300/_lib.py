@@ -17,6 +17,7 @@ ST_OK = 0
 ST_MEM_HOST, ST_MEM_DEVICE = 0, 1
 ST_IR_PER_COMPONENT = 1
 ST_REFIT_KEEP_CURVATURE = 1
+ST_RAYS_FIBONACCI, ST_RAYS_ZONAL = 0, 1
 ST_COMP_SPECULAR, ST_COMP_DIFFRACTION, ST_COMP_DIRECT = 1, 2, 4
 
 
@@ -76,6 +77,7 @@ SIGNATURES = {
     "st_simulate_batch": (I32, [P, I32, P, P, P]),
     "st_autotune": (I32, [P, P, P, P]),
     "st_scene_update_vertices": (I32, [P, P, I32, I32]),
+    "st_ray_directions": (I32, [P, I32, I64, P]),
     "st_impulse_response": (I32, [P, P, I32, I32, I32, F64, F64, F64, I32, P, P, I32, I32, P]),
     "st_accumulate_specular_noalloc": (I32, [P, P, P, P, P, I64, I32, P, P, I32, I32, F64, F64, I32, I32, P, P, P,
                                              P, P, P]),

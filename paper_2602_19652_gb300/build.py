@@ -31,6 +31,7 @@ UNITS = {
     "st_adjoint.cu": [],
     "st_noalloc.cu": [],
     "st_signal.cu": [],
+    "st_rays.cu": ["-fmad=false"],
 }
 
 

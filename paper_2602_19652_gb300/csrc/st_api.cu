@@ -102,6 +102,7 @@ struct st_ctx {
     BatchState* batch = nullptr;
     std::vector<st_scene*> scenes;  // scenes loaded into this context (freed by st_destroy)
     DevBuf sig_e, sig_g;             // impulse responses: call spectrum [F], combined spectra [rows][F]
+    DevBuf ray_tab;                  // zone table of the zonal ray set
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -262,7 +263,8 @@ st_status st_destroy(st_ctx* c) {
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
                           &P->meta, &P->dep})
             release(*b);
-    for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->sig_e, &c->sig_g})
+    for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->sig_e, &c->sig_g,
+                      &c->ray_tab})
         release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -1110,6 +1112,14 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
     }
     if (want_pos)
         CKC(c, adjoint_pos(micp, mic_slices, emitp, emit_slices, M, grad_mic, grad_emitter, s), "adjoint reduce");
+    return ST_OK;
+}
+
+st_status st_ray_directions(st_ctx* c, int32_t kind, int64_t n, float* out) {
+    if (!c || !out || n < 1 || (kind != ST_RAYS_FIBONACCI && kind != ST_RAYS_ZONAL) || n >= ((int64_t)1 << 40))
+        return fail(c, ST_ERR_ARG, "ray_directions: null output, n < 1 or unknown kind");
+    enter(c);
+    CKC(c, ray_directions(kind, n, out, c->ray_tab, c->stream), "ray directions");
     return ST_OK;
 }
 

@@ -256,6 +256,8 @@ cudaError_t accumulate(const AccumArgs& a, cudaStream_t s);
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s);
 int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb, int32_t tile_tp = 0,
                      int32_t tile_kb = 0);
+// emitter ray sets (st_rays.cu): kind 0 spherical Fibonacci, 1 zonal equal-area centres
+cudaError_t ray_directions(int kind, int64_t n, float* out, DevBuf& scratch, cudaStream_t s);
 // impulse responses / received signals from accumulated spectra (st_signal.cu)
 cudaError_t signal_response(const float2* S, int n_comp, int M, int F, double f_lo, double f_hi, double fs,
                             int n_samples, const float* window, const float* call, int call_len, int per_comp,
