@@ -79,7 +79,7 @@ def _declare(L):
                               I32, P, I32, P, I32, P]
     L.ora_spectra.restype = C.c_int
     L.ora_spectra_grad.argtypes = [C.POINTER(SpecParams), I64, I32, P, P, P, P, P, P, P, I64, P, P, P, P,
-                                   P, P, P, P]
+                                   P, P, P, P, P]
     L.ora_spectra_grad.restype = C.c_int
 
 
@@ -229,11 +229,11 @@ class _Keep:
 
 
 def spec_params(wl, mics=None, k_band=None, emitter=None, c=343.0, a0=0.0, a1_per_khz=0.033,
-                reflection_mode=0, direct_gain=1.0):
+                reflection_mode=0, direct_gain=1.0, beta_band=None):
     keep = _Keep()
     keep.band = _c(wl.band_hz, np.float32)
     keep.k = _c(wl.k_band if k_band is None else k_band, np.float32)
-    keep.beta = _c(wl.beta_band, np.float32)
+    keep.beta = _c(wl.beta_band if beta_band is None else beta_band, np.float32)
     keep.diff = _c(wl.diff_band, np.float32)
     keep.mics = _c(wl.mics if mics is None else mics, np.float32)
     keep.s = _c(wl.emitter if emitter is None else emitter, np.float32)
@@ -275,8 +275,10 @@ def spectra(params, rec, dirs, tri_mat, cand_tri=None, cand_p=None, cand_keep=No
     return out[..., 0] + 1j * out[..., 1]
 
 
-def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand_keep=None, direct_vis=None):
-    """G: complex [3][M][F] = dL/dRe S + j dL/dIm S.  Returns (dk [n_mat][n_bands], dmic [M][3], demit [3])."""
+def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand_keep=None, direct_vis=None,
+                 with_beta=False):
+    """G: complex [3][M][F] = dL/dRe S + j dL/dIm S.  Returns (dk [n_mat][n_bands], dmic [M][3], demit [3]),
+    and dbeta [n_mat][n_bands] (lobe widths, specular paths) as a fourth item when with_beta."""
     P_ = params.P
     N, B = rec["tri"].shape
     dirs, tm = _c(dirs, np.float32), _c(tri_mat, np.int32)
@@ -287,12 +289,13 @@ def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand
     dk = np.zeros((P_.n_mat, P_.n_bands), np.float64)
     dmic = np.zeros((P_.M, 3), np.float64)
     demit = np.zeros(3, np.float64)
+    dbeta = np.zeros((P_.n_mat, P_.n_bands), np.float64) if with_beta else None
     rc = lib().ora_spectra_grad(C.byref(P_), N, B, _p(rec["tri"]), _p(rec["p"]), _p(rec["d"]), _p(rec["r"]),
                                 _p(rec["los"]), _p(dirs), _p(tm), K, _p(ct), _p(cp), _p(ck), _p(dv), _p(Gr),
-                                _p(dk), _p(dmic), _p(demit))
+                                _p(dk), _p(dmic), _p(demit), _p(dbeta))
     if rc != 0:
         raise ValueError("oracle gradient needs omni emitter and microphones")
-    return dk, dmic, demit
+    return (dk, dmic, demit, dbeta) if with_beta else (dk, dmic, demit)
 
 
 # ------------------------------------------------------------------------------------ pipeline

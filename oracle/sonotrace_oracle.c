@@ -1088,10 +1088,11 @@ ORA_API int ora_spectra_grad(const OraSpecParams* P, int64_t N, int32_t B, const
                              const float* rec_d, const double* rec_r, const uint8_t* rec_los, const float* dirs,
                              const int32_t* tri_mat, int64_t K, const int32_t* cand_tri, const float* cand_p,
                              const uint8_t* cand_keep, const uint8_t* direct_vis, const double* G,
-                             double* dk, double* dmic, double* demit) {
+                             double* dk, double* dmic, double* demit, double* dbeta) {
     if (P->emit_table || P->mic_tables) return -1;
     int F = P->F, M = P->M;
     memset(dk, 0, sizeof(double) * (size_t)P->n_mat * P->n_bands);
+    if (dbeta) memset(dbeta, 0, sizeof(double) * (size_t)P->n_mat * P->n_bands);
     memset(dmic, 0, sizeof(double) * 3 * (size_t)M);
     memset(demit, 0, sizeof(double) * 3);
     for (int m = 0; m < M; ++m) {
@@ -1155,6 +1156,20 @@ ORA_API int ora_spectra_grad(const OraSpecParams* P, int64_t N, int32_t B, const
                         }
                     }
                     double A = base * kc;
+                    /* lobe widths: lobe = exp(-gamma^2 g), g = (1 - w) / (2 beta_b0^2) + w / (2 beta_b1^2)
+                     * => d lobe / d beta_b = lobe gamma^2 weight_b / beta_b^3 (last hit's material) */
+                    if (dbeta) {
+                        const float* brow = P->beta_band + (int64_t)mj * P->n_bands;
+                        double d = A * re_gz * gm * gm;
+                        if (P->n_bands == 1) {
+                            double bb = (double)brow[0];
+                            dbeta[(int64_t)mj * P->n_bands] += d / (bb * bb * bb);
+                        } else {
+                            double bl = (double)brow[b0], bh = (double)brow[b0 + 1];
+                            dbeta[(int64_t)mj * P->n_bands + b0] += d * (1.0 - w) / (bl * bl * bl);
+                            dbeta[(int64_t)mj * P->n_bands + b0 + 1] += d * w / (bh * bh * bh);
+                        }
+                    }
                     /* dA/dr = A (-2/r - alpha ln10 / 20); dphase/dr = 2 pi f / c */
                     double dlnA_dr = -2.0 / r - alpha * M_LN10 / 20.0;
                     acc_r += A * (dlnA_dr * re_gz - (2.0 * M_PI * f / P->c) * im_gz);

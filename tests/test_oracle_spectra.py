@@ -178,3 +178,39 @@ def test_gradient_matches_central_differences():
         terms = np.concatenate([(dk * hk * vk).ravel(), (dmic * hx * vm).ravel(), demit * hx * vs])
         an = terms.sum()
         assert abs(fd - an) <= 1e-6 * np.abs(terms).sum(), (fd, an)
+
+
+def test_beta_gradient_matches_central_differences():
+    """Lobe-width gradient (specular paths, the last hit's material) vs central differences with
+    Richardson extrapolation; beta values and steps exactly representable in float32."""
+    wl, out, ct, cp, keep = _grad_problem()
+    rec = out["rec"]
+    q = lambda x, e: np.round(np.asarray(x, np.float64) * 2.0 ** e) / 2.0 ** e
+    b0 = q(wl.beta_band, 14)
+    rng = np.random.default_rng(405)
+
+    def spectra_at(b):
+        assert np.array_equal(b.astype(np.float32).astype(np.float64), b)
+        p = oracle.spec_params(wl, beta_band=b.astype(np.float32))
+        return oracle.spectra(p, rec, wl.dirs, wl.tri_mat)
+
+    S0 = spectra_at(b0)
+    St = spectra_at(q(b0 * 1.2, 14))
+    G = 2.0 * (S0 - St)
+    p = oracle.spec_params(wl, beta_band=b0.astype(np.float32))
+    _, _, _, dbeta = oracle.spectra_grad(p, rec, wl.dirs, wl.tri_mat, G, with_beta=True)
+    assert np.abs(dbeta).max() > 0
+
+    def loss(b):
+        return float(np.sum(np.abs(spectra_at(b) - St) ** 2))
+
+    for _ in range(10):
+        v = q(rng.uniform(-1, 1, b0.shape), 5)
+
+        def D(h):
+            return (loss(b0 + h * v) - loss(b0 - h * v)) / 2.0
+
+        h = 2.0 ** -12
+        fd = (8.0 * D(h / 2) - D(h)) / 3.0
+        terms = (dbeta * h * v).ravel()
+        assert abs(fd - terms.sum()) <= 1e-6 * np.abs(terms).sum(), (fd, terms.sum())
