@@ -195,6 +195,10 @@ st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
  * order.  Stream-ordered; allocates reduction buffers on first use. */
 st_status st_backward(st_ctx* ctx, st_scene* scene, const void* grad_spectra, float* grad_k, float* grad_mic,
                       float* grad_emitter);
+/* Adjoint with respect to the lobe widths: grad_beta [n_mat][n_bands] device float32, the gradient of
+ * the loss through the specular lobe exp(-gamma^2 / (2 beta^2)) of each path's last hit (the lobe
+ * exponent interpolated between bands through 1 / (2 beta^2)).  Same conditions as st_backward. */
+st_status st_backward_beta(st_ctx* ctx, st_scene* scene, const void* grad_spectra, float* grad_beta);
 
 /* Batched form: many poses (over one or more precomputed scenes) simulated together.  Every stage
  * runs over all jobs in one launch (one per bounce level for tracing), and the per-job accumulations

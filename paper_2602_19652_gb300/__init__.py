@@ -153,6 +153,13 @@ class Context:
         self._check(self.L.st_backward(self.h, scene.h, vp(g), vp(gk), vp(gm), vp(ge)))
         return gk, gm, ge
 
+    def backward_beta(self, scene: "Scene", grad_spectra: torch.Tensor, n_mat: int, n_bands: int):
+        """dL/dbeta [n_mat][n_bands] (lobe widths of the specular paths) for grad_spectra = dL/dRe S + j dL/dIm S."""
+        g = grad_spectra.contiguous().to(torch.complex64)
+        gb = torch.zeros((n_mat, n_bands), dtype=torch.float32, device=g.device)
+        self._check(self.L.st_backward_beta(self.h, scene.h, C.c_void_p(g.data_ptr()), C.c_void_p(gb.data_ptr())))
+        return gb
+
     def direct_visibility(self):
         v = np.empty(self.M, np.uint8)
         self._check(self.L.st_get_direct_visibility(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST))

@@ -74,6 +74,7 @@ SIGNATURES = {
     "st_get_diffraction": (I32, [P, P, P, P, P, I64, I32]),
     "st_get_direct_visibility": (I32, [P, P, I32]),
     "st_backward": (I32, [P, P, P, P, P, P]),
+    "st_backward_beta": (I32, [P, P, P, P]),
     "st_simulate_batch": (I32, [P, I32, P, P, P]),
     "st_autotune": (I32, [P, P, P, P]),
     "st_scene_update_vertices": (I32, [P, P, I32, I32]),

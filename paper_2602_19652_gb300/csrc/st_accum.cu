@@ -528,6 +528,10 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
     if (e2 != cudaSuccess) return e2;
     if ((e = grow(T.band, (size_t)nb * 4)) != cudaSuccess) return e;
     if ((e = grow(T.kband, (size_t)n_mat * nb * 4)) != cudaSuccess) return e;
+    if ((e = grow(T.bband, (size_t)n_mat * nb * 4)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(T.bband.p, S.beta_band.data(), (size_t)n_mat * nb * 4, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return e;
     if ((e = cudaMemcpyAsync(T.band.p, S.band_hz.data(), (size_t)nb * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(T.kband.p, S.k_band.data(), (size_t)n_mat * nb * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;

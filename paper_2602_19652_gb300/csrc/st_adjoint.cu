@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             cmul2(orr, oi, w1r, w1i, fmul2(w1i, pk2(-1.0f, -1.0f)));
             u64 c0r = 0ull, c0i = 0ull, qr = 0ull, qi = 0ull, cg = 0ull;
             float y[KT];
+            const float2 ngv = up2(ng);  // -gamma^2 of the two microphones (lobe sums)
             const ulonglong2* trow = reinterpret_cast<const ulonglong2*>(C.tab) + (size_t)p * KB + s;
 #pragma unroll
             for (int kk = 0; kk < KT; ++kk) {
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 qi = fadd2(qi, c0i);
                 if (KIND == 0) cg = ffma2(t.y, wr, cg);
                 const float2 wr2 = up2(wr);
-                y[kk] = wr2.x + wr2.y;
+                y[kk] = j.do_beta ? fmaf(wr2.x, ngv.x, wr2.y * ngv.y) : wr2.x + wr2.y;
                 if (kk & 1) cmul2(orr, oi, w2r, w2i, nw2i); else cmul2(er, ei, w2r, w2i, nw2i);
             }
             if (j.do_pos) {
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 const int len = meta & 15, matj = (meta >> 8) & 255;
                 const uint32_t c0 = __float_as_uint(pd[p * 12 + 9]), c1 = __float_as_uint(pd[p * 12 + 10]);
                 float cnt[kNV] = {0.f, 0.f, 0.f, 0.f};
-                if (a.reflection_mode == 1) {
+                if (a.reflection_mode == 1 || j.do_beta) {  // one material: the last hit's
                     const int q = matj - j.mat_base;
 #pragma unroll
                     for (int u = 0; u < kNV; ++u)
@@ -412,6 +413,54 @@ __global__ void __launch_bounds__(kDkThreads) k_dk_contract(const float* V, int 
     if (threadIdx.x == 0) dk[(size_t)mat * n_bands + b] = (float)red[0];
 }
 
+// dbeta[mat][b] = sum_k Vg[mat][k] dg_k / dbeta_b, g_k = (1 - w) / (2 beta_b0^2) + w / (2 beta_b1^2), Vg the lobe
+// sums dL/dg; one block per (material, band), threads over the bins in float64, fixed-order tree sum
+__global__ void __launch_bounds__(kDkThreads) k_dbeta_contract(const float* V, int F, int mat_base, int n_bands,
+                                                              const float* band_hz, const float* beta_tab,
+                                                              double f_lo, double df, float* dbeta) {
+    __shared__ double red[kDkThreads];
+    const int u = blockIdx.x / n_bands, b = blockIdx.x % n_bands;
+    const int mat = mat_base + u;
+    const double be = (double)beta_tab[(size_t)mat * n_bands + b];
+    const double dgdb = -1.0 / (be * be * be);
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < F; k += kDkThreads) {
+        const double v = (double)V[(size_t)u * F + k];
+        if (v == 0.0) continue;
+        const double f = F == 1 ? f_lo : f_lo + (double)k * df;
+        double wb = 1.0;
+        if (n_bands > 1) {
+            int b0;
+            double w;
+            if (f <= (double)band_hz[0]) {
+                b0 = 0;
+                w = 0.0;
+            } else if (f >= (double)band_hz[n_bands - 1]) {
+                b0 = n_bands - 2;
+                w = 1.0;
+            } else {
+                int lo = 0, hi = n_bands - 1;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((double)band_hz[mid] <= f) lo = mid; else hi = mid;
+                }
+                b0 = lo;
+                w = (f - (double)band_hz[b0]) / ((double)band_hz[b0 + 1] - (double)band_hz[b0]);
+            }
+            wb = (b == b0) ? 1.0 - w : (b == b0 + 1 ? w : 0.0);
+        }
+        if (wb == 0.0) continue;
+        acc += v * wb * dgdb;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kDkThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dbeta[(size_t)mat * n_bands + b] = (float)red[0];
+}
+
 // positions: dmic[m] = sum of all partial slices in order; demit = sum of emitter slices in order
 __global__ void k_pos_reduce(const float* mic_parts, int n_mic_slices, const float* emit_parts, int n_emit_slices,
                              int M, float* dmic, float* demit) {
@@ -512,6 +561,21 @@ cudaError_t adjoint_dk(const float* v_part, int n_slices, int F, int mat_base, i
     if (e != cudaSuccess) return e;
     note_launch();
     k_dk_contract<<<n, kDkThreads, 0, s>>>(v, F, mat_base, n_bands, band_hz_dev, k_dev, f_lo, df, dk);
+    return cudaGetLastError();
+}
+
+cudaError_t adjoint_dbeta(const float* v_part, int n_slices, int F, int mat_base, int n_mat_launch, int n_bands,
+                          const float* band_hz_dev, const float* beta_dev, double f_lo, double df, float* dbeta,
+                          cudaStream_t s) {
+    const int n = n_mat_launch * n_bands;
+    if (n <= 0) return cudaSuccess;
+    float* v = const_cast<float*>(v_part);
+    note_launch();
+    k_v_reduce<<<(kNV * F + 127) / 128, 128, 0, s>>>(v, n_slices, F);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_dbeta_contract<<<n, kDkThreads, 0, s>>>(v, F, mat_base, n_bands, band_hz_dev, beta_dev, f_lo, df, dbeta);
     return cudaGetLastError();
 }
 

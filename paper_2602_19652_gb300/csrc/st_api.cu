@@ -263,7 +263,8 @@ st_status st_destroy(st_ctx* c) {
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
                           &P->meta, &P->dep})
             release(*b);
-    for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->sig_e, &c->sig_g,
+    for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->tables.bband,
+                      &c->sig_e, &c->sig_g,
                       &c->ray_tab})
         release(*b);
     for (auto& e : c->ev)
@@ -968,8 +969,8 @@ st_status st_get_direct_visibility(st_ctx* c, uint8_t* vis, int32_t mem) {
     return ST_OK;
 }
 
-st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* grad_k, float* grad_mic,
-                      float* grad_emitter) {
+static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra, float* grad_k, float* grad_mic,
+                               float* grad_emitter, float* grad_beta) {
     if (!c || !sc || !grad_spectra) return fail(c, ST_ERR_ARG, "backward: null argument");
     if (!c->has_last || c->last_scene != sc || c->last_scene_version != sc->version)
         return fail(c, ST_ERR_STATE, "backward: needs the last simulate of this scene, unchanged since");
@@ -1036,6 +1037,7 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
     float* micp = ptr<float>(c->adj_mic);
     float* emitp = ptr<float>(c->adj_emit);
     if (grad_k) CKC(c, cudaMemsetAsync(grad_k, 0, (size_t)S.n_mat * S.n_bands * 4, s), "memset");
+    if (grad_beta) CKC(c, cudaMemsetAsync(grad_beta, 0, (size_t)S.n_mat * S.n_bands * 4, s), "memset");
 
     auto set_paths = [&](AccumArgs& x, PathList& PL) {
         x.px = ptr<float>(PL.px);
@@ -1074,6 +1076,29 @@ st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* 
                                   S.n_bands, ptr<float>(T.band), ptr<float>(T.kband), c->f_lo, T.df, grad_k, S.n_mat,
                                   s),
                     "adjoint dk");
+        }
+    }
+    // ---- specular: lobe-width sums (the last hit's material), in batches of four materials
+    if ((p.components & ST_COMP_SPECULAR) && c->last_N > 0 && grad_beta) {
+        AccumArgs x = aa;
+        x.kind = 0;
+        x.d_count = cnt + 2;
+        x.n_chunks = chunks;
+        set_paths(x, c->paths);
+        for (int bt = 0; bt < (S.n_mat + 3) / 4; ++bt) {
+            AdjointArgs jj = ja;
+            jj.G = G;
+            jj.do_pos = 0;
+            jj.do_k = 1;
+            jj.do_beta = 1;
+            jj.mat_base = 4 * bt;
+            jj.v_part = ptr<float>(c->adj_v);
+            jj.mic_part = micp;
+            jj.emit_part = emitp;
+            CKC(c, adjoint_launch(x, jj, g, s), "adjoint lobe widths");
+            CKC(c, adjoint_dbeta(ptr<float>(c->adj_v), chunks * g.n_mb, F, 4 * bt, std::min(4, S.n_mat - 4 * bt),
+                                 S.n_bands, ptr<float>(T.band), ptr<float>(T.bband), c->f_lo, T.df, grad_beta, s),
+                "adjoint dbeta");
         }
     }
     // ---- diffraction: positions
@@ -1143,6 +1168,16 @@ st_status st_impulse_response(st_ctx* c, const void* spectra, int32_t n_comp, in
     return ST_OK;
 }
 
+st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* grad_k, float* grad_mic,
+                      float* grad_emitter) {
+    return backward_impl(c, sc, grad_spectra, grad_k, grad_mic, grad_emitter, nullptr);
+}
+
+st_status st_backward_beta(st_ctx* c, st_scene* sc, const void* grad_spectra, float* grad_beta) {
+    if (!grad_beta) return fail(c, ST_ERR_ARG, "backward_beta: null output");
+    return backward_impl(c, sc, grad_spectra, nullptr, nullptr, nullptr, grad_beta);
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ batched form
@@ -1179,7 +1214,7 @@ void batch_release(BatchState& B) {
         release(*b);
     for (auto& d : B.partial) release(d);
     for (auto& T : B.tables)
-        for (DevBuf* b : {&T.lk, &T.g2, &T.lid, &T.qhi, &T.qlo, &T.bw, &T.band, &T.kband}) release(*b);
+        for (DevBuf* b : {&T.lk, &T.g2, &T.lid, &T.qhi, &T.qlo, &T.bw, &T.band, &T.kband, &T.bband}) release(*b);
     for (PathList* P : {&B.spec, &B.diff})
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
                           &P->meta, &P->dep})

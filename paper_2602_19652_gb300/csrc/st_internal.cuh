@@ -211,7 +211,7 @@ struct PathList {
 
 struct AccumTables {
     int32_t F = 0, n_mat = 0, n_bands = 0;
-    DevBuf band, kband;  // device copies of the band centres and reflection band values (adjoint)
+    DevBuf band, kband, bband;  // device copies of the band centres, reflection and lobe-width band values (adjoint)
     DevBuf lk;     // [n_mat][F] log2 k(mat, f)
     DevBuf g2;     // [n_mat][F] lobe exponent 1/(2 beta^2) * log2(e)
     DevBuf lid;    // [n_mat][F] log2 I_d(mat, f)
@@ -365,6 +365,7 @@ struct AdjointArgs {
     const float2* G;        // [M][F] dL/dRe S + j dL/dIm S of this component
     int do_pos;             // accumulate microphone / emitter position gradients
     int do_k;               // accumulate reflection sums V for materials mat_base .. mat_base + 3
+    int do_beta;            // with do_k: V holds the lobe sums -gamma^2 Re w of the last hit's material instead
     int mat_base;
     float* v_part;          // [n_chunks * n_mb][4][F]
     float* mic_part;        // [n_chunks * n_bb][M][3]
@@ -397,6 +398,9 @@ cudaError_t adjoint_direct(const DirectAccumArgs& a, const float* qhi, const flo
 cudaError_t adjoint_dk(const float* v_part, int n_slices, int F, int mat_base, int n_mat_launch, int n_bands,
                        const float* band_hz_dev, const float* k_dev, double f_lo, double df, float* dk, int n_mat,
                        cudaStream_t s);
+cudaError_t adjoint_dbeta(const float* v_part, int n_slices, int F, int mat_base, int n_mat_launch, int n_bands,
+                          const float* band_hz_dev, const float* beta_dev, double f_lo, double df, float* dbeta,
+                          cudaStream_t s);
 cudaError_t adjoint_pos(const float* mic_parts, int n_mic_slices, const float* emit_parts, int n_emit_slices, int M,
                         float* dmic, float* demit, cudaStream_t s);
 

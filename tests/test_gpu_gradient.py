@@ -78,3 +78,46 @@ def test_autograd_function(torch_st):
     # autograd forms dL/dS of |S|^2 through abs(), so it differs from 2 S by rounding only
     for a, b in ((k.grad, gk), (m.grad, gm), (e.grad, ge)):
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_lobe_width_gradient_matches_oracle(torch_st, mode):
+    """st_backward_beta against the oracle's float64 analytic gradient (itself pinned to central
+    differences): both reflection modes, the clutter scene's four materials over 16 bands."""
+    import oracle
+    torch, st = torch_st
+    wl = synth.clutter(seed=202, target_tris=20_000, n_rays=20_000, bounces=4, n_mics=6, n_bins=40,
+                       diffraction=False)
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance, reflection_mode=mode)
+    S = ctx.simulate(sc, p)
+    rng = np.random.default_rng(8)
+    target = torch.as_tensor(rng.normal(size=S.shape) + 1j * rng.normal(size=S.shape), dtype=torch.complex64,
+                             device=S.device) * S.abs().mean()
+    G = 2.0 * (S - target)
+    gb = ctx.backward_beta(sc, G, wl.k_band.shape[0], wl.k_band.shape[1]).cpu().numpy()
+    o = oracle.simulate(wl, reflection_mode=mode)
+    _, _, _, db = oracle.spectra_grad(o["params"], o["rec"], wl.dirs, wl.tri_mat,
+                                      G.cpu().numpy().astype(np.complex128), direct_vis=o["direct_vis"],
+                                      with_beta=True)
+    assert np.abs(db).max() > 0
+    assert rel(gb, db) <= TOL, rel(gb, db)
+
+
+def test_autograd_lobe_widths(torch_st):
+    torch, st = torch_st
+    wl = synth.gradient_problem(n_rays=1000)
+    wl.n_bins = 32
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    k = torch.tensor(wl.k_band, device="cuda")
+    m = torch.tensor(wl.mics, device="cuda")
+    e = torch.tensor(wl.emitter, device="cuda")
+    b = torch.tensor(wl.beta_band, device="cuda", requires_grad=True)
+    S = st.SpectraFn.apply(ctx, sc, p, k, m, e, b)
+    (S.abs() ** 2).sum().backward()
+    gb = ctx.backward_beta(sc, 2.0 * S.detach(), b.shape[0], b.shape[1])
+    assert float(gb.abs().max()) > 0
+    assert torch.allclose(b.grad, gb, rtol=1e-4, atol=1e-4 * float(gb.abs().max()))
