@@ -79,7 +79,7 @@ def _declare(L):
                               I32, P, I32, P, I32, P]
     L.ora_spectra.restype = C.c_int
     L.ora_spectra_grad.argtypes = [C.POINTER(SpecParams), I64, I32, P, P, P, P, P, P, P, I64, P, P, P, P,
-                                   P, P, P, P, P]
+                                   P, P, P, P, P, P, P]
     L.ora_spectra_grad.restype = C.c_int
 
 
@@ -276,9 +276,11 @@ def spectra(params, rec, dirs, tri_mat, cand_tri=None, cand_p=None, cand_keep=No
 
 
 def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand_keep=None, direct_vis=None,
-                 with_beta=False):
+                 with_beta=False, tri_nrm=None):
     """G: complex [3][M][F] = dL/dRe S + j dL/dIm S.  Returns (dk [n_mat][n_bands], dmic [M][3], demit [3]),
-    and dbeta [n_mat][n_bands] (lobe widths, specular paths) as a fourth item when with_beta."""
+    and dbeta [n_mat][n_bands] (lobe widths, specular paths) as a fourth item when with_beta.  demit holds
+    the diffraction and direct paths; given the triangle normals tri_nrm [T][3], it also holds the
+    specular paths through their hit points (ray directions and triangle chains frozen)."""
     P_ = params.P
     N, B = rec["tri"].shape
     dirs, tm = _c(dirs, np.float32), _c(tri_mat, np.int32)
@@ -290,11 +292,15 @@ def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand
     dmic = np.zeros((P_.M, 3), np.float64)
     demit = np.zeros(3, np.float64)
     dbeta = np.zeros((P_.n_mat, P_.n_bands), np.float64) if with_beta else None
+    nrm = _c(tri_nrm, np.float32)
+    dspec = np.zeros(3, np.float64) if nrm is not None else None
     rc = lib().ora_spectra_grad(C.byref(P_), N, B, _p(rec["tri"]), _p(rec["p"]), _p(rec["d"]), _p(rec["r"]),
                                 _p(rec["los"]), _p(dirs), _p(tm), K, _p(ct), _p(cp), _p(ck), _p(dv), _p(Gr),
-                                _p(dk), _p(dmic), _p(demit), _p(dbeta))
+                                _p(dk), _p(dmic), _p(demit), _p(dbeta), _p(nrm), _p(dspec))
     if rc != 0:
         raise ValueError("oracle gradient needs omni emitter and microphones")
+    if dspec is not None:
+        demit = demit + dspec
     return (dk, dmic, demit, dbeta) if with_beta else (dk, dmic, demit)
 
 

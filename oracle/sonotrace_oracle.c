@@ -1088,11 +1088,13 @@ ORA_API int ora_spectra_grad(const OraSpecParams* P, int64_t N, int32_t B, const
                              const float* rec_d, const double* rec_r, const uint8_t* rec_los, const float* dirs,
                              const int32_t* tri_mat, int64_t K, const int32_t* cand_tri, const float* cand_p,
                              const uint8_t* cand_keep, const uint8_t* direct_vis, const double* G,
-                             double* dk, double* dmic, double* demit, double* dbeta) {
+                             double* dk, double* dmic, double* demit, double* dbeta, const float* tri_nrm,
+                             double* demit_spec) {
     if (P->emit_table || P->mic_tables) return -1;
     int F = P->F, M = P->M;
     memset(dk, 0, sizeof(double) * (size_t)P->n_mat * P->n_bands);
     if (dbeta) memset(dbeta, 0, sizeof(double) * (size_t)P->n_mat * P->n_bands);
+    if (demit_spec) memset(demit_spec, 0, sizeof(double) * 3);
     memset(dmic, 0, sizeof(double) * 3 * (size_t)M);
     memset(demit, 0, sizeof(double) * 3);
     for (int m = 0; m < M; ++m) {
@@ -1176,6 +1178,36 @@ ORA_API int ora_spectra_grad(const OraSpecParams* P, int64_t N, int32_t B, const
                     acc_g += A * (-2.0 * gm * g) * re_gz;
                 }
                 for (int k = 0; k < 3; ++k) dmic[3 * m + k] += acc_r * u[k] + acc_g * dgdm[k];
+                /* emitter through the hit points (ray directions and triangle chain frozen): hit q is
+                 * the intersection of the line from P_{q-1} along d_q with triangle q's plane, so
+                 * dP_q/dP_{q-1} = I - d_q n_q^T / (n_q . d_q) and dt_q/dP_{q-1} = -n_q^T / (n_q . d_q),
+                 * P_{-1} = s.  With J = dP_j/ds and dr_j/ds = sum_q dt_q/ds:
+                 * dL/ds += (dr_j/ds) acc_r - J^T (acc_r u + acc_g dgamma/dm)   (d|m - P|/dP = -u,
+                 * dgamma/dP = -dgamma/dm). */
+                if (demit_spec && tri_nrm) {
+                    double J[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, drds[3] = {0, 0, 0};
+                    float d0f[3];
+                    rotate_qf(P->q, dirs + 3 * i, d0f);
+                    double dq[3] = {d0f[0], d0f[1], d0f[2]};
+                    for (int32_t q = 0; q <= j; ++q) {
+                        const float* nf = tri_nrm + 3 * (int64_t)rec_tri[i * B + q];
+                        double n[3] = {nf[0], nf[1], nf[2]};
+                        double nd = n[0] * dq[0] + n[1] * dq[1] + n[2] * dq[2];
+                        double nJ[3];
+                        for (int c2 = 0; c2 < 3; ++c2) nJ[c2] = n[0] * J[c2] + n[1] * J[3 + c2] + n[2] * J[6 + c2];
+                        for (int c2 = 0; c2 < 3; ++c2) drds[c2] -= nJ[c2] / nd;
+                        for (int r2 = 0; r2 < 3; ++r2)
+                            for (int c2 = 0; c2 < 3; ++c2) J[3 * r2 + c2] -= dq[r2] * nJ[c2] / nd;
+                        const float* dn = rec_d + 3 * (i * B + q);
+                        dq[0] = dn[0];
+                        dq[1] = dn[1];
+                        dq[2] = dn[2];
+                    }
+                    double gp[3];
+                    for (int k = 0; k < 3; ++k) gp[k] = acc_r * u[k] + acc_g * dgdm[k];
+                    for (int c2 = 0; c2 < 3; ++c2)
+                        demit_spec[c2] += drds[c2] * acc_r - (J[c2] * gp[0] + J[3 + c2] * gp[1] + J[6 + c2] * gp[2]);
+                }
             }
         }
         /* ---- diffraction */

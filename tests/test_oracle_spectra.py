@@ -214,3 +214,105 @@ def test_beta_gradient_matches_central_differences():
         fd = (8.0 * D(h / 2) - D(h)) / 3.0
         terms = (dbeta * h * v).ravel()
         assert abs(fd - terms.sum()) <= 1e-6 * np.abs(terms).sum(), (fd, terms.sum())
+
+
+def _rot32(q, v):
+    """q applied to v in float32 with the tracing's operation order (no fused products)."""
+    f = np.float32
+    q = [f(x) for x in q]
+    v = [f(x) for x in v]
+    t = [f(2.0) * (q[2] * v[2] - q[3] * v[1]), f(2.0) * (q[3] * v[0] - q[1] * v[2]), f(2.0) * (q[1] * v[1] - q[2] * v[0])]
+    c = [q[2] * t[2] - q[3] * t[1], q[3] * t[0] - q[1] * t[2], q[1] * t[1] - q[2] * t[0]]
+    return np.array([(v[k] + q[0] * t[k]) + c[k] for k in range(3)], np.float64)
+
+
+def _frozen_chain_spectra(wl, rec, s, a1_per_khz=0.033, c=343.0, s_ref=None):
+    """Specular spectra in float64 with every record's triangle chain and ray direction frozen and its
+    hit points re-intersected from the emitter position s (the plain formula of Eq. 2-4, reflection
+    product over the chain, lobe of the last hit).  With s_ref, hit points and lengths are the stored
+    records' plus the float64 displacement between the intersections from s and from s_ref (the
+    records are float32: at s_ref this reproduces them exactly)."""
+    F = wl.n_bins
+    f = wl.f_lo + np.arange(F) * ((wl.f_hi - wl.f_lo) / (F - 1))
+    band = wl.band_hz.astype(np.float64)
+    b0 = np.clip(np.searchsorted(band, f, side="right") - 1, 0, len(band) - 2)
+    w = np.clip((f - band[b0]) / (band[b0 + 1] - band[b0]), 0.0, 1.0)
+    kb, bb = wl.k_band.astype(np.float64), wl.beta_band.astype(np.float64)
+    kf = (1 - w) * kb[:, b0] + w * kb[:, b0 + 1]                       # [n_mat][F]
+    gf = (1 - w) / (2 * bb[:, b0] ** 2) + w / (2 * bb[:, b0 + 1] ** 2)
+    alpha = a1_per_khz * f / 1000.0
+    V = wl.verts.astype(np.float64)
+    nrm = oracle.tri_normals(wl.verts, wl.tris).astype(np.float64)
+    M = len(wl.mics)
+    S = np.zeros((M, F), np.complex128)
+    N, B = rec["tri"].shape
+    for i in range(N):
+        Pq = np.asarray(s, np.float64)
+        Pb = np.asarray(s if s_ref is None else s_ref, np.float64)
+        d = _rot32(wl.emitter_quat, wl.dirs[i])
+        r, rb, chain = 0.0, 0.0, []
+        for j in range(B):
+            tri = rec["tri"][i, j]
+            if tri < 0:
+                break
+            n = nrm[tri]
+            t = n @ (V[wl.tris[tri, 0]] - Pq) / (n @ d)
+            tb = n @ (V[wl.tris[tri, 0]] - Pb) / (n @ d)
+            Pq, Pb = Pq + t * d, Pb + tb * d
+            r, rb = r + t, rb + tb
+            chain.append(wl.tri_mat[tri])
+            d = rec["d"][i, j].astype(np.float64)
+            if not rec["los"][i, j]:
+                continue
+            kprod = np.prod(kf[chain], axis=0)
+            Pu, ru = Pq, r
+            if s_ref is not None:
+                Pu = rec["p"][i, j].astype(np.float64) + (Pq - Pb)
+                ru = float(rec["r"][i, j]) + (r - rb)
+            for m in range(M):
+                v = wl.mics[m].astype(np.float64) - Pu
+                dist = np.linalg.norm(v)
+                u = v / dist
+                gm = math.atan2(np.linalg.norm(np.cross(d, u)), d @ u)
+                rr = ru + dist
+                A = np.exp(-gm * gm * gf[chain[-1]]) * kprod * 10.0 ** (-alpha * rr / 20.0) / rr ** 2
+                S[m] += A * np.exp(2j * np.pi * f * rr / c)
+    return S
+
+
+def test_specular_emitter_gradient_matches_central_differences():
+    """Emitter-position gradient through the specular hit points (chains and directions frozen)
+    against central differences of a float64 frozen-chain restatement, Richardson extrapolated."""
+    wl, out, _, _, _ = _grad_problem(n_rays=200, F=10)
+    rec = out["rec"]
+    s0 = wl.emitter.astype(np.float64)
+    spec = lambda s: _frozen_chain_spectra(wl, rec, s, s_ref=s0)
+    S0 = spec(s0)
+    # at s0 the restatement reproduces the oracle's spectra from the stored records
+    Sref = oracle.spectra(oracle.spec_params(wl), rec, wl.dirs, wl.tri_mat)[0]
+    assert np.linalg.norm(S0 - Sref) <= 1e-9 * np.linalg.norm(Sref)
+    # the re-intersection from s0 itself lands on the stored hit points (float32 rounding apart)
+    S_raw = _frozen_chain_spectra(wl, rec, s0)
+    assert np.linalg.norm(S_raw - Sref) <= 1e-3 * np.linalg.norm(Sref)
+    St = spec(s0 + np.array([0.01, -0.02, 0.015]))
+    G = np.zeros((3,) + S0.shape, np.complex128)
+    G[0] = 2.0 * (S0 - St)
+    nrm = oracle.tri_normals(wl.verts, wl.tris)
+    _, _, demit = oracle.spectra_grad(oracle.spec_params(wl), rec, wl.dirs, wl.tri_mat, G, tri_nrm=nrm)
+    assert np.abs(demit).max() > 0
+
+    def loss(s):
+        return float(np.sum(np.abs(spec(s) - St) ** 2))
+
+    rng = np.random.default_rng(406)
+    for _ in range(3):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+
+        def D(h):
+            return (loss(s0 + h * v) - loss(s0 - h * v)) / 2.0
+
+        h = 1e-4
+        fd = (8.0 * D(h / 2) - D(h)) / 3.0
+        an = float(demit @ (h * v))
+        assert abs(fd - an) <= 1e-4 * np.abs(demit * h * v).sum() + 1e-12, (fd, an)
