@@ -189,7 +189,10 @@ st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
  * [3][n_mics][n_bins] laid out like the spectra.  Writes, as device float32 (any may be NULL):
  *   grad_k [n_mat][n_bands]: reflection band values (specular paths; assumes k > 0 at every bin),
  *   grad_mic [n_mics][3]:    microphone positions (specular, diffraction and direct paths),
- *   grad_emitter [3]:        emitter position through the diffraction and direct paths only.
+ *   grad_emitter [3]:        emitter position: diffraction and direct paths, and specular paths
+ *                            through their hit points (ray directions and triangle chains frozen:
+ *                            hit q moves along d_q with the line from hit q-1, dP_q/dP_{q-1} =
+ *                            I - d_q n_q^T / (n_q . d_q)).
  * Needs omni receivers; position gradients also need an omni emitter (ST_ERR_ARG otherwise).  scene must be the one of the
  * last simulate, unchanged since (ST_ERR_STATE otherwise).  Deterministic: every sum runs in a fixed
  * order.  Stream-ordered; allocates reduction buffers on first use. */

@@ -84,7 +84,7 @@ __device__ __forceinline__ void rs_reduce(float (&v)[8], int tp, unsigned wm) {
 // per path, folds its subtile's share of the position gradients into registers (the derivative of
 // the path length and of the lobe angle are linear in the per-subtile sums C0, C1, Cg), and its
 // share of the reflection sums V into kNV x VR registers after a reduce-scatter over the pair lanes.
-template <int KT, int KIND, int TPL>
+template <int KT, int KIND, int TPL, int EMIT>
 __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     k_adjoint(const AccumArgs a, const AdjointArgs j, const Geom g) {
     static_assert(KT == 8, "the reduce-scatter of the reflection sums takes 8 bins per thread");
@@ -92,10 +92,13 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     extern __shared__ float4 smem4[];
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB;
     const Buf B0 = buf_at<KT>(smem4, g, 0), B1 = buf_at<KT>(smem4, g, 1);
-    // after the two pipeline buffers: pd [3][PT][12], pv [3][PT], material tables
+    // after the two pipeline buffers: pd [3][PT][12], pv [3][PT], (EMIT) chain jacobians [3][PT][12], material tables
     float* pdb = reinterpret_cast<float*>(reinterpret_cast<char*>(smem4) + 2 * g.buf_bytes);
     int* pvb = reinterpret_cast<int*>(pdb + 3 * PT * 12);
-    float* mt = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(pvb + 3 * PT) + 15) & ~uintptr_t(15));
+    // (16-byte aligned: each path's 12 floats are read as three float4)
+    float* pjb = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(pvb + 3 * PT) + 15) & ~uintptr_t(15));
+    float* mt = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(pjb + (EMIT ? 3 * PT * 12 : 0)) + 15) & ~uintptr_t(15));
 
     const int mb = blockIdx.x % g.n_mb, bb = blockIdx.x / g.n_mb;
     const int mic0 = mb * g.MP, kb = bb * KB;
@@ -109,6 +112,15 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     const int64_t n_tiles = (count + PT - 1) / PT;
     const int64_t per = (n_tiles + a.n_chunks - 1) / a.n_chunks;
     const int64_t t0 = (int64_t)blockIdx.y * per, t1 = min(n_tiles, t0 + per);
+    // chain jacobians of one tile's paths (EMIT), next to their path data
+    auto load_jac = [&](int64_t pbase, float* dst) {
+        if (EMIT) {
+            for (int e = threadIdx.x; e < PT * 12; e += blockDim.x) {
+                const int64_t rel = pbase + e / 12;
+                dst[e] = rel < count ? a.jac[rel * 12 + e % 12] : 0.0f;
+            }
+        }
+    };
 
     // G of the thread's two microphones and KT bins, packed over the microphones
     u64 Gr[KT], Gi[KT];
@@ -156,7 +168,11 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             }
         }
         load_paths<KIND>(a, PT, t0 * PT, count, pdb, pvb);
-        if (t0 + 1 < t1) load_paths<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
+        load_jac(t0 * PT, pjb);
+        if (t0 + 1 < t1) {
+            load_paths<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
+            load_jac((t0 + 1) * PT, pjb + PT * 12);
+        }
         __syncthreads();
         produce<KT, KIND, 1>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, j.s);
         __syncthreads();
@@ -218,13 +234,42 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 dl = ffma2(nAiS, c0i, dl);
                 dl = ffma2(D1r, q1r, dl);
                 dl = ffma2(nD1i, q1i, dl);
-                dmx = ffma2(dl, ad[0], dmx);
-                dmy = ffma2(dl, ad[1], dmy);
-                dmz = ffma2(dl, ad[2], dmz);
+                if (KIND == 0 && EMIT) {
+                    // microphone share g = dl u + cg v'; emitter through the hit point and the path length:
+                    // dL/ds += (dr/ds) dl - J^T g  (J = dP/ds, both per path, frozen chain)
+                    const u64 gx = ffma2(cg, ad[3], fmul2(dl, ad[0]));
+                    const u64 gy = ffma2(cg, ad[4], fmul2(dl, ad[1]));
+                    const u64 gz = ffma2(cg, ad[5], fmul2(dl, ad[2]));
+                    dmx = fadd2(dmx, gx);
+                    dmy = fadd2(dmy, gy);
+                    dmz = fadd2(dmz, gz);
+                    const float* jp = pjb + pb * PT * 12 + p * 12;
+                    const float4 j0 = *reinterpret_cast<const float4*>(jp);      // J00 J01 J02 J10
+                    const float4 j1 = *reinterpret_cast<const float4*>(jp + 4);  // J11 J12 J20 J21
+                    const float4 j2 = *reinterpret_cast<const float4*>(jp + 8);  // J22 drx dry drz
+                    dex = ffma2(pk2(j2.y, j2.y), dl, dex);
+                    dex = ffma2(pk2(-j0.x, -j0.x), gx, dex);
+                    dex = ffma2(pk2(-j0.w, -j0.w), gy, dex);
+                    dex = ffma2(pk2(-j1.z, -j1.z), gz, dex);
+                    dey = ffma2(pk2(j2.z, j2.z), dl, dey);
+                    dey = ffma2(pk2(-j0.y, -j0.y), gx, dey);
+                    dey = ffma2(pk2(-j1.x, -j1.x), gy, dey);
+                    dey = ffma2(pk2(-j1.w, -j1.w), gz, dey);
+                    dez = ffma2(pk2(j2.w, j2.w), dl, dez);
+                    dez = ffma2(pk2(-j0.z, -j0.z), gx, dez);
+                    dez = ffma2(pk2(-j1.y, -j1.y), gy, dez);
+                    dez = ffma2(pk2(-j2.x, -j2.x), gz, dez);
+                } else {
+                    dmx = ffma2(dl, ad[0], dmx);
+                    dmy = ffma2(dl, ad[1], dmy);
+                    dmz = ffma2(dl, ad[2], dmz);
+                }
                 if (KIND == 0) {  // lobe angle
-                    dmx = ffma2(cg, ad[3], dmx);
-                    dmy = ffma2(cg, ad[4], dmy);
-                    dmz = ffma2(cg, ad[5], dmz);
+                    if (!EMIT) {
+                        dmx = ffma2(cg, ad[3], dmx);
+                        dmy = ffma2(cg, ad[4], dmy);
+                        dmz = ffma2(cg, ad[5], dmz);
+                    }
                 } else {  // emitter: dr/ds = -unit(o - s)
                     dex = ffma2(dl, ad[3], dex);
                     dey = ffma2(dl, ad[4], dey);
@@ -260,6 +305,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         if (tile + 2 < t1) {
             const int nb2 = (int)((tile + 2 - t0) % 3);
             load_paths<KIND>(a, PT, (tile + 2) * PT, count, pdb + nb2 * PT * 12, pvb + nb2 * PT);
+            load_jac((tile + 2) * PT, pjb + nb2 * PT * 12);
         }
         __syncthreads();
     }
@@ -311,6 +357,51 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 for (int v = 0; v < VR; ++v)
                     if (k0 + v < a.F) j.v_part[((size_t)(blockIdx.y * g.n_mb + mb) * kNV + u) * a.F + k0 + v] = V[u][v];
         }
+    }
+}
+
+// per compacted specular path (record id = idx[c] = ray * B + j): dP_j/ds and dr_j/ds along the frozen chain.
+// Hit q is the intersection of the line from P_{q-1} along d_q with triangle q's plane:
+// dP_q/dP_{q-1} = I - d_q n_q^T / (n_q . d_q), dt_q/dP_{q-1} = -n_q^T / (n_q . d_q), P_{-1} = s.
+__global__ void k_chain_jacobians(const uint32_t* idx, const uint32_t* count, int32_t B, const int32_t* rec_tri,
+                                  const float* rec_d, const float* nrm, const float* dirs, float4 qv, float* jac) {
+    const int64_t n = *count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+        const int64_t id = idx[c];
+        const int64_t ray = id / B;
+        const int jj = (int)(id - ray * B);
+        // emitted direction: q applied to the ray's local direction
+        const float vx = dirs[3 * ray], vy = dirs[3 * ray + 1], vz = dirs[3 * ray + 2];
+        const float tx = 2.0f * (qv.z * vz - qv.w * vy), ty = 2.0f * (qv.w * vx - qv.y * vz),
+                    tz = 2.0f * (qv.y * vy - qv.z * vx);
+        float d[3] = {vx + qv.x * tx + (qv.z * tz - qv.w * ty), vy + qv.x * ty + (qv.w * tx - qv.y * tz),
+                      vz + qv.x * tz + (qv.y * ty - qv.z * tx)};
+        float J[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}, dr[3] = {0.f, 0.f, 0.f};
+        for (int q = 0; q <= jj; ++q) {
+            const int32_t t = rec_tri[ray * B + q];
+            const float n0 = nrm[3 * t], n1 = nrm[3 * t + 1], n2 = nrm[3 * t + 2];
+            const float inv = 1.0f / (n0 * d[0] + n1 * d[1] + n2 * d[2]);
+            float nJ[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) nJ[k] = (n0 * J[k] + n1 * J[3 + k] + n2 * J[6 + k]) * inv;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dr[k] -= nJ[k];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) J[3 * r + k] -= d[r] * nJ[k];
+            const float* dn = rec_d + 3 * (ray * B + q);
+            d[0] = dn[0];
+            d[1] = dn[1];
+            d[2] = dn[2];
+        }
+        float* o = jac + c * 12;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) o[k] = J[k];
+        o[9] = dr[0];
+        o[10] = dr[1];
+        o[11] = dr[2];
     }
 }
 
@@ -477,18 +568,19 @@ __global__ void k_pos_reduce(const float* mic_parts, int n_mic_slices, const flo
     }
 }
 
-template <int KT, int KIND, int TPL>
+template <int KT, int KIND, int TPL, int EMIT = 0>
 cudaError_t launch_adjoint(const AccumArgs& a, const AdjointArgs& j, const Geom& g, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_adjoint<KT, KIND, TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_adjoint<KT, KIND, TPL, EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((unsigned)(g.n_mb * g.n_bb), (unsigned)a.n_chunks);
+    const size_t smem = g.smem + (EMIT ? (size_t)3 * g.PT * 12 * 4 + 16 : 0);
     note_launch();
-    k_adjoint<KT, KIND, TPL><<<grid, g.TP * g.NS, g.smem, s>>>(a, j, g);
+    k_adjoint<KT, KIND, TPL, EMIT><<<grid, g.TP * g.NS, smem, s>>>(a, j, g);
     return cudaGetLastError();
 }
 
@@ -531,6 +623,15 @@ acc::Geom adjoint_geom(int M, int F, int n_mat) {
 
 cudaError_t adjoint_launch(const AccumArgs& a, const AdjointArgs& j, const acc::Geom& g, cudaStream_t s) {
     if (a.kind == 1) return launch_adjoint<8, 1, 0>(a, j, g, s);
+    if (a.jac && j.do_pos) {
+        switch (g.TP) {
+            case 1: return launch_adjoint<8, 0, 0, 1>(a, j, g, s);
+            case 2: return launch_adjoint<8, 0, 1, 1>(a, j, g, s);
+            case 4: return launch_adjoint<8, 0, 2, 1>(a, j, g, s);
+            case 8: return launch_adjoint<8, 0, 3, 1>(a, j, g, s);
+            default: return launch_adjoint<8, 0, 4, 1>(a, j, g, s);
+        }
+    }
     switch (g.TP) {
         case 1: return launch_adjoint<8, 0, 0>(a, j, g, s);
         case 2: return launch_adjoint<8, 0, 1>(a, j, g, s);
@@ -561,6 +662,16 @@ cudaError_t adjoint_dk(const float* v_part, int n_slices, int F, int mat_base, i
     if (e != cudaSuccess) return e;
     note_launch();
     k_dk_contract<<<n, kDkThreads, 0, s>>>(v, F, mat_base, n_bands, band_hz_dev, k_dev, f_lo, df, dk);
+    return cudaGetLastError();
+}
+
+cudaError_t chain_jacobians(const uint32_t* idx, const uint32_t* count, int64_t n_max, int32_t B, const int32_t* rec_tri,
+                            const float* rec_d, const float* nrm, const float* dirs, const float q[4], float* jac,
+                            cudaStream_t s) {
+    if (n_max <= 0) return cudaSuccess;
+    note_launch();
+    k_chain_jacobians<<<grid_for(n_max, 256), 256, 0, s>>>(idx, count, B, rec_tri, rec_d, nrm, dirs,
+                                                           make_float4(q[0], q[1], q[2], q[3]), jac);
     return cudaGetLastError();
 }
 

@@ -103,6 +103,7 @@ struct st_ctx {
     std::vector<st_scene*> scenes;  // scenes loaded into this context (freed by st_destroy)
     DevBuf sig_e, sig_g;             // impulse responses: call spectrum [F], combined spectra [rows][F]
     DevBuf ray_tab;                  // zone table of the zonal ray set
+    DevBuf adj_jac;                  // backward: chain jacobians of the specular paths [paths][12]
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -265,7 +266,7 @@ st_status st_destroy(st_ctx* c) {
             release(*b);
     for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->tables.bband,
                       &c->sig_e, &c->sig_g,
-                      &c->ray_tab})
+                      &c->ray_tab, &c->adj_jac})
         release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -1060,6 +1061,24 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         x.d_count = cnt + 2;
         x.n_chunks = chunks;
         set_paths(x, c->paths);
+        if (grad_emitter) {
+            // the emitter moves the hit points: chain jacobians of the visible records, in the order of
+            // the path list (the compaction of the last simulate, repeated)
+            const int64_t NB = c->last_N * c->last_B;
+            CKC(c, flags_visible_records(ptr<int32_t>(c->rec_tri), ptr<uint8_t>(c->rec_los), NB,
+                                         ptr<uint32_t>(c->sflags), s),
+                "flags");
+            CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, cnt + 2, c->scratch.p, s),
+                "scan");
+            CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, ptr<uint32_t>(c->sidx), s),
+                "compact");
+            CKC(c, grow(c->adj_jac, (size_t)NB * 48), "alloc");
+            CKC(c, chain_jacobians(ptr<uint32_t>(c->sidx), cnt + 2, NB, c->last_B, ptr<int32_t>(c->rec_tri),
+                                   ptr<float>(c->rec_d), ptr<float>(S.nrm), ptr<float>(c->dirs), c->q,
+                                   ptr<float>(c->adj_jac), s),
+                "chain jacobians");
+            x.jac = ptr<float>(c->adj_jac);
+        }
         const int n_batches = grad_k ? (S.n_mat + 3) / 4 : 1;
         for (int bt = 0; bt < n_batches; ++bt) {
             AdjointArgs jj = ja;

@@ -249,6 +249,7 @@ struct AccumArgs {
     int32_t reflection_mode;
     float2* partial;        // [n_chunks][M][F]
     int32_t n_chunks;
+    const float* jac;       // adjoint only: per specular path dP/ds (3x3 row-major) and dr/ds, or null
 };
 cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, double f_lo, double f_hi, double c,
                                double a0, double a1, cudaStream_t s);
@@ -398,6 +399,10 @@ cudaError_t adjoint_direct(const DirectAccumArgs& a, const float* qhi, const flo
 cudaError_t adjoint_dk(const float* v_part, int n_slices, int F, int mat_base, int n_mat_launch, int n_bands,
                        const float* band_hz_dev, const float* k_dev, double f_lo, double df, float* dk, int n_mat,
                        cudaStream_t s);
+// per compacted specular path: dP_j/ds (3x3 row-major) and dr_j/ds along its frozen chain (12 floats)
+cudaError_t chain_jacobians(const uint32_t* idx, const uint32_t* count, int64_t n_max, int32_t B, const int32_t* rec_tri,
+                            const float* rec_d, const float* nrm, const float* dirs, const float q[4], float* jac,
+                            cudaStream_t s);
 cudaError_t adjoint_dbeta(const float* v_part, int n_slices, int F, int mat_base, int n_mat_launch, int n_bands,
                           const float* band_hz_dev, const float* beta_dev, double f_lo, double df, float* dbeta,
                           cudaStream_t s);

@@ -1,4 +1,5 @@
-"""GPU adjoint (st_backward) against the oracle's float64 analytic gradient, and the autograd
+"""GPU adjoint (st_backward) against the oracle's float64 analytic gradient (the emitter gradient
+including the specular paths through their hit points), and the autograd
 wrapper against st_backward, on frozen path sets.  Bar: relative error <= 1e-3 per gradient block
 (the oracle's gradient is itself pinned to float64 central differences in test_oracle_spectra)."""
 import numpy as np
@@ -37,7 +38,8 @@ def grads_vs_oracle(torch, st, wl, curv=None, mode=0):
     gk, gm, ge = ctx.backward(sc, G, wl.k_band.shape[0], wl.k_band.shape[1])
     o = oracle.simulate(wl, curv=None if curv is None else dict(budget=curv), reflection_mode=mode)
     dk, dmic, demit = oracle.spectra_grad(o["params"], o["rec"], wl.dirs, wl.tri_mat, G.cpu().numpy().astype(np.complex128),
-                                          o.get("cand_tri"), o.get("cand_p"), o.get("cand_keep"), o["direct_vis"])
+                                          o.get("cand_tri"), o.get("cand_p"), o.get("cand_keep"), o["direct_vis"],
+                                          tri_nrm=oracle.tri_normals(wl.verts, wl.tris))
     return gk.cpu().numpy(), gm.cpu().numpy(), ge.cpu().numpy(), dk, dmic, demit
 
 
