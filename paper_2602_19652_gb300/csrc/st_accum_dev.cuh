@@ -221,6 +221,51 @@ __device__ __forceinline__ void load_paths(const AccumArgs& a, int PT, int64_t p
     }
 }
 
+// asynchronous 4-byte global -> shared copies (cp.async): the issuing thread does not wait for the data;
+// cp_async_wait_all before the barrier that publishes the tile
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// path data of one tile into pd / pv as load_paths does, with the words spread over the CTA's threads
+// and copied asynchronously (the copies overlap the tile phase that issues them)
+template <int KIND>
+__device__ __forceinline__ void load_paths_async(const AccumArgs& a, int PT, int64_t pbase, int64_t count, float* pd,
+                                                 int* pv) {
+    const int64_t base = a.d_base ? (int64_t)*a.d_base : 0;
+    for (int e = threadIdx.x; e < PT * 12; e += blockDim.x) {
+        const int p = e / 12, k = e - p * 12;
+        const int64_t rel = pbase + p;
+        const bool ok = rel < count;
+        if (k == 0) pv[p] = ok;
+        if (!ok) continue;  // the words of an invalid path are never read
+        const int64_t pi = base + rel;
+        float* d = pd + p * 12 + k;
+        const float* src = nullptr;
+        switch (k) {
+            case 0: src = a.px + pi; break;
+            case 1: src = a.py + pi; break;
+            case 2: src = a.pz + pi; break;
+            case 3: src = KIND == 0 ? a.dx + pi : nullptr; break;
+            case 4: src = KIND == 0 ? a.dy + pi : nullptr; break;
+            case 5: src = KIND == 0 ? a.dz + pi : nullptr; break;
+            case 6: src = a.rhi + pi; break;
+            case 7: src = a.rlo + pi; break;
+            case 8: src = reinterpret_cast<const float*>(a.meta + pi); break;
+            case 9: src = KIND == 0 ? reinterpret_cast<const float*>(a.chain_lo + pi) : nullptr; break;
+            case 10: src = KIND == 0 ? reinterpret_cast<const float*>(a.chain_hi + pi) : nullptr; break;
+            default:
+                if (a.dep) src = a.dep + pi; else *d = -1.0f;
+                break;
+        }
+        if (src) cp_async4(d, src);
+    }
+    cp_async_commit();
+}
+
 // tables and anchors of one tile (reads pd / pv, writes buffer B); ADJ: also the position-gradient
 // vectors of the adjoint (es = emitter position, diffraction only)
 template <int KT, int KIND, int ADJ = 0>

@@ -165,8 +165,9 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
         }
         if (DIR)
             for (int i = tid; i < KB; i += nthr) bwt[i] = a.bw[min(kb + i, a.F - 1)];
-        load_paths<KIND>(a, PT, t0 * PT, count, pdb, pvb);
-        if (t0 + 1 < t1) load_paths<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
+        load_paths_async<KIND>(a, PT, t0 * PT, count, pdb, pvb);
+        if (t0 + 1 < t1) load_paths_async<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
+        cp_async_wait_all();
         __syncthreads();
         nproduce<KIND>(a, g, B0, pdb, pvb, kb);
         __syncthreads();
@@ -179,6 +180,10 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
         const NBuf& Pn = b ? B0 : B1;
         const float* pd = pdb + pb * PT * 12;
         const int* pv = pvb + pb * PT;
+        if (tile + 2 < t1) {  // slot of tile-1, free: in flight during this phase
+            const int nb2 = (int)((tile + 2 - t0) % 3);
+            load_paths_async<KIND>(a, PT, (tile + 2) * PT, count, pdb + nb2 * PT * 12, pvb + nb2 * PT);
+        }
         if (tile + 1 < t1) {
             const int nb = (int)((tile + 1 - t0) % 3);
             nproduce<KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, kb);
@@ -288,10 +293,7 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
             };
             if (e0) terms(std::true_type{}); else terms(std::false_type{});
         }
-        if (tile + 2 < t1) {
-            const int nb2 = (int)((tile + 2 - t0) % 3);
-            load_paths<KIND>(a, PT, (tile + 2) * PT, count, pdb + nb2 * PT * 12, pvb + nb2 * PT);
-        }
+        cp_async_wait_all();
         __syncthreads();
     }
     // ---- partial spectra of this chunk: sum of the path groups in order, 4 bins per pass

@@ -167,12 +167,13 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 }
             }
         }
-        load_paths<KIND>(a, PT, t0 * PT, count, pdb, pvb);
+        load_paths_async<KIND>(a, PT, t0 * PT, count, pdb, pvb);
         load_jac(t0 * PT, pjb);
         if (t0 + 1 < t1) {
-            load_paths<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
+            load_paths_async<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
             load_jac((t0 + 1) * PT, pjb + PT * 12);
         }
+        cp_async_wait_all();
         __syncthreads();
         produce<KT, KIND, 1>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, j.s);
         __syncthreads();
@@ -184,6 +185,11 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         const Buf& Pn = b ? B0 : B1;
         const float* pd = pdb + pb * PT * 12;
         const int* pv = pvb + pb * PT;
+        if (tile + 2 < t1) {  // slot of tile-1, free: in flight during this phase
+            const int nb2 = (int)((tile + 2 - t0) % 3);
+            load_paths_async<KIND>(a, PT, (tile + 2) * PT, count, pdb + nb2 * PT * 12, pvb + nb2 * PT);
+            load_jac((tile + 2) * PT, pjb + nb2 * PT * 12);
+        }
         if (tile + 1 < t1) {
             const int nb = (int)((tile + 1 - t0) % 3);
             produce<KT, KIND, 1>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, j.s);
@@ -302,11 +308,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                     for (int v = 0; v < VR; ++v) V[u][v] = fmaf(cnt[u], y[v], V[u][v]);
             }
         }
-        if (tile + 2 < t1) {
-            const int nb2 = (int)((tile + 2 - t0) % 3);
-            load_paths<KIND>(a, PT, (tile + 2) * PT, count, pdb + nb2 * PT * 12, pvb + nb2 * PT);
-            load_jac((tile + 2) * PT, pjb + nb2 * PT * 12);
-        }
+        cp_async_wait_all();
         __syncthreads();
     }
     // ---- outputs of this CTA (shared memory reused)
