@@ -104,6 +104,7 @@ struct st_ctx {
     DevBuf sig_e, sig_g;             // impulse responses: call spectrum [F], combined spectra [rows][F]
     DevBuf ray_tab;                  // zone table of the zonal ray set
     DevBuf adj_jac;                  // backward: chain jacobians of the specular paths [paths][12]
+    DevBuf hit_tri, hit_t, vis_q, los_q, trav_cnt;  // lane-refill traversal: closest hits, query queues, counters
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -266,7 +267,7 @@ st_status st_destroy(st_ctx* c) {
             release(*b);
     for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->tables.bband,
                       &c->sig_e, &c->sig_g,
-                      &c->ray_tab, &c->adj_jac})
+                      &c->ray_tab, &c->adj_jac, &c->hit_tri, &c->hit_t, &c->vis_q, &c->los_q, &c->trav_cnt})
         release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -569,6 +570,10 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, grow(c->queries, 64), "alloc");
     CKC(c, grow(c->flags, 16), "alloc");
     CKC(c, grow(c->R, 16), "alloc");
+    CKC(c, grow(c->hit_tri, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    CKC(c, grow(c->hit_t, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    CKC(c, grow(c->vis_q, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    CKC(c, grow(c->trav_cnt, 64), "alloc");
     CKC(c, grow(c->rec_tri, (size_t)std::max<int64_t>(NB, 1) * 4), "alloc");
     CKC(c, grow(c->rec_p, (size_t)std::max<int64_t>(NB, 1) * 12), "alloc");
     CKC(c, grow(c->rec_d, (size_t)std::max<int64_t>(NB, 1) * 12), "alloc");
@@ -587,6 +592,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         CKC(c, grow(c->cand_tri, (size_t)K * 4), "alloc");
         CKC(c, grow(c->cand_p, (size_t)K * 12), "alloc");
         CKC(c, grow(c->keep, (size_t)K), "alloc");
+        CKC(c, grow(c->los_q, (size_t)K * 4), "alloc");
     }
     const int32_t chunks_spec = accum_chunks(NB, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb);
     const int32_t chunks_diff = accum_chunks(K, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb);
@@ -660,6 +666,11 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         ta.rec_los = ptr<uint8_t>(c->rec_los);
         ta.flags = ptr<uint32_t>(c->flags);
         ta.queries = qctr;
+        ta.hit_tri = ptr<int32_t>(c->hit_tri);
+        ta.hit_t = ptr<float>(c->hit_t);
+        ta.vis_q = ptr<uint32_t>(c->vis_q);
+        ta.vis_n = ptr<uint32_t>(c->trav_cnt);
+        ta.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 16);
         CKC(c, trace_rays(ta, s, c->tune.rays_per_block > 0 ? c->tune.rays_per_block : 128), "trace");
     }
     if (stats) CKC(c, cudaEventRecord(c->ev[1], s), "event");
@@ -694,6 +705,9 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         da.keep = ptr<uint8_t>(c->keep);
         da.flags = ptr<uint32_t>(c->flags);
         da.queries = qctr;
+        da.los_q = ptr<uint32_t>(c->los_q);
+        da.los_n = ptr<uint32_t>(c->trav_cnt) + 1;
+        da.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 32);
         CKC(c, diffraction_sample(da, s), "diffraction");
     }
     if (stats) CKC(c, cudaEventRecord(c->ev[2], s), "event");

@@ -138,6 +138,11 @@ struct TraceArgs {
     // queues
     uint32_t* q_in; uint32_t* q_out;
     uint32_t* n_in; uint32_t* n_out;
+    // closest hits of the current bounce [N], the visibility queue (record ids) and the lane-refill
+    // counters (three per bounce)
+    int32_t* hit_tri; float* hit_t;
+    uint32_t* vis_q; uint32_t* vis_n;
+    unsigned long long* ctr;
     // records [N][B]
     int32_t* rec_tri;
     float* rec_p;    // [N][B][3]
@@ -177,6 +182,8 @@ struct DiffArgs {
     int32_t* cand_tri;
     float* cand_p;        // [K][3]
     uint8_t* keep;
+    uint32_t* los_q; uint32_t* los_n;  // candidates that passed the filters: their line-of-sight queries
+    unsigned long long* ctr;           // lane-refill counter of the line-of-sight kernel
     uint32_t* flags;
     unsigned long long* queries;
 };

@@ -7,10 +7,16 @@
 // when the float32 triangle test would hit inside it; the closest hit is the smallest
 // (t, triangle index), which makes the result independent of the tree's shape.
 //
-// Bounces run as a wavefront: one launch per bounce over a compacted queue of live rays; each
-// thread finds the closest hit, reflects, accumulates the float64 path length, traces the
-// visibility ray to the receiver reference point and writes the record [ray][bounce].
+// Bounces run as a wavefront over a compacted queue of live rays, three launches per bounce: closest
+// hits, shading (reflection, float64 path length, the record [ray][bounce], the next queue and the
+// visibility queue), and the visibility rays to the receiver reference point.  The traversal kernels
+// are persistent with lane refill: a lane whose query has finished takes the next one from a
+// warp-aggregated atomic counter while the other lanes of its warp continue, so a warp is not held by
+// its longest query.  Results do not depend on the order: closest hits are the smallest (t, triangle
+// index), visibility is the absence of any hit in the segment.
 // Compiled with -fmad=false (see st_geom.cuh).
+#include <algorithm>
+
 #include "st_geom.cuh"
 #include "st_internal.cuh"
 #include "st_trace_dev.cuh"
@@ -21,46 +27,103 @@ namespace {
 
 using namespace trv;
 
-// One bounce of Algorithm 1 over the live-ray queue.
-__global__ void __launch_bounds__(256, 4) k_bounce(const TraceArgs a, int j, int64_t n_first) {
+// lanes that need a query claim consecutive indices from *ctr (one atomic per warp and round); -1 for
+// lanes that did not ask.  All 32 lanes of the warp call it.
+__device__ __forceinline__ int64_t claim(unsigned long long* ctr, bool need, unsigned long long* queries) {
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, need);
+    if (m == 0u) return -1;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long b = 0;
+    if (lane == leader) b = atomicAdd(ctr, (unsigned long long)__popc(m));
+    b = __shfl_sync(full, b, leader);
+    (void)queries;
+    return need ? (int64_t)(b + (unsigned long long)__popc(m & ((1u << lane) - 1u))) : -1;
+}
+
+constexpr int kTravBlock = 128;
+constexpr int kRefill = 8;  // a warp stops stepping to refill once this many of its lanes wait for a query
+
+// Closest hits of one bounce: item idx of the live-ray queue (the first bounce in direction order).
+__global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, int j, int64_t n_first) {
     const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    const int64_t n = (j == 0) ? n_first : (int64_t)*a.n_in;
+    const unsigned full = 0xffffffffu;
+    int2 stack[kStack];
+    TravState S;
+    int64_t ray = -1;
+    bool live = false, exhausted = false;
+    while (true) {
+        const bool need = !live && !exhausted;
+        const int64_t idx = claim(a.ctr + 0, need, nullptr);
+        if (need) {
+            if (idx < n) {
+                ray = (j == 0) ? (a.perm ? (int64_t)a.perm[idx] : idx) : (int64_t)a.q_in[idx];
+                f3 o, d;
+                int32_t prev;
+                if (j == 0) {
+                    o = f3{a.s[0], a.s[1], a.s[2]};
+                    d = rotate(a.q, f3{a.dirs[3 * ray], a.dirs[3 * ray + 1], a.dirs[3 * ray + 2]});
+                    prev = -1;
+                } else {
+                    o = f3{a.ox[ray], a.oy[ray], a.oz[ray]};
+                    d = f3{a.dx[ray], a.dy[ray], a.dz[ray]};
+                    prev = a.prev[ray];
+                }
+                trav_init(S, T, o, d, prev, a.t_min, __int_as_float(0x7f800000));
+                live = true;
+            } else {
+                exhausted = true;
+            }
+        }
+        if (__ballot_sync(full, live) == 0u) break;
+        while (true) {
+            if (live && trav_step<false>(T, S, stack, a.flags)) {
+                trav_count<false>(T, S);
+                a.hit_tri[ray] = S.best;
+                a.hit_t[ray] = S.tb;
+                live = false;
+            }
+            const unsigned lv = __ballot_sync(full, live);
+            const unsigned nd = __ballot_sync(full, !live && !exhausted);
+            if (lv == 0u || __popc(nd) >= kRefill) break;
+        }
+    }
+}
+
+// Shading of one bounce: record, next queue, visibility queue (Algorithm 1's steps after the hit).
+__global__ void k_shade(const TraceArgs a, int j, int64_t n_first) {
     const int64_t n_live = (j == 0) ? n_first : (int64_t)*a.n_in;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const f3 R{a.R[0], a.R[1], a.R[2]};  // device copy written by k_centroid
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_live; idx += stride) {
         const int64_t ray = (j == 0) ? (a.perm ? (int64_t)a.perm[idx] : idx) : (int64_t)a.q_in[idx];
+        warp_count(a.queries + 0);
+        const int32_t tri = a.hit_tri[ray];
+        if (tri < 0) continue;
+        const float t = a.hit_t[ray];
         f3 o, d;
         double r;
-        int32_t prev;
         if (j == 0) {
             o = f3{a.s[0], a.s[1], a.s[2]};
             d = rotate(a.q, f3{a.dirs[3 * ray], a.dirs[3 * ray + 1], a.dirs[3 * ray + 2]});
             r = 0.0;
-            prev = -1;
         } else {
             o = f3{a.ox[ray], a.oy[ray], a.oz[ray]};
             d = f3{a.dx[ray], a.dy[ray], a.dz[ray]};
             r = a.racc[ray];
-            prev = a.prev[ray];
         }
-        float t;
-        const int32_t tri = traverse<false>(T, o, d, prev, a.t_min, __int_as_float(0x7f800000), &t, a.flags);
-        warp_count(a.queries + 0);
-        if (tri < 0) continue;
-        warp_count(a.queries + 1);
         const float tdx = t * d.x, tdy = t * d.y, tdz = t * d.z;
         const f3 P{o.x + tdx, o.y + tdy, o.z + tdz};
-        const f3 n{a.nrm[3 * tri], a.nrm[3 * tri + 1], a.nrm[3 * tri + 2]};
-        const float dn = dot(d, n);
+        const f3 nv{a.nrm[3 * tri], a.nrm[3 * tri + 1], a.nrm[3 * tri + 2]};
+        const float dn = dot(d, nv);
         const float k2 = 2.0f * dn;
-        const float knx = k2 * n.x, kny = k2 * n.y, knz = k2 * n.z;
+        const float knx = k2 * nv.x, kny = k2 * nv.y, knz = k2 * nv.z;
         float len;
         const f3 dr = normalize(f3{d.x - knx, d.y - kny, d.z - knz}, &len);
         r = r + (double)t;
-        const bool vis = visible(T, P, R, tri, a.t_min, a.los_eps, a.flags);
         const int64_t id = ray * a.B + j;
         a.rec_tri[id] = tri;
-        a.rec_los[id] = vis ? 1 : 0;
+        a.rec_los[id] = 0;
         a.rec_r[id] = r;
         a.rec_p[3 * id] = P.x;
         a.rec_p[3 * id + 1] = P.y;
@@ -68,6 +131,15 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const TraceArgs a, int j, int
         a.rec_d[3 * id] = dr.x;
         a.rec_d[3 * id + 1] = dr.y;
         a.rec_d[3 * id + 2] = dr.z;
+        const int lane = threadIdx.x & 31;
+        {  // visibility query of this record (warp-aggregated append)
+            const unsigned active = __activemask();
+            const int leader = __ffs(active) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(a.vis_n, (uint32_t)__popc(active));
+            base = __shfl_sync(active, base, leader);
+            a.vis_q[base + __popc(active & ((1u << lane) - 1u))] = (uint32_t)id;
+        }
         if (r < a.r_max && j + 1 < a.B) {
             a.ox[ray] = P.x;
             a.oy[ray] = P.y;
@@ -77,9 +149,7 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const TraceArgs a, int j, int
             a.dz[ray] = dr.z;
             a.racc[ray] = r;
             a.prev[ray] = tri;
-            // warp-aggregated append to the next queue
             const unsigned active = __activemask();
-            const int lane = threadIdx.x & 31;
             const int leader = __ffs(active) - 1;
             uint32_t base = 0;
             if (lane == leader) base = atomicAdd(a.n_out, (uint32_t)__popc(active));
@@ -89,10 +159,63 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const TraceArgs a, int j, int
     }
 }
 
+// Visibility of `target` from the points of a queue (record or candidate ids): out[id] = 1 when no
+// triangle other than excl[id] lies on the segment (t_min, |target - p| - eps).
+// The target is tgt_dev[0..2] when given (the receiver reference point, written on the device), else (tx, ty, tz).
+__global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const uint32_t* queue, const uint32_t* count,
+                                                           const float* pts, const int32_t* excl,
+                                                           const float* tgt_dev, float tx, float ty, float tz,
+                                                           float t_min, float eps, uint8_t* out,
+                                                           unsigned long long* ctr, uint32_t* flags,
+                                                           unsigned long long* queries) {
+    const int64_t n = *count;
+    const unsigned full = 0xffffffffu;
+    const f3 target = tgt_dev ? f3{tgt_dev[0], tgt_dev[1], tgt_dev[2]} : f3{tx, ty, tz};
+    int2 stack[kStack];
+    TravState S;
+    int64_t id = -1;
+    bool live = false, exhausted = false;
+    while (true) {
+        const bool need = !live && !exhausted;
+        const int64_t idx = claim(ctr, need, nullptr);
+        if (need) {
+            if (idx < n) {
+                id = queue[idx];
+                warp_count(queries + 1);
+                const f3 o{pts[3 * id], pts[3 * id + 1], pts[3 * id + 2]};
+                float L;
+                const f3 u = normalize(sub(target, o), &L);
+                const float tmax = L - eps;
+                if (!(tmax > t_min)) {
+                    out[id] = 1;
+                } else {
+                    trav_init(S, T, o, u, excl[id], t_min, tmax);
+                    live = true;
+                }
+            } else {
+                exhausted = true;
+            }
+        }
+        const unsigned lv0 = __ballot_sync(full, live);
+        const unsigned nd0 = __ballot_sync(full, !live && !exhausted);
+        if (lv0 == 0u && nd0 == 0u) break;
+        while (true) {
+            if (live && trav_step<true>(T, S, stack, flags)) {
+                trav_count<true>(T, S);
+                out[id] = S.best < 0 ? 1 : 0;
+                live = false;
+            }
+            const unsigned lv = __ballot_sync(full, live);
+            const unsigned nd = __ballot_sync(full, !live && !exhausted);
+            if (lv == 0u || __popc(nd) >= kRefill) break;
+        }
+    }
+}
+
 // Sec. III-D: sample g of the global list -> mesh m, local index s; Philox(s, m, pose, 0) selects a
-// triangle through the mesh's integer CDF and a barycentric point; then the filters.
+// triangle through the mesh's integer CDF and a barycentric point; then the field-of-view and
+// incidence filters; the candidates that pass are queued for the line-of-sight test (k_visible).
 __global__ void __launch_bounds__(128, 8) k_diffraction(const DiffArgs a) {
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const f3 s{a.s[0], a.s[1], a.s[2]};
     const f3 fwd{a.fwd[0], a.fwd[1], a.fwd[2]};
@@ -149,15 +272,20 @@ __global__ void __launch_bounds__(128, 8) k_diffraction(const DiffArgs a) {
             const f3 n{a.nrm[3 * t], a.nrm[3 * t + 1], a.nrm[3 * t + 2]};
             if (!(fabsf(dot(n, vn)) >= a.cos_inc)) ok = false;
         }
-        if (ok) {
-            warp_count(a.queries + 1);
-            ok = visible(T, o, s, t, a.t_min, a.los_eps, a.flags);
-        }
         a.cand_tri[g] = t;
         a.cand_p[3 * g] = p[0];
         a.cand_p[3 * g + 1] = p[1];
         a.cand_p[3 * g + 2] = p[2];
-        a.keep[g] = ok ? 1 : 0;
+        a.keep[g] = 0;  // set by the line-of-sight kernel for the candidates that passed the filters
+        if (ok) {
+            const unsigned active = __activemask();
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(active) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(a.los_n, (uint32_t)__popc(active));
+            base = __shfl_sync(active, base, leader);
+            a.los_q[base + __popc(active & ((1u << lane) - 1u))] = (uint32_t)g;
+        }
     }
 }
 
@@ -222,8 +350,15 @@ cudaError_t direction_order(const float* dirs, int64_t n, uint64_t* keys, uint32
     return radix_sort_u64(keys, perm, n, 32, scratch, s);
 }
 
+// persistent traversal grid: eight 128-thread CTAs per SM (64 registers)
+static unsigned trav_grid(int64_t n) {
+    const int64_t full = 152 * 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (n + kTravBlock - 1) / kTravBlock));
+}
+
 cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
     const unsigned grid = grid_for(a.N, block, 152 * 16);
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     for (int j = 0; j < a.B; ++j) {
         if (j > 0) {
             uint32_t* t = a.q_in;
@@ -234,19 +369,35 @@ cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
             a.n_out = c;
         }
         cudaError_t e = cudaMemsetAsync(a.n_out, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.vis_n, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.ctr, 0, 2 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
         note_launch();
-        k_bounce<<<grid, block, 0, s>>>(a, j, a.N);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        k_closest<<<trav_grid(a.N), kTravBlock, 0, s>>>(a, j, a.N);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        note_launch();
+        k_shade<<<grid, block, 0, s>>>(a, j, a.N);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        note_launch();
+        k_visible<<<trav_grid(a.N), kTravBlock, 0, s>>>(T, a.vis_q, a.vis_n, a.rec_p, a.rec_tri, a.R, 0.0f, 0.0f, 0.0f,
+                                                        a.t_min, a.los_eps, a.rec_los, a.ctr + 1, a.flags, a.queries);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 cudaError_t diffraction_sample(DiffArgs& a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(a.los_n, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.ctr, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     note_launch();
     k_diffraction<<<grid_for(a.K, 128, 152 * 16), 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    note_launch();
+    k_visible<<<trav_grid(a.K), kTravBlock, 0, s>>>(T, a.los_q, a.los_n, a.cand_p, a.cand_tri, nullptr, a.s[0], a.s[1],
+                                                    a.s[2], a.t_min, a.los_eps, a.keep, a.ctr, a.flags, a.queries);
     return cudaGetLastError();
 }
 

@@ -38,120 +38,148 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
     return tn <= tf;
 }
 
+// Resumable traversal: the state of one query, advanced by one wide node or one leaf per step, so that
+// a kernel can give a finished lane a new query while the other lanes of its warp continue.
+struct TravState {
+    WRay wr;
+    f3 o, inv;
+    int32_t exclude;
+    float t_min, t_max, tb;  // closest: tb = best t so far (+inf at first); any-hit: segment end (exclusive)
+    int32_t best, ref;
+    int sp, guard, n_nodes, n_tris;
+};
+
+__device__ __forceinline__ void trav_init(TravState& S, const Trav& T, f3 o, f3 d, int32_t exclude, float t_min,
+                                          float t_max) {
+    S.wr = wray(o, d);
+    S.o = o;
+    S.inv = f3{safe_inv(d.x), safe_inv(d.y), safe_inv(d.z)};
+    S.exclude = exclude;
+    S.t_min = t_min;
+    S.t_max = t_max;
+    S.tb = t_max;
+    S.best = -1;
+    S.ref = T.root;
+    S.sp = 0;
+    // every node of a proper tree is visited at most once: more iterations than nodes means a
+    // malformed hierarchy, reported through the flags instead of looping
+    S.guard = T.max_iter;
+    S.n_nodes = 0;
+    S.n_tris = 0;
+}
+
+// one node or leaf; true when the query has finished (S.best = hit triangle or -1, S.tb = its t)
+template <bool AnyHit>
+__device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* stack, uint32_t* flags) {
+    if (--S.guard < 0) {
+        atomicOr(flags, kFlagBadTree);
+        return true;
+    }
+    if (S.ref >= 0) {
+        // 4-wide node: children's bounds as lo.x, hi.x, lo.y, hi.y, lo.z, hi.z rows, then the refs
+        const float4* nd = T.nodes + 8 * (size_t)S.ref;
+        const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+        const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        ++S.n_nodes;
+        // boxes are padded, so a box holding a hit at t > t_min >= 0 exits at t > 0 after rounding
+        const f3 o = S.o, inv = S.inv;
+        const float tb = S.tb;
+        float t0, t1, t2, t3;
+        const int32_t r0 = __float_as_int(rf.x), r1 = __float_as_int(rf.y), r2 = __float_as_int(rf.z),
+                      r3 = __float_as_int(rf.w);
+        const bool h0 = slab(lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, o, inv, 0.0f, tb, &t0);
+        const bool h1 = slab(lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, o, inv, 0.0f, tb, &t1);
+        const bool h2 = r2 != kEmptyRef && slab(lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, o, inv, 0.0f, tb, &t2);
+        const bool h3 = r3 != kEmptyRef && slab(lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, o, inv, 0.0f, tb, &t3);
+        // order the hit children by entry distance (misses last): the nearest is visited next, the
+        // others are pushed farthest first (hit keys are clamped below +inf, so the hits sort strictly
+        // before the misses)
+        const float inf = __int_as_float(0x7f800000), big = 3.0e38f;
+        float k0 = h0 ? fminf(t0, big) : inf, k1 = h1 ? fminf(t1, big) : inf;
+        float k2 = h2 ? fminf(t2, big) : inf, k3 = h3 ? fminf(t3, big) : inf;
+        int32_t c0 = r0, c1 = r1, c2 = r2, c3 = r3;
+        auto cx = [](float& ka, int32_t& ca, float& kb, int32_t& cb) {
+            if (kb < ka) {
+                const float tk = ka;
+                ka = kb;
+                kb = tk;
+                const int32_t tc = ca;
+                ca = cb;
+                cb = tc;
+            }
+        };
+        cx(k0, c0, k1, c1);
+        cx(k2, c2, k3, c3);
+        cx(k0, c0, k2, c2);
+        cx(k1, c1, k3, c3);
+        cx(k1, c1, k2, c2);
+        const int nh = (int)h0 + (int)h1 + (int)h2 + (int)h3;
+        if (nh > 0) {
+            if (S.sp + nh - 1 > kStack) {
+                atomicOr(flags, kFlagStackOverflow);
+            } else {
+                if (nh > 3) stack[S.sp++] = make_int2(c3, __float_as_int(k3));
+                if (nh > 2) stack[S.sp++] = make_int2(c2, __float_as_int(k2));
+                if (nh > 1) stack[S.sp++] = make_int2(c1, __float_as_int(k1));
+            }
+            S.ref = c0;
+            return false;
+        }
+    } else {
+        const int32_t code = ~S.ref;
+        const int first = code >> 3, cnt = (code & 7) + 1;
+        for (int i = first; i < first + cnt; ++i) {
+            const float4 v0 = __ldg(&T.tri_v[3 * i + 0]);
+            const int32_t id = __float_as_int(v0.w);
+            if (id == S.exclude) continue;
+            const float4 v1 = __ldg(&T.tri_v[3 * i + 1]);
+            const float4 v2 = __ldg(&T.tri_v[3 * i + 2]);
+            ++S.n_tris;
+            float th;
+            if (!wt_hit(S.wr, f3{v0.x, v0.y, v0.z}, f3{v1.x, v1.y, v1.z}, f3{v2.x, v2.y, v2.z}, &th)) continue;
+            if (!(th > S.t_min)) continue;
+            if (AnyHit) {
+                if (th < S.t_max) {
+                    S.tb = th;
+                    S.best = id;
+                    return true;
+                }
+            } else if (th < S.tb || (th == S.tb && id < S.best)) {
+                S.tb = th;
+                S.best = id;
+            }
+        }
+    }
+    // pop, skipping entries whose box starts beyond the best hit
+    while (S.sp > 0) {
+        const int2 top = stack[--S.sp];
+        if (__int_as_float(top.y) <= S.tb) {
+            S.ref = top.x;
+            return false;
+        }
+    }
+    return true;
+}
+
+template <bool AnyHit>
+__device__ __forceinline__ void trav_count(const Trav& T, const TravState& S) {
+    if (T.visits) {
+        atomicAdd(&T.visits[AnyHit ? 2 : 0], (unsigned long long)S.n_nodes);
+        atomicAdd(&T.visits[AnyHit ? 3 : 1], (unsigned long long)S.n_tris);
+    }
+}
+
 template <bool AnyHit>
 __device__ __forceinline__ int32_t traverse(const Trav& T, f3 o, f3 d, int32_t exclude, float t_min, float t_max,
                                             float* t_out, uint32_t* flags) {
-    const WRay wr = wray(o, d);
-    const f3 inv{safe_inv(d.x), safe_inv(d.y), safe_inv(d.z)};
-    int32_t best = -1;
-    float tb = t_max;  // closest: +inf; any-hit: the segment end (exclusive)
+    TravState S;
     int2 stack[kStack];
-    int sp = 0;
-    int32_t ref = T.root;
-    // every node of a proper tree is visited at most once: more iterations than nodes means a
-    // malformed hierarchy, reported through the flags instead of looping
-    int guard = T.max_iter;
-    int n_nodes = 0, n_tris = 0;
-    // the search interval for boxes: [-inf, tb]; t_min is enforced on triangles only
-    while (true) {
-        if (--guard < 0) {
-            atomicOr(flags, kFlagBadTree);
-            break;
-        }
-        if (ref >= 0) {
-            // 4-wide node: children's bounds as lo.x, hi.x, lo.y, hi.y, lo.z, hi.z rows, then the refs
-            const float4* nd = T.nodes + 8 * (size_t)ref;
-            const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
-            const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
-            ++n_nodes;
-            // boxes are padded, so a box holding a hit at t > t_min >= 0 exits at t > 0 after rounding
-            float t0, t1, t2, t3;
-            const int32_t r0 = __float_as_int(rf.x), r1 = __float_as_int(rf.y), r2 = __float_as_int(rf.z),
-                          r3 = __float_as_int(rf.w);
-            const bool h0 = slab(lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, o, inv, 0.0f, tb, &t0);
-            const bool h1 = slab(lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, o, inv, 0.0f, tb, &t1);
-            const bool h2 = r2 != kEmptyRef && slab(lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, o, inv, 0.0f, tb, &t2);
-            const bool h3 = r3 != kEmptyRef && slab(lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, o, inv, 0.0f, tb, &t3);
-            // order the hit children by entry distance (misses last): the nearest is visited next, the
-            // others are pushed farthest first
-            // (hit keys are clamped below +inf, so the hits sort strictly before the misses)
-            const float inf = __int_as_float(0x7f800000), big = 3.0e38f;
-            float k0 = h0 ? fminf(t0, big) : inf, k1 = h1 ? fminf(t1, big) : inf;
-            float k2 = h2 ? fminf(t2, big) : inf, k3 = h3 ? fminf(t3, big) : inf;
-            int32_t c0 = r0, c1 = r1, c2 = r2, c3 = r3;
-            auto cx = [](float& ka, int32_t& ca, float& kb, int32_t& cb) {
-                if (kb < ka) {
-                    const float tk = ka;
-                    ka = kb;
-                    kb = tk;
-                    const int32_t tc = ca;
-                    ca = cb;
-                    cb = tc;
-                }
-            };
-            cx(k0, c0, k1, c1);
-            cx(k2, c2, k3, c3);
-            cx(k0, c0, k2, c2);
-            cx(k1, c1, k3, c3);
-            cx(k1, c1, k2, c2);
-            const int nh = (int)h0 + (int)h1 + (int)h2 + (int)h3;
-            if (nh > 0) {
-                if (sp + nh - 1 > kStack) {
-                    atomicOr(flags, kFlagStackOverflow);
-                } else {
-                    if (nh > 3) stack[sp++] = make_int2(c3, __float_as_int(k3));
-                    if (nh > 2) stack[sp++] = make_int2(c2, __float_as_int(k2));
-                    if (nh > 1) stack[sp++] = make_int2(c1, __float_as_int(k1));
-                }
-                ref = c0;
-                continue;
-            }
-        } else {
-            const int32_t code = ~ref;
-            const int first = code >> 3, cnt = (code & 7) + 1;
-            for (int i = first; i < first + cnt; ++i) {
-                const float4 v0 = __ldg(&T.tri_v[3 * i + 0]);
-                const int32_t id = __float_as_int(v0.w);
-                if (id == exclude) continue;
-                const float4 v1 = __ldg(&T.tri_v[3 * i + 1]);
-                const float4 v2 = __ldg(&T.tri_v[3 * i + 2]);
-                ++n_tris;
-                float th;
-                if (!wt_hit(wr, f3{v0.x, v0.y, v0.z}, f3{v1.x, v1.y, v1.z}, f3{v2.x, v2.y, v2.z}, &th)) continue;
-                if (!(th > t_min)) continue;
-                if (AnyHit) {
-                    if (th < t_max) {
-                        *t_out = th;
-                        if (T.visits) {
-                            atomicAdd(&T.visits[2], (unsigned long long)n_nodes);
-                            atomicAdd(&T.visits[3], (unsigned long long)n_tris);
-                        }
-                        return id;
-                    }
-                } else if (th < tb || (th == tb && id < best)) {
-                    tb = th;
-                    best = id;
-                }
-            }
-        }
-        // pop, skipping entries whose box starts beyond the best hit
-        bool found = false;
-        while (sp > 0) {
-            const int2 top = stack[--sp];
-            if (__int_as_float(top.y) <= tb) {
-                ref = top.x;
-                found = true;
-                break;
-            }
-        }
-        if (!found) break;
+    trav_init(S, T, o, d, exclude, t_min, t_max);
+    while (!trav_step<AnyHit>(T, S, stack, flags)) {
     }
-    if (T.visits) {
-        atomicAdd(&T.visits[AnyHit ? 2 : 0], (unsigned long long)n_nodes);
-        atomicAdd(&T.visits[AnyHit ? 3 : 1], (unsigned long long)n_tris);
-    }
-    *t_out = tb;
-    return best;
+    trav_count<AnyHit>(T, S);
+    *t_out = S.tb;
+    return S.best;
 }
 
 // Visibility of `target` from o: direction normalize(target - o), t in (t_min, |target - o| - eps).
