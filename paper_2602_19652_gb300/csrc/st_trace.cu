@@ -42,7 +42,7 @@ __device__ __forceinline__ int64_t claim(unsigned long long* ctr, bool need, uns
 }
 
 constexpr int kTravBlock = 128;
-constexpr int kRefill = 8;  // a warp stops stepping to refill once this many of its lanes wait for a query
+constexpr int kRefill = 24;  // a warp stops stepping to refill once this many of its lanes wait for a query
 
 // Closest hits of one bounce: item idx of the live-ray queue (the first bounce in direction order).
 __global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, int j, int64_t n_first) {
