@@ -120,6 +120,7 @@ struct BatchState {
     DevBuf st_o[3], st_d[3], st_r, st_prev, q0, q1, counts, queries, flags;
     DevBuf rec_tri, rec_p, rec_d, rec_r, rec_los, cand_tri, cand_p, keep, dvis, ranges;
     DevBuf sflags, sscan, sidx, scratch;
+    DevBuf hit_tri, hit_t, vis_q, los_q;  // lane-refill traversal
     std::vector<DevBuf> partial;  // one per branch
     PathList spec, diff;
     int64_t N_total = 0, R_total = 0, K_total = 0, M_total = 0, MF_total = 0;
@@ -1243,7 +1244,8 @@ void batch_release(BatchState& B) {
     for (DevBuf* b : {&B.jobs_dev, &B.offs, &B.derived, &B.perm, &B.ord_keys, &B.ord_scr, &B.st_o[0], &B.st_o[1],
                       &B.st_o[2], &B.st_d[0], &B.st_d[1], &B.st_d[2], &B.st_r, &B.st_prev, &B.q0, &B.q1, &B.counts,
                       &B.queries, &B.flags, &B.rec_tri, &B.rec_p, &B.rec_d, &B.rec_r, &B.rec_los, &B.cand_tri,
-                      &B.cand_p, &B.keep, &B.dvis, &B.ranges, &B.sflags, &B.sscan, &B.sidx, &B.scratch})
+                      &B.cand_p, &B.keep, &B.dvis, &B.ranges, &B.sflags, &B.sscan, &B.sidx, &B.scratch, &B.hit_tri,
+                      &B.hit_t, &B.vis_q, &B.los_q})
         release(*b);
     for (auto& d : B.partial) release(d);
     for (auto& T : B.tables)
@@ -1317,6 +1319,13 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     a.ranges = ptr<uint32_t>(B.ranges);
     a.flags = ptr<uint32_t>(B.flags);
     a.queries = ptr<unsigned long long>(B.queries);
+    a.hit_tri = ptr<int32_t>(B.hit_tri);
+    a.hit_t = ptr<float>(B.hit_t);
+    a.vis_q = ptr<uint32_t>(B.vis_q);
+    a.los_q = ptr<uint32_t>(B.los_q);
+    a.vis_n = cnt + 4;  // counts: [0] [1] live queues, [2] [3] compaction totals, [4] [5] visibility queues,
+    a.los_n = cnt + 5;  // bytes 32..55 the three query counters
+    a.ctr = reinterpret_cast<unsigned long long*>(cnt + 8);
     const int64_t Rn = std::max<int64_t>(B.R_total, 1);
     CB(cudaMemsetAsync(B.flags.p, 0, 16, s));
     CB(cudaMemsetAsync(B.counts.p, 0, 64, s));
@@ -1543,6 +1552,9 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     CKC(c, grow(B.st_prev, (size_t)N1 * 4), "batch alloc");
     CKC(c, grow(B.q0, (size_t)N1 * 4), "batch alloc");
     CKC(c, grow(B.q1, (size_t)N1 * 4), "batch alloc");
+    CKC(c, grow(B.hit_tri, (size_t)N1 * 4), "batch alloc");
+    CKC(c, grow(B.hit_t, (size_t)N1 * 4), "batch alloc");
+    CKC(c, grow(B.vis_q, (size_t)N1 * 4), "batch alloc");
     CKC(c, grow(B.counts, 64), "batch alloc");
     CKC(c, grow(B.queries, 64), "batch alloc");
     CKC(c, grow(B.flags, 16), "batch alloc");
@@ -1554,6 +1566,7 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     CKC(c, grow(B.cand_tri, (size_t)K1 * 4), "batch alloc");
     CKC(c, grow(B.cand_p, (size_t)K1 * 12), "batch alloc");
     CKC(c, grow(B.keep, (size_t)K1), "batch alloc");
+    CKC(c, grow(B.los_q, (size_t)K1 * 4), "batch alloc");
     CKC(c, grow(B.dvis, (size_t)std::max<int64_t>(B.M_total, 1)), "batch alloc");
     CKC(c, grow(B.ranges, (size_t)n_jobs * 16), "batch alloc");
     CKC(c, grow(B.sflags, (size_t)(R1 + K1) * 4), "batch alloc");

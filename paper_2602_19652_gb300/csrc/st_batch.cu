@@ -8,6 +8,8 @@
 // spectra.  Poses are read from device memory at run time, so a captured CUDA graph of the batch can
 // be replayed after the caller updates them in place.  Compiled with -fmad=false like the single-pose
 // tracing kernels (same float32 steps, so the batched path sets equal the single-pose ones).
+#include <algorithm>
+
 #include "st_geom.cuh"
 #include "st_internal.cuh"
 #include "st_trace_dev.cuh"
@@ -34,54 +36,117 @@ __global__ void k_batch_prep(const JobDev* J, int n_jobs) {
     b.fwd[2] = f.z;
 }
 
-// one bounce level of Algorithm 1 over the live rays of every job (global ray ids)
-__global__ void __launch_bounds__(256, 4) k_bounce_batch(const BatchArgs a, int j, int64_t n_first) {
+// Global ray id of item idx of bounce j's live queue: the first bounce walks each job's rays in its
+// direction order.
+__device__ __forceinline__ int64_t batch_ray(const BatchArgs& a, int j, int64_t idx, int* job_out) {
+    int64_t g = (j == 0) ? idx : (int64_t)a.q_in[idx];
+    const int job = find_job(a.ray_offs, a.n_jobs, g);
+    if (j == 0) {
+        const JobDev& b = a.jobs[job];
+        if (b.perm) g = b.ray_off + (int64_t)b.perm[g - b.ray_off];
+    }
+    *job_out = job;
+    return g;
+}
+
+// Closest hits of bounce j over the live rays of every job (Algorithm 1), persistent with lane refill:
+// each lane traverses its own job's scene.
+__global__ void __launch_bounds__(kTravBlock, 8) k_closest_batch(const BatchArgs a, int j, int64_t n_first) {
+    const int64_t n = (j == 0) ? n_first : (int64_t)*a.n_in;
+    const unsigned full = 0xffffffffu;
+    int2 stack[kStack];
+    TravState S;
+    Trav T{nullptr, nullptr, 0, 0, nullptr};
+    int64_t g = -1;
+    bool live = false, exhausted = false;
+    while (true) {
+        const bool need = !live && !exhausted;
+        const int64_t idx = claim(a.ctr + 0, need);
+        if (need) {
+            if (idx < n) {
+                int job;
+                g = batch_ray(a, j, idx, &job);
+                const JobDev& b = a.jobs[job];
+                if (j < b.B) {
+                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+                    f3 o, d;
+                    int32_t prev;
+                    if (j == 0) {
+                        const int64_t local = g - b.ray_off;
+                        const float q[4] = {b.q[0], b.q[1], b.q[2], b.q[3]};
+                        o = f3{b.s[0], b.s[1], b.s[2]};
+                        d = rotate(q, f3{b.dirs[3 * local], b.dirs[3 * local + 1], b.dirs[3 * local + 2]});
+                        prev = -1;
+                    } else {
+                        o = f3{a.ox[g], a.oy[g], a.oz[g]};
+                        d = f3{a.dx[g], a.dy[g], a.dz[g]};
+                        prev = a.prev[g];
+                    }
+                    trav_init(S, T, o, d, prev, a.t_min, __int_as_float(0x7f800000));
+                    live = true;
+                } else {
+                    a.hit_tri[g] = -1;
+                }
+            } else {
+                exhausted = true;
+            }
+        }
+        const unsigned lv0 = __ballot_sync(full, live);
+        const unsigned nd0 = __ballot_sync(full, !live && !exhausted);
+        if (lv0 == 0u && nd0 == 0u) break;
+        while (true) {
+            if (live && trav_step<false>(T, S, stack, a.flags)) {
+                a.hit_tri[g] = S.best;
+                a.hit_t[g] = S.tb;
+                live = false;
+            }
+            const unsigned lv = __ballot_sync(full, live);
+            const unsigned nd = __ballot_sync(full, !live && !exhausted);
+            if (lv == 0u || __popc(nd) >= kRefill) break;
+        }
+    }
+}
+
+// Shading of bounce j over every job: the record [job][ray][bounce], the next live queue and the queue
+// of records whose visibility to their job's receiver reference point is to be tested.
+__global__ void k_shade_batch(const BatchArgs a, int j, int64_t n_first) {
     const int64_t n_live = (j == 0) ? n_first : (int64_t)*a.n_in;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_live; idx += stride) {
-        int64_t g = (j == 0) ? idx : (int64_t)a.q_in[idx];
-        const int job = find_job(a.ray_offs, a.n_jobs, g);
+        int job;
+        const int64_t g = batch_ray(a, j, idx, &job);
         const JobDev& b = a.jobs[job];
         if (j >= b.B) continue;
-        int64_t local = g - b.ray_off;
-        if (j == 0 && b.perm) {  // first bounce in the job's direction order
-            local = b.perm[local];
-            g = b.ray_off + local;
-        }
-        const Trav T{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+        warp_count(a.queries + 0);
+        const int32_t tri = a.hit_tri[g];
+        if (tri < 0) continue;
+        warp_count(a.queries + 1);
+        const float t = a.hit_t[g];
+        const int64_t local = g - b.ray_off;
         f3 o, d;
         double r;
-        int32_t prev;
         if (j == 0) {
             const float q[4] = {b.q[0], b.q[1], b.q[2], b.q[3]};
             o = f3{b.s[0], b.s[1], b.s[2]};
             d = rotate(q, f3{b.dirs[3 * local], b.dirs[3 * local + 1], b.dirs[3 * local + 2]});
             r = 0.0;
-            prev = -1;
         } else {
             o = f3{a.ox[g], a.oy[g], a.oz[g]};
             d = f3{a.dx[g], a.dy[g], a.dz[g]};
             r = a.racc[g];
-            prev = a.prev[g];
         }
-        float t;
-        const int32_t tri = traverse<false>(T, o, d, prev, a.t_min, __int_as_float(0x7f800000), &t, a.flags);
-        warp_count(a.queries + 0);
-        if (tri < 0) continue;
-        warp_count(a.queries + 1);
         const float tdx = t * d.x, tdy = t * d.y, tdz = t * d.z;
         const f3 P{o.x + tdx, o.y + tdy, o.z + tdz};
-        const f3 n{b.nrm[3 * tri], b.nrm[3 * tri + 1], b.nrm[3 * tri + 2]};
-        const float dn = dot(d, n);
+        const f3 nv{b.nrm[3 * tri], b.nrm[3 * tri + 1], b.nrm[3 * tri + 2]};
+        const float dn = dot(d, nv);
         const float k2 = 2.0f * dn;
-        const float knx = k2 * n.x, kny = k2 * n.y, knz = k2 * n.z;
+        const float knx = k2 * nv.x, kny = k2 * nv.y, knz = k2 * nv.z;
         float len;
         const f3 dr = normalize(f3{d.x - knx, d.y - kny, d.z - knz}, &len);
         r = r + (double)t;
-        const bool vis = visible(T, P, f3{b.R[0], b.R[1], b.R[2]}, tri, a.t_min, a.los_eps, a.flags);
         const int64_t id = b.rec_off + local * b.B + j;
         a.rec_tri[id] = tri;
-        a.rec_los[id] = vis ? 1 : 0;
+        a.rec_los[id] = 0;
         a.rec_r[id] = r;
         a.rec_p[3 * id] = P.x;
         a.rec_p[3 * id + 1] = P.y;
@@ -89,6 +154,15 @@ __global__ void __launch_bounds__(256, 4) k_bounce_batch(const BatchArgs a, int 
         a.rec_d[3 * id] = dr.x;
         a.rec_d[3 * id + 1] = dr.y;
         a.rec_d[3 * id + 2] = dr.z;
+        const int lane = threadIdx.x & 31;
+        {
+            const unsigned active = __activemask();
+            const int leader = __ffs(active) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(a.vis_n, (uint32_t)__popc(active));
+            base = __shfl_sync(active, base, leader);
+            a.vis_q[base + __popc(active & ((1u << lane) - 1u))] = (uint32_t)id;
+        }
         if (r < a.r_max && j + 1 < b.B) {
             a.ox[g] = P.x;
             a.oy[g] = P.y;
@@ -99,7 +173,6 @@ __global__ void __launch_bounds__(256, 4) k_bounce_batch(const BatchArgs a, int 
             a.racc[g] = r;
             a.prev[g] = tri;
             const unsigned active = __activemask();
-            const int lane = threadIdx.x & 31;
             const int leader = __ffs(active) - 1;
             uint32_t base = 0;
             if (lane == leader) base = atomicAdd(a.n_out, (uint32_t)__popc(active));
@@ -109,14 +182,67 @@ __global__ void __launch_bounds__(256, 4) k_bounce_batch(const BatchArgs a, int 
     }
 }
 
-// diffraction samples of every job (global sample index), same steps as the single-pose kernel
+// Visibility over a queue of global ids (records or diffraction candidates) of every job: out[id] = 1
+// when no triangle other than excl[id] lies on the segment from pts[id] towards the job's receiver
+// reference point (to_emitter = 0) or its emitter (to_emitter = 1), ending los_eps short of it.
+__global__ void __launch_bounds__(kTravBlock, 8) k_visible_batch(const BatchArgs a, const uint32_t* queue,
+                                                                 const uint32_t* count, const int64_t* offs,
+                                                                 const float* pts, const int32_t* excl, int to_emitter,
+                                                                 uint8_t* out, unsigned long long* ctr) {
+    const int64_t n = *count;
+    const unsigned full = 0xffffffffu;
+    int2 stack[kStack];
+    TravState S;
+    Trav T{nullptr, nullptr, 0, 0, nullptr};
+    int64_t id = -1;
+    bool live = false, exhausted = false;
+    while (true) {
+        const bool need = !live && !exhausted;
+        const int64_t idx = claim(ctr, need);
+        if (need) {
+            if (idx < n) {
+                id = queue[idx];
+                const JobDev& b = a.jobs[find_job(offs, a.n_jobs, id)];
+                const float* tp = to_emitter ? b.s : b.R;
+                const f3 target{tp[0], tp[1], tp[2]};
+                const f3 o{pts[3 * id], pts[3 * id + 1], pts[3 * id + 2]};
+                float L;
+                const f3 u = normalize(sub(target, o), &L);
+                const float tmax = L - a.los_eps;
+                if (!(tmax > a.t_min)) {
+                    out[id] = 1;
+                } else {
+                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+                    trav_init(S, T, o, u, excl[id], a.t_min, tmax);
+                    live = true;
+                }
+            } else {
+                exhausted = true;
+            }
+        }
+        const unsigned lv0 = __ballot_sync(full, live);
+        const unsigned nd0 = __ballot_sync(full, !live && !exhausted);
+        if (lv0 == 0u && nd0 == 0u) break;
+        while (true) {
+            if (live && trav_step<true>(T, S, stack, a.flags)) {
+                out[id] = S.best < 0 ? 1 : 0;
+                live = false;
+            }
+            const unsigned lv = __ballot_sync(full, live);
+            const unsigned nd = __ballot_sync(full, !live && !exhausted);
+            if (lv == 0u || __popc(nd) >= kRefill) break;
+        }
+    }
+}
+
+// diffraction samples of every job (global sample index), same steps as the single-pose kernel; the
+// candidates that pass the filters are queued for the line-of-sight test (k_visible_batch)
 __global__ void __launch_bounds__(128, 8) k_diffraction_batch(const BatchArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.K_total; g += stride) {
         const int job = find_job(a.samp_offs, a.n_jobs, g);
         const JobDev& b = a.jobs[job];
         const int64_t gl = g - b.samp_off;
-        const Trav T{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
         int lo = 0, hi = b.n_obj;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -169,15 +295,21 @@ __global__ void __launch_bounds__(128, 8) k_diffraction_batch(const BatchArgs a)
             const f3 n{b.nrm[3 * t], b.nrm[3 * t + 1], b.nrm[3 * t + 2]};
             if (!(fabsf(dot(n, vn)) >= a.cos_inc)) ok = false;
         }
-        if (ok) {
-            warp_count(a.queries + 1);
-            ok = visible(T, o, s, t, a.t_min, a.los_eps, a.flags);
-        }
         a.cand_tri[g] = t;
         a.cand_p[3 * g] = p[0];
         a.cand_p[3 * g + 1] = p[1];
         a.cand_p[3 * g + 2] = p[2];
-        a.keep[g] = ok ? 1 : 0;
+        a.keep[g] = 0;  // set by the line-of-sight kernel for the candidates that passed the filters
+        if (ok) {
+            warp_count(a.queries + 1);
+            const unsigned active = __activemask();
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(active) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(a.los_n, (uint32_t)__popc(active));
+            base = __shfl_sync(active, base, leader);
+            a.los_q[base + __popc(active & ((1u << lane) - 1u))] = (uint32_t)g;
+        }
     }
 }
 
@@ -226,6 +358,12 @@ cudaError_t batch_prep(const JobDev* jobs, int n_jobs, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// persistent traversal grid: eight 128-thread CTAs per SM (64 registers)
+static unsigned trav_grid(int64_t n) {
+    const int64_t full = 152 * 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (n + kTravBlock - 1) / kTravBlock));
+}
+
 cudaError_t batch_trace(BatchArgs& a, int max_b, int64_t n_total, int block, cudaStream_t s) {
     const unsigned grid = grid_for(n_total, block, 152 * 16);
     for (int j = 0; j < max_b; ++j) {
@@ -238,19 +376,34 @@ cudaError_t batch_trace(BatchArgs& a, int max_b, int64_t n_total, int block, cud
             a.n_out = c;
         }
         cudaError_t e = cudaMemsetAsync(a.n_out, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.vis_n, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a.ctr, 0, 2 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
         note_launch();
-        k_bounce_batch<<<grid, block, 0, s>>>(a, j, n_total);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        k_closest_batch<<<trav_grid(n_total), kTravBlock, 0, s>>>(a, j, n_total);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        note_launch();
+        k_shade_batch<<<grid, block, 0, s>>>(a, j, n_total);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        note_launch();
+        k_visible_batch<<<trav_grid(n_total), kTravBlock, 0, s>>>(a, a.vis_q, a.vis_n, a.rec_offs, a.rec_p, a.rec_tri,
+                                                                  0, a.rec_los, a.ctr + 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 cudaError_t batch_diffraction(const BatchArgs& a, cudaStream_t s) {
     if (a.K_total <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(a.los_n, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.ctr + 2, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     note_launch();
     k_diffraction_batch<<<grid_for(a.K_total, 128, 152 * 16), 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
+    k_visible_batch<<<trav_grid(a.K_total), kTravBlock, 0, s>>>(a, a.los_q, a.los_n, a.samp_offs, a.cand_p,
+                                                                a.cand_tri, 1, a.keep, a.ctr + 2);
     return cudaGetLastError();
 }
 

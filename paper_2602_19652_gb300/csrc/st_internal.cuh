@@ -352,6 +352,11 @@ struct BatchArgs {
     // candidates [K_total], direct visibility [M_total]
     int32_t* cand_tri; float* cand_p; uint8_t* keep; uint8_t* dvis;
     uint32_t* ranges;          // [n_jobs][4]: specular first path, count, diffraction first path, count
+    // lane-refill traversal: closest hits [N_total], visibility queues of record / candidate ids and
+    // their lengths, query counters ([0] closest hits, [1] record visibility, [2] candidate visibility)
+    int32_t* hit_tri; float* hit_t;
+    uint32_t* vis_q; uint32_t* vis_n; uint32_t* los_q; uint32_t* los_n;
+    unsigned long long* ctr;
     uint32_t* flags;
     unsigned long long* queries;
 };

@@ -27,23 +27,6 @@ namespace {
 
 using namespace trv;
 
-// lanes that need a query claim consecutive indices from *ctr (one atomic per warp and round); -1 for
-// lanes that did not ask.  All 32 lanes of the warp call it.
-__device__ __forceinline__ int64_t claim(unsigned long long* ctr, bool need, unsigned long long* queries) {
-    const unsigned full = 0xffffffffu;
-    const unsigned m = __ballot_sync(full, need);
-    if (m == 0u) return -1;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    unsigned long long b = 0;
-    if (lane == leader) b = atomicAdd(ctr, (unsigned long long)__popc(m));
-    b = __shfl_sync(full, b, leader);
-    (void)queries;
-    return need ? (int64_t)(b + (unsigned long long)__popc(m & ((1u << lane) - 1u))) : -1;
-}
-
-constexpr int kTravBlock = 128;
-constexpr int kRefill = 24;  // a warp stops stepping to refill once this many of its lanes wait for a query
-
 // Closest hits of one bounce: item idx of the live-ray queue (the first bounce in direction order).
 __global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, int j, int64_t n_first) {
     const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
@@ -55,7 +38,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, in
     bool live = false, exhausted = false;
     while (true) {
         const bool need = !live && !exhausted;
-        const int64_t idx = claim(a.ctr + 0, need, nullptr);
+        const int64_t idx = claim(a.ctr + 0, need);
         if (need) {
             if (idx < n) {
                 ray = (j == 0) ? (a.perm ? (int64_t)a.perm[idx] : idx) : (int64_t)a.q_in[idx];
@@ -177,7 +160,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const u
     bool live = false, exhausted = false;
     while (true) {
         const bool need = !live && !exhausted;
-        const int64_t idx = claim(ctr, need, nullptr);
+        const int64_t idx = claim(ctr, need);
         if (need) {
             if (idx < n) {
                 id = queue[idx];

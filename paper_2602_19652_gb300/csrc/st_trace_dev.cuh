@@ -182,6 +182,22 @@ __device__ __forceinline__ int32_t traverse(const Trav& T, f3 o, f3 d, int32_t e
     return S.best;
 }
 
+// Lane refill (persistent traversal kernels): the lanes that need a query claim consecutive indices
+// from *ctr (one atomic per warp and round); -1 for lanes that did not ask.  All 32 lanes call it.
+__device__ __forceinline__ int64_t claim(unsigned long long* ctr, bool need) {
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, need);
+    if (m == 0u) return -1;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long b = 0;
+    if (lane == leader) b = atomicAdd(ctr, (unsigned long long)__popc(m));
+    b = __shfl_sync(full, b, leader);
+    return need ? (int64_t)(b + (unsigned long long)__popc(m & ((1u << lane) - 1u))) : -1;
+}
+
+constexpr int kTravBlock = 128;
+constexpr int kRefill = 24;  // a warp stops stepping to refill once this many of its lanes wait for a query
+
 // Visibility of `target` from o: direction normalize(target - o), t in (t_min, |target - o| - eps).
 __device__ __forceinline__ bool visible(const Trav& T, f3 o, f3 target, int32_t exclude, float t_min, float eps,
                                         uint32_t* flags) {
