@@ -38,7 +38,7 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
     return tn <= tf;
 }
 
-// Resumable traversal: the state of one query, advanced by one wide node or one leaf per step, so that
+// Resumable traversal: the state of one query, advanced by one wide node or one leaf triangle per step, so that
 // a kernel can give a finished lane a new query while the other lanes of its warp continue.
 struct TravState {
     WRay wr;
@@ -68,7 +68,7 @@ __device__ __forceinline__ void trav_init(TravState& S, const Trav& T, f3 o, f3 
     S.n_tris = 0;
 }
 
-// one node or leaf; true when the query has finished (S.best = hit triangle or -1, S.tb = its t)
+// one node or one leaf triangle; true when the query has finished (S.best = hit triangle or -1, S.tb = its t)
 template <bool AnyHit>
 __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* stack, uint32_t* flags) {
     if (--S.guard < 0) {
@@ -126,28 +126,34 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* sta
             return false;
         }
     } else {
+        // one triangle of the leaf per step (leaf code: first triangle << 3 | triangles left after it), so
+        // lanes in leaves and lanes in inner nodes of the same warp stay in step
         const int32_t code = ~S.ref;
-        const int first = code >> 3, cnt = (code & 7) + 1;
-        for (int i = first; i < first + cnt; ++i) {
-            const float4 v0 = __ldg(&T.tri_v[3 * i + 0]);
-            const int32_t id = __float_as_int(v0.w);
-            if (id == S.exclude) continue;
+        const int i = code >> 3, rest = code & 7;
+        const float4 v0 = __ldg(&T.tri_v[3 * i + 0]);
+        const int32_t id = __float_as_int(v0.w);
+        if (id != S.exclude) {
             const float4 v1 = __ldg(&T.tri_v[3 * i + 1]);
             const float4 v2 = __ldg(&T.tri_v[3 * i + 2]);
             ++S.n_tris;
             float th;
-            if (!wt_hit(S.wr, f3{v0.x, v0.y, v0.z}, f3{v1.x, v1.y, v1.z}, f3{v2.x, v2.y, v2.z}, &th)) continue;
-            if (!(th > S.t_min)) continue;
-            if (AnyHit) {
-                if (th < S.t_max) {
+            if (wt_hit(S.wr, f3{v0.x, v0.y, v0.z}, f3{v1.x, v1.y, v1.z}, f3{v2.x, v2.y, v2.z}, &th) &&
+                th > S.t_min) {
+                if (AnyHit) {
+                    if (th < S.t_max) {
+                        S.tb = th;
+                        S.best = id;
+                        return true;
+                    }
+                } else if (th < S.tb || (th == S.tb && id < S.best)) {
                     S.tb = th;
                     S.best = id;
-                    return true;
                 }
-            } else if (th < S.tb || (th == S.tb && id < S.best)) {
-                S.tb = th;
-                S.best = id;
             }
+        }
+        if (rest > 0) {
+            S.ref = ~(((i + 1) << 3) | (rest - 1));
+            return false;
         }
     }
     // pop, skipping entries whose box starts beyond the best hit
