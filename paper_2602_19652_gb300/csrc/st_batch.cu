@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_closest_batch(const BatchArgs
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefill) break;
+            if (lv == 0u || __popc(nd) >= kRefillClosest) break;
         }
     }
 }
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_batch(const BatchArgs
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefill) break;
+            if (lv == 0u || __popc(nd) >= kRefillAny) break;
         }
     }
 }

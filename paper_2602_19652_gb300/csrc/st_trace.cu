@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, in
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefill) break;
+            if (lv == 0u || __popc(nd) >= kRefillClosest) break;
         }
     }
 }
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const u
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefill) break;
+            if (lv == 0u || __popc(nd) >= kRefillAny) break;
         }
     }
 }
