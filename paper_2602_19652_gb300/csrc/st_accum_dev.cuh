@@ -125,7 +125,7 @@ struct Geom {
 //   tab [PT][KB] float4      per (path, bin): (log2 X, log2 X, g, g) specular, (X, X, -, -) diffraction,
 //                            bin kb + s*KT + kk stored at i = kk*NS + s
 //   za  [PT][NS][TP] ulonglong2  phasor at bin kb + s*KT of the two mics of pair tp (re pair, im pair)
-//   wst [PT][TP][4] u64      one-bin step (re, im) and two-bin step (re, im) of the pair
+//   wst [PT][4][TP] u64      one-bin step re, im and two-bin step re, im of the pair (component-major)
 //   ngp [PT][TP] u64         -gamma^2 of the pair
 //   adj [PT][TP][7] u64      (adjoint only) unit(m - P) xyz, lobe-angle vector xyz (specular) or
 //                            -unit(o - s) xyz (diffraction), 1 / r of the pair
@@ -380,14 +380,14 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
         const int pair = ml >> 1, half = ml & 1;
         const int m = mic0 + ml;
         float* zf = reinterpret_cast<float*>(B.za + (size_t)p * NS * TP + pair);
-        float* wf = reinterpret_cast<float*>(B.wst + ((size_t)p * TP + pair) * 4);
+        float* wf = reinterpret_cast<float*>(B.wst + (size_t)p * 4 * TP + pair);  // component c at wf[2 TP c]
         float* nf = reinterpret_cast<float*>(B.ngp + (size_t)p * TP + pair);
         if (!pv[p] || m >= a.M) {
             for (int s_ = 0; s_ < NS; ++s_) {
                 zf[(size_t)s_ * TP * 4 + half] = 0.0f;
                 zf[(size_t)s_ * TP * 4 + 2 + half] = 0.0f;
             }
-            for (int q = 0; q < 4; ++q) wf[2 * q + half] = 0.0f;
+            for (int q = 0; q < 4; ++q) wf[2 * TP * q + half] = 0.0f;
             nf[half] = 0.0f;
             for (int b = 0; b < g.NB; ++b) B.dband[((size_t)p * MP + ml) * g.NB + b] = 0.0f;
             if (ADJ) {
@@ -447,9 +447,9 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
         const float2 W1 = make_float2(a1 * c1, a1 * s1);
         const float2 W2 = cmul(W1, W1);  // two bins
         wf[0 + half] = W1.x;
-        wf[2 + half] = W1.y;
-        wf[4 + half] = W2.x;
-        wf[6 + half] = W2.y;
+        wf[2 * TP + half] = W1.y;
+        wf[4 * TP + half] = W2.x;
+        wf[6 * TP + half] = W2.y;
         nf[half] = -gam2;
         float2 WK = W2;  // KT bins by repeated squaring (KT is a power of two)
         for (int q = 2; q < KT; q *= 2) WK = cmul(WK, WK);

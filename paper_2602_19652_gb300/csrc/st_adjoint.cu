@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         }
         for (int p = 0; p < PT; ++p) {
             const ulonglong2 z0 = C.za[((size_t)p * NS + s) * TP + tp];
-            const u64* w = C.wst + ((size_t)p * TP + tp) * 4;
-            const u64 w1r = w[0], w1i = w[1], w2r = w[2], w2i = w[3];
+            const u64* w = C.wst + (size_t)p * 4 * TP + tp;  // component-major: conflict-free 64-bit loads
+            const u64 w1r = w[0], w1i = w[TP], w2r = w[2 * TP], w2i = w[3 * TP];
             const u64 nw2i = fmul2(w2i, pk2(-1.0f, -1.0f));
             const u64 ng = C.ngp[(size_t)p * TP + tp];
             u64 er = z0.x, ei = z0.y, orr = er, oi = ei;
