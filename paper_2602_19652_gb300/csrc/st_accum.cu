@@ -125,6 +125,9 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
                 if (KIND == 0) {
                     mt[e] = a.lk[(int64_t)mat * a.F + k];
                     mt[nm * KB + e] = a.g2[(int64_t)mat * a.F + k];
+                } else if (g.mat_direct) {  // the factor itself, as a pair for the two microphones of a thread
+                    const float x = (kb + s_ * KT + kk < a.F) ? ex2(a.lid[(int64_t)mat * a.F + k]) : 0.0f;
+                    reinterpret_cast<u64*>(mt)[e] = pk2(x, x);
                 } else {
                     mt[e] = a.lid[(int64_t)mat * a.F + k];
                 }
@@ -155,15 +158,21 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
             u64 orr = er, oi = ei;     // odd chain: bins 1, 3, 5, ...
             cmul2(orr, oi, w1r, w1i, fmul2(w1i, pk2(-1.0f, -1.0f)));
             const ulonglong2* trow = reinterpret_cast<const ulonglong2*>(C.tab) + (size_t)p * KB + s;
+            // diffraction with the material table read directly: the producer left the offset of the path's
+            // material row in the (otherwise unused) lobe slot
+            const u64* mrow = reinterpret_cast<const u64*>(mt) + s;
+            if (KIND == 1 && g.mat_direct) mrow += (int)(uint32_t)ng;
 #pragma unroll
             for (int kk = 0; kk < KT; ++kk) {
-                const ulonglong2 t = trow[kk * NS];
                 u64 E;
-                if (KIND == 0) {
+                if (KIND == 1 && g.mat_direct) {
+                    E = mrow[kk * NS];
+                } else if (KIND == 0) {
+                    const ulonglong2 t = trow[kk * NS];
                     const float2 arg = up2(ffma2(ng, t.y, t.x));
                     E = pk2(ex2(arg.x), ex2(arg.y));
                 } else {
-                    E = t.x;
+                    E = trow[kk * NS].x;
                 }
                 if (DIR) {  // receiver directivity, linear between bands
                     const float2 bwv = bwt[kk * NS + s];
@@ -402,7 +411,7 @@ cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
     read_tile_env();
     const int tp = a.tile_tp > 0 ? a.tile_tp : g_tile_tp;
     const size_t budget = a.tile_kb > 0 ? (size_t)a.tile_kb * 1024 : g_tile_budget;
-    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, tp, budget, DIR ? a.n_bands_tab : 0);
+    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, tp, budget, DIR ? a.n_bands_tab : 0, KIND == 1 && !a.etab);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =

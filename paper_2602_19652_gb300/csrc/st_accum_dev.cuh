@@ -116,6 +116,9 @@ struct Geom {
     int NB;                  // receiver directivity bands held per (path, mic); 0 = omni receivers
     int ADJ;                 // adjoint layout: per (path, pair) position-gradient vectors after ngp
     int mat_cached;          // material tables held in shared memory (n_mat small enough)
+    int mat_direct;          // diffraction without an emitter table: the term loop reads the per-(material, bin)
+                             // factor from the cached material table, at the row offset the producer leaves in
+                             // ngp; no per-(path, bin) table (tab has no space in the buffers)
     size_t mat_bytes;        // their size
     size_t buf_bytes;        // one pipeline buffer (tables + anchors of PT paths)
     size_t smem;
@@ -126,7 +129,7 @@ struct Geom {
 //                            bin kb + s*KT + kk stored at i = kk*NS + s
 //   za  [PT][NS][TP] ulonglong2  phasor at bin kb + s*KT of the two mics of pair tp (re pair, im pair)
 //   wst [PT][4][TP] u64      one-bin step re, im and two-bin step re, im of the pair (component-major)
-//   ngp [PT][TP] u64         -gamma^2 of the pair
+//   ngp [PT][TP] u64         -gamma^2 of the pair (diffraction, mat_direct: the path's material row offset)
 //   adj [PT][TP][7] u64      (adjoint only) unit(m - P) xyz, lobe-angle vector xyz (specular) or
 //                            -unit(o - s) xyz (diffraction), 1 / r of the pair
 // then two path-data buffers pd [PT][12] + valid [PT], then the per-CTA material tables.
@@ -144,7 +147,7 @@ __device__ __forceinline__ Buf buf_at(float4* base, const Geom& g, int b) {
     Buf B;
     char* p = reinterpret_cast<char*>(base) + (size_t)b * g.buf_bytes;
     B.tab = reinterpret_cast<float4*>(p);
-    B.za = reinterpret_cast<ulonglong2*>(B.tab + (size_t)g.PT * g.KB);
+    B.za = reinterpret_cast<ulonglong2*>(B.tab + (g.mat_direct ? (size_t)0 : (size_t)g.PT * g.KB));
     B.wst = reinterpret_cast<u64*>(B.za + (size_t)g.PT * g.NS * g.TP);
     B.ngp = B.wst + (size_t)g.PT * g.TP * 4;
     B.adj = B.ngp + (size_t)g.PT * g.TP;
@@ -275,10 +278,12 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
     const bool cached = g.mat_cached > 0;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // 1a: per (path, bin) factors, written in table order.  With NS % 4 == 0 and the material tables in
+    // 1a: per (path, bin) factors, written in table order (not needed when the term loop reads the
+    // material table directly).  With NS % 4 == 0 and the material tables in
     // shared memory, a thread builds four adjacent entries (same path and kk, subtiles s..s+3): one chain
     // decode, 128-bit loads of the material rows and four conflict-free 128-bit stores.
-    if (cached && (NS & 3) == 0 && !a.etab) {
+    if (KIND == 1 && g.mat_direct) {
+    } else if (cached && (NS & 3) == 0 && !a.etab) {
         const int KB4 = KB >> 2;
         const float invKB4 = 1.0f / (float)KB4;
         for (int e = tid; e < PT * KB4; e += nthr) {
@@ -450,7 +455,12 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
         wf[2 * TP + half] = W1.y;
         wf[4 * TP + half] = W2.x;
         wf[6 * TP + half] = W2.y;
-        nf[half] = -gam2;
+        if (KIND == 1 && g.mat_direct) {  // offset of the path's row in the material table (term loop)
+            const int matp = min((int)((__float_as_uint(d[8]) >> 8) & 255u), a.n_mat_tab - 1);
+            reinterpret_cast<int*>(nf)[half] = matp * KB;
+        } else {
+            nf[half] = -gam2;
+        }
         float2 WK = W2;  // KT bins by repeated squaring (KT is a power of two)
         for (int q = 2; q < KT; q *= 2) WK = cmul(WK, WK);
         for (int s_ = 0; s_ < NS; ++s_) {
@@ -463,7 +473,8 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
 
 
 // tp_max: mic pairs per CTA at most; budget: shared-memory bytes per CTA
-inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t budget = 96 * 1024, int dir_nb = 0) {
+inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t budget = 96 * 1024, int dir_nb = 0,
+                      int mat_direct = 0) {
     Geom g;
     g.NB = dir_nb;
     g.ADJ = 0;
@@ -476,9 +487,11 @@ inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t bu
     g.KB = g.NS * KT;
     g.n_mb = (M + g.MP - 1) / g.MP;
     g.n_bb = (F + g.KB - 1) / g.KB;
-    const size_t per_path = (size_t)g.KB * 16 + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40 + (size_t)g.MP * dir_nb * 4;
-    const size_t mat_bytes = (size_t)2 * n_mat * g.KB * 4;
+    const size_t mat_bytes = (size_t)2 * n_mat * g.KB * 4;  // two floats or one packed pair per (material, bin)
     g.mat_cached = mat_bytes <= 24 * 1024 ? 1 : 0;
+    g.mat_direct = (mat_direct && g.mat_cached) ? 1 : 0;
+    const size_t per_path = (g.mat_direct ? (size_t)0 : (size_t)g.KB * 16) + (size_t)g.NS * g.TP * 16 +
+                            (size_t)g.TP * 40 + (size_t)g.MP * dir_nb * 4;
     // fixed region: cached material tables, then (directional receivers) per-bin band interpolation
     g.mat_bytes = (g.mat_cached ? mat_bytes : 0) + (dir_nb ? (size_t)g.KB * 8 : 0);
     const size_t fixed = g.mat_bytes;

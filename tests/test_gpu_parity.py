@@ -113,6 +113,21 @@ def test_ragged_sizes_and_single_mic_bin(st):
             assert rel_l2(S[c], o["spectra"][c]) <= TOL, (M, F, c)
 
 
+@pytest.mark.parametrize("M,F", [(12, 196), (5, 84), (33, 35), (32, 512)])
+def test_ragged_sizes_with_diffraction(st, M, F):
+    """Diffraction accumulated at tile shapes with partial warps and ragged bin runs (12 mics x 196 bins: 78
+    threads per CTA, 13 runs of 16 bins), each CTA running several path tiles."""
+    import oracle
+    wl = small_clutter(target_tris=3000, n_rays=1537, n_mics=M, n_bins=F, bounces=2)
+    ctx, sc, S, stats = gpu_run(st, wl, curv=st.curv_params(sample_budget=60_000))
+    o = oracle.simulate(wl, curv=dict(budget=60_000))
+    ct, cp, keep = ctx.diffraction()
+    assert np.array_equal(keep, o["cand_keep"])
+    assert keep.sum() > 2000
+    for c in range(3):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, (M, F, c, rel_l2(S[c], o["spectra"][c]))
+
+
 @pytest.mark.parametrize("T", [1, 2, 3, 4, 5, 7, 8, 9, 31, 32, 33, 1000])
 def test_bvh_small_triangle_counts(st, T):
     """Leaf-size and warp boundaries of the LBVH: GPU closest hits equal brute force."""
