@@ -162,6 +162,9 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 if (KIND == 0) {
                     mt[e] = a.lk[(int64_t)mat * a.F + k];
                     mt[nm * KB + e] = a.g2[(int64_t)mat * a.F + k];
+                } else if (g.mat_direct) {  // the factor itself, as a pair for the two microphones of a thread
+                    const float x = (kb + s_ * KT + kk < a.F) ? ex2(a.lid[(int64_t)mat * a.F + k]) : 0.0f;
+                    reinterpret_cast<u64*>(mt)[e] = pk2(x, x);
                 } else {
                     mt[e] = a.lid[(int64_t)mat * a.F + k];
                 }
@@ -206,15 +209,23 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             float y[KT];
             const float2 ngv = up2(ng);  // -gamma^2 of the two microphones (lobe sums)
             const ulonglong2* trow = reinterpret_cast<const ulonglong2*>(C.tab) + (size_t)p * KB + s;
+            // diffraction with the material table read directly: row offset left by the producer in ngp
+            const u64* mrow = reinterpret_cast<const u64*>(mt) + s;
+            if (KIND == 1 && g.mat_direct) mrow += (int)(uint32_t)ng;
 #pragma unroll
             for (int kk = 0; kk < KT; ++kk) {
-                const ulonglong2 t = trow[kk * NS];
+                ulonglong2 t = make_ulonglong2(0ull, 0ull);
                 u64 E;
-                if (KIND == 0) {
-                    const float2 arg = up2(ffma2(ng, t.y, t.x));
-                    E = pk2(ex2(arg.x), ex2(arg.y));
+                if (KIND == 1 && g.mat_direct) {
+                    E = mrow[kk * NS];
                 } else {
-                    E = t.x;
+                    t = trow[kk * NS];
+                    if (KIND == 0) {
+                        const float2 arg = up2(ffma2(ng, t.y, t.x));
+                        E = pk2(ex2(arg.x), ex2(arg.y));
+                    } else {
+                        E = t.x;
+                    }
                 }
                 const u64 zr = (kk & 1) ? orr : er, zi = (kk & 1) ? oi : ei;
                 const u64 Tr = fmul2(E, zr), Ti = fmul2(E, zi);
@@ -591,7 +602,8 @@ cudaError_t launch_adjoint(const AccumArgs& a, const AdjointArgs& j, const Geom&
 namespace {
 
 size_t adjoint_per_path(const acc::Geom& g) {
-    return (size_t)g.KB * 16 + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40 + (size_t)g.TP * 56;
+    return (g.mat_direct ? (size_t)0 : (size_t)g.KB * 16) + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40 +
+           (size_t)g.TP * 56;
 }
 
 }  // namespace
@@ -602,11 +614,11 @@ size_t adjoint_smem(const acc::Geom& g) {
     return std::max(total, red);
 }
 
-acc::Geom adjoint_geom(int M, int F, int n_mat) {
+acc::Geom adjoint_geom(int M, int F, int n_mat, int mat_direct) {
     // tile shape of the forward with 8 bins per thread and up to 16 microphone pairs per CTA, the pair
     // count a power of two (the reflection sums are reduce-scattered across the pair lanes); paths
     // per tile as many as fit about 100 KB, so that two CTAs share an SM
-    acc::Geom g = acc::make_geom(M, F, 8, n_mat, 16, 200 * 1024);
+    acc::Geom g = acc::make_geom(M, F, 8, n_mat, 16, 200 * 1024, 0, mat_direct);
     int tp2 = 1;
     while (tp2 * 2 <= g.TP) tp2 *= 2;
     g.TP = tp2;

@@ -1149,7 +1149,10 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         jj.v_part = ptr<float>(c->adj_v);
         jj.mic_part = micp + (size_t)spec_mic_slices * M * 3;
         jj.emit_part = emitp + (size_t)spec_emit_slices * 3;
-        CKC(c, adjoint_launch(x, jj, g, s), "adjoint diffraction");
+        // same tile shape (pairs, runs, bin blocks) as the specular launches; without an emitter table the
+        // per-(material, bin) factor is read from the material table, so tiles hold more paths
+        const acc::Geom gd = adjoint_geom(M, F, T.n_mat, aa.etab ? 0 : 1);
+        CKC(c, adjoint_launch(x, jj, gd, s), "adjoint diffraction");
     }
     // ---- direct path
     if (want_pos && (p.components & ST_COMP_DIRECT)) {
