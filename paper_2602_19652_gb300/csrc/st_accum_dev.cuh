@@ -46,7 +46,8 @@ __device__ __forceinline__ ff ff_sqrt(ff x) {
     if (!(x.hi > 0.0f)) return ff{0.0f, 0.0f};
     float s = sqrtf(x.hi);
     ff p = two_prod(s, s);
-    float d = (((x.hi - p.hi) - p.lo) + x.lo) / (2.0f * s);
+    // the correction is ~2^-24 of s: a reciprocal good to a few ulp keeps the sum to ~2^-46
+    float d = (((x.hi - p.hi) - p.lo) + x.lo) * __fdividef(0.5f, s);
     return fast_two_sum(s, d);
 }
 // |a - b| for float32 points, ~2^-44 relative
@@ -70,7 +71,7 @@ __device__ __forceinline__ float ex2(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float log2_ff(ff r) { return log2f(r.hi) + r.lo / (r.hi * 0.69314718055994531f); }
+__device__ __forceinline__ float log2_ff(ff r) { return log2f(r.hi) + __fdividef(r.lo, r.hi * 0.69314718055994531f); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -408,7 +409,7 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
         if (g.NB > 0) mic_bands(a, m, d[0] - mx, d[1] - my, d[2] - mz, B.dband + ((size_t)p * MP + ml) * g.NB, g.NB);
         float gam2 = 0.0f;
         if (KIND == 0 || ADJ) {
-            const float inv = 1.0f / dist.hi;
+            const float inv = __fdividef(1.0f, dist.hi);
             const float ux = (mx - d[0]) * inv, uy = (my - d[1]) * inv, uz = (mz - d[2]) * inv;
             float* af = reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7);
             if (KIND == 0) {
