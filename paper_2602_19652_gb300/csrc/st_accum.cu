@@ -144,6 +144,9 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
         const int b = (int)((tile - t0) & 1);
         const Buf& C = b ? B1 : B0;
         const Buf& Pn = b ? B0 : B1;
+        // path data of tile+2 into pd buffer b, in flight during this tile (buffer b held this tile's path data,
+        // read by its producer one step ago; the term loop reads only the tile buffers)
+        if (tile + 2 < t1) load_paths_cp<KIND>(a, PT, (tile + 2) * PT, count, pdb + b * PT * 12, pvb + b * PT);
         if (tile + 1 < t1) {
             const int nb = b ^ 1;  // path data of tile+1 sits in pd buffer nb
             produce<KT, KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB);
@@ -197,9 +200,7 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
                 }
             }
         }
-        if (tile + 2 < t1) {  // pd buffer b held tile's path data, used by produce(tile) one step ago
-            load_paths<KIND>(a, PT, (tile + 2) * PT, count, pdb + b * PT * 12, pvb + b * PT);
-        }
+        cp_async_wait_all();
         __syncthreads();
     }
     // ---- partial spectra of this chunk

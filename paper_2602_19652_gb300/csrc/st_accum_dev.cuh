@@ -234,6 +234,37 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// path data of one tile into pd / pv as load_paths does, one thread per path, copied asynchronously: the
+// copies are in flight while the tile phase runs; cp_async_wait_all before the barrier that publishes them
+template <int KIND>
+__device__ __forceinline__ void load_paths_cp(const AccumArgs& a, int PT, int64_t pbase, int64_t count, float* pd,
+                                              int* pv) {
+    const int64_t base = a.d_base ? (int64_t)*a.d_base : 0;
+    for (int p = threadIdx.x; p < PT; p += blockDim.x) {
+        const int64_t rel = pbase + p;
+        const bool ok = rel < count;
+        pv[p] = ok;
+        if (!ok) continue;
+        const int64_t pi = base + rel;
+        float* d = pd + p * 12;
+        cp_async4(d + 0, a.px + pi);
+        cp_async4(d + 1, a.py + pi);
+        cp_async4(d + 2, a.pz + pi);
+        cp_async4(d + 6, a.rhi + pi);
+        cp_async4(d + 7, a.rlo + pi);
+        cp_async4(d + 8, a.meta + pi);
+        if (a.dep) cp_async4(d + 11, a.dep + pi); else d[11] = -1.0f;
+        if (KIND == 0) {
+            cp_async4(d + 3, a.dx + pi);
+            cp_async4(d + 4, a.dy + pi);
+            cp_async4(d + 5, a.dz + pi);
+            cp_async4(d + 9, a.chain_lo + pi);
+            cp_async4(d + 10, a.chain_hi + pi);
+        }
+    }
+    cp_async_commit();
+}
+
 // path data of one tile into pd / pv as load_paths does, with the words spread over the CTA's threads
 // and copied asynchronously (the copies overlap the tile phase that issues them)
 template <int KIND>
