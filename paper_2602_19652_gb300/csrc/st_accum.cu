@@ -605,6 +605,35 @@ cudaError_t compact_indices(const uint32_t* flags, const uint32_t* scan, int64_t
     return cudaGetLastError();
 }
 
+// Emitter-table row of every compacted specular path (the floor of its angle coordinate), 0xffff past the
+// count: sorting the compacted list by it lets the paths of an accumulator tile share table rows.
+__global__ void k_theta_keys(const GatherArgs g, int64_t cap, uint64_t* keys) {
+    const int64_t n = *g.count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cap; c += stride) {
+        uint64_t key = 0xffffu;
+        if (c < n) {
+            const int64_t ray = (int64_t)g.idx[c] / g.B;
+            const float3 d = rot(g.q, g.dirs[3 * ray], g.dirs[3 * ray + 1], g.dirs[3 * ray + 2]);
+            const float l = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+            const float cth = (g.fwd[0] * d.x + g.fwd[1] * d.y + g.fwd[2] * d.z) / l;
+            const float x = acosf(fminf(1.0f, fmaxf(-1.0f, cth))) * g.inv_dtheta;
+            key = (uint64_t)min((int)x, 0xfffe);
+        }
+        keys[c] = key;
+    }
+}
+
+cudaError_t theta_order(const GatherArgs& g, int64_t cap, uint32_t* idx, uint64_t* keys, void* scratch,
+                        cudaStream_t s) {
+    if (cap <= 1) return cudaSuccess;
+    note_launch();
+    k_theta_keys<<<grid_for(cap, 256), 256, 0, s>>>(g, cap, keys);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return radix_sort_u64(keys, idx, cap, 16, scratch, s);  // stable: equal rows keep the compaction order
+}
+
 cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s) {
     PathList& P = *g.out;
     note_launch();

@@ -64,6 +64,7 @@ struct st_ctx {
     float s[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0};
     int64_t N = 0;
     DevBuf dirs, etab, perm, ord_keys, ord_scr;
+    DevBuf th_keys, th_scr;          // emitter-table row order of the specular path list
     int32_t n_theta = 0;
     float fov_half = 4.0f;
     // receivers
@@ -256,7 +257,7 @@ st_status st_destroy(st_ctx* c) {
     enter(c);
     cudaStreamSynchronize(c->stream);
     for (DevBuf* b : {&c->mic_q, &c->mic_tab, &c->tables.bw}) release(*b);
-    for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
+    for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->th_keys, &c->th_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
                       &c->st_d[2], &c->st_r, &c->st_prev, &c->q0, &c->q1, &c->counts, &c->queries, &c->flags, &c->R, &c->rec_tri,
                       &c->rec_p, &c->rec_d, &c->rec_r, &c->rec_los, &c->sflags, &c->sscan, &c->sidx, &c->scratch,
                       &c->cand_tri, &c->cand_p, &c->keep, &c->dvis, &c->partial, &c->host_out, &c->tables.lk,
@@ -584,6 +585,10 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, grow(c->sscan, (size_t)nflag * 4), "alloc");
     CKC(c, grow(c->sidx, (size_t)nflag * 4), "alloc");
     CKC(c, grow(c->scratch, scan_scratch_bytes(nflag)), "alloc");
+    if (c->n_theta > 0 && NB > 1) {  // emitter-table row order of the specular path list
+        CKC(c, grow(c->th_keys, (size_t)NB * 8), "alloc");
+        CKC(c, grow(c->th_scr, sort_scratch_bytes(NB)), "alloc");
+    }
     CKC(c, grow(c->dvis, (size_t)M), "alloc");
     st_status ps = ensure_paths(c, c->paths, std::max<int64_t>(NB, 1));
     if (ps != ST_OK) return ps;
@@ -793,6 +798,9 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
             "compact");
         ga.count = cnt + 2;
         ga.out = &c->paths;
+        if (ga.has_etab && NB > 1) {  // paths in emitter-table row order: a tile's paths share table rows
+            CKC(c, theta_order(ga, NB, ptr<uint32_t>(c->sidx), ptr<uint64_t>(c->th_keys), c->th_scr.p, s), "order");
+        }
         CKC(c, gather_specular(ga, s), "gather");
         AccumArgs x = aa;
         x.kind = 0;

@@ -289,6 +289,10 @@ struct GatherArgs {
     PathList* out;
 };
 cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s);
+// Stable sort of the compacted specular indices idx[0 .. cap) by emitter-table row (entries past *g.count
+// last); keys [cap] and scratch (sort_scratch_bytes(cap)) are the caller's.
+cudaError_t theta_order(const GatherArgs& g, int64_t cap, uint32_t* idx, uint64_t* keys, void* scratch,
+                        cudaStream_t s);
 cudaError_t gather_diffraction(const GatherArgs& g, cudaStream_t s);
 cudaError_t flags_visible_records(const int32_t* rec_tri, const uint8_t* rec_los, int64_t n, uint32_t* flags,
                                   cudaStream_t s);
