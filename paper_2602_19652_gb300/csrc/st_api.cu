@@ -65,6 +65,7 @@ struct st_ctx {
     int64_t N = 0;
     DevBuf dirs, etab, perm, ord_keys, ord_scr;
     DevBuf th_keys, th_scr;          // emitter-table row order of the specular path list
+    DevBuf vs_keys, vs_scr;          // hit-point Morton order of the visibility queries
     int32_t n_theta = 0;
     float fov_half = 4.0f;
     // receivers
@@ -179,6 +180,10 @@ st_status cuda_fail(st_ctx* c, cudaError_t e, const char* where) {
 cudaMemcpyKind kind_in(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_out(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
+// triangle count from which the visibility queries of a simulate are sorted by hit point (the 4-wide
+// hierarchy and the triangles then take well over half of L2)
+constexpr int64_t kVisSortTris = 1000000;
+
 uint64_t g_scene_version = 1;
 
 void batch_release(BatchState& B);
@@ -257,7 +262,7 @@ st_status st_destroy(st_ctx* c) {
     enter(c);
     cudaStreamSynchronize(c->stream);
     for (DevBuf* b : {&c->mic_q, &c->mic_tab, &c->tables.bw}) release(*b);
-    for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->th_keys, &c->th_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
+    for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->th_keys, &c->th_scr, &c->vs_keys, &c->vs_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
                       &c->st_d[2], &c->st_r, &c->st_prev, &c->q0, &c->q1, &c->counts, &c->queries, &c->flags, &c->R, &c->rec_tri,
                       &c->rec_p, &c->rec_d, &c->rec_r, &c->rec_los, &c->sflags, &c->sscan, &c->sidx, &c->scratch,
                       &c->cand_tri, &c->cand_p, &c->keep, &c->dvis, &c->partial, &c->host_out, &c->tables.lk,
@@ -585,6 +590,13 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, grow(c->sscan, (size_t)nflag * 4), "alloc");
     CKC(c, grow(c->sidx, (size_t)nflag * 4), "alloc");
     CKC(c, grow(c->scratch, scan_scratch_bytes(nflag)), "alloc");
+    // Scenes whose hierarchy and triangles are well beyond L2 trace their visibility queries in the Morton
+    // order of the hit points (all go to one point, so neighbours in that order share most nodes)
+    const bool vsort = S.n_tris >= kVisSortTris && N > 1;
+    if (vsort) {
+        CKC(c, grow(c->vs_keys, (size_t)N * 8), "alloc");
+        CKC(c, grow(c->vs_scr, sort_scratch_bytes(N)), "alloc");
+    }
     if (c->n_theta > 0 && NB > 1) {  // emitter-table row order of the specular path list
         CKC(c, grow(c->th_keys, (size_t)NB * 8), "alloc");
         CKC(c, grow(c->th_scr, sort_scratch_bytes(NB)), "alloc");
@@ -677,6 +689,13 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         ta.vis_q = ptr<uint32_t>(c->vis_q);
         ta.vis_n = ptr<uint32_t>(c->trav_cnt);
         ta.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 16);
+        ta.sort_keys = vsort ? ptr<uint64_t>(c->vs_keys) : nullptr;
+        ta.sort_scr = vsort ? c->vs_scr.p : nullptr;
+        for (int k = 0; k < 3; ++k) {
+            const float ext = S.bounds_hi[k] - S.bounds_lo[k];
+            ta.blo[k] = S.bounds_lo[k];
+            ta.bscale[k] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+        }
         CKC(c, trace_rays(ta, s, c->tune.rays_per_block > 0 ? c->tune.rays_per_block : 128), "trace");
     }
     if (stats) CKC(c, cudaEventRecord(c->ev[1], s), "event");

@@ -143,6 +143,10 @@ struct TraceArgs {
     int32_t* hit_tri; float* hit_t;
     uint32_t* vis_q; uint32_t* vis_n;
     unsigned long long* ctr;
+    // optional: visibility queue sorted by the Morton code of the hit points (scene bounds lo, 1024 / extent)
+    // before it is traced, so that neighbouring lanes share nodes; keys [N] and sort scratch, or null
+    uint64_t* sort_keys; void* sort_scr;
+    float blo[3], bscale[3];
     // records [N][B]
     int32_t* rec_tri;
     float* rec_p;    // [N][B][3]

@@ -291,6 +291,38 @@ __global__ void k_centroid(const float* mics, int32_t M, float* R) {
     for (int k = 0; k < 3; ++k) R[k] = (float)(acc[k] / (double)M);
 }
 
+// 10 bits of x spread to every third bit
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+// Morton code (kVisBits per axis) of the hit point of every queued visibility query, 2^(3 kVisBits) past the
+// count (10 bits measured faster than 5 or 7 on the vegetation workload, the sort included)
+constexpr int kVisBits = 10;
+__global__ void k_vis_keys(const TraceArgs a, uint64_t* keys) {
+    const int64_t n = *a.vis_n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += stride) {
+        uint64_t key = 1ull << (3 * kVisBits);
+        if (c < n) {
+            const int64_t id = a.vis_q[c];
+            const float cells = (float)(1 << kVisBits);
+            uint32_t m = 0;
+            for (int k = 0; k < 3; ++k) {
+                const float u = (a.rec_p[3 * id + k] - a.blo[k]) * a.bscale[k] * (cells * (1.0f / 1024.0f));
+                m |= spread10((uint32_t)fminf(fmaxf(u, 0.0f), cells - 1.0f)) << (2 - k);
+            }
+            key = m;
+        }
+        keys[c] = key;
+    }
+}
+
 // Octahedral map of a direction to [0,1]^2, 16 bits per axis, Morton-interleaved: nearby directions
 // get nearby keys, so sorting by the key groups rays that traverse the same part of the scene.
 __device__ __forceinline__ uint32_t spread16(uint32_t x) {
@@ -361,6 +393,13 @@ cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
         note_launch();
         k_shade<<<grid, block, 0, s>>>(a, j, a.N);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (a.sort_keys) {  // stable sort: equal codes keep the queue order
+            note_launch();
+            k_vis_keys<<<grid_for(a.N, 256), 256, 0, s>>>(a, a.sort_keys);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = radix_sort_u64(a.sort_keys, a.vis_q, a.N, 3 * kVisBits + 1, a.sort_scr, s)) != cudaSuccess)
+                return e;
+        }
         note_launch();
         k_visible<<<trav_grid(a.N), kTravBlock, 0, s>>>(T, a.vis_q, a.vis_n, a.rec_p, a.rec_tri, a.R, 0.0f, 0.0f, 0.0f,
                                                         a.t_min, a.los_eps, a.rec_los, a.ctr + 1, a.flags, a.queries);
