@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 if (m2 < a.M) g2 = j.G[(int64_t)m2 * a.F + k];
             }
             Gr[kk] = pk2(g1.x, g2.x);
-            Gi[kk] = pk2(g1.y, g2.y);
+            // diffraction keeps -Im G: the Horner sums below use conj(G) E directly
+            Gi[kk] = KIND == 1 ? pk2(-g1.y, -g2.y) : pk2(g1.y, g2.y);
         }
     }
     float V[kNV][VR];
@@ -206,45 +207,64 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             u64 er = z0.x, ei = z0.y, orr = er, oi = ei;
             cmul2(orr, oi, w1r, w1i, fmul2(w1i, pk2(-1.0f, -1.0f)));
             u64 c0r = 0ull, c0i = 0ull, qr = 0ull, qi = 0ull, cg = 0ull;
+            u64 c1r = 0ull, c1i = 0ull;  // diffraction: C1 = sum_kk kk conj(G) T directly
             float y[KT];
             const float2 ngv = up2(ng);  // -gamma^2 of the two microphones (lobe sums)
             const ulonglong2* trow = reinterpret_cast<const ulonglong2*>(C.tab) + (size_t)p * KB + s;
             // diffraction with the material table read directly: row offset left by the producer in ngp
             const u64* mrow = reinterpret_cast<const u64*>(mt) + s;
             if (KIND == 1 && g.mat_direct) mrow += (int)(uint32_t)ng;
+            if (KIND == 1) {
+                // Diffraction (positions only): with u_kk = conj(G_kk) E_kk and z_kk = z0 W^kk,
+                //   C0 = z0 P(W), C1 = z0 W P'(W),  P(W) = sum_kk u_kk W^kk,
+                // P and P' by Horner's scheme from the top bin (no explicit phasor chain).
+                const u64 nw1i = fmul2(w1i, pk2(-1.0f, -1.0f));
+                auto Eat = [&](int kk) -> u64 { return g.mat_direct ? mrow[kk * NS] : trow[kk * NS].x; };
+                u64 E = Eat(KT - 1);
+                u64 pr = fmul2(Gr[KT - 1], E), pim = fmul2(Gi[KT - 1], E), dpr = 0ull, dpi = 0ull;
 #pragma unroll
-            for (int kk = 0; kk < KT; ++kk) {
-                ulonglong2 t = make_ulonglong2(0ull, 0ull);
-                u64 E;
-                if (KIND == 1 && g.mat_direct) {
-                    E = mrow[kk * NS];
-                } else {
-                    t = trow[kk * NS];
-                    if (KIND == 0) {
-                        const float2 arg = up2(ffma2(ng, t.y, t.x));
-                        E = pk2(ex2(arg.x), ex2(arg.y));
-                    } else {
-                        E = t.x;
-                    }
+                for (int kk = KT - 2; kk >= 0; --kk) {
+                    E = Eat(kk);
+                    const u64 ur = fmul2(Gr[kk], E), ui = fmul2(Gi[kk], E);
+                    const u64 ndr = ffma2(dpr, w1r, ffma2(dpi, nw1i, pr));  // P' <- P' W + P
+                    const u64 ndi = ffma2(dpr, w1i, ffma2(dpi, w1r, pim));
+                    const u64 npr = ffma2(pr, w1r, ffma2(pim, nw1i, ur));  // P <- P W + u
+                    const u64 npi = ffma2(pr, w1i, ffma2(pim, w1r, ui));
+                    dpr = ndr;
+                    dpi = ndi;
+                    pr = npr;
+                    pim = npi;
                 }
-                const u64 zr = (kk & 1) ? orr : er, zi = (kk & 1) ? oi : ei;
-                const u64 Tr = fmul2(E, zr), Ti = fmul2(E, zi);
-                const u64 wr = ffma2(Gr[kk], Tr, fmul2(Gi[kk], Ti));        // Re(conj(G) T)
-                const u64 wi = fsub2(fmul2(Gr[kk], Ti), fmul2(Gi[kk], Tr));  // Im(conj(G) T)
-                c0r = fadd2(c0r, wr);
-                c0i = fadd2(c0i, wi);
-                qr = fadd2(qr, c0r);  // running sum of prefix sums: sum_kk kk w = KT C0 - Q
-                qi = fadd2(qi, c0i);
-                if (KIND == 0) cg = ffma2(t.y, wr, cg);
-                const float2 wr2 = up2(wr);
-                y[kk] = j.do_beta ? fmaf(wr2.x, ngv.x, wr2.y * ngv.y) : wr2.x + wr2.y;
-                if (kk & 1) cmul2(orr, oi, w2r, w2i, nw2i); else cmul2(er, ei, w2r, w2i, nw2i);
+                c0r = ffma2(er, pr, fmul2(fmul2(ei, pk2(-1.0f, -1.0f)), pim));
+                c0i = ffma2(er, pim, fmul2(ei, pr));
+                const u64 tr = ffma2(w1r, dpr, fmul2(nw1i, dpi)), ti = ffma2(w1r, dpi, fmul2(w1i, dpr));
+                c1r = ffma2(er, tr, fmul2(fmul2(ei, pk2(-1.0f, -1.0f)), ti));
+                c1i = ffma2(er, ti, fmul2(ei, tr));
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < KT; ++kk) {  // specular
+                    const ulonglong2 t = trow[kk * NS];
+                    const float2 arg = up2(ffma2(ng, t.y, t.x));
+                    const u64 E = pk2(ex2(arg.x), ex2(arg.y));
+                    const u64 zr = (kk & 1) ? orr : er, zi = (kk & 1) ? oi : ei;
+                    const u64 Tr = fmul2(E, zr), Ti = fmul2(E, zi);
+                    const u64 wr = ffma2(Gr[kk], Tr, fmul2(Gi[kk], Ti));        // Re(conj(G) T)
+                    const u64 wi = fsub2(fmul2(Gr[kk], Ti), fmul2(Gi[kk], Tr));  // Im(conj(G) T)
+                    c0r = fadd2(c0r, wr);
+                    c0i = fadd2(c0i, wi);
+                    qr = fadd2(qr, c0r);  // running sum of prefix sums: sum_kk kk w = KT C0 - Q
+                    qi = fadd2(qi, c0i);
+                    if (KIND == 0) cg = ffma2(t.y, wr, cg);
+                    const float2 wr2 = up2(wr);
+                    y[kk] = j.do_beta ? fmaf(wr2.x, ngv.x, wr2.y * ngv.y) : wr2.x + wr2.y;
+                    if (kk & 1) cmul2(orr, oi, w2r, w2i, nw2i); else cmul2(er, ei, w2r, w2i, nw2i);
+                }
             }
             if (j.do_pos) {
                 const u64* ad = C.adj + ((size_t)p * TP + tp) * 7;
                 // C1 relative to the subtile's first bin
-                const u64 q1r = fsub2(fmul2(pk2((float)KT, (float)KT), c0r), qr);
-                const u64 q1i = fsub2(fmul2(pk2((float)KT, (float)KT), c0i), qi);
+                const u64 q1r = KIND == 1 ? c1r : fsub2(fmul2(pk2((float)KT, (float)KT), c0r), qr);
+                const u64 q1i = KIND == 1 ? c1i : fsub2(fmul2(pk2((float)KT, (float)KT), c0i), qi);
                 const u64 d0r = ffma2(pk2(-2.0f, -2.0f), ad[6], ArS);  // -2/r - a(kb_s)
                 // dL/dr share: Re(D0 C0 + D1 C1), D0 = d0r + j w(kb_s), D1 = -a_step + j w_step
                 u64 dl = fmul2(d0r, c0r);
