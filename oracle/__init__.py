@@ -11,6 +11,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   curvature, metric  sphere (G ~ 1/R), cylinder side (G ~ 1/(2R)), plane (G = 0)
   diffraction_cdf    exact integer prefix sums; sample histogram chi-square vs weights
   trace              brute force == BVH bit for bit; shoebox unfolding closed form
+  los_per_mic        empty convex room: every microphone visible and spectra equal to the reference-point
+                     test; a plane wall between two microphone groups: the half-space each group is in
   spectra            single-path closed forms; direct path closed form; reciprocity
   spectra_grad       float64 central finite differences
   (absolute scale of spectra against measurements: parity unpinned -- the paper has no data)
@@ -76,7 +78,9 @@ def _declare(L):
     L.ora_diffraction_filter.argtypes = [P, P, P, P, I64, P, P, F32, F32, F32, F32, P, I32]
     L.ora_direct_visibility.argtypes = [P, P, I32, P, F32, F32, P]
     L.ora_spectra.argtypes = [C.POINTER(SpecParams), I64, I32, P, P, P, P, P, P, P, I64, P, P, P, P,
-                              I32, P, I32, P, I32, P]
+                              I32, P, I32, P, I32, P, P]
+    L.ora_los_per_mic.argtypes = [P, I64, P, P, I32, P, F32, F32, P, P, I32]
+    L.ora_los_per_mic.restype = C.c_int
     L.ora_spectra.restype = C.c_int
     L.ora_spectra_grad.argtypes = [C.POINTER(SpecParams), I64, I32, P, P, P, P, P, P, P, I64, P, P, P, P,
                                    P, P, P, P, P, P, P]
@@ -216,6 +220,21 @@ def diffraction_filter(scene: Scene, s, q, cand_tri, cand_p, fov_half=math.pi, c
     return keep
 
 
+def los_per_mic(scene: Scene, rec, mics, t_min=1e-5, los_eps=1e-4, nthreads=0):
+    """Receiver test per microphone (the variant of reading 6 with one visibility ray per microphone):
+    returns rec with 'mask' (uint64 [N][B], bit m = microphone m visible from the hit point) and 'los'
+    (any microphone visible).  M <= 64."""
+    m = _c(mics, np.float32)
+    if not 1 <= len(m) <= 64:
+        raise ValueError("per-microphone receiver test: 1 <= M <= 64")
+    N, B = rec["tri"].shape
+    mask = np.zeros((N, B), np.uint64)
+    los = np.zeros((N, B), np.uint8)
+    lib().ora_los_per_mic(scene.h, N * B, _p(_c(rec["tri"], np.int32)), _p(_c(rec["p"], np.float32)), len(m), _p(m),
+                          t_min, los_eps, _p(mask), _p(los), nthreads)
+    return dict(rec, mask=mask, los=los)
+
+
 def direct_visibility(scene: Scene, s, mics, t_min=1e-5, los_eps=1e-4):
     s, m = _c(s, np.float32), _c(mics, np.float32)
     vis = np.zeros(len(m), dtype=np.uint8)
@@ -271,7 +290,7 @@ def spectra(params, rec, dirs, tri_mat, cand_tri=None, cand_p=None, cand_keep=No
     out = np.zeros((3, nm, nk, 2), dtype=np.float64)
     lib().ora_spectra(C.byref(P_), N, B, _p(rec["tri"]), _p(rec["p"]), _p(rec["d"]), _p(rec["r"]), _p(rec["los"]),
                       _p(dirs), _p(tm), K, _p(ct), _p(cp), _p(ck), _p(dv), nm, _p(msa), nk, _p(ksa), nthreads,
-                      _p(out))
+                      _p(_c(rec.get("mask"), np.uint64)), _p(out))
     return out[..., 0] + 1j * out[..., 1]
 
 
@@ -307,9 +326,10 @@ def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand
 # ------------------------------------------------------------------------------------ pipeline
 def simulate(wl, *, c=343.0, a0=0.0, a1_per_khz=0.033, t_min=1e-5, los_eps=1e-4, reflection_mode=0,
              direct_gain=1.0, theta_inc_deg=80.0, curv=None, seed=0, pose=0, components=7, use_bvh=None,
-             ms=None, ks=None, nthreads=0, ray_subset=None):
+             ms=None, ks=None, nthreads=0, ray_subset=None, los_mode=0):
     """The whole hot path on the CPU for one workload.  Returns a dict with the path records,
-    diffraction candidates and spectra (complex128 [3][M][F])."""
+    diffraction candidates and spectra (complex128 [3][M][F]).  los_mode 1: the receiver test of each record
+    is made per microphone (records then carry 'mask')."""
     curv = dict(eta=1.0, area_ref=1e-4, dither=1e-3, hc_frac=0.25, samples_per_vertex=64, budget=4_000_000,
                 seed=0) | (curv or {})
     scene = Scene(wl.verts, wl.tris, use_bvh=use_bvh)
@@ -317,6 +337,8 @@ def simulate(wl, *, c=343.0, a0=0.0, a1_per_khz=0.033, t_min=1e-5, los_eps=1e-4,
     dirs = wl.dirs if ray_subset is None else wl.dirs[ray_subset]
     rec = trace(scene, wl.emitter, wl.emitter_quat, dirs, wl.bounces, r_max=wl.max_distance, t_min=t_min,
                 los_eps=los_eps, R=R, nthreads=nthreads)
+    if los_mode == 1:
+        rec = los_per_mic(scene, rec, wl.mics, t_min, los_eps, nthreads)
     out = dict(rec=rec, R=R, scene=scene)
     cand_tri = cand_p = keep = None
     if wl.diffraction and (components & 2):

@@ -772,6 +772,33 @@ ORA_API int ora_trace(void* scene, const float* nrm, const float s[3], const flo
 }
 
 /*
+ * Receiver test per microphone (the variant of reading 6 with one visibility ray per microphone instead of
+ * one towards the receiver reference point): bit m of rec_mask[id] is set when microphone m is visible from
+ * the record's hit point (the hit triangle excluded, stopping los_eps short), and rec_los[id] becomes 1
+ * when any bit is.  Records without a hit (tri < 0) get 0.  M <= 64.
+ */
+ORA_API int ora_los_per_mic(void* scene, int64_t NB, const int32_t* rec_tri, const float* rec_p, int32_t M,
+                            const float* mics, float t_min, float los_eps, uint64_t* rec_mask, uint8_t* rec_los,
+                            int32_t nthreads) {
+    const OraScene* S = (const OraScene*)scene;
+    if (M < 1 || M > 64) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t id = 0; id < NB; ++id) {
+        uint64_t mask = 0;
+        if (rec_tri[id] >= 0) {
+            for (int32_t m = 0; m < M; ++m)
+                if (visible(S, rec_p + 3 * id, mics + 3 * m, rec_tri[id], t_min, los_eps)) mask |= (uint64_t)1 << m;
+        }
+        rec_mask[id] = mask;
+        rec_los[id] = mask != 0;
+    }
+    return 0;
+}
+
+/*
  * Sec. III-D filters for each candidate point o on triangle T:
  *   field of view: the angle between the emitter forward axis (q applied to +x) and
  *     normalize(o - s) is at most fov_half: dot >= cos_fov (skipped when cos_fov <= -1);
@@ -1019,7 +1046,7 @@ ORA_API int ora_spectra(const OraSpecParams* P, int64_t N, int32_t B, const int3
                         const float* rec_d, const double* rec_r, const uint8_t* rec_los, const float* dirs,
                         const int32_t* tri_mat, int64_t K, const int32_t* cand_tri, const float* cand_p,
                         const uint8_t* cand_keep, const uint8_t* direct_vis, int32_t n_m, const int32_t* ms,
-                        int32_t n_k, const int32_t* ks, int32_t nthreads, double* out) {
+                        int32_t n_k, const int32_t* ks, int32_t nthreads, const uint64_t* rec_mask, double* out) {
     int nm = ms ? n_m : P->M;
     int nk = ks ? n_k : P->F;
     memset(out, 0, sizeof(double) * 3 * (size_t)nm * nk * 2);
@@ -1044,6 +1071,7 @@ ORA_API int ora_spectra(const OraSpecParams* P, int64_t N, int32_t B, const int3
                 if (rec_tri[id] < 0) break;
                 p.chain[j] = tri_mat[rec_tri[id]];
                 if (!rec_los[id]) continue;
+                if (rec_mask && !((rec_mask[id] >> m) & 1u)) continue;  /* per-microphone receiver test */
                 for (int k = 0; k < 3; ++k) { p.P[k] = rec_p[3 * id + k]; p.dref[k] = rec_d[3 * id + k]; }
                 p.r_pre = rec_r[id];
                 p.chain_len = j + 1;
