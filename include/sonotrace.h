@@ -52,6 +52,13 @@ typedef int32_t st_status;
 #define ST_COMP_DIFFRACTION 2 /* index 1: G(f), Eq. 8 */
 #define ST_COMP_DIRECT 4     /* index 2: P(f), Eq. 12 */
 
+/* Receiver test of a specular hit (st_sim_params.los_mode).  The paper leaves the test unstated: the
+   default casts one visibility ray per hit towards the receiver reference point (the microphones'
+   centroid) and lets the hit reach every microphone when it is visible; the per-microphone variant casts
+   one ray per microphone and lets the hit reach only the microphones it sees (M <= 64). */
+#define ST_LOS_REFERENCE 0
+#define ST_LOS_PER_MIC 1
+
 typedef struct st_ctx st_ctx;
 typedef struct st_scene st_scene;
 
@@ -81,6 +88,9 @@ typedef struct st_sim_params {
     float direct_gain;          /* I_p of Eq. 11 (default 1) */
     uint64_t seed;              /* Philox key of the diffraction samples (default 0) */
     uint32_t pose_index;        /* Philox counter word distinguishing poses (default 0) */
+    int32_t los_mode;           /* ST_LOS_* (default ST_LOS_REFERENCE); ST_LOS_PER_MIC needs M <= 64 and
+                                   N * B * M < 2^32, single-pose st_simulate only, and no st_backward after
+                                   it; st_accumulate_specular_noalloc takes the caller's records and ignores it */
 } st_sim_params;
 
 /* Optional statistics of one simulate call (filled after the stream is synchronised). */
@@ -177,6 +187,11 @@ st_status st_simulate_host(st_ctx* ctx, st_scene* scene, const st_sim_params* pa
  * (-1 = none), hit point [3], reflected direction [3], path length (float64), receiver-point
  * visibility.  Synchronises. */
 st_status st_get_paths(st_ctx* ctx, int32_t* tri, float* point, float* dir, double* r, uint8_t* los, int32_t mem);
+/* Per-microphone receiver test of the last simulate (made with ST_LOS_PER_MIC, else ST_ERR_STATE):
+ * [n_rays][B] masks, bit m set when microphone m is visible from the record's hit point (0 for records
+ * without a hit); the record's visibility flag of st_get_paths is then "any bit set".  Synchronises.
+ * The paper states no receiver test; this is the per-microphone reading of its receiver connection. */
+st_status st_get_receiver_masks(st_ctx* ctx, uint64_t* mask, int32_t mem);
 /* Diffraction samples of the last simulate: *n_out = count; triangle, point [3], kept flag
  * (arrays of at least `capacity` entries; any may be NULL).  Synchronises. */
 st_status st_get_diffraction(st_ctx* ctx, int64_t* n_out, int32_t* tri, float* point, uint8_t* keep,

@@ -14,11 +14,13 @@ import torch
 
 from . import _lib
 from .autograd import SpectraFn  # noqa: E402
-from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
+from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_LOS_PER_MIC, ST_LOS_REFERENCE,
+                   ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
                    Job, SimParams, SonotraceError, Stats, Tune, check, load)
 
 __all__ = ["Context", "Scene", "BatchJob", "SpectraFn", "CurvParams", "SimParams", "Stats", "Tune", "SonotraceError",
-           "sim_params", "curv_params", "ST_COMP_SPECULAR", "ST_COMP_DIFFRACTION", "ST_COMP_DIRECT"]
+           "sim_params", "curv_params", "ST_COMP_SPECULAR", "ST_COMP_DIFFRACTION", "ST_COMP_DIRECT",
+           "ST_LOS_REFERENCE", "ST_LOS_PER_MIC"]
 
 
 def curv_params(**kw) -> CurvParams:
@@ -130,6 +132,12 @@ class Context:
         cp = lambda a: a.ctypes.data_as(C.c_void_p)
         self._check(self.L.st_get_paths(self.h, cp(tri), cp(p), cp(d), cp(r), cp(los), ST_MEM_HOST))
         return dict(tri=tri, p=p, d=d, r=r, los=los)
+
+    def receiver_masks(self, B: int):
+        """[N][B] uint64 per-microphone visibility of the last simulate (made with ST_LOS_PER_MIC)."""
+        m = np.empty((self.N, B), np.uint64)
+        self._check(self.L.st_get_receiver_masks(self.h, m.ctypes.data_as(C.c_void_p), ST_MEM_HOST))
+        return m
 
     def diffraction(self):
         n = C.c_int64(0)

@@ -19,6 +19,7 @@ ST_IR_PER_COMPONENT = 1
 ST_REFIT_KEEP_CURVATURE = 1
 ST_RAYS_FIBONACCI, ST_RAYS_ZONAL = 0, 1
 ST_COMP_SPECULAR, ST_COMP_DIFFRACTION, ST_COMP_DIRECT = 1, 2, 4
+ST_LOS_REFERENCE, ST_LOS_PER_MIC = 0, 1
 
 
 class CurvParams(C.Structure):
@@ -30,7 +31,7 @@ class SimParams(C.Structure):
     _fields_ = [("max_bounces", I32), ("max_distance", F64), ("c", F64), ("alpha0_db_m", F64),
                 ("alpha1_db_m_khz", F64), ("t_min", F32), ("los_eps", F32), ("reflection_mode", I32),
                 ("components", I32), ("theta_inc_rad", F32), ("direct_gain", F32), ("seed", U64),
-                ("pose_index", U32)]
+                ("pose_index", U32), ("los_mode", I32)]
 
 
 class Stats(C.Structure):
@@ -71,6 +72,7 @@ SIGNATURES = {
     "st_simulate": (I32, [P, P, P, P, P]),
     "st_simulate_host": (I32, [P, P, P, P, P]),
     "st_get_paths": (I32, [P, P, P, P, P, P, I32]),
+    "st_get_receiver_masks": (I32, [P, P, I32]),
     "st_get_diffraction": (I32, [P, P, P, P, P, I64, I32]),
     "st_get_direct_visibility": (I32, [P, P, I32]),
     "st_backward": (I32, [P, P, P, P, P, P]),

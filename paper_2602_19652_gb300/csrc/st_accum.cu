@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int tp = tid % TP, s = tid / TP;
 
+    const int64_t pb0 = a.d_base ? (int64_t)*a.d_base : 0;  // global index of this launch's first path
     const int64_t count = (int64_t)*a.d_count;
     const int64_t n_tiles = (count + PT - 1) / PT;
     const int64_t per = (n_tiles + a.n_chunks - 1) / a.n_chunks;
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
         load_paths<KIND>(a, PT, t0 * PT, count, pdb, pvb);
         if (t0 + 1 < t1) load_paths<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
         __syncthreads();
-        produce<KT, KIND>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB);
+        produce<KT, KIND>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, nullptr, pb0 + t0 * PT);
         __syncthreads();
     }
     // software pipeline: consume tile t from buffer b while producing tile t+1 into buffer b^1
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
         if (tile + 2 < t1) load_paths_cp<KIND>(a, PT, (tile + 2) * PT, count, pdb + b * PT * 12, pvb + b * PT);
         if (tile + 1 < t1) {
             const int nb = b ^ 1;  // path data of tile+1 sits in pd buffer nb
-            produce<KT, KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB);
+            produce<KT, KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, nullptr,
+                              pb0 + (tile + 1) * PT);
         }
         for (int p = 0; p < PT; ++p) {
             const ulonglong2 z0 = C.za[((size_t)p * NS + s) * TP + tp];
@@ -325,7 +327,8 @@ __device__ __forceinline__ float3 rot(const float q[4], float vx, float vy, floa
 }
 
 __global__ void k_gather_spec(const GatherArgs g, float* px, float* py, float* pz, float* dx, float* dy, float* dz,
-                              float* rhi, float* rlo, uint32_t* chl, uint32_t* chh, uint32_t* meta, float* dep) {
+                              float* rhi, float* rlo, uint32_t* chl, uint32_t* chh, uint32_t* meta, float* dep,
+                              uint64_t* mask) {
     const int64_t n = *g.count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
@@ -352,6 +355,7 @@ __global__ void k_gather_spec(const GatherArgs g, float* px, float* py, float* p
         chl[c] = lo;
         chh[c] = hi;
         meta[c] = (uint32_t)(j + 1) | ((uint32_t)matj << 8);
+        if (g.rec_mask) mask[c] = g.rec_mask[id];
         if (g.has_etab) {
             const float3 d = rot(g.q, g.dirs[3 * ray], g.dirs[3 * ray + 1], g.dirs[3 * ray + 2]);
             const float l = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
@@ -640,7 +644,7 @@ cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s) {
     k_gather_spec<<<grid_for(g.N * g.B, 256), 256, 0, s>>>(
         g, ptr<float>(P.px), ptr<float>(P.py), ptr<float>(P.pz), ptr<float>(P.dx), ptr<float>(P.dy), ptr<float>(P.dz),
         ptr<float>(P.rhi), ptr<float>(P.rlo), ptr<uint32_t>(P.chain_lo), ptr<uint32_t>(P.chain_hi),
-        ptr<uint32_t>(P.meta), ptr<float>(P.dep));
+        ptr<uint32_t>(P.meta), ptr<float>(P.dep), g.rec_mask ? ptr<uint64_t>(P.mask) : nullptr);
     return cudaGetLastError();
 }
 

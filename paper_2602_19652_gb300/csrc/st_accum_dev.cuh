@@ -306,7 +306,7 @@ __device__ __forceinline__ void load_paths_async(const AccumArgs& a, int PT, int
 template <int KT, int KIND, int ADJ = 0>
 __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const Buf& B, const float* pd, const int* pv,
                                         const float* mt, int mic0, int kb, float invNS, float invKB,
-                                        const float* es = nullptr) {
+                                        const float* es = nullptr, int64_t pglob = 0) {
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
     const bool cached = g.mat_cached > 0;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -419,7 +419,8 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
         float* zf = reinterpret_cast<float*>(B.za + (size_t)p * NS * TP + pair);
         float* wf = reinterpret_cast<float*>(B.wst + (size_t)p * 4 * TP + pair);  // component c at wf[2 TP c]
         float* nf = reinterpret_cast<float*>(B.ngp + (size_t)p * TP + pair);
-        if (!pv[p] || m >= a.M) {
+        // (per-microphone receiver test: a microphone that does not see the path gets a zero anchor)
+        if (!pv[p] || m >= a.M || (a.mask && !((a.mask[pglob + p] >> m) & 1ull))) {
             for (int s_ = 0; s_ < NS; ++s_) {
                 zf[(size_t)s_ * TP * 4 + half] = 0.0f;
                 zf[(size_t)s_ * TP * 4 + 2 + half] = 0.0f;

@@ -66,14 +66,15 @@ __device__ __forceinline__ NBuf nbuf_at(char* base, const NGeom& g, int b) {
 // item 1 + e = bin step raised to 2^e
 template <int KIND>
 __device__ __forceinline__ void nproduce(const AccumArgs& a, const NGeom& g, const NBuf& B, const float* pd,
-                                         const int* pv, int kb) {
+                                         const int* pv, int kb, int64_t pglob) {
     const int items = g.LNS + 3;
     for (int e = threadIdx.x; e < g.PT * 2 * items; e += blockDim.x) {
         const int p = e / (2 * items), rem = e - p * 2 * items;
         const int half = rem / items, it = rem - half * items;
         const int m = half;
         float* zf = reinterpret_cast<float*>(it == 0 ? B.zb + p : B.pw + (size_t)p * (g.LNS + 2) + (it - 1));
-        if (!pv[p] || m >= a.M) {
+        // (per-microphone receiver test: a microphone that does not see the path gets a zero anchor)
+        if (!pv[p] || m >= a.M || (a.mask && !((a.mask[pglob + p] >> m) & 1ull))) {
             zf[half] = 0.0f;
             zf[2 + half] = 0.0f;
             if (it == 0) {
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
     const int s = tid % NS, grp = tid / NS;
 
     const int64_t count = (int64_t)*a.d_count;
+    const int64_t pb0 = a.d_base ? (int64_t)*a.d_base : 0;  // global index of this launch's first path
     const int64_t n_tiles = (count + PT - 1) / PT;
     const int64_t per = (n_tiles + a.n_chunks - 1) / a.n_chunks;
     const int64_t t0 = (int64_t)blockIdx.y * per, t1 = min(n_tiles, t0 + per);
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
         if (t0 + 1 < t1) load_paths_async<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
         cp_async_wait_all();
         __syncthreads();
-        nproduce<KIND>(a, g, B0, pdb, pvb, kb);
+        nproduce<KIND>(a, g, B0, pdb, pvb, kb, pb0 + t0 * PT);
         __syncthreads();
     }
     const u64 one = pk2(1.0f, 1.0f), zero = 0ull, neg = pk2(-1.0f, -1.0f);
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
         }
         if (tile + 1 < t1) {
             const int nb = (int)((tile + 1 - t0) % 3);
-            nproduce<KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, kb);
+            nproduce<KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, kb, pb0 + (tile + 1) * PT);
         }
         for (int q = 0; q < g.PPG; ++q) {
             const int p = grp * g.PPG + q;

@@ -106,7 +106,8 @@ struct st_ctx {
     DevBuf sig_e, sig_g;             // impulse responses: call spectrum [F], combined spectra [rows][F]
     DevBuf ray_tab;                  // zone table of the zonal ray set
     DevBuf adj_jac;                  // backward: chain jacobians of the specular paths [paths][12]
-    DevBuf hit_tri, hit_t, vis_q, los_q, trav_cnt;  // lane-refill traversal: closest hits, query queues, counters
+    DevBuf hit_tri, hit_t, vis_q, los_q, trav_cnt;
+    DevBuf rec_mask;                 // per-microphone receiver test: visible microphones of each record  // lane-refill traversal: closest hits, query queues, counters
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -219,6 +220,7 @@ void st_sim_params_default(st_sim_params* p) {
     p->direct_gain = 1.0f;
     p->seed = 0;
     p->pose_index = 0;
+    p->los_mode = ST_LOS_REFERENCE;
 }
 
 const char* st_status_string(st_status s) {
@@ -270,11 +272,12 @@ st_status st_destroy(st_ctx* c) {
         release(*b);
     for (PathList* P : {&c->paths, &c->paths_diff})
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
-                          &P->meta, &P->dep})
+                          &P->meta, &P->dep, &P->mask})
             release(*b);
     for (DevBuf* b : {&c->adj_v, &c->adj_mic, &c->adj_emit, &c->tables.band, &c->tables.kband, &c->tables.bband,
                       &c->sig_e, &c->sig_g,
-                      &c->ray_tab, &c->adj_jac, &c->hit_tri, &c->hit_t, &c->vis_q, &c->los_q, &c->trav_cnt})
+                      &c->ray_tab, &c->adj_jac, &c->hit_tri, &c->hit_t, &c->vis_q, &c->los_q, &c->trav_cnt,
+                      &c->rec_mask})
         release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -538,6 +541,11 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     if (p.max_bounces < 1 || p.max_bounces > kMaxBounces || !(p.c > 0.0) || !(p.t_min >= 0.0f) ||
         !(p.los_eps >= 0.0f) || p.reflection_mode < 0 || p.reflection_mode > 1)
         return fail(c, ST_ERR_ARG, "simulate: 1..8 bounces, c > 0, t_min >= 0, los_eps >= 0");
+    if (p.los_mode != ST_LOS_REFERENCE && p.los_mode != ST_LOS_PER_MIC)
+        return fail(c, ST_ERR_ARG, "simulate: los_mode must be ST_LOS_REFERENCE or ST_LOS_PER_MIC");
+    if (p.los_mode == ST_LOS_PER_MIC &&
+        (c->M > 64 || (uint64_t)c->N * (uint64_t)p.max_bounces * (uint64_t)c->M >= ((uint64_t)1 << 32)))
+        return fail(c, ST_ERR_ARG, "simulate: the per-microphone receiver test needs M <= 64 and N * B * M < 2^32");
     if (c->n_theta > 0 && c->etab.cap < (size_t)c->n_theta * c->F * 4)
         return fail(c, ST_ERR_ARG, "simulate: emitter table was set for a different bin count");
     if (c->mic_nb > 0 && c->mic_nb != sc->S.n_bands)
@@ -579,7 +587,12 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, grow(c->R, 16), "alloc");
     CKC(c, grow(c->hit_tri, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
     CKC(c, grow(c->hit_t, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
-    CKC(c, grow(c->vis_q, (size_t)std::max<int64_t>(N, 1) * 4), "alloc");
+    const bool per_mic = p.los_mode == ST_LOS_PER_MIC;
+    CKC(c, grow(c->vis_q, (size_t)std::max<int64_t>(N, 1) * (per_mic ? (size_t)M : 1) * 4), "alloc");
+    if (per_mic) {
+        CKC(c, grow(c->rec_mask, (size_t)std::max<int64_t>(NB, 1) * 8), "alloc");
+        CKC(c, grow(c->paths.mask, (size_t)std::max<int64_t>(NB, 1) * 8), "alloc");
+    }
     CKC(c, grow(c->trav_cnt, 64), "alloc");
     CKC(c, grow(c->rec_tri, (size_t)std::max<int64_t>(NB, 1) * 4), "alloc");
     CKC(c, grow(c->rec_p, (size_t)std::max<int64_t>(NB, 1) * 12), "alloc");
@@ -592,7 +605,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     CKC(c, grow(c->scratch, scan_scratch_bytes(nflag)), "alloc");
     // Scenes whose hierarchy and triangles are well beyond L2 trace their visibility queries in the Morton
     // order of the hit points (all go to one point, so neighbours in that order share most nodes)
-    const bool vsort = S.n_tris >= kVisSortTris && N > 1;
+    const bool vsort = S.n_tris >= kVisSortTris && N > 1 && !per_mic;
     if (vsort) {
         CKC(c, grow(c->vs_keys, (size_t)N * 8), "alloc");
         CKC(c, grow(c->vs_scr, sort_scratch_bytes(N)), "alloc");
@@ -626,6 +639,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     unsigned long long* qctr = ptr<unsigned long long>(c->queries);
     CKC(c, cudaMemsetAsync(c->rec_tri.p, 0xff, (size_t)std::max<int64_t>(NB, 1) * 4, s), "memset");
     CKC(c, cudaMemsetAsync(c->rec_los.p, 0, (size_t)std::max<int64_t>(NB, 1), s), "memset");
+    if (per_mic) CKC(c, cudaMemsetAsync(c->rec_mask.p, 0, (size_t)std::max<int64_t>(NB, 1) * 8, s), "memset");
     CKC(c, cudaMemsetAsync(c->rec_r.p, 0, (size_t)std::max<int64_t>(NB, 1) * 8, s), "memset");
     CKC(c, cudaMemsetAsync(c->rec_p.p, 0, (size_t)std::max<int64_t>(NB, 1) * 12, s), "memset");
     CKC(c, cudaMemsetAsync(c->rec_d.p, 0, (size_t)std::max<int64_t>(NB, 1) * 12, s), "memset");
@@ -689,6 +703,9 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         ta.vis_q = ptr<uint32_t>(c->vis_q);
         ta.vis_n = ptr<uint32_t>(c->trav_cnt);
         ta.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 16);
+        ta.rec_mask = per_mic ? ptr<uint64_t>(c->rec_mask) : nullptr;
+        ta.mics = ptr<float>(c->mics);
+        ta.M = M;
         ta.sort_keys = vsort ? ptr<uint64_t>(c->vs_keys) : nullptr;
         ta.sort_scr = vsort ? c->vs_scr.p : nullptr;
         for (int k = 0; k < 3; ++k) {
@@ -791,6 +808,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     ga.keep = ptr<uint8_t>(c->keep);
     memcpy(ga.s, c->s, 12);
     ga.idx = ptr<uint32_t>(c->sidx);
+    ga.rec_mask = per_mic ? ptr<uint64_t>(c->rec_mask) : nullptr;
     auto set_paths = [&](AccumArgs& x, PathList& PL) {
         x.px = ptr<float>(PL.px);
         x.py = ptr<float>(PL.py);
@@ -826,6 +844,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         x.n_paths = NB;
         x.d_count = cnt + 2;
         set_paths(x, c->paths);
+        x.mask = per_mic ? ptr<uint64_t>(c->paths.mask) : nullptr;
         x.n_chunks = chunks_spec;
         if (stats) CKC(c, cudaEventRecord(c->ev[4], s), "event");
         CKC(c, accumulate(x, s), "accumulate specular");
@@ -987,6 +1006,17 @@ st_status st_get_paths(st_ctx* c, int32_t* tri, float* point, float* dir, double
     return ST_OK;
 }
 
+st_status st_get_receiver_masks(st_ctx* c, uint64_t* mask, int32_t mem) {
+    if (!c || !mask) return ST_ERR_ARG;
+    if (!c->has_last || c->last_params.los_mode != ST_LOS_PER_MIC)
+        return fail(c, ST_ERR_STATE, "get_receiver_masks: the last simulate made no per-microphone receiver test");
+    enter(c);
+    const size_t nb = (size_t)c->last_N * c->last_B;
+    CKC(c, cudaMemcpyAsync(mask, c->rec_mask.p, nb * 8, kind_out(mem), c->stream), "get_receiver_masks");
+    CKC(c, cudaStreamSynchronize(c->stream), "get_receiver_masks sync");
+    return ST_OK;
+}
+
 st_status st_get_diffraction(st_ctx* c, int64_t* n_out, int32_t* tri, float* point, uint8_t* keep, int64_t capacity,
                              int32_t mem) {
     if (!c || !n_out) return ST_ERR_ARG;
@@ -1020,6 +1050,8 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
     if ((grad_mic || grad_emitter) && c->n_theta > 0)
         return fail(c, ST_ERR_ARG, "backward: position gradients need an omni emitter");
     if (c->mic_nb > 0) return fail(c, ST_ERR_ARG, "backward: needs omni receivers");
+    if (c->last_params.los_mode != ST_LOS_REFERENCE)
+        return fail(c, ST_ERR_ARG, "backward: needs a simulate with the reference-point receiver test");
     enter(c);
     cudaStream_t s = c->stream;
     const st_sim_params& p = c->last_params;
@@ -1282,7 +1314,7 @@ void batch_release(BatchState& B) {
         for (DevBuf* b : {&T.lk, &T.g2, &T.lid, &T.qhi, &T.qlo, &T.bw, &T.band, &T.kband, &T.bband}) release(*b);
     for (PathList* P : {&B.spec, &B.diff})
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
-                          &P->meta, &P->dep})
+                          &P->meta, &P->dep, &P->mask})
             release(*b);
     for (auto st : B.streams) cudaStreamDestroy(st);
     for (auto ev : B.events) cudaEventDestroy(ev);
@@ -1485,6 +1517,8 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     st_sim_params p;
     st_sim_params_default(&p);
     if (params) p = *params;
+    if (p.los_mode != ST_LOS_REFERENCE)
+        return fail(c, ST_ERR_ARG, "simulate_batch: the batched form makes the reference-point receiver test only");
     st_tune tn = tune ? *tune : c->tune;
     if (!tune_ok(tn)) return fail(c, ST_ERR_ARG, "simulate_batch: tune out of range");
     for (int j = 0; j < n_jobs; ++j) {
@@ -1606,7 +1640,7 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     for (PathList* P : {&B.spec, &B.diff}) {
         const int64_t nP = P == &B.spec ? R1 : K1;
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
-                          &P->meta, &P->dep})
+                          &P->meta, &P->dep, &P->mask})
             CKC(c, grow(*b, (size_t)nP * 4), "batch alloc");
         P->n_max = nP;
     }
@@ -1717,6 +1751,7 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
     if (params) p = *params;
     p.max_bounces = J->max_bounces;
     p.pose_index = J->pose_index;
+    p.los_mode = ST_LOS_REFERENCE;  // the tuned shapes serve the batched form
     DevBuf out_buf;
     CKC(c, grow(out_buf, (size_t)3 * J->n_mics * J->n_bins * 8), "autotune alloc");
     const st_tune saved = c->tune;

@@ -147,6 +147,9 @@ struct TraceArgs {
     // before it is traced, so that neighbouring lanes share nodes; keys [N] and sort scratch, or null
     uint64_t* sort_keys; void* sort_scr;
     float blo[3], bscale[3];
+    // per-microphone receiver test (ST_LOS_PER_MIC): M queries per record (query = record id * M + m), the
+    // record's bit m of rec_mask set when microphone m is visible; null rec_mask: one query per record
+    uint64_t* rec_mask; const float* mics; int32_t M;
     // records [N][B]
     int32_t* rec_tri;
     float* rec_p;    // [N][B][3]
@@ -216,6 +219,7 @@ void mic_centroid_host_order(const float* mics_dev, int32_t M, float* R_dev, cud
 struct PathList {
     int64_t n_max = 0;
     DevBuf px, py, pz, dx, dy, dz, rhi, rlo, chain_lo, chain_hi, meta, dep;
+    DevBuf mask;  // u64 per path, per-microphone receiver test only (grown separately)
     // meta: bits 0..3 = chain length (specular) or 0 (diffraction), bits 8..15 = material of the
     // last leg's surface
 };
@@ -236,6 +240,8 @@ struct AccumArgs {
     int64_t n_paths;        // upper bound; actual count in *d_count
     const uint32_t* d_count;
     const uint32_t* d_base; // optional: first path of this launch in the path arrays (device), null = 0
+    const uint64_t* mask;   // optional (per-microphone receiver test): bit m of mask[path] = microphone m
+                            // receives the path; null = every microphone
     int32_t tile_tp, tile_kb;  // optional tile override: mic pairs per CTA, shared-memory KB (0 = default)
     const float* px; const float* py; const float* pz;
     const float* dx; const float* dy; const float* dz;
@@ -291,6 +297,7 @@ struct GatherArgs {
     const uint32_t* idx;   // compacted source indices
     const uint32_t* count;
     PathList* out;
+    const uint64_t* rec_mask;  // optional: per-microphone visibility of the records, copied to out->mask
 };
 cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s);
 // Stable sort of the compacted specular indices idx[0 .. cap) by emitter-table row (entries past *g.count

@@ -115,7 +115,16 @@ __global__ void k_shade(const TraceArgs a, int j, int64_t n_first) {
         a.rec_d[3 * id + 1] = dr.y;
         a.rec_d[3 * id + 2] = dr.z;
         const int lane = threadIdx.x & 31;
-        {  // visibility query of this record (warp-aggregated append)
+        if (a.rec_mask) {  // one visibility query per microphone (warp-aggregated append of M entries a lane)
+            a.rec_mask[id] = 0ull;
+            const unsigned active = __activemask();
+            const int leader = __ffs(active) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(a.vis_n, (uint32_t)__popc(active) * (uint32_t)a.M);
+            base = __shfl_sync(active, base, leader);
+            const uint32_t q0 = base + (uint32_t)__popc(active & ((1u << lane) - 1u)) * (uint32_t)a.M;
+            for (int m = 0; m < a.M; ++m) a.vis_q[q0 + m] = (uint32_t)id * (uint32_t)a.M + (uint32_t)m;
+        } else {  // visibility query of this record (warp-aggregated append)
             const unsigned active = __activemask();
             const int leader = __ffs(active) - 1;
             uint32_t base = 0;
@@ -186,6 +195,61 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const u
             if (live && trav_step<true>(T, S, stack, flags)) {
                 trav_count<true>(T, S);
                 out[id] = S.best < 0 ? 1 : 0;
+                live = false;
+            }
+            const unsigned lv = __ballot_sync(full, live);
+            const unsigned nd = __ballot_sync(full, !live && !exhausted);
+            if (lv == 0u || __popc(nd) >= kRefillAny) break;
+        }
+    }
+}
+
+// Per-microphone receiver test: query q of the queue is record q / M and microphone q % M; a visible
+// microphone sets its bit of the record's mask (and the record's flag: some microphone sees it).
+__global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics(const TraceArgs a, unsigned long long* ctr) {
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    const int64_t n = *a.vis_n;
+    const unsigned full = 0xffffffffu;
+    int2 stack[kStack];
+    TravState S;
+    int64_t id = -1;
+    int m = 0;
+    bool live = false, exhausted = false;
+    while (true) {
+        const bool need = !live && !exhausted;
+        const int64_t idx = claim(ctr, need);
+        if (need) {
+            if (idx < n) {
+                const uint32_t q = a.vis_q[idx];
+                id = (int64_t)(q / (uint32_t)a.M);
+                m = (int)(q - (uint32_t)id * (uint32_t)a.M);
+                warp_count(a.queries + 1);
+                const f3 o{a.rec_p[3 * id], a.rec_p[3 * id + 1], a.rec_p[3 * id + 2]};
+                const f3 target{a.mics[3 * m], a.mics[3 * m + 1], a.mics[3 * m + 2]};
+                float L;
+                const f3 u = normalize(sub(target, o), &L);
+                const float tmax = L - a.los_eps;
+                if (!(tmax > a.t_min)) {
+                    atomicOr(reinterpret_cast<unsigned long long*>(&a.rec_mask[id]), 1ull << m);
+                    a.rec_los[id] = 1;
+                } else {
+                    trav_init(S, T, o, u, a.rec_tri[id], a.t_min, tmax);
+                    live = true;
+                }
+            } else {
+                exhausted = true;
+            }
+        }
+        const unsigned lv0 = __ballot_sync(full, live);
+        const unsigned nd0 = __ballot_sync(full, !live && !exhausted);
+        if (lv0 == 0u && nd0 == 0u) break;
+        while (true) {
+            if (live && trav_step<true>(T, S, stack, a.flags)) {
+                trav_count<true>(T, S);
+                if (S.best < 0) {
+                    atomicOr(reinterpret_cast<unsigned long long*>(&a.rec_mask[id]), 1ull << m);
+                    a.rec_los[id] = 1;
+                }
                 live = false;
             }
             const unsigned lv = __ballot_sync(full, live);
@@ -401,8 +465,12 @@ cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
                 return e;
         }
         note_launch();
-        k_visible<<<trav_grid(a.N), kTravBlock, 0, s>>>(T, a.vis_q, a.vis_n, a.rec_p, a.rec_tri, a.R, 0.0f, 0.0f, 0.0f,
-                                                        a.t_min, a.los_eps, a.rec_los, a.ctr + 1, a.flags, a.queries);
+        if (a.rec_mask)
+            k_visible_mics<<<trav_grid(a.N * a.M), kTravBlock, 0, s>>>(a, a.ctr + 1);
+        else
+            k_visible<<<trav_grid(a.N), kTravBlock, 0, s>>>(T, a.vis_q, a.vis_n, a.rec_p, a.rec_tri, a.R, 0.0f, 0.0f,
+                                                            0.0f, a.t_min, a.los_eps, a.rec_los, a.ctr + 1, a.flags,
+                                                            a.queries);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

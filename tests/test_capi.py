@@ -45,10 +45,12 @@ def test_host_only_calls(lib):
     L = st.load()
     p = st.sim_params()
     assert p.max_bounces == 3 and abs(p.c - 343.0) < 1e-12 and p.components == 7
+    assert p.los_mode == st.ST_LOS_REFERENCE == 0 and st.ST_LOS_PER_MIC == 1
     c = st.curv_params()
     assert c.samples_per_vertex == 64 and c.sample_budget == 4_000_000
     assert L.st_status_string(0) == b"ok"
     assert L.st_status_string(-4) == b"invalid mesh"
     assert L.st_destroy(None) == -1
     assert L.st_simulate(None, None, None, None, None) == -1
+    assert L.st_get_receiver_masks(None, None, 0) == -1
     assert L.st_set_frequencies(None, 4, 1.0, 2.0) == -1
