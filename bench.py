@@ -286,12 +286,13 @@ def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 
             "max_rel_l2_batched_vs_plain": err, "first_call_s": first_call_s}
 
 
-def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2):
-    """Device time of one simulate on another workload (scene prebuilt, L2 flushed before each step)."""
+def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: int = 0):
+    """Device time of one simulate on another workload (scene prebuilt, L2 flushed before each step);
+    los_mode 1: the receiver test of every hit made per microphone."""
     dev = torch.cuda.current_device()
     ctx = st.Context(dev)
     sc = st.from_workload(ctx, wl)
-    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance, los_mode=los_mode)
     out = torch.empty((3, len(wl.mics), wl.n_bins), dtype=torch.complex64, device=f"cuda:{dev}")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream()
@@ -313,7 +314,8 @@ def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2):
            "value": segs / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_step": t / steps,
            "mic_spectra_per_s": len(wl.mics) * steps / (t / 1e3),
            "ms_trace": stats.ms_trace, "ms_diffraction": stats.ms_diffraction, "ms_accumulate": stats.ms_accumulate,
-           "visible_records": stats.visible_records, "diffraction_kept": stats.candidates_kept}
+           "visible_records": stats.visible_records, "diffraction_kept": stats.candidates_kept,
+           "anyhit_segments": stats.shadow_queries}
     ctx.close()
     return res
 
@@ -489,6 +491,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain pose sweep")
+    ap.add_argument("--no-per-mic", action="store_true", help="skip the per-microphone receiver-test timing")
     ap.add_argument("--no-vegetation", action="store_true", help="skip the full-size vegetation simulate timing")
     ap.add_argument("--case", default=None, choices=["accum", "adjoint", "trace", "narrow"],
                     help="run a small case of one kernel family a few times and exit (for profiler captures)")
@@ -628,6 +631,9 @@ def main():
     vegetation = None
     if not args.no_vegetation and args.workload != "vegetation":
         vegetation = measure_workload(st, torch, synth.vegetation(seed=303))
+    per_mic = None
+    if not args.no_per_mic and len(wl.mics) <= 64:
+        per_mic = measure_workload(st, torch, wl, los_mode=st.ST_LOS_PER_MIC)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -648,7 +654,7 @@ def main():
                          "ms_accumulate": s0.ms_accumulate},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
             "traversal": traversal, "signal": signal, "scene_update": scene_update, "batched": batched,
-            "vegetation": vegetation,
+            "vegetation": vegetation, "receiver_test_per_mic": per_mic,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
     print(json.dumps(line))
     if world > 1:
