@@ -2,12 +2,14 @@
 //
 // A job table in device memory describes every pose (scene arrays, sensor inputs read from the
 // caller's device memory, offsets into the batch's global arrays).  Every stage runs over the union of
-// all jobs' work items in one persistent grid-stride launch, each item finding its job by binary
-// search over the jobs' offsets: ray generation and one launch per bounce level (a single live-ray
-// queue across jobs), diffraction sampling and filters, direct visibility, path gathering and direct
-// spectra.  Poses are read from device memory at run time, so a captured CUDA graph of the batch can
-// be replayed after the caller updates them in place.  Compiled with -fmad=false like the single-pose
-// tracing kernels (same float32 steps, so the batched path sets equal the single-pose ones).
+// all jobs' work items, each item finding its job by binary search over the jobs' offsets: ray
+// generation with the first bounce, per bounce level a closest-hit, a shading and a visibility launch
+// over one live-ray queue across jobs (the traversal launches persistent with lane refill, each lane
+// traversing its own job's scene), diffraction sampling and filters with a queued line-of-sight launch,
+// direct visibility, path gathering and direct spectra.  Poses are read from device memory at run time,
+// so a captured CUDA graph of the batch can be replayed after the caller updates them in place.
+// Compiled with -fmad=false like the single-pose tracing kernels (same float32 steps, so the batched
+// path sets equal the single-pose ones).
 #include <algorithm>
 
 #include "st_geom.cuh"

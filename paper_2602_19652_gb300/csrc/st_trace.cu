@@ -1,19 +1,21 @@
 // Ray tracing kernels (Algorithm 1, Sec. III-D filters, Sec. III-E visibility).
 //
-// Traversal: stack-based walk of the 64-byte two-child LBVH nodes (both child boxes and child
-// references in four float4 loads through the read-only path), nearer child first, far child
-// pushed with its entry distance so it is skipped on pop when a closer hit is known.  Boxes are
-// padded at build time and the slab test widens the far distance, so a box is never rejected
-// when the float32 triangle test would hit inside it; the closest hit is the smallest
-// (t, triangle index), which makes the result independent of the tree's shape.
+// Traversal (st_trace_dev.cuh): stack-based walk of the 4-wide BVH (128-byte nodes: the four children's
+// boxes as six float4 rows and their references, seven 128-bit loads through the read-only path), the
+// nearest hit child next and the others pushed farthest first with their entry distances, skipped on
+// pop when a closer hit is known.  Boxes are padded at build time and the slab test widens the far
+// distance, so a box is never rejected when the float32 triangle test would hit inside it; the closest
+// hit is the smallest (t, triangle index), which makes the result independent of the tree's shape.
 //
 // Bounces run as a wavefront over a compacted queue of live rays, three launches per bounce: closest
 // hits, shading (reflection, float64 path length, the record [ray][bounce], the next queue and the
-// visibility queue), and the visibility rays to the receiver reference point.  The traversal kernels
-// are persistent with lane refill: a lane whose query has finished takes the next one from a
-// warp-aggregated atomic counter while the other lanes of its warp continue, so a warp is not held by
-// its longest query.  Results do not depend on the order: closest hits are the smallest (t, triangle
-// index), visibility is the absence of any hit in the segment.
+// visibility queue), and the visibility rays (to the receiver reference point, or one per microphone
+// with the per-microphone receiver test).  The traversal kernels are persistent with lane refill: a
+// query advances one wide node or one leaf triangle per step, and a lane whose query has finished takes
+// the next one from a warp-aggregated atomic counter while the other lanes of its warp continue.  In
+// large scenes the visibility queue is sorted by the Morton code of the hit points first.  Results do not
+// depend on the order: closest hits are the smallest (t, triangle index), visibility is the absence of
+// any hit in the segment.
 // Compiled with -fmad=false (see st_geom.cuh).
 #include <algorithm>
 
