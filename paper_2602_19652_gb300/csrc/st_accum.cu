@@ -12,6 +12,9 @@
 //       W = 2^(r log2-decay per bin) e^(j 2 pi frac(r df / c))                   -> shared memory
 //   2.  per thread (R mics x KT consecutive bins): S += 2^(-gamma^2 g + log2 X) z ;  z *= W
 // so the inner loop is one ex2, one FFMA for the exponent and six FP32 ops for the complex update.
+// Diffraction paths without an emitter table skip 1a: their factor depends on the material and the bin
+// only, and the term loop reads it from the CTA's material table at the row the producer names.
+// With the per-microphone receiver test a microphone that does not see the path gets a zero anchor.
 // The phase never loses precision: only frac(f r / c) enters FP32, and the recurrence runs at most
 // KT steps from an exactly reduced anchor.
 #include <math.h>
