@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
             u64 er = z0.x, ei = z0.y;  // even chain: bins 0, 2, 4, ...
             u64 orr = er, oi = ei;     // odd chain: bins 1, 3, 5, ...
             cmul2(orr, oi, w1r, w1i, fmul2(w1i, pk2(-1.0f, -1.0f)));
-            const ulonglong2* trow = reinterpret_cast<const ulonglong2*>(C.tab) + (size_t)p * KB + s;
+            const float2* trow = reinterpret_cast<const float2*>(C.tab) + (size_t)p * KB + s;
+            const float2 ngv = up2(ng);  // -gamma^2 of the two microphones
             // diffraction with the material table read directly: the producer left the offset of the path's
             // material row in the (otherwise unused) lobe slot
             const u64* mrow = reinterpret_cast<const u64*>(mt) + s;
@@ -176,11 +177,10 @@ __global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) 
                 if (KIND == 1 && g.mat_direct) {
                     E = mrow[kk * NS];
                 } else if (KIND == 0) {
-                    const ulonglong2 t = trow[kk * NS];
-                    const float2 arg = up2(ffma2(ng, t.y, t.x));
-                    E = pk2(ex2(arg.x), ex2(arg.y));
+                    const float2 t = trow[kk * NS];  // (log2 X, g)
+                    E = pk2(ex2(fmaf(ngv.x, t.y, t.x)), ex2(fmaf(ngv.y, t.y, t.x)));
                 } else {
-                    E = trow[kk * NS].x;
+                    E = reinterpret_cast<const u64*>(trow)[kk * NS];  // (X, X)
                 }
                 if (DIR) {  // receiver directivity, linear between bands
                     const float2 bwv = bwt[kk * NS + s];

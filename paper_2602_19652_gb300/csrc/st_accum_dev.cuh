@@ -126,7 +126,7 @@ struct Geom {
 };
 
 // Shared memory: two pipeline buffers, each
-//   tab [PT][KB] float4      per (path, bin): (log2 X, log2 X, g, g) specular, (X, X, -, -) diffraction,
+//   tab [PT][KB] float2      per (path, bin): (log2 X, g) specular, (X, X) diffraction,
 //                            bin kb + s*KT + kk stored at i = kk*NS + s
 //   za  [PT][NS][TP] ulonglong2  phasor at bin kb + s*KT of the two mics of pair tp (re pair, im pair)
 //   wst [PT][4][TP] u64      one-bin step re, im and two-bin step re, im of the pair (component-major)
@@ -148,7 +148,7 @@ __device__ __forceinline__ Buf buf_at(float4* base, const Geom& g, int b) {
     Buf B;
     char* p = reinterpret_cast<char*>(base) + (size_t)b * g.buf_bytes;
     B.tab = reinterpret_cast<float4*>(p);
-    B.za = reinterpret_cast<ulonglong2*>(B.tab + (g.mat_direct ? (size_t)0 : (size_t)g.PT * g.KB));
+    B.za = reinterpret_cast<ulonglong2*>(p + (g.mat_direct ? (size_t)0 : (size_t)g.PT * g.KB * 8));
     B.wst = reinterpret_cast<u64*>(B.za + (size_t)g.PT * g.NS * g.TP);
     B.ngp = B.wst + (size_t)g.PT * g.TP * 4;
     B.adj = B.ngp + (size_t)g.PT * g.TP;
@@ -353,18 +353,15 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
                 if (k0 + 2 * KT >= a.F) lx4.z = kNegInf;
                 if (k0 + 3 * KT >= a.F) lx4.w = kNegInf;
             }
-            float4* dst = B.tab + (size_t)p * KB + i;
+            // four 8-byte entries (32-byte aligned: i is a multiple of 4)
+            float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float2*>(B.tab) + (size_t)p * KB + i);
             if (KIND == 0) {
-                dst[0] = make_float4(lx4.x, lx4.x, g4.x, g4.x);
-                dst[1] = make_float4(lx4.y, lx4.y, g4.y, g4.y);
-                dst[2] = make_float4(lx4.z, lx4.z, g4.z, g4.z);
-                dst[3] = make_float4(lx4.w, lx4.w, g4.w, g4.w);
+                dst[0] = make_float4(lx4.x, g4.x, lx4.y, g4.y);
+                dst[1] = make_float4(lx4.z, g4.z, lx4.w, g4.w);
             } else {
                 const float x0 = ex2(lx4.x), x1 = ex2(lx4.y), x2 = ex2(lx4.z), x3 = ex2(lx4.w);
-                dst[0] = make_float4(x0, x0, 0.f, 0.f);
-                dst[1] = make_float4(x1, x1, 0.f, 0.f);
-                dst[2] = make_float4(x2, x2, 0.f, 0.f);
-                dst[3] = make_float4(x3, x3, 0.f, 0.f);
+                dst[0] = make_float4(x0, x0, x1, x1);
+                dst[1] = make_float4(x2, x2, x3, x3);
             }
         }
     } else {
@@ -404,10 +401,10 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
                 }
             }
             if (KIND == 0) {
-                B.tab[(size_t)p * KB + i] = make_float4(lx, lx, gg, gg);
+                reinterpret_cast<float2*>(B.tab)[(size_t)p * KB + i] = make_float2(lx, gg);
             } else {
                 const float x = ex2(lx);
-                B.tab[(size_t)p * KB + i] = make_float4(x, x, 0.0f, 0.0f);
+                reinterpret_cast<float2*>(B.tab)[(size_t)p * KB + i] = make_float2(x, x);
             }
         }
     }
@@ -523,7 +520,7 @@ inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t bu
     const size_t mat_bytes = (size_t)2 * n_mat * g.KB * 4;  // two floats or one packed pair per (material, bin)
     g.mat_cached = mat_bytes <= 24 * 1024 ? 1 : 0;
     g.mat_direct = (mat_direct && g.mat_cached) ? 1 : 0;
-    const size_t per_path = (g.mat_direct ? (size_t)0 : (size_t)g.KB * 16) + (size_t)g.NS * g.TP * 16 +
+    const size_t per_path = (g.mat_direct ? (size_t)0 : (size_t)g.KB * 8) + (size_t)g.NS * g.TP * 16 +
                             (size_t)g.TP * 40 + (size_t)g.MP * dir_nb * 4;
     // fixed region: cached material tables, then (directional receivers) per-bin band interpolation
     g.mat_bytes = (g.mat_cached ? mat_bytes : 0) + (dir_nb ? (size_t)g.KB * 8 : 0);

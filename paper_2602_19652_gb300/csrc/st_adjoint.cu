@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             u64 c1r = 0ull, c1i = 0ull;  // diffraction: C1 = sum_kk kk conj(G) T directly
             float y[KT];
             const float2 ngv = up2(ng);  // -gamma^2 of the two microphones (lobe sums)
-            const ulonglong2* trow = reinterpret_cast<const ulonglong2*>(C.tab) + (size_t)p * KB + s;
+            const float2* trow = reinterpret_cast<const float2*>(C.tab) + (size_t)p * KB + s;
             // diffraction with the material table read directly: row offset left by the producer in ngp
             const u64* mrow = reinterpret_cast<const u64*>(mt) + s;
             if (KIND == 1 && g.mat_direct) mrow += (int)(uint32_t)ng;
@@ -219,7 +219,9 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 //   C0 = z0 P(W), C1 = z0 W P'(W),  P(W) = sum_kk u_kk W^kk,
                 // P and P' by Horner's scheme from the top bin (no explicit phasor chain).
                 const u64 nw1i = fmul2(w1i, pk2(-1.0f, -1.0f));
-                auto Eat = [&](int kk) -> u64 { return g.mat_direct ? mrow[kk * NS] : trow[kk * NS].x; };
+                auto Eat = [&](int kk) -> u64 {
+                    return g.mat_direct ? mrow[kk * NS] : reinterpret_cast<const u64*>(trow)[kk * NS];
+                };
                 u64 E = Eat(KT - 1);
                 u64 pr = fmul2(Gr[KT - 1], E), pim = fmul2(Gi[KT - 1], E), dpr = 0ull, dpi = 0ull;
 #pragma unroll
@@ -243,9 +245,8 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             } else {
 #pragma unroll
                 for (int kk = 0; kk < KT; ++kk) {  // specular
-                    const ulonglong2 t = trow[kk * NS];
-                    const float2 arg = up2(ffma2(ng, t.y, t.x));
-                    const u64 E = pk2(ex2(arg.x), ex2(arg.y));
+                    const float2 t = trow[kk * NS];  // (log2 X, g)
+                    const u64 E = pk2(ex2(fmaf(ngv.x, t.y, t.x)), ex2(fmaf(ngv.y, t.y, t.x)));
                     const u64 zr = (kk & 1) ? orr : er, zi = (kk & 1) ? oi : ei;
                     const u64 Tr = fmul2(E, zr), Ti = fmul2(E, zi);
                     const u64 wr = ffma2(Gr[kk], Tr, fmul2(Gi[kk], Ti));        // Re(conj(G) T)
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                     c0i = fadd2(c0i, wi);
                     qr = fadd2(qr, c0r);  // running sum of prefix sums: sum_kk kk w = KT C0 - Q
                     qi = fadd2(qi, c0i);
-                    if (KIND == 0) cg = ffma2(t.y, wr, cg);
+                    if (KIND == 0) cg = ffma2(pk2(t.y, t.y), wr, cg);
                     const float2 wr2 = up2(wr);
                     y[kk] = j.do_beta ? fmaf(wr2.x, ngv.x, wr2.y * ngv.y) : wr2.x + wr2.y;
                     if (kk & 1) cmul2(orr, oi, w2r, w2i, nw2i); else cmul2(er, ei, w2r, w2i, nw2i);
@@ -622,7 +623,7 @@ cudaError_t launch_adjoint(const AccumArgs& a, const AdjointArgs& j, const Geom&
 namespace {
 
 size_t adjoint_per_path(const acc::Geom& g) {
-    return (g.mat_direct ? (size_t)0 : (size_t)g.KB * 16) + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40 +
+    return (g.mat_direct ? (size_t)0 : (size_t)g.KB * 8) + (size_t)g.NS * g.TP * 16 + (size_t)g.TP * 40 +
            (size_t)g.TP * 56;
 }
 
