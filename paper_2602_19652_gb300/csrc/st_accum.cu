@@ -396,7 +396,7 @@ __global__ void k_gather_diff(const GatherArgs g, float* px, float* py, float* p
 
 // accumulator tile shape: mic pairs per CTA and shared-memory budget (set by the tuner or ST_ACCUM_TILE="tp,kb")
 int g_tile_tp = 16;
-size_t g_tile_budget = 96 * 1024;
+size_t g_tile_budget = 104 * 1024;  // two CTAs per SM (swept 88-110 KB: 104 fastest on the clutter workload)
 int g_tile_kt = 16;
 bool g_tile_env_read = false;
 
