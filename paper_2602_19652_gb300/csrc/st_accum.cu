@@ -84,8 +84,10 @@ __global__ void k_tables(int32_t F, int32_t n_mat, int32_t n_bands, const float*
     }
 }
 
+// two CTAs per SM (128 registers) stated explicitly: left to the heuristic, small edits elsewhere in the unit
+// have turned it into one CTA of 236 registers; the directional variants keep one CTA (250 registers)
 template <int KT, int KIND, int DIR>
-__global__ void __launch_bounds__(256) k_accum(const AccumArgs a, const Geom g) {
+__global__ void __launch_bounds__(256, DIR ? 1 : 2) k_accum(const AccumArgs a, const Geom g) {
     static_assert((KT & (KT - 1)) == 0 && KT >= 2, "KT must be a power of two");
     extern __shared__ float4 smem4[];
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
