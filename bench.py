@@ -433,7 +433,7 @@ def measure_scene_update(st, torch, ctx, sc, wl, reps: int = 3):
 def run_case(st, torch, case: str, reps: int):
     """Small cases of single kernels for profiling (ncu captures): no timing output."""
     dev = torch.cuda.current_device()
-    if case in ("accum", "adjoint", "trace"):
+    if case in ("accum", "adjoint", "trace", "trace_per_mic"):
         wl = synth.clutter(seed=202, n_rays=200_000)
     elif case == "narrow":
         wl = synth.vegetation(seed=303, n_rays=500_000)
@@ -441,7 +441,8 @@ def run_case(st, torch, case: str, reps: int):
         raise SystemExit(f"unknown case {case}")
     ctx = st.Context(dev)
     sc = st.from_workload(ctx, wl)
-    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance,
+                      los_mode=st.ST_LOS_PER_MIC if case == "trace_per_mic" else st.ST_LOS_REFERENCE)
     S = ctx.simulate(sc, p)
     if case == "adjoint":
         G = (torch.randn_like(S.real) + 1j * torch.randn_like(S.real)).to(torch.complex64)
@@ -493,7 +494,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain pose sweep")
     ap.add_argument("--no-per-mic", action="store_true", help="skip the per-microphone receiver-test timing")
     ap.add_argument("--no-vegetation", action="store_true", help="skip the full-size vegetation simulate timing")
-    ap.add_argument("--case", default=None, choices=["accum", "adjoint", "trace", "narrow"],
+    ap.add_argument("--case", default=None, choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow"],
                     help="run a small case of one kernel family a few times and exit (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
