@@ -606,9 +606,10 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     // Scenes whose hierarchy and triangles are well beyond L2 trace their visibility queries in the Morton
     // order of the hit points (all go to one point, so neighbours in that order share most nodes)
     const bool vsort = S.n_tris >= kVisSortTris && N > 1 && !per_mic;
-    if (vsort) {
-        CKC(c, grow(c->vs_keys, (size_t)N * 8), "alloc");
-        CKC(c, grow(c->vs_scr, sort_scratch_bytes(N)), "alloc");
+    if (vsort || K > 1) {  // (the line-of-sight queue of the diffraction candidates is sorted likewise)
+        const int64_t nk = std::max<int64_t>(vsort ? N : 1, K);
+        CKC(c, grow(c->vs_keys, (size_t)nk * 8), "alloc");
+        CKC(c, grow(c->vs_scr, sort_scratch_bytes(nk)), "alloc");
     }
     if (c->n_theta > 0 && NB > 1) {  // emitter-table row order of the specular path list
         CKC(c, grow(c->th_keys, (size_t)NB * 8), "alloc");
@@ -750,6 +751,13 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         da.los_q = ptr<uint32_t>(c->los_q);
         da.los_n = ptr<uint32_t>(c->trav_cnt) + 1;
         da.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 32);
+        da.sort_keys = K > 1 ? ptr<uint64_t>(c->vs_keys) : nullptr;
+        da.sort_scr = K > 1 ? c->vs_scr.p : nullptr;
+        for (int k = 0; k < 3; ++k) {
+            const float ext = S.bounds_hi[k] - S.bounds_lo[k];
+            da.blo[k] = S.bounds_lo[k];
+            da.bscale[k] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+        }
         CKC(c, diffraction_sample(da, s), "diffraction");
     }
     if (stats) CKC(c, cudaEventRecord(c->ev[2], s), "event");

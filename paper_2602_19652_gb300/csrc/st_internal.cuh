@@ -193,6 +193,9 @@ struct DiffArgs {
     unsigned long long* ctr;           // lane-refill counter of the line-of-sight kernel
     uint32_t* flags;
     unsigned long long* queries;
+    // optional: line-of-sight queue sorted by the Morton code of the candidate points (keys [K], scratch)
+    uint64_t* sort_keys; void* sort_scr;
+    float blo[3], bscale[3];
 };
 cudaError_t diffraction_sample(DiffArgs& a, cudaStream_t s);
 

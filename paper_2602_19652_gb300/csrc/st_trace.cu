@@ -389,6 +389,27 @@ __global__ void k_vis_keys(const TraceArgs a, uint64_t* keys) {
     }
 }
 
+// Morton code (kLosBits per axis) of the candidate point of every queued line-of-sight query
+constexpr int kLosBits = 10;  // swept 0, 5, 10 bits: 10 fastest on the clutter workload (5 on vegetation)
+__global__ void k_los_keys(const DiffArgs a, uint64_t* keys) {
+    const int64_t n = *a.los_n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.K; c += stride) {
+        uint64_t key = 1ull << (3 * kLosBits);
+        if (c < n) {
+            const int64_t g = a.los_q[c];
+            const float cells = (float)(1 << kLosBits);
+            uint32_t m = 0;
+            for (int k = 0; k < 3; ++k) {
+                const float u = (a.cand_p[3 * g + k] - a.blo[k]) * a.bscale[k] * (cells * (1.0f / 1024.0f));
+                m |= spread10((uint32_t)fminf(fmaxf(u, 0.0f), cells - 1.0f)) << (2 - k);
+            }
+            key = m;
+        }
+        keys[c] = key;
+    }
+}
+
 // Octahedral map of a direction to [0,1]^2, 16 bits per axis, Morton-interleaved: nearby directions
 // get nearby keys, so sorting by the key groups rays that traverse the same part of the scene.
 __device__ __forceinline__ uint32_t spread16(uint32_t x) {
@@ -486,6 +507,12 @@ cudaError_t diffraction_sample(DiffArgs& a, cudaStream_t s) {
     note_launch();
     k_diffraction<<<grid_for(a.K, 128, 152 * 16), 128, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.sort_keys && kLosBits > 0) {  // stable: equal codes keep the queue order
+        note_launch();
+        k_los_keys<<<grid_for(a.K, 256), 256, 0, s>>>(a, a.sort_keys);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = radix_sort_u64(a.sort_keys, a.los_q, a.K, 3 * kLosBits + 1, a.sort_scr, s)) != cudaSuccess) return e;
+    }
     const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
     note_launch();
     k_visible<<<trav_grid(a.K), kTravBlock, 0, s>>>(T, a.los_q, a.los_n, a.cand_p, a.cand_tri, nullptr, a.s[0], a.s[1],
