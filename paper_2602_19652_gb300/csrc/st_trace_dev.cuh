@@ -205,7 +205,7 @@ constexpr int kTravBlock = 128;
 // a warp stops stepping to refill once this many of its lanes wait for a query (closest-hit and
 // any-hit kernels)
 constexpr int kRefillClosest = 16;
-constexpr int kRefillAny = 16;
+constexpr int kRefillAny = 28;
 
 // Visibility of `target` from o: direction normalize(target - o), t in (t_min, |target - o| - eps).
 __device__ __forceinline__ bool visible(const Trav& T, f3 o, f3 target, int32_t exclude, float t_min, float eps,
