@@ -89,6 +89,21 @@ def test_two_ears_with_directivity(st):
         assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
 
 
+def test_single_microphone_equals_reference_point_test(st):
+    # one microphone behind the wall: the wall's own hit points see it, the floor's in front of it do not
+    wl = dataclasses.replace(_wall_workload(2000), mics=np.array([[-1.0, 0.0, 1.0]], np.float32))
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl)
+    S0 = ctx.simulate(sc, st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)).cpu().numpy()
+    los0 = ctx.paths(wl.bounces)["los"]
+    S1 = ctx.simulate(sc, st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance,
+                                        los_mode=st.ST_LOS_PER_MIC)).cpu().numpy()
+    assert np.array_equal(ctx.paths(wl.bounces)["los"], los0)
+    assert np.array_equal(ctx.receiver_masks(wl.bounces), los0.astype(np.uint64))
+    assert 0 < los0.sum() < (ctx.paths(wl.bounces)["tri"] >= 0).sum()
+    assert np.array_equal(S1, S0)
+
+
 def test_mode_argument_checks(st):
     wl = synth.shoebox(seed=7, n_rays=64, bounces=2, n_mics=65, n_bins=8)
     ctx = st.Context(0)

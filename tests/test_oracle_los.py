@@ -4,6 +4,7 @@ visibility ray per microphone instead of one towards the array's reference point
 The expectations come from the geometry, not from the oracle's visibility code: in an empty convex room
 every hit point on a wall sees every interior point, and a plane wall separates the half-spaces on its two
 sides."""
+import dataclasses
 import math
 
 import numpy as np
@@ -26,6 +27,18 @@ def test_convex_room_every_microphone_visible_and_spectra_unchanged():
     assert np.array_equal(rec["los"], hit.astype(np.uint8))
     assert np.array_equal(o0["rec"]["los"], rec["los"])
     # the same (record, microphone) terms: identical sums
+    assert np.array_equal(o1["spectra"], o0["spectra"])
+
+
+def test_single_microphone_equals_reference_point_test():
+    """With one microphone the reference point is the microphone itself: both tests cast the same rays.
+    One microphone behind the wall: the wall's own hit points see it, the floor's in front of it do not."""
+    wl = dataclasses.replace(_wall_workload(2000), mics=np.array([[-1.0, 0.0, 1.0]], np.float32))
+    o0 = oracle.simulate(wl, components=1)
+    o1 = oracle.simulate(wl, components=1, los_mode=1)
+    assert np.array_equal(o1["rec"]["los"], o0["rec"]["los"])
+    assert np.array_equal(o1["rec"]["mask"], o0["rec"]["los"].astype(np.uint64))
+    assert 0 < o0["rec"]["los"].sum() < (o0["rec"]["tri"] >= 0).sum()
     assert np.array_equal(o1["spectra"], o0["spectra"])
 
 
