@@ -1005,6 +1005,7 @@ st_status st_get_paths(st_ctx* c, int32_t* tri, float* point, float* dir, double
     if (!c->has_last) return fail(c, ST_ERR_STATE, "get_paths: no simulate yet");
     enter(c);
     const size_t nb = (size_t)c->last_N * c->last_B;
+    if (nb == 0) return ST_OK;  // no emitter rays: nothing to copy
     if (tri) CKC(c, cudaMemcpyAsync(tri, c->rec_tri.p, nb * 4, kind_out(mem), c->stream), "get_paths");
     if (point) CKC(c, cudaMemcpyAsync(point, c->rec_p.p, nb * 12, kind_out(mem), c->stream), "get_paths");
     if (dir) CKC(c, cudaMemcpyAsync(dir, c->rec_d.p, nb * 12, kind_out(mem), c->stream), "get_paths");
@@ -1020,6 +1021,7 @@ st_status st_get_receiver_masks(st_ctx* c, uint64_t* mask, int32_t mem) {
         return fail(c, ST_ERR_STATE, "get_receiver_masks: the last simulate made no per-microphone receiver test");
     enter(c);
     const size_t nb = (size_t)c->last_N * c->last_B;
+    if (nb == 0) return ST_OK;
     CKC(c, cudaMemcpyAsync(mask, c->rec_mask.p, nb * 8, kind_out(mem), c->stream), "get_receiver_masks");
     CKC(c, cudaStreamSynchronize(c->stream), "get_receiver_masks sync");
     return ST_OK;

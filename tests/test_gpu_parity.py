@@ -4,6 +4,7 @@ Bars: path sets (hit triangle per bounce, hit points, reflected directions, floa
 visibility flags), curvature, diffraction samples and filters bit-exact; spectra within 1e-4
 relative L2 error per component (the target tolerance of the path; float32 amplitudes with
 float-float range-reduced phases on the GPU against float64 throughout in the oracle)."""
+import dataclasses
 import math
 
 import numpy as np
@@ -126,6 +127,27 @@ def test_ragged_sizes_with_diffraction(st, M, F):
     assert keep.sum() > 2000
     for c in range(3):
         assert rel_l2(S[c], o["spectra"][c]) <= TOL, (M, F, c, rel_l2(S[c], o["spectra"][c]))
+
+
+@pytest.mark.parametrize("los_mode", [0, 1])
+def test_zero_rays_direct_and_diffraction_only(st, los_mode):
+    """An emitter with no rays: no specular records (the specular spectra are exactly zero) while the
+    direct path and diffraction still follow the oracle, in both receiver-test modes."""
+    import oracle
+    wl = dataclasses.replace(small_clutter(target_tris=3000, n_rays=1, n_mics=3, n_bins=20, bounces=2),
+                             dirs=np.zeros((0, 3), np.float32))
+    ctx, sc, S, stats = gpu_run(st, wl, curv=st.curv_params(sample_budget=60_000), los_mode=los_mode)
+    o = oracle.simulate(wl, curv=dict(budget=60_000), los_mode=los_mode)
+    assert stats.records == 0 and ctx.paths(wl.bounces)["tri"].shape == (0, wl.bounces)
+    if los_mode:
+        assert ctx.receiver_masks(wl.bounces).shape == (0, wl.bounces)
+    assert np.all(S[0] == 0)
+    _, _, keep = ctx.diffraction()
+    assert np.array_equal(keep, o["cand_keep"]) and keep.sum() > 1000
+    assert np.array_equal(ctx.direct_visibility(), o["direct_vis"])
+    for c in (1, 2):
+        assert np.abs(o["spectra"][c]).sum() > 0
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
 
 
 @pytest.mark.parametrize("T", [1, 2, 3, 4, 5, 7, 8, 9, 31, 32, 33, 1000])
