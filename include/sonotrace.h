@@ -114,8 +114,10 @@ typedef struct st_stats {
                                    queries, then by any-hit queries (0 otherwise) */
 } st_stats;
 
+/* Fill a parameter block with the library defaults (every field; the caller owns the block). */
 void st_curv_params_default(st_curv_params* p);
 void st_sim_params_default(st_sim_params* p);
+/* Static name of a status code ("unknown status" for a value outside the list above). */
 const char* st_status_string(st_status s);
 /* Message of the last failing call on ctx (owned by ctx, valid until the next call). */
 const char* st_last_error(const st_ctx* ctx);
@@ -126,6 +128,8 @@ st_status st_create(st_ctx** out, int32_t device, void* cuda_stream);
 /* Frees the context, its working memory and every scene still loaded into it (their handles become
  * invalid: do not pass them to st_scene_destroy afterwards). */
 st_status st_destroy(st_ctx* ctx);
+/* Issue later work on another stream of the same device (a cudaStream_t; NULL = legacy default).  Work
+ * already issued stays on the old stream: synchronise it first if later calls read its results. */
 st_status st_set_stream(st_ctx* ctx, void* cuda_stream);
 
 /* Scene (Sec. III-B: the registered objects' meshes).  verts [n_verts][3], tris [n_tris][3]
@@ -156,6 +160,8 @@ st_status st_scene_update_vertices(st_scene* scene, const float* verts, int32_t 
 /* Copy per-vertex G [n_verts], per-triangle C [n_tris] and the diffraction sample count per
  * mesh out (any may be NULL).  n_samples has one entry per mesh id up to max(tri_object). */
 st_status st_scene_get_curvature(st_scene* scene, float* G, float* C, int64_t* n_samples, int32_t mem);
+/* Synchronise the context's stream, then free the scene's device memory; NULL is ST_ERR_ARG.  A recorded
+ * batch is recorded again at its next st_simulate_batch; st_backward needs a new simulate. */
 st_status st_scene_destroy(st_scene* scene);
 
 /* Emitter (Algorithm 1 inputs): position, orientation quaternion (w, x, y, z; forward is +x
@@ -167,10 +173,12 @@ st_status st_set_emitter(st_ctx* ctx, const float pos[3], const float quat[4], i
 /* Receivers: positions [n_mics][3]; optional orientations [n_mics][4] and directivity tables
  * [n_mics][n_el][n_az][n_bands] on the (az, el) grid az = -pi + 2 pi i / n_az, el = -pi/2 +
  * pi j / (n_el - 1) of the arrival direction in the microphone frame, bands = the materials'
- * band centres (NULL = omni). */
+ * band centres (NULL = omni).  1..4096 microphones; with tables n_el >= 2, n_az >= 1 and 1..64 bands
+ * (ST_ERR_ARG otherwise). */
 st_status st_set_receivers(st_ctx* ctx, int32_t n_mics, const float* pos, const float* quats,
                            const float* tables, int32_t n_el, int32_t n_az, int32_t n_bands, int32_t mem);
-/* Uniform frequency grid f_k = f_lo + k (f_hi - f_lo) / (n_bins - 1), k = 0..n_bins-1, Hz. */
+/* Uniform frequency grid f_k = f_lo + k (f_hi - f_lo) / (n_bins - 1), k = 0..n_bins-1, Hz (one bin: f_lo).
+ * 1..2^20 bins and 0 < f_lo < f_hi (ST_ERR_ARG otherwise). */
 st_status st_set_frequencies(st_ctx* ctx, int32_t n_bins, double f_lo, double f_hi);
 
 /* One simulation: tracing, diffraction, direct path, accumulation.  spectra_out is caller-owned
