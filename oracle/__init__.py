@@ -83,7 +83,7 @@ def _declare(L):
     L.ora_los_per_mic.restype = C.c_int
     L.ora_spectra.restype = C.c_int
     L.ora_spectra_grad.argtypes = [C.POINTER(SpecParams), I64, I32, P, P, P, P, P, P, P, I64, P, P, P, P,
-                                   P, P, P, P, P, P, P]
+                                   P, P, P, P, P, P, P, P]
     L.ora_spectra_grad.restype = C.c_int
 
 
@@ -299,7 +299,8 @@ def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand
     """G: complex [3][M][F] = dL/dRe S + j dL/dIm S.  Returns (dk [n_mat][n_bands], dmic [M][3], demit [3]),
     and dbeta [n_mat][n_bands] (lobe widths, specular paths) as a fourth item when with_beta.  demit holds
     the diffraction and direct paths; given the triangle normals tri_nrm [T][3], it also holds the
-    specular paths through their hit points (ray directions and triangle chains frozen)."""
+    specular paths through their hit points (ray directions and triangle chains frozen).  Records carrying
+    'mask' (the per-microphone receiver test) reach only the microphones whose bit is set."""
     P_ = params.P
     N, B = rec["tri"].shape
     dirs, tm = _c(dirs, np.float32), _c(tri_mat, np.int32)
@@ -315,7 +316,8 @@ def spectra_grad(params, rec, dirs, tri_mat, G, cand_tri=None, cand_p=None, cand
     dspec = np.zeros(3, np.float64) if nrm is not None else None
     rc = lib().ora_spectra_grad(C.byref(P_), N, B, _p(rec["tri"]), _p(rec["p"]), _p(rec["d"]), _p(rec["r"]),
                                 _p(rec["los"]), _p(dirs), _p(tm), K, _p(ct), _p(cp), _p(ck), _p(dv), _p(Gr),
-                                _p(dk), _p(dmic), _p(demit), _p(dbeta), _p(nrm), _p(dspec))
+                                _p(dk), _p(dmic), _p(demit), _p(dbeta), _p(nrm), _p(dspec),
+                                _p(_c(rec.get("mask"), np.uint64)))
     if rc != 0:
         raise ValueError("oracle gradient needs omni emitter and microphones")
     if dspec is not None:

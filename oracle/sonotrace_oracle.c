@@ -1110,6 +1110,8 @@ ORA_API int ora_spectra(const OraSpecParams* P, int64_t N, int32_t B, const int3
  *   dmic[M][3]: microphone positions (all three components; omni microphones).
  *   demit[3]:   emitter position through the diffraction and direct paths (omni emitter);
  *               the specular paths' dependence on the emitter (through the whole chain) is not included.
+ * rec_mask (NULL or [N][B]): with the per-microphone receiver test a record reaches microphone m only
+ * when bit m is set, as in ora_spectra; the terms it does not reach have no gradient.
  * Directivity tables must be absent for the position gradients (returns -1 otherwise).
  */
 ORA_API int ora_spectra_grad(const OraSpecParams* P, int64_t N, int32_t B, const int32_t* rec_tri, const float* rec_p,
@@ -1117,7 +1119,7 @@ ORA_API int ora_spectra_grad(const OraSpecParams* P, int64_t N, int32_t B, const
                              const int32_t* tri_mat, int64_t K, const int32_t* cand_tri, const float* cand_p,
                              const uint8_t* cand_keep, const uint8_t* direct_vis, const double* G,
                              double* dk, double* dmic, double* demit, double* dbeta, const float* tri_nrm,
-                             double* demit_spec) {
+                             double* demit_spec, const uint64_t* rec_mask) {
     if (P->emit_table || P->mic_tables) return -1;
     int F = P->F, M = P->M;
     memset(dk, 0, sizeof(double) * (size_t)P->n_mat * P->n_bands);
@@ -1135,6 +1137,7 @@ ORA_API int ora_spectra_grad(const OraSpecParams* P, int64_t N, int32_t B, const
                 if (rec_tri[id] < 0) break;
                 chain[j] = tri_mat[rec_tri[id]];
                 if (!rec_los[id]) continue;
+                if (rec_mask && !((rec_mask[id] >> m) & 1u)) continue;  /* per-microphone receiver test */
                 double Pp[3] = {rec_p[3 * id], rec_p[3 * id + 1], rec_p[3 * id + 2]};
                 double dr[3] = {rec_d[3 * id], rec_d[3 * id + 1], rec_d[3 * id + 2]};
                 double v[3] = {mf[0] - Pp[0], mf[1] - Pp[1], mf[2] - Pp[2]};

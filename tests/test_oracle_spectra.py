@@ -180,6 +180,86 @@ def test_gradient_matches_central_differences():
         assert abs(fd - an) <= 1e-6 * np.abs(terms).sum(), (fd, an)
 
 
+def test_gradient_with_microphone_masks_matches_central_differences():
+    """The per-microphone receiver test: records with random microphone masks (each record reaches only
+    the microphones whose bit is set, in the spectra and in the gradient).  The reflection, microphone and
+    lobe-width gradients against central differences of the masked spectra, the emitter gradient through
+    the hit points against those of the masked frozen-chain restatement, Richardson extrapolated; a
+    gradient that ignored the masks would differ from them."""
+    wl, out, _, _, _ = _grad_problem()
+    rec = dict(out["rec"])
+    M = len(wl.mics)
+    rng = np.random.default_rng(406)
+    hit_vis = (rec["tri"] >= 0) & (rec["los"] != 0)
+    mask = np.where(hit_vis, rng.integers(0, 1 << M, rec["tri"].shape, dtype=np.uint64), 0).astype(np.uint64)
+    rec["mask"], rec["los"] = mask, (mask != 0).astype(np.uint8)
+    full = np.uint64((1 << M) - 1)
+    assert np.sum((mask != 0) & (mask != full)) > 100
+    nrm = oracle.tri_normals(wl.verts, wl.tris)
+    q = lambda x, e: np.round(np.asarray(x, np.float64) * 2.0 ** e) / 2.0 ** e
+    k0, m0, s0, b0 = q(wl.k_band, 12), q(wl.mics, 12), q(wl.emitter, 12), q(wl.beta_band, 14)
+
+    def spectra_at(k, m, s, b):
+        for a in (k, m, s, b):
+            assert np.array_equal(a.astype(np.float32).astype(np.float64), a)
+        p = oracle.spec_params(wl, mics=m.astype(np.float32), k_band=k.astype(np.float32),
+                               emitter=s.astype(np.float32), beta_band=b.astype(np.float32))
+        return oracle.spectra(p, rec, wl.dirs, wl.tri_mat)
+
+    # the masks change the spectra (a mask-blind sum would differ)
+    full_rec = dict(rec, mask=np.where(mask != 0, full, np.uint64(0)).astype(np.uint64))
+    p0 = oracle.spec_params(wl)
+    assert not np.allclose(oracle.spectra(p0, rec, wl.dirs, wl.tri_mat)[0],
+                           oracle.spectra(p0, full_rec, wl.dirs, wl.tri_mat)[0])
+    S0 = spectra_at(k0, m0, s0, b0)
+    St = spectra_at(q(k0 * 0.9, 12), m0 + 2.0 ** -7, s0 - 2.0 ** -7, q(b0 * 1.2, 14))
+    G = 2.0 * (S0 - St)
+    p = oracle.spec_params(wl, mics=m0.astype(np.float32), k_band=k0.astype(np.float32),
+                           emitter=s0.astype(np.float32), beta_band=b0.astype(np.float32))
+    dk, dmic, _, dbeta = oracle.spectra_grad(p, rec, wl.dirs, wl.tri_mat, G, with_beta=True)
+    assert np.abs(dk).max() > 0 and np.abs(dmic).max() > 0 and np.abs(dbeta).max() > 0
+
+    def loss(k, m, s, b):
+        return float(np.sum(np.abs(spectra_at(k, m, s, b) - St) ** 2))
+
+    for _ in range(6):
+        vk = q(rng.uniform(-1, 1, k0.shape), 5)
+        vm = q(rng.uniform(-1, 1, m0.shape), 5)
+        vb = q(rng.uniform(-1, 1, b0.shape), 5)
+
+        def D(h_k, h_x, h_b):
+            return (loss(k0 + h_k * vk, m0 + h_x * vm, s0, b0 + h_b * vb)
+                    - loss(k0 - h_k * vk, m0 - h_x * vm, s0, b0 - h_b * vb)) / 2.0
+
+        hk, hx, hb = 2.0 ** -10, 2.0 ** -16, 2.0 ** -12
+        fd = (8.0 * D(hk / 2, hx / 2, hb / 2) - D(hk, hx, hb)) / 3.0
+        terms = np.concatenate([(dk * hk * vk).ravel(), (dmic * hx * vm).ravel(), (dbeta * hb * vb).ravel()])
+        assert abs(fd - terms.sum()) <= 1e-6 * np.abs(terms).sum(), (fd, terms.sum())
+    # the emitter through the hit points: central differences of the masked frozen-chain restatement, which
+    # at the stored emitter reproduces the oracle's masked spectra
+    se = wl.emitter.astype(np.float64)
+    spec = lambda s_: _frozen_chain_spectra(wl, rec, s_, s_ref=se)
+    Se = spec(se)
+    Sref = oracle.spectra(oracle.spec_params(wl), rec, wl.dirs, wl.tri_mat)[0]
+    assert np.linalg.norm(Se - Sref) <= 1e-9 * np.linalg.norm(Sref)
+    Ste = spec(se + np.array([0.01, -0.02, 0.015]))
+    Ge = np.zeros((3,) + Se.shape, np.complex128)
+    Ge[0] = 2.0 * (Se - Ste)
+    _, _, demit_s = oracle.spectra_grad(oracle.spec_params(wl), rec, wl.dirs, wl.tri_mat, Ge, tri_nrm=nrm)
+    assert np.abs(demit_s).max() > 0
+    for _ in range(3):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+
+        def Ds(h):
+            return (np.sum(np.abs(spec(se + h * v) - Ste) ** 2) - np.sum(np.abs(spec(se - h * v) - Ste) ** 2)) / 2.0
+
+        h = 1e-4
+        fd = (8.0 * Ds(h / 2) - Ds(h)) / 3.0
+        an = float(demit_s @ (h * v))
+        assert abs(fd - an) <= 1e-4 * np.abs(demit_s * h * v).sum() + 1e-12, (fd, an)
+
+
 def test_beta_gradient_matches_central_differences():
     """Lobe-width gradient (specular paths, the last hit's material) vs central differences with
     Richardson extrapolation; beta values and steps exactly representable in float32."""
@@ -270,6 +350,8 @@ def _frozen_chain_spectra(wl, rec, s, a1_per_khz=0.033, c=343.0, s_ref=None):
                 Pu = rec["p"][i, j].astype(np.float64) + (Pq - Pb)
                 ru = float(rec["r"][i, j]) + (r - rb)
             for m in range(M):
+                if "mask" in rec and not (int(rec["mask"][i, j]) >> m) & 1:
+                    continue  # per-microphone receiver test: microphone m does not see this hit
                 v = wl.mics[m].astype(np.float64) - Pu
                 dist = np.linalg.norm(v)
                 u = v / dist
