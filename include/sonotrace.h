@@ -89,8 +89,9 @@ typedef struct st_sim_params {
     uint64_t seed;              /* Philox key of the diffraction samples (default 0) */
     uint32_t pose_index;        /* Philox counter word distinguishing poses (default 0) */
     int32_t los_mode;           /* ST_LOS_* (default ST_LOS_REFERENCE); ST_LOS_PER_MIC needs M <= 64 and
-                                   N * B * M < 2^32, single-pose st_simulate only, and no st_backward after
-                                   it; st_accumulate_specular_noalloc takes the caller's records and ignores it */
+                                   N * B * M < 2^32 and single-pose st_simulate only (st_backward then
+                                   follows the masks); st_accumulate_specular_noalloc takes the caller's
+                                   records and ignores it */
 } st_sim_params;
 
 /* Optional statistics of one simulate call (filled after the stream is synchronised). */
@@ -216,6 +217,7 @@ st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
  *                            through their hit points (ray directions and triangle chains frozen:
  *                            hit q moves along d_q with the line from hit q-1, dP_q/dP_{q-1} =
  *                            I - d_q n_q^T / (n_q . d_q)).
+ * After a simulate with ST_LOS_PER_MIC each specular path reaches only the microphones of its mask here too.
  * Needs omni receivers; position gradients also need an omni emitter (ST_ERR_ARG otherwise).  scene must be the one of the
  * last simulate, unchanged since (ST_ERR_STATE otherwise).  Deterministic: every sum runs in a fixed
  * order.  Stream-ordered; allocates reduction buffers on first use. */

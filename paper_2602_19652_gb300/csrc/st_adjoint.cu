@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         }
         cp_async_wait_all();
         __syncthreads();
-        produce<KT, KIND, 1>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, j.s);
+        produce<KT, KIND, 1>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, j.s, t0 * PT);
         __syncthreads();
     }
     for (int64_t tile = t0; tile < t1; ++tile) {
@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         }
         if (tile + 1 < t1) {
             const int nb = (int)((tile + 1 - t0) % 3);
-            produce<KT, KIND, 1>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, j.s);
+            produce<KT, KIND, 1>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, j.s,
+                                 (tile + 1) * PT);
         }
         for (int p = 0; p < PT; ++p) {
             const ulonglong2 z0 = C.za[((size_t)p * NS + s) * TP + tp];

@@ -1060,8 +1060,6 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
     if ((grad_mic || grad_emitter) && c->n_theta > 0)
         return fail(c, ST_ERR_ARG, "backward: position gradients need an omni emitter");
     if (c->mic_nb > 0) return fail(c, ST_ERR_ARG, "backward: needs omni receivers");
-    if (c->last_params.los_mode != ST_LOS_REFERENCE)
-        return fail(c, ST_ERR_ARG, "backward: needs a simulate with the reference-point receiver test");
     enter(c);
     cudaStream_t s = c->stream;
     const st_sim_params& p = c->last_params;
@@ -1072,6 +1070,9 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
     const float2* G = static_cast<const float2*>(grad_spectra);
     const bool want_pos = grad_mic || grad_emitter;
     uint32_t* cnt = ptr<uint32_t>(c->counts);
+    // per-microphone receiver test: the specular path list carries each path's microphone mask (the
+    // producers give a microphone that does not see the path a zero anchor, so its terms add nothing)
+    const uint64_t* spec_mask = p.los_mode == ST_LOS_PER_MIC ? ptr<uint64_t>(c->paths.mask) : nullptr;
 
     const double l10 = log(10.0) / 20.0;
     AccumArgs aa{};
@@ -1145,6 +1146,7 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         x.d_count = cnt + 2;
         x.n_chunks = chunks;
         set_paths(x, c->paths);
+        x.mask = spec_mask;
         if (grad_emitter) {
             // the emitter moves the hit points: chain jacobians of the visible records, in the order of
             // the path list (the compaction of the last simulate, repeated)
@@ -1188,6 +1190,7 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         x.d_count = cnt + 2;
         x.n_chunks = chunks;
         set_paths(x, c->paths);
+        x.mask = spec_mask;
         for (int bt = 0; bt < (S.n_mat + 3) / 4; ++bt) {
             AdjointArgs jj = ja;
             jj.G = G;
