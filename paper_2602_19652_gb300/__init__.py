@@ -216,6 +216,43 @@ class Context:
                                              None if tune is None else C.byref(tune)))
         return [j.out for j in jobs]
 
+    def simulate_emitters(self, scene: "Scene", emitters, emitter_quats, dirs, mics, n_bins: int, f_lo: float,
+                          f_hi: float, max_bounces: int, params: SimParams | None = None, pose_index: int = 0,
+                          fov_half: float = math.pi) -> torch.Tensor:
+        """Several emitters (positions [S][3], orientations [S][4]) sending the same ray set into one scene
+        towards one receiver array, in one batched call: complex64 [S][3][M][F], emitter s's specular,
+        diffraction and direct spectra (the sum over s is the array's spectra when all emitters send the
+        same call).  Every emitter filters the same diffraction samples (one pose index).  The jobs share
+        the ray and microphone tensors and are kept, so a later call with the same sizes replays the
+        recorded graph with the new emitter poses.  Omni emitters and receivers, as in simulate_batch."""
+        dev = f"cuda:{self.device}"
+        E = np.ascontiguousarray(emitters, np.float32).reshape(-1, 3)
+        Q = np.ascontiguousarray(emitter_quats, np.float32).reshape(-1, 4)
+        if len(E) != len(Q) or len(E) == 0:
+            raise ValueError("simulate_emitters: one orientation per emitter, at least one emitter")
+        src_d = torch.as_tensor(dirs, dtype=torch.float32)
+        src_m = torch.as_tensor(mics, dtype=torch.float32)
+        key = (scene.h.value, len(E), tuple(src_d.shape), tuple(src_m.shape), int(n_bins), float(f_lo),
+               float(f_hi), int(max_bounces), int(pose_index), float(np.float32(fov_half)))
+        with torch.cuda.stream(self.stream):  # the copies are ordered before the library's work
+            if getattr(self, "_emit_key", None) != key:
+                # the context's own copies of the rays and microphones, shared by the jobs
+                d = torch.empty(tuple(src_d.shape), dtype=torch.float32, device=dev)
+                m = torch.empty(tuple(src_m.shape), dtype=torch.float32, device=dev)
+                d.copy_(src_d)
+                m.copy_(src_m)
+                self._emit_jobs = [BatchJob(scene, E[i], Q[i], d, m, n_bins, f_lo, f_hi, max_bounces,
+                                            pose_index=pose_index, fov_half=fov_half, device=self.device)
+                                   for i in range(len(E))]
+                self._emit_key, self._emit_refs = key, (d, m)
+            else:
+                d, m = self._emit_refs
+                d.copy_(src_d)
+                m.copy_(src_m)
+                for i, j in enumerate(self._emit_jobs):
+                    j.set_pose(emitter=E[i], emitter_quat=Q[i])
+            return torch.stack(self.simulate_batch(self._emit_jobs, params))
+
     def autotune(self, job: "BatchJob", params: SimParams | None = None) -> Tune:
         t = Tune()
         self._check(self.L.st_autotune(self.h, C.byref(job.job), None if params is None else C.byref(params),
@@ -232,10 +269,16 @@ class BatchJob:
                  max_bounces: int, pose_index: int = 0, fov_half: float = math.pi, device: int = 0):
         dev = f"cuda:{device}"
         self.scene = scene
-        self.emitter = torch.as_tensor(np.asarray(emitter, np.float32), device=dev).contiguous()
-        self.emitter_quat = torch.as_tensor(np.asarray(emitter_quat, np.float32), device=dev).contiguous()
-        self.dirs = torch.as_tensor(np.asarray(dirs, np.float32), device=dev).contiguous()
-        self.mics = torch.as_tensor(np.asarray(mics, np.float32), device=dev).contiguous()
+
+        def f32(x):  # a float32 device tensor on this device is used as it is (jobs may share rays, mics)
+            if isinstance(x, torch.Tensor):
+                return x.to(device=dev, dtype=torch.float32).contiguous()
+            return torch.as_tensor(np.asarray(x, np.float32), device=dev).contiguous()
+
+        self.emitter = f32(emitter)
+        self.emitter_quat = f32(emitter_quat)
+        self.dirs = f32(dirs)
+        self.mics = f32(mics)
         self.N, self.M, self.F = int(self.dirs.shape[0]), int(self.mics.shape[0]), int(n_bins)
         self.out = torch.empty((3, self.M, self.F), dtype=torch.complex64, device=dev)
         vp = lambda t: C.c_void_p(t.data_ptr())
