@@ -187,6 +187,31 @@ class Scene:
         return bool(lib().ora_visible(self.h, _p(o), _p(g), exclude, t_min, eps))
 
 
+def expand_instances(protos, inst_proto, inst_xform):
+    """World triangles of a scene given as instances of shared meshes (Sec. III-B registers objects; a
+    forest repeats plant meshes): instance i, in order, is prototype inst_proto[i] = (verts, tris with
+    local indices, tri_mat) under x -> A x + b, inst_xform[i] = [A | b] (3 x 4).  Each world coordinate
+    is ((A_r0 x + A_r1 y) + A_r2 z) + b_r with every product and sum rounded to float32 (numpy float32
+    arithmetic), instance i's vertices and triangles follow instance i-1's, and instance i is object i.
+    Returns (verts f32 [V][3], tris i32 [T][3], tri_mat i32 [T], tri_obj i32 [T])."""
+    V, T, Mt, O = [], [], [], []
+    base = 0
+    for i, (q, X) in enumerate(zip(np.asarray(inst_proto), np.asarray(inst_xform, np.float32).reshape(-1, 3, 4))):
+        pv, pt, pm = protos[int(q)]
+        pv = np.asarray(pv, np.float32).reshape(-1, 3)
+        x, y, z = pv[:, 0], pv[:, 1], pv[:, 2]
+        w = np.empty_like(pv)
+        for r in range(3):
+            w[:, r] = ((X[r, 0] * x + X[r, 1] * y) + X[r, 2] * z) + X[r, 3]
+        V.append(w)
+        T.append(np.asarray(pt, np.int64).reshape(-1, 3) + base)
+        Mt.append(np.asarray(pm, np.int32).reshape(-1))
+        O.append(np.full(len(Mt[-1]), i, np.int32))
+        base += len(pv)
+    return (np.concatenate(V).astype(np.float32), np.concatenate(T).astype(np.int32), np.concatenate(Mt),
+            np.concatenate(O))
+
+
 def mic_centroid(mics):
     m = _c(mics, np.float32)
     R = np.zeros(3, dtype=np.float32)

@@ -353,6 +353,74 @@ def vegetation(seed: int = 303, target_tris: int = 2_000_000, n_rays: int = 4_00
         mic_quats=np.tile(_identity_quat(), (2, 1)))
 
 
+@dataclass
+class InstancedScene:
+    """Shared meshes and their instances (the scene's world triangles are made by the code under test)."""
+    protos: list                 # [(verts f32 [v][3], tris i32 [t][3] local indices, tri_mat i32 [t]), ...]
+    inst_proto: np.ndarray       # [n_inst] i32 prototype of each instance
+    inst_xform: np.ndarray       # [n_inst][3][4] f32 row-major [A | b]: x -> A x + b
+    base: Workload               # sensor, materials, rays, grid; its own geometry arrays are empty
+
+
+def _plant_protos():
+    """Plant meshes with their base at the origin: a trunk (closed cylinder) under an icosphere crown, a
+    bush (icosphere resting on the ground), a rock (box)."""
+    tv, tf = cylinder(0.08, 2.0, 12)
+    cv, cf = icosphere(2)
+    cv = cv * 0.7 + np.array([0.0, 0.0, 2.5])
+    tree_v = np.concatenate([tv, cv])
+    tree_f = np.concatenate([tf, cf + len(tv)])
+    tree_m = np.concatenate([np.full(len(tf), 1), np.full(len(cf), 2)])
+    bv, bf = icosphere(3)
+    bv = bv * 0.45 + np.array([0.0, 0.0, 0.45])
+    rv, rf, _ = _box_tris((-0.3, -0.2, 0.0), (0.3, 0.2, 0.25))
+    return [(tree_v.astype(F32), tree_f.astype(np.int32), tree_m.astype(np.int32)),
+            (bv.astype(F32), bf.astype(np.int32), np.full(len(bf), 2, np.int32)),
+            (rv.astype(F32), rf.astype(np.int32), np.full(len(rf), 3, np.int32))]
+
+
+def instanced_forest(seed: int = 606, n_inst: int = 400, n_rays: int = 100_000, bounces: int = 3, n_mics: int = 8,
+                     n_bins: int = 128, diffraction: bool = True) -> InstancedScene:
+    """A forest floor as instances of a few shared meshes (the paper's forest repeats plant models):
+    prototype 0 a 20 x 20 m ground quad (one instance, identity), prototypes 1-3 a tree, a bush and a
+    rock placed uniformly in the area outside a 1.5 m clearing around the sensor, each rotated about the
+    vertical by a uniform angle and scaled uniformly by 0.6-1.4 (rocks also tilted by up to 30 degrees
+    about a horizontal axis); 4 materials; a 12 cm disc array of n_mics microphones with an omni emitter
+    1 m above the centre."""
+    rng = np.random.default_rng(seed)
+    ground = (np.array([[0, 0, 0], [20, 0, 0], [20, 20, 0], [0, 20, 0]], F32), np.array([[0, 1, 2], [0, 2, 3]], np.int32),
+              np.zeros(2, np.int32))
+    protos = [ground] + _plant_protos()
+    sensor = np.array([10.0, 10.0, 1.0])
+    xf = [np.concatenate([np.eye(3), np.zeros((3, 1))], 1)]
+    kind = [0]
+    while len(kind) < n_inst:
+        c = np.array([rng.uniform(0.5, 19.5), rng.uniform(0.5, 19.5), 0.0])
+        if np.linalg.norm((c - sensor)[:2]) < 1.5:
+            continue
+        q = int(rng.integers(1, 4))
+        a = rng.uniform(0, 2 * math.pi)
+        Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+        if q == 3:
+            t = rng.uniform(0, math.radians(30))
+            Rz = Rz @ np.array([[1, 0, 0], [0, math.cos(t), -math.sin(t)], [0, math.sin(t), math.cos(t)]])
+        xf.append(np.concatenate([Rz * rng.uniform(0.6, 1.4), c[:, None]], 1))
+        kind.append(q)
+    n_bands = 16
+    band = np.linspace(20e3, 80e3, n_bands).astype(F32)
+    empty = np.zeros((0, 3), F32)
+    base = Workload(
+        name="instanced_forest", verts=empty, tris=np.zeros((0, 3), np.int32), tri_mat=np.zeros(0, np.int32),
+        tri_obj=np.zeros(0, np.int32), band_hz=band, k_band=smooth_band_curves(rng, 4, n_bands, 0.3, 0.95),
+        beta_band=np.deg2rad(smooth_band_curves(rng, 4, n_bands, 5.0, 30.0)).astype(F32),
+        diff_band=smooth_band_curves(rng, 4, n_bands, 0.02, 0.08),
+        emitter=(sensor + np.array([0.01, 0.0, 0.0])).astype(F32), emitter_quat=_identity_quat(),
+        dirs=fibonacci_directions(n_rays), mics=planar_disc_array(rng, n_mics, 0.06, sensor, 0), n_bins=n_bins,
+        f_lo=20e3, f_hi=80e3, bounces=bounces, max_distance=60.0, diffraction=diffraction)
+    return InstancedScene(protos=protos, inst_proto=np.array(kind, np.int32),
+                          inst_xform=np.array(xf, np.float64).astype(F32), base=base)
+
+
 def gradient_problem(seed: int = 404, n_rays: int = 10_000) -> Workload:
     """Shoebox geometry with four wall materials, a 32-mic disc array and 128 bins
     (the differentiation workload)."""
