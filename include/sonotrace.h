@@ -158,6 +158,33 @@ st_status st_scene_precompute(st_scene* scene, const st_curv_params* params);
  * re-record.  A non-finite vertex returns ST_ERR_MESH and leaves the scene needing a precompute. */
 #define ST_REFIT_KEEP_CURVATURE 1
 st_status st_scene_update_vertices(st_scene* scene, const float* verts, int32_t mem, int32_t flags);
+/* Instanced scene (Sec. III-B registers objects; a forest repeats a few plant meshes many times).
+ * n_proto shared meshes, concatenated: prototype p owns vertices proto_vert_offset[p] ..
+ * proto_vert_offset[p+1] of proto_verts [.][3] and triangles proto_tri_offset[p] .. proto_tri_offset[p+1]
+ * of proto_tris [.][3] (vertex indices local to the prototype) with materials proto_tri_material [.];
+ * offsets [n_proto + 1], starting at 0 and ascending.  n_inst instances: instance i is prototype
+ * inst_proto[i] under the affine map x -> A x + b, inst_xform [n_inst][12] the row-major 3 x 4 matrices
+ * [A | b].  The world scene is expanded on the device: instance i's vertices and triangles follow
+ * instance i-1's, each world coordinate ((A_r0 x + A_r1 y) + A_r2 z) + b_r rounded to float32 in that
+ * order, and instance i is mesh (object) i for the diffraction CDFs.  All pointers are host memory,
+ * copied.  Then as a loaded scene: set materials, precompute.  ST_ERR_ARG: a null pointer, no
+ * prototype, 0 or >= 2^24 instances, offsets not ascending from 0, more than 2^31 world vertices or 2^28
+ * world triangles, none at all; ST_ERR_MESH: a local index or prototype id out of range, a non-finite
+ * vertex or transform. */
+st_status st_scene_load_instances(st_ctx* ctx, int32_t n_proto, const int64_t* proto_vert_offset,
+                                  const float* proto_verts, const int64_t* proto_tri_offset, const int32_t* proto_tris,
+                                  const int32_t* proto_tri_material, int32_t n_inst, const int32_t* inst_proto,
+                                  const float* inst_xform, st_scene** out);
+/* Moves the instances of a precomputed instanced scene: new transforms inst_xform [n_inst][12] (host
+ * or device per mem), the world vertices expanded again on the device, then the refit of
+ * st_scene_update_vertices with the same flags (ST_REFIT_KEEP_CURVATURE for rotations and
+ * translations).  ST_ERR_STATE for a scene not loaded by st_scene_load_instances or not precomputed;
+ * ST_ERR_MESH when a world vertex is not finite (the scene then needs a precompute). */
+st_status st_scene_set_instance_transforms(st_scene* scene, const float* inst_xform, int32_t mem, int32_t flags);
+/* The scene's triangles as loaded or expanded: counts (either may be NULL), then verts [n_verts][3],
+ * tris [n_tris][3], tri_material [n_tris], tri_object [n_tris] (any may be NULL).  Synchronises. */
+st_status st_scene_get_geometry(st_scene* scene, int64_t* n_verts, int64_t* n_tris, float* verts, int32_t* tris,
+                                int32_t* tri_material, int32_t* tri_object, int32_t mem);
 /* Copy per-vertex G [n_verts], per-triangle C [n_tris] and the diffraction sample count per
  * mesh out (any may be NULL).  n_samples has one entry per mesh id up to max(tri_object). */
 st_status st_scene_get_curvature(st_scene* scene, float* G, float* C, int64_t* n_samples, int32_t mem);

@@ -297,8 +297,11 @@ class BatchJob:
 class Scene:
     """A triangle scene owned by a Context: load, set materials, precompute (BVH, curvature, CDFs)."""
 
-    def __init__(self, ctx: Context, verts, tris, tri_mat, tri_obj):
+    def __init__(self, ctx: Context, verts, tris, tri_mat, tri_obj, _handle=None):
         self.ctx = ctx
+        if _handle is not None:  # made by from_instances
+            self.h = _handle
+            return
         v = np.ascontiguousarray(verts, np.float32)
         t = np.ascontiguousarray(tris, np.int32)
         m = np.ascontiguousarray(tri_mat, np.int32)
@@ -328,6 +331,53 @@ class Scene:
         assert v.shape == (self.n_verts, 3)
         self.ctx._check(self.ctx.L.st_scene_update_vertices(self.h, v.ctypes.data_as(C.c_void_p), ST_MEM_HOST,
                                                             _lib.ST_REFIT_KEEP_CURVATURE if keep_curvature else 0))
+
+    @classmethod
+    def from_instances(cls, ctx: Context, protos, inst_proto, inst_xform) -> "Scene":
+        """A scene of instances of shared meshes: protos = [(verts [v][3], tris [t][3] local indices,
+        tri_mat [t]), ...], inst_proto [n_inst] prototype ids, inst_xform [n_inst][3][4] row-major [A | b]
+        (x -> A x + b).  Expanded on the device; instance i is object i."""
+        pv = np.ascontiguousarray(np.concatenate([np.asarray(p[0], np.float32).reshape(-1, 3) for p in protos]))
+        pt = np.ascontiguousarray(np.concatenate([np.asarray(p[1], np.int32).reshape(-1, 3) for p in protos]))
+        pm = np.ascontiguousarray(np.concatenate([np.asarray(p[2], np.int32).reshape(-1) for p in protos]))
+        voff = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(np.asarray(p[0]).reshape(-1, 3)) for p in protos])]),
+                                    np.int64)
+        toff = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(np.asarray(p[1]).reshape(-1, 3)) for p in protos])]),
+                                    np.int64)
+        ip = np.ascontiguousarray(inst_proto, np.int32).reshape(-1)
+        xf = np.ascontiguousarray(inst_xform, np.float32).reshape(-1, 12)
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+        h = C.c_void_p()
+        ctx._check(ctx.L.st_scene_load_instances(ctx.h, len(protos), cp(voff), cp(pv), cp(toff), cp(pt), cp(pm), len(ip),
+                                                 cp(ip), cp(xf), C.byref(h)))
+        sc = cls(ctx, None, None, None, None, _handle=h)
+        nv, nt = C.c_int64(0), C.c_int64(0)
+        ctx._check(ctx.L.st_scene_get_geometry(h, C.byref(nv), C.byref(nt), None, None, None, None, ST_MEM_HOST))
+        sc.n_verts, sc.n_tris, sc.n_obj, sc.n_inst = nv.value, nt.value, len(ip), len(ip)
+        return sc
+
+    def set_instance_transforms(self, inst_xform, keep_curvature: bool = False):
+        """New instance transforms [n_inst][3][4] (numpy or a device tensor), then a refit (see the C header)."""
+        if isinstance(inst_xform, torch.Tensor):
+            x = inst_xform.to(dtype=torch.float32).contiguous()
+            assert x.numel() == 12 * self.n_inst and x.is_cuda
+            ptr_, mem = C.c_void_p(x.data_ptr()), ST_MEM_DEVICE
+        else:
+            x = np.ascontiguousarray(inst_xform, np.float32)
+            assert x.size == 12 * self.n_inst
+            ptr_, mem = x.ctypes.data_as(C.c_void_p), ST_MEM_HOST
+        self.ctx._check(self.ctx.L.st_scene_set_instance_transforms(
+            self.h, ptr_, mem, _lib.ST_REFIT_KEEP_CURVATURE if keep_curvature else 0))
+
+    def geometry(self):
+        """(verts [V][3], tris [T][3], tri_mat [T], tri_obj [T]) of the scene as loaded or expanded."""
+        v = np.empty((self.n_verts, 3), np.float32)
+        t = np.empty((self.n_tris, 3), np.int32)
+        m = np.empty(self.n_tris, np.int32)
+        o = np.empty(self.n_tris, np.int32)
+        cp = lambda a: a.ctypes.data_as(C.c_void_p)
+        self.ctx._check(self.ctx.L.st_scene_get_geometry(self.h, None, None, cp(v), cp(t), cp(m), cp(o), ST_MEM_HOST))
+        return v, t, m, o
 
     def curvature(self):
         G = np.empty(self.n_verts, np.float32)

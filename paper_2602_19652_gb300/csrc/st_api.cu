@@ -11,7 +11,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "st_accum_dev.cuh"
@@ -141,6 +143,8 @@ struct st_scene {
     bool has_materials = false;
     uint64_t version = 0;
     st::CurvParamsDev cp{};  // parameters of the last precompute (reused by refits)
+    bool instanced = false;  // loaded by st_scene_load_instances
+    st::InstanceDev inst;
 };
 
 // Entry of every call on a context: select its device and drop a stale, non-sticky error left by
@@ -155,6 +159,9 @@ static void scene_free(st_scene* sc) {
     for (DevBuf* b : {&S.verts, &S.tris, &S.tri_mat, &S.tri_obj, &S.nrm, &S.nodes, &S.tri_v, &S.G, &S.C, &S.mesh_tris,
                       &S.mesh_off, &S.cdf, &S.n_samples, &S.sample_off, &S.bvh_child, &S.bvh_range, &S.bvh_par_i,
                       &S.bvh_par_l, &S.bvh_perm, &S.bvh_wflag, &S.bvh_widx})
+        st::release(*b);
+    st::InstanceDev& I = sc->inst;
+    for (DevBuf* b : {&I.pverts, &I.ptris, &I.pmat, &I.pvoff, &I.ptoff, &I.iproto, &I.vbase, &I.tbase, &I.xform})
         st::release(*b);
     delete sc;
 }
@@ -391,6 +398,20 @@ st_status st_scene_precompute(st_scene* sc, const st_curv_params* params) {
     return ST_OK;
 }
 
+// Refit of a precomputed scene whose vertex buffer holds new positions (same triangles).
+static st_status refit_scene(st_scene* sc, int32_t flags, const char* what) {
+    st_ctx* c = sc->ctx;
+    bool mesh_err = false;
+    std::string msg;
+    cudaError_t e = scene_build(sc->S, sc->cp, c->stream, &mesh_err, &msg, true,
+                                (flags & ST_REFIT_KEEP_CURVATURE) != 0);
+    sc->version = g_scene_version++;
+    if (e != cudaSuccess || mesh_err) sc->S.built = false;  // precompute again before the next simulate
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    if (mesh_err) return fail(c, ST_ERR_MESH, std::string(what) + ": " + msg);
+    return ST_OK;
+}
+
 st_status st_scene_update_vertices(st_scene* sc, const float* verts, int32_t mem, int32_t flags) {
     if (!sc) return ST_ERR_ARG;
     st_ctx* c = sc->ctx;
@@ -400,14 +421,133 @@ st_status st_scene_update_vertices(st_scene* sc, const float* verts, int32_t mem
     enter(c);
     CKC(c, cudaMemcpyAsync(sc->S.verts.p, verts, (size_t)sc->S.n_verts * 12, kind_in(mem), c->stream),
         "scene_update_vertices copy");
-    bool mesh_err = false;
-    std::string msg;
-    cudaError_t e = scene_build(sc->S, sc->cp, c->stream, &mesh_err, &msg, true,
-                                (flags & ST_REFIT_KEEP_CURVATURE) != 0);
+    return refit_scene(sc, flags, "scene_update_vertices");
+}
+
+st_status st_scene_load_instances(st_ctx* c, int32_t n_proto, const int64_t* proto_vert_offset,
+                                  const float* proto_verts, const int64_t* proto_tri_offset, const int32_t* proto_tris,
+                                  const int32_t* proto_tri_material, int32_t n_inst, const int32_t* inst_proto,
+                                  const float* inst_xform, st_scene** out) {
+    if (!c || !out) return ST_ERR_ARG;
+    *out = nullptr;
+    if (n_proto < 1 || n_inst < 1 || n_inst >= (1 << 24) || !proto_vert_offset || !proto_verts || !proto_tri_offset ||
+        !proto_tris || !proto_tri_material || !inst_proto || !inst_xform)
+        return fail(c, ST_ERR_ARG, "scene_load_instances: null pointer, no prototype, or 1..2^24 instances");
+    if (proto_vert_offset[0] != 0 || proto_tri_offset[0] != 0)
+        return fail(c, ST_ERR_ARG, "scene_load_instances: offsets must start at 0");
+    for (int32_t q = 0; q < n_proto; ++q)
+        if (proto_vert_offset[q + 1] < proto_vert_offset[q] || proto_tri_offset[q + 1] < proto_tri_offset[q] ||
+            proto_vert_offset[q + 1] >= (1ll << 31) || proto_tri_offset[q + 1] >= (1ll << 28))
+            return fail(c, ST_ERR_ARG, "scene_load_instances: offsets must ascend (< 2^31 vertices, < 2^28 triangles)");
+    const int64_t pv = proto_vert_offset[n_proto], pt = proto_tri_offset[n_proto];
+    // prototype meshes: local indices in range, finite vertices
+    for (int32_t q = 0; q < n_proto; ++q) {
+        const int64_t nvq = proto_vert_offset[q + 1] - proto_vert_offset[q];
+        for (int64_t t = proto_tri_offset[q]; t < proto_tri_offset[q + 1]; ++t)
+            for (int k = 0; k < 3; ++k)
+                if (proto_tris[3 * t + k] < 0 || proto_tris[3 * t + k] >= nvq)
+                    return fail(c, ST_ERR_MESH, "scene_load_instances: prototype vertex index out of range");
+    }
+    for (int64_t e = 0; e < 3 * pv; ++e)
+        if (!std::isfinite(proto_verts[e])) return fail(c, ST_ERR_MESH, "scene_load_instances: non-finite vertex");
+    // instance table: world bases
+    std::vector<int64_t> vbase(n_inst + 1), tbase(n_inst + 1);
+    vbase[0] = tbase[0] = 0;
+    for (int32_t i = 0; i < n_inst; ++i) {
+        const int32_t q = inst_proto[i];
+        if (q < 0 || q >= n_proto) return fail(c, ST_ERR_MESH, "scene_load_instances: prototype id out of range");
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(inst_xform[12 * (int64_t)i + k]))
+                return fail(c, ST_ERR_MESH, "scene_load_instances: non-finite transform");
+        vbase[i + 1] = vbase[i] + (proto_vert_offset[q + 1] - proto_vert_offset[q]);
+        tbase[i + 1] = tbase[i] + (proto_tri_offset[q + 1] - proto_tri_offset[q]);
+        if (vbase[i + 1] >= (1ll << 31) || tbase[i + 1] >= (1ll << 28))
+            return fail(c, ST_ERR_ARG, "scene_load_instances: more than 2^31 vertices or 2^28 triangles in the world");
+    }
+    const int64_t NV = vbase[n_inst], NT = tbase[n_inst];
+    if (NV < 1 || NT < 1) return fail(c, ST_ERR_ARG, "scene_load_instances: the instances hold no triangle");
+    enter(c);
+    st_scene* sc = new st_scene();
+    sc->ctx = c;
+    sc->instanced = true;
+    st::InstanceDev& I = sc->inst;
+    I.n_proto = n_proto;
+    I.n_inst = n_inst;
+    I.nv = NV;
+    I.nt = NT;
+    SceneDev& S = sc->S;
+    S.n_verts = NV;
+    S.n_tris = NT;
+    S.n_obj = n_inst;
+    cudaError_t e = cudaSuccess;
+    const std::pair<DevBuf*, size_t> allocs[] = {
+        {&I.pverts, (size_t)std::max<int64_t>(pv, 1) * 12}, {&I.ptris, (size_t)std::max<int64_t>(pt, 1) * 12},
+        {&I.pmat, (size_t)std::max<int64_t>(pt, 1) * 4},    {&I.pvoff, (size_t)(n_proto + 1) * 8},
+        {&I.ptoff, (size_t)(n_proto + 1) * 8},              {&I.iproto, (size_t)n_inst * 4},
+        {&I.vbase, (size_t)(n_inst + 1) * 8},               {&I.tbase, (size_t)(n_inst + 1) * 8},
+        {&I.xform, (size_t)n_inst * 48},                    {&S.verts, (size_t)NV * 12},
+        {&S.tris, (size_t)NT * 12},                         {&S.tri_mat, (size_t)NT * 4},
+        {&S.tri_obj, (size_t)NT * 4}};
+    for (const auto& [b, bytes] : allocs)
+        if (e == cudaSuccess) e = grow(*b, bytes);
+    auto up = [&](DevBuf& b, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes > 0) e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    };
+    up(I.pverts, proto_verts, (size_t)pv * 12);
+    up(I.ptris, proto_tris, (size_t)pt * 12);
+    up(I.pmat, proto_tri_material, (size_t)pt * 4);
+    up(I.pvoff, proto_vert_offset, (size_t)(n_proto + 1) * 8);
+    up(I.ptoff, proto_tri_offset, (size_t)(n_proto + 1) * 8);
+    up(I.iproto, inst_proto, (size_t)n_inst * 4);
+    up(I.vbase, vbase.data(), (size_t)(n_inst + 1) * 8);
+    up(I.tbase, tbase.data(), (size_t)(n_inst + 1) * 8);
+    up(I.xform, inst_xform, (size_t)n_inst * 48);
+    if (e == cudaSuccess) e = st::expand_instance_verts(I, ptr<float>(I.xform), ptr<float>(S.verts), c->stream);
+    if (e == cudaSuccess)
+        e = st::expand_instance_tris(I, ptr<int32_t>(S.tris), ptr<int32_t>(S.tri_mat), ptr<int32_t>(S.tri_obj), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host tables above are released on return
+    if (e != cudaSuccess) {
+        scene_free(sc);
+        return cuda_fail(c, e, "scene_load_instances");
+    }
     sc->version = g_scene_version++;
-    if (e != cudaSuccess || mesh_err) sc->S.built = false;  // precompute again before the next simulate
-    if (e != cudaSuccess) return cuda_fail(c, e, "scene_update_vertices");
-    if (mesh_err) return fail(c, ST_ERR_MESH, "scene_update_vertices: " + msg);
+    c->scenes.push_back(sc);
+    *out = sc;
+    return ST_OK;
+}
+
+st_status st_scene_set_instance_transforms(st_scene* sc, const float* inst_xform, int32_t mem, int32_t flags) {
+    if (!sc) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (!inst_xform || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
+        return fail(c, ST_ERR_ARG, "scene_set_instance_transforms: null pointer or bad memory kind");
+    if (!sc->instanced) return fail(c, ST_ERR_STATE, "scene_set_instance_transforms: not an instanced scene");
+    if (!sc->S.built) return fail(c, ST_ERR_STATE, "scene_set_instance_transforms: precompute first");
+    enter(c);
+    st::InstanceDev& I = sc->inst;
+    CKC(c, cudaMemcpyAsync(I.xform.p, inst_xform, (size_t)I.n_inst * 48, kind_in(mem), c->stream),
+        "scene_set_instance_transforms copy");
+    CKC(c, st::expand_instance_verts(I, ptr<float>(I.xform), ptr<float>(sc->S.verts), c->stream),
+        "scene_set_instance_transforms expand");
+    return refit_scene(sc, flags, "scene_set_instance_transforms");  // non-finite results: ST_ERR_MESH
+}
+
+st_status st_scene_get_geometry(st_scene* sc, int64_t* n_verts, int64_t* n_tris, float* verts, int32_t* tris,
+                                int32_t* tri_material, int32_t* tri_object, int32_t mem) {
+    if (!sc) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE) return fail(c, ST_ERR_ARG, "scene_get_geometry: bad memory kind");
+    if (n_verts) *n_verts = sc->S.n_verts;
+    if (n_tris) *n_tris = sc->S.n_tris;
+    enter(c);
+    const SceneDev& S = sc->S;
+    if (verts) CKC(c, cudaMemcpyAsync(verts, S.verts.p, (size_t)S.n_verts * 12, kind_out(mem), c->stream), "get verts");
+    if (tris) CKC(c, cudaMemcpyAsync(tris, S.tris.p, (size_t)S.n_tris * 12, kind_out(mem), c->stream), "get tris");
+    if (tri_material)
+        CKC(c, cudaMemcpyAsync(tri_material, S.tri_mat.p, (size_t)S.n_tris * 4, kind_out(mem), c->stream), "get mat");
+    if (tri_object)
+        CKC(c, cudaMemcpyAsync(tri_object, S.tri_obj.p, (size_t)S.n_tris * 4, kind_out(mem), c->stream), "get obj");
+    CKC(c, cudaStreamSynchronize(c->stream), "get geometry sync");
     return ST_OK;
 }
 

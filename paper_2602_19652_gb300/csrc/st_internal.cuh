@@ -111,6 +111,25 @@ struct CurvParamsDev {
 cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bool* mesh_error, std::string* msg,
                         bool refit = false, bool keep_curvature = false);
 
+// Instanced scene: the prototypes (concatenated) and the instance table, kept on the device so that new
+// transforms expand the world vertices again.  Instance i is a copy of prototype iproto[i]; it owns world
+// vertices vbase[i] .. vbase[i+1] and triangles tbase[i] .. tbase[i+1].
+struct InstanceDev {
+    int32_t n_proto = 0, n_inst = 0;
+    int64_t nv = 0, nt = 0;  // world vertices and triangles
+    DevBuf pverts;           // [pv][3] f32 prototype vertices
+    DevBuf ptris;            // [pt][3] i32 prototype-local vertex indices
+    DevBuf pmat;             // [pt] i32 materials
+    DevBuf pvoff, ptoff;     // [n_proto + 1] i64 prototype vertex / triangle offsets
+    DevBuf iproto;           // [n_inst] i32
+    DevBuf vbase, tbase;     // [n_inst + 1] i64
+    DevBuf xform;            // [n_inst][12] f32 row-major [A | b]
+};
+// world vertices [nv][3] from the transforms xf [n_inst][12] (device)
+cudaError_t expand_instance_verts(const InstanceDev& I, const float* xf, float* out, cudaStream_t s);
+// world triangles [nt][3], their materials and objects (object = instance id)
+cudaError_t expand_instance_tris(const InstanceDev& I, int32_t* tris, int32_t* mat, int32_t* obj, cudaStream_t s);
+
 // ------------------------------------------------------------------ tracing (st_trace.cu)
 struct TraceArgs {
     // scene

@@ -914,4 +914,69 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
     return cudaSuccess;
 }
 
+// ------------------------------------------------------------------ instanced scenes
+// Instance i of prototype iproto[i] owns world vertices vbase[i] .. vbase[i+1] and triangles tbase[i] ..
+// tbase[i+1]; the instance of an element is found by binary search over the (ascending) bases.
+namespace {
+
+__device__ __forceinline__ int instance_of(const int64_t* base, int32_t n_inst, int64_t e) {
+    int lo = 0, hi = n_inst - 1;  // largest i with base[i] <= e (base[0] = 0 <= e)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// x' = A x + b per instance, each component ((A_r0 x + A_r1 y) + A_r2 z) + b_r, every product and sum
+// rounded to float32 in that order (this unit is compiled without contraction)
+__global__ void k_inst_verts(const float* __restrict__ pv, const int64_t* __restrict__ pvoff,
+                             const int32_t* __restrict__ iproto, const int64_t* __restrict__ vbase,
+                             const float* __restrict__ xf, int32_t n_inst, int64_t nv, float* __restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        const int i = instance_of(vbase, n_inst, v);
+        const int64_t src = pvoff[iproto[i]] + (v - vbase[i]);
+        const float x = pv[3 * src], y = pv[3 * src + 1], z = pv[3 * src + 2];
+        const float* a = xf + 12 * (int64_t)i;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) out[3 * v + r] = ((a[4 * r] * x + a[4 * r + 1] * y) + a[4 * r + 2] * z) + a[4 * r + 3];
+    }
+}
+
+__global__ void k_inst_tris(const int32_t* __restrict__ pt, const int32_t* __restrict__ pmat,
+                            const int64_t* __restrict__ ptoff, const int32_t* __restrict__ iproto,
+                            const int64_t* __restrict__ vbase, const int64_t* __restrict__ tbase, int32_t n_inst,
+                            int64_t nt, int32_t* __restrict__ tris, int32_t* __restrict__ mat,
+                            int32_t* __restrict__ obj) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = instance_of(tbase, n_inst, t);
+        const int64_t src = ptoff[iproto[i]] + (t - tbase[i]);
+        const int32_t off = (int32_t)vbase[i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tris[3 * t + k] = pt[3 * src + k] + off;
+        mat[t] = pmat[src];
+        obj[t] = i;
+    }
+}
+
+}  // namespace
+
+cudaError_t expand_instance_verts(const InstanceDev& I, const float* xf, float* out, cudaStream_t s) {
+    if (I.nv == 0) return cudaSuccess;
+    note_launch();
+    k_inst_verts<<<grid_for(I.nv, kB), kB, 0, s>>>(ptr<float>(I.pverts), ptr<int64_t>(I.pvoff), ptr<int32_t>(I.iproto),
+                                                   ptr<int64_t>(I.vbase), xf, I.n_inst, I.nv, out);
+    return cudaGetLastError();
+}
+
+cudaError_t expand_instance_tris(const InstanceDev& I, int32_t* tris, int32_t* mat, int32_t* obj, cudaStream_t s) {
+    if (I.nt == 0) return cudaSuccess;
+    note_launch();
+    k_inst_tris<<<grid_for(I.nt, kB), kB, 0, s>>>(ptr<int32_t>(I.ptris), ptr<int32_t>(I.pmat), ptr<int64_t>(I.ptoff),
+                                                  ptr<int32_t>(I.iproto), ptr<int64_t>(I.vbase), ptr<int64_t>(I.tbase),
+                                                  I.n_inst, I.nt, tris, mat, obj);
+    return cudaGetLastError();
+}
+
 }  // namespace st
