@@ -155,7 +155,9 @@ st_status st_scene_precompute(st_scene* scene, const st_curv_params* params);
  * Welding, curvature, metric, CDFs and sample counts are recomputed too, unless flags holds
  * ST_REFIT_KEEP_CURVATURE (valid when whole meshes move rigidly, which leaves them unchanged up to
  * rounding).  The scene's version changes: simulate again before st_backward; recorded batches
- * re-record.  A non-finite vertex returns ST_ERR_MESH and leaves the scene needing a precompute. */
+ * re-record.  A non-finite vertex returns ST_ERR_MESH and leaves the scene unbuilt (simulate returns
+ * ST_ERR_STATE) until a later update with finite positions, which then builds it in full with the
+ * parameters of its last precompute.  ST_ERR_STATE before the scene's first successful precompute. */
 #define ST_REFIT_KEEP_CURVATURE 1
 st_status st_scene_update_vertices(st_scene* scene, const float* verts, int32_t mem, int32_t flags);
 /* Instanced scene (Sec. III-B registers objects; a forest repeats a few plant meshes many times).
@@ -178,8 +180,9 @@ st_status st_scene_load_instances(st_ctx* ctx, int32_t n_proto, const int64_t* p
 /* Moves the instances of a precomputed instanced scene: new transforms inst_xform [n_inst][12] (host
  * or device per mem), the world vertices expanded again on the device, then the refit of
  * st_scene_update_vertices with the same flags (ST_REFIT_KEEP_CURVATURE for rotations and
- * translations).  ST_ERR_STATE for a scene not loaded by st_scene_load_instances or not precomputed;
- * ST_ERR_MESH when a world vertex is not finite (the scene then needs a precompute). */
+ * translations).  ST_ERR_STATE for a scene not loaded by st_scene_load_instances or never precomputed;
+ * ST_ERR_MESH when a world vertex is not finite (the scene is then unbuilt until a later call with finite
+ * maps, as for st_scene_update_vertices). */
 st_status st_scene_set_instance_transforms(st_scene* scene, const float* inst_xform, int32_t mem, int32_t flags);
 /* The scene's triangles as loaded or expanded: counts (either may be NULL), then verts [n_verts][3],
  * tris [n_tris][3], tri_material [n_tris], tri_object [n_tris] (any may be NULL).  Synchronises. */

@@ -14,13 +14,13 @@ import torch
 
 from . import _lib
 from .autograd import SpectraFn  # noqa: E402
-from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_LOS_PER_MIC, ST_LOS_REFERENCE,
-                   ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
+from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_ERR_ARG, ST_ERR_MESH, ST_ERR_STATE,
+                   ST_LOS_PER_MIC, ST_LOS_REFERENCE, ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
                    Job, SimParams, SonotraceError, Stats, Tune, check, load)
 
 __all__ = ["Context", "Scene", "BatchJob", "SpectraFn", "CurvParams", "SimParams", "Stats", "Tune", "SonotraceError",
            "sim_params", "curv_params", "ST_COMP_SPECULAR", "ST_COMP_DIFFRACTION", "ST_COMP_DIRECT",
-           "ST_LOS_REFERENCE", "ST_LOS_PER_MIC"]
+           "ST_LOS_REFERENCE", "ST_LOS_PER_MIC", "ST_ERR_ARG", "ST_ERR_MESH", "ST_ERR_STATE"]
 
 
 def curv_params(**kw) -> CurvParams:

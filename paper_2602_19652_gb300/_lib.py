@@ -14,6 +14,8 @@ P = C.c_void_p
 I32, I64, U32, U64, F32, F64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float, C.c_double
 
 ST_OK = 0
+# status codes (include/sonotrace.h)
+ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_OOM, ST_ERR_MESH, ST_ERR_TIMEOUT, ST_ERR_STATE, ST_ERR_OVERFLOW = -1, -2, -3, -4, -5, -6, -7
 ST_MEM_HOST, ST_MEM_DEVICE = 0, 1
 ST_IR_PER_COMPONENT = 1
 ST_REFIT_KEEP_CURVATURE = 1

@@ -143,6 +143,7 @@ struct st_scene {
     bool has_materials = false;
     uint64_t version = 0;
     st::CurvParamsDev cp{};  // parameters of the last precompute (reused by refits)
+    bool precomputed = false;  // a precompute succeeded once (cp holds its parameters)
     bool instanced = false;  // loaded by st_scene_load_instances
     st::InstanceDev inst;
 };
@@ -394,17 +395,20 @@ st_status st_scene_precompute(st_scene* sc, const st_curv_params* params) {
     if (e != cudaSuccess) return cuda_fail(c, e, "scene_precompute");
     if (mesh_err) return fail(c, ST_ERR_MESH, "scene_precompute: " + msg);
     sc->cp = cp;
+    sc->precomputed = true;
     sc->version = g_scene_version++;
     return ST_OK;
 }
 
-// Refit of a precomputed scene whose vertex buffer holds new positions (same triangles).
+// Refit of a precomputed scene whose vertex buffer holds new positions (same triangles); a scene left
+// unbuilt by a failed update is built in full instead, with the parameters of its last precompute.
 static st_status refit_scene(st_scene* sc, int32_t flags, const char* what) {
     st_ctx* c = sc->ctx;
     bool mesh_err = false;
     std::string msg;
-    cudaError_t e = scene_build(sc->S, sc->cp, c->stream, &mesh_err, &msg, true,
-                                (flags & ST_REFIT_KEEP_CURVATURE) != 0);
+    const bool refit = sc->S.built;
+    cudaError_t e = scene_build(sc->S, sc->cp, c->stream, &mesh_err, &msg, refit,
+                                refit && (flags & ST_REFIT_KEEP_CURVATURE) != 0);
     sc->version = g_scene_version++;
     if (e != cudaSuccess || mesh_err) sc->S.built = false;  // precompute again before the next simulate
     if (e != cudaSuccess) return cuda_fail(c, e, what);
@@ -417,7 +421,7 @@ st_status st_scene_update_vertices(st_scene* sc, const float* verts, int32_t mem
     st_ctx* c = sc->ctx;
     if (!verts || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
         return fail(c, ST_ERR_ARG, "scene_update_vertices: null pointer or bad memory kind");
-    if (!sc->S.built) return fail(c, ST_ERR_STATE, "scene_update_vertices: precompute first");
+    if (!sc->precomputed) return fail(c, ST_ERR_STATE, "scene_update_vertices: precompute first");
     enter(c);
     CKC(c, cudaMemcpyAsync(sc->S.verts.p, verts, (size_t)sc->S.n_verts * 12, kind_in(mem), c->stream),
         "scene_update_vertices copy");
@@ -522,7 +526,7 @@ st_status st_scene_set_instance_transforms(st_scene* sc, const float* inst_xform
     if (!inst_xform || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
         return fail(c, ST_ERR_ARG, "scene_set_instance_transforms: null pointer or bad memory kind");
     if (!sc->instanced) return fail(c, ST_ERR_STATE, "scene_set_instance_transforms: not an instanced scene");
-    if (!sc->S.built) return fail(c, ST_ERR_STATE, "scene_set_instance_transforms: precompute first");
+    if (!sc->precomputed) return fail(c, ST_ERR_STATE, "scene_set_instance_transforms: precompute first");
     enter(c);
     st::InstanceDev& I = sc->inst;
     CKC(c, cudaMemcpyAsync(I.xform.p, inst_xform, (size_t)I.n_inst * 48, kind_in(mem), c->stream),
