@@ -286,6 +286,129 @@ def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 
             "max_rel_l2_batched_vs_plain": err, "first_call_s": first_call_s}
 
 
+def measure_emitters(st, torch, ctx, sc, wl, n_emitters: int = 4, reps: int = 3):
+    """Several emitters sending the workload's ray set into its scene towards its array: one batched call
+    (Context.simulate_emitters) against one plain st_simulate per emitter (set_emitter + simulate, the
+    sensor inputs on the device).  Emitters within 0.5 m of the sensor, random orientations, one pose
+    index; L2 flushed before each timed pass; both arms' spectra compared."""
+    dev = torch.cuda.current_device()
+    rng = np.random.default_rng(707)
+    E = (wl.emitter + rng.uniform(-0.5, 0.5, (n_emitters, 3)) * np.array([1.0, 1.0, 0.2])).astype(np.float32)
+    Q = rng.normal(size=(n_emitters, 4))
+    Q = (Q / np.linalg.norm(Q, axis=1, keepdims=True)).astype(np.float32)
+    dirs = torch.as_tensor(wl.dirs, device=f"cuda:{dev}")
+    p = st.sim_params(max_distance=wl.max_distance)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ms = []
+        for i in range(reps):
+            flush.fill_(i & 255)
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ms))
+
+    def batched():
+        return ctx.simulate_emitters(sc, E, Q, dirs, wl.mics, wl.n_bins, wl.f_lo, wl.f_hi, wl.bounces, p)
+
+    t0 = time.perf_counter()
+    batched()  # first call: eager run and graph recording
+    torch.cuda.synchronize()
+    first_call_s = time.perf_counter() - t0
+    batched_ms = timed(batched)
+    out_b = batched().clone()
+    outs = torch.empty_like(out_b)
+    pp = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    ctx.set_frequencies(wl.n_bins, wl.f_lo, wl.f_hi)
+    ctx.set_receivers(wl.mics)
+
+    def plain():
+        for e in range(n_emitters):
+            ctx.set_emitter(E[e], Q[e], dirs, None, wl.fov_half)
+            ctx.simulate(sc, pp, out=outs[e])
+
+    plain()
+    plain_ms = timed(plain)
+    err = max(float(torch.linalg.vector_norm(out_b[e, c] - outs[e, c]) / torch.linalg.vector_norm(outs[e, c]))
+              for e in range(n_emitters) for c in range(3) if float(torch.linalg.vector_norm(outs[e, c])) > 0)
+    ctx.set_emitter(wl.emitter, wl.emitter_quat, wl.dirs, wl.emitter_table, wl.fov_half)
+    n_rays = n_emitters * len(wl.dirs)
+    return {"workload": f"{n_emitters} emitters x {len(wl.dirs)} rays x {wl.bounces} bounces into the {wl.name} scene, "
+                        f"{len(wl.mics)} mics x {wl.n_bins} bins, diffraction on",
+            "batched_ms": batched_ms, "plain_ms": plain_ms, "speedup": plain_ms / batched_ms,
+            "batched_emitter_rays_per_s": n_rays / (batched_ms / 1e3), "first_call_s": first_call_s,
+            "max_rel_l2_batched_vs_plain": err}
+
+
+def measure_instances(st, torch, n_inst: int = 8000, n_rays: int = 1_000_000, reps: int = 3):
+    """Instanced forest (shared plant meshes under affine maps, expanded on the device): host time of
+    st_scene_load_instances (checks, upload of prototypes and instance table, expansion), device times of
+    the precompute, of moving every plant (new maps, expansion and refit; keeping the curvature, as the
+    moves are rotations and translations, and recomputing it) and of one simulate; bytes uploaded
+    against those of the same scene loaded flat."""
+    dev = torch.cuda.current_device()
+    fo = synth.instanced_forest(seed=606, n_inst=n_inst, n_rays=n_rays, bounces=3, n_mics=8, n_bins=128)
+    b = fo.base
+    ctx = st.Context(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sc = st.Scene.from_instances(ctx, fo.protos, fo.inst_proto, fo.inst_xform)
+    load_s = time.perf_counter() - t0
+    sc.set_materials(b.band_hz, b.k_band, b.beta_band, b.diff_band)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ms = []
+        for i in range(reps):
+            ev[0].record(stream)
+            fn(i)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ms))
+
+    curv = st.curv_params(sample_budget=1_000_000)
+    precompute_ms = timed(lambda i: sc.precompute(curv))
+    rng = np.random.default_rng(8)
+    X = fo.inst_xform.astype(np.float64)
+    moved = X.copy()
+    for i in range(1, n_inst):  # every plant turned about the vertical and shifted
+        a = rng.uniform(-0.2, 0.2)
+        R = np.array([[np.cos(a), -np.sin(a), 0.0], [np.sin(a), np.cos(a), 0.0], [0.0, 0.0, 1.0]])
+        moved[i, :, :3] = R @ X[i, :, :3]
+        moved[i, :2, 3] += rng.uniform(-0.05, 0.05, 2)
+    poses = [torch.as_tensor(m.astype(np.float32), device=f"cuda:{dev}") for m in (moved, X)]
+    move_keep_ms = timed(lambda i: sc.set_instance_transforms(poses[i & 1], keep_curvature=True))
+    move_full_ms = timed(lambda i: sc.set_instance_transforms(poses[i & 1]))
+    sc.set_instance_transforms(poses[1])
+    ctx.set_frequencies(b.n_bins, b.f_lo, b.f_hi)
+    ctx.set_emitter(b.emitter, b.emitter_quat, b.dirs)
+    ctx.set_receivers(b.mics)
+    p = st.sim_params(max_bounces=b.bounces, max_distance=b.max_distance)
+    out = torch.empty((3, len(b.mics), b.n_bins), dtype=torch.complex64, device=f"cuda:{dev}")
+    ctx.simulate(sc, p, out=out)
+    stats = []
+    sim_ms = timed(lambda i: stats.append(ctx.simulate(sc, p, out=out, stats=True)[1]))
+    segs = stats[-1].closest_queries + stats[-1].shadow_queries
+    pv = sum(len(q[0]) for q in fo.protos)
+    pt = sum(len(q[1]) for q in fo.protos)
+    up_inst = pv * 12 + pt * 16 + n_inst * 52 + (len(fo.protos) + 1) * 16
+    up_flat = sc.n_verts * 12 + sc.n_tris * 20
+    res = {"workload": f"instanced forest: {n_inst} instances of {len(fo.protos)} meshes, {sc.n_tris} triangles, "
+                       f"{n_rays} rays x {b.bounces} bounces, {len(b.mics)} mics x {b.n_bins} bins, diffraction on",
+           "load_instances_s": load_s, "precompute_ms": precompute_ms, "move_refit_keep_curvature_ms": move_keep_ms,
+           "move_refit_ms": move_full_ms, "simulate_ms": sim_ms, "value": segs / (sim_ms / 1e3) / 1e6, "unit": UNIT,
+           "upload_bytes_instanced": int(up_inst), "upload_bytes_flat": int(up_flat)}
+    ctx.close()
+    return res
+
+
 def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: int = 0):
     """Device time of one simulate on another workload (scene prebuilt, L2 flushed before each step);
     los_mode 1: the receiver test of every hit made per microphone."""
@@ -431,8 +554,18 @@ def measure_scene_update(st, torch, ctx, sc, wl, reps: int = 3):
 
 
 def run_case(st, torch, case: str, reps: int):
-    """Small cases of single kernels for profiling (ncu captures): no timing output."""
+    """Small cases of single kernels for profiling (ncu captures): no timing output; "emitters" and
+    "instances" print their measurement alone."""
     dev = torch.cuda.current_device()
+    if case == "instances":
+        print(json.dumps(measure_instances(st, torch)))
+        return
+    if case == "emitters":
+        wl = synth.clutter(seed=202)
+        ctx = st.Context(dev)
+        sc = st.from_workload(ctx, wl)
+        print(json.dumps(measure_emitters(st, torch, ctx, sc, wl)))
+        return
     if case in ("accum", "adjoint", "trace", "trace_per_mic"):
         wl = synth.clutter(seed=202, n_rays=200_000)
     elif case == "narrow":
@@ -494,7 +627,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain pose sweep")
     ap.add_argument("--no-per-mic", action="store_true", help="skip the per-microphone receiver-test timing")
     ap.add_argument("--no-vegetation", action="store_true", help="skip the full-size vegetation simulate timing")
-    ap.add_argument("--case", default=None, choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow"],
+    ap.add_argument("--no-emitters", action="store_true", help="skip the several-emitters timing")
+    ap.add_argument("--no-instances", action="store_true", help="skip the instanced-forest timing")
+    ap.add_argument("--case", default=None,
+                    choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow", "emitters", "instances"],
                     help="run a small case of one kernel family a few times and exit (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -635,6 +771,12 @@ def main():
     per_mic = None
     if not args.no_per_mic and len(wl.mics) <= 64:
         per_mic = measure_workload(st, torch, wl, los_mode=st.ST_LOS_PER_MIC)
+    emitters = None
+    if not args.no_emitters and wl.emitter_table is None and wl.mic_tables is None:
+        emitters = measure_emitters(st, torch, ctx, sc, wl)
+    instances = None
+    if not args.no_instances:
+        instances = measure_instances(st, torch)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -655,7 +797,8 @@ def main():
                          "ms_accumulate": s0.ms_accumulate},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
             "traversal": traversal, "signal": signal, "scene_update": scene_update, "batched": batched,
-            "vegetation": vegetation, "receiver_test_per_mic": per_mic,
+            "vegetation": vegetation, "receiver_test_per_mic": per_mic, "emitters": emitters,
+            "instances": instances,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
     print(json.dumps(line))
     if world > 1:

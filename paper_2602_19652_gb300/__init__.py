@@ -84,11 +84,12 @@ class Context:
 
     def set_emitter(self, pos, quat, dirs, table=None, fov_half: float = math.pi):
         self.quat, self.dirs, self.fov_half = quat, dirs, fov_half
-        pos = np.ascontiguousarray(pos, np.float32)
-        quat = np.ascontiguousarray(quat, np.float32)
+        # every pointer of the call in device memory, as ST_MEM_DEVICE says
+        pos = _dev(pos, torch.float32).reshape(3).contiguous()
+        quat = _dev(quat, torch.float32).reshape(4).contiguous()
         d = _dev(dirs, torch.float32)
         tab = None if table is None else _dev(table, torch.float32)
-        self._check(self.L.st_set_emitter(self.h, pos.ctypes.data_as(C.c_void_p), quat.ctypes.data_as(C.c_void_p),
+        self._check(self.L.st_set_emitter(self.h, _ptr(pos), _ptr(quat),
                                           int(d.shape[0]), _ptr(d), None if tab is None else _ptr(tab),
                                           0 if tab is None else int(tab.shape[0]), float(np.float32(fov_half)),
                                           ST_MEM_DEVICE))
