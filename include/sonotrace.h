@@ -89,9 +89,9 @@ typedef struct st_sim_params {
     uint64_t seed;              /* Philox key of the diffraction samples (default 0) */
     uint32_t pose_index;        /* Philox counter word distinguishing poses (default 0) */
     int32_t los_mode;           /* ST_LOS_* (default ST_LOS_REFERENCE); ST_LOS_PER_MIC needs M <= 64 and
-                                   N * B * M < 2^32 and single-pose st_simulate only (st_backward then
-                                   follows the masks); st_accumulate_specular_noalloc takes the caller's
-                                   records and ignores it */
+                                   N * B * M < 2^32 (st_backward then follows the masks); in
+                                   st_simulate_batch M <= 64 per job and sum(N M) < 2^32;
+                                   st_accumulate_specular_noalloc takes the caller's records and ignores it */
 } st_sim_params;
 
 /* Optional statistics of one simulate call (filled after the stream is synchronised). */

@@ -438,7 +438,7 @@ cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
 // path list entries of every job (same layout as the single-pose gather; omni emitter)
 __global__ void k_gather_spec_batch(const BatchArgs a, const uint32_t* idx, const uint32_t* count, float* px, float* py,
                                     float* pz, float* dx, float* dy, float* dz, float* rhi, float* rlo, uint32_t* chl,
-                                    uint32_t* chh, uint32_t* meta, float* dep) {
+                                    uint32_t* chh, uint32_t* meta, float* dep, uint64_t* mask) {
     const int64_t n = *count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
@@ -469,6 +469,7 @@ __global__ void k_gather_spec_batch(const BatchArgs a, const uint32_t* idx, cons
         chh[c] = hi;
         meta[c] = (uint32_t)(j + 1) | ((uint32_t)matj << 8);
         dep[c] = -1.0f;
+        if (mask) mask[c] = a.rec_mask[id];  // per-microphone receiver test
     }
 }
 
@@ -669,7 +670,7 @@ cudaError_t batch_gather_spec(const BatchArgs& a, const uint32_t* idx, const uin
     k_gather_spec_batch<<<grid_for(a.R_total, 256), 256, 0, s>>>(
         a, idx, count, ptr<float>(P.px), ptr<float>(P.py), ptr<float>(P.pz), ptr<float>(P.dx), ptr<float>(P.dy),
         ptr<float>(P.dz), ptr<float>(P.rhi), ptr<float>(P.rlo), ptr<uint32_t>(P.chain_lo), ptr<uint32_t>(P.chain_hi),
-        ptr<uint32_t>(P.meta), ptr<float>(P.dep));
+        ptr<uint32_t>(P.meta), ptr<float>(P.dep), a.rec_mask ? ptr<uint64_t>(P.mask) : nullptr);
     return cudaGetLastError();
 }
 

@@ -126,6 +126,9 @@ struct BatchState {
     DevBuf rec_tri, rec_p, rec_d, rec_r, rec_los, cand_tri, cand_p, keep, dvis, ranges;
     DevBuf sflags, sscan, sidx, scratch;
     DevBuf hit_tri, hit_t, vis_q, los_q;  // lane-refill traversal
+    DevBuf rec_mask, vis_qm;              // per-microphone receiver test
+    bool per_mic = false;
+    int64_t Q_total = 0;                  // per-microphone visibility queries a bounce, at most
     std::vector<DevBuf> partial;  // one per branch
     PathList spec, diff;
     int64_t N_total = 0, R_total = 0, K_total = 0, M_total = 0, MF_total = 0;
@@ -1464,7 +1467,7 @@ void batch_release(BatchState& B) {
                       &B.st_o[2], &B.st_d[0], &B.st_d[1], &B.st_d[2], &B.st_r, &B.st_prev, &B.q0, &B.q1, &B.counts,
                       &B.queries, &B.flags, &B.rec_tri, &B.rec_p, &B.rec_d, &B.rec_r, &B.rec_los, &B.cand_tri,
                       &B.cand_p, &B.keep, &B.dvis, &B.ranges, &B.sflags, &B.sscan, &B.sidx, &B.scratch, &B.hit_tri,
-                      &B.hit_t, &B.vis_q, &B.los_q})
+                      &B.hit_t, &B.vis_q, &B.los_q, &B.rec_mask, &B.vis_qm})
         release(*b);
     for (auto& d : B.partial) release(d);
     for (auto& T : B.tables)
@@ -1542,6 +1545,9 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     a.hit_t = ptr<float>(B.hit_t);
     a.vis_q = ptr<uint32_t>(B.vis_q);
     a.los_q = ptr<uint32_t>(B.los_q);
+    a.rec_mask = B.per_mic ? ptr<uint64_t>(B.rec_mask) : nullptr;
+    a.vis_qm = B.per_mic ? ptr<uint64_t>(B.vis_qm) : nullptr;
+    a.Q_total = B.Q_total;
     a.vis_n = cnt + 4;  // counts: [0] [1] live queues, [2] [3] compaction totals, [4] [5] visibility queues,
     a.los_n = cnt + 5;  // bytes 32..55 the three query counters
     a.ctr = reinterpret_cast<unsigned long long*>(cnt + 8);
@@ -1629,6 +1635,7 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
             y.chain_hi = ptr<uint32_t>(B.spec.chain_hi);
             y.meta = ptr<uint32_t>(B.spec.meta);
             y.dep = ptr<float>(B.spec.dep);
+            y.mask = B.per_mic ? ptr<uint64_t>(B.spec.mask) : nullptr;  // indexed from y.d_base
             y.n_chunks = B.chunks_spec[j];
             CB(accumulate(y, bs));
             CB(reduce_partials(y.partial, y.n_chunks, MF, out, bs));
@@ -1674,8 +1681,9 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     st_sim_params p;
     st_sim_params_default(&p);
     if (params) p = *params;
-    if (p.los_mode != ST_LOS_REFERENCE)
-        return fail(c, ST_ERR_ARG, "simulate_batch: the batched form makes the reference-point receiver test only");
+    if (p.los_mode != ST_LOS_REFERENCE && p.los_mode != ST_LOS_PER_MIC)
+        return fail(c, ST_ERR_ARG, "simulate_batch: los_mode must be ST_LOS_REFERENCE or ST_LOS_PER_MIC");
+    const bool per_mic = p.los_mode == ST_LOS_PER_MIC;
     st_tune tn = tune ? *tune : c->tune;
     if (!tune_ok(tn)) return fail(c, ST_ERR_ARG, "simulate_batch: tune out of range");
     for (int j = 0; j < n_jobs; ++j) {
@@ -1686,6 +1694,16 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
             J.n_mics < 1 || J.n_mics > kMaxMics || J.n_bins < 1 || J.max_bounces < 1 || J.max_bounces > kMaxBounces ||
             !(J.f_lo > 0.0) || !(J.f_hi >= J.f_lo) || (J.n_bins > 1 && !(J.f_hi > J.f_lo)))
             return fail(c, ST_ERR_ARG, "simulate_batch: bad job");
+    }
+    if (per_mic) {  // queue entries (record << 6 | m) and a 32-bit queue length
+        int64_t q = 0;
+        for (int j = 0; j < n_jobs; ++j) {
+            if (jobs[j].n_mics > 64)
+                return fail(c, ST_ERR_ARG, "simulate_batch: the per-microphone receiver test needs M <= 64 per job");
+            q += jobs[j].n_rays * jobs[j].n_mics;
+        }
+        if (q >= (1ll << 32))
+            return fail(c, ST_ERR_ARG, "simulate_batch: the per-microphone receiver test needs sum(N M) < 2^32");
     }
     enter(c);
     cudaStream_t s = c->stream;
@@ -1712,7 +1730,7 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     key = fnv(key, pd, sizeof(pd));
     const double pg = p.direct_gain;
     key = fnv(key, &pg, sizeof(pg));
-    const int64_t pi[3] = {(int64_t)p.components, (int64_t)p.reflection_mode, (int64_t)p.seed};
+    const int64_t pi[4] = {(int64_t)p.components, (int64_t)p.reflection_mode, (int64_t)p.seed, (int64_t)p.los_mode};
     key = fnv(key, pi, sizeof(pi));
     const int32_t ti[3] = {tn.rays_per_block, tn.mic_pairs_per_cta, tn.smem_kb};
     key = fnv(key, ti, sizeof(ti));
@@ -1750,6 +1768,9 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
         mf_o[j + 1] = mf_o[j] + (int64_t)J.n_mics * J.n_bins;
         B.max_b = std::max(B.max_b, (int)J.max_bounces);
     }
+    B.per_mic = per_mic;
+    B.Q_total = 0;
+    for (int j = 0; j < n_jobs; ++j) B.Q_total += per_mic ? jobs[j].n_rays * jobs[j].n_mics : 0;
     B.N_total = ray_o[n_jobs];
     B.R_total = rec_o[n_jobs];
     B.K_total = smp_o[n_jobs];
@@ -1776,6 +1797,10 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     CKC(c, grow(B.hit_tri, (size_t)N1 * 4), "batch alloc");
     CKC(c, grow(B.hit_t, (size_t)N1 * 4), "batch alloc");
     CKC(c, grow(B.vis_q, (size_t)N1 * 4), "batch alloc");
+    if (per_mic) {
+        CKC(c, grow(B.rec_mask, (size_t)R1 * 8), "batch alloc");
+        CKC(c, grow(B.vis_qm, (size_t)std::max<int64_t>(B.Q_total, 1) * 8), "batch alloc");
+    }
     CKC(c, grow(B.counts, 64), "batch alloc");
     CKC(c, grow(B.queries, 64), "batch alloc");
     CKC(c, grow(B.flags, 16), "batch alloc");
@@ -1797,8 +1822,9 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     for (PathList* P : {&B.spec, &B.diff}) {
         const int64_t nP = P == &B.spec ? R1 : K1;
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
-                          &P->meta, &P->dep, &P->mask})
+                          &P->meta, &P->dep})
             CKC(c, grow(*b, (size_t)nP * 4), "batch alloc");
+        if (per_mic && P == &B.spec) CKC(c, grow(P->mask, (size_t)nP * 8), "batch alloc");  // u64 per path
         P->n_max = nP;
     }
     std::vector<size_t> part_bytes(B.n_branches, 256);

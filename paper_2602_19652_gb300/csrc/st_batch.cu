@@ -157,7 +157,11 @@ __global__ void k_shade_batch(const BatchArgs a, int j, int64_t n_first) {
         a.rec_d[3 * id + 1] = dr.y;
         a.rec_d[3 * id + 2] = dr.z;
         const int lane = threadIdx.x & 31;
-        {
+        if (a.rec_mask) {  // one visibility query per microphone of the job (M <= 64)
+            a.rec_mask[id] = 0ull;
+            const uint32_t base = atomicAdd(a.vis_n, (uint32_t)b.M);
+            for (int m = 0; m < b.M; ++m) a.vis_qm[base + m] = ((uint64_t)id << 6) | (uint64_t)m;
+        } else {
             const unsigned active = __activemask();
             const int leader = __ffs(active) - 1;
             uint32_t base = 0;
@@ -228,6 +232,62 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_batch(const BatchArgs
         while (true) {
             if (live && trav_step<true>(T, S, stack, a.flags)) {
                 out[id] = S.best < 0 ? 1 : 0;
+                live = false;
+            }
+            const unsigned lv = __ballot_sync(full, live);
+            const unsigned nd = __ballot_sync(full, !live && !exhausted);
+            if (lv == 0u || __popc(nd) >= kRefillAny) break;
+        }
+    }
+}
+
+// Per-microphone receiver test of every job: entry (record << 6 | m) of the queue tests the segment from the
+// record's hit point towards microphone m of its job (the single-pose kernel's float32 steps) and sets bit
+// m of the record's mask, and its visibility flag, when nothing but the record's own triangle lies on it.
+__global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics_batch(const BatchArgs a, unsigned long long* ctr) {
+    const int64_t n = *a.vis_n;
+    const unsigned full = 0xffffffffu;
+    int2 stack[kStack];
+    TravState S;
+    Trav T{nullptr, nullptr, 0, 0, nullptr};
+    int64_t id = -1;
+    int m = 0;
+    bool live = false, exhausted = false;
+    while (true) {
+        const bool need = !live && !exhausted;
+        const int64_t idx = claim(ctr, need);
+        if (need) {
+            if (idx < n) {
+                const uint64_t e = a.vis_qm[idx];
+                id = (int64_t)(e >> 6);
+                m = (int)(e & 63u);
+                const JobDev& b = a.jobs[find_job(a.rec_offs, a.n_jobs, id)];
+                const f3 o{a.rec_p[3 * id], a.rec_p[3 * id + 1], a.rec_p[3 * id + 2]};
+                const f3 target{b.mics[3 * m], b.mics[3 * m + 1], b.mics[3 * m + 2]};
+                float L;
+                const f3 u = normalize(sub(target, o), &L);
+                const float tmax = L - a.los_eps;
+                if (!(tmax > a.t_min)) {
+                    atomicOr(reinterpret_cast<unsigned long long*>(&a.rec_mask[id]), 1ull << m);
+                    a.rec_los[id] = 1;
+                } else {
+                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+                    trav_init(S, T, o, u, a.rec_tri[id], a.t_min, tmax);
+                    live = true;
+                }
+            } else {
+                exhausted = true;
+            }
+        }
+        const unsigned lv0 = __ballot_sync(full, live);
+        const unsigned nd0 = __ballot_sync(full, !live && !exhausted);
+        if (lv0 == 0u && nd0 == 0u) break;
+        while (true) {
+            if (live && trav_step<true>(T, S, stack, a.flags)) {
+                if (S.best < 0) {
+                    atomicOr(reinterpret_cast<unsigned long long*>(&a.rec_mask[id]), 1ull << m);
+                    a.rec_los[id] = 1;
+                }
                 live = false;
             }
             const unsigned lv = __ballot_sync(full, live);
@@ -388,8 +448,11 @@ cudaError_t batch_trace(BatchArgs& a, int max_b, int64_t n_total, int block, cud
         k_shade_batch<<<grid, block, 0, s>>>(a, j, n_total);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         note_launch();
-        k_visible_batch<<<trav_grid(n_total), kTravBlock, 0, s>>>(a, a.vis_q, a.vis_n, a.rec_offs, a.rec_p, a.rec_tri,
-                                                                  0, a.rec_los, a.ctr + 1);
+        if (a.rec_mask)
+            k_visible_mics_batch<<<trav_grid(a.Q_total), kTravBlock, 0, s>>>(a, a.ctr + 1);
+        else
+            k_visible_batch<<<trav_grid(n_total), kTravBlock, 0, s>>>(a, a.vis_q, a.vis_n, a.rec_offs, a.rec_p,
+                                                                      a.rec_tri, 0, a.rec_los, a.ctr + 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

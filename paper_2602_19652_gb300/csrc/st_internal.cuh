@@ -396,6 +396,11 @@ struct BatchArgs {
     unsigned long long* ctr;
     uint32_t* flags;
     unsigned long long* queries;
+    // per-microphone receiver test (null otherwise): visible microphones of each record [R_total], and the
+    // visibility queue of (record << 6 | microphone) entries, at most Q_total = sum over jobs of N x M a bounce
+    uint64_t* rec_mask;
+    uint64_t* vis_qm;
+    int64_t Q_total;
 };
 
 cudaError_t batch_prep(const JobDev* jobs, int n_jobs, cudaStream_t s);

@@ -173,6 +173,43 @@ def test_several_emitters_in_one_call(st):
         assert not np.array_equal(out[0], out[1])
 
 
+def test_batch_per_microphone_receiver_test(st):
+    """The per-microphone receiver test in the batched form: three poses in the clutter scene with
+    microphones spread over 16 x 16 m (hits that some microphones see and others do not; the first job
+    with two microphones, the narrow accumulator) against the single-pose per-microphone path (2e-5), the
+    first job against the oracle (1e-4), and the specular spectra differ from the reference-point test's."""
+    import oracle
+    wl = synth.clutter(seed=202, target_tris=20_000, n_rays=8_000, bounces=3, n_mics=12, n_bins=48)
+    wl = dataclasses.replace(wl, max_distance=60.0)
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, st.curv_params(sample_budget=50_000))
+    rng = np.random.default_rng(17)
+    jobs, wl_jobs = [], []
+    for k in range(3):
+        M = 2 if k == 0 else 12
+        mics = np.stack([rng.uniform(2, 18, M), rng.uniform(2, 18, M), rng.uniform(0.3, 2.0, M)], 1).astype(np.float32)
+        e = (wl.emitter + rng.uniform(-0.3, 0.3, 3) * np.array([1.0, 1.0, 0.2])).astype(np.float32)
+        wj = dataclasses.replace(wl, mics=mics, emitter=e, emitter_quat=unit_quat(rng))
+        jobs.append(st.BatchJob(sc, wj.emitter, wj.emitter_quat, wj.dirs, wj.mics, wj.n_bins, wj.f_lo, wj.f_hi,
+                                wj.bounces, pose_index=k, fov_half=wj.fov_half))
+        wl_jobs.append(wj)
+    p = st.sim_params(max_distance=60.0, los_mode=st.ST_LOS_PER_MIC)
+    outs = [o.cpu().numpy().copy() for o in ctx.simulate_batch(jobs, p)]
+    ref_mode = [o.cpu().numpy().copy() for o in ctx.simulate_batch(jobs, st.sim_params(max_distance=60.0))]
+    again = [o.cpu().numpy().copy() for o in ctx.simulate_batch(jobs, p)]  # recorded again for this mode
+    for j, (job, wj) in enumerate(zip(jobs, wl_jobs)):
+        assert np.array_equal(again[j], outs[j])
+        ref = single(st, ctx, sc, wj, j, los_mode=st.ST_LOS_PER_MIC)
+        for c in range(3):
+            assert rel_l2(outs[j][c], ref[c]) <= TOL_SINGLE, (j, c, rel_l2(outs[j][c], ref[c]))
+        assert rel_l2(outs[j][0], ref_mode[j][0]) > 1e-3, j  # the masks change the specular spectra
+    o = oracle.simulate(wl_jobs[0], curv=dict(budget=50_000), pose=0, los_mode=1)
+    m0 = o["rec"]["mask"][o["rec"]["tri"] >= 0]
+    assert np.sum(m0 == 1) + np.sum(m0 == 2) > 100  # records that reach one microphone of the two
+    for c in range(3):
+        assert rel_l2(outs[0][c], o["spectra"][c]) <= TOL, (c, rel_l2(outs[0][c], o["spectra"][c]))
+
+
 def test_autotune_shapes_give_same_results(st):
     ctx = st.Context(0)
     scenes, jobs, wl_jobs = make_case(st, ctx, seed=14, n_scenes=1, poses=2)

@@ -2,7 +2,7 @@
 microphone masks bit for bit, spectra within the spectra tolerance, for the general accumulator (a spread
 array whose microphones see different hit points), a plane wall between two microphone groups, and the
 two-microphone accumulator with directivity tables; the gradients of the adjoint over masked records; and
-the argument checks of the mode."""
+the argument checks of the mode (the batched form's parity is in test_gpu_batch)."""
 import dataclasses
 
 import numpy as np
@@ -154,6 +154,8 @@ def test_mode_argument_checks(st):
         ctx.receiver_masks(2)
     ctx.simulate(sc, st.sim_params(max_bounces=2, los_mode=st.ST_LOS_PER_MIC))
     assert ctx.receiver_masks(2).shape == (64, 2)
-    job = st.BatchJob(sc, wl.emitter, wl.emitter_quat, wl.dirs, wl.mics[:4], 8, wl.f_lo, wl.f_hi, 2)
-    with pytest.raises(st.SonotraceError):
+    job = st.BatchJob(sc, wl.emitter, wl.emitter_quat, wl.dirs, wl.mics, 8, wl.f_lo, wl.f_hi, 2)
+    with pytest.raises(st.SonotraceError):  # 65 microphones in a job
         ctx.simulate_batch([job], st.sim_params(los_mode=st.ST_LOS_PER_MIC))
+    with pytest.raises(st.SonotraceError):
+        ctx.simulate_batch([job], st.sim_params(los_mode=2))
