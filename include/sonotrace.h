@@ -264,7 +264,9 @@ st_status st_backward_beta(st_ctx* ctx, st_scene* scene, const void* grad_spectr
  * scenes, sizes, pointers, params, tune) runs eagerly and records the graph; later calls with the
  * same structure replay it, reading the poses (emitter, emitter_quat, dirs, mics) from the job
  * pointers at run time, so callers update them in place between calls.  Omni emitter and receivers;
- * params NULL = defaults; tune NULL = defaults.  Writes every job's spectra_out
+ * either receiver test (params->los_mode); params NULL = defaults; tune NULL = defaults.  ST_ERR_ARG for
+ * a bad job, or with ST_LOS_PER_MIC more than 64 microphones in a job or sum(N M) >= 2^32; ST_ERR_STATE
+ * for a scene not precomputed or of another context.  Writes every job's spectra_out
  * (complex64 [3][n_mics][n_bins]).  Stream-ordered on the context's stream. */
 typedef struct st_job {
     st_scene* scene;            /* precomputed scene */
