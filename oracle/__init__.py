@@ -12,9 +12,12 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   diffraction_cdf    exact integer prefix sums; sample histogram chi-square vs weights
   trace              brute force == BVH bit for bit; shoebox unfolding closed form
   los_per_mic        empty convex room: every microphone visible and spectra equal to the reference-point
-                     test; a plane wall between two microphone groups: the half-space each group is in
+                     test; a plane wall between two microphone groups: the half-space each group is in;
+                     one microphone: identical to the reference-point test
   spectra            single-path closed forms; direct path closed form; reciprocity
-  spectra_grad       float64 central finite differences
+  spectra_grad       float64 central finite differences (also over records with microphone masks)
+  expand_instances   identity maps, exact translations and quarter turns, rotations that keep edge-length
+                     ratios and every triangle's facing
   (absolute scale of spectra against measurements: parity unpinned -- the paper has no data)
 """
 from __future__ import annotations
