@@ -11,6 +11,7 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   curvature, metric  sphere (G ~ 1/R), cylinder side (G ~ 1/(2R)), plane (G = 0)
   diffraction_cdf    exact integer prefix sums; sample histogram chi-square vs weights
   trace              brute force == BVH bit for bit; shoebox unfolding closed form
+  diffraction_filter hand-placed candidates: field of view, incidence limit, line of sight, orientation
   los_per_mic        empty convex room: every microphone visible and spectra equal to the reference-point
                      test; a plane wall between two microphone groups: the half-space each group is in;
                      one microphone: identical to the reference-point test
