@@ -148,3 +148,28 @@ def test_sampling_distribution_and_points():
     ct2, _ = oracle.diffraction_samples(v, f, cd, seed=9, pose=4)
     ct3, _ = oracle.diffraction_samples(v, f, cd, seed=9, pose=3)
     assert not np.array_equal(ct, ct2) and np.array_equal(ct, ct3)
+
+
+def test_curvature_rigid_invariance_and_inverse_length_scaling():
+    """Mean curvature is a geometric invariant: a rotation and translation leave G unchanged and a uniform
+    scale by s divides it by s, on an irregular mesh (a randomly perturbed icosphere, so that no symmetry
+    hides a wrong weight).  The scales are powers of two, so the scaled vertices are exact and only the
+    operator's own float32 rounding differs; a turn and a shift round the moved vertices, so they are
+    compared within a tolerance well above that rounding and far below any wrong weight."""
+    rng = np.random.default_rng(5)
+    v, f = synth.icosphere(3)
+    v = v * (1.0 + 0.15 * rng.uniform(-1, 1, (len(v), 1)))  # bumpy: curvature varies over the mesh
+    v = v.astype(np.float32)
+    f = f.astype(np.int32)
+    G = oracle.curvature(v, f).astype(np.float64)
+    assert G.std() > 0.2 * np.abs(G).mean()  # far from constant
+    for s in (0.25, 4.0):
+        Gs = oracle.curvature((v * np.float32(s)).astype(np.float32), f).astype(np.float64)
+        assert np.allclose(Gs * s, G, rtol=1e-5, atol=1e-6 * np.abs(G).max())
+    # a turn about a tilted axis and a shift
+    a = 0.7
+    R = np.array([[math.cos(a), -math.sin(a), 0.0], [math.sin(a), math.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    R = R @ np.array([[1.0, 0.0, 0.0], [0.0, math.cos(0.4), -math.sin(0.4)], [0.0, math.sin(0.4), math.cos(0.4)]])
+    w = (v.astype(np.float64) @ R.T + np.array([3.0, -5.0, 1.5])).astype(np.float32)
+    Gw = oracle.curvature(w, f).astype(np.float64)
+    assert np.max(np.abs(Gw - G)) <= 1e-3 * np.abs(G).max()
