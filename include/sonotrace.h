@@ -341,23 +341,28 @@ st_status st_impulse_response(st_ctx* ctx, const void* spectra, int32_t n_comp, 
  * laid out as st_get_paths returns them: rec_tri [n_rays][max_bounces] (-1 = no hit), rec_point and
  * rec_dir [n_rays][max_bounces][3], rec_r [n_rays][max_bounces] (float64), rec_los [n_rays]
  * [max_bounces]; tri_material [n_tris]; mics [n_mics][3]; all device pointers.  The material band
- * tables (band_hz [n_bands], k and beta [n_mat][n_bands]) are host pointers.  Omni emitter and
+ * tables (band_hz [n_bands], k and beta [n_mat][n_bands]) are host pointers, read by stream-ordered
+ * copies (keep them unchanged until the call's work on cuda_stream has finished).  Omni emitter and
  * receivers.  Uses params->c, alpha0/alpha1 and reflection_mode (NULL = defaults).  Writes
- * spectra_out, device complex64 [n_mics][n_bins], on cuda_stream.
+ * spectra_out, device complex64 [n_mics][n_bins], on cuda_stream.  max_bounces is 1..8.
+ * Precondition: every triangle id of a visible record's chain is in 0..n_tris-1 and its material in
+ * 0..n_mat-1; a record whose chain breaks this contributes nothing (nothing is read out of range).
  *
  * It calls no allocator.  Its scratch is one array of ST_NOALLOC_SCRATCH_BYTES compiled into the
  * library; every GPU that loads the library holds it until the process exits.  Sizes whose tables
  * plus one chunk of partial spectra (about 8 * n_mics * n_bins + 8 * n_mat * n_bins bytes) exceed
- * it return ST_ERR_ARG.  The first call on a device looks up the array's device address; make that
- * call before any stream capture.  All calls share the array: calls that overlap on the GPU race
- * and give wrong results, so order them on one stream.  No state carries over between calls. */
+ * it return ST_ERR_ARG.  The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture begins.  All calls share the
+ * array: calls that overlap on the GPU race and give wrong results, so order them on one stream.
+ * Every call rewrites all of the scratch it reads, so no state carries over between calls. */
 #define ST_NOALLOC_SCRATCH_BYTES (8u << 20)
 st_status st_accumulate_specular_noalloc(const int32_t* rec_tri, const float* rec_point, const float* rec_dir,
                                          const double* rec_r, const uint8_t* rec_los, int64_t n_rays,
-                                         int32_t max_bounces, const int32_t* tri_material, const float* mics,
-                                         int32_t n_mics, int32_t n_bins, double f_lo, double f_hi, int32_t n_mat,
-                                         int32_t n_bands, const float* band_hz, const float* k, const float* beta,
-                                         const st_sim_params* params, void* spectra_out, void* cuda_stream);
+                                         int32_t max_bounces, const int32_t* tri_material, int64_t n_tris,
+                                         const float* mics, int32_t n_mics, int32_t n_bins, double f_lo,
+                                         double f_hi, int32_t n_mat, int32_t n_bands, const float* band_hz,
+                                         const float* k, const float* beta, const st_sim_params* params,
+                                         void* spectra_out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

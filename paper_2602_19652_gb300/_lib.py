@@ -87,7 +87,7 @@ SIGNATURES = {
     "st_scene_get_geometry": (I32, [P, P, P, P, P, P, P, I32]),
     "st_ray_directions": (I32, [P, I32, I64, P]),
     "st_impulse_response": (I32, [P, P, I32, I32, I32, F64, F64, F64, I32, P, P, I32, I32, P]),
-    "st_accumulate_specular_noalloc": (I32, [P, P, P, P, P, I64, I32, P, P, I32, I32, F64, F64, I32, I32, P, P, P,
+    "st_accumulate_specular_noalloc": (I32, [P, P, P, P, P, I64, I32, P, I64, P, I32, I32, F64, F64, I32, I32, P, P, P,
                                              P, P, P]),
 }
 

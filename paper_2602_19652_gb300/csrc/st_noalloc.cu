@@ -25,6 +25,7 @@ constexpr int kMaxDevices = 64;
 constexpr int kChunksMax = 64;
 constexpr int kThreads = 256;
 constexpr int kTile = 64;
+constexpr int kMaxChain = 8;  // the largest max_bounces the entry point accepts
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -129,7 +130,8 @@ __device__ __forceinline__ ff2 na_sqrt(ff2 x) {
 // memory; each term is evaluated directly (float-float path length and phase reduction, sincospi).
 __global__ void __launch_bounds__(kThreads) k_na_accum(const int32_t* rec_tri, const float* rec_p, const float* rec_d,
                                                        const double* rec_r, const uint8_t* rec_los, int64_t n_rec,
-                                                       int B, const int32_t* tri_mat, const float* mics, int M, int F,
+                                                       int B, const int32_t* tri_mat, int64_t n_tris,
+                                                       const float* mics, int M, int F,
                                                        int n_mat, int reflection_mode, float atm2_0,
                                                        float atm2_step, size_t off_lk, size_t off_g2, size_t off_qhi,
                                                        size_t off_qlo, size_t off_partial, int chunks) {
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_na_accum(const int32_t* rec_tri, c
     const float* qlo = reinterpret_cast<const float*>(g_noalloc_scratch + off_qlo);
     float2* partial = reinterpret_cast<float2*>(g_noalloc_scratch + off_partial);
     __shared__ float sp[kTile][8];       // P.xyz, d'.xyz, r hi, r lo
-    __shared__ int32_t sm[kTile][9];     // valid, chain length, materials
+    __shared__ int32_t sm[kTile][2 + kMaxChain];  // valid, chain length, materials of hits 0..j
     const int64_t o = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool active = o < (int64_t)M * F;
     const int m = active ? (int)(o / F) : 0, k = active ? (int)(o % F) : 0;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_na_accum(const int32_t* rec_tri, c
             sm[t][0] = valid;
             if (valid) {
                 const int64_t ray = id / B;
-                const int j = (int)(id % B);
+                const int j = (int)(id % B);  // j < B <= kMaxChain
                 for (int c = 0; c < 3; ++c) {
                     sp[t][c] = rec_p[3 * id + c];
                     sp[t][3 + c] = rec_d[3 * id + c];
@@ -167,7 +169,18 @@ __global__ void __launch_bounds__(kThreads) k_na_accum(const int32_t* rec_tri, c
                 sp[t][6] = (float)r;
                 sp[t][7] = (float)(r - (double)(float)r);
                 sm[t][1] = j + 1;
-                for (int qq = 0; qq <= j && qq < 8; ++qq) sm[t][2 + qq] = tri_mat[rec_tri[ray * B + qq]];
+                // a chain whose triangle or material id is out of range contributes nothing (the
+                // ids come from the caller; nothing is read outside tri_mat or the tables)
+                for (int qq = 0; qq <= j; ++qq) {
+                    const int32_t tri = rec_tri[ray * B + qq];
+                    const int32_t mat = (tri >= 0 && (int64_t)tri < n_tris) ? tri_mat[tri] : -1;
+                    if (mat < 0 || mat >= n_mat) {
+                        valid = 0;
+                        break;
+                    }
+                    sm[t][2 + qq] = mat;
+                }
+                sm[t][0] = valid;
             }
         }
         __syncthreads();
@@ -223,12 +236,13 @@ __global__ void k_na_reduce(size_t off_partial, int chunks, int64_t MF, float2* 
 extern "C" __attribute__((visibility("default"))) st_status st_accumulate_specular_noalloc(const int32_t* rec_tri, const float* rec_point,
                                                      const float* rec_dir, const double* rec_r, const uint8_t* rec_los,
                                                      int64_t n_rays, int32_t max_bounces, const int32_t* tri_material,
-                                                     const float* mics, int32_t n_mics, int32_t n_bins, double f_lo,
+                                                     int64_t n_tris, const float* mics, int32_t n_mics, int32_t n_bins, double f_lo,
                                                      double f_hi, int32_t n_mat, int32_t n_bands, const float* band_hz,
                                                      const float* k, const float* beta, const st_sim_params* params,
                                                      void* spectra_out, void* cuda_stream) {
     if (!rec_tri || !rec_point || !rec_dir || !rec_r || !rec_los || !tri_material || !mics || !band_hz || !k ||
-        !beta || !spectra_out || n_rays < 0 || max_bounces < 1 || max_bounces > 8 || n_mics < 1 || n_bins < 1 ||
+        !beta || !spectra_out || n_rays < 0 || max_bounces < 1 || max_bounces > kMaxChain || n_tris < 1 ||
+        n_mics < 1 || n_bins < 1 ||
         n_mat < 1 || n_mat > 255 || n_bands < 1 || n_bands > 64 || !(f_lo > 0.0) || !(f_hi >= f_lo))
         return ST_ERR_ARG;
     st_sim_params p;
@@ -271,7 +285,8 @@ extern "C" __attribute__((visibility("default"))) st_status st_accumulate_specul
     dim3 grid((unsigned)((MF + kThreads - 1) / kThreads), (unsigned)chunks);
     st::note_launch();
     k_na_accum<<<grid, kThreads, 0, s>>>(rec_tri, rec_point, rec_dir, rec_r, rec_los, n_rays * max_bounces,
-                                         max_bounces, tri_material, mics, n_mics, n_bins, n_mat, p.reflection_mode,
+                                         max_bounces, tri_material, n_tris, mics, n_mics, n_bins, n_mat,
+                                         p.reflection_mode,
                                          atm2_0, atm2_step, Lo.lk, Lo.g2, Lo.qhi, Lo.qlo, Lo.partial, chunks);
     if (cudaGetLastError() != cudaSuccess) return ST_ERR_CUDA;
     st::note_launch();

@@ -197,3 +197,25 @@ def test_narrow_arrays(st, M, F, mode):
     o = oracle.simulate(wl, curv=dict(budget=20_000), reflection_mode=mode)
     for c in range(3):
         assert rel_l2(S[c], o["spectra"][c]) <= TOL, (M, F, mode, c, rel_l2(S[c], o["spectra"][c]))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_eight_bounces(st, mode):
+    """The largest chain length the interface accepts (B = 8, every byte of the packed material chain in
+    use): the four-material room with the 32-microphone array (general accumulator) in both reflection
+    modes, and a clutter scene with diffraction and one microphone pair (narrow accumulator)."""
+    import oracle
+    wl = synth.shoebox(seed=404, n_rays=3000, bounces=8, n_bins=128, n_mics=32, four_materials=True)
+    ctx, sc, S, stats = gpu_run(st, wl, reflection_mode=mode)
+    o = oracle.simulate(wl, reflection_mode=mode)
+    g = ctx.paths(wl.bounces)
+    compare_paths(g, o["rec"])
+    assert (g["tri"][:, 7] >= 0).sum() > 1000
+    for c in (0, 2):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
+    wl = small_clutter(target_tris=5000, n_rays=4000, n_mics=2, n_bins=300, bounces=8)
+    ctx, sc, S, stats = gpu_run(st, wl, curv=st.curv_params(sample_budget=20_000), reflection_mode=mode)
+    o = oracle.simulate(wl, curv=dict(budget=20_000), reflection_mode=mode)
+    compare_paths(ctx.paths(wl.bounces), o["rec"])
+    for c in range(3):
+        assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
