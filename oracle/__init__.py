@@ -64,6 +64,8 @@ def _declare(L):
     L.ora_weld.restype = C.c_int
     L.ora_curvature.argtypes = [I64, P, I64, P, P]
     L.ora_curvature.restype = C.c_int
+    L.ora_curvature_mixed.argtypes = [I64, P, I64, P, P, P]
+    L.ora_curvature_mixed.restype = C.c_int
     L.ora_tri_metric.argtypes = [I64, P, I64, P, P, F32, F32, P]
     L.ora_diffraction_cdf.argtypes = [I64, P, I64, P, P, P, I32, F64, U64, F32, I32, I64, P, P, P, P]
     L.ora_diffraction_cdf.restype = C.c_int
@@ -123,12 +125,14 @@ def weld(verts):
     return out
 
 
-def curvature(verts, tris):
+def curvature(verts, tris, mixed_area=False):
+    """G_v per input vertex; with mixed_area, also each vertex's mixed area A_mixed (Meyer et al.)."""
     v, t = _c(verts, np.float32), _c(tris, np.int32)
     G = np.zeros(len(v), dtype=np.float32)
-    if lib().ora_curvature(len(v), _p(v), len(t), _p(t), _p(G)) != 0:
+    A = np.zeros(len(v), dtype=np.float32) if mixed_area else None
+    if lib().ora_curvature_mixed(len(v), _p(v), len(t), _p(t), _p(G), _p(A)) != 0:
         raise MemoryError("oracle curvature")
-    return G
+    return (G, A) if mixed_area else G
 
 
 def tri_metric(verts, tris, G, eta=1.0, area_ref=1e-4):

@@ -177,7 +177,16 @@ ORA_API int ora_weld(int64_t nv, const float* V, int32_t* canon) {
  * vertices use the same formula over the triangles they have.  G is written per input vertex
  * (every copy of a welded vertex receives the value of its canonical vertex).
  */
+ORA_API int ora_curvature_mixed(int64_t nv, const float* V, int64_t nt, const int32_t* tris, float* G,
+                                float* A_mixed);
 ORA_API int ora_curvature(int64_t nv, const float* V, int64_t nt, const int32_t* tris, float* G) {
+    return ora_curvature_mixed(nv, V, nt, tris, G, NULL);
+}
+
+/* As ora_curvature; A_mixed (NULL or [nv]) also receives each vertex's mixed area (per input vertex,
+ * the canonical vertex's value), the denominator of K_v. */
+ORA_API int ora_curvature_mixed(int64_t nv, const float* V, int64_t nt, const int32_t* tris, float* G,
+                                float* A_mixed) {
     int32_t* canon = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
     int64_t* off = (int64_t*)calloc((size_t)nv + 1, sizeof(int64_t));
     if (!canon || !off) return -1;
@@ -197,6 +206,7 @@ ORA_API int ora_curvature(int64_t nv, const float* V, int64_t nt, const int32_t*
             if (!dup) adj[fill[cv]++] = (int32_t)t;
         }
     float* Gc = (float*)calloc((size_t)nv + 1, sizeof(float));
+    float* Ac = (float*)calloc((size_t)nv + 1, sizeof(float));
     for (int64_t v = 0; v < nv; ++v) {
         if (canon[v] != v) continue;
         float S[3] = {0.0f, 0.0f, 0.0f};
@@ -251,9 +261,12 @@ ORA_API int ora_curvature(int64_t nv, const float* V, int64_t nt, const int32_t*
             g = 0.5f * sqrtf(dot3f(K, K));
         }
         Gc[v] = g;
+        Ac[v] = Amix;
     }
     for (int64_t v = 0; v < nv; ++v) G[v] = Gc[canon[v]];
-    free(Gc); free(adj); free(fill); free(off); free(canon);
+    if (A_mixed)
+        for (int64_t v = 0; v < nv; ++v) A_mixed[v] = Ac[canon[v]];
+    free(Ac); free(Gc); free(adj); free(fill); free(off); free(canon);
     return 0;
 }
 

@@ -84,6 +84,27 @@ def icosphere(subdiv: int):
     return v, f
 
 
+def uv_sphere(n_lat: int, n_lon: int):
+    """Unit latitude-longitude sphere: two pole vertices, n_lat - 1 rings of n_lon vertices, each quad
+    between rings split along one diagonal, pole fans (about half of its triangles are obtuse)."""
+    V = [[0.0, 0.0, 1.0]]
+    for i in range(1, n_lat):
+        th = math.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2.0 * math.pi * j / n_lon
+            V.append([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    V.append([0.0, 0.0, -1.0])
+    south = len(V) - 1
+    F = [[0, 1 + j, 1 + (j + 1) % n_lon] for j in range(n_lon)]
+    for i in range(n_lat - 2):
+        for j in range(n_lon):
+            a, b = 1 + i * n_lon + j, 1 + i * n_lon + (j + 1) % n_lon
+            F += [[a, a + n_lon, b + n_lon], [a, b + n_lon, b]]
+    last = 1 + (n_lat - 2) * n_lon
+    F += [[last + j, south, last + (j + 1) % n_lon] for j in range(n_lon)]
+    return np.array(V, dtype=np.float64), np.array(F, dtype=np.int64)
+
+
 def cylinder(radius: float, height: float, seg: int):
     """Closed vertical cylinder (side quads + two cap fans), base at z=0."""
     a = np.arange(seg) * (2.0 * math.pi / seg)

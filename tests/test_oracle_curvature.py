@@ -173,3 +173,106 @@ def test_curvature_rigid_invariance_and_inverse_length_scaling():
     w = (v.astype(np.float64) @ R.T + np.array([3.0, -5.0, 1.5])).astype(np.float32)
     Gw = oracle.curvature(w, f).astype(np.float64)
     assert np.max(np.abs(Gw - G)) <= 1e-3 * np.abs(G).max()
+
+
+def _obtuse_triangles(v, f):
+    p = v.astype(np.float64)[f]
+    n = 0
+    for k in range(3):
+        a = p[:, (k + 1) % 3] - p[:, k]
+        b = p[:, (k + 2) % 3] - p[:, k]
+        n += int(((a * b).sum(1) < 0).sum())
+    return n
+
+
+def _voronoi_cells(p):
+    """Areas of the three Voronoi cells of a non-obtuse planar triangle p [3][2], built from its
+    circumcentre: cell of vertex i = polygon (p_i, midpoint to p_j, circumcentre, midpoint to p_k)."""
+    (ax, ay), (bx, by), (cx, cy) = p
+    d = 2.0 * (ax * (by - cy) + bx * (cy - ay) + cx * (ay - by))
+    ux = ((ax * ax + ay * ay) * (by - cy) + (bx * bx + by * by) * (cy - ay) + (cx * cx + cy * cy) * (ay - by)) / d
+    uy = ((ax * ax + ay * ay) * (cx - bx) + (bx * bx + by * by) * (ax - cx) + (cx * cx + cy * cy) * (bx - ax)) / d
+    out = []
+    for i in range(3):
+        P0, P1, P2 = p[i], p[(i + 1) % 3], p[(i + 2) % 3]
+        poly = [P0, (P0 + P1) / 2, np.array([ux, uy]), (P0 + P2) / 2]
+        s = sum(poly[q][0] * poly[(q + 1) % 4][1] - poly[(q + 1) % 4][0] * poly[q][1] for q in range(4))
+        out.append(abs(s) / 2)
+    return np.array(out)
+
+
+def test_mixed_area_of_single_triangles():
+    """Meyer et al.'s mixed area at each vertex of one triangle, from the geometry alone: a non-obtuse
+    triangle gives each vertex its Voronoi cell (circumcentre construction, shoelace areas: 11/16, 11/16
+    and 5/8 for (0,0), (2,0), (1,2)); a right angle gives its vertex half the area; an obtuse triangle
+    gives half its area to the obtuse vertex and a quarter to each other vertex, wherever the obtuse
+    vertex sits in the triangle's order.  A mixed area that takes the Voronoi formula for obtuse
+    triangles, or swaps the halves and quarters, fails here."""
+    cases = [
+        ([[0, 0, 0], [2, 0, 0], [1, 2, 0]], [0.6875, 0.6875, 0.625]),
+        ([[0, 0, 0], [1, 0, 0], [0, 1, 0]], [0.25, 0.125, 0.125]),
+        ([[0, 0, 0], [4, 0, 0], [2, 1, 0]], [0.5, 0.5, 1.0]),
+        ([[2, 1, 0], [0, 0, 0], [4, 0, 0]], [1.0, 0.5, 0.5]),
+        ([[0, 0, 0], [2, 1, 0], [4, 0, 0]], [0.5, 1.0, 0.5]),
+    ]
+    f = np.array([[0, 1, 2]], np.int32)
+    for v, want in cases:
+        v = np.array(v, np.float32)
+        _, A = oracle.curvature(v, f, mixed_area=True)
+        assert np.allclose(A, want, rtol=1e-6), (v.tolist(), A, want)
+        # the same triangle tilted into 3-D by a turn about (1, 2, 3): the areas do not change
+        ax = np.array([1.0, 2.0, 3.0]) / math.sqrt(14.0)
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        R = np.eye(3) + math.sin(0.9) * K + (1 - math.cos(0.9)) * K @ K
+        _, A3 = oracle.curvature((v.astype(np.float64) @ R.T).astype(np.float32), f, mixed_area=True)
+        assert np.allclose(A3, want, rtol=1e-5), (A3, want)
+    # random acute triangles against the circumcentre construction
+    rng = np.random.default_rng(8)
+    n = 0
+    while n < 50:
+        p = rng.uniform(-1, 1, (3, 2))
+        e = [p[(k + 1) % 3] - p[k] for k in range(3)]
+        if min(np.dot(e[k], -e[(k + 2) % 3]) for k in range(3)) <= 0.05:
+            continue                                    # keep clearly acute triangles only
+        n += 1
+        v = np.concatenate([p, np.zeros((3, 1))], 1).astype(np.float32)
+        _, A = oracle.curvature(v, f, mixed_area=True)
+        assert np.allclose(A, _voronoi_cells(v[:, :2].astype(np.float64)), rtol=2e-5)
+
+
+@pytest.mark.parametrize("mesh", ["bumpy_icosphere", "uv_sphere", "three_sided_cylinder"])
+def test_mixed_areas_tile_the_surface(mesh):
+    """The mixed areas partition every triangle among its vertices (Voronoi cells of a non-obtuse
+    triangle, 1/2 + 1/4 + 1/4 of an obtuse one), so over a closed mesh they add up to its area.  Each
+    mesh here has obtuse triangles: a bumpy icosphere (147 of 1,280), a latitude-longitude sphere (about
+    half) and a cylinder with three sides (its cap fans are obtuse at the centre).  Swapping the half
+    and the quarter gives 5/4 of every obtuse triangle's area."""
+    if mesh == "bumpy_icosphere":
+        rng = np.random.default_rng(5)
+        v, f = synth.icosphere(3)
+        v = v * (1.0 + 0.15 * rng.uniform(-1, 1, (len(v), 1)))
+    elif mesh == "uv_sphere":
+        v, f = synth.uv_sphere(24, 48)
+        v = 0.7 * v
+    else:
+        v, f = synth.cylinder(0.1, 0.4, 3)
+    v, f = v.astype(np.float32), f.astype(np.int32)
+    assert _obtuse_triangles(v, f) > 0
+    _, A = oracle.curvature(v, f, mixed_area=True)
+    canon = oracle.weld(v)
+    total = A[np.unique(canon)].astype(np.float64).sum()
+    p = v.astype(np.float64)[f]
+    area = 0.5 * np.linalg.norm(np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), axis=1).sum()
+    assert abs(total - area) <= 1e-5 * area, (total, area)
+    assert np.all(A > 0)
+
+
+@pytest.mark.parametrize("R", [0.4, 3.0])
+def test_uv_sphere_curvature(R):
+    """Mean curvature 1/R on a latitude-longitude sphere, whose triangles are about half obtuse (so
+    the obtuse branches of the mixed area carry most vertices' denominators), within 1 %."""
+    v, f = synth.uv_sphere(24, 48)
+    v, f = (R * v).astype(np.float32), f.astype(np.int32)
+    assert _obtuse_triangles(v, f) > len(f) // 3
+    G = oracle.curvature(v, f)
+    assert np.allclose(G, 1.0 / R, rtol=0.01), np.abs(G * R - 1).max()
