@@ -31,13 +31,77 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-METRIC = "Mrays/s (closest-hit + any-hit segments per second, spectra at <=1e-4 rel-L2 vs oracle)"
+METRIC = "Mrays/s (closest + any-hit segments/s; spectra <=1e-4 rel-L2 vs oracle)"
 UNIT = "Mrays/s"
 FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by-complex multiply-accumulate (4)
-# dram__bytes_read.sum + dram__bytes_write.sum per k_accum launch on this workload, from an ncu capture of the
-# current kernel (the diffraction launch at full size, the specular launch on 200k rays scaled by the visible
-# records: the path list is read once); set to None when the kernel changes until it is captured again
-ACCUM_DRAM_BYTES_PER_LAUNCH = 34.81e6
+# dram__bytes_read.sum + dram__bytes_write.sum per k_accum launch on the clutter workload, from an ncu capture
+# (the diffraction launch at full size, the specular launch on 200k rays scaled by the visible records: the path
+# list is read once), with the hash of the accumulator's sources it was taken on: the bench reports it only while
+# the sources still hash to that value (else null, until the kernel is captured again)
+ACCUM_TRAFFIC = {"sources_sha16": "", "bytes_per_launch": None}
+ACCUM_SOURCES = ("st_accum.cu", "st_accum_dev.cuh", "st_internal.cuh")
+
+
+def accum_sources_sha16():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ACCUM_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_19652_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def accum_roofline(stats_list, n_sm, sm_mhz, peak_src, kernel="k_accum (spectrum accumulator)", traffic=None):
+    """FP32 roofline of the accumulator launches of the given simulate steps: 10 flops per (path, mic, bin)
+    term over the launches' device time, against 128 FP32 lanes x 2 x the SM clock per SM."""
+    acc_ms = sum(s.ms_accum_kernel for s in stats_list)
+    launches = sum(s.accum_launches for s in stats_list)
+    terms = sum(s.terms for s in stats_list)
+    peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_TERM * terms / (acc_ms / 1e3) / 1e12 if acc_ms > 0 else 0.0
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {peak_src})",
+            "work": f"{FLOPS_PER_TERM} FP32 flops per (path, mic, bin) term, {terms / max(launches, 1):.3e} "
+                    f"terms per launch", "ms_per_launch": acc_ms / max(launches, 1), "traffic": traffic}
+
+
+def e2e_simulate(st, ctx, sc, wl, params, n_steps):
+    """Seconds and bytes of n_steps simulates through the C ABI with host buffers: the emitter's ray set and
+    the receivers copied in from host memory and the spectra returned to host memory by every call."""
+    import ctypes as C
+    import torch
+    L = st.load()
+    dirs_h = torch.from_numpy(np.ascontiguousarray(wl.dirs)).pin_memory()
+    mics_h = np.ascontiguousarray(wl.mics, np.float32)
+    spec_h = np.empty((3, len(wl.mics), wl.n_bins), np.complex64)
+    pos = np.ascontiguousarray(wl.emitter, np.float32)
+    quat = np.ascontiguousarray(wl.emitter_quat, np.float32)
+    cp = lambda a: a.ctypes.data_as(C.c_void_p)
+    etab = None if wl.emitter_table is None else np.ascontiguousarray(wl.emitter_table, np.float32)
+    mq = None if wl.mic_quats is None else np.ascontiguousarray(wl.mic_quats, np.float32)
+    mt = None if wl.mic_tables is None else np.ascontiguousarray(wl.mic_tables, np.float32)
+
+    def one():
+        st.check(L.st_set_emitter(ctx.h, cp(pos), cp(quat), len(wl.dirs), C.c_void_p(dirs_h.data_ptr()),
+                                  None if etab is None else cp(etab), 0 if etab is None else etab.shape[0],
+                                  float(np.float32(wl.fov_half)), st.ST_MEM_HOST), ctx.h)
+        st.check(L.st_set_receivers(ctx.h, len(mics_h), cp(mics_h), None if mq is None else cp(mq),
+                                    None if mt is None else cp(mt), 0 if mt is None else mt.shape[1],
+                                    0 if mt is None else mt.shape[2], 0 if mt is None else mt.shape[3],
+                                    st.ST_MEM_HOST), ctx.h)
+        st.check(L.st_simulate_host(ctx.h, sc.h, C.byref(params), cp(spec_h), None), ctx.h)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        one()  # each call returns with its spectra on the host
+    dt = time.perf_counter() - t0
+    h2d = wl.dirs.nbytes + mics_h.nbytes + pos.nbytes + quat.nbytes + sum(
+        a.nbytes for a in (etab, mq, mt) if a is not None)
+    return dt, int(h2d), int(spec_h.nbytes)
 
 
 def load_peaks():
@@ -68,7 +132,7 @@ def workload_config(wl, args):
             "bins": wl.n_bins, "diffraction": bool(wl.diffraction),
             "step": "scene precompute + simulate" if args.include_precompute else "simulate (scene prebuilt)",
             "l2": "flushed between steps (256 MiB write)",
-            "parallelism": f"{args.gpus} independent poses (one per GPU)"}
+            "parallelism": f"{args.gpus} pose(s), one per GPU"}
 
 
 class ClockSampler:
@@ -409,9 +473,10 @@ def measure_instances(st, torch, n_inst: int = 8000, n_rays: int = 1_000_000, re
     return res
 
 
-def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: int = 0):
+def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: int = 0, roofline=None, e2e=False):
     """Device time of one simulate on another workload (scene prebuilt, L2 flushed before each step);
-    los_mode 1: the receiver test of every hit made per microphone."""
+    los_mode 1: the receiver test of every hit made per microphone.  roofline = (n_sm, sm_mhz, peak_src):
+    also the accumulator's FP32 roofline; e2e: also the end-to-end rate through host buffers."""
     dev = torch.cuda.current_device()
     ctx = st.Context(dev)
     sc = st.from_workload(ctx, wl)
@@ -422,7 +487,7 @@ def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: i
     for _ in range(warmup):
         ctx.simulate(sc, p, out=out)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ms, segs, stats = [], 0, None
+    ms, segs, stats, all_stats = [], 0, None, []
     for i in range(steps):
         flush.fill_(i & 255)
         ev[0].record(stream)
@@ -431,6 +496,7 @@ def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: i
         torch.cuda.synchronize()
         ms.append(ev[0].elapsed_time(ev[1]))
         segs += stats.closest_queries + stats.shadow_queries
+        all_stats.append(stats)
     t = float(sum(ms))
     res = {"config": f"{wl.name}: {wl.n_tris} triangles, {len(wl.dirs)} rays x {wl.bounces} bounces, "
                      f"{len(wl.mics)} mics, {wl.n_bins} bins, diffraction {'on' if wl.diffraction else 'off'}",
@@ -439,6 +505,15 @@ def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: i
            "ms_trace": stats.ms_trace, "ms_diffraction": stats.ms_diffraction, "ms_accumulate": stats.ms_accumulate,
            "visible_records": stats.visible_records, "diffraction_kept": stats.candidates_kept,
            "anyhit_segments": stats.shadow_queries}
+    if roofline is not None:
+        n_sm, sm_mhz, peak_src = roofline
+        kern = "k_accum_narrow (one microphone pair)" if len(wl.mics) <= 2 else "k_accum (spectrum accumulator)"
+        res["roofline"] = accum_roofline(all_stats, n_sm, sm_mhz, peak_src, kernel=kern)
+    if e2e:
+        n = max(3, steps)
+        dt, h2d, d2h = e2e_simulate(st, ctx, sc, wl, p, n)
+        res["e2e"] = {"value": segs / steps * n / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / n}
     ctx.close()
     return res
 
@@ -612,6 +687,60 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _r(x, n=4):
+    """x rounded to n significant digits (floats only)."""
+    if isinstance(x, float) and x != 0.0 and math.isfinite(x):
+        return round(x, n - 1 - int(math.floor(math.log10(abs(x)))))
+    return x
+
+
+def compact_line(d):
+    """The headline line: the contract's keys, with every other part of the metric (backward / forward
+    time, batched vs plain, the vegetation workload's rate, roofline and end-to-end rate) in short form."""
+    rf = d["roofline"]
+    line = {k: d[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                              "higher_is_better", "scaling", "vs_baseline", "dtype", "data")}
+    line["value"], line["ms_per_step"] = _r(line["value"], 6), _r(line["ms_per_step"], 5)
+    c = d["config"]
+    line["config"] = {"workload": f"{c['workload'].split(':')[0]}: {c['triangles']} tris, {c['rays']} rays x "
+                                  f"{c['bounces']} bounces, {c['mics']} mics x {c['bins']} bins"
+                                  f"{', diffraction' if c['diffraction'] else ''}",
+                      "step": c["step"], "l2": "flushed (256 MiB write)", "parallelism": c["parallelism"]}
+    line["roofline"] = {"bound": rf["bound"], "kernel": rf["kernel"].split(" ")[0], "achieved": _r(rf["achieved"]),
+                        "peak": _r(rf["peak"]), "unit": rf["unit"], "frac": _r(rf["frac"]), "traffic": rf["traffic"]}
+    cb = d.get("cpu_baseline")
+    if cb:
+        line["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"],
+                                "kind": cb["kind"], "sample": cb["sample_short"]}
+    else:
+        line["cpu_baseline"] = None
+    e = d["e2e"]
+    line["e2e"] = {"value": _r(e["value"]), "unit": e["unit"], "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                   "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
+    ck = d["clocks"]
+    line["clocks"] = {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons")}
+    line["gpu_launches"] = d["gpu_launches"]
+    line["mic_spectra_per_s"] = _r(d["mic_spectra_per_s"])
+    if d.get("adjoint"):
+        line["bwd_over_fwd"] = {("gradient" if k.startswith("gradient") else k.split(" ")[0]): _r(v["bwd_over_fwd"], 3)
+                                for k, v in d["adjoint"].items()}
+    if d.get("batched"):
+        b = d["batched"]
+        line["batched_vs_plain"] = {"speedup": _r(b["speedup"], 3), "batched_ms": _r(b["batched_ms"]),
+                                    "plain_ms": _r(b["plain_ms"]), "poses": 256}
+    v = d.get("vegetation")
+    if v:
+        vr, ve = v["roofline"], v["e2e"]
+        line["vegetation"] = {"value": _r(v["value"]), "ms_per_step": _r(v["ms_per_step"]),
+                              "roofline": {"bound": vr["bound"], "kernel": vr["kernel"].split(" ")[0],
+                                           "achieved": _r(vr["achieved"]), "peak": _r(vr["peak"]),
+                                           "unit": vr["unit"], "frac": _r(vr["frac"]), "traffic": vr["traffic"]},
+                              "e2e": {"value": _r(ve["value"]), "unit": ve["unit"],
+                                      "h2d_bytes_per_step": ve["h2d_bytes_per_step"],
+                                      "d2h_bytes_per_step": ve["d2h_bytes_per_step"]}}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -694,57 +823,23 @@ def main():
                                                           [segs, len(wl.mics) * args.steps], dev)
     value = segs_all / (total_ms_all / 1e3) / 1e6
 
-    # ---- dominant kernel: the accumulator (FP32/XU-pipe arithmetic)
-    acc_ms = sum(s.ms_accum_kernel for s in st_list)
-    acc_launches = sum(s.accum_launches for s in st_list)
-    terms = sum(s.terms for s in st_list)
+    # ---- dominant kernel: the accumulator (FP32-pipe arithmetic)
     clocks = clk.summary()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = FLOPS_PER_TERM * terms / (acc_ms / 1e3) / 1e12 if acc_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_accum (spectrum accumulator)", "achieved": achieved, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {peak_src})",
-                "work": f"{FLOPS_PER_TERM} FP32 flops per (path, mic, bin) term, {terms / max(acc_launches, 1):.3e} "
-                        f"terms per launch", "ms_per_launch": acc_ms / max(acc_launches, 1),
-                "traffic": ACCUM_DRAM_BYTES_PER_LAUNCH}
+    traffic = ACCUM_TRAFFIC["bytes_per_launch"] if ACCUM_TRAFFIC["sources_sha16"] == accum_sources_sha16() else None
+    roofline = accum_roofline(st_list, n_sm, sm_mhz, peak_src, traffic=traffic)
 
     # ---- end to end through the C ABI with host buffers
-    e2e = None
-    if True:
-        dirs_h = torch.from_numpy(np.ascontiguousarray(wl.dirs)).pin_memory()
-        mics_h = np.ascontiguousarray(wl.mics, np.float32)
-        spec_h = np.empty((3, len(wl.mics), wl.n_bins), np.complex64)
-        import ctypes as C
-        L = st.load()
-        pos = np.ascontiguousarray(wl.emitter, np.float32)
-        quat = np.ascontiguousarray(wl.emitter_quat, np.float32)
-        cp = lambda a: a.ctypes.data_as(C.c_void_p)
-
-        def e2e_step():
-            st.check(L.st_set_emitter(ctx.h, cp(pos), cp(quat), len(wl.dirs), C.c_void_p(dirs_h.data_ptr()),
-                                      None, 0, float(np.float32(wl.fov_half)), st.ST_MEM_HOST), ctx.h)
-            st.check(L.st_set_receivers(ctx.h, len(mics_h), cp(mics_h), None, None, 0, 0, 0, st.ST_MEM_HOST), ctx.h)
-            if args.include_precompute:
-                sc.precompute()
-            st.check(L.st_simulate_host(ctx.h, sc.h, C.byref(params), cp(spec_h), None), ctx.h)
-
-        for _ in range(2):
-            e2e_step()
-        n_e2e = max(3, args.steps // 2)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for i in range(n_e2e):
-            e2e_step()  # host buffers in and out: each call returns with its spectra on the host
-        t_e2e = time.perf_counter() - t0
-        (t_e2e_max,), (segs_e2e,) = over_ranks(dist, world, [t_e2e], [segs / len(st_list) * n_e2e], dev)
-        h2d = wl.dirs.nbytes + mics_h.nbytes + pos.nbytes + quat.nbytes
-        e2e = {"value": segs_e2e / t_e2e_max / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(spec_h.nbytes),
-               "ms_per_step": 1e3 * t_e2e_max / n_e2e}
+    if world > 1:
+        dist.barrier()
+    n_e2e = max(3, args.steps // 2)
+    if args.include_precompute:
+        sc.precompute()
+    t_e2e, h2d, d2h = e2e_simulate(st, ctx, sc, wl, params, n_e2e)
+    (t_e2e_max,), (segs_e2e,) = over_ranks(dist, world, [t_e2e], [segs / len(st_list) * n_e2e], dev)
+    e2e = {"value": segs_e2e / t_e2e_max / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": 1e3 * t_e2e_max / n_e2e}
 
     # the remaining measurements run on rank 0 alone
     if rank != 0:
@@ -767,7 +862,8 @@ def main():
         batched = measure_batched(st, torch)
     vegetation = None
     if not args.no_vegetation and args.workload != "vegetation":
-        vegetation = measure_workload(st, torch, synth.vegetation(seed=303))
+        vegetation = measure_workload(st, torch, synth.vegetation(seed=303), roofline=(n_sm, sm_mhz, peak_src),
+                                      e2e=True)
     per_mic = None
     if not args.no_per_mic and len(wl.mics) <= 64:
         per_mic = measure_workload(st, torch, wl, los_mode=st.ST_LOS_PER_MIC)
@@ -782,12 +878,14 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         segs_c, dt_c, desc = oracle_sample(wl, args.cpu_rays)
         cpu = {"value": segs_c / dt_c / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
-               "seconds": dt_c}
+               "seconds": dt_c,
+               "sample_short": f"1/{max(1, len(wl.dirs) // args.cpu_rays)} of the rays and diffraction samples, "
+                               f"all mics x bins, {dt_c:.1f} s"}
 
     s0 = st_list[-1]
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    detail = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (float-float path lengths and phases)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (float-float r and phase)",
             "data": "synthetic", "config": workload_config(wl, args),
             "mic_spectra_per_s": spectra_all / (total_ms_all / 1e3),
             "per_step": {"closest_segments": s0.closest_queries, "anyhit_segments": s0.shadow_queries,
@@ -800,7 +898,10 @@ def main():
             "vegetation": vegetation, "receiver_test_per_mic": per_mic, "emitters": emitters,
             "instances": instances,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}
-    print(json.dumps(line))
+    # every measurement in full on stderr; stdout carries one compact line (the headline with the
+    # figures of the metric's other parts), short enough to be kept whole by a reader of the last 1.5 kB
+    print("bench detail " + json.dumps(detail), file=sys.stderr)
+    print(json.dumps(compact_line(detail), separators=(",", ":")))
     if world > 1:
         dist.destroy_process_group()
 

@@ -42,7 +42,7 @@ typedef int32_t st_status;
 #define ST_ERR_MESH (-4)     /* index out of range or non-finite vertex in the mesh */
 #define ST_ERR_TIMEOUT (-5)  /* a bounded device-side wait gave up */
 #define ST_ERR_STATE (-6)    /* call out of order (e.g. simulate before set_receivers) */
-#define ST_ERR_OVERFLOW (-7) /* a fixed-size device structure overflowed (traversal stack) */
+#define ST_ERR_OVERFLOW (-7) /* a fixed-size device structure overflowed (reserved: the traversal stack restarts instead) */
 
 #define ST_MEM_HOST 0
 #define ST_MEM_DEVICE 1
@@ -113,6 +113,7 @@ typedef struct st_stats {
     int64_t kernel_launches;    /* kernels launched by this call */
     int64_t visits[4];          /* with ST_COUNT_VISITS=1: BVH nodes and triangles visited by closest-hit
                                    queries, then by any-hit queries (0 otherwise) */
+    int64_t stack_restarts;     /* traversal queries that outgrew their stack and restarted from the root */
 } st_stats;
 
 /* Fill a parameter block with the library defaults (every field; the caller owns the block). */
@@ -211,6 +212,13 @@ st_status st_set_receivers(st_ctx* ctx, int32_t n_mics, const float* pos, const 
 /* Uniform frequency grid f_k = f_lo + k (f_hi - f_lo) / (n_bins - 1), k = 0..n_bins-1, Hz (one bin: f_lo).
  * 1..2^20 bins and 0 < f_lo < f_hi (ST_ERR_ARG otherwise). */
 st_status st_set_frequencies(st_ctx* ctx, int32_t n_bins, double f_lo, double f_hi);
+/* The same grid given as its bins, f_hz [n_bins] ascending, Hz, host memory (the paper's frequency
+ * bins of the spectra, Sec. III-C / III-F).  The accumulators advance each path's phasor by one
+ * constant bin spacing, so the bins must be uniformly spaced: every inner bin within 4 float32 ulps
+ * of f_hz[0] + k (f_hz[n-1] - f_hz[0]) / (n - 1).  Then equal to st_set_frequencies(n_bins,
+ * f_hz[0], f_hz[n_bins-1]).  Errors: ST_ERR_ARG for a null pointer, 0 or more than 2^20 bins,
+ * f_hz[0] <= 0, bins not strictly ascending or not uniformly spaced (the context keeps its grid). */
+st_status st_set_frequency_grid(st_ctx* ctx, int32_t n_bins, const float* f_hz);
 
 /* One simulation: tracing, diffraction, direct path, accumulation.  spectra_out is caller-owned
  * device memory of 3 * n_mics * n_bins complex64 values laid out [component][mic][bin]; every
@@ -289,11 +297,17 @@ typedef struct st_tune {
     int32_t rays_per_block;     /* tracing block size: 64, 128 or 256 */
     int32_t mic_pairs_per_cta;  /* accumulator: microphone pairs per CTA, 1..16 */
     int32_t smem_kb;            /* accumulator: shared-memory budget per CTA, 32..160 KB */
-    int32_t reserved;
+    int32_t stack_depth;        /* traversal stack entries per query, 1..128 (0 = 128).  A query that would
+                                   need more restarts from the root with a walk that needs no stack (fixed
+                                   child order, parent references in the nodes), keeping its best hit, so
+                                   results do not depend on it; st_stats.stack_restarts counts the restarts */
 } st_tune;
 
 st_status st_simulate_batch(st_ctx* ctx, int32_t n_jobs, const st_job* jobs, const st_sim_params* params,
                             const st_tune* tune);
+/* Sets the context's launch shapes (as st_autotune does); later st_simulate calls use them.  ST_ERR_ARG for
+ * a null pointer or a value outside the ranges above. */
+st_status st_set_tune(st_ctx* ctx, const st_tune* tune);
 /* Times candidate launch shapes on one sample job through the single-pose path and writes the
  * fastest to *out (also kept as the context's default for st_simulate).  Replaces the context's
  * emitter, receivers and frequency grid with the sample job's (omni).  Synchronises. */
@@ -331,6 +345,12 @@ st_status st_ray_directions(st_ctx* ctx, int32_t kind, int64_t n, float* out);
 st_status st_impulse_response(st_ctx* ctx, const void* spectra, int32_t n_comp, int32_t n_mics, int32_t n_bins,
                               double f_lo, double f_hi, double fs, int32_t n_samples, const float* window,
                               const float* call, int32_t call_len, int32_t flags, float* out);
+
+/* Testing hook for the failure paths (no counterpart in the paper): after `after` further device
+ * allocations by this library succeed, the next one fails as cudaMalloc does when the device is out of
+ * memory (the call that needs it returns ST_ERR_OOM; no memory is allocated for it), and injection
+ * switches off.  after < 0 switches it off.  Process-wide, not thread-safe; the library never calls it. */
+void st_inject_alloc_failure(int64_t after);
 
 /* Allocation-free specular accumulation.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory where they need spectra -- code running inside another

@@ -254,7 +254,8 @@ def diffraction_filter(scene: Scene, s, q, cand_tri, cand_p, fov_half=math.pi, c
 
 
 def los_per_mic(scene: Scene, rec, mics, t_min=1e-5, los_eps=1e-4, nthreads=0):
-    """Receiver test per microphone (the variant of reading 6 with one visibility ray per microphone):
+    """Receiver test per microphone (Algorithm 1 leaves the receiver test unstated; the default casts one
+    visibility ray per hit towards the microphones' centroid, this variant one ray per microphone):
     returns rec with 'mask' (uint64 [N][B], bit m = microphone m visible from the hit point) and 'los'
     (any microphone visible).  M <= 64."""
     m = _c(mics, np.float32)

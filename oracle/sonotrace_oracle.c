@@ -785,8 +785,9 @@ ORA_API int ora_trace(void* scene, const float* nrm, const float s[3], const flo
 }
 
 /*
- * Receiver test per microphone (the variant of reading 6 with one visibility ray per microphone instead of
- * one towards the receiver reference point): bit m of rec_mask[id] is set when microphone m is visible from
+ * Receiver test per microphone.  Algorithm 1 leaves the receiver test unstated; the default test casts one
+ * visibility ray per hit towards the receiver reference point (the microphones' centroid), this variant
+ * one ray per microphone: bit m of rec_mask[id] is set when microphone m is visible from
  * the record's hit point (the hit triangle excluded, stopping los_eps short), and rec_los[id] becomes 1
  * when any bit is.  Records without a hit (tri < 0) get 0.  M <= 64.
  */

@@ -14,8 +14,8 @@ import torch
 
 from . import _lib
 from .autograd import SpectraFn  # noqa: E402
-from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_ERR_ARG, ST_ERR_MESH, ST_ERR_STATE,
-                   ST_LOS_PER_MIC, ST_LOS_REFERENCE, ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
+from ._lib import (ST_COMP_DIFFRACTION, ST_COMP_DIRECT, ST_COMP_SPECULAR, ST_ERR_ARG, ST_ERR_MESH, ST_ERR_OOM,
+                   ST_ERR_OVERFLOW, ST_ERR_STATE, ST_LOS_PER_MIC, ST_LOS_REFERENCE, ST_MEM_DEVICE, ST_MEM_HOST, CurvParams,
                    Job, SimParams, SonotraceError, Stats, Tune, check, load)
 
 __all__ = ["Context", "Scene", "BatchJob", "SpectraFn", "CurvParams", "SimParams", "Stats", "Tune", "SonotraceError",
@@ -81,6 +81,12 @@ class Context:
     def set_frequencies(self, n_bins: int, f_lo: float, f_hi: float):
         self._check(self.L.st_set_frequencies(self.h, int(n_bins), float(f_lo), float(f_hi)))
         self.F = int(n_bins)
+
+    def set_frequency_grid(self, f_hz):
+        """The frequency bins as an ascending, uniformly spaced array (Hz)."""
+        f = np.ascontiguousarray(f_hz, dtype=np.float32).reshape(-1)
+        self._check(self.L.st_set_frequency_grid(self.h, int(len(f)), f.ctypes.data_as(C.c_void_p)))
+        self.F = int(len(f))
 
     def set_emitter(self, pos, quat, dirs, table=None, fov_half: float = math.pi):
         self.quat, self.dirs, self.fov_half = quat, dirs, fov_half
@@ -253,6 +259,11 @@ class Context:
                 for i, j in enumerate(self._emit_jobs):
                     j.set_pose(emitter=E[i], emitter_quat=Q[i])
             return torch.stack(self.simulate_batch(self._emit_jobs, params))
+
+    def set_tune(self, rays_per_block: int = 0, mic_pairs_per_cta: int = 0, smem_kb: int = 0, stack_depth: int = 0):
+        """Launch shapes of later simulate calls (0 = the library's default for each)."""
+        t = Tune(rays_per_block, mic_pairs_per_cta, smem_kb, stack_depth)
+        self._check(self.L.st_set_tune(self.h, C.byref(t)))
 
     def autotune(self, job: "BatchJob", params: SimParams | None = None) -> Tune:
         t = Tune()

@@ -41,7 +41,7 @@ class Stats(C.Structure):
                 ("visible_records", I64), ("candidates", I64), ("candidates_kept", I64), ("terms", I64),
                 ("ms_trace", F32), ("ms_diffraction", F32), ("ms_accumulate", F32), ("ms_total", F32),
                 ("ms_accum_kernel", F32), ("accum_launches", I32), ("kernel_launches", I64),
-                ("visits", I64 * 4)]
+                ("visits", I64 * 4), ("stack_restarts", I64)]
 
 
 class Job(C.Structure):
@@ -51,7 +51,7 @@ class Job(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("rays_per_block", I32), ("mic_pairs_per_cta", I32), ("smem_kb", I32), ("reserved", I32)]
+    _fields_ = [("rays_per_block", I32), ("mic_pairs_per_cta", I32), ("smem_kb", I32), ("stack_depth", I32)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/sonotrace.h
@@ -87,6 +87,9 @@ SIGNATURES = {
     "st_scene_get_geometry": (I32, [P, P, P, P, P, P, P, I32]),
     "st_ray_directions": (I32, [P, I32, I64, P]),
     "st_impulse_response": (I32, [P, P, I32, I32, I32, F64, F64, F64, I32, P, P, I32, I32, P]),
+    "st_set_frequency_grid": (I32, [P, I32, P]),
+    "st_set_tune": (I32, [P, P]),
+    "st_inject_alloc_failure": (None, [I64]),
     "st_accumulate_specular_noalloc": (I32, [P, P, P, P, P, I64, I32, P, I64, P, I32, I32, F64, F64, I32, I32, P, P, P,
                                              P, P, P]),
 }

@@ -3,8 +3,9 @@
 SpectraFn.apply(ctx, scene, params, k_band, mics, emitter[, beta_band]) returns the complex64
 spectra [3][M][F] and differentiates them with respect to the reflection band values k_band
 [n_mat][n_bands], the microphone positions mics [M][3], the emitter position [3] (through the
-diffraction and direct paths) and, when given, the lobe widths beta_band [n_mat][n_bands] (radians),
-with the path set of the forward call frozen.  PyTorch passes
+diffraction and direct paths, and through the specular hit points: ray directions and triangle chains
+frozen, each hit point moving on its triangle's plane) and, when given, the lobe widths beta_band
+[n_mat][n_bands] (radians), with the path set of the forward call frozen.  PyTorch passes
 dL/dRe S + j dL/dIm S as the incoming gradient, which is the convention st_backward expects."""
 from __future__ import annotations
 

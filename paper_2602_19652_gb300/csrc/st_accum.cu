@@ -401,6 +401,7 @@ int g_tile_tp = 16;
 size_t g_tile_budget = 104 * 1024;  // two CTAs per SM (swept 88-110 KB: 104 fastest on the clutter workload)
 int g_tile_kt = 16;
 bool g_tile_env_read = false;
+bool g_tile_env_set = false;  // ST_ACCUM_TILE gave the tile shape
 
 void read_tile_env() {
     if (g_tile_env_read) return;
@@ -413,15 +414,20 @@ void read_tile_env() {
         g_tile_tp = tp;
         g_tile_budget = (size_t)kbudget * 1024;
         g_tile_kt = kt;
+        g_tile_env_set = true;
     }
 }
 
 template <int KT, int KIND, int DIR>
 cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
     read_tile_env();
-    const int tp = a.tile_tp > 0 ? a.tile_tp : g_tile_tp;
+    // diffraction paths whose factor is read from the material table: half the microphone pairs per CTA, so
+    // that a CTA covers twice the bins and each (path, microphone) anchor is formed half as often (the tile
+    // has no per-(path, bin) table whose cost would grow in return)
+    const bool direct_mat = KIND == 1 && !a.etab;
+    const int tp = a.tile_tp > 0 ? a.tile_tp : (direct_mat && !g_tile_env_set ? std::max(1, g_tile_tp / 2) : g_tile_tp);
     const size_t budget = a.tile_kb > 0 ? (size_t)a.tile_kb * 1024 : g_tile_budget;
-    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, tp, budget, DIR ? a.n_bands_tab : 0, KIND == 1 && !a.etab);
+    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, tp, budget, DIR ? a.n_bands_tab : 0, direct_mat);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =

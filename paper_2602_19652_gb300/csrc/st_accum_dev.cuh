@@ -301,6 +301,97 @@ __device__ __forceinline__ void load_paths_async(const AccumArgs& a, int PT, int
     cp_async_commit();
 }
 
+// Scalar values of microphone mic0 + ml for path p of the tile: writes its half of the pair's step words, lobe
+// (or material row) word, receiver band values and, in the adjoint, gradient vectors; returns its phasor at the
+// CTA's first bin and the step over one subtile (KT bins), both zero for a microphone the path does not reach.
+template <int KT, int KIND, int ADJ>
+__device__ __forceinline__ void anchor_mic(const AccumArgs& a, const Geom& g, const Buf& B, const float* pd,
+                                           const int* pv, int p, int ml, int mic0, int kb, const float* es,
+                                           int64_t pglob, float2* z_out, float2* wk_out) {
+    const int TP = g.TP, KB = g.KB, MP = g.MP;
+    const int pair = ml >> 1, half = ml & 1;
+    const int m = mic0 + ml;
+    float* wf = reinterpret_cast<float*>(B.wst + (size_t)p * 4 * TP + pair);  // component c at wf[2 TP c]
+    float* nf = reinterpret_cast<float*>(B.ngp + (size_t)p * TP + pair);
+    // (per-microphone receiver test: a microphone that does not see the path gets a zero anchor)
+    if (!pv[p] || m >= a.M || (a.mask && !((a.mask[pglob + p] >> m) & 1ull))) {
+        *z_out = make_float2(0.0f, 0.0f);
+        *wk_out = make_float2(0.0f, 0.0f);
+        for (int q = 0; q < 4; ++q) wf[2 * TP * q + half] = 0.0f;
+        nf[half] = 0.0f;
+        for (int b = 0; b < g.NB; ++b) B.dband[((size_t)p * MP + ml) * g.NB + b] = 0.0f;
+        if (ADJ) {
+            float* af = reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7);
+            for (int q = 0; q < 7; ++q) af[2 * q + half] = 0.0f;
+        }
+        return;
+    }
+    const float* d = pd + p * 12;
+    const float mx = a.mics[3 * m], my = a.mics[3 * m + 1], mz = a.mics[3 * m + 2];
+    const ff dist = dist_ff(mx, my, mz, d[0], d[1], d[2]);
+    const ff r = ff_add(ff{d[6], d[7]}, dist);
+    if (g.NB > 0) mic_bands(a, m, d[0] - mx, d[1] - my, d[2] - mz, B.dband + ((size_t)p * MP + ml) * g.NB, g.NB);
+    float gam2 = 0.0f;
+    if (KIND == 0 || ADJ) {
+        const float inv = __fdividef(1.0f, dist.hi);
+        const float ux = (mx - d[0]) * inv, uy = (my - d[1]) * inv, uz = (mz - d[2]) * inv;
+        float* af = reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7);
+        if (KIND == 0) {
+            const float cg = d[3] * ux + d[4] * uy + d[5] * uz;
+            const float cx = d[4] * uz - d[5] * uy, cy = d[5] * ux - d[3] * uz, cz = d[3] * uy - d[4] * ux;
+            const float sg = sqrtf(cx * cx + cy * cy + cz * cz);
+            const float gm = atan2f(sg, cg);
+            gam2 = gm * gm;
+            if (ADJ) {
+                // d gamma / d m = -(d' - cos(gamma) u) / (|m - P| sin gamma); with dL/dgamma =
+                // -2 ln2 gamma sum_k g_k Re w the microphone gradient gains (sum_k g_k Re w) times this vector
+                const float f = sg > 1e-20f ? 2.0f * 0.69314718055994531f * gm / (dist.hi * sg) : 0.0f;
+                af[6 + half] = f * (d[3] - cg * ux);
+                af[8 + half] = f * (d[4] - cg * uy);
+                af[10 + half] = f * (d[5] - cg * uz);
+            }
+        } else if (ADJ) {
+            const float iv = 1.0f / d[6];  // -unit(o - s): d r / d s of a diffraction path
+            af[6 + half] = -((d[0] - es[0]) * iv);
+            af[8 + half] = -((d[1] - es[1]) * iv);
+            af[10 + half] = -((d[2] - es[2]) * iv);
+        }
+        if (ADJ) {
+            af[0 + half] = ux;
+            af[2 + half] = uy;
+            af[4 + half] = uz;
+        }
+    }
+    const float rh = r.hi;
+    if (ADJ) reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7)[12 + half] = 1.0f / rh;
+    const float L0 = -2.0f * log2_ff(r) + rh * (a.atm2_0 + a.atm2_step * (float)kb);
+    const ff x0 = ff_mul(r, ff{a.qhi[min(kb, a.F - 1)], a.qlo[min(kb, a.F - 1)]});
+    float s0, c0;
+    sincospif(2.0f * ff_frac(x0), &s0, &c0);
+    const float A0 = ex2(L0);
+    const float2 z = make_float2(A0 * c0, A0 * s0);
+    const ff xs = ff_mul(r, ff{a.dq_hi, a.dq_lo});
+    float s1, c1;
+    sincospif(2.0f * ff_frac(xs), &s1, &c1);
+    const float a1 = ex2(rh * a.atm2_step);
+    const float2 W1 = make_float2(a1 * c1, a1 * s1);
+    const float2 W2 = cmul(W1, W1);  // two bins
+    wf[0 + half] = W1.x;
+    wf[2 * TP + half] = W1.y;
+    wf[4 * TP + half] = W2.x;
+    wf[6 * TP + half] = W2.y;
+    if (KIND == 1 && g.mat_direct) {  // offset of the path's row in the material table (term loop)
+        const int matp = min((int)((__float_as_uint(d[8]) >> 8) & 255u), a.n_mat_tab - 1);
+        reinterpret_cast<int*>(nf)[half] = matp * KB;
+    } else {
+        nf[half] = -gam2;
+    }
+    float2 WK = W2;  // KT bins by repeated squaring (KT is a power of two)
+    for (int q = 2; q < KT; q *= 2) WK = cmul(WK, WK);
+    *z_out = z;
+    *wk_out = WK;
+}
+
 // tables and anchors of one tile (reads pd / pv, writes buffer B); ADJ: also the position-gradient
 // vectors of the adjoint (es = emitter position, diffraction only)
 template <int KT, int KIND, int ADJ = 0>
@@ -408,95 +499,38 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
             }
         }
     }
-    // 1b: per (path, mic) anchors
-    for (int e = tid; e < PT * MP; e += nthr) {
-        const int p = e / MP, ml = e - p * MP;
-        const int pair = ml >> 1, half = ml & 1;
-        const int m = mic0 + ml;
-        float* zf = reinterpret_cast<float*>(B.za + (size_t)p * NS * TP + pair);
-        float* wf = reinterpret_cast<float*>(B.wst + (size_t)p * 4 * TP + pair);  // component c at wf[2 TP c]
-        float* nf = reinterpret_cast<float*>(B.ngp + (size_t)p * TP + pair);
-        // (per-microphone receiver test: a microphone that does not see the path gets a zero anchor)
-        if (!pv[p] || m >= a.M || (a.mask && !((a.mask[pglob + p] >> m) & 1ull))) {
+    // 1b: per (path, mic) anchors and the phasors at the subtile starts.  Specular paths of the forward go by
+    // microphone pair (the two microphones' values, then one packed complex step per subtile and a 128-bit
+    // store); diffraction and the adjoint by microphone (more items in flight: this phase is latency-bound
+    // when the tile has fewer (path, pair) items than threads).
+    if (KIND == 0 && !ADJ) {
+        for (int e = tid; e < PT * TP; e += nthr) {
+            const int p = e / TP, pair = e - p * TP;
+            float2 zz[2], wk[2];
+#pragma unroll
+            for (int half = 0; half < 2; ++half)
+                anchor_mic<KT, KIND, ADJ>(a, g, B, pd, pv, p, 2 * pair + half, mic0, kb, es, pglob, &zz[half],
+                                                &wk[half]);
+            u64 zr = pk2(zz[0].x, zz[1].x), zi = pk2(zz[0].y, zz[1].y);
+            const u64 kr = pk2(wk[0].x, wk[1].x), ki = pk2(wk[0].y, wk[1].y), nki = pk2(-wk[0].y, -wk[1].y);
+            ulonglong2* zo = B.za + (size_t)p * NS * TP + pair;
             for (int s_ = 0; s_ < NS; ++s_) {
-                zf[(size_t)s_ * TP * 4 + half] = 0.0f;
-                zf[(size_t)s_ * TP * 4 + 2 + half] = 0.0f;
-            }
-            for (int q = 0; q < 4; ++q) wf[2 * TP * q + half] = 0.0f;
-            nf[half] = 0.0f;
-            for (int b = 0; b < g.NB; ++b) B.dband[((size_t)p * MP + ml) * g.NB + b] = 0.0f;
-            if (ADJ) {
-                float* af = reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7);
-                for (int q = 0; q < 7; ++q) af[2 * q + half] = 0.0f;
-            }
-            continue;
-        }
-        const float* d = pd + p * 12;
-        const float mx = a.mics[3 * m], my = a.mics[3 * m + 1], mz = a.mics[3 * m + 2];
-        const ff dist = dist_ff(mx, my, mz, d[0], d[1], d[2]);
-        const ff r = ff_add(ff{d[6], d[7]}, dist);
-        if (g.NB > 0) mic_bands(a, m, d[0] - mx, d[1] - my, d[2] - mz, B.dband + ((size_t)p * MP + ml) * g.NB, g.NB);
-        float gam2 = 0.0f;
-        if (KIND == 0 || ADJ) {
-            const float inv = __fdividef(1.0f, dist.hi);
-            const float ux = (mx - d[0]) * inv, uy = (my - d[1]) * inv, uz = (mz - d[2]) * inv;
-            float* af = reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7);
-            if (KIND == 0) {
-                const float cg = d[3] * ux + d[4] * uy + d[5] * uz;
-                const float cx = d[4] * uz - d[5] * uy, cy = d[5] * ux - d[3] * uz, cz = d[3] * uy - d[4] * ux;
-                const float sg = sqrtf(cx * cx + cy * cy + cz * cz);
-                const float gm = atan2f(sg, cg);
-                gam2 = gm * gm;
-                if (ADJ) {
-                    // d gamma / d m = -(d' - cos(gamma) u) / (|m - P| sin gamma); with dL/dgamma =
-                    // -2 ln2 gamma sum_k g_k Re w the microphone gradient gains (sum_k g_k Re w) times this vector
-                    const float f = sg > 1e-20f ? 2.0f * 0.69314718055994531f * gm / (dist.hi * sg) : 0.0f;
-                    af[6 + half] = f * (d[3] - cg * ux);
-                    af[8 + half] = f * (d[4] - cg * uy);
-                    af[10 + half] = f * (d[5] - cg * uz);
-                }
-            } else if (ADJ) {
-                const float iv = 1.0f / d[6];  // -unit(o - s): d r / d s of a diffraction path
-                af[6 + half] = -((d[0] - es[0]) * iv);
-                af[8 + half] = -((d[1] - es[1]) * iv);
-                af[10 + half] = -((d[2] - es[2]) * iv);
-            }
-            if (ADJ) {
-                af[0 + half] = ux;
-                af[2 + half] = uy;
-                af[4 + half] = uz;
+                zo[(size_t)s_ * TP] = make_ulonglong2(zr, zi);
+                cmul2(zr, zi, kr, ki, nki);
             }
         }
-        const float rh = r.hi;
-        if (ADJ) reinterpret_cast<float*>(B.adj + ((size_t)p * TP + pair) * 7)[12 + half] = 1.0f / rh;
-        const float L0 = -2.0f * log2_ff(r) + rh * (a.atm2_0 + a.atm2_step * (float)kb);
-        const ff x0 = ff_mul(r, ff{a.qhi[min(kb, a.F - 1)], a.qlo[min(kb, a.F - 1)]});
-        float s0, c0;
-        sincospif(2.0f * ff_frac(x0), &s0, &c0);
-        const float A0 = ex2(L0);
-        float2 z = make_float2(A0 * c0, A0 * s0);
-        const ff xs = ff_mul(r, ff{a.dq_hi, a.dq_lo});
-        float s1, c1;
-        sincospif(2.0f * ff_frac(xs), &s1, &c1);
-        const float a1 = ex2(rh * a.atm2_step);
-        const float2 W1 = make_float2(a1 * c1, a1 * s1);
-        const float2 W2 = cmul(W1, W1);  // two bins
-        wf[0 + half] = W1.x;
-        wf[2 * TP + half] = W1.y;
-        wf[4 * TP + half] = W2.x;
-        wf[6 * TP + half] = W2.y;
-        if (KIND == 1 && g.mat_direct) {  // offset of the path's row in the material table (term loop)
-            const int matp = min((int)((__float_as_uint(d[8]) >> 8) & 255u), a.n_mat_tab - 1);
-            reinterpret_cast<int*>(nf)[half] = matp * KB;
-        } else {
-            nf[half] = -gam2;
-        }
-        float2 WK = W2;  // KT bins by repeated squaring (KT is a power of two)
-        for (int q = 2; q < KT; q *= 2) WK = cmul(WK, WK);
-        for (int s_ = 0; s_ < NS; ++s_) {
-            zf[(size_t)s_ * TP * 4 + half] = z.x;
-            zf[(size_t)s_ * TP * 4 + 2 + half] = z.y;
-            z = cmul(z, WK);
+    } else {
+        for (int e = tid; e < PT * MP; e += nthr) {
+            const int p = e / MP, ml = e - p * MP;
+            const int pair = ml >> 1, half = ml & 1;
+            float2 z, wk;
+            anchor_mic<KT, KIND, ADJ>(a, g, B, pd, pv, p, ml, mic0, kb, es, pglob, &z, &wk);
+            float* zf = reinterpret_cast<float*>(B.za + (size_t)p * NS * TP + pair);
+            for (int s_ = 0; s_ < NS; ++s_) {
+                zf[(size_t)s_ * TP * 4 + half] = z.x;
+                zf[(size_t)s_ * TP * 4 + 2 + half] = z.y;
+                z = cmul(z, wk);
+            }
         }
     }
 }

@@ -23,6 +23,12 @@ using namespace st;
 
 namespace st {
 
+namespace {
+// allocation-failure injection (st_inject_alloc_failure): allocations left before the injected
+// failure, or -1 when off
+int64_t g_fail_alloc_after = -1;
+}  // namespace
+
 cudaError_t grow(DevBuf& b, size_t bytes) {
     if (bytes <= b.cap && b.p) return cudaSuccess;
     if (b.p) {
@@ -31,6 +37,7 @@ cudaError_t grow(DevBuf& b, size_t bytes) {
         b.cap = 0;
     }
     size_t want = std::max<size_t>(bytes, 256);
+    if (g_fail_alloc_after >= 0 && g_fail_alloc_after-- == 0) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         b.p = nullptr;
@@ -657,6 +664,27 @@ st_status st_set_receivers(st_ctx* c, int32_t n_mics, const float* pos, const fl
     return ST_OK;
 }
 
+void st_inject_alloc_failure(int64_t after) { st::g_fail_alloc_after = after < 0 ? -1 : after; }
+
+st_status st_set_frequency_grid(st_ctx* c, int32_t n_bins, const float* f_hz) {
+    if (!c) return ST_ERR_ARG;
+    if (!f_hz || n_bins <= 0 || n_bins > (1 << 20)) return fail(c, ST_ERR_ARG, "set_frequency_grid: 1..2^20 bins");
+    const double f_lo = f_hz[0], f_hi = f_hz[n_bins - 1];
+    if (!(f_lo > 0.0) || !std::isfinite(f_hi)) return fail(c, ST_ERR_ARG, "set_frequency_grid: 0 < f_0, finite bins");
+    const double df = n_bins > 1 ? (f_hi - f_lo) / (double)(n_bins - 1) : 0.0;
+    for (int32_t k = 1; k < n_bins; ++k)
+        if (!((double)f_hz[k] > (double)f_hz[k - 1]))
+            return fail(c, ST_ERR_ARG, "set_frequency_grid: bins must be strictly ascending");
+    // the accumulators advance every path's phasor by one constant bin spacing (one complex step per
+    // bin), so the bins must lie on f_0 + k df: each within the float32 rounding of that grid point
+    for (int32_t k = 1; k + 1 < n_bins; ++k) {
+        const double want = f_lo + (double)k * df;
+        if (std::fabs((double)f_hz[k] - want) > 4.0 * 1.2e-7 * std::fabs(want))
+            return fail(c, ST_ERR_ARG, "set_frequency_grid: bins must be uniformly spaced");
+    }
+    return st_set_frequencies(c, n_bins, f_lo, f_hi);
+}
+
 st_status st_set_frequencies(st_ctx* c, int32_t n_bins, double f_lo, double f_hi) {
     if (!c) return ST_ERR_ARG;
     if (n_bins <= 0 || n_bins > (1 << 20) || !(f_lo > 0.0) || !(f_hi >= f_lo) || (n_bins > 1 && !(f_hi > f_lo)))
@@ -816,6 +844,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         ta.root = S.root;
         ta.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
         ta.visits = c->count_visits ? qctr + 2 : nullptr;
+        ta.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
+        ta.restarts = qctr + 6;
         ta.nrm = ptr<float>(S.nrm);
         memcpy(ta.s, c->s, 12);
         memcpy(ta.q, c->q, 16);
@@ -873,6 +903,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         da.root = S.root;
         da.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
         da.visits = c->count_visits ? qctr + 2 : nullptr;
+        da.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
+        da.restarts = qctr + 6;
         da.nrm = ptr<float>(S.nrm);
         da.verts = ptr<float>(S.verts);
         da.tris = ptr<int32_t>(S.tris);
@@ -1037,6 +1069,8 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         dv.root = S.root;
         dv.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
         dv.visits = c->count_visits ? qctr + 2 : nullptr;
+        dv.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
+        dv.restarts = qctr + 6;
         memcpy(dv.s, c->s, 12);
         dv.mics = ptr<float>(c->mics);
         dv.M = M;
@@ -1092,9 +1126,9 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     // device-side error flags are checked whenever the caller synchronises through stats
     if (stats) {
         uint32_t h[4] = {0, 0, 0, 0}, fl = 0;
-        unsigned long long hq[6] = {0, 0, 0, 0, 0, 0};
+        unsigned long long hq[7] = {0, 0, 0, 0, 0, 0, 0};
         CKC(c, cudaMemcpyAsync(h, cnt, 16, cudaMemcpyDeviceToHost, s), "stats");
-        CKC(c, cudaMemcpyAsync(hq, qctr, 48, cudaMemcpyDeviceToHost, s), "stats");
+        CKC(c, cudaMemcpyAsync(hq, qctr, 56, cudaMemcpyDeviceToHost, s), "stats");
         CKC(c, cudaMemcpyAsync(&fl, c->flags.p, 4, cudaMemcpyDeviceToHost, s), "stats");
         CKC(c, cudaStreamSynchronize(s), "stats sync");
         memset(stats, 0, sizeof(*stats));
@@ -1102,6 +1136,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         stats->closest_queries = (int64_t)hq[0];
         stats->shadow_queries = (int64_t)hq[1];
         for (int k = 0; k < 4; ++k) stats->visits[k] = (int64_t)hq[2 + k];
+        stats->stack_restarts = (int64_t)hq[6];
         stats->records = 0;
         stats->visible_records = h[2];
         stats->candidates = K;
@@ -1129,7 +1164,6 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
             stats->accum_launches++;
         }
         stats->terms = ((int64_t)((n_accum & 1) ? h[2] : 0) + (int64_t)((n_accum & 2) ? h[3] : 0)) * M * F;
-        if (fl & kFlagStackOverflow) return fail(c, ST_ERR_OVERFLOW, "traversal stack overflow");
         if (fl & kFlagBadTree) return fail(c, ST_ERR_CUDA, "malformed BVH: traversal exceeded the node count");
     }
     return ST_OK;
@@ -1451,7 +1485,7 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
 bool tune_ok(const st_tune& t) {
     return (t.rays_per_block == 0 || t.rays_per_block == 64 || t.rays_per_block == 128 || t.rays_per_block == 256) &&
            (t.mic_pairs_per_cta == 0 || (t.mic_pairs_per_cta >= 1 && t.mic_pairs_per_cta <= 16)) &&
-           (t.smem_kb == 0 || (t.smem_kb >= 32 && t.smem_kb <= 160));
+           (t.smem_kb == 0 || (t.smem_kb >= 32 && t.smem_kb <= 160)) && t.stack_depth >= 0 && t.stack_depth <= kStack;
 }
 
 void batch_free_graph(BatchState& B) {
@@ -1540,6 +1574,7 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     a.dvis = ptr<uint8_t>(B.dvis);
     a.ranges = ptr<uint32_t>(B.ranges);
     a.flags = ptr<uint32_t>(B.flags);
+    a.stack_limit = tn.stack_depth > 0 ? std::min(tn.stack_depth, kStack) : kStack;
     a.queries = ptr<unsigned long long>(B.queries);
     a.hit_tri = ptr<int32_t>(B.hit_tri);
     a.hit_t = ptr<float>(B.hit_t);
@@ -1732,7 +1767,7 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     key = fnv(key, &pg, sizeof(pg));
     const int64_t pi[4] = {(int64_t)p.components, (int64_t)p.reflection_mode, (int64_t)p.seed, (int64_t)p.los_mode};
     key = fnv(key, pi, sizeof(pi));
-    const int32_t ti[3] = {tn.rays_per_block, tn.mic_pairs_per_cta, tn.smem_kb};
+    const int32_t ti[4] = {tn.rays_per_block, tn.mic_pairs_per_cta, tn.smem_kb, tn.stack_depth};
     key = fnv(key, ti, sizeof(ti));
     if (B.valid && B.key == key && B.exec) {
         const int ne = (int)B.events.size();
@@ -1901,7 +1936,6 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     CKC(c, cudaStreamSynchronize(ms), "batch run");
     uint32_t fl = 0;
     CKC(c, cudaMemcpy(&fl, B.flags.p, 4, cudaMemcpyDeviceToHost), "batch flags");
-    if (fl & kFlagStackOverflow) return fail(c, ST_ERR_OVERFLOW, "traversal stack overflow");
     if (fl & kFlagBadTree) return fail(c, ST_ERR_CUDA, "malformed BVH: traversal exceeded the node count");
     CKC(c, cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal), "batch capture");
     cudaError_t ie = batch_issue(c, B, jobs, p, tn, ms);
@@ -1916,6 +1950,13 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     CKC(c, cudaGraphInstantiate(&B.exec, g, 0), "batch instantiate");
     B.key = key;
     B.valid = true;
+    return ST_OK;
+}
+
+st_status st_set_tune(st_ctx* c, const st_tune* tune) {
+    if (!c || !tune) return fail(c, ST_ERR_ARG, "set_tune: null argument");
+    if (!tune_ok(*tune)) return fail(c, ST_ERR_ARG, "set_tune: value out of range");
+    c->tune = *tune;
     return ST_OK;
 }
 
@@ -1940,7 +1981,7 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
     const st_tune saved = c->tune;
     const int rpb[3] = {64, 128, 256};
     const int tiles[5][2] = {{16, 96}, {8, 96}, {16, 64}, {4, 96}, {16, 128}};
-    st_tune best = {128, 16, 96, 0};
+    st_tune best = {128, 16, 96, saved.stack_depth};
     // tracing block size with the default tile, then the accumulator tile with the best block size
     for (int phase = 0; phase < 2; ++phase) {
         const int n_cand = phase == 0 ? 3 : 5;

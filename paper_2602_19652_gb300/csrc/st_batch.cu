@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_closest_batch(const BatchArgs
                 g = batch_ray(a, j, idx, &job);
                 const JobDev& b = a.jobs[job];
                 if (j < b.B) {
-                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
                     f3 o, d;
                     int32_t prev;
                     if (j == 0) {
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_batch(const BatchArgs
                 if (!(tmax > a.t_min)) {
                     out[id] = 1;
                 } else {
-                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
                     trav_init(S, T, o, u, excl[id], a.t_min, tmax);
                     live = true;
                 }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics_batch(const Batc
                     atomicOr(reinterpret_cast<unsigned long long*>(&a.rec_mask[id]), 1ull << m);
                     a.rec_los[id] = 1;
                 } else {
-                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
                     trav_init(S, T, o, u, a.rec_tri[id], a.t_min, tmax);
                     live = true;
                 }
@@ -381,7 +381,7 @@ __global__ void k_direct_batch(const BatchArgs a) {
         const int job = find_job(a.mic_offs, a.n_jobs, g);
         const JobDev& b = a.jobs[job];
         const int m = (int)(g - b.mic_off);
-        const Trav T{b.nodes, b.tri_v, b.root, b.max_iter, nullptr};
+        const Trav T{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
         warp_count(a.queries + 1);
         a.dvis[g] = visible(T, f3{b.s[0], b.s[1], b.s[2]}, f3{b.mics[3 * m], b.mics[3 * m + 1], b.mics[3 * m + 2]},
                             -1, a.t_min, a.los_eps, a.flags)

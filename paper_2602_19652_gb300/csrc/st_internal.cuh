@@ -19,7 +19,7 @@ constexpr int kMaxBounces = 8;     // B limit (material chain packed in 8 bytes)
 constexpr int kMaxMics = 4096;
 
 // error flag bits written by kernels into Ctx::d_flags
-constexpr uint32_t kFlagStackOverflow = 1u;
+constexpr uint32_t kFlagStackOverflow = 1u;  // (unused: a traversal that would overflow its stack restarts)
 constexpr uint32_t kFlagBadIndex = 2u;
 constexpr uint32_t kFlagBadVertex = 4u;
 constexpr uint32_t kFlagBadTree = 8u;
@@ -138,6 +138,8 @@ struct TraceArgs {
     int32_t root;
     int32_t max_iter;
     unsigned long long* visits;
+    int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
+    unsigned long long* restarts;  // device counter of stackless restarts (or null)
     const float* nrm;
     // rays
     float s[3];
@@ -189,6 +191,8 @@ struct DiffArgs {
     int32_t root;
     int32_t max_iter;
     unsigned long long* visits;
+    int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
+    unsigned long long* restarts;  // device counter of stackless restarts (or null)
     const float* nrm;
     const float* verts;
     const int32_t* tris;
@@ -224,6 +228,8 @@ struct DirectArgs {
     int32_t root;
     int32_t max_iter;
     unsigned long long* visits;
+    int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
+    unsigned long long* restarts;  // device counter of stackless restarts (or null)
     float s[3];
     const float* mics;
     int32_t M;
@@ -396,6 +402,7 @@ struct BatchArgs {
     unsigned long long* ctr;
     uint32_t* flags;
     unsigned long long* queries;
+    int32_t stack_limit;       // traversal stack entries per query (1..kStack; more: the query restarts stackless)
     // per-microphone receiver test (null otherwise): visible microphones of each record [R_total], and the
     // visibility queue of (record << 6 | microphone) entries, at most Q_total = sum over jobs of N x M a bounce
     uint64_t* rec_mask;

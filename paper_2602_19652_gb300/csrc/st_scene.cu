@@ -600,6 +600,7 @@ __global__ void k_pack_wide(int n, const int2* child, const int2* range, const B
         };
         const int2 c = child[i];
         const int32_t cs[2] = {c.x, c.y};
+        const int32_t self = (int32_t)idx[i];
         for (int sd = 0; sd < 2; ++sd) {
             const int32_t r = child_ref(cs[sd], range);
             if (r < 0) {
@@ -609,6 +610,9 @@ __global__ void k_pack_wide(int n, const int2* child, const int2* range, const B
                 const int32_t gs[2] = {g.x, g.y};
                 for (int t = 0; t < 2; ++t) {
                     const int32_t rg = child_ref(gs[t], range);
+                    if (rg >= 0)  // row 7 of a child node: its parent and its slot here (the stackless walk)
+                        nodes[8 * (size_t)idx[rg] + 7] = make_float4(__int_as_float(self), __int_as_float(cnt), 0.0f,
+                                                                     0.0f);
                     add(box_tmp[2 * r + t], rg < 0 ? rg : (int32_t)idx[rg]);
                 }
             }
@@ -627,7 +631,7 @@ __global__ void k_pack_wide(int n, const int2* child, const int2* range, const B
         }
         o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
                            __int_as_float(ref[3]));
-        o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (i == 0) o[7] = make_float4(__int_as_float(-1), 0.0f, 0.0f, 0.0f);  // the root has no parent
     }
 }
 

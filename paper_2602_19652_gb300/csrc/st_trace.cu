@@ -31,7 +31,7 @@ using namespace trv;
 
 // Closest hits of one bounce: item idx of the live-ray queue (the first bounce in direction order).
 __global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, int j, int64_t n_first) {
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
     const int64_t n = (j == 0) ? n_first : (int64_t)*a.n_in;
     const unsigned full = 0xffffffffu;
     int2 stack[kStack];
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const u
 // Per-microphone receiver test: query q of the queue is record q / M and microphone q % M; a visible
 // microphone sets its bit of the record's mask (and the record's flag: some microphone sees it).
 __global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics(const TraceArgs a, unsigned long long* ctr) {
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
     const int64_t n = *a.vis_n;
     const unsigned full = 0xffffffffu;
     int2 stack[kStack];
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(128, 8) k_diffraction(const DiffArgs a) {
 }
 
 __global__ void k_direct(const DirectArgs a) {
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= a.M) return;
     const f3 s{a.s[0], a.s[1], a.s[2]};
@@ -460,7 +460,7 @@ static unsigned trav_grid(int64_t n) {
 
 cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
     const unsigned grid = grid_for(a.N, block, 152 * 16);
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
     for (int j = 0; j < a.B; ++j) {
         if (j > 0) {
             uint32_t* t = a.q_in;
@@ -513,7 +513,7 @@ cudaError_t diffraction_sample(DiffArgs& a, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = radix_sort_u64(a.sort_keys, a.los_q, a.K, 3 * kLosBits + 1, a.sort_scr, s)) != cudaSuccess) return e;
     }
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits};
+    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
     note_launch();
     k_visible<<<trav_grid(a.K), kTravBlock, 0, s>>>(T, a.los_q, a.los_n, a.cand_p, a.cand_tri, nullptr, a.s[0], a.s[1],
                                                     a.s[2], a.t_min, a.los_eps, a.keep, a.ctr, a.flags, a.queries);

@@ -15,6 +15,8 @@ struct Trav {
     int32_t root;
     int32_t max_iter;               // 2 * node count + 8: bound on loop iterations of one traversal
     unsigned long long* visits;     // optional [4]: nodes and triangles visited (closest, any-hit)
+    int32_t stack_limit = kStack;   // stack entries a query may use (1..kStack) before it restarts stackless
+    unsigned long long* restarts = nullptr;  // optional: queries that restarted from the root
 };
 
 __device__ __forceinline__ float safe_inv(float d) {
@@ -68,6 +70,36 @@ __device__ __forceinline__ void trav_init(TravState& S, const Trav& T, f3 o, f3 
     S.n_tris = 0;
 }
 
+// one triangle of a leaf (leaf code: first triangle << 3 | triangles left after it); true when an any-hit
+// query has found its hit.  S.ref becomes the code of the next triangle, or `after` when the leaf is done.
+template <bool AnyHit>
+__device__ __forceinline__ bool leaf_step(const Trav& T, TravState& S, int32_t after) {
+    const int32_t code = ~S.ref;
+    const int i = code >> 3, rest = code & 7;
+    const float4 v0 = __ldg(&T.tri_v[3 * i + 0]);
+    const int32_t id = __float_as_int(v0.w);
+    if (id != S.exclude) {
+        const float4 v1 = __ldg(&T.tri_v[3 * i + 1]);
+        const float4 v2 = __ldg(&T.tri_v[3 * i + 2]);
+        ++S.n_tris;
+        float th;
+        if (wt_hit(S.wr, f3{v0.x, v0.y, v0.z}, f3{v1.x, v1.y, v1.z}, f3{v2.x, v2.y, v2.z}, &th) && th > S.t_min) {
+            if (AnyHit) {
+                if (th < S.t_max) {
+                    S.tb = th;
+                    S.best = id;
+                    return true;
+                }
+            } else if (th < S.tb || (th == S.tb && id < S.best)) {
+                S.tb = th;
+                S.best = id;
+            }
+        }
+    }
+    S.ref = rest > 0 ? ~(((i + 1) << 3) | (rest - 1)) : after;
+    return false;
+}
+
 // one node or one leaf triangle; true when the query has finished (S.best = hit triangle or -1, S.tb = its t)
 template <bool AnyHit>
 __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* stack, uint32_t* flags) {
@@ -91,6 +123,27 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* sta
         const bool h1 = slab(lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, o, inv, 0.0f, tb, &t1);
         const bool h2 = r2 != kEmptyRef && slab(lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, o, inv, 0.0f, tb, &t2);
         const bool h3 = r3 != kEmptyRef && slab(lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, o, inv, 0.0f, tb, &t3);
+        if (S.sp < 0) {
+            // Restart walk of a query whose short stack overflowed: depth first from the root in fixed child
+            // order, without a stack.  stack[0] = (this node, first slot still to visit); a node's row 7 holds
+            // its parent and its slot there.  A child is entered when its box meets [0, tb] with the best hit so
+            // far, so the result is the stack walk's: a subtree skipped for a farther tb holds no triangle
+            // nearer than the final tb.
+            const int from = stack[0].y;
+            const int c = (from <= 0 && h0) ? 0 : (from <= 1 && h1) ? 1 : (from <= 2 && h2) ? 2 : (from <= 3 && h3) ? 3 : -1;
+            if (c >= 0) {
+                const int32_t ref = c == 0 ? r0 : c == 1 ? r1 : c == 2 ? r2 : r3;
+                // into the child node, or through the leaf's triangles and back to the next slot here
+                stack[0] = ref >= 0 ? make_int2(ref, 0) : make_int2(S.ref, c + 1);
+                S.ref = ref;
+                return false;
+            }
+            if (S.ref == T.root) return true;  // every child of the root done
+            const float4 up = __ldg(nd + 7);
+            S.ref = __float_as_int(up.x);
+            stack[0] = make_int2(S.ref, __float_as_int(up.y) + 1);  // the parent, after this node's slot
+            return false;
+        }
         // order the hit children by entry distance (misses last): the nearest is visited next, the
         // others are pushed farthest first (hit keys are clamped below +inf, so the hits sort strictly
         // before the misses)
@@ -115,8 +168,14 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* sta
         cx(k1, c1, k2, c2);
         const int nh = (int)h0 + (int)h1 + (int)h2 + (int)h3;
         if (nh > 0) {
-            if (S.sp + nh - 1 > kStack) {
-                atomicOr(flags, kFlagStackOverflow);
+            if (S.sp + nh - 1 > T.stack_limit) {
+                // the short stack is full: restart from the root with the stackless walk, keeping the best hit
+                if (T.restarts) atomicAdd(T.restarts, 1ull);
+                S.sp = -1;
+                stack[0] = make_int2(T.root, 0);
+                S.ref = T.root;
+                S.guard = T.max_iter > (1 << 27) ? (1 << 30) : 8 * T.max_iter;  // each node down once, up <= 4 times
+                return false;
             } else {
                 if (nh > 3) stack[S.sp++] = make_int2(c3, __float_as_int(k3));
                 if (nh > 2) stack[S.sp++] = make_int2(c2, __float_as_int(k2));
@@ -126,33 +185,12 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* sta
             return false;
         }
     } else {
-        // one triangle of the leaf per step (leaf code: first triangle << 3 | triangles left after it), so
-        // lanes in leaves and lanes in inner nodes of the same warp stay in step
-        const int32_t code = ~S.ref;
-        const int i = code >> 3, rest = code & 7;
-        const float4 v0 = __ldg(&T.tri_v[3 * i + 0]);
-        const int32_t id = __float_as_int(v0.w);
-        if (id != S.exclude) {
-            const float4 v1 = __ldg(&T.tri_v[3 * i + 1]);
-            const float4 v2 = __ldg(&T.tri_v[3 * i + 2]);
-            ++S.n_tris;
-            float th;
-            if (wt_hit(S.wr, f3{v0.x, v0.y, v0.z}, f3{v1.x, v1.y, v1.z}, f3{v2.x, v2.y, v2.z}, &th) &&
-                th > S.t_min) {
-                if (AnyHit) {
-                    if (th < S.t_max) {
-                        S.tb = th;
-                        S.best = id;
-                        return true;
-                    }
-                } else if (th < S.tb || (th == S.tb && id < S.best)) {
-                    S.tb = th;
-                    S.best = id;
-                }
-            }
-        }
-        if (rest > 0) {
-            S.ref = ~(((i + 1) << 3) | (rest - 1));
+        // one triangle of a leaf per step, so lanes in leaves and lanes in inner nodes of the same warp stay
+        // in step
+        if (leaf_step<AnyHit>(T, S, 1)) return true;
+        if (S.ref < 0) return false;
+        if (S.sp < 0) {  // restart walk: back to the node that holds the leaf
+            S.ref = stack[0].x;
             return false;
         }
     }

@@ -222,3 +222,23 @@ def test_autotune_shapes_give_same_results(st):
     for a, b in zip(tuned, base):
         for c in range(3):
             assert rel_l2(a[c], b[c]) <= TOL_SINGLE
+
+
+def test_batch_stack_restarts_keep_results_exact():
+    """The batched kernels take the stack limit of their tune: with 2-entry stacks (most queries restart
+    stackless from the root) every job's spectra equal those of the default stack bit for bit."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_19652_gb300 as st
+    wl = synth.clutter(seed=212, target_tris=6000, n_rays=3000, bounces=3, n_mics=4, n_bins=32)
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, st.curv_params(sample_budget=20_000))
+    jobs = [st.BatchJob(sc, wl.emitter + np.float32(0.1 * i), wl.emitter_quat, wl.dirs, wl.mics, wl.n_bins, wl.f_lo,
+                        wl.f_hi, wl.bounces, pose_index=i) for i in range(3)]
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    ctx.simulate_batch(jobs, p)
+    ref = [j.out.cpu().numpy().copy() for j in jobs]
+    ctx.simulate_batch(jobs, p, tune=st.Tune(0, 0, 0, 2))
+    for j, r in zip(jobs, ref):
+        assert np.array_equal(j.out.cpu().numpy(), r)

@@ -112,3 +112,60 @@ def test_order_and_argument_checks(st):
     sc.update_vertices(wl.verts)  # a refit: the path set of the last simulate no longer belongs to the scene
     assert status_of(st, ctx.backward, sc, G, *wl.k_band.shape) == st.ST_ERR_STATE
     assert np.array_equal(ctx.simulate(sc, p).cpu().numpy(), S.cpu().numpy())
+
+
+def test_frequency_grid_array(st):
+    """Bins given as an ascending, uniformly spaced array give the spectra of the same grid given by its
+    ends, bit for bit; a non-uniform, descending or empty array is rejected and the context keeps its
+    grid."""
+    wl = synth.clutter(seed=31, target_tris=3000, n_rays=2000, bounces=3, n_mics=4, n_bins=37)
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, st.curv_params(sample_budget=20_000))
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    S_ref = ctx.simulate(sc, p).cpu().numpy()
+    f = np.linspace(wl.f_lo, wl.f_hi, wl.n_bins)
+    ctx.set_frequency_grid(f.astype(np.float32))
+    assert np.array_equal(ctx.simulate(sc, p).cpu().numpy(), S_ref)
+    g = f.copy()
+    g[5] += 0.3 * (f[1] - f[0])
+    assert status_of(st, ctx.set_frequency_grid, g) == st.ST_ERR_ARG
+    assert status_of(st, ctx.set_frequency_grid, f[::-1].copy()) == st.ST_ERR_ARG
+    assert status_of(st, ctx.set_frequency_grid, np.zeros(0, np.float32)) == st.ST_ERR_ARG
+    assert np.array_equal(ctx.simulate(sc, p).cpu().numpy(), S_ref)
+    ctx.set_frequency_grid(np.array([wl.f_lo], np.float32))
+    assert ctx.simulate(sc, p).shape == (3, len(wl.mics), 1)
+
+
+def test_injected_allocation_failure(st):
+    """A device allocation that fails (injected on the host: the allocator returns the out-of-memory
+    error without allocating) makes the call that needs it return ST_ERR_OOM; the context then still
+    works, and its spectra equal a fresh context's bit for bit."""
+    L = st.load()
+    wl = synth.clutter(seed=31, target_tris=3000, n_rays=3000, bounces=3, n_mics=4, n_bins=32)
+    try:
+        ctx = st.Context(0)
+        sc = st.from_workload(ctx, wl, st.curv_params(sample_budget=20_000))
+        p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+        for after in (0, 1, 3, 7):
+            L.st_inject_alloc_failure(after)
+            ctx2 = st.Context(0)
+            try:
+                sc2 = st.from_workload(ctx2, wl, st.curv_params(sample_budget=20_000))
+                code = status_of(st, ctx2.simulate, sc2, p)
+            except st.SonotraceError as e:  # the failure hit the scene load or precompute
+                code = e.status
+            L.st_inject_alloc_failure(-1)
+            assert code == st.ST_ERR_OOM, (after, code)
+        # a simulate that needs larger buffers than the last one fails at its first allocation ...
+        wl2 = synth.clutter(seed=31, target_tris=3000, n_rays=9000, bounces=3, n_mics=4, n_bins=32)
+        ctx.set_emitter(wl2.emitter, wl2.emitter_quat, wl2.dirs)
+        L.st_inject_alloc_failure(0)
+        assert status_of(st, ctx.simulate, sc, p) == st.ST_ERR_OOM
+        L.st_inject_alloc_failure(-1)
+        # ... and the next one, with nothing injected, regrows them and gives the fresh context's spectra
+        S = ctx.simulate(sc, p).cpu().numpy()
+        fresh = st.Context(0)
+        scf = st.from_workload(fresh, wl2, st.curv_params(sample_budget=20_000))
+        assert np.array_equal(S, fresh.simulate(scf, p).cpu().numpy())
+    finally:
+        L.st_inject_alloc_failure(-1)

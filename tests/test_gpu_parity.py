@@ -219,3 +219,67 @@ def test_eight_bounces(st, mode):
     compare_paths(ctx.paths(wl.bounces), o["rec"])
     for c in range(3):
         assert rel_l2(S[c], o["spectra"][c]) <= TOL, (c, rel_l2(S[c], o["spectra"][c]))
+
+
+def test_phase_at_the_largest_f_r_over_c(st):
+    """The phase far from the origin of the range reduction: one ray to a mirror 60 m away and back to a
+    microphone beside the emitter and to one 100 m behind it on the reflected ray (paths of about 120 and
+    220 m), and the direct paths (0.5 and 100 m), over 1024 bins from 20 to 120 kHz, the vegetation
+    workload's band: up to 7.7e4 cycles of f r / c.  Air absorption is off so that every amplitude stays
+    well inside float32's range.  Every bin of the specular and direct spectra is compared on its own with
+    the oracle's float64 value (relative error 1e-5 per bin, far inside the 1e-4 relative L2 bar)."""
+    import oracle
+    v = np.array([[60, -80, -80], [60, 80, -80], [60, 0, 120]], np.float32)
+    d = np.array([[60.0, 0.25, 0.0]]) / np.linalg.norm([60.0, 0.25, 0.0])
+    wl = synth.Workload(name="mirror", verts=v, tris=np.array([[0, 1, 2]], np.int32), tri_mat=np.zeros(1, np.int32),
+                        tri_obj=np.zeros(1, np.int32), band_hz=np.array([20e3, 120e3], np.float32),
+                        k_band=np.array([[0.9, 0.7]], np.float32), beta_band=np.array([[0.3, 0.2]], np.float32),
+                        diff_band=np.full((1, 2), 0.05, np.float32), emitter=np.zeros(3, np.float32),
+                        emitter_quat=np.array([1, 0, 0, 0], np.float32), dirs=d.astype(np.float32),
+                        mics=np.array([[0.0, 0.5, 0.0], [-100.0, 0.917, 0.0]], np.float32), n_bins=1024,
+                        f_lo=20e3, f_hi=120e3, bounces=1)
+    comp = st.ST_COMP_SPECULAR | st.ST_COMP_DIRECT
+    ctx, sc, S, stats = gpu_run(st, wl, components=comp, alpha1_db_m_khz=0.0)
+    o = oracle.simulate(wl, components=5, a1_per_khz=0.0)
+    compare_paths(ctx.paths(wl.bounces), o["rec"])
+    assert o["rec"]["los"][0, 0] == 1 and o["rec"]["r"][0, 0] > 59.0
+    for c in (0, 2):
+        ref = o["spectra"][c]
+        assert np.abs(ref).min() > 0
+        err = np.abs(S[c] - ref) / np.abs(ref)
+        assert err.max() <= 1e-5, (c, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3, 6])
+def test_stack_restarts_keep_results_exact(st, depth):
+    """A query whose short stack would overflow restarts from the root with the stackless walk (fixed child
+    order, parent references in the nodes) and keeps its best hit: with stacks of 1 to 6 entries, where most
+    queries restart, every path record, diffraction filter, direct visibility and spectrum is bit-identical
+    to the default 128-entry stack, and the path records equal the oracle's."""
+    import oracle
+    wl = small_clutter(target_tris=8000, n_rays=6000, bounces=4, n_mics=4, n_bins=48)
+    curv = st.curv_params(sample_budget=40_000)
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, curv)
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    S0, s0 = ctx.simulate(sc, p, stats=True)
+    S0 = S0.cpu().numpy()
+    g0 = ctx.paths(wl.bounces)
+    ct0, cp0, k0 = ctx.diffraction()
+    dv0 = ctx.direct_visibility()
+    assert s0.stack_restarts == 0
+    ctx.set_tune(stack_depth=depth)
+    S1, s1 = ctx.simulate(sc, p, stats=True)
+    assert s1.stack_restarts > 0
+    g1 = ctx.paths(wl.bounces)
+    for k in ("tri", "p", "d", "r", "los"):
+        assert np.array_equal(g0[k], g1[k]), k
+    ct1, cp1, k1 = ctx.diffraction()
+    assert np.array_equal(k0, k1) and np.array_equal(dv0, ctx.direct_visibility())
+    assert np.array_equal(S0, S1.cpu().numpy())
+    o = oracle.simulate(wl, curv=dict(budget=40_000))
+    compare_paths(g1, o["rec"])
+    assert np.array_equal(k1, o["cand_keep"])
+    ctx.set_tune(stack_depth=0)
+    with pytest.raises(st.SonotraceError):
+        ctx.set_tune(stack_depth=129)
