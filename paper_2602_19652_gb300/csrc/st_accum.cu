@@ -86,10 +86,12 @@ __global__ void k_tables(int32_t F, int32_t n_mat, int32_t n_bands, const float*
 
 // two CTAs per SM (128 registers) stated explicitly: left to the heuristic, small edits elsewhere in the unit
 // have turned it into one CTA of 236 registers; the directional variants keep one CTA (250 registers)
+// One CTA of the accumulation: microphone block bx % n_mb, bin block bx / n_mb, chunk by of the path list.
+// Threads past TP * NS (a block larger than the tile, as in the persistent batched launch) take part in
+// the loads, the producer and the barriers only.
 template <int KT, int KIND, int DIR>
-__global__ void __launch_bounds__(256, DIR ? 1 : 2) k_accum(const AccumArgs a, const Geom g) {
+__device__ __forceinline__ void accum_cta(const AccumArgs& a, const Geom& g, int bx, int by, float4* smem4) {
     static_assert((KT & (KT - 1)) == 0 && KT >= 2, "KT must be a power of two");
-    extern __shared__ float4 smem4[];
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
     const Buf B0 = buf_at<KT>(smem4, g, 0), B1 = buf_at<KT>(smem4, g, 1);
     float* pdb = reinterpret_cast<float*>(reinterpret_cast<char*>(smem4) + 2 * g.buf_bytes);  // [2][PT][12]
@@ -97,16 +99,17 @@ __global__ void __launch_bounds__(256, DIR ? 1 : 2) k_accum(const AccumArgs a, c
     // material tables: 16-byte aligned for the 128-bit loads of phase 1a
     float* mt = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(pvb + 2 * PT) + 15) & ~uintptr_t(15));
 
-    const int mb = blockIdx.x % g.n_mb, bb = blockIdx.x / g.n_mb;
+    const int mb = bx % g.n_mb, bb = bx / g.n_mb;
     const int mic0 = mb * MP, kb = bb * KB;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int tp = tid % TP, s = tid / TP;
+    const bool cons = tid < TP * NS;  // a thread of the tile (term loop and outputs)
+    const int tp = tid % TP, s = cons ? tid / TP : 0;
 
     const int64_t pb0 = a.d_base ? (int64_t)*a.d_base : 0;  // global index of this launch's first path
     const int64_t count = (int64_t)*a.d_count;
     const int64_t n_tiles = (count + PT - 1) / PT;
     const int64_t per = (n_tiles + a.n_chunks - 1) / a.n_chunks;
-    const int64_t t0 = (int64_t)blockIdx.y * per, t1 = min(n_tiles, t0 + per);
+    const int64_t t0 = (int64_t)by * per, t1 = min(n_tiles, t0 + per);
 
     u64 Sr[KT], Si[KT];
 #pragma unroll
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(256, DIR ? 1 : 2) k_accum(const AccumArgs a, c
             produce<KT, KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, nullptr,
                               pb0 + (tile + 1) * PT);
         }
-        for (int p = 0; p < PT; ++p) {
+        for (int p = 0; p < (cons ? PT : 0); ++p) {
             const ulonglong2 z0 = C.za[((size_t)p * NS + s) * TP + tp];
             const u64* w = C.wst + (size_t)p * 4 * TP + tp;  // component-major: conflict-free 64-bit loads
             const u64 w1r = w[0], w1i = w[TP], w2r = w[2 * TP], w2i = w[3 * TP];
@@ -214,14 +217,74 @@ __global__ void __launch_bounds__(256, DIR ? 1 : 2) k_accum(const AccumArgs a, c
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int m = mic0 + 2 * tp + h;
-        if (m >= a.M) continue;
-        float2* out = a.partial + ((size_t)blockIdx.y * a.M + m) * a.F;
+        if (!cons || m >= a.M) continue;
+        float2* out = a.partial + ((size_t)by * a.M + m) * a.F;
 #pragma unroll
         for (int kk = 0; kk < KT; ++kk) {
             const int k = kb + s * KT + kk;
             const float2 re = up2(Sr[kk]), im = up2(Si[kk]);
             if (k < a.F) out[k] = h == 0 ? make_float2(re.x, im.x) : make_float2(re.y, im.y);
         }
+    }
+}
+
+template <int KT, int KIND, int DIR>
+__global__ void __launch_bounds__(256, DIR ? 1 : 2) k_accum(const AccumArgs a, const Geom g) {
+    extern __shared__ float4 smem4[];
+    accum_cta<KT, KIND, DIR>(a, g, blockIdx.x, blockIdx.y, smem4);
+}
+
+// Persistent accumulation of a batch: each CTA takes work items -- one CTA's worth of one (job, path kind)
+// accumulation: its microphone block, bin block and chunk -- from a device counter until none is left, and
+// runs them with the single-pose CTA body.  Items are claimed in task order; no item waits for another.  One
+// launch per path kind (the tasks of that kind).
+template <int KIND>
+__global__ void __launch_bounds__(256, 2) k_accum_queue(const AccumTask* tasks, int32_t n_tasks, int64_t n_items,
+                                                        unsigned long long* counter) {
+    extern __shared__ float4 smem4[];
+    __shared__ long long item_s;
+    __shared__ int task_s;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(counter, 1ull);
+            int lo = 0, hi = n_tasks - 1;  // last task whose first item is <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tasks[mid].item0 <= it) lo = mid; else hi = mid - 1;
+            }
+            item_s = it;
+            task_s = lo;
+        }
+        __syncthreads();
+        const long long it = item_s;
+        const AccumTask& T = tasks[task_s];
+        __syncthreads();  // every thread has read the claim before the next one overwrites it
+        if (it >= n_items) break;
+        const int nxy = T.g.n_mb * T.g.n_bb;
+        const int local = (int)(it - T.item0);
+        accum_cta<16, KIND, 0>(T.a, T.g, local % nxy, local / nxy, smem4);
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
+// Fixed-order sums of every task's chunk partials into its output: one thread per (task, microphone, bin).
+__global__ void k_reduce_tasks(const AccumTask* tasks, int32_t n_tasks, int64_t n_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_out; i += stride) {
+        int lo = 0, hi = n_tasks - 1;  // last task whose first output is <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tasks[mid].out0 <= i) lo = mid; else hi = mid - 1;
+        }
+        const AccumTask& T = tasks[lo];
+        const int64_t MF = (int64_t)T.a.M * T.a.F, l = i - T.out0;
+        float sx = 0.0f, sy = 0.0f;
+        for (int c = 0; c < T.a.n_chunks; ++c) {
+            const float2 v = T.a.partial[(int64_t)c * MF + l];
+            sx += v.x;
+            sy += v.y;
+        }
+        T.out[l] = make_float2(sx, sy);
     }
 }
 
@@ -418,16 +481,21 @@ void read_tile_env() {
     }
 }
 
-template <int KT, int KIND, int DIR>
-cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
+// tile shape of one accumulation (kind 0 specular, 1 diffraction): the tuner's or the defaults
+Geom accum_geom(const AccumArgs& a, int kind, int kt, int dir) {
     read_tile_env();
     // diffraction paths whose factor is read from the material table: half the microphone pairs per CTA, so
     // that a CTA covers twice the bins and each (path, microphone) anchor is formed half as often (the tile
     // has no per-(path, bin) table whose cost would grow in return)
-    const bool direct_mat = KIND == 1 && !a.etab;
+    const bool direct_mat = kind == 1 && !a.etab;
     const int tp = a.tile_tp > 0 ? a.tile_tp : (direct_mat && !g_tile_env_set ? std::max(1, g_tile_tp / 2) : g_tile_tp);
     const size_t budget = a.tile_kb > 0 ? (size_t)a.tile_kb * 1024 : g_tile_budget;
-    const Geom g = make_geom(a.M, a.F, KT, a.n_mat_tab, tp, budget, DIR ? a.n_bands_tab : 0, direct_mat);
+    return make_geom(a.M, a.F, kt, a.n_mat_tab, tp, budget, dir ? a.n_bands_tab : 0, direct_mat);
+}
+
+template <int KT, int KIND, int DIR>
+cudaError_t launch_accum(const AccumArgs& a, cudaStream_t s) {
+    const Geom g = accum_geom(a, KIND, KT, DIR);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
@@ -579,6 +647,41 @@ cudaError_t accumulate(const AccumArgs& a, cudaStream_t s) {
     if (a.mic_tab) return a.kind == 0 ? launch_accum<16, 0, 1>(a, s) : launch_accum<16, 1, 1>(a, s);
     if (g_tile_kt == 8) return a.kind == 0 ? launch_accum<8, 0, 0>(a, s) : launch_accum<8, 1, 0>(a, s);
     return a.kind == 0 ? launch_accum<16, 0, 0>(a, s) : launch_accum<16, 1, 0>(a, s);
+}
+
+cudaError_t accum_task(const AccumArgs& a, float2* out, AccumTask* t) {
+    t->a = a;
+    t->g = accum_geom(a, a.kind, 16, 0);
+    t->out = out;
+    return cudaSuccess;
+}
+
+cudaError_t accumulate_queue(int kind, const AccumTask* tasks, int32_t n_tasks, int64_t n_items, size_t smem,
+                             unsigned long long* counter, cudaStream_t s) {
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[kind]) {
+        cudaError_t e = cudaFuncSetAttribute(kind == 0 ? k_accum_queue<0> : k_accum_queue<1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set[kind] = true;
+    }
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n_tasks <= 0 || n_items <= 0) return e;
+    int dev = 0, n_sm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = smem > 110 * 1024 ? 1 : 2;
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)n_sm * per_sm, n_items);
+    note_launch();
+    if (kind == 0) k_accum_queue<0><<<grid, 256, smem, s>>>(tasks, n_tasks, n_items, counter);
+    else k_accum_queue<1><<<grid, 256, smem, s>>>(tasks, n_tasks, n_items, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_tasks(const AccumTask* tasks, int32_t n_tasks, int64_t n_out, cudaStream_t s) {
+    if (n_tasks <= 0 || n_out <= 0) return cudaSuccess;
+    note_launch();
+    k_reduce_tasks<<<grid_for(n_out, 256), 256, 0, s>>>(tasks, n_tasks, n_out);
+    return cudaGetLastError();
 }
 
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s) {

@@ -567,4 +567,23 @@ inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t bu
 }
 
 }  // namespace acc
+
+// One (job, path kind) accumulation of a batch for the persistent launch: its arguments (a.partial: its chunk
+// partials [n_chunks][M][F]), tile shape and output [M][F]; its work items (CTAs) are item0 .. item0 +
+// n_mb n_bb n_chunks - 1 of the launch and its outputs out0 .. out0 + M F - 1 of the reduction.
+struct AccumTask {
+    AccumArgs a;
+    acc::Geom g;
+    float2* out;
+    int64_t item0, out0;
+};
+// fills t->a, t->g and t->out (the general accumulator's tile shape, 16 bins per thread, omni receivers)
+cudaError_t accum_task(const AccumArgs& a, float2* out, AccumTask* t);
+// the persistent accumulation of the tasks of one path kind (device table, items numbered from 0); smem = the
+// largest tile's shared memory; counter: one device word, reset here
+cudaError_t accumulate_queue(int kind, const AccumTask* tasks, int32_t n_tasks, int64_t n_items, size_t smem,
+                             unsigned long long* counter, cudaStream_t s);
+// fixed-order sums of the tasks' chunk partials into their outputs (outputs numbered from 0 over the tasks)
+cudaError_t reduce_tasks(const AccumTask* tasks, int32_t n_tasks, int64_t n_out, cudaStream_t s);
+
 }  // namespace st

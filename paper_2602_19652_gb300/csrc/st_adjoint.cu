@@ -87,7 +87,7 @@ __device__ __forceinline__ void rs_reduce(float (&v)[8], int tp, unsigned wm) {
 template <int KT, int KIND, int TPL, int EMIT>
 __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     k_adjoint(const AccumArgs a, const AdjointArgs j, const Geom g) {
-    static_assert(KT == 8, "the reduce-scatter of the reflection sums takes 8 bins per thread");
+    static_assert(KIND == 1 || KT == 8, "the reduce-scatter of the reflection sums takes 8 bins per thread");
     constexpr int VR = RS<TPL>::VR;
     extern __shared__ float4 smem4[];
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 }
             }
             // reflection-coefficient sums for the materials of the path's chain
-            if (KIND == 0 && j.do_k && pv[p]) {
+            if constexpr (KIND == 0) if (j.do_k && pv[p]) {
                 rs_reduce<TPL>(y, tp, wm);
                 const uint32_t meta = __float_as_uint(pd[p * 12 + 8]);
                 const int len = meta & 15, matj = (meta >> 8) & 255;
@@ -636,11 +636,11 @@ size_t adjoint_smem(const acc::Geom& g) {
     return std::max(total, red);
 }
 
-acc::Geom adjoint_geom(int M, int F, int n_mat, int mat_direct) {
-    // tile shape of the forward with 8 bins per thread and up to 16 microphone pairs per CTA, the pair
-    // count a power of two (the reflection sums are reduce-scattered across the pair lanes); paths
-    // per tile as many as fit about 100 KB, so that two CTAs share an SM
-    acc::Geom g = acc::make_geom(M, F, 8, n_mat, 16, 200 * 1024, 0, mat_direct);
+acc::Geom adjoint_geom(int M, int F, int n_mat, int mat_direct, int tp_max, int kt) {
+    // tile shape of the forward with kt bins per thread (8 where the reflection sums are reduce-scattered across
+    // the pair lanes, 16 for diffraction paths) and up to tp_max microphone pairs per CTA, the pair count a power
+    // of two; paths per tile as many as fit about 100 KB, so that two CTAs share an SM
+    acc::Geom g = acc::make_geom(M, F, kt, n_mat, tp_max, 200 * 1024, 0, mat_direct);
     int tp2 = 1;
     while (tp2 * 2 <= g.TP) tp2 *= 2;
     g.TP = tp2;
@@ -658,7 +658,7 @@ acc::Geom adjoint_geom(int M, int F, int n_mat, int mat_direct) {
 }
 
 cudaError_t adjoint_launch(const AccumArgs& a, const AdjointArgs& j, const acc::Geom& g, cudaStream_t s) {
-    if (a.kind == 1) return launch_adjoint<8, 1, 0>(a, j, g, s);
+    if (a.kind == 1) return g.KB == 16 * g.NS ? launch_adjoint<16, 1, 0>(a, j, g, s) : launch_adjoint<8, 1, 0>(a, j, g, s);
     if (a.jac && j.do_pos) {
         switch (g.TP) {
             case 1: return launch_adjoint<8, 0, 0, 1>(a, j, g, s);

@@ -124,7 +124,7 @@ struct st_ctx {
 struct BatchState {
     uint64_t key = 0;
     bool valid = false;
-    int32_t n_jobs = 0, max_b = 0, n_branches = 0;
+    int32_t n_jobs = 0, max_b = 0;
     std::vector<AccumTables> tables;
     std::vector<JobDev> jobs;
     std::vector<int32_t> chunks_spec, chunks_diff;
@@ -136,13 +136,19 @@ struct BatchState {
     DevBuf rec_mask, vis_qm;              // per-microphone receiver test
     bool per_mic = false;
     int64_t Q_total = 0;                  // per-microphone visibility queries a bounce, at most
-    std::vector<DevBuf> partial;  // one per branch
+    DevBuf narrow_partial;  // chunk partials of the one-pair jobs (accumulated one after the other)
+    // persistent accumulation: one task per (job, path kind) -- the specular tasks, then the diffraction ones
+    // -- their chunk partials, the work-item counter, item counts and the largest tile's shared memory
+    std::vector<int32_t> narrow_jobs;  // jobs of one microphone pair: the narrow accumulator, launched per job
+    DevBuf tasks, part_all, qctr;
+    int32_t n_tasks_spec = 0, n_tasks_diff = 0;
+    int64_t items_spec = 0, items_diff = 0, n_out = 0;
+    size_t smem_spec = 0, smem_diff = 0;
     PathList spec, diff;
     int64_t N_total = 0, R_total = 0, K_total = 0, M_total = 0, MF_total = 0;
     cudaStream_t main = nullptr;     // the batch runs here (capturable even when the context's stream is
                                      // the legacy default stream), ordered after/before the context's stream
-    std::vector<cudaStream_t> streams;  // accumulation branches
-    std::vector<cudaEvent_t> events;    // [0] fork, [1..n_branches] joins, then context -> main, main -> context
+    std::vector<cudaEvent_t> events;    // context -> main, main -> context
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -198,6 +204,9 @@ st_status cuda_fail(st_ctx* c, cudaError_t e, const char* where) {
 
 cudaMemcpyKind kind_in(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_out(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+// a batched job's accumulation takes about 1/kBatchChunkDiv of the chunks that would fill the GPU alone
+constexpr int kBatchChunkDiv = 8;
 
 // triangle count from which the visibility queries of a simulate are sorted by hit point (the 4-wide
 // hierarchy and the triangles then take well over half of L2)
@@ -1286,7 +1295,21 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
     ja.w_0 = (float)(2.0 * M_PI * c->f_lo / p.c);
     ja.w_step = (float)(2.0 * M_PI * T.df / p.c);
 
-    const acc::Geom g = adjoint_geom(M, F, T.n_mat);
+    // microphone pairs per CTA of the specular and diffraction adjoints (ST_ADJ_TP="spec,diff" overrides); the
+    // diffraction adjoint takes 16 bins per thread and 8 pairs, so that a CTA covers 512 bins and forms each
+    // (path, microphone) anchor once on such grids
+    int adj_tp[2] = {16, 8};
+    if (const char* e = getenv("ST_ADJ_TP")) {
+        int u = 0, v = 0;
+        if (sscanf(e, "%d,%d", &u, &v) == 2 && u >= 1 && u <= 16 && v >= 1 && v <= 16) {
+            adj_tp[0] = u;
+            adj_tp[1] = v;
+        }
+    }
+    const acc::Geom g = adjoint_geom(M, F, T.n_mat, 0, adj_tp[0]);
+    // same tile shape for the diffraction paths; without an emitter table their per-(material, bin) factor is
+    // read from the material table, so tiles hold more paths
+    const acc::Geom gd = adjoint_geom(M, F, T.n_mat, aa.etab ? 0 : 1, adj_tp[1], 16);
     const int ctas = g.n_mb * g.n_bb;
     // chunking from the path lists' capacities (the counts stay on the device: no synchronisation)
     const int64_t n_paths = std::max<int64_t>(c->last_N * c->last_B, c->last_K);
@@ -1294,8 +1317,9 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
     const int32_t chunks = (int32_t)std::max<int64_t>(
         1, std::min<int64_t>(152 / std::max(ctas, 1) * 2, (tiles + 7) / 8));
     const int spec_mic_slices = chunks * g.n_bb, spec_emit_slices = chunks * ctas;
-    const int mic_slices = 2 * spec_mic_slices + 1;                 // specular, diffraction, direct
-    const int emit_slices = 2 * spec_emit_slices + M;               // direct: one slice per microphone
+    const int diff_mic_slices = chunks * gd.n_bb, diff_emit_slices = chunks * gd.n_mb * gd.n_bb;
+    const int mic_slices = spec_mic_slices + diff_mic_slices + 1;     // specular, diffraction, direct
+    const int emit_slices = spec_emit_slices + diff_emit_slices + M;  // direct: one slice per microphone
     CKC(c, grow(c->adj_v, (size_t)chunks * g.n_mb * 4 * F * 4), "alloc");
     CKC(c, grow(c->adj_mic, (size_t)mic_slices * M * 3 * 4), "alloc");
     CKC(c, grow(c->adj_emit, (size_t)emit_slices * 3 * 4), "alloc");
@@ -1402,9 +1426,6 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         jj.v_part = ptr<float>(c->adj_v);
         jj.mic_part = micp + (size_t)spec_mic_slices * M * 3;
         jj.emit_part = emitp + (size_t)spec_emit_slices * 3;
-        // same tile shape (pairs, runs, bin blocks) as the specular launches; without an emitter table the
-        // per-(material, bin) factor is read from the material table, so tiles hold more paths
-        const acc::Geom gd = adjoint_geom(M, F, T.n_mat, aa.etab ? 0 : 1);
         CKC(c, adjoint_launch(x, jj, gd, s), "adjoint diffraction");
     }
     // ---- direct path
@@ -1422,7 +1443,8 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         da.a1 = p.alpha1_db_m_khz;
         da.gain = p.direct_gain;
         CKC(c, adjoint_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), G + 2 * MF,
-                              micp + (size_t)2 * spec_mic_slices * M * 3, emitp + (size_t)2 * spec_emit_slices * 3, s),
+                              micp + (size_t)(spec_mic_slices + diff_mic_slices) * M * 3,
+                              emitp + (size_t)(spec_emit_slices + diff_emit_slices) * 3, s),
             "adjoint direct");
     }
     if (want_pos)
@@ -1503,22 +1525,131 @@ void batch_release(BatchState& B) {
                       &B.cand_p, &B.keep, &B.dvis, &B.ranges, &B.sflags, &B.sscan, &B.sidx, &B.scratch, &B.hit_tri,
                       &B.hit_t, &B.vis_q, &B.los_q, &B.rec_mask, &B.vis_qm})
         release(*b);
-    for (auto& d : B.partial) release(d);
+    release(B.narrow_partial);
+    for (DevBuf* d : {&B.tasks, &B.part_all, &B.qctr}) release(*d);
     for (auto& T : B.tables)
         for (DevBuf* b : {&T.lk, &T.g2, &T.lid, &T.qhi, &T.qlo, &T.bw, &T.band, &T.kband, &T.bband}) release(*b);
     for (PathList* P : {&B.spec, &B.diff})
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
                           &P->meta, &P->dep, &P->mask})
             release(*b);
-    for (auto st : B.streams) cudaStreamDestroy(st);
     for (auto ev : B.events) cudaEventDestroy(ev);
     if (B.main) cudaStreamDestroy(B.main);
     B.main = nullptr;
-    B.streams.clear();
     B.events.clear();
 }
 
-// All stages of one batch on stream s (branch streams fork from s and join back).
+// All stages of one batch on stream s.
+// Accumulation arguments of job j's path kind (0 specular, 1 diffraction) in the batch's path lists.
+AccumArgs batch_accum_args(BatchState& B, const st_job* jobs, int j, int kind, const st_sim_params& p,
+                           const st_tune& tn) {
+    const JobDev& jd = B.jobs[j];
+    AccumTables& T = B.tables[j];
+    SceneDev& S = jobs[j].scene->S;
+    const double l2 = log2(10.0) / 20.0;
+    AccumArgs x{};
+    x.mics = jobs[j].mics;
+    x.M = jd.M;
+    x.F = jd.F;
+    x.lk = ptr<float>(T.lk);
+    x.g2 = ptr<float>(T.g2);
+    x.lid = ptr<float>(T.lid);
+    x.n_mat_tab = T.n_mat;
+    x.n_bands_tab = S.n_bands;
+    x.bw = ptr<float2>(T.bw);
+    x.qhi = ptr<float>(T.qhi);
+    x.qlo = ptr<float>(T.qlo);
+    const double dq = T.df / p.c;
+    x.dq_hi = (float)dq;
+    x.dq_lo = (float)(dq - (double)x.dq_hi);
+    x.atm2_0 = (float)(-(p.alpha0_db_m + p.alpha1_db_m_khz * jobs[j].f_lo / 1000.0) * l2);
+    x.atm2_step = (float)(-(p.alpha1_db_m_khz * T.df / 1000.0) * l2);
+    x.reflection_mode = p.reflection_mode;
+    x.tile_tp = tn.mic_pairs_per_cta;
+    x.tile_kb = tn.smem_kb;
+    x.kind = kind;
+    uint32_t* rg = ptr<uint32_t>(B.ranges) + 4 * j;
+    PathList& L = kind == 0 ? B.spec : B.diff;
+    x.n_paths = kind == 0 ? jd.N * jd.B : jd.K;
+    x.d_base = rg + (kind == 0 ? 0 : 2);
+    x.d_count = rg + (kind == 0 ? 1 : 3);
+    x.px = ptr<float>(L.px);
+    x.py = ptr<float>(L.py);
+    x.pz = ptr<float>(L.pz);
+    x.dx = ptr<float>(L.dx);
+    x.dy = ptr<float>(L.dy);
+    x.dz = ptr<float>(L.dz);
+    x.rhi = ptr<float>(L.rhi);
+    x.rlo = ptr<float>(L.rlo);
+    x.chain_lo = ptr<uint32_t>(L.chain_lo);
+    x.chain_hi = ptr<uint32_t>(L.chain_hi);
+    x.meta = ptr<uint32_t>(L.meta);
+    x.dep = ptr<float>(L.dep);
+    x.mask = (kind == 0 && B.per_mic) ? ptr<uint64_t>(B.spec.mask) : nullptr;  // indexed from x.d_base
+    x.n_chunks = kind == 0 ? B.chunks_spec[j] : B.chunks_diff[j];
+    return x;
+}
+
+// The persistent accumulation's task table: per job its specular task (rays) and its diffraction task
+// (samples), each with its chunk partials in one buffer; items and outputs numbered in table order.
+cudaError_t batch_tasks(st_ctx* c, BatchState& B, const st_job* jobs, const st_sim_params& p, const st_tune& tn,
+                        cudaStream_t s) {
+    (void)c;
+    std::vector<AccumTask> spec, diff;
+    B.narrow_jobs.clear();
+    for (int j = 0; j < B.n_jobs; ++j) {
+        const JobDev& jd = B.jobs[j];
+        if (narrow_accum(jd.M)) {  // the single-pose path's accumulator for this shape (same sums)
+            B.narrow_jobs.push_back(j);
+            continue;
+        }
+        float2* out = static_cast<float2*>(jobs[j].spectra_out);
+        const int64_t MF = (int64_t)jd.M * jd.F;
+        if (jd.N > 0) {
+            AccumTask t{};
+            accum_task(batch_accum_args(B, jobs, j, 0, p, tn), out, &t);
+            spec.push_back(t);
+        }
+        if (jd.K > 0) {
+            AccumTask t{};
+            accum_task(batch_accum_args(B, jobs, j, 1, p, tn), out + MF, &t);
+            diff.push_back(t);
+        }
+    }
+    B.n_tasks_spec = (int32_t)spec.size();
+    B.n_tasks_diff = (int32_t)diff.size();
+    std::vector<AccumTask> all(spec);
+    all.insert(all.end(), diff.begin(), diff.end());
+    size_t part = 0;
+    int64_t out0 = 0;
+    B.items_spec = B.items_diff = 0;
+    B.smem_spec = B.smem_diff = 0;
+    for (size_t i = 0; i < all.size(); ++i) {
+        AccumTask& t = all[i];
+        const bool is_spec = i < spec.size();
+        int64_t& items = is_spec ? B.items_spec : B.items_diff;
+        size_t& sm = is_spec ? B.smem_spec : B.smem_diff;
+        t.item0 = items;
+        items += (int64_t)t.g.n_mb * t.g.n_bb * t.a.n_chunks;
+        sm = std::max(sm, t.g.smem);
+        t.out0 = out0;
+        out0 += (int64_t)t.a.M * t.a.F;
+        t.a.partial = reinterpret_cast<float2*>((size_t)part);  // offset for now
+        part += (size_t)t.a.n_chunks * t.a.M * t.a.F * 8;
+    }
+    B.n_out = out0;
+    cudaError_t e;
+    if ((e = grow(B.part_all, std::max<size_t>(part, 256))) != cudaSuccess) return e;
+    for (auto& t : all) t.a.partial = reinterpret_cast<float2*>(static_cast<char*>(B.part_all.p) + (size_t)t.a.partial);
+    if ((e = grow(B.tasks, std::max<size_t>(all.size(), 1) * sizeof(AccumTask))) != cudaSuccess) return e;
+    if ((e = grow(B.qctr, 16)) != cudaSuccess) return e;
+    if (!all.empty() &&
+        (e = cudaMemcpyAsync(B.tasks.p, all.data(), all.size() * sizeof(AccumTask), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(s);  // the host table is freed on return
+}
+
 cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_sim_params& p, const st_tune& tn,
                         cudaStream_t s) {
     cudaError_t e;
@@ -1618,89 +1749,24 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     if (spec || B.K_total > 0)
         CB(batch_ranges(a, ptr<uint32_t>(B.sscan), cnt + 2, ptr<uint32_t>(B.sscan) + Koff, cnt + 3, s));
     if (p.components & ST_COMP_DIRECT) CB(batch_direct_accum(a, s));
-    // per-job accumulation on parallel branches
-    CB(cudaEventRecord(B.events[0], s));
-    for (int b = 0; b < B.n_branches; ++b) CB(cudaStreamWaitEvent(B.streams[b], B.events[0], 0));
-    const double l2 = log2(10.0) / 20.0;
-    for (int j = 0; j < n; ++j) {
-        const int br = j % B.n_branches;
-        cudaStream_t bs = B.streams[br];
-        const JobDev& jd = B.jobs[j];
-        AccumTables& T = B.tables[j];
-        SceneDev& S = jobs[j].scene->S;
-        AccumArgs x{};
-        x.mics = jobs[j].mics;
-        x.M = jd.M;
-        x.F = jd.F;
-        x.lk = ptr<float>(T.lk);
-        x.g2 = ptr<float>(T.g2);
-        x.lid = ptr<float>(T.lid);
-        x.n_mat_tab = T.n_mat;
-        x.n_bands_tab = S.n_bands;
-        x.bw = ptr<float2>(T.bw);
-        x.qhi = ptr<float>(T.qhi);
-        x.qlo = ptr<float>(T.qlo);
-        const double dq = T.df / p.c;
-        x.dq_hi = (float)dq;
-        x.dq_lo = (float)(dq - (double)x.dq_hi);
-        x.atm2_0 = (float)(-(p.alpha0_db_m + p.alpha1_db_m_khz * jobs[j].f_lo / 1000.0) * l2);
-        x.atm2_step = (float)(-(p.alpha1_db_m_khz * T.df / 1000.0) * l2);
-        x.reflection_mode = p.reflection_mode;
-        x.partial = ptr<float2>(B.partial[br]);
-        x.tile_tp = tn.mic_pairs_per_cta;
-        x.tile_kb = tn.smem_kb;
-        const int64_t MF = (int64_t)jd.M * jd.F;
-        float2* out = static_cast<float2*>(jobs[j].spectra_out);
-        uint32_t* rg = ptr<uint32_t>(B.ranges) + 4 * j;
-        if (spec) {
-            AccumArgs y = x;
-            y.kind = 0;
-            y.n_paths = jd.N * jd.B;
-            y.d_base = rg + 0;
-            y.d_count = rg + 1;
-            y.px = ptr<float>(B.spec.px);
-            y.py = ptr<float>(B.spec.py);
-            y.pz = ptr<float>(B.spec.pz);
-            y.dx = ptr<float>(B.spec.dx);
-            y.dy = ptr<float>(B.spec.dy);
-            y.dz = ptr<float>(B.spec.dz);
-            y.rhi = ptr<float>(B.spec.rhi);
-            y.rlo = ptr<float>(B.spec.rlo);
-            y.chain_lo = ptr<uint32_t>(B.spec.chain_lo);
-            y.chain_hi = ptr<uint32_t>(B.spec.chain_hi);
-            y.meta = ptr<uint32_t>(B.spec.meta);
-            y.dep = ptr<float>(B.spec.dep);
-            y.mask = B.per_mic ? ptr<uint64_t>(B.spec.mask) : nullptr;  // indexed from y.d_base
-            y.n_chunks = B.chunks_spec[j];
-            CB(accumulate(y, bs));
-            CB(reduce_partials(y.partial, y.n_chunks, MF, out, bs));
+    {  // every job's accumulation: two persistent launches over (job, tile) items, one reduction
+        const AccumTask* tk = ptr<AccumTask>(B.tasks);
+        unsigned long long* qc = ptr<unsigned long long>(B.qctr);
+        if (spec) CB(accumulate_queue(0, tk, B.n_tasks_spec, B.items_spec, B.smem_spec, qc, s));
+        if (B.K_total > 0) CB(accumulate_queue(1, tk + B.n_tasks_spec, B.n_tasks_diff, B.items_diff, B.smem_diff, qc + 1, s));
+        if (spec || B.K_total > 0) CB(reduce_tasks(tk, B.n_tasks_spec + B.n_tasks_diff, B.n_out, s));
+        for (const int j : B.narrow_jobs) {
+            const JobDev& jd = B.jobs[j];
+            const int64_t MF = (int64_t)jd.M * jd.F;
+            float2* out = static_cast<float2*>(jobs[j].spectra_out);
+            for (int kind = 0; kind < 2; ++kind) {
+                if (kind == 0 ? !(spec && jd.N > 0) : jd.K <= 0) continue;
+                AccumArgs y = batch_accum_args(B, jobs, j, kind, p, tn);
+                y.partial = ptr<float2>(B.narrow_partial);
+                CB(accumulate(y, s));
+                CB(reduce_partials(y.partial, y.n_chunks, MF, out + kind * MF, s));
+            }
         }
-        if (jd.K > 0) {
-            AccumArgs y = x;
-            y.kind = 1;
-            y.n_paths = jd.K;
-            y.d_base = rg + 2;
-            y.d_count = rg + 3;
-            y.px = ptr<float>(B.diff.px);
-            y.py = ptr<float>(B.diff.py);
-            y.pz = ptr<float>(B.diff.pz);
-            y.dx = ptr<float>(B.diff.dx);
-            y.dy = ptr<float>(B.diff.dy);
-            y.dz = ptr<float>(B.diff.dz);
-            y.chain_lo = ptr<uint32_t>(B.diff.chain_lo);
-            y.chain_hi = ptr<uint32_t>(B.diff.chain_hi);
-            y.rhi = ptr<float>(B.diff.rhi);
-            y.rlo = ptr<float>(B.diff.rlo);
-            y.meta = ptr<uint32_t>(B.diff.meta);
-            y.dep = ptr<float>(B.diff.dep);
-            y.n_chunks = B.chunks_diff[j];
-            CB(accumulate(y, bs));
-            CB(reduce_partials(y.partial, y.n_chunks, MF, out + MF, bs));
-        }
-    }
-    for (int b = 0; b < B.n_branches; ++b) {
-        CB(cudaEventRecord(B.events[1 + b], B.streams[b]));
-        CB(cudaStreamWaitEvent(s, B.events[1 + b], 0));
     }
 #undef CB
     return cudaSuccess;
@@ -1786,7 +1852,6 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     B.jobs.resize(n_jobs);
     B.chunks_spec.resize(n_jobs);
     B.chunks_diff.resize(n_jobs);
-    B.n_branches = std::min(8, n_jobs);
     std::vector<int64_t> ho(5 * (size_t)(n_jobs + 1), 0);
     int64_t* ray_o = ho.data();
     int64_t* rec_o = ray_o + (n_jobs + 1);
@@ -1862,7 +1927,7 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
         if (per_mic && P == &B.spec) CKC(c, grow(P->mask, (size_t)nP * 8), "batch alloc");  // u64 per path
         P->n_max = nP;
     }
-    std::vector<size_t> part_bytes(B.n_branches, 256);
+    size_t narrow_part = 256;  // chunk partials of the largest one-pair job (launched on its own)
     float* derived = ptr<float>(B.derived);
     for (int j = 0; j < n_jobs; ++j) {
         const st_job& J = jobs[j];
@@ -1912,21 +1977,20 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
         d.f_lo = J.f_lo;
         d.df = B.tables[j].df;
         d.out = static_cast<float2*>(J.spectra_out);
-        // chunks: the branches share the GPU, so each job uses about 1/branches of it
-        const int nb = B.n_branches;
+        // chunks: the jobs share the GPU, so each job's accumulation is split into about an eighth of the
+        // chunks that would fill it alone (fewer partial spectra to sum)
+        const int nb = kBatchChunkDiv;
         B.chunks_spec[j] = std::max(1, accum_chunks(d.N * d.B, d.M, d.F, S.n_mat, 0, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
         B.chunks_diff[j] = std::max(1, accum_chunks(d.K, d.M, d.F, S.n_mat, 0, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
-        const size_t need = (size_t)std::max(B.chunks_spec[j], B.chunks_diff[j]) * d.M * d.F * 8;
-        part_bytes[j % nb] = std::max(part_bytes[j % nb], need);
+        if (narrow_accum(d.M))
+            narrow_part = std::max(narrow_part, (size_t)std::max(B.chunks_spec[j], B.chunks_diff[j]) * d.M * d.F * 8);
     }
-    B.partial.resize(B.n_branches);
-    for (int b = 0; b < B.n_branches; ++b) CKC(c, grow(B.partial[b], part_bytes[b]), "batch alloc");
+    CKC(c, grow(B.narrow_partial, narrow_part), "batch alloc");
+    CKC(c, batch_tasks(c, B, jobs, p, tn, s), "batch tasks");
     CKC(c, grow(B.jobs_dev, sizeof(JobDev) * (size_t)n_jobs), "batch alloc");
     CKC(c, cudaMemcpyAsync(B.jobs_dev.p, B.jobs.data(), sizeof(JobDev) * (size_t)n_jobs, cudaMemcpyHostToDevice, s),
         "batch copy");
-    B.streams.resize(B.n_branches);
-    for (auto& st : B.streams) CKC(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch streams");
-    B.events.resize(3 + B.n_branches);
+    B.events.resize(2);  // context -> batch stream, batch stream -> context
     for (auto& ev : B.events) CKC(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch events");
     CKC(c, cudaStreamCreateWithFlags(&B.main, cudaStreamNonBlocking), "batch streams");
     CKC(c, cudaStreamSynchronize(s), "batch setup");

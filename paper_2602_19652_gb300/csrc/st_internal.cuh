@@ -452,7 +452,7 @@ cudaError_t accumulate_direct(const DirectAccumArgs& a, const float* qhi, const 
 namespace acc {
 struct Geom;
 }
-acc::Geom adjoint_geom(int M, int F, int n_mat, int mat_direct = 0);
+acc::Geom adjoint_geom(int M, int F, int n_mat, int mat_direct = 0, int tp_max = 16, int kt = 8);
 size_t adjoint_smem(const acc::Geom& g);
 cudaError_t adjoint_launch(const AccumArgs& a, const AdjointArgs& j, const acc::Geom& g, cudaStream_t s);
 cudaError_t adjoint_direct(const DirectAccumArgs& a, const float* qhi, const float* qlo, const float2* G,

@@ -123,3 +123,17 @@ def test_autograd_lobe_widths(torch_st):
     gb = ctx.backward_beta(sc, 2.0 * S.detach(), b.shape[0], b.shape[1])
     assert float(gb.abs().max()) > 0
     assert torch.allclose(b.grad, gb, rtol=1e-4, atol=1e-4 * float(gb.abs().max()))
+
+
+def test_gradient_workload_full_size(torch_st):
+    """The differentiation workload at its stated size: the four-material room, 10k rays x 3 bounces, the
+    32-microphone disc array, 128 bins; gradients of the L2 loss against target spectra with respect to the
+    4 x 16 reflection values and the 32 microphone positions (and the emitter) within 1e-3 of the oracle's
+    float64 analytic gradient."""
+    torch, st = torch_st
+    wl = synth.gradient_problem(n_rays=10_000)
+    assert wl.n_bins == 128 and len(wl.mics) == 32 and wl.k_band.shape == (4, 16)
+    gk, gm, ge, dk, dmic, demit = grads_vs_oracle(torch, st, wl)
+    assert rel(gk, dk) <= TOL, rel(gk, dk)
+    assert rel(gm, dmic) <= TOL, rel(gm, dmic)
+    assert rel(ge, demit) <= TOL, rel(ge, demit)
