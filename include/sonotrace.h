@@ -301,6 +301,11 @@ typedef struct st_tune {
                                    need more restarts from the root with a walk that needs no stack (fixed
                                    child order, parent references in the nodes), keeping its best hit, so
                                    results do not depend on it; st_stats.stack_restarts counts the restarts */
+    int32_t refill_lanes;       /* rays per warp refill: the persistent traversal kernels give new queries to a
+                                   warp's idle lanes once this many of its 32 lanes wait, 1..32 (0 = 16 for
+                                   closest hits, 28 for visibility rays) */
+    int32_t bins_per_thread;    /* frequency tile: bins a thread of the general accumulator advances, 8 or 16
+                                   (0 = 16; the batched form takes 16) */
 } st_tune;
 
 st_status st_simulate_batch(st_ctx* ctx, int32_t n_jobs, const st_job* jobs, const st_sim_params* params,

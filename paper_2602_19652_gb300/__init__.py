@@ -260,9 +260,10 @@ class Context:
                     j.set_pose(emitter=E[i], emitter_quat=Q[i])
             return torch.stack(self.simulate_batch(self._emit_jobs, params))
 
-    def set_tune(self, rays_per_block: int = 0, mic_pairs_per_cta: int = 0, smem_kb: int = 0, stack_depth: int = 0):
+    def set_tune(self, rays_per_block: int = 0, mic_pairs_per_cta: int = 0, smem_kb: int = 0, stack_depth: int = 0,
+                 refill_lanes: int = 0, bins_per_thread: int = 0):
         """Launch shapes of later simulate calls (0 = the library's default for each)."""
-        t = Tune(rays_per_block, mic_pairs_per_cta, smem_kb, stack_depth)
+        t = Tune(rays_per_block, mic_pairs_per_cta, smem_kb, stack_depth, refill_lanes, bins_per_thread)
         self._check(self.L.st_set_tune(self.h, C.byref(t)))
 
     def autotune(self, job: "BatchJob", params: SimParams | None = None) -> Tune:

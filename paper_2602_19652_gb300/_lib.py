@@ -51,7 +51,8 @@ class Job(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("rays_per_block", I32), ("mic_pairs_per_cta", I32), ("smem_kb", I32), ("stack_depth", I32)]
+    _fields_ = [("rays_per_block", I32), ("mic_pairs_per_cta", I32), ("smem_kb", I32), ("stack_depth", I32),
+                ("refill_lanes", I32), ("bins_per_thread", I32)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/sonotrace.h

@@ -570,12 +570,12 @@ __global__ void k_gather_diff_batch(const BatchArgs a, const uint32_t* idx, cons
 }  // namespace
 
 int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb, int32_t tile_tp,
-                     int32_t tile_kb) {
+                     int32_t tile_kb, int32_t tile_kt) {
     if (narrow_accum(M)) return narrow_chunks(n_paths_hint, M, F, n_mat, dir_nb);
     read_tile_env();
     const int tp = tile_tp > 0 ? tile_tp : g_tile_tp;
     const size_t budget = tile_kb > 0 ? (size_t)tile_kb * 1024 : g_tile_budget;
-    const Geom g = make_geom(M, F, dir_nb ? 16 : g_tile_kt, n_mat, tp, budget, dir_nb);
+    const Geom g = make_geom(M, F, dir_nb ? 16 : (tile_kt > 0 ? tile_kt : g_tile_kt), n_mat, tp, budget, dir_nb);
     const int ctas_per_chunk = g.n_mb * g.n_bb;
     const int threads = g.TP * g.NS;
     int resident = std::max(1, std::min(2048 / std::max(threads, 32), (int)((220 * 1024) / std::max<size_t>(g.smem, 1))));
@@ -645,7 +645,8 @@ cudaError_t accumulate(const AccumArgs& a, cudaStream_t s) {
     if (narrow_accum(a.M)) return accumulate_narrow(a, s);
     read_tile_env();
     if (a.mic_tab) return a.kind == 0 ? launch_accum<16, 0, 1>(a, s) : launch_accum<16, 1, 1>(a, s);
-    if (g_tile_kt == 8) return a.kind == 0 ? launch_accum<8, 0, 0>(a, s) : launch_accum<8, 1, 0>(a, s);
+    if ((a.tile_kt > 0 ? a.tile_kt : g_tile_kt) == 8)
+        return a.kind == 0 ? launch_accum<8, 0, 0>(a, s) : launch_accum<8, 1, 0>(a, s);
     return a.kind == 0 ? launch_accum<16, 0, 0>(a, s) : launch_accum<16, 1, 0>(a, s);
 }
 

@@ -810,8 +810,10 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         CKC(c, grow(c->keep, (size_t)K), "alloc");
         CKC(c, grow(c->los_q, (size_t)K * 4), "alloc");
     }
-    const int32_t chunks_spec = accum_chunks(NB, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb);
-    const int32_t chunks_diff = accum_chunks(K, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb);
+    const int32_t chunks_spec =
+        accum_chunks(NB, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb, c->tune.bins_per_thread);
+    const int32_t chunks_diff =
+        accum_chunks(K, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb, c->tune.bins_per_thread);
     const int32_t chunks = std::max(chunks_spec, chunks_diff);
     CKC(c, grow(c->partial, (size_t)chunks * M * F * 8), "alloc");
 
@@ -855,6 +857,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         ta.visits = c->count_visits ? qctr + 2 : nullptr;
         ta.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
         ta.restarts = qctr + 6;
+        ta.refill = c->tune.refill_lanes;
         ta.nrm = ptr<float>(S.nrm);
         memcpy(ta.s, c->s, 12);
         memcpy(ta.q, c->q, 16);
@@ -914,6 +917,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         da.visits = c->count_visits ? qctr + 2 : nullptr;
         da.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
         da.restarts = qctr + 6;
+        da.refill = c->tune.refill_lanes;
         da.nrm = ptr<float>(S.nrm);
         da.verts = ptr<float>(S.verts);
         da.tris = ptr<int32_t>(S.tris);
@@ -983,6 +987,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     aa.partial = ptr<float2>(c->partial);
     aa.tile_tp = c->tune.mic_pairs_per_cta;
     aa.tile_kb = c->tune.smem_kb;
+    aa.tile_kt = c->tune.bins_per_thread;
 
     GatherArgs ga{};
     ga.N = N;
@@ -1080,6 +1085,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
         dv.visits = c->count_visits ? qctr + 2 : nullptr;
         dv.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
         dv.restarts = qctr + 6;
+        dv.refill = c->tune.refill_lanes;
         memcpy(dv.s, c->s, 12);
         dv.mics = ptr<float>(c->mics);
         dv.M = M;
@@ -1507,7 +1513,9 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
 bool tune_ok(const st_tune& t) {
     return (t.rays_per_block == 0 || t.rays_per_block == 64 || t.rays_per_block == 128 || t.rays_per_block == 256) &&
            (t.mic_pairs_per_cta == 0 || (t.mic_pairs_per_cta >= 1 && t.mic_pairs_per_cta <= 16)) &&
-           (t.smem_kb == 0 || (t.smem_kb >= 32 && t.smem_kb <= 160)) && t.stack_depth >= 0 && t.stack_depth <= kStack;
+           (t.smem_kb == 0 || (t.smem_kb >= 32 && t.smem_kb <= 160)) && t.stack_depth >= 0 && t.stack_depth <= kStack &&
+           t.refill_lanes >= 0 && t.refill_lanes <= 32 &&
+           (t.bins_per_thread == 0 || t.bins_per_thread == 8 || t.bins_per_thread == 16);
 }
 
 void batch_free_graph(BatchState& B) {
@@ -1706,6 +1714,7 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     a.ranges = ptr<uint32_t>(B.ranges);
     a.flags = ptr<uint32_t>(B.flags);
     a.stack_limit = tn.stack_depth > 0 ? std::min(tn.stack_depth, kStack) : kStack;
+    a.refill = tn.refill_lanes;
     a.queries = ptr<unsigned long long>(B.queries);
     a.hit_tri = ptr<int32_t>(B.hit_tri);
     a.hit_t = ptr<float>(B.hit_t);
@@ -1833,7 +1842,8 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     key = fnv(key, &pg, sizeof(pg));
     const int64_t pi[4] = {(int64_t)p.components, (int64_t)p.reflection_mode, (int64_t)p.seed, (int64_t)p.los_mode};
     key = fnv(key, pi, sizeof(pi));
-    const int32_t ti[4] = {tn.rays_per_block, tn.mic_pairs_per_cta, tn.smem_kb, tn.stack_depth};
+    const int32_t ti[6] = {tn.rays_per_block, tn.mic_pairs_per_cta, tn.smem_kb, tn.stack_depth, tn.refill_lanes,
+                           tn.bins_per_thread};
     key = fnv(key, ti, sizeof(ti));
     if (B.valid && B.key == key && B.exec) {
         const int ne = (int)B.events.size();
@@ -2045,18 +2055,31 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
     const st_tune saved = c->tune;
     const int rpb[3] = {64, 128, 256};
     const int tiles[5][2] = {{16, 96}, {8, 96}, {16, 64}, {4, 96}, {16, 128}};
-    st_tune best = {128, 16, 96, saved.stack_depth};
-    // tracing block size with the default tile, then the accumulator tile with the best block size
-    for (int phase = 0; phase < 2; ++phase) {
-        const int n_cand = phase == 0 ? 3 : 5;
+    const int kts[2] = {16, 8};
+    const int depths[3] = {0, 48, 24};
+    const int refills[4] = {0, 12, 20, 32};
+    st_tune best = {128, 16, 96, 0, 0, 0};
+    // one parameter at a time, each with the best of the earlier ones: the tracing block size, the accumulator
+    // tile (microphone pairs and shared memory), its bins per thread (frequency tile), the traversal stack depth
+    // and the lane-refill threshold (rays per warp refill); tracing phases are timed on tracing and diffraction,
+    // the others on the accumulator kernels
+    const int n_phase[5] = {3, 5, 2, 3, 4};
+    for (int phase = 0; phase < 5; ++phase) {
+        const int n_cand = n_phase[phase];
         st_tune winner = best;
         float winner_ms = 1e30f;
         for (int i = 0; i < n_cand; ++i) {
             st_tune t = best;
             if (phase == 0) t.rays_per_block = rpb[i];
-            else {
+            else if (phase == 1) {
                 t.mic_pairs_per_cta = tiles[i][0];
                 t.smem_kb = tiles[i][1];
+            } else if (phase == 2) {
+                t.bins_per_thread = kts[i];
+            } else if (phase == 3) {
+                t.stack_depth = depths[i];
+            } else {
+                t.refill_lanes = refills[i];
             }
             c->tune = t;
             st_stats st;
@@ -2068,7 +2091,8 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
                     release(out_buf);
                     return r;
                 }
-                if (rep > 0) acc += phase == 0 ? st.ms_trace : st.ms_accum_kernel;
+                const bool tracing = phase == 0 || phase >= 3;
+                if (rep > 0) acc += tracing ? st.ms_trace + st.ms_diffraction : st.ms_accum_kernel;
             }
             if (acc < winner_ms) {
                 winner_ms = acc;

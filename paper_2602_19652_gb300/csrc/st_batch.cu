@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_closest_batch(const BatchArgs
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefillClosest) break;
+            if (lv == 0u || __popc(nd) >= (a.refill > 0 ? a.refill : kRefillClosest)) break;
         }
     }
 }
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_batch(const BatchArgs
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefillAny) break;
+            if (lv == 0u || __popc(nd) >= (a.refill > 0 ? a.refill : kRefillAny)) break;
         }
     }
 }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics_batch(const Batc
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefillAny) break;
+            if (lv == 0u || __popc(nd) >= (a.refill > 0 ? a.refill : kRefillAny)) break;
         }
     }
 }

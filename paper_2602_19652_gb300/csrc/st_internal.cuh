@@ -140,6 +140,7 @@ struct TraceArgs {
     unsigned long long* visits;
     int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
     unsigned long long* restarts;  // device counter of stackless restarts (or null)
+    int32_t refill;  // lane-refill threshold of the persistent traversal kernels (0 = default)
     const float* nrm;
     // rays
     float s[3];
@@ -193,6 +194,7 @@ struct DiffArgs {
     unsigned long long* visits;
     int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
     unsigned long long* restarts;  // device counter of stackless restarts (or null)
+    int32_t refill;  // lane-refill threshold of the persistent traversal kernels (0 = default)
     const float* nrm;
     const float* verts;
     const int32_t* tris;
@@ -230,6 +232,7 @@ struct DirectArgs {
     unsigned long long* visits;
     int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
     unsigned long long* restarts;  // device counter of stackless restarts (or null)
+    int32_t refill;  // lane-refill threshold of the persistent traversal kernels (0 = default)
     float s[3];
     const float* mics;
     int32_t M;
@@ -271,6 +274,7 @@ struct AccumArgs {
     const uint64_t* mask;   // optional (per-microphone receiver test): bit m of mask[path] = microphone m
                             // receives the path; null = every microphone
     int32_t tile_tp, tile_kb;  // optional tile override: mic pairs per CTA, shared-memory KB (0 = default)
+    int32_t tile_kt;           // optional: bins per thread of the general accumulator, 8 or 16 (0 = default)
     const float* px; const float* py; const float* pz;
     const float* dx; const float* dy; const float* dz;
     const float* rhi; const float* rlo;
@@ -301,7 +305,7 @@ cudaError_t build_accum_tables(AccumTables& T, const SceneDev& S, int32_t F, dou
 cudaError_t accumulate(const AccumArgs& a, cudaStream_t s);
 cudaError_t reduce_partials(const float2* partial, int32_t n_chunks, int64_t MF, float2* out, cudaStream_t s);
 int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb, int32_t tile_tp = 0,
-                     int32_t tile_kb = 0);
+                     int32_t tile_kb = 0, int32_t tile_kt = 0);
 // emitter ray sets (st_rays.cu): kind 0 spherical Fibonacci, 1 zonal equal-area centres
 cudaError_t ray_directions(int kind, int64_t n, float* out, DevBuf& scratch, cudaStream_t s);
 // impulse responses / received signals from accumulated spectra (st_signal.cu)
@@ -403,6 +407,7 @@ struct BatchArgs {
     uint32_t* flags;
     unsigned long long* queries;
     int32_t stack_limit;       // traversal stack entries per query (1..kStack; more: the query restarts stackless)
+    int32_t refill;            // lane-refill threshold of the persistent traversal kernels (0 = default)
     // per-microphone receiver test (null otherwise): visible microphones of each record [R_total], and the
     // visibility queue of (record << 6 | microphone) entries, at most Q_total = sum over jobs of N x M a bounce
     uint64_t* rec_mask;

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, in
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefillClosest) break;
+            if (lv == 0u || __popc(nd) >= (T.refill > 0 ? T.refill : kRefillClosest)) break;
         }
     }
 }
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const u
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefillAny) break;
+            if (lv == 0u || __popc(nd) >= (T.refill > 0 ? T.refill : kRefillAny)) break;
         }
     }
 }
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics(const TraceArgs 
             }
             const unsigned lv = __ballot_sync(full, live);
             const unsigned nd = __ballot_sync(full, !live && !exhausted);
-            if (lv == 0u || __popc(nd) >= kRefillAny) break;
+            if (lv == 0u || __popc(nd) >= (T.refill > 0 ? T.refill : kRefillAny)) break;
         }
     }
 }

@@ -17,6 +17,7 @@ struct Trav {
     unsigned long long* visits;     // optional [4]: nodes and triangles visited (closest, any-hit)
     int32_t stack_limit = kStack;   // stack entries a query may use (1..kStack) before it restarts stackless
     unsigned long long* restarts = nullptr;  // optional: queries that restarted from the root
+    int32_t refill = 0;  // lanes of a warp waiting for a query before it refills them (0: the kernel's default)
 };
 
 __device__ __forceinline__ float safe_inv(float d) {

@@ -218,6 +218,7 @@ def test_autotune_shapes_give_same_results(st):
     t = ctx.autotune(jobs[0], p)
     assert t.rays_per_block in (64, 128, 256)
     assert 1 <= t.mic_pairs_per_cta <= 16 and 32 <= t.smem_kb <= 160
+    assert t.bins_per_thread in (8, 16) and t.stack_depth in (0, 48, 24) and t.refill_lanes in (0, 12, 20, 32)
     tuned = [o.cpu().numpy() for o in ctx.simulate_batch(jobs, p, t)]
     for a, b in zip(tuned, base):
         for c in range(3):
@@ -242,3 +243,23 @@ def test_batch_stack_restarts_keep_results_exact():
     ctx.simulate_batch(jobs, p, tune=st.Tune(0, 0, 0, 2))
     for j, r in zip(jobs, ref):
         assert np.array_equal(j.out.cpu().numpy(), r)
+
+
+def test_single_pose_tuning_parameters(st):
+    """Each tuned parameter of the single-pose path: the stack depth and the lane-refill threshold change
+    only the order in which queries are traced (spectra bit-identical), the accumulator's 8 or 16 bins per
+    thread only the order of its float32 sums (within the single-pose tolerance)."""
+    wl = synth.clutter(seed=214, target_tris=6000, n_rays=4000, bounces=3, n_mics=8, n_bins=100)
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, st.curv_params(sample_budget=20_000))
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    ref = ctx.simulate(sc, p).cpu().numpy()
+    for kw in (dict(refill_lanes=8), dict(refill_lanes=32), dict(stack_depth=24, refill_lanes=20)):
+        ctx.set_tune(**kw)
+        assert np.array_equal(ctx.simulate(sc, p).cpu().numpy(), ref), kw
+    ctx.set_tune(bins_per_thread=8)
+    S8 = ctx.simulate(sc, p).cpu().numpy()
+    for c in range(3):
+        assert rel_l2(S8[c], ref[c]) <= TOL_SINGLE
+    with pytest.raises(st.SonotraceError):
+        ctx.set_tune(bins_per_thread=4)
