@@ -562,16 +562,16 @@ def measure_traversal(st, torch, wl, ms_trace: float, ms_diffraction: float, hbm
     q_d = (s_all.shadow_queries - s_spec.shadow_queries)
     l2 = l2_probe_gbs(torch)
     ft, fd = bt / (ms_trace / 1e3) / 1e9, bd / (ms_diffraction / 1e3) / 1e9
-    return {"bytes_per_node": 112, "bytes_per_triangle": 48, "hbm_peak_gbs": hbm_gbs, "l2_probe_gbs": l2,
+    return {"bytes_per_node": 112, "bytes_per_triangle": 48, "l2_probe_gbs": l2,
             "frac_of_l2_probe": {"bounces": ft / l2, "diffraction": fd / l2},
             "bounces": {"kernels": "k_closest + k_shade + k_visible (records), all bounces",
                         "queries": int(q_t), "nodes": int(vs[0] + vs[2]), "triangles": int(vs[1] + vs[3]),
                         "nodes_per_query": (vs[0] + vs[2]) / max(q_t, 1), "ms": ms_trace,
-                        "fetch_gbs": ft, "frac_of_hbm": ft / hbm_gbs},
+                        "fetch_gbs": ft},
             "diffraction": {"kernels": "k_diffraction + k_visible (line of sight to the emitter)",
                             "queries": int(q_d), "nodes": int(vd[0] + vd[2]), "triangles": int(vd[1] + vd[3]),
                             "nodes_per_query": (vd[0] + vd[2]) / max(q_d, 1), "ms": ms_diffraction,
-                            "fetch_gbs": fd, "frac_of_hbm": fd / hbm_gbs}}
+                            "fetch_gbs": fd}}
 
 
 def measure_signal(st, torch, ctx, S, wl, reps: int = 5):
