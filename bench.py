@@ -410,20 +410,17 @@ def measure_emitters(st, torch, ctx, sc, wl, n_emitters: int = 4, reps: int = 3)
 
 
 def measure_instances(st, torch, n_inst: int = 8000, n_rays: int = 1_000_000, reps: int = 3):
-    """Instanced forest (shared plant meshes under affine maps, expanded on the device): host time of
-    st_scene_load_instances (checks, upload of prototypes and instance table, expansion), device times of
-    the precompute, of moving every plant (new maps, expansion and refit; keeping the curvature, as the
-    moves are rotations and translations, and recomputing it) and of one simulate; bytes uploaded
-    against those of the same scene loaded flat."""
+    """Instanced forest (shared plant meshes under affine maps, expanded on the device), in both scene
+    structures (one BVH over the expanded triangles; per-prototype BVHs under a BVH over the instances):
+    host time of st_scene_load_instances (checks, upload of prototypes and instance table, expansion),
+    device times of the precompute, of moving every plant (new maps, expansion and refit or rebuild of the
+    top level; keeping the curvature, as the moves are rotations and translations, and recomputing it) and
+    of one simulate, the device memory the built scene holds, and the bytes uploaded against those of the
+    same scene loaded flat."""
     dev = torch.cuda.current_device()
     fo = synth.instanced_forest(seed=606, n_inst=n_inst, n_rays=n_rays, bounces=3, n_mics=8, n_bins=128)
     b = fo.base
     ctx = st.Context(dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sc = st.Scene.from_instances(ctx, fo.protos, fo.inst_proto, fo.inst_xform)
-    load_s = time.perf_counter() - t0
-    sc.set_materials(b.band_hz, b.k_band, b.beta_band, b.diff_band)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
@@ -438,7 +435,6 @@ def measure_instances(st, torch, n_inst: int = 8000, n_rays: int = 1_000_000, re
         return float(np.median(ms))
 
     curv = st.curv_params(sample_budget=1_000_000)
-    precompute_ms = timed(lambda i: sc.precompute(curv))
     rng = np.random.default_rng(8)
     X = fo.inst_xform.astype(np.float64)
     moved = X.copy()
@@ -448,27 +444,47 @@ def measure_instances(st, torch, n_inst: int = 8000, n_rays: int = 1_000_000, re
         moved[i, :, :3] = R @ X[i, :, :3]
         moved[i, :2, 3] += rng.uniform(-0.05, 0.05, 2)
     poses = [torch.as_tensor(m.astype(np.float32), device=f"cuda:{dev}") for m in (moved, X)]
-    move_keep_ms = timed(lambda i: sc.set_instance_transforms(poses[i & 1], keep_curvature=True))
-    move_full_ms = timed(lambda i: sc.set_instance_transforms(poses[i & 1]))
-    sc.set_instance_transforms(poses[1])
     ctx.set_frequencies(b.n_bins, b.f_lo, b.f_hi)
     ctx.set_emitter(b.emitter, b.emitter_quat, b.dirs)
     ctx.set_receivers(b.mics)
     p = st.sim_params(max_bounces=b.bounces, max_distance=b.max_distance)
     out = torch.empty((3, len(b.mics), b.n_bins), dtype=torch.complex64, device=f"cuda:{dev}")
-    ctx.simulate(sc, p, out=out)
-    stats = []
-    sim_ms = timed(lambda i: stats.append(ctx.simulate(sc, p, out=out, stats=True)[1]))
-    segs = stats[-1].closest_queries + stats[-1].shadow_queries
-    pv = sum(len(q[0]) for q in fo.protos)
-    pt = sum(len(q[1]) for q in fo.protos)
-    up_inst = pv * 12 + pt * 16 + n_inst * 52 + (len(fo.protos) + 1) * 16
-    up_flat = sc.n_verts * 12 + sc.n_tris * 20
-    res = {"workload": f"instanced forest: {n_inst} instances of {len(fo.protos)} meshes, {sc.n_tris} triangles, "
-                       f"{n_rays} rays x {b.bounces} bounces, {len(b.mics)} mics x {b.n_bins} bins, diffraction on",
-           "load_instances_s": load_s, "precompute_ms": precompute_ms, "move_refit_keep_curvature_ms": move_keep_ms,
-           "move_refit_ms": move_full_ms, "simulate_ms": sim_ms, "value": segs / (sim_ms / 1e3) / 1e6, "unit": UNIT,
-           "upload_bytes_instanced": int(up_inst), "upload_bytes_flat": int(up_flat)}
+    res, spectra = {}, []
+    for two_level in (False, True):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        t0 = time.perf_counter()
+        sc = st.Scene.from_instances(ctx, fo.protos, fo.inst_proto, fo.inst_xform)
+        load_s = time.perf_counter() - t0
+        sc.set_materials(b.band_hz, b.k_band, b.beta_band, b.diff_band)
+        if two_level:
+            sc.set_structure(True)
+        precompute_ms = timed(lambda i: sc.precompute(curv))
+        torch.cuda.synchronize()
+        scene_bytes = free0 - torch.cuda.mem_get_info(dev)[0]
+        move_keep_ms = timed(lambda i: sc.set_instance_transforms(poses[i & 1], keep_curvature=True))
+        move_full_ms = timed(lambda i: sc.set_instance_transforms(poses[i & 1]))
+        sc.set_instance_transforms(poses[1])
+        ctx.simulate(sc, p, out=out)
+        stats = []
+        sim_ms = timed(lambda i: stats.append(ctx.simulate(sc, p, out=out, stats=True)[1]))
+        spectra.append(out.cpu().numpy())
+        segs = stats[-1].closest_queries + stats[-1].shadow_queries
+        r = {"load_instances_s": load_s, "precompute_ms": precompute_ms, "move_refit_keep_curvature_ms": move_keep_ms,
+             "move_refit_ms": move_full_ms, "simulate_ms": sim_ms, "value": segs / (sim_ms / 1e3) / 1e6, "unit": UNIT,
+             "scene_device_bytes": int(scene_bytes)}
+        if two_level:
+            res["two_level"] = r
+        else:
+            pv = sum(len(q[0]) for q in fo.protos)
+            pt = sum(len(q[1]) for q in fo.protos)
+            res.update({"workload": f"instanced forest: {n_inst} instances of {len(fo.protos)} meshes, {sc.n_tris} "
+                                    f"triangles, {n_rays} rays x {b.bounces} bounces, {len(b.mics)} mics x {b.n_bins} "
+                                    f"bins, diffraction on",
+                        **r, "upload_bytes_instanced": int(pv * 12 + pt * 16 + n_inst * 52 + (len(fo.protos) + 1) * 16),
+                        "upload_bytes_flat": int(sc.n_verts * 12 + sc.n_tris * 20)})
+        sc.close()
+    res["two_level"]["spectra_equal_to_flat"] = bool(np.array_equal(spectra[0], spectra[1]))
     ctx.close()
     return res
 

@@ -185,6 +185,21 @@ st_status st_scene_load_instances(st_ctx* ctx, int32_t n_proto, const int64_t* p
  * ST_ERR_MESH when a world vertex is not finite (the scene is then unbuilt until a later call with finite
  * maps, as for st_scene_update_vertices). */
 st_status st_scene_set_instance_transforms(st_scene* scene, const float* inst_xform, int32_t mem, int32_t flags);
+/* Hierarchy of an instanced scene.  ST_STRUCTURE_FLAT (the default): one BVH over the expanded world
+ * triangles.  ST_STRUCTURE_TWO_LEVEL: a 4-wide BVH per prototype over its triangles in object space, built
+ * once, and a top-level BVH over the instances' world boxes, rebuilt by every precompute and instance
+ * move; a ray enters a prototype's BVH after moving into the instance's object space, but triangles are
+ * tested in world space with their vertices mapped as in the expansion, so every result (path records,
+ * filters, spectra) is bit-identical to the flat structure's.  No hierarchy over the world triangles is
+ * kept (less memory, faster precompute and moves); the expanded triangles, normals, curvature and CDFs
+ * stay.  Takes effect at once on a precomputed scene (rebuilt with its last precompute's parameters).
+ * ST_ERR_ARG for another value; ST_ERR_STATE for two levels on a scene not loaded by
+ * st_scene_load_instances; ST_ERR_MESH when an instance map is singular.  A two-level scene is traced by
+ * st_simulate and its variants; st_simulate_batch rejects it (ST_ERR_ARG) and st_scene_update_vertices
+ * returns ST_ERR_STATE (it moves by st_scene_set_instance_transforms). */
+#define ST_STRUCTURE_FLAT 0
+#define ST_STRUCTURE_TWO_LEVEL 1
+st_status st_scene_set_structure(st_scene* scene, int32_t structure);
 /* The scene's triangles as loaded or expanded: counts (either may be NULL), then verts [n_verts][3],
  * tris [n_tris][3], tri_material [n_tris], tri_object [n_tris] (any may be NULL).  Synchronises. */
 st_status st_scene_get_geometry(st_scene* scene, int64_t* n_verts, int64_t* n_tris, float* verts, int32_t* tris,

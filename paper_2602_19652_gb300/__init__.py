@@ -382,6 +382,12 @@ class Scene:
         self.ctx._check(self.ctx.L.st_scene_set_instance_transforms(
             self.h, ptr_, mem, _lib.ST_REFIT_KEEP_CURVATURE if keep_curvature else 0))
 
+    def set_structure(self, two_level: bool):
+        """Hierarchy of an instanced scene: one BVH over the expanded triangles (two_level=False, the default)
+        or per-prototype BVHs in object space under a BVH over the instances (see the C header)."""
+        self.ctx._check(self.ctx.L.st_scene_set_structure(
+            self.h, _lib.ST_STRUCTURE_TWO_LEVEL if two_level else _lib.ST_STRUCTURE_FLAT))
+
     def geometry(self):
         """(verts [V][3], tris [T][3], tri_mat [T], tri_obj [T]) of the scene as loaded or expanded."""
         v = np.empty((self.n_verts, 3), np.float32)

@@ -19,6 +19,7 @@ ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_OOM, ST_ERR_MESH, ST_ERR_TIMEOUT, ST_ERR_STATE, 
 ST_MEM_HOST, ST_MEM_DEVICE = 0, 1
 ST_IR_PER_COMPONENT = 1
 ST_REFIT_KEEP_CURVATURE = 1
+ST_STRUCTURE_FLAT, ST_STRUCTURE_TWO_LEVEL = 0, 1
 ST_RAYS_FIBONACCI, ST_RAYS_ZONAL = 0, 1
 ST_COMP_SPECULAR, ST_COMP_DIFFRACTION, ST_COMP_DIRECT = 1, 2, 4
 ST_LOS_REFERENCE, ST_LOS_PER_MIC = 0, 1
@@ -85,6 +86,7 @@ SIGNATURES = {
     "st_scene_update_vertices": (I32, [P, P, I32, I32]),
     "st_scene_load_instances": (I32, [P, I32, P, P, P, P, P, I32, P, P, P]),
     "st_scene_set_instance_transforms": (I32, [P, P, I32, I32]),
+    "st_scene_set_structure": (I32, [P, I32]),
     "st_scene_get_geometry": (I32, [P, P, P, P, P, P, P, I32]),
     "st_ray_directions": (I32, [P, I32, I64, P]),
     "st_impulse_response": (I32, [P, P, I32, I32, I32, F64, F64, F64, I32, P, P, I32, I32, P]),

@@ -175,7 +175,8 @@ static void scene_free(st_scene* sc) {
     SceneDev& S = sc->S;
     for (DevBuf* b : {&S.verts, &S.tris, &S.tri_mat, &S.tri_obj, &S.nrm, &S.nodes, &S.tri_v, &S.G, &S.C, &S.mesh_tris,
                       &S.mesh_off, &S.cdf, &S.n_samples, &S.sample_off, &S.bvh_child, &S.bvh_range, &S.bvh_par_i,
-                      &S.bvh_par_l, &S.bvh_perm, &S.bvh_wflag, &S.bvh_widx})
+                      &S.bvh_par_l, &S.bvh_perm, &S.bvh_wflag, &S.bvh_widx, &S.blas_nodes, &S.blas_tri, &S.blas_root,
+                      &S.proto_box, &S.inst_rec, &S.tlas_inst})
         st::release(*b);
     st::InstanceDev& I = sc->inst;
     for (DevBuf* b : {&I.pverts, &I.ptris, &I.pmat, &I.pvoff, &I.ptoff, &I.iproto, &I.vbase, &I.tbase, &I.xform})
@@ -183,6 +184,25 @@ static void scene_free(st_scene* sc) {
     delete sc;
 }
 
+
+// Scene fields of the traversal arguments: the world-triangle BVH of a flat scene, or the top level and the
+// prototypes' BVHs of a two-level one (whose iteration bound also counts instance steps and every instance's
+// own nodes and triangles).
+template <class A>
+static void scene_trav_args(A& a, const SceneDev& S) {
+    a.nodes = ptr<float4>(S.nodes);
+    a.tri_v = ptr<float4>(S.tri_v);
+    a.root = S.root;
+    a.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+    if (S.two_level) {
+        const int64_t n_inst = S.inst ? S.inst->n_inst : 0;
+        a.bnodes = ptr<float4>(S.blas_nodes);
+        a.btri = ptr<float4>(S.blas_tri);
+        a.inst = ptr<float4>(S.inst_rec);
+        a.tinst = ptr<int32_t>(S.tlas_inst);
+        a.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 3 * n_inst + 8, (int64_t)1 << 30);
+    }
+}
 
 namespace {
 
@@ -441,6 +461,8 @@ st_status st_scene_update_vertices(st_scene* sc, const float* verts, int32_t mem
     if (!verts || (mem != ST_MEM_HOST && mem != ST_MEM_DEVICE))
         return fail(c, ST_ERR_ARG, "scene_update_vertices: null pointer or bad memory kind");
     if (!sc->precomputed) return fail(c, ST_ERR_STATE, "scene_update_vertices: precompute first");
+    if (sc->S.two_level)
+        return fail(c, ST_ERR_STATE, "scene_update_vertices: a two-level scene moves by st_scene_set_instance_transforms");
     enter(c);
     CKC(c, cudaMemcpyAsync(sc->S.verts.p, verts, (size_t)sc->S.n_verts * 12, kind_in(mem), c->stream),
         "scene_update_vertices copy");
@@ -494,6 +516,9 @@ st_status st_scene_load_instances(st_ctx* c, int32_t n_proto, const int64_t* pro
     sc->ctx = c;
     sc->instanced = true;
     st::InstanceDev& I = sc->inst;
+    sc->S.inst = &I;
+    I.pvoff_h.assign(proto_vert_offset, proto_vert_offset + n_proto + 1);
+    I.ptoff_h.assign(proto_tri_offset, proto_tri_offset + n_proto + 1);
     I.n_proto = n_proto;
     I.n_inst = n_inst;
     I.nv = NV;
@@ -553,6 +578,33 @@ st_status st_scene_set_instance_transforms(st_scene* sc, const float* inst_xform
     CKC(c, st::expand_instance_verts(I, ptr<float>(I.xform), ptr<float>(sc->S.verts), c->stream),
         "scene_set_instance_transforms expand");
     return refit_scene(sc, flags, "scene_set_instance_transforms");  // non-finite results: ST_ERR_MESH
+}
+
+st_status st_scene_set_structure(st_scene* sc, int32_t structure) {
+    if (!sc) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (structure != ST_STRUCTURE_FLAT && structure != ST_STRUCTURE_TWO_LEVEL)
+        return fail(c, ST_ERR_ARG, "scene_set_structure: ST_STRUCTURE_FLAT or ST_STRUCTURE_TWO_LEVEL");
+    if (structure == ST_STRUCTURE_TWO_LEVEL && !sc->instanced)
+        return fail(c, ST_ERR_STATE, "scene_set_structure: two levels need a scene loaded by st_scene_load_instances");
+    const bool tl = structure == ST_STRUCTURE_TWO_LEVEL;
+    if (tl == sc->S.two_level) return ST_OK;
+    enter(c);
+    CKC(c, cudaStreamSynchronize(c->stream), "scene_set_structure sync");  // earlier simulates may read the scene
+    sc->S.two_level = tl;
+    sc->S.tl_ready = false;
+    sc->S.bvh_ready = false;
+    if (c->batch) c->batch->valid = false;
+    if (!sc->precomputed) return ST_OK;
+    // rebuild with the parameters of the last precompute
+    bool mesh_err = false;
+    std::string msg;
+    cudaError_t e = scene_build(sc->S, sc->cp, c->stream, &mesh_err, &msg);
+    sc->version = g_scene_version++;
+    if (e != cudaSuccess || mesh_err) sc->S.built = false;
+    if (e != cudaSuccess) return cuda_fail(c, e, "scene_set_structure");
+    if (mesh_err) return fail(c, ST_ERR_MESH, "scene_set_structure: " + msg);
+    return ST_OK;
 }
 
 st_status st_scene_get_geometry(st_scene* sc, int64_t* n_verts, int64_t* n_tris, float* verts, int32_t* tris,
@@ -850,10 +902,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     // ---- Algorithm 1
     if (p.components & ST_COMP_SPECULAR && N > 0) {
         TraceArgs ta{};
-        ta.nodes = ptr<float4>(S.nodes);
-        ta.tri_v = ptr<float4>(S.tri_v);
-        ta.root = S.root;
-        ta.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+        scene_trav_args(ta, S);
         ta.visits = c->count_visits ? qctr + 2 : nullptr;
         ta.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
         ta.restarts = qctr + 6;
@@ -910,10 +959,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     // ---- diffraction (Sec. III-D)
     if (K > 0) {
         DiffArgs da{};
-        da.nodes = ptr<float4>(S.nodes);
-        da.tri_v = ptr<float4>(S.tri_v);
-        da.root = S.root;
-        da.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+        scene_trav_args(da, S);
         da.visits = c->count_visits ? qctr + 2 : nullptr;
         da.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
         da.restarts = qctr + 6;
@@ -1078,10 +1124,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     // ---- direct path (Eq. 11-12)
     if (p.components & ST_COMP_DIRECT) {
         DirectArgs dv{};
-        dv.nodes = ptr<float4>(S.nodes);
-        dv.tri_v = ptr<float4>(S.tri_v);
-        dv.root = S.root;
-        dv.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+        scene_trav_args(dv, S);
         dv.visits = c->count_visits ? qctr + 2 : nullptr;
         dv.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
         dv.restarts = qctr + 6;
@@ -1800,6 +1843,8 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
         const st_job& J = jobs[j];
         if (!J.scene || !J.scene->S.built || !J.scene->has_materials || J.scene->ctx != c)
             return fail(c, ST_ERR_STATE, "simulate_batch: every job needs a precomputed scene of this context");
+        if (J.scene->S.two_level)
+            return fail(c, ST_ERR_ARG, "simulate_batch: two-level scenes are traced by st_simulate");
         if (!J.emitter || !J.emitter_quat || !J.mics || !J.spectra_out || (J.n_rays > 0 && !J.dirs) || J.n_rays < 0 ||
             J.n_mics < 1 || J.n_mics > kMaxMics || J.n_bins < 1 || J.max_bounces < 1 || J.max_bounces > kMaxBounces ||
             !(J.f_lo > 0.0) || !(J.f_hi >= J.f_lo) || (J.n_bins > 1 && !(J.f_hi > J.f_lo)))

@@ -39,6 +39,13 @@ __device__ __forceinline__ f3 normalize(f3 v, float* len) {
 }
 __device__ __forceinline__ float comp(f3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
+// One row of an instance's affine map x -> A x + b: ((A_r0 x + A_r1 y) + A_r2 z) + b_r with row = (A_r0, A_r1,
+// A_r2, b_r), every product and sum rounded on its own.  The instance expansion and the two-level traversal's
+// world-space triangle test both use it, so a triangle reached through either has the same vertices.
+__device__ __forceinline__ float affine_row(float4 row, float x, float y, float z) {
+    return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(row.x, x), __fmul_rn(row.y, y)), __fmul_rn(row.z, z)), row.w);
+}
+
 // q = (w, x, y, z) applied to v: t = 2 (q_v x v); v' = (v + w t) + q_v x t.
 __device__ __forceinline__ f3 rotate(const float q[4], f3 v) {
     f3 qv{q[1], q[2], q[3]};

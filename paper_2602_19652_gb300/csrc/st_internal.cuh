@@ -37,6 +37,8 @@ T* ptr(const DevBuf& b) {
 }
 
 // ------------------------------------------------------------------ scene on the device
+struct InstanceDev;
+
 struct SceneDev {
     int64_t n_verts = 0, n_tris = 0;
     DevBuf verts;      // [V][3] f32
@@ -68,6 +70,17 @@ struct SceneDev {
     int32_t n_mat = 0, n_bands = 0;
     std::vector<float> band_hz, k_band, beta_band, diff_band;
     bool built = false;
+    // Two-level structure of an instanced scene (on request): nodes / root / n_nodes then hold the top-level
+    // BVH over the instances' world boxes and no world-triangle hierarchy is kept.  Each prototype has a
+    // 4-wide BVH over its own triangles in object space, built once (blas_*); inst_rec holds 8 float4 per
+    // instance (map rows, inverse rows with |A^-1|_inf, prototype root and first world triangle, world box)
+    // and tlas_inst the instance ids in top-level leaf order.
+    const InstanceDev* inst = nullptr;  // the instance tables of an instanced scene
+    bool two_level = false;
+    bool tl_ready = false;    // the two-level structure matches the current transforms
+    bool blas_ready = false;  // the prototypes' BVHs are built
+    DevBuf blas_nodes, blas_tri, blas_root, proto_box, inst_rec, tlas_inst;
+    int64_t blas_n_nodes = 0;
 };
 
 struct st_scene_impl;
@@ -124,6 +137,7 @@ struct InstanceDev {
     DevBuf iproto;           // [n_inst] i32
     DevBuf vbase, tbase;     // [n_inst + 1] i64
     DevBuf xform;            // [n_inst][12] f32 row-major [A | b]
+    std::vector<int64_t> pvoff_h, ptoff_h;  // host copies of the prototype offsets
 };
 // world vertices [nv][3] from the transforms xf [n_inst][12] (device)
 cudaError_t expand_instance_verts(const InstanceDev& I, const float* xf, float* out, cudaStream_t s);
@@ -141,6 +155,12 @@ struct TraceArgs {
     int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
     unsigned long long* restarts;  // device counter of stackless restarts (or null)
     int32_t refill;  // lane-refill threshold of the persistent traversal kernels (0 = default)
+    // two-level scenes (null for flat ones): prototypes' object-space BVH nodes and leaf-order triangles,
+    // instance records, instance ids of the top-level leaves (nodes / root are then the top level)
+    const float4* bnodes = nullptr;
+    const float4* btri = nullptr;
+    const float4* inst = nullptr;
+    const int32_t* tinst = nullptr;
     const float* nrm;
     // rays
     float s[3];
@@ -195,6 +215,12 @@ struct DiffArgs {
     int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
     unsigned long long* restarts;  // device counter of stackless restarts (or null)
     int32_t refill;  // lane-refill threshold of the persistent traversal kernels (0 = default)
+    // two-level scenes (null for flat ones): prototypes' object-space BVH nodes and leaf-order triangles,
+    // instance records, instance ids of the top-level leaves (nodes / root are then the top level)
+    const float4* bnodes = nullptr;
+    const float4* btri = nullptr;
+    const float4* inst = nullptr;
+    const int32_t* tinst = nullptr;
     const float* nrm;
     const float* verts;
     const int32_t* tris;
@@ -233,6 +259,12 @@ struct DirectArgs {
     int32_t stack_limit;  // traversal stack entries per query (1..kStack; a query that needs more restarts stackless)
     unsigned long long* restarts;  // device counter of stackless restarts (or null)
     int32_t refill;  // lane-refill threshold of the persistent traversal kernels (0 = default)
+    // two-level scenes (null for flat ones): prototypes' object-space BVH nodes and leaf-order triangles,
+    // instance records, instance ids of the top-level leaves (nodes / root are then the top level)
+    const float4* bnodes = nullptr;
+    const float4* btri = nullptr;
+    const float4* inst = nullptr;
+    const int32_t* tinst = nullptr;
     float s[3];
     const float* mics;
     int32_t M;

@@ -456,6 +456,26 @@ __global__ void k_morton(const float* V, const int32_t* T, int64_t nt, const uin
     }
 }
 
+// Morton keys of n points P [n][3] in the bounds bnd (the top level's instance box centres)
+__global__ void k_morton_pts(const float* P, int64_t n, const uint32_t* bnd, uint64_t* keys, uint32_t* vals) {
+    float lo[3], ext[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = unord(bnd[k]);
+        ext[k] = unord(bnd[3 + k]) - lo[k];
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        uint64_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            float u = ext[k] > 0.0f ? (P[3 * t + k] - lo[k]) / ext[k] : 0.5f;
+            u = fminf(fmaxf(u, 0.0f), 1.0f);
+            q[k] = (uint32_t)(u * 2097151.0f);
+        }
+        keys[t] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+        vals[t] = (uint32_t)t;
+    }
+}
+
 __device__ __forceinline__ int delta(const uint64_t* k, int n, int i, int j) {
     if (j < 0 || j >= n) return -1;
     uint64_t a = k[i], b = k[j];
@@ -498,14 +518,14 @@ struct Box {
     float lo[3], hi[3];
 };
 
-// Bottom-up boxes: each leaf writes its box into its parent's slot; the second child to arrive at
-// a node unites both slots and climbs.  box_tmp: [n-1][2] boxes.
-__global__ void k_boxes(const float* V, const int32_t* T, int n, const uint32_t* sorted_tri, const int2* child,
-                        const int32_t* parent_int, const int32_t* parent_leaf, float pad, Box* box_tmp,
-                        uint32_t* visits, uint32_t* err) {
-    int stride = gridDim.x * blockDim.x;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        int64_t t = sorted_tri[p];
+// leaf boxes: a triangle's vertex bounds grown by pad; an instance's world box (from its record)
+struct TriLeafBox {
+    const float* V;
+    const int32_t* T;
+    const uint32_t* sorted;
+    float pad;
+    __device__ __forceinline__ Box operator()(int p) const {
+        const int64_t t = sorted[p];
         Box b;
         for (int k = 0; k < 3; ++k) {
             float a = V[3 * (int64_t)T[3 * t] + k], bb = V[3 * (int64_t)T[3 * t + 1] + k],
@@ -513,6 +533,27 @@ __global__ void k_boxes(const float* V, const int32_t* T, int n, const uint32_t*
             b.lo[k] = fminf(fminf(a, bb), c) - pad;
             b.hi[k] = fmaxf(fmaxf(a, bb), c) + pad;
         }
+        return b;
+    }
+};
+struct InstLeafBox {
+    const float4* rec;
+    const int32_t* sorted;
+    __device__ __forceinline__ Box operator()(int p) const {
+        const int64_t i = sorted[p];
+        const float4 lo = rec[8 * i + 6], hi = rec[8 * i + 7];
+        return Box{{lo.x, lo.y, lo.z}, {hi.x, hi.y, hi.z}};
+    }
+};
+
+// Bottom-up boxes: each leaf writes its box into its parent's slot; the second child to arrive at
+// a node unites both slots and climbs.  box_tmp: [n-1][2] boxes.
+template <class LeafBox>
+__global__ void k_boxes(const LeafBox leaf, int n, const int2* child, const int32_t* parent_int,
+                        const int32_t* parent_leaf, Box* box_tmp, uint32_t* visits, uint32_t* err) {
+    int stride = gridDim.x * blockDim.x;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const Box b = leaf(p);
         int node = parent_leaf[p];
         int slot = (child[node].x == ~p) ? 0 : 1;
         box_tmp[2 * node + slot] = b;
@@ -553,11 +594,11 @@ __host__ __device__ __forceinline__ int32_t leaf_ref(int first, int count) { ret
 
 // child reference of binary node i's side c: a leaf code for single triangles and for subtrees of at
 // most kLeafMax triangles (a contiguous range of the leaf order), else the internal node index
-__device__ __forceinline__ int32_t child_ref(int32_t cc, const int2* range) {
-    if (cc < 0) return leaf_ref(~cc, 1);
+__device__ __forceinline__ int32_t child_ref(int32_t cc, const int2* range, int32_t leaf_off) {
+    if (cc < 0) return leaf_ref(~cc + leaf_off, 1);
     const int2 r = range[cc];
     const int cnt = r.y - r.x + 1;
-    return cnt <= kLeafMax ? leaf_ref(r.x, cnt) : cc;
+    return cnt <= kLeafMax ? leaf_ref(r.x + leaf_off, cnt) : cc;
 }
 
 // Binary internal nodes that stay internal (range above kLeafMax, or the root) at even depth become
@@ -583,8 +624,10 @@ __global__ void k_wide_flags(int n, const int2* range, const int32_t* parent_int
     }
 }
 
+// nodes: the first node of this hierarchy; stored node references are offset by node_off and leaf codes'
+// first triangles by leaf_off (several hierarchies in one array)
 __global__ void k_pack_wide(int n, const int2* child, const int2* range, const Box* box_tmp, const uint32_t* flag,
-                            const uint32_t* idx, float4* nodes) {
+                            const uint32_t* idx, float4* nodes, int32_t node_off, int32_t leaf_off) {
     int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += stride) {
         if (!flag[i]) continue;
@@ -600,20 +643,20 @@ __global__ void k_pack_wide(int n, const int2* child, const int2* range, const B
         };
         const int2 c = child[i];
         const int32_t cs[2] = {c.x, c.y};
-        const int32_t self = (int32_t)idx[i];
+        const int32_t self = (int32_t)idx[i] + node_off;
         for (int sd = 0; sd < 2; ++sd) {
-            const int32_t r = child_ref(cs[sd], range);
+            const int32_t r = child_ref(cs[sd], range, leaf_off);
             if (r < 0) {
                 add(box_tmp[2 * i + sd], r);
             } else {
                 const int2 g = child[r];
                 const int32_t gs[2] = {g.x, g.y};
                 for (int t = 0; t < 2; ++t) {
-                    const int32_t rg = child_ref(gs[t], range);
+                    const int32_t rg = child_ref(gs[t], range, leaf_off);
                     if (rg >= 0)  // row 7 of a child node: its parent and its slot here (the stackless walk)
                         nodes[8 * (size_t)idx[rg] + 7] = make_float4(__int_as_float(self), __int_as_float(cnt), 0.0f,
                                                                      0.0f);
-                    add(box_tmp[2 * r + t], rg < 0 ? rg : (int32_t)idx[rg]);
+                    add(box_tmp[2 * r + t], rg < 0 ? rg : (int32_t)idx[rg] + node_off);
                 }
             }
         }
@@ -650,10 +693,12 @@ __global__ void k_reorder(const float* V, const int32_t* T, int64_t nt, const ui
 
 }  // namespace
 
+static cudaError_t build_two_level(SceneDev& S, float pad_world, uint32_t* flags, cudaStream_t s);
+
 cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bool* mesh_error, std::string* msg,
                         bool refit, bool keep_curvature) {
     *mesh_error = false;
-    refit = refit && S.bvh_ready;
+    refit = refit && (S.two_level ? S.tl_ready : S.bvh_ready);
     keep_curvature = keep_curvature && refit;
     const int64_t nv = S.n_verts, nt = S.n_tris;
     const float* V = ptr<float>(S.verts);
@@ -823,7 +868,7 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
     note_launch();
     k_bounds<<<grid_for(nv, kB, 152 * 4), kB, 0, s>>>(V, nv, ptr<uint32_t>(bnd));
     CK(cudaGetLastError());
-    if (!refit) {
+    if (!refit && !S.two_level) {
         note_launch();
         k_morton<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(bnd), ptr<uint64_t>(keys), ptr<uint32_t>(vals));
         CK(cudaGetLastError());
@@ -850,60 +895,70 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
         }
         const float pad = (float)(1e-5 * sqrt(diag2) + 1e-7);
         const int n = (int)nt;
-        CK(grow(S.tri_v, (size_t)nt * 3 * sizeof(float4)));
-        note_launch();
-        k_reorder<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(S.bvh_perm), ptr<float4>(S.tri_v));
-        CK(cudaGetLastError());
-        if (n == 1 || n <= kLeafMax) {
-            CK(grow(S.nodes, 8 * sizeof(float4)));
-            S.root = leaf_ref(0, n);
+        if (S.two_level) {
+            // no hierarchy over the world triangles: the prototypes' BVHs and one over the instances
+            for (DevBuf* b : {&S.tri_v, &S.bvh_child, &S.bvh_range, &S.bvh_par_i, &S.bvh_par_l, &S.bvh_perm,
+                              &S.bvh_wflag, &S.bvh_widx})
+                release(*b);
+            S.bvh_ready = false;
+            CK(build_two_level(S, pad, ptr<uint32_t>(flags), s));
         } else {
-            S.root = 0;
-            int2* child_p = ptr<int2>(S.bvh_child);
-            int2* range_p = ptr<int2>(S.bvh_range);
-            if (!refit) {
-                CK(grow(S.bvh_child, (size_t)(n - 1) * sizeof(int2)));
-                CK(grow(S.bvh_range, (size_t)(n - 1) * sizeof(int2)));
-                CK(grow(S.bvh_par_i, (size_t)n * 4));
-                CK(grow(S.bvh_par_l, (size_t)n * 4));
-                child_p = ptr<int2>(S.bvh_child);
-                range_p = ptr<int2>(S.bvh_range);
+            S.tl_ready = false;
+            CK(grow(S.tri_v, (size_t)nt * 3 * sizeof(float4)));
+            note_launch();
+            k_reorder<<<grid_for(nt, kB), kB, 0, s>>>(V, T, nt, ptr<uint32_t>(S.bvh_perm), ptr<float4>(S.tri_v));
+            CK(cudaGetLastError());
+            if (n == 1 || n <= kLeafMax) {
+                CK(grow(S.nodes, 8 * sizeof(float4)));
+                S.root = leaf_ref(0, n);
+            } else {
+                S.root = 0;
+                int2* child_p = ptr<int2>(S.bvh_child);
+                int2* range_p = ptr<int2>(S.bvh_range);
+                if (!refit) {
+                    CK(grow(S.bvh_child, (size_t)(n - 1) * sizeof(int2)));
+                    CK(grow(S.bvh_range, (size_t)(n - 1) * sizeof(int2)));
+                    CK(grow(S.bvh_par_i, (size_t)n * 4));
+                    CK(grow(S.bvh_par_l, (size_t)n * 4));
+                    child_p = ptr<int2>(S.bvh_child);
+                    range_p = ptr<int2>(S.bvh_range);
+                    note_launch();
+                    k_karras<<<grid_for(n - 1, kB), kB, 0, s>>>(ptr<uint64_t>(keys), n, child_p, range_p,
+                                                                ptr<int32_t>(S.bvh_par_i), ptr<int32_t>(S.bvh_par_l));
+                    CK(cudaGetLastError());
+                }
+                CK(grow(boxes, (size_t)(n - 1) * 2 * sizeof(Box)));
+                CK(grow(visits, (size_t)(n - 1) * 4));
+                CK(cudaMemsetAsync(visits.p, 0, (size_t)(n - 1) * 4, s));
                 note_launch();
-                k_karras<<<grid_for(n - 1, kB), kB, 0, s>>>(ptr<uint64_t>(keys), n, child_p, range_p,
-                                                            ptr<int32_t>(S.bvh_par_i), ptr<int32_t>(S.bvh_par_l));
+                k_boxes<<<grid_for(n, kB), kB, 0, s>>>(TriLeafBox{V, T, ptr<uint32_t>(S.bvh_perm), pad}, n, child_p,
+                                                       ptr<int32_t>(S.bvh_par_i), ptr<int32_t>(S.bvh_par_l),
+                                                       ptr<Box>(boxes), ptr<uint32_t>(visits), ptr<uint32_t>(flags));
+                CK(cudaGetLastError());
+                if (!refit) {
+                    // 4-wide BVH: flag the binary nodes that become wide nodes, number them
+                    CK(grow(S.bvh_wflag, (size_t)(n - 1) * 4));
+                    CK(grow(S.bvh_widx, (size_t)(n - 1) * 4));
+                    CK(grow(wscan_scr, scan_scratch_bytes(n - 1)));
+                    CK(grow(wtotal, 4));
+                    note_launch();
+                    k_wide_flags<<<grid_for(n - 1, kB), kB, 0, s>>>(n, range_p, ptr<int32_t>(S.bvh_par_i),
+                                                                    ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(flags));
+                    CK(cudaGetLastError());
+                    CK(exclusive_scan_u32(ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(S.bvh_widx), n - 1,
+                                          ptr<uint32_t>(wtotal), wscan_scr.p, s));
+                    uint32_t n4 = 0;
+                    CK(cudaMemcpyAsync(&n4, wtotal.p, 4, cudaMemcpyDeviceToHost, s));
+                    CK(cudaStreamSynchronize(s));
+                    CK(grow(S.nodes, (size_t)std::max<uint32_t>(n4, 1) * 8 * sizeof(float4)));
+                    S.n_nodes = n4;
+                }
+                note_launch();
+                k_pack_wide<<<grid_for(n - 1, kB), kB, 0, s>>>(n, child_p, range_p, ptr<Box>(boxes),
+                                                               ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(S.bvh_widx),
+                                                               ptr<float4>(S.nodes), 0, 0);
                 CK(cudaGetLastError());
             }
-            CK(grow(boxes, (size_t)(n - 1) * 2 * sizeof(Box)));
-            CK(grow(visits, (size_t)(n - 1) * 4));
-            CK(cudaMemsetAsync(visits.p, 0, (size_t)(n - 1) * 4, s));
-            note_launch();
-            k_boxes<<<grid_for(n, kB), kB, 0, s>>>(V, T, n, ptr<uint32_t>(S.bvh_perm), child_p,
-                                                   ptr<int32_t>(S.bvh_par_i), ptr<int32_t>(S.bvh_par_l), pad,
-                                                   ptr<Box>(boxes), ptr<uint32_t>(visits), ptr<uint32_t>(flags));
-            CK(cudaGetLastError());
-            if (!refit) {
-                // 4-wide BVH: flag the binary nodes that become wide nodes, number them
-                CK(grow(S.bvh_wflag, (size_t)(n - 1) * 4));
-                CK(grow(S.bvh_widx, (size_t)(n - 1) * 4));
-                CK(grow(wscan_scr, scan_scratch_bytes(n - 1)));
-                CK(grow(wtotal, 4));
-                note_launch();
-                k_wide_flags<<<grid_for(n - 1, kB), kB, 0, s>>>(n, range_p, ptr<int32_t>(S.bvh_par_i),
-                                                                ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(flags));
-                CK(cudaGetLastError());
-                CK(exclusive_scan_u32(ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(S.bvh_widx), n - 1,
-                                      ptr<uint32_t>(wtotal), wscan_scr.p, s));
-                uint32_t n4 = 0;
-                CK(cudaMemcpyAsync(&n4, wtotal.p, 4, cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-                CK(grow(S.nodes, (size_t)std::max<uint32_t>(n4, 1) * 8 * sizeof(float4)));
-                S.n_nodes = n4;
-            }
-            note_launch();
-            k_pack_wide<<<grid_for(n - 1, kB), kB, 0, s>>>(n, child_p, range_p, ptr<Box>(boxes),
-                                                           ptr<uint32_t>(S.bvh_wflag), ptr<uint32_t>(S.bvh_widx),
-                                                           ptr<float4>(S.nodes));
-            CK(cudaGetLastError());
         }
     }
     CK(cudaMemcpyAsync(&hflags, flags.p, 4, cudaMemcpyDeviceToHost, s));
@@ -913,8 +968,14 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
         *msg = "LBVH construction produced a malformed hierarchy";
         return cudaSuccess;
     }
+    if (hflags & kFlagBadVertex) {
+        *mesh_error = true;
+        *msg = "an instance map is singular or its inverse is not finite";
+        return cudaSuccess;
+    }
     S.built = true;
-    S.bvh_ready = true;
+    S.bvh_ready = !S.two_level;
+    S.tl_ready = S.two_level;
     return cudaSuccess;
 }
 
@@ -944,7 +1005,8 @@ __global__ void k_inst_verts(const float* __restrict__ pv, const int64_t* __rest
         const float x = pv[3 * src], y = pv[3 * src + 1], z = pv[3 * src + 2];
         const float* a = xf + 12 * (int64_t)i;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) out[3 * v + r] = ((a[4 * r] * x + a[4 * r + 1] * y) + a[4 * r + 2] * z) + a[4 * r + 3];
+        for (int r = 0; r < 3; ++r)
+            out[3 * v + r] = affine_row(make_float4(a[4 * r], a[4 * r + 1], a[4 * r + 2], a[4 * r + 3]), x, y, z);
     }
 }
 
@@ -964,7 +1026,281 @@ __global__ void k_inst_tris(const int32_t* __restrict__ pt, const int32_t* __res
     }
 }
 
+// Instance records of the two-level structure (8 float4 per instance): rows (A_r, b_r); rows of A^-1 computed
+// in float64 and rounded, with |A^-1|_inf rounded up (w of row 0), the prototype's root reference (w of row 1)
+// and the first world triangle (w of row 2); the world box of the prototype's vertex bounds pbox under the
+// map, from float64 interval arithmetic rounded outwards, grown by the float32 rounding bound of a mapped
+// vertex and by pad (w of the box's hi: 1 for a prototype without triangles, which the walk skips).  Also the
+// box centre for the top level's Morton keys.  A singular map (or a non-finite inverse) sets kFlagBadVertex.
+__global__ void k_inst_records(const float* __restrict__ xf, const int32_t* __restrict__ iproto,
+                               const int64_t* __restrict__ tbase, const int64_t* __restrict__ ptoff, int32_t n_inst,
+                               const float* __restrict__ pbox, const int32_t* __restrict__ proot, float pad,
+                               float4* __restrict__ rec, float* __restrict__ cen, uint32_t* flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
+        const float* a = xf + 12 * (int64_t)i;
+        double A[3][3], b[3];
+        for (int r = 0; r < 3; ++r) {
+            for (int k = 0; k < 3; ++k) A[r][k] = a[4 * r + k];
+            b[r] = a[4 * r + 3];
+        }
+        const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1], c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2],
+                     c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+        const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+        double inv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        bool ok = isfinite(det) && fabs(det) > 1e-300;
+        if (ok) {
+            const double id = 1.0 / det;
+            inv[0][0] = c00 * id;
+            inv[1][0] = c01 * id;
+            inv[2][0] = c02 * id;
+            inv[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * id;
+            inv[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * id;
+            inv[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * id;
+            inv[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * id;
+            inv[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id;
+            inv[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id;
+        }
+        float fi[3][3];
+        double ninv = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            double row = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                fi[r][k] = (float)inv[r][k];
+                ok = ok && isfinite(fi[r][k]);
+                row += fabs((double)fi[r][k]);
+            }
+            ninv = fmax(ninv, row);
+        }
+        if (!ok) atomicOr(flags, kFlagBadVertex);
+        const int q = iproto[i];
+        const bool empty = ptoff[q + 1] == ptoff[q];
+        const float* pb = pbox + 6 * q;
+        float lo[3], hi[3];
+        for (int r = 0; r < 3; ++r) {
+            double c = b[r], e = 0.0, mag = fabs(b[r]);
+            for (int k = 0; k < 3; ++k) {
+                const double l = pb[k], h = pb[3 + k];
+                c += A[r][k] * (0.5 * (l + h));
+                e += fabs(A[r][k]) * (0.5 * (h - l));
+                mag += fabs(A[r][k]) * fmax(fabs(l), fabs(h));
+            }
+            const double slack = mag * 4.76837158203125e-07;  // 2^-21: six float32 roundings of the mapped vertex
+            lo[r] = __fsub_rd(__double2float_rd(c - e - slack), pad);
+            hi[r] = __fadd_ru(__double2float_ru(c + e + slack), pad);
+        }
+        float4* o = rec + 8 * (int64_t)i;
+        for (int r = 0; r < 3; ++r) o[r] = make_float4(a[4 * r], a[4 * r + 1], a[4 * r + 2], a[4 * r + 3]);
+        o[3] = make_float4(fi[0][0], fi[0][1], fi[0][2], __double2float_ru(ninv * (1.0 + 1e-6)));
+        o[4] = make_float4(fi[1][0], fi[1][1], fi[1][2], __int_as_float(proot[q]));
+        o[5] = make_float4(fi[2][0], fi[2][1], fi[2][2], __int_as_float((int32_t)tbase[i]));
+        o[6] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        o[7] = make_float4(hi[0], hi[1], hi[2], empty ? 1.0f : 0.0f);
+        for (int r = 0; r < 3; ++r) cen[3 * (int64_t)i + r] = 0.5f * lo[r] + 0.5f * hi[r];
+    }
+}
+
+// top level of at most kLeafMax instances: one root node holding each instance as a leaf of its own
+__global__ void k_tlas_small(const float4* __restrict__ rec, const int32_t* __restrict__ tinst, int32_t n,
+                             float4* __restrict__ nodes) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float lo[3][4], hi[3][4];
+    int32_t ref[4];
+    for (int j = 0; j < 4; ++j) {
+        const bool use = j < n;
+        const float4 l = use ? rec[8 * (int64_t)tinst[j] + 6] : make_float4(0, 0, 0, 0);
+        const float4 h = use ? rec[8 * (int64_t)tinst[j] + 7] : make_float4(0, 0, 0, 0);
+        lo[0][j] = l.x, lo[1][j] = l.y, lo[2][j] = l.z;
+        hi[0][j] = h.x, hi[1][j] = h.y, hi[2][j] = h.z;
+        ref[j] = use ? leaf_ref(j, 1) : kEmptyRef;
+    }
+    for (int k = 0; k < 3; ++k) {
+        nodes[2 * k] = make_float4(lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
+        nodes[2 * k + 1] = make_float4(hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
+    }
+    nodes[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
+                           __int_as_float(ref[3]));
+    nodes[7] = make_float4(__int_as_float(-1), 0.0f, 0.0f, 0.0f);
+}
+
 }  // namespace
+
+// Scratch of one 4-wide build over n primitives (binary topology, boxes, wide-node numbering).
+struct WideScratch {
+    DevBuf child, range, par_i, par_l, boxes, visits, wflag, widx, wscan, wtotal;
+    ~WideScratch() {
+        for (DevBuf* b : {&child, &range, &par_i, &par_l, &boxes, &visits, &wflag, &widx, &wscan, &wtotal}) release(*b);
+    }
+};
+
+// 4-wide BVH over n > kLeafMax primitives whose Morton keys are sorted in keys (leaf p's box from leaf(p)):
+// Karras topology, boxes bottom-up, the wide nodes written from nodes[node_off] on (at most node_cap nodes
+// in all) with references offset by node_off and leaf codes by leaf_off; the node count in *n4.
+template <class LeafBox>
+static cudaError_t wide_from_sorted(int n, const uint64_t* keys, LeafBox leaf, float4* nodes, int64_t node_cap,
+                                    int32_t node_off, int32_t leaf_off, uint32_t* flags, WideScratch& w,
+                                    cudaStream_t s, int64_t* n4_out) {
+    CK(grow(w.child, (size_t)(n - 1) * sizeof(int2)));
+    CK(grow(w.range, (size_t)(n - 1) * sizeof(int2)));
+    CK(grow(w.par_i, (size_t)n * 4));
+    CK(grow(w.par_l, (size_t)n * 4));
+    CK(grow(w.boxes, (size_t)(n - 1) * 2 * sizeof(Box)));
+    CK(grow(w.visits, (size_t)(n - 1) * 4));
+    CK(grow(w.wflag, (size_t)(n - 1) * 4));
+    CK(grow(w.widx, (size_t)(n - 1) * 4));
+    CK(grow(w.wscan, scan_scratch_bytes(n - 1)));
+    CK(grow(w.wtotal, 4));
+    note_launch();
+    k_karras<<<grid_for(n - 1, kB), kB, 0, s>>>(keys, n, ptr<int2>(w.child), ptr<int2>(w.range), ptr<int32_t>(w.par_i),
+                                                ptr<int32_t>(w.par_l));
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(w.visits.p, 0, (size_t)(n - 1) * 4, s));
+    note_launch();
+    k_boxes<<<grid_for(n, kB), kB, 0, s>>>(leaf, n, ptr<int2>(w.child), ptr<int32_t>(w.par_i), ptr<int32_t>(w.par_l),
+                                           ptr<Box>(w.boxes), ptr<uint32_t>(w.visits), flags);
+    CK(cudaGetLastError());
+    note_launch();
+    k_wide_flags<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(w.range), ptr<int32_t>(w.par_i),
+                                                    ptr<uint32_t>(w.wflag), flags);
+    CK(cudaGetLastError());
+    CK(exclusive_scan_u32(ptr<uint32_t>(w.wflag), ptr<uint32_t>(w.widx), n - 1, ptr<uint32_t>(w.wtotal), w.wscan.p, s));
+    uint32_t n4 = 0;
+    CK(cudaMemcpyAsync(&n4, w.wtotal.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if ((int64_t)node_off + n4 > node_cap) return cudaErrorInvalidValue;  // cannot happen: n4 <= n - 1
+    note_launch();
+    k_pack_wide<<<grid_for(n - 1, kB), kB, 0, s>>>(n, ptr<int2>(w.child), ptr<int2>(w.range), ptr<Box>(w.boxes),
+                                                   ptr<uint32_t>(w.wflag), ptr<uint32_t>(w.widx),
+                                                   nodes + 8 * (int64_t)node_off, node_off, leaf_off);
+    CK(cudaGetLastError());
+    *n4_out = n4;
+    return cudaSuccess;
+}
+
+// The two-level structure of an instanced scene: the prototypes' BVHs (object space, once), then the
+// instance records and the top-level BVH over the instances' world boxes (every build and move).
+static cudaError_t build_two_level(SceneDev& S, float pad_world, uint32_t* flags, cudaStream_t s) {
+    const InstanceDev& I = *S.inst;
+    const int32_t P = I.n_proto;
+    int64_t nmax = std::max<int64_t>(I.n_inst, 1);
+    for (int32_t q = 0; q < P; ++q) nmax = std::max(nmax, I.ptoff_h[q + 1] - I.ptoff_h[q]);
+    DevBuf keys, vals, sort_scr, bnd, cen;
+    struct Rel {
+        DevBuf* b[5];
+        ~Rel() {
+            for (DevBuf* x : b) release(*x);
+        }
+    } rel{{&keys, &vals, &sort_scr, &bnd, &cen}};
+    CK(grow(keys, (size_t)nmax * 8));
+    CK(grow(vals, (size_t)nmax * 4));
+    CK(grow(sort_scr, sort_scratch_bytes(nmax)));
+    CK(grow(bnd, 64));
+    WideScratch w;
+    auto bounds = [&](const float* pts, int64_t n, float lo[3], float hi[3]) -> cudaError_t {
+        const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+        CK(cudaMemcpyAsync(bnd.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        note_launch();
+        k_bounds<<<grid_for(n, kB, 152 * 4), kB, 0, s>>>(pts, n, ptr<uint32_t>(bnd));
+        CK(cudaGetLastError());
+        uint32_t hb[6];
+        CK(cudaMemcpyAsync(hb, bnd.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < 6; ++k) {
+            const uint32_t u = hb[k], bits = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+            float f;
+            memcpy(&f, &bits, 4);
+            (k < 3 ? lo[k] : hi[k - 3]) = f;
+        }
+        return cudaSuccess;
+    };
+    if (!S.blas_ready) {
+        int64_t cap = 1;
+        for (int32_t q = 0; q < P; ++q) cap += std::max<int64_t>(I.ptoff_h[q + 1] - I.ptoff_h[q] - 1, 0);
+        const int64_t pt = I.ptoff_h[P];
+        CK(grow(S.blas_nodes, (size_t)cap * 8 * sizeof(float4)));
+        CK(grow(S.blas_tri, (size_t)std::max<int64_t>(pt, 1) * 3 * sizeof(float4)));
+        std::vector<int32_t> root(P, kEmptyRef);
+        std::vector<float> box(6 * (size_t)P, 0.0f);
+        int64_t node_off = 0;
+        for (int32_t q = 0; q < P; ++q) {
+            const int64_t nvq = I.pvoff_h[q + 1] - I.pvoff_h[q], ntq = I.ptoff_h[q + 1] - I.ptoff_h[q];
+            if (ntq == 0 || nvq == 0) continue;
+            const float* Vq = ptr<float>(I.pverts) + 3 * I.pvoff_h[q];
+            const int32_t* Tq = ptr<int32_t>(I.ptris) + 3 * I.ptoff_h[q];
+            float lo[3], hi[3];
+            CK(bounds(Vq, nvq, lo, hi));
+            double diag2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                box[6 * q + k] = lo[k];
+                box[6 * q + 3 + k] = hi[k];
+                diag2 += ((double)hi[k] - lo[k]) * ((double)hi[k] - lo[k]);
+            }
+            const float pad_q = (float)(1e-5 * sqrt(diag2) + 1e-7);
+            note_launch();
+            k_morton<<<grid_for(ntq, kB), kB, 0, s>>>(Vq, Tq, ntq, ptr<uint32_t>(bnd), ptr<uint64_t>(keys),
+                                                      ptr<uint32_t>(vals));
+            CK(cudaGetLastError());
+            CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), ntq, 63, sort_scr.p, s));
+            note_launch();
+            k_reorder<<<grid_for(ntq, kB), kB, 0, s>>>(Vq, Tq, ntq, ptr<uint32_t>(vals),
+                                                       ptr<float4>(S.blas_tri) + 3 * I.ptoff_h[q]);
+            CK(cudaGetLastError());
+            if (ntq <= kLeafMax) {
+                root[q] = leaf_ref((int)I.ptoff_h[q], (int)ntq);
+            } else {
+                int64_t n4 = 0;
+                CK(wide_from_sorted((int)ntq, ptr<uint64_t>(keys), TriLeafBox{Vq, Tq, ptr<uint32_t>(vals), pad_q},
+                                    ptr<float4>(S.blas_nodes), cap, (int32_t)node_off, (int32_t)I.ptoff_h[q], flags, w,
+                                    s, &n4));
+                root[q] = (int32_t)node_off;
+                node_off += n4;
+            }
+        }
+        S.blas_n_nodes = node_off;
+        CK(grow(S.blas_root, (size_t)P * 4));
+        CK(grow(S.proto_box, (size_t)P * 24));
+        CK(cudaMemcpyAsync(S.blas_root.p, root.data(), (size_t)P * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(S.proto_box.p, box.data(), (size_t)P * 24, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // the host tables above go out of scope
+        S.blas_ready = true;
+    }
+    // instance records and the top level
+    const int32_t n = I.n_inst;
+    CK(grow(S.inst_rec, (size_t)n * 8 * sizeof(float4)));
+    CK(grow(S.tlas_inst, (size_t)n * 4));
+    CK(grow(cen, (size_t)n * 12));
+    note_launch();
+    k_inst_records<<<grid_for(n, kB), kB, 0, s>>>(ptr<float>(I.xform), ptr<int32_t>(I.iproto), ptr<int64_t>(I.tbase),
+                                                  ptr<int64_t>(I.ptoff), n, ptr<float>(S.proto_box),
+                                                  ptr<int32_t>(S.blas_root), pad_world, ptr<float4>(S.inst_rec),
+                                                  ptr<float>(cen), flags);
+    CK(cudaGetLastError());
+    float lo[3], hi[3];
+    CK(bounds(ptr<float>(cen), n, lo, hi));
+    note_launch();
+    k_morton_pts<<<grid_for(n, kB), kB, 0, s>>>(ptr<float>(cen), n, ptr<uint32_t>(bnd), ptr<uint64_t>(keys),
+                                                ptr<uint32_t>(vals));
+    CK(cudaGetLastError());
+    CK(radix_sort_u64(ptr<uint64_t>(keys), ptr<uint32_t>(vals), n, 63, sort_scr.p, s));
+    CK(cudaMemcpyAsync(S.tlas_inst.p, vals.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    if (n <= kLeafMax) {
+        if (S.nodes.cap > ((size_t)1 << 20)) release(S.nodes);
+        CK(grow(S.nodes, 8 * sizeof(float4)));
+        note_launch();
+        k_tlas_small<<<1, 32, 0, s>>>(ptr<float4>(S.inst_rec), ptr<int32_t>(S.tlas_inst), n, ptr<float4>(S.nodes));
+        CK(cudaGetLastError());
+        S.n_nodes = 1;
+    } else {
+        const size_t need = (size_t)(n - 1) * 8 * sizeof(float4);
+        if (S.nodes.cap > 4 * need + ((size_t)1 << 20)) release(S.nodes);  // a flat scene's hierarchy before
+        CK(grow(S.nodes, need));
+        int64_t n4 = 0;
+        CK(wide_from_sorted(n, ptr<uint64_t>(keys), InstLeafBox{ptr<float4>(S.inst_rec), ptr<int32_t>(S.tlas_inst)},
+                            ptr<float4>(S.nodes), n - 1, 0, 0, flags, w, s, &n4));
+        S.n_nodes = n4;
+    }
+    S.root = 0;
+    return cudaSuccess;
+}
 
 cudaError_t expand_instance_verts(const InstanceDev& I, const float* xf, float* out, cudaStream_t s) {
     if (I.nv == 0) return cudaSuccess;

@@ -29,13 +29,29 @@ namespace {
 
 using namespace trv;
 
+// the traversal view of a scene's arguments (flat, or two-level when `inst` is set)
+template <class A>
+__host__ __device__ __forceinline__ Trav trav_of(const A& a) {
+    Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts, a.refill};
+    T.bnodes = a.bnodes;
+    T.btri = a.btri;
+    T.inst = a.inst;
+    T.tinst = a.tinst;
+    return T;
+}
+
+// traversal kernels: eight 128-thread CTAs per SM (64 registers) on flat scenes, six on two-level ones
+// (the object-space ray and the instance state take more registers)
+#define ST_TRAV_BOUNDS __launch_bounds__(kTravBlock, TL ? 6 : 8)
+
 // Closest hits of one bounce: item idx of the live-ray queue (the first bounce in direction order).
-__global__ void __launch_bounds__(kTravBlock, 8) k_closest(const TraceArgs a, int j, int64_t n_first) {
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
+template <bool TL>
+__global__ void ST_TRAV_BOUNDS k_closest(const TraceArgs a, int j, int64_t n_first) {
+    const Trav T = trav_of(a);
     const int64_t n = (j == 0) ? n_first : (int64_t)*a.n_in;
     const unsigned full = 0xffffffffu;
     int2 stack[kStack];
-    TravState S;
+    typename TravStateOf<TL>::type S;
     int64_t ray = -1;
     bool live = false, exhausted = false;
     while (true) {
@@ -156,7 +172,8 @@ __global__ void k_shade(const TraceArgs a, int j, int64_t n_first) {
 // Visibility of `target` from the points of a queue (record or candidate ids): out[id] = 1 when no
 // triangle other than excl[id] lies on the segment (t_min, |target - p| - eps).
 // The target is tgt_dev[0..2] when given (the receiver reference point, written on the device), else (tx, ty, tz).
-__global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const uint32_t* queue, const uint32_t* count,
+template <bool TL>
+__global__ void ST_TRAV_BOUNDS k_visible(const Trav T, const uint32_t* queue, const uint32_t* count,
                                                            const float* pts, const int32_t* excl,
                                                            const float* tgt_dev, float tx, float ty, float tz,
                                                            float t_min, float eps, uint8_t* out,
@@ -166,7 +183,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const u
     const unsigned full = 0xffffffffu;
     const f3 target = tgt_dev ? f3{tgt_dev[0], tgt_dev[1], tgt_dev[2]} : f3{tx, ty, tz};
     int2 stack[kStack];
-    TravState S;
+    typename TravStateOf<TL>::type S;
     int64_t id = -1;
     bool live = false, exhausted = false;
     while (true) {
@@ -208,12 +225,13 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible(const Trav T, const u
 
 // Per-microphone receiver test: query q of the queue is record q / M and microphone q % M; a visible
 // microphone sets its bit of the record's mask (and the record's flag: some microphone sees it).
-__global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics(const TraceArgs a, unsigned long long* ctr) {
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
+template <bool TL>
+__global__ void ST_TRAV_BOUNDS k_visible_mics(const TraceArgs a, unsigned long long* ctr) {
+    const Trav T = trav_of(a);
     const int64_t n = *a.vis_n;
     const unsigned full = 0xffffffffu;
     int2 stack[kStack];
-    TravState S;
+    typename TravStateOf<TL>::type S;
     int64_t id = -1;
     int m = 0;
     bool live = false, exhausted = false;
@@ -338,14 +356,15 @@ __global__ void __launch_bounds__(128, 8) k_diffraction(const DiffArgs a) {
     }
 }
 
+template <bool TL>
 __global__ void k_direct(const DirectArgs a) {
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
+    const Trav T = trav_of(a);
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= a.M) return;
     const f3 s{a.s[0], a.s[1], a.s[2]};
     const f3 mic{a.mics[3 * m], a.mics[3 * m + 1], a.mics[3 * m + 2]};
     warp_count(a.queries + 1);
-    a.vis[m] = visible(T, s, mic, -1, a.t_min, a.los_eps, a.flags) ? 1 : 0;
+    a.vis[m] = visible<TL>(T, s, mic, -1, a.t_min, a.los_eps, a.flags) ? 1 : 0;
 }
 
 // Receiver reference point: float64 sum of the microphones in order, divided by M, rounded.
@@ -452,15 +471,16 @@ cudaError_t direction_order(const float* dirs, int64_t n, uint64_t* keys, uint32
     return radix_sort_u64(keys, perm, n, 32, scratch, s);
 }
 
-// persistent traversal grid: eight 128-thread CTAs per SM (64 registers)
-static unsigned trav_grid(int64_t n) {
-    const int64_t full = 152 * 8;
+// persistent traversal grid: one CTA per resident slot (eight per SM on flat scenes, six on two-level ones)
+static unsigned trav_grid(int64_t n, bool tl) {
+    const int64_t full = 152 * (tl ? 6 : 8);
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (n + kTravBlock - 1) / kTravBlock));
 }
 
 cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
     const unsigned grid = grid_for(a.N, block, 152 * 16);
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
+    const Trav T = trav_of(a);
+    const bool tl = a.inst != nullptr;
     for (int j = 0; j < a.B; ++j) {
         if (j > 0) {
             uint32_t* t = a.q_in;
@@ -475,7 +495,10 @@ cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
         if (e == cudaSuccess) e = cudaMemsetAsync(a.ctr, 0, 2 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
         note_launch();
-        k_closest<<<trav_grid(a.N), kTravBlock, 0, s>>>(a, j, a.N);
+        if (tl)
+            k_closest<true><<<trav_grid(a.N, true), kTravBlock, 0, s>>>(a, j, a.N);
+        else
+            k_closest<false><<<trav_grid(a.N, false), kTravBlock, 0, s>>>(a, j, a.N);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         note_launch();
         k_shade<<<grid, block, 0, s>>>(a, j, a.N);
@@ -488,12 +511,14 @@ cudaError_t trace_rays(TraceArgs& a, cudaStream_t s, int block) {
                 return e;
         }
         note_launch();
-        if (a.rec_mask)
-            k_visible_mics<<<trav_grid(a.N * a.M), kTravBlock, 0, s>>>(a, a.ctr + 1);
+        if (a.rec_mask && tl)
+            k_visible_mics<true><<<trav_grid(a.N * a.M, true), kTravBlock, 0, s>>>(a, a.ctr + 1);
+        else if (a.rec_mask)
+            k_visible_mics<false><<<trav_grid(a.N * a.M, false), kTravBlock, 0, s>>>(a, a.ctr + 1);
         else
-            k_visible<<<trav_grid(a.N), kTravBlock, 0, s>>>(T, a.vis_q, a.vis_n, a.rec_p, a.rec_tri, a.R, 0.0f, 0.0f,
-                                                            0.0f, a.t_min, a.los_eps, a.rec_los, a.ctr + 1, a.flags,
-                                                            a.queries);
+            (tl ? k_visible<true> : k_visible<false>)<<<trav_grid(a.N, tl), kTravBlock, 0, s>>>(
+                T, a.vis_q, a.vis_n, a.rec_p, a.rec_tri, a.R, 0.0f, 0.0f, 0.0f, a.t_min, a.los_eps, a.rec_los,
+                a.ctr + 1, a.flags, a.queries);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -513,17 +538,19 @@ cudaError_t diffraction_sample(DiffArgs& a, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = radix_sort_u64(a.sort_keys, a.los_q, a.K, 3 * kLosBits + 1, a.sort_scr, s)) != cudaSuccess) return e;
     }
-    const Trav T{a.nodes, a.tri_v, a.root, a.max_iter, a.visits, a.stack_limit, a.restarts};
+    const Trav T = trav_of(a);
+    const bool tl = a.inst != nullptr;
     note_launch();
-    k_visible<<<trav_grid(a.K), kTravBlock, 0, s>>>(T, a.los_q, a.los_n, a.cand_p, a.cand_tri, nullptr, a.s[0], a.s[1],
-                                                    a.s[2], a.t_min, a.los_eps, a.keep, a.ctr, a.flags, a.queries);
+    (tl ? k_visible<true> : k_visible<false>)<<<trav_grid(a.K, tl), kTravBlock, 0, s>>>(
+        T, a.los_q, a.los_n, a.cand_p, a.cand_tri, nullptr, a.s[0], a.s[1], a.s[2], a.t_min, a.los_eps, a.keep, a.ctr,
+        a.flags, a.queries);
     return cudaGetLastError();
 }
 
 cudaError_t direct_visibility(DirectArgs& a, cudaStream_t s) {
     if (a.M <= 0) return cudaSuccess;
     note_launch();
-    k_direct<<<(a.M + 63) / 64, 64, 0, s>>>(a);
+    (a.inst ? k_direct<true> : k_direct<false>)<<<(a.M + 63) / 64, 64, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,16 @@ struct Trav {
     int32_t stack_limit = kStack;   // stack entries a query may use (1..kStack) before it restarts stackless
     unsigned long long* restarts = nullptr;  // optional: queries that restarted from the root
     int32_t refill = 0;  // lanes of a warp waiting for a query before it refills them (0: the kernel's default)
+    // Two-level scenes (instances of shared meshes): `nodes` / `root` are then the top-level BVH over the
+    // instances' world boxes, whose leaf codes index `tinst` (instance ids in leaf order); every prototype has
+    // a 4-wide BVH over its triangles in object space (`bnodes`, `btri`: triangles in leaf order, the
+    // prototype-local index in the first `w`).  `inst` holds 8 float4 per instance: the rows (A_r, b_r) of
+    // its map, the rows of A^-1 (w: |A^-1|_inf, the prototype's root reference, the first world triangle),
+    // and its world box (lo, hi).  Null for flat scenes.
+    const float4* __restrict__ bnodes = nullptr;
+    const float4* __restrict__ btri = nullptr;
+    const float4* __restrict__ inst = nullptr;
+    const int32_t* __restrict__ tinst = nullptr;
 };
 
 __device__ __forceinline__ float safe_inv(float d) {
@@ -206,6 +216,271 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* sta
     return true;
 }
 
+// ---------------------------------------------------------------- two-level scenes
+// A query walks the top-level BVH in world space; at an instance whose world box it enters it moves into
+// the instance's object space (o' = A^-1 (o - b), d' = A^-1 d: the same ray parameter t in both spaces) and
+// walks the prototype's BVH, whose boxes are grown by a bound on the rounding of o' and d' up to the
+// instance box's exit distance, so that a box is never rejected where the world-space test would hit.
+// Triangles are tested in world space with the world ray: their vertices are mapped by `affine_row`, as
+// in the flat expansion, so hits, t and triangle ids (first world triangle of the instance + local index)
+// are those of the same scene loaded flat, whatever the two hierarchies look like.
+struct TravStateTL : TravState {
+    f3 wo, wd, winv;  // the world ray (o and inv hold the object-space ray inside an instance)
+    float pad;        // growth of the current instance's object-space boxes (0 at the top level)
+    int32_t inst;     // current instance (-1: top level)
+    int32_t isp;      // stack depth when the instance was entered (stack walk)
+    int32_t broot;    // the current prototype's root reference
+    int32_t tbase;    // the current instance's first world triangle
+};
+
+__device__ __forceinline__ void trav_init(TravStateTL& S, const Trav& T, f3 o, f3 d, int32_t exclude, float t_min,
+                                          float t_max) {
+    trav_init(static_cast<TravState&>(S), T, o, d, exclude, t_min, t_max);
+    S.wo = o;
+    S.wd = d;
+    S.winv = S.inv;
+    S.pad = 0.0f;
+    S.inst = -1;
+    S.isp = 0;
+    S.broot = 0;
+    S.tbase = 0;
+}
+
+// slab test of a box grown by g on every side; entry and exit distances
+__device__ __forceinline__ bool slab_g(float lx, float ly, float lz, float hx, float hy, float hz, f3 o, f3 inv,
+                                       float g, float tmax, float* tn_out, float* tf_out) {
+    const float t0x = ((lx - g) - o.x) * inv.x, t1x = ((hx + g) - o.x) * inv.x;
+    const float t0y = ((ly - g) - o.y) * inv.y, t1y = ((hy + g) - o.y) * inv.y;
+    const float t0z = ((lz - g) - o.z) * inv.z, t1z = ((hz + g) - o.z) * inv.z;
+    const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+    tf = tf * 1.0000004f;
+    *tn_out = tn;
+    *tf_out = tf;
+    return tn <= tf;
+}
+
+// into instance i, whose world box the ray leaves at tf
+__device__ __forceinline__ void tl_enter(const Trav& T, TravStateTL& S, int32_t i, float tf) {
+    const float4* r = T.inst + 8 * (size_t)i;
+    const float4 f0 = __ldg(r), f1 = __ldg(r + 1), f2 = __ldg(r + 2);
+    const float4 g0 = __ldg(r + 3), g1 = __ldg(r + 4), g2 = __ldg(r + 5);
+    const float ux = S.wo.x - f0.w, uy = S.wo.y - f1.w, uz = S.wo.z - f2.w;
+    const f3 d = S.wd;
+    S.o = f3{(g0.x * ux + g0.y * uy) + g0.z * uz, (g1.x * ux + g1.y * uy) + g1.z * uz,
+             (g2.x * ux + g2.y * uy) + g2.z * uz};
+    const f3 dd{(g0.x * d.x + g0.y * d.y) + g0.z * d.z, (g1.x * d.x + g1.y * d.y) + g1.z * d.z,
+                (g2.x * d.x + g2.y * d.y) + g2.z * d.z};
+    S.inv = f3{safe_inv(dd.x), safe_inv(dd.y), safe_inv(dd.z)};
+    // |rounding of o' + t d'| <= 4 u |A^-1|_inf (|o - b|_inf + t |d|_inf) for u = 2^-24 and t <= tf; 2^-20
+    // leaves a factor 4, and also covers the rounding of the slab differences when |o'| exceeds the
+    // prototype's own padding
+    const float um = fmaxf(fmaxf(fabsf(ux), fabsf(uy)), fabsf(uz));
+    S.pad = 9.5367431640625e-07f * g0.w * (um + fmaxf(tf, 0.0f));
+    S.inst = i;
+    S.broot = __float_as_int(g1.w);
+    S.tbase = __float_as_int(g2.w);
+}
+
+__device__ __forceinline__ void tl_exit(TravStateTL& S) {
+    S.o = S.wo;
+    S.inv = S.winv;
+    S.pad = 0.0f;
+    S.inst = -1;
+}
+
+// stackless walk: stack[0] = resume point of the current level, and inside an instance stack[1].x = the
+// top-level leaf's next instance (a leaf code) or 1 when it has none, stack[2] = the top-level resume point
+__device__ __forceinline__ void tl_exit_stackless(TravStateTL& S, int2* stack) {
+    tl_exit(S);
+    stack[0] = stack[2];
+    const int32_t cont = stack[1].x;
+    S.ref = cont < 0 ? cont : stack[0].x;
+}
+
+__device__ __forceinline__ void tl_restart(const Trav& T, TravStateTL& S, int2* stack) {
+    if (T.restarts) atomicAdd(T.restarts, 1ull);
+    if (S.inst >= 0) tl_exit(S);
+    S.sp = -1;
+    stack[0] = make_int2(T.root, 0);
+    S.ref = T.root;  // a node: two-level scenes always have a top-level root node
+    S.guard = T.max_iter > (1 << 27) ? (1 << 30) : 8 * T.max_iter;
+}
+
+// one triangle of a prototype leaf, tested in world space
+template <bool AnyHit>
+__device__ __forceinline__ bool leaf_step_tl(const Trav& T, TravStateTL& S, int32_t after) {
+    const int32_t code = ~S.ref;
+    const int i = code >> 3, rest = code & 7;
+    const float4 v0 = __ldg(&T.btri[3 * i + 0]);
+    const int32_t id = S.tbase + __float_as_int(v0.w);
+    if (id != S.exclude) {
+        const float4 v1 = __ldg(&T.btri[3 * i + 1]);
+        const float4 v2 = __ldg(&T.btri[3 * i + 2]);
+        const float4* r = T.inst + 8 * (size_t)S.inst;
+        const float4 f0 = __ldg(r), f1 = __ldg(r + 1), f2 = __ldg(r + 2);
+        ++S.n_tris;
+        const f3 w0{affine_row(f0, v0.x, v0.y, v0.z), affine_row(f1, v0.x, v0.y, v0.z), affine_row(f2, v0.x, v0.y, v0.z)};
+        const f3 w1{affine_row(f0, v1.x, v1.y, v1.z), affine_row(f1, v1.x, v1.y, v1.z), affine_row(f2, v1.x, v1.y, v1.z)};
+        const f3 w2{affine_row(f0, v2.x, v2.y, v2.z), affine_row(f1, v2.x, v2.y, v2.z), affine_row(f2, v2.x, v2.y, v2.z)};
+        float th;
+        if (wt_hit(S.wr, w0, w1, w2, &th) && th > S.t_min) {
+            if (AnyHit) {
+                if (th < S.t_max) {
+                    S.tb = th;
+                    S.best = id;
+                    return true;
+                }
+            } else if (th < S.tb || (th == S.tb && id < S.best)) {
+                S.tb = th;
+                S.best = id;
+            }
+        }
+    }
+    S.ref = rest > 0 ? ~(((i + 1) << 3) | (rest - 1)) : after;
+    return false;
+}
+
+// one node (either level), one instance of a top-level leaf or one prototype triangle; true when finished
+template <bool AnyHit>
+__device__ __forceinline__ bool trav_step(const Trav& T, TravStateTL& S, int2* stack, uint32_t* flags) {
+    if (--S.guard < 0) {
+        atomicOr(flags, kFlagBadTree);
+        return true;
+    }
+    const bool in = S.inst >= 0;
+    if (S.ref >= 0) {
+        const float4* nd = (in ? T.bnodes : T.nodes) + 8 * (size_t)S.ref;
+        const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+        const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        ++S.n_nodes;
+        const f3 o = S.o, inv = S.inv;
+        const float tb = S.tb, g = S.pad;
+        float t0, t1, t2, t3, e;
+        const int32_t r0 = __float_as_int(rf.x), r1 = __float_as_int(rf.y), r2 = __float_as_int(rf.z),
+                      r3 = __float_as_int(rf.w);
+        const bool h0 = slab_g(lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, o, inv, g, tb, &t0, &e);
+        const bool h1 = slab_g(lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, o, inv, g, tb, &t1, &e);
+        const bool h2 = r2 != kEmptyRef && slab_g(lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, o, inv, g, tb, &t2, &e);
+        const bool h3 = r3 != kEmptyRef && slab_g(lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, o, inv, g, tb, &t3, &e);
+        if (S.sp < 0) {  // restart walk (see the flat step), one level at a time
+            const int from = stack[0].y;
+            const int c = (from <= 0 && h0) ? 0 : (from <= 1 && h1) ? 1 : (from <= 2 && h2) ? 2 : (from <= 3 && h3) ? 3 : -1;
+            if (c >= 0) {
+                const int32_t ref = c == 0 ? r0 : c == 1 ? r1 : c == 2 ? r2 : r3;
+                stack[0] = ref >= 0 ? make_int2(ref, 0) : make_int2(S.ref, c + 1);
+                S.ref = ref;
+                return false;
+            }
+            if (in && S.ref == S.broot) {  // the prototype's BVH is done: back to the top level
+                tl_exit_stackless(S, stack);
+                return false;
+            }
+            if (!in && S.ref == T.root) return true;
+            const float4 up = __ldg(nd + 7);
+            S.ref = __float_as_int(up.x);
+            stack[0] = make_int2(S.ref, __float_as_int(up.y) + 1);
+            return false;
+        }
+        const float inf = __int_as_float(0x7f800000), big = 3.0e38f;
+        float k0 = h0 ? fminf(t0, big) : inf, k1 = h1 ? fminf(t1, big) : inf;
+        float k2 = h2 ? fminf(t2, big) : inf, k3 = h3 ? fminf(t3, big) : inf;
+        int32_t c0 = r0, c1 = r1, c2 = r2, c3 = r3;
+        auto cx = [](float& ka, int32_t& ca, float& kb, int32_t& cb) {
+            if (kb < ka) {
+                const float tk = ka;
+                ka = kb;
+                kb = tk;
+                const int32_t tc = ca;
+                ca = cb;
+                cb = tc;
+            }
+        };
+        cx(k0, c0, k1, c1);
+        cx(k2, c2, k3, c3);
+        cx(k0, c0, k2, c2);
+        cx(k1, c1, k3, c3);
+        cx(k1, c1, k2, c2);
+        const int nh = (int)h0 + (int)h1 + (int)h2 + (int)h3;
+        if (nh > 0) {
+            if (S.sp + nh - 1 > T.stack_limit) {
+                tl_restart(T, S, stack);
+                return false;
+            }
+            if (nh > 3) stack[S.sp++] = make_int2(c3, __float_as_int(k3));
+            if (nh > 2) stack[S.sp++] = make_int2(c2, __float_as_int(k2));
+            if (nh > 1) stack[S.sp++] = make_int2(c1, __float_as_int(k1));
+            S.ref = c0;
+            return false;
+        }
+    } else if (in) {
+        if (leaf_step_tl<AnyHit>(T, S, 1)) return true;
+        if (S.ref < 0) return false;
+        if (S.sp < 0) {
+            if (S.broot < 0) tl_exit_stackless(S, stack);  // the prototype's BVH is this one leaf
+            else S.ref = stack[0].x;
+            return false;
+        }
+    } else {
+        // one instance of a top-level leaf: into its object space when the ray enters its world box
+        const int32_t code = ~S.ref;
+        const int k = code >> 3, rest = code & 7;
+        const int32_t cont = rest > 0 ? ~(((k + 1) << 3) | (rest - 1)) : 1;
+        const int32_t i = __ldg(T.tinst + k);
+        const float4* r = T.inst + 8 * (size_t)i;
+        const float4 blo = __ldg(r + 6), bhi = __ldg(r + 7);
+        ++S.n_nodes;
+        float tn, tf;
+        // (w of the box's hi is 1 for an instance of a prototype without triangles: never entered)
+        if (bhi.w == 0.0f && slab_g(blo.x, blo.y, blo.z, bhi.x, bhi.y, bhi.z, S.o, S.inv, 0.0f, S.tb, &tn, &tf)) {
+            if (S.sp < 0) {
+                stack[1] = make_int2(cont, 0);
+                stack[2] = stack[0];
+                tl_enter(T, S, i, tf);
+                if (S.broot >= 0) stack[0] = make_int2(S.broot, 0);
+                S.ref = S.broot;
+                return false;
+            }
+            if (cont < 0) {  // the leaf's next instance, resumed when this one is done (key 0: never skipped)
+                if (S.sp + 1 > T.stack_limit) {
+                    tl_restart(T, S, stack);
+                    return false;
+                }
+                stack[S.sp++] = make_int2(cont, 0);
+            }
+            S.isp = S.sp;
+            tl_enter(T, S, i, tf);
+            S.ref = S.broot;
+            return false;
+        }
+        S.ref = cont;
+        if (S.ref < 0) return false;
+        if (S.sp < 0) {
+            S.ref = stack[0].x;
+            return false;
+        }
+    }
+    // pop; an instance is left when its entries are used up
+    while (true) {
+        if (S.inst >= 0 && S.sp == S.isp) tl_exit(S);
+        if (S.sp <= 0) return true;
+        const int2 top = stack[--S.sp];
+        if (__int_as_float(top.y) <= S.tb) {
+            S.ref = top.x;
+            return false;
+        }
+    }
+}
+
+template <bool TL>
+struct TravStateOf {
+    using type = TravState;
+};
+template <>
+struct TravStateOf<true> {
+    using type = TravStateTL;
+};
+
 template <bool AnyHit>
 __device__ __forceinline__ void trav_count(const Trav& T, const TravState& S) {
     if (T.visits) {
@@ -214,10 +489,10 @@ __device__ __forceinline__ void trav_count(const Trav& T, const TravState& S) {
     }
 }
 
-template <bool AnyHit>
+template <bool AnyHit, bool TL = false>
 __device__ __forceinline__ int32_t traverse(const Trav& T, f3 o, f3 d, int32_t exclude, float t_min, float t_max,
                                             float* t_out, uint32_t* flags) {
-    TravState S;
+    typename TravStateOf<TL>::type S;
     int2 stack[kStack];
     trav_init(S, T, o, d, exclude, t_min, t_max);
     while (!trav_step<AnyHit>(T, S, stack, flags)) {
@@ -247,6 +522,7 @@ constexpr int kRefillClosest = 16;
 constexpr int kRefillAny = 28;
 
 // Visibility of `target` from o: direction normalize(target - o), t in (t_min, |target - o| - eps).
+template <bool TL = false>
 __device__ __forceinline__ bool visible(const Trav& T, f3 o, f3 target, int32_t exclude, float t_min, float eps,
                                         uint32_t* flags) {
     float L;
@@ -254,7 +530,7 @@ __device__ __forceinline__ bool visible(const Trav& T, f3 o, f3 target, int32_t 
     const float tmax = L - eps;
     if (!(tmax > t_min)) return true;
     float th;
-    return traverse<true>(T, o, u, exclude, t_min, tmax, &th, flags) < 0;
+    return traverse<true, TL>(T, o, u, exclude, t_min, tmax, &th, flags) < 0;
 }
 
 // adds the number of active lanes to a 64-bit counter with one atomic per warp
