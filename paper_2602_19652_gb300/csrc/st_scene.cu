@@ -1099,6 +1099,40 @@ __global__ void k_inst_records(const float* __restrict__ xf, const int32_t* __re
     }
 }
 
+// Tighter world boxes: the bounds of each instance's expanded world vertices (the very vertices its
+// triangles are tested with) grown by pad, intersected with the box from the map; one warp per instance.
+__global__ void k_inst_world_boxes(const float* __restrict__ V, const int64_t* __restrict__ vbase, int32_t n_inst,
+                                   float pad, float4* __restrict__ rec, float* __restrict__ cen) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_inst; i += warps) {
+        float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+        for (int64_t v = vbase[i] + lane; v < vbase[i + 1]; v += 32)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fminf(lo[k], V[3 * v + k]);
+                hi[k] = fmaxf(hi[k], V[3 * v + k]);
+            }
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            }
+        if (lane == 0 && vbase[i + 1] > vbase[i]) {
+            float4* o = rec + 8 * i;
+            const float4 l0 = o[6], h0 = o[7];
+            const float4 l = make_float4(fmaxf(l0.x, __fsub_rd(lo[0], pad)), fmaxf(l0.y, __fsub_rd(lo[1], pad)),
+                                         fmaxf(l0.z, __fsub_rd(lo[2], pad)), 0.0f);
+            const float4 h = make_float4(fminf(h0.x, __fadd_ru(hi[0], pad)), fminf(h0.y, __fadd_ru(hi[1], pad)),
+                                         fminf(h0.z, __fadd_ru(hi[2], pad)), h0.w);
+            o[6] = l;
+            o[7] = h;
+            cen[3 * i] = 0.5f * l.x + 0.5f * h.x;
+            cen[3 * i + 1] = 0.5f * l.y + 0.5f * h.y;
+            cen[3 * i + 2] = 0.5f * l.z + 0.5f * h.z;
+        }
+    }
+}
+
 // top level of at most kLeafMax instances: one root node holding each instance as a leaf of its own
 __global__ void k_tlas_small(const float4* __restrict__ rec, const int32_t* __restrict__ tinst, int32_t n,
                              float4* __restrict__ nodes) {
@@ -1273,6 +1307,10 @@ static cudaError_t build_two_level(SceneDev& S, float pad_world, uint32_t* flags
                                                   ptr<int64_t>(I.ptoff), n, ptr<float>(S.proto_box),
                                                   ptr<int32_t>(S.blas_root), pad_world, ptr<float4>(S.inst_rec),
                                                   ptr<float>(cen), flags);
+    CK(cudaGetLastError());
+    note_launch();
+    k_inst_world_boxes<<<grid_for((int64_t)n * 32, kB), kB, 0, s>>>(ptr<float>(S.verts), ptr<int64_t>(I.vbase), n,
+                                                                     pad_world, ptr<float4>(S.inst_rec), ptr<float>(cen));
     CK(cudaGetLastError());
     float lo[3], hi[3];
     CK(bounds(ptr<float>(cen), n, lo, hi));
