@@ -1359,14 +1359,18 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
     // same tile shape for the diffraction paths; without an emitter table their per-(material, bin) factor is
     // read from the material table, so tiles hold more paths
     const acc::Geom gd = adjoint_geom(M, F, T.n_mat, aa.etab ? 0 : 1, adj_tp[1], 16);
+    // chunking from the path lists' capacities (the counts stay on the device: no synchronisation), per path
+    // kind: two CTAs per SM over the kind's own tile grid
+    auto chunks_for = [](const acc::Geom& gg, int64_t n_paths) {
+        const int ctas_ = std::max(gg.n_mb * gg.n_bb, 1);
+        const int64_t tiles = std::max<int64_t>(1, (n_paths + gg.PT - 1) / gg.PT);
+        return (int32_t)std::max<int64_t>(1, std::min<int64_t>(std::max(152 * 2 / ctas_, 1), (tiles + 7) / 8));
+    };
+    const int32_t chunks = chunks_for(g, c->last_N * c->last_B);
+    const int32_t chunks_d = chunks_for(gd, c->last_K);
     const int ctas = g.n_mb * g.n_bb;
-    // chunking from the path lists' capacities (the counts stay on the device: no synchronisation)
-    const int64_t n_paths = std::max<int64_t>(c->last_N * c->last_B, c->last_K);
-    const int64_t tiles = std::max<int64_t>(1, (n_paths + g.PT - 1) / g.PT);
-    const int32_t chunks = (int32_t)std::max<int64_t>(
-        1, std::min<int64_t>(152 / std::max(ctas, 1) * 2, (tiles + 7) / 8));
     const int spec_mic_slices = chunks * g.n_bb, spec_emit_slices = chunks * ctas;
-    const int diff_mic_slices = chunks * gd.n_bb, diff_emit_slices = chunks * gd.n_mb * gd.n_bb;
+    const int diff_mic_slices = chunks_d * gd.n_bb, diff_emit_slices = chunks_d * gd.n_mb * gd.n_bb;
     const int mic_slices = spec_mic_slices + diff_mic_slices + 1;     // specular, diffraction, direct
     const int emit_slices = spec_emit_slices + diff_emit_slices + M;  // direct: one slice per microphone
     CKC(c, grow(c->adj_v, (size_t)chunks * g.n_mb * 4 * F * 4), "alloc");
@@ -1466,7 +1470,7 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         AccumArgs x = aa;
         x.kind = 1;
         x.d_count = cnt + 3;
-        x.n_chunks = chunks;
+        x.n_chunks = chunks_d;
         set_paths(x, c->paths_diff);
         AdjointArgs jj = ja;
         jj.G = G + MF;
