@@ -305,6 +305,13 @@ typedef struct st_job {
     uint32_t pose_index;        /* Philox counter word of the diffraction samples */
     float fov_half_rad;         /* diffraction field of view half-angle (>= pi: off) */
     void* spectra_out;          /* device complex64 [3][n_mics][n_bins] */
+    /* Directivity (Sec. III-F), as st_set_emitter and st_set_receivers take it, in device memory; NULL:
+     * omni.  The tables are read at run time, like the poses. */
+    const float* dir_table;     /* [n_theta][n_bins] emitter pattern over the angle from its forward axis */
+    int32_t n_theta;            /* >= 2 with dir_table */
+    const float* mic_quats;     /* [n_mics][4] microphone orientations (NULL: identity) */
+    const float* mic_tables;    /* [n_mics][n_el][n_az][n_bands] receiver transfer on the scene's bands */
+    int32_t n_el, n_az;         /* >= 2 and >= 1 with mic_tables */
 } st_job;
 
 /* Launch shapes picked by st_autotune (0 = default). */

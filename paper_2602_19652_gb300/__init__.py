@@ -279,7 +279,10 @@ class BatchJob:
     job's output, complex64 [3][M][F]."""
 
     def __init__(self, scene: "Scene", emitter, emitter_quat, dirs, mics, n_bins: int, f_lo: float, f_hi: float,
-                 max_bounces: int, pose_index: int = 0, fov_half: float = math.pi, device: int = 0):
+                 max_bounces: int, pose_index: int = 0, fov_half: float = math.pi, device: int = 0,
+                 emitter_table=None, mic_quats=None, mic_tables=None):
+        """emitter_table [n_theta][n_bins], mic_quats [M][4], mic_tables [M][n_el][n_az][n_bands]: directivity
+        as Context.set_emitter / set_receivers take it (None: omni)."""
         dev = f"cuda:{device}"
         self.scene = scene
 
@@ -299,6 +302,17 @@ class BatchJob:
                        n_rays=self.N, mics=vp(self.mics), n_mics=self.M, n_bins=self.F, f_lo=float(f_lo),
                        f_hi=float(f_hi), max_bounces=int(max_bounces), pose_index=int(pose_index),
                        fov_half_rad=float(np.float32(fov_half)), spectra_out=vp(self.out))
+        self.emitter_table = None if emitter_table is None else f32(emitter_table)
+        self.mic_quats = None if mic_quats is None else f32(mic_quats)
+        self.mic_tables = None if mic_tables is None else f32(mic_tables)
+        if self.emitter_table is not None:
+            self.job.dir_table = vp(self.emitter_table)
+            self.job.n_theta = int(self.emitter_table.shape[0])
+        if self.mic_quats is not None:
+            self.job.mic_quats = vp(self.mic_quats)
+        if self.mic_tables is not None:
+            self.job.mic_tables = vp(self.mic_tables)
+            self.job.n_el, self.job.n_az = int(self.mic_tables.shape[1]), int(self.mic_tables.shape[2])
 
     def set_pose(self, emitter=None, emitter_quat=None, mics=None):
         """Copy a new pose into the job's tensors (same shapes), stream-ordered on torch's current stream."""

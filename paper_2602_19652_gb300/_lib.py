@@ -48,7 +48,8 @@ class Stats(C.Structure):
 class Job(C.Structure):
     _fields_ = [("scene", P), ("emitter", P), ("emitter_quat", P), ("dirs", P), ("n_rays", I64), ("mics", P),
                 ("n_mics", I32), ("n_bins", I32), ("f_lo", F64), ("f_hi", F64), ("max_bounces", I32),
-                ("pose_index", U32), ("fov_half_rad", F32), ("spectra_out", P)]
+                ("pose_index", U32), ("fov_half_rad", F32), ("spectra_out", P), ("dir_table", P), ("n_theta", I32),
+                ("mic_quats", P), ("mic_tables", P), ("n_el", I32), ("n_az", I32)]
 
 
 class Tune(C.Structure):

@@ -302,12 +302,19 @@ __global__ void k_reduce(const float2* __restrict__ partial, int32_t n_chunks, i
 }
 
 // ---------------------------------------------------------------- direct path (Eq. 11-12)
+__device__ float2 direct_term(const DirectAccumArgs& a, const float* qhi, const float* qlo, int m, int k);
+
 __global__ void k_direct_accum(const DirectAccumArgs a, const float* qhi, const float* qlo) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)a.M * a.F) return;
     const int m = (int)(idx / a.F), k = (int)(idx % a.F);
-    float2 v = make_float2(0.0f, 0.0f);
-    if (a.vis[m]) {
+    a.out[idx] = a.vis[m] ? direct_term(a, qhi, qlo, m, k) : make_float2(0.0f, 0.0f);
+}
+
+// the direct path's term at microphone m and bin k (visible)
+__device__ float2 direct_term(const DirectAccumArgs& a, const float* qhi, const float* qlo, int m, int k) {
+    float2 v;
+    {
         const float mx = a.mics[3 * m], my = a.mics[3 * m + 1], mz = a.mics[3 * m + 2];
         const ff r = dist_ff(mx, my, mz, a.s[0], a.s[1], a.s[2]);
         const double f = a.F == 1 ? a.f_lo : a.f_lo + (double)k * a.df;
@@ -344,10 +351,10 @@ __global__ void k_direct_accum(const DirectAccumArgs a, const float* qhi, const 
         }
         v = make_float2(A * cs, A * sn);
     }
-    a.out[idx] = v;
+    return v;
 }
 
-// direct path of every job of a batch: one thread per (job, mic, bin); omni emitter and receivers
+// direct path of every job of a batch: one thread per (job, mic, bin), the single-pose term
 __global__ void k_direct_accum_batch(const BatchArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.MF_total; g += stride) {
@@ -356,16 +363,30 @@ __global__ void k_direct_accum_batch(const BatchArgs a) {
         const int m = (int)(local / b.F), k = (int)(local % b.F);
         float2 v = make_float2(0.0f, 0.0f);
         if (a.dvis[b.mic_off + m]) {
-            const float mx = b.mics[3 * m], my = b.mics[3 * m + 1], mz = b.mics[3 * m + 2];
-            const ff r = dist_ff(mx, my, mz, b.s[0], b.s[1], b.s[2]);
-            const double f = b.F == 1 ? b.f_lo : b.f_lo + (double)k * b.df;
-            const float alpha = (float)(a.a0 + a.a1 * (f / 1000.0));
-            const float L = log2f(a.direct_gain) - 2.0f * log2_ff(r) - alpha * r.hi * (3.3219280948873623f / 20.0f);
-            const ff x = ff_mul(r, ff{b.qhi[k], b.qlo[k]});
-            float sn, cs;
-            sincospif(2.0f * ff_frac(x), &sn, &cs);
-            const float A = exp2f(L);
-            v = make_float2(A * cs, A * sn);
+            DirectAccumArgs d{};
+            d.s[0] = b.s[0];
+            d.s[1] = b.s[1];
+            d.s[2] = b.s[2];
+            d.mics = b.mics;
+            d.M = b.M;
+            d.F = b.F;
+            d.f_lo = b.f_lo;
+            d.df = b.df;
+            d.a0 = a.a0;
+            d.a1 = a.a1;
+            d.gain = a.direct_gain;
+            d.etab = b.etab;
+            d.n_theta = b.n_theta;
+            d.fwd[0] = b.fwd[0];
+            d.fwd[1] = b.fwd[1];
+            d.fwd[2] = b.fwd[2];
+            d.mic_tab = b.mic_tab;
+            d.mic_q = b.mic_q;
+            d.n_el = b.n_el;
+            d.n_az = b.n_az;
+            d.n_bands = b.n_bands;
+            d.bw = b.bw;
+            v = direct_term(d, b.qhi, b.qlo, m, k);
         }
         b.out[(size_t)2 * b.M * b.F + local] = v;
     }
@@ -542,7 +563,15 @@ __global__ void k_gather_spec_batch(const BatchArgs a, const uint32_t* idx, cons
         chl[c] = lo;
         chh[c] = hi;
         meta[c] = (uint32_t)(j + 1) | ((uint32_t)matj << 8);
-        dep[c] = -1.0f;
+        if (b.etab) {  // emission angle of the path's primary ray, as the single-pose gather
+            const int64_t rg = ray;
+            const float3 d = rot(b.q, b.dirs[3 * rg], b.dirs[3 * rg + 1], b.dirs[3 * rg + 2]);
+            const float l = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+            const float cth = (b.fwd[0] * d.x + b.fwd[1] * d.y + b.fwd[2] * d.z) / l;
+            dep[c] = acosf(fminf(1.0f, fmaxf(-1.0f, cth))) * b.inv_dtheta;
+        } else {
+            dep[c] = -1.0f;
+        }
         if (mask) mask[c] = a.rec_mask[id];  // per-microphone receiver test
     }
 }
@@ -563,7 +592,13 @@ __global__ void k_gather_diff_batch(const BatchArgs a, const uint32_t* idx, cons
         rhi[c] = r.hi;
         rlo[c] = r.lo;
         meta[c] = ((uint32_t)b.tri_mat[a.cand_tri[i]] & 255u) << 8;
-        dep[c] = -1.0f;
+        if (b.etab) {
+            const float vx = ox - b.s[0], vy = oy - b.s[1], vz = oz - b.s[2];
+            const float cth = (b.fwd[0] * vx + b.fwd[1] * vy + b.fwd[2] * vz) / r.hi;
+            dep[c] = acosf(fminf(1.0f, fmaxf(-1.0f, cth))) * b.inv_dtheta;
+        } else {
+            dep[c] = -1.0f;
+        }
     }
 }
 

@@ -139,7 +139,7 @@ struct BatchState {
     DevBuf narrow_partial;  // chunk partials of the one-pair jobs (accumulated one after the other)
     // persistent accumulation: one task per (job, path kind) -- the specular tasks, then the diffraction ones
     // -- their chunk partials, the work-item counter, item counts and the largest tile's shared memory
-    std::vector<int32_t> narrow_jobs;  // jobs of one microphone pair: the narrow accumulator, launched per job
+    std::vector<int32_t> narrow_jobs;  // jobs accumulated on their own (one microphone pair, or receiver tables)
     DevBuf tasks, part_all, qctr;
     int32_t n_tasks_spec = 0, n_tasks_diff = 0;
     int64_t items_spec = 0, items_diff = 0, n_out = 0;
@@ -1594,6 +1594,11 @@ void batch_release(BatchState& B) {
     B.events.clear();
 }
 
+// Jobs accumulated one after the other by the single-pose path's launch (not through the work queue): one
+// microphone pair (the narrow accumulator is several times faster for them) and receiver directivity tables
+// (the tile's per-microphone band tables).
+static bool solo_accum(const JobDev& d) { return narrow_accum(d.M) || d.mic_tab != nullptr; }
+
 // All stages of one batch on stream s.
 // Accumulation arguments of job j's path kind (0 specular, 1 diffraction) in the batch's path lists.
 AccumArgs batch_accum_args(BatchState& B, const st_job* jobs, int j, int kind, const st_sim_params& p,
@@ -1623,6 +1628,12 @@ AccumArgs batch_accum_args(BatchState& B, const st_job* jobs, int j, int kind, c
     x.tile_tp = tn.mic_pairs_per_cta;
     x.tile_kb = tn.smem_kb;
     x.kind = kind;
+    x.etab = jd.etab;
+    x.n_theta = jd.n_theta;
+    x.mic_tab = jd.mic_tab;
+    x.mic_q = jd.mic_q;
+    x.n_el = jd.n_el;
+    x.n_az = jd.n_az;
     uint32_t* rg = ptr<uint32_t>(B.ranges) + 4 * j;
     PathList& L = kind == 0 ? B.spec : B.diff;
     x.n_paths = kind == 0 ? jd.N * jd.B : jd.K;
@@ -1654,7 +1665,7 @@ cudaError_t batch_tasks(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     B.narrow_jobs.clear();
     for (int j = 0; j < B.n_jobs; ++j) {
         const JobDev& jd = B.jobs[j];
-        if (narrow_accum(jd.M)) {  // the single-pose path's accumulator for this shape (same sums)
+        if (solo_accum(jd)) {  // the single-pose path's accumulator for this shape (same sums)
             B.narrow_jobs.push_back(j);
             continue;
         }
@@ -1853,6 +1864,9 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
             J.n_mics < 1 || J.n_mics > kMaxMics || J.n_bins < 1 || J.max_bounces < 1 || J.max_bounces > kMaxBounces ||
             !(J.f_lo > 0.0) || !(J.f_hi >= J.f_lo) || (J.n_bins > 1 && !(J.f_hi > J.f_lo)))
             return fail(c, ST_ERR_ARG, "simulate_batch: bad job");
+        if ((J.dir_table && J.n_theta < 2) || (J.mic_tables && (J.n_el < 2 || J.n_az < 1 || J.scene->S.n_bands > 64)))
+            return fail(c, ST_ERR_ARG, "simulate_batch: directivity tables need n_theta >= 2, n_el >= 2, n_az >= 1, "
+                                       "<= 64 bands");
     }
     if (per_mic) {  // queue entries (record << 6 | m) and a 32-bit queue length
         int64_t q = 0;
@@ -1873,8 +1887,11 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
     key = fnv(key, &n_jobs, sizeof(n_jobs));
     for (int j = 0; j < n_jobs; ++j) {
         const st_job& J = jobs[j];
-        const void* ptrs[6] = {J.scene, J.emitter, J.emitter_quat, J.dirs, J.mics, J.spectra_out};
+        const void* ptrs[9] = {J.scene, J.emitter, J.emitter_quat, J.dirs, J.mics, J.spectra_out, J.dir_table,
+                               J.mic_quats, J.mic_tables};
         key = fnv(key, ptrs, sizeof(ptrs));
+        const int32_t dv[3] = {J.dir_table ? J.n_theta : 0, J.mic_tables ? J.n_el : 0, J.mic_tables ? J.n_az : 0};
+        key = fnv(key, dv, sizeof(dv));
         key = fnv(key, &J.scene->version, sizeof(uint64_t));
         key = fnv(key, &J.n_rays, sizeof(J.n_rays));
         const int32_t iv[3] = {J.n_mics, J.n_bins, J.max_bounces};
@@ -2022,6 +2039,15 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
         d.perm = J.n_rays > 0 ? ptr<uint32_t>(B.perm) + ray_o[j] : nullptr;
         d.qhi = ptr<float>(B.tables[j].qhi);
         d.qlo = ptr<float>(B.tables[j].qlo);
+        d.bw = ptr<float2>(B.tables[j].bw);
+        d.etab = J.dir_table;
+        d.n_theta = J.dir_table ? J.n_theta : 0;
+        d.inv_dtheta = J.dir_table ? (float)((J.n_theta - 1) / M_PI) : 0.0f;
+        d.mic_tab = J.mic_tables;
+        d.mic_q = J.mic_tables ? J.mic_quats : nullptr;
+        d.n_el = J.mic_tables ? J.n_el : 0;
+        d.n_az = J.mic_tables ? J.n_az : 0;
+        d.n_bands = S.n_bands;
         d.N = J.n_rays;
         d.K = smp_o[j + 1] - smp_o[j];
         d.ray_off = ray_o[j];
@@ -2039,9 +2065,11 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
         // chunks: the jobs share the GPU, so each job's accumulation is split into about an eighth of the
         // chunks that would fill it alone (fewer partial spectra to sum)
         const int nb = kBatchChunkDiv;
-        B.chunks_spec[j] = std::max(1, accum_chunks(d.N * d.B, d.M, d.F, S.n_mat, 0, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
-        B.chunks_diff[j] = std::max(1, accum_chunks(d.K, d.M, d.F, S.n_mat, 0, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
-        if (narrow_accum(d.M))
+        const int dir_nb = J.mic_tables ? S.n_bands : 0;
+        B.chunks_spec[j] =
+            std::max(1, accum_chunks(d.N * d.B, d.M, d.F, S.n_mat, dir_nb, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
+        B.chunks_diff[j] = std::max(1, accum_chunks(d.K, d.M, d.F, S.n_mat, dir_nb, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
+        if (solo_accum(d))
             narrow_part = std::max(narrow_part, (size_t)std::max(B.chunks_spec[j], B.chunks_diff[j]) * d.M * d.F * 8);
     }
     CKC(c, grow(B.narrow_partial, narrow_part), "batch alloc");

@@ -401,6 +401,14 @@ struct JobDev {
     const uint32_t* perm;   // [N] first-bounce processing order
     const float* qhi;
     const float* qlo;
+    const float2* bw;       // [F] band index and weight of each bin
+    // directivity (null: omni): emitter table [n_theta][F] (angle coordinate theta * inv_dtheta), receiver
+    // tables [M][n_el][n_az][n_bands] and orientations [M][4]
+    const float* etab;
+    const float* mic_tab;
+    const float* mic_q;
+    int32_t n_theta, n_el, n_az, n_bands;
+    float inv_dtheta;
     // sizes and offsets into the batch's global arrays
     int64_t N, K, ray_off, rec_off, samp_off, mic_off, mf_off;
     int32_t B, M, F;
