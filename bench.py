@@ -38,7 +38,7 @@ FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by
 # (the diffraction launch at full size, the specular launch on 200k rays scaled by the visible records: the path
 # list is read once), with the hash of the accumulator's sources it was taken on: the bench reports it only while
 # the sources still hash to that value (else null, until the kernel is captured again)
-ACCUM_TRAFFIC = {"sources_sha16": "831e84b5e5042143", "bytes_per_launch": 38.7e6}
+ACCUM_TRAFFIC = {"sources_sha16": "a3c4ee20590f299a", "bytes_per_launch": 38.7e6}
 ACCUM_SOURCES = ("st_accum.cu", "st_accum_dev.cuh", "st_internal.cuh")
 
 

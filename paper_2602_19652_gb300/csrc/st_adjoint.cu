@@ -146,6 +146,9 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         for (int v = 0; v < VR; ++v) V[q][v] = 0.0f;
     // position gradients of the thread's two microphones (and the emitter, diffraction), packed
     u64 dmx = 0ull, dmy = 0ull, dmz = 0ull, dex = 0ull, dey = 0ull, dez = 0ull;
+    // diffraction: the emitter direction is the same for both microphones of a pair, so the emitter gradient
+    // is summed over the pair first (three scalar registers instead of three packed pairs)
+    float esx = 0.0f, esy = 0.0f, esz = 0.0f;
     // d ln T / dr at this subtile's first bin, without the -2/r spreading term: (-a, w); per bin: (-a_step, w_step)
     const float kbs = (float)(kb + s * KT);
     const float ars = -(j.a_0 + j.a_step * kbs), nais = -(j.w_0 + j.w_step * kbs);
@@ -310,9 +313,11 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                         dmz = ffma2(cg, ad[5], dmz);
                     }
                 } else {  // emitter: dr/ds = -unit(o - s)
-                    dex = ffma2(dl, ad[3], dex);
-                    dey = ffma2(dl, ad[4], dey);
-                    dez = ffma2(dl, ad[5], dez);
+                    const float2 d2 = up2(dl);
+                    const float dsum = d2.x + d2.y;
+                    esx = fmaf(dsum, up2(ad[3]).x, esx);
+                    esy = fmaf(dsum, up2(ad[4]).x, esy);
+                    esz = fmaf(dsum, up2(ad[5]).x, esz);
                 }
             }
             // reflection-coefficient sums for the materials of the path's chain
@@ -356,9 +361,9 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             o[0] = x.x; o[1] = y2.x; o[2] = z.x;
             o[3] = x.y; o[4] = y2.y; o[5] = z.y;
             const float2 ex = up2(dex), ey = up2(dey), ez = up2(dez);
-            rede[tid * 3 + 0] = ex.x + ex.y;
-            rede[tid * 3 + 1] = ey.x + ey.y;
-            rede[tid * 3 + 2] = ez.x + ez.y;
+            rede[tid * 3 + 0] = KIND == 1 ? esx : ex.x + ex.y;
+            rede[tid * 3 + 1] = KIND == 1 ? esy : ey.x + ey.y;
+            rede[tid * 3 + 2] = KIND == 1 ? esz : ez.x + ez.y;
         }
         __syncthreads();
         if (tid < g.MP && mic0 + tid < a.M) {  // microphone mic0 + tid: fixed-order sum over the subtiles

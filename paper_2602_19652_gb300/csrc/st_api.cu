@@ -16,6 +16,9 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+#include <stdarg.h>
+
 #include "st_accum_dev.cuh"
 #include "st_internal.cuh"
 
@@ -185,6 +188,33 @@ static void scene_free(st_scene* sc) {
 }
 
 
+// ---- logging (ST_LOG=1: every error, 2: also one line per simulate, backward, precompute and batch) and
+// NVTX ranges around the entry points and the stages of a simulate (seen by profilers that record NVTX)
+static int log_level() {
+    static const int lv = [] {
+        const char* e = getenv("ST_LOG");
+        return e ? atoi(e) : 0;
+    }();
+    return lv;
+}
+
+static void st_log(int level, const char* fmt, ...) {
+    if (log_level() < level) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    fprintf(stderr, "sonotrace: %s\n", buf);
+}
+
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Scene fields of the traversal arguments: the world-triangle BVH of a flat scene, or the top level and the
 // prototypes' BVHs of a two-level one (whose iteration bound also counts instance steps and every instance's
 // own nodes and triangles).
@@ -208,6 +238,7 @@ namespace {
 
 st_status fail(st_ctx* c, st_status code, const std::string& msg) {
     if (c) c->err = msg;
+    st_log(1, "error %d: %s", (int)code, msg.c_str());
     return code;
 }
 
@@ -225,7 +256,8 @@ st_status cuda_fail(st_ctx* c, cudaError_t e, const char* where) {
 cudaMemcpyKind kind_in(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_out(int32_t mem) { return mem == ST_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
-// a batched job's accumulation takes about 1/kBatchChunkDiv of the chunks that would fill the GPU alone
+// a batched job's accumulation takes about 1/kBatchChunkDiv of the chunks that would fill the GPU alone (a job
+// of a million paths or more takes them all: it is accumulated on its own)
 constexpr int kBatchChunkDiv = 8;
 
 // triangle count from which the visibility queries of a simulate are sorted by hit point (the 4-wide
@@ -417,7 +449,7 @@ st_status st_scene_set_materials(st_scene* sc, int32_t n_mat, int32_t n_bands, c
     return ST_OK;
 }
 
-st_status st_scene_precompute(st_scene* sc, const st_curv_params* params) {
+static st_status precompute_impl(st_scene* sc, const st_curv_params* params) {
     if (!sc) return ST_ERR_ARG;
     st_ctx* c = sc->ctx;
     if (!sc->has_materials) return fail(c, ST_ERR_STATE, "scene_precompute: set materials first");
@@ -766,7 +798,8 @@ static st_status ensure_paths(st_ctx* c, PathList& P, int64_t n) {
     return ST_OK;
 }
 
-st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void* spectra_out, st_stats* stats) {
+static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* params, void* spectra_out,
+                               st_stats* stats) {
     if (!c || !sc || !spectra_out) return fail(c, ST_ERR_ARG, "simulate: null argument");
     if (!c->has_emitter || !c->has_rx || !c->has_freq)
         return fail(c, ST_ERR_STATE, "simulate: set emitter, receivers and frequencies first");
@@ -901,6 +934,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
 
     // ---- Algorithm 1
     if (p.components & ST_COMP_SPECULAR && N > 0) {
+        NvtxRange range("st_simulate: trace");
         TraceArgs ta{};
         scene_trav_args(ta, S);
         ta.visits = c->count_visits ? qctr + 2 : nullptr;
@@ -958,6 +992,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
 
     // ---- diffraction (Sec. III-D)
     if (K > 0) {
+        NvtxRange range("st_simulate: diffraction sampling");
         DiffArgs da{};
         scene_trav_args(da, S);
         da.visits = c->count_visits ? qctr + 2 : nullptr;
@@ -1074,6 +1109,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     int n_accum = 0;  // bit 0: specular launch issued, bit 1: diffraction launch issued
     // ---- specular accumulation (Eq. 2-4)
     if (p.components & ST_COMP_SPECULAR && NB > 0) {
+        NvtxRange range("st_simulate: specular accumulation");
         CKC(c, flags_visible_records(ptr<int32_t>(c->rec_tri), ptr<uint8_t>(c->rec_los), NB, ptr<uint32_t>(c->sflags), s),
             "flags");
         CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, cnt + 2, c->scratch.p, s),
@@ -1101,6 +1137,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     }
     // ---- diffraction accumulation (Eq. 7-8)
     if (K > 0) {
+        NvtxRange range("st_simulate: diffraction accumulation");
         CKC(c, flags_from_u8(ptr<uint8_t>(c->keep), K, ptr<uint32_t>(c->sflags), s), "flags");
         CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), K, cnt + 3, c->scratch.p, s),
             "scan");
@@ -1123,6 +1160,7 @@ st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void
     }
     // ---- direct path (Eq. 11-12)
     if (p.components & ST_COMP_DIRECT) {
+        NvtxRange range("st_simulate: direct path");
         DirectArgs dv{};
         scene_trav_args(dv, S);
         dv.visits = c->count_visits ? qctr + 2 : nullptr;
@@ -1535,11 +1573,17 @@ st_status st_impulse_response(st_ctx* c, const void* spectra, int32_t n_comp, in
 
 st_status st_backward(st_ctx* c, st_scene* sc, const void* grad_spectra, float* grad_k, float* grad_mic,
                       float* grad_emitter) {
-    return backward_impl(c, sc, grad_spectra, grad_k, grad_mic, grad_emitter, nullptr);
+    NvtxRange range("st_backward");
+    const st_status r = backward_impl(c, sc, grad_spectra, grad_k, grad_mic, grad_emitter, nullptr);
+    if (r == ST_OK)
+        st_log(2, "backward: %s%s%s", grad_k ? "reflection " : "", grad_mic ? "microphones " : "",
+               grad_emitter ? "emitter" : "");
+    return r;
 }
 
 st_status st_backward_beta(st_ctx* c, st_scene* sc, const void* grad_spectra, float* grad_beta) {
     if (!grad_beta) return fail(c, ST_ERR_ARG, "backward_beta: null output");
+    NvtxRange range("st_backward_beta");
     return backward_impl(c, sc, grad_spectra, nullptr, nullptr, nullptr, grad_beta);
 }
 
@@ -1595,9 +1639,11 @@ void batch_release(BatchState& B) {
 }
 
 // Jobs accumulated one after the other by the single-pose path's launch (not through the work queue): one
-// microphone pair (the narrow accumulator is several times faster for them) and receiver directivity tables
-// (the tile's per-microphone band tables).
-static bool solo_accum(const JobDev& d) { return narrow_accum(d.M) || d.mic_tab != nullptr; }
+// microphone pair (the narrow accumulator is several times faster for them), receiver directivity tables
+// (the tile's per-microphone band tables), and jobs of a million paths or more, which fill the GPU alone
+// with their full chunk count (in the queue they would take a fraction of it).
+static bool big_job(const JobDev& d) { return d.N * (int64_t)d.B >= (1 << 20) || d.K >= (1 << 20); }
+static bool solo_accum(const JobDev& d) { return narrow_accum(d.M) || d.mic_tab != nullptr || big_job(d); }
 
 // All stages of one batch on stream s.
 // Accumulation arguments of job j's path kind (0 specular, 1 diffraction) in the batch's path lists.
@@ -1843,8 +1889,8 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
 
 extern "C" {
 
-st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const st_sim_params* params,
-                            const st_tune* tune) {
+static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jobs, const st_sim_params* params,
+                                     const st_tune* tune) {
     if (!c || n_jobs <= 0 || !jobs) return fail(c, ST_ERR_ARG, "simulate_batch: need jobs");
     st_sim_params p;
     st_sim_params_default(&p);
@@ -2064,7 +2110,7 @@ st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const
         d.out = static_cast<float2*>(J.spectra_out);
         // chunks: the jobs share the GPU, so each job's accumulation is split into about an eighth of the
         // chunks that would fill it alone (fewer partial spectra to sum)
-        const int nb = kBatchChunkDiv;
+        const int nb = big_job(d) ? 1 : kBatchChunkDiv;
         const int dir_nb = J.mic_tables ? S.n_bands : 0;
         B.chunks_spec[j] =
             std::max(1, accum_chunks(d.N * d.B, d.M, d.F, S.n_mat, dir_nb, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
@@ -2184,5 +2230,31 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
     return ST_OK;
 }
 
-}  // extern "C"
+// ---- entry points with NVTX ranges and ST_LOG lines around the implementations above
+st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void* spectra_out, st_stats* stats) {
+    NvtxRange range("st_simulate");
+    const st_status r = simulate_impl(c, sc, params, spectra_out, stats);
+    if (r == ST_OK)
+        st_log(2, "simulate: %lld rays x %d bounces, %lld diffraction samples, %d mics x %d bins",
+               (long long)c->last_N, (int)c->last_B, (long long)c->last_K, (int)c->last_M, (int)c->last_F);
+    return r;
+}
 
+st_status st_scene_precompute(st_scene* sc, const st_curv_params* params) {
+    NvtxRange range("st_scene_precompute");
+    const st_status r = precompute_impl(sc, params);
+    if (r == ST_OK)
+        st_log(2, "precompute: %lld triangles, %lld diffraction samples%s", (long long)sc->S.n_tris,
+               (long long)sc->S.total_samples, sc->S.two_level ? ", two-level" : "");
+    return r;
+}
+
+st_status st_simulate_batch(st_ctx* c, int32_t n_jobs, const st_job* jobs, const st_sim_params* params,
+                            const st_tune* tune) {
+    NvtxRange range("st_simulate_batch");
+    const st_status r = simulate_batch_impl(c, n_jobs, jobs, params, tune);
+    if (r == ST_OK) st_log(2, "simulate_batch: %d jobs", (int)n_jobs);
+    return r;
+}
+
+}  // extern "C"

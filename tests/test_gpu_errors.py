@@ -169,3 +169,38 @@ def test_injected_allocation_failure(st):
         assert np.array_equal(S, fresh.simulate(scf, p).cpu().numpy())
     finally:
         L.st_inject_alloc_failure(-1)
+
+
+def test_log_levels(tmp_path):
+    """ST_LOG=1 writes every error to stderr, ST_LOG=2 also one line per simulate and precompute; unset, the
+    library writes nothing (checked in child processes: the level is read once per process)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "run.py"
+    script.write_text(
+        "import sys\n"
+        f"sys.path[:0] = [{root!r}, {os.path.join(root, 'tests')!r}]\n"
+        "import numpy as np, paper_2602_19652_gb300 as st, synth\n"
+        "ctx = st.Context(0)\n"
+        "wl = synth.shoebox(seed=101, n_rays=500)\n"
+        "try:\n"
+        "    ctx.simulate(st.Scene(ctx, wl.verts, wl.tris, wl.tri_mat, wl.tri_obj))\n"
+        "except st.SonotraceError:\n"
+        "    pass\n"
+        "sc = st.from_workload(ctx, wl)\n"
+        "ctx.simulate(sc)\n")
+    out = {}
+    for level in (None, "1", "2"):
+        env = dict(os.environ)
+        env.pop("ST_LOG", None)
+        if level:
+            env["ST_LOG"] = level
+        r = subprocess.run([sys.executable, str(script)], env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        out[level] = [l for l in r.stderr.splitlines() if l.startswith("sonotrace:")]
+    assert out[None] == []
+    assert any("error" in l and "simulate" in l for l in out["1"]) and not any("simulate: " in l and "rays" in l
+                                                                              for l in out["1"])
+    assert any("precompute:" in l for l in out["2"]) and any("rays x" in l for l in out["2"])
