@@ -350,6 +350,86 @@ def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 
             "max_rel_l2_batched_vs_plain": err, "first_call_s": first_call_s}
 
 
+def measure_batched_directional(st, torch, n_poses: int = 64, rays_per_pose: int = 32768, reps: int = 3):
+    """Batched form against plain per-pose calls on bat poses with directivity (Sec. III-F): a 200k-triangle
+    leaf-disc scene, n_poses head poses near the centre (random headings; the ears at +-1 cm across the
+    head, oriented with it), the piston emitter table and two ear tables, 1024 bins 20-120 kHz, 4 bounces,
+    diffraction on (65,536 samples), field of view pi/2.  Plain calls set the pose's emitter (with its table)
+    and receivers (with theirs) from device memory and simulate; L2 flushed before each timed pass."""
+    dev = torch.cuda.current_device()
+    wl = synth.vegetation(seed=303, target_tris=200_000, n_rays=rays_per_pose, bounces=4, n_bins=1024,
+                          leaves_per_mesh=256)
+    ctx = st.Context(dev)
+    sc = st.Scene(ctx, wl.verts, wl.tris, wl.tri_mat, wl.tri_obj)
+    sc.set_materials(wl.band_hz, wl.k_band, wl.beta_band, wl.diff_band)
+    sc.precompute(st.curv_params(sample_budget=65536))
+    rng = np.random.default_rng(808)
+    d = f"cuda:{dev}"
+    etab = torch.as_tensor(wl.emitter_table, device=d)
+    mtab = torch.as_tensor(wl.mic_tables, device=d)
+    dirs = torch.as_tensor(wl.dirs, device=d)
+    fov = float(np.float32(math.pi / 2))
+    jobs, poses = [], []
+    for i in range(n_poses):
+        q = rng.normal(size=4)
+        q = (q / np.linalg.norm(q)).astype(np.float32)
+        w, x, y, z = (float(v) for v in q)
+        R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        e = rng.uniform(-0.1, 0.1, 3).astype(np.float32)
+        mics = (e + (R @ np.array([[0.0, 0.01, 0.0], [0.0, -0.01, 0.0]]).T).T).astype(np.float32)
+        mq = np.tile(q, (2, 1)).astype(np.float32)
+        jobs.append(st.BatchJob(sc, e, q, dirs, mics, wl.n_bins, wl.f_lo, wl.f_hi, wl.bounces, pose_index=i,
+                                fov_half=fov, device=dev, emitter_table=etab, mic_quats=mq, mic_tables=mtab))
+        poses.append((torch.as_tensor(e, device=d), torch.as_tensor(q, device=d), torch.as_tensor(mics, device=d),
+                      torch.as_tensor(mq, device=d)))
+    p = st.sim_params(max_distance=wl.max_distance)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=d)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ms = []
+        for i in range(reps):
+            flush.fill_(i & 255)
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ms))
+
+    ctx.simulate_batch(jobs, p)
+    ctx.simulate_batch(jobs, p)
+    batched_ms = timed(lambda: ctx.simulate_batch(jobs, p))
+    batched_out = [j.out.clone() for j in jobs]
+    plain_out = [torch.empty_like(j.out) for j in jobs]
+    pp = [st.sim_params(max_distance=wl.max_distance, max_bounces=wl.bounces, pose_index=i) for i in range(n_poses)]
+    ctx.set_frequencies(wl.n_bins, wl.f_lo, wl.f_hi)
+
+    def plain():
+        for i, (e, q, m, mq) in enumerate(poses):
+            ctx.set_emitter(e, q, dirs, etab, fov)
+            ctx.set_receivers(m, mq, mtab)
+            ctx.simulate(sc, pp[i], out=plain_out[i])
+
+    plain()
+    plain_ms = timed(plain)
+    err = 0.0
+    for a, b in zip(batched_out, plain_out):
+        for c in range(3):
+            nb = float(torch.linalg.vector_norm(b[c]))
+            if nb > 0:
+                err = max(err, float(torch.linalg.vector_norm(a[c] - b[c])) / nb)
+    ctx.close()
+    return {"workload": f"{n_poses} bat poses in a {wl.n_tris}-triangle leaf-disc scene, {rays_per_pose} rays x "
+                        f"{wl.bounces} bounces, 2 ears x {wl.n_bins} bins, piston emitter and ear tables, diffraction "
+                        f"65536 samples",
+            "batched_ms": batched_ms, "plain_ms": plain_ms, "speedup": plain_ms / batched_ms,
+            "max_rel_l2_batched_vs_plain": err}
+
+
 def measure_emitters(st, torch, ctx, sc, wl, n_emitters: int = 4, reps: int = 3):
     """Several emitters sending the workload's ray set into its scene towards its array: one batched call
     (Context.simulate_emitters) against one plain st_simulate per emitter (set_emitter + simulate, the
@@ -651,6 +731,9 @@ def run_case(st, torch, case: str, reps: int):
     if case == "instances":
         print(json.dumps(measure_instances(st, torch)))
         return
+    if case == "batched_bat":
+        print(json.dumps(measure_batched_directional(st, torch)))
+        return
     if case == "emitters":
         wl = synth.clutter(seed=202)
         ctx = st.Context(dev)
@@ -744,6 +827,10 @@ def compact_line(d):
         b = d["batched"]
         line["batched_vs_plain"] = {"speedup": _r(b["speedup"], 3), "batched_ms": _r(b["batched_ms"]),
                                     "plain_ms": _r(b["plain_ms"]), "poses": 256}
+    if d.get("batched_directional"):
+        b = d["batched_directional"]
+        line["batched_vs_plain_bat"] = {"speedup": _r(b["speedup"], 3), "batched_ms": _r(b["batched_ms"]),
+                                        "plain_ms": _r(b["plain_ms"]), "poses": 64}
     v = d.get("vegetation")
     if v:
         vr, ve = v["roofline"], v["e2e"]
@@ -775,7 +862,7 @@ def main():
     ap.add_argument("--no-emitters", action="store_true", help="skip the several-emitters timing")
     ap.add_argument("--no-instances", action="store_true", help="skip the instanced-forest timing")
     ap.add_argument("--case", default=None,
-                    choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow", "emitters", "instances"],
+                    choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow", "emitters", "instances", "batched_bat"],
                     help="run a small case of one kernel family a few times and exit (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -873,9 +960,10 @@ def main():
                    measure_adjoint(st, torch, synth.gradient_problem(seed=404)),
                    f"{wl.name} workload": measure_adjoint(st, torch, wl)}
 
-    batched = None
+    batched = batched_dir = None
     if not args.no_batched:
         batched = measure_batched(st, torch)
+        batched_dir = measure_batched_directional(st, torch)
     vegetation = None
     if not args.no_vegetation and args.workload != "vegetation":
         vegetation = measure_workload(st, torch, synth.vegetation(seed=303), roofline=(n_sm, sm_mhz, peak_src),
@@ -910,7 +998,7 @@ def main():
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
                          "ms_accumulate": s0.ms_accumulate},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
-            "traversal": traversal, "signal": signal, "scene_update": scene_update, "batched": batched,
+            "traversal": traversal, "signal": signal, "scene_update": scene_update, "batched": batched, "batched_directional": batched_dir,
             "vegetation": vegetation, "receiver_test_per_mic": per_mic, "emitters": emitters,
             "instances": instances,
             "gpu_launches": int(sum(s.kernel_launches for s in st_list))}

@@ -103,6 +103,16 @@ __device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 // (zr, zi) *= (wr, wi) for two microphones at once; nwi = -wi
 __device__ __forceinline__ void cmul2(u64& zr, u64& zi, u64 wr, u64 wi, u64 nwi) {
     const u64 t1 = fmul2(zr, wr), t2 = fmul2(zi, wr);
@@ -160,7 +170,9 @@ __device__ __forceinline__ Buf buf_at(float4* base, const Geom& g, int b) {
 // from the microphone towards the point the sound comes from): rotate into the microphone frame by the
 // conjugate of its orientation, azimuth atan2(y, x) on the periodic grid -pi + 2 pi i / n_az, elevation
 // asin(z) on -pi/2 + pi j / (n_el - 1), bilinear in (az, el).
-__device__ __forceinline__ void mic_bands(const AccumArgs& a, int m, float vx, float vy, float vz, float* out, int NB) {
+// (out[b * stride] for band b)
+__device__ __forceinline__ void mic_bands(const AccumArgs& a, int m, float vx, float vy, float vz, float* out, int NB,
+                                          int stride = 1) {
     const float l = sqrtf(vx * vx + vy * vy + vz * vz);
     float x = vx / l, y = vy / l, z = vz / l;
     if (a.mic_q) {
@@ -192,7 +204,7 @@ __device__ __forceinline__ void mic_bands(const AccumArgs& a, int m, float vx, f
     for (int b = 0; b < NB; ++b) {
         const float lo = (1.0f - wa) * t00[b] + wa * t01[b];
         const float hi = (1.0f - wa) * t10[b] + wa * t11[b];
-        out[b] = (1.0f - wb) * lo + wb * hi;
+        out[b * stride] = (1.0f - wb) * lo + wb * hi;
     }
 }
 

@@ -42,7 +42,8 @@ struct NGeom {
     size_t buf_bytes, mat_bytes, smem;
 };
 
-// one pipeline buffer: zb [PT] ulonglong2, pw [PT][LNS + 2] ulonglong2, ngp [PT] u64, dband [PT][2][NB] f32
+// one pipeline buffer: zb [PT] ulonglong2, pw [PT][LNS + 2] ulonglong2, ngp [PT] u64, dband [PT][NB][2] f32 (the
+// two microphones' values of a band side by side, read as one packed pair)
 struct NBuf {
     ulonglong2* zb;
     ulonglong2* pw;
@@ -79,7 +80,7 @@ __device__ __forceinline__ void nproduce(const AccumArgs& a, const NGeom& g, con
             zf[2 + half] = 0.0f;
             if (it == 0) {
                 reinterpret_cast<float*>(B.ngp + p)[half] = 0.0f;
-                for (int b = 0; b < g.NB; ++b) B.dband[((size_t)p * 2 + half) * g.NB + b] = 0.0f;
+                for (int b = 0; b < g.NB; ++b) B.dband[((size_t)p * g.NB + b) * 2 + half] = 0.0f;
             }
             continue;
         }
@@ -99,7 +100,7 @@ __device__ __forceinline__ void nproduce(const AccumArgs& a, const NGeom& g, con
                 gam2 = gm * gm;
             }
             reinterpret_cast<float*>(B.ngp + p)[half] = -gam2;
-            if (g.NB > 0) mic_bands(a, m, d[0] - mx, d[1] - my, d[2] - mz, B.dband + ((size_t)p * 2 + half) * g.NB, g.NB);
+            if (g.NB > 0) mic_bands(a, m, d[0] - mx, d[1] - my, d[2] - mz, B.dband + (size_t)p * 2 * g.NB + half, g.NB, 2);
             const float L0 = -2.0f * log2_ff(r) + rh * (a.atm2_0 + a.atm2_step * (float)kb);
             const ff x0 = ff_mul(r, ff{a.qhi[min(kb, a.F - 1)], a.qlo[min(kb, a.F - 1)]});
             float s0, c0;
@@ -238,8 +239,7 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
                 ew = x - (float)itn;
                 e0 = a.etab + (int64_t)itn * a.F;
             }
-            const float* d1 = C.dband + (size_t)p * 2 * g.NB;
-            const float* d2 = d1 + g.NB;
+            const u64* dp = reinterpret_cast<const u64*>(C.dband) + (size_t)p * g.NB;
             // the term loop, specialised on the emitter table (its loads then carry no condition)
             auto terms = [&](auto has_e) {
                 constexpr bool HE = decltype(has_e)::value;
@@ -270,15 +270,12 @@ __global__ void __launch_bounds__(kNThreads, 2) k_accum_narrow(const AccumArgs a
                         const float x = ex2(lx);
                         E = pk2(x, x);
                     }
-                    if (DIR) {
+                    if (DIR) {  // both microphones' bands at once
                         const float2 bwv = bwt[i];
                         const int b0 = (int)bwv.x;
-                        float D1 = d1[b0], D2 = d2[b0];
-                        if (g.NB > 1) {
-                            D1 = fmaf(bwv.y, d1[b0 + 1] - D1, D1);
-                            D2 = fmaf(bwv.y, d2[b0 + 1] - D2, D2);
-                        }
-                        E = fmul2(E, pk2(D1 * de, D2 * de));
+                        u64 D = dp[b0];
+                        if (g.NB > 1) D = ffma2(pk2(bwv.y, bwv.y), fsub2(dp[b0 + 1], D), D);
+                        E = fmul2(E, HE ? fmul2(D, pk2(de, de)) : D);
                     } else if (HE) {
                         E = fmul2(E, pk2(de, de));
                     }

@@ -26,17 +26,6 @@ namespace {
 
 using namespace acc;
 
-__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
-    u64 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fsub2(u64 a, u64 b) {
-    u64 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
 constexpr int kNV = 4;  // materials whose reflection gradient one launch accumulates
 
 // Reduce-scatter of 8 per-bin values over the TP = 2^TPL lanes of a microphone-pair group (TP
