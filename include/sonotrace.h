@@ -399,7 +399,10 @@ void st_inject_alloc_failure(int64_t after);
  * library; every GPU that loads the library holds it until the process exits.  Sizes whose tables
  * plus one chunk of partial spectra (about 8 * n_mics * n_bins + 8 * n_mat * n_bins bytes) exceed
  * it return ST_ERR_ARG.  The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture begins.  All calls share the
+ * device current); make that first call before any stream capture begins.  The call itself is not
+ * meant for capture into a CUDA graph: its host band tables are copied with cudaMemcpyAsync, which a
+ * capture would either refuse (pageable memory) or replay from the host buffer as it is at replay time
+ * (pinned memory).  All calls share the
  * array: calls that overlap on the GPU race and give wrong results, so order them on one stream.
  * Every call rewrites all of the scratch it reads, so no state carries over between calls. */
 #define ST_NOALLOC_SCRATCH_BYTES (8u << 20)
