@@ -185,6 +185,16 @@ st_status st_scene_load_instances(st_ctx* ctx, int32_t n_proto, const int64_t* p
  * ST_ERR_MESH when a world vertex is not finite (the scene is then unbuilt until a later call with finite
  * maps, as for st_scene_update_vertices). */
 st_status st_scene_set_instance_transforms(st_scene* scene, const float* inst_xform, int32_t mem, int32_t flags);
+/* Checkpoint / resume of a precomputed scene loaded flat: st_scene_serialize writes the mesh, the material
+ * tables, the curvature, metric and CDFs, the 4-wide BVH with its refit topology and the precompute's
+ * parameters into buf (host memory, *bytes long); buf NULL returns the size needed in *bytes.
+ * st_scene_deserialize makes a new scene of ctx from such a blob, precomputed: simulates on it give the
+ * same bits as on the serialised scene.  The blob carries a format version and a checksum of its contents;
+ * a blob that is truncated, modified or of another version returns ST_ERR_ARG before anything reaches the
+ * device.  ST_ERR_STATE for a scene not precomputed, or loaded by st_scene_load_instances; ST_ERR_ARG for a
+ * buffer smaller than *bytes (which then holds the size needed).  Synchronises the context's stream. */
+st_status st_scene_serialize(st_scene* scene, void* buf, size_t* bytes);
+st_status st_scene_deserialize(st_ctx* ctx, const void* buf, size_t bytes, st_scene** out);
 /* Hierarchy of an instanced scene.  ST_STRUCTURE_FLAT (the default): one BVH over the expanded world
  * triangles.  ST_STRUCTURE_TWO_LEVEL: a 4-wide BVH per prototype over its triangles in object space, built
  * once, and a top-level BVH over the instances' world boxes, rebuilt by every precompute and instance

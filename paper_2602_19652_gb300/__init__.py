@@ -396,6 +396,30 @@ class Scene:
         self.ctx._check(self.ctx.L.st_scene_set_instance_transforms(
             self.h, ptr_, mem, _lib.ST_REFIT_KEEP_CURVATURE if keep_curvature else 0))
 
+    def serialize(self) -> bytes:
+        """Host blob of the precomputed scene (checkpoint; see the C header)."""
+        n = C.c_size_t(0)
+        self.ctx._check(self.ctx.L.st_scene_serialize(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self.ctx._check(self.ctx.L.st_scene_serialize(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    @classmethod
+    def deserialize(cls, ctx: Context, blob: bytes) -> "Scene":
+        """A precomputed scene of ctx from a blob of Scene.serialize (resume; no precompute needed)."""
+        h = C.c_void_p()
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        ctx._check(ctx.L.st_scene_deserialize(ctx.h, buf, len(blob), C.byref(h)))
+        sc = cls(ctx, None, None, None, None, _handle=h)
+        nv, nt = C.c_int64(0), C.c_int64(0)
+        ctx._check(ctx.L.st_scene_get_geometry(h, C.byref(nv), C.byref(nt), None, None, None, None, ST_MEM_HOST))
+        sc.n_verts, sc.n_tris = nv.value, nt.value
+        o = np.empty(sc.n_tris, np.int32)
+        ctx._check(ctx.L.st_scene_get_geometry(h, None, None, None, None, None, o.ctypes.data_as(C.c_void_p),
+                                               ST_MEM_HOST))
+        sc.n_obj = int(o.max()) + 1
+        return sc
+
     def set_structure(self, two_level: bool):
         """Hierarchy of an instanced scene: one BVH over the expanded triangles (two_level=False, the default)
         or per-prototype BVHs in object space under a BVH over the instances (see the C header)."""

@@ -88,6 +88,8 @@ SIGNATURES = {
     "st_scene_load_instances": (I32, [P, I32, P, P, P, P, P, I32, P, P, P]),
     "st_scene_set_instance_transforms": (I32, [P, P, I32, I32]),
     "st_scene_set_structure": (I32, [P, I32]),
+    "st_scene_serialize": (I32, [P, P, C.POINTER(C.c_size_t)]),
+    "st_scene_deserialize": (I32, [P, P, C.c_size_t, C.POINTER(P)]),
     "st_scene_get_geometry": (I32, [P, P, P, P, P, P, P, I32]),
     "st_ray_directions": (I32, [P, I32, I64, P]),
     "st_impulse_response": (I32, [P, P, I32, I32, I32, F64, F64, F64, I32, P, P, I32, I32, P]),

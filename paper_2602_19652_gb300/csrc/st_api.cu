@@ -2230,6 +2230,202 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
     return ST_OK;
 }
 
+// ---- checkpoint / resume of a precomputed flat scene
+// Blob: "STSC", format version, a header of sizes and parameters, the material tables, then every device
+// array of the scene as (u64 byte count, bytes, zero padding to 8 bytes), in a fixed order.
+namespace {
+constexpr uint32_t kBlobMagic = 0x43535453u;  // "STSC"
+constexpr uint32_t kBlobVersion = 1;
+struct BlobHeader {
+    uint32_t magic, version;
+    int64_t n_verts, n_tris, n_nodes, total_samples;
+    int32_t n_obj, root, n_mat, n_bands;
+    float bounds_lo[3], bounds_hi[3];
+    float eta, area_ref, hc_frac;
+    int32_t samples_per_vertex;
+    double dither;
+    int64_t budget;
+    uint64_t seed;
+    uint64_t checksum;  // FNV-1a over everything after the header
+};
+
+// the scene's device arrays with their sizes in bytes, from the counts (a flat precomputed scene has all of
+// them; the binary topology only above one leaf)
+std::vector<std::pair<DevBuf*, size_t>> scene_arrays(SceneDev& S) {
+    const size_t nv = (size_t)S.n_verts, nt = (size_t)S.n_tris, no = (size_t)S.n_obj;
+    const bool tree = nt > (size_t)kLeafMax;
+    return {{&S.verts, nv * 12},
+            {&S.tris, nt * 12},
+            {&S.tri_mat, nt * 4},
+            {&S.tri_obj, nt * 4},
+            {&S.nrm, nt * 12},
+            {&S.nodes, (size_t)std::max<int64_t>(S.n_nodes, 1) * 128},
+            {&S.tri_v, nt * 48},
+            {&S.G, nv * 4},
+            {&S.C, nt * 4},
+            {&S.mesh_tris, nt * 4},
+            {&S.mesh_off, (no + 1) * 8},
+            {&S.cdf, nt * 8},
+            {&S.n_samples, (no + 1) * 8},
+            {&S.sample_off, (no + 1) * 8},
+            {&S.bvh_child, tree ? (nt - 1) * 8 : 0},
+            {&S.bvh_range, tree ? (nt - 1) * 8 : 0},
+            {&S.bvh_par_i, tree ? nt * 4 : 0},
+            {&S.bvh_par_l, tree ? nt * 4 : 0},
+            {&S.bvh_perm, nt * 4},
+            {&S.bvh_wflag, tree ? (nt - 1) * 4 : 0},
+            {&S.bvh_widx, tree ? (nt - 1) * 4 : 0}};
+}
+
+size_t pad8(size_t n) { return (n + 7) & ~size_t(7); }
+
+uint64_t fnv1a(const char* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= (uint8_t)p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+}  // namespace
+
+st_status st_scene_serialize(st_scene* sc, void* buf, size_t* bytes) {
+    if (!sc || !bytes) return ST_ERR_ARG;
+    st_ctx* c = sc->ctx;
+    if (!sc->precomputed || !sc->S.built || !sc->S.bvh_ready)
+        return fail(c, ST_ERR_STATE, "scene_serialize: a precomputed scene is needed");
+    if (sc->instanced) return fail(c, ST_ERR_STATE, "scene_serialize: instanced scenes are not serialised");
+    SceneDev& S = sc->S;
+    const auto arrays = scene_arrays(S);
+    const size_t nb = (size_t)S.n_mat * S.n_bands;
+    size_t total = pad8(sizeof(BlobHeader)) + pad8((size_t)S.n_bands * 4) + 3 * pad8(nb * 4);
+    for (const auto& a : arrays) total += 8 + pad8(a.second);
+    if (!buf) {
+        *bytes = total;
+        return ST_OK;
+    }
+    if (*bytes < total) {
+        *bytes = total;
+        return fail(c, ST_ERR_ARG, "scene_serialize: buffer too small (*bytes holds the size needed)");
+    }
+    enter(c);
+    char* o = static_cast<char*>(buf);
+    memset(o, 0, total);
+    BlobHeader h{};
+    h.magic = kBlobMagic;
+    h.version = kBlobVersion;
+    h.n_verts = S.n_verts;
+    h.n_tris = S.n_tris;
+    h.n_nodes = S.n_nodes;
+    h.total_samples = S.total_samples;
+    h.n_obj = S.n_obj;
+    h.root = S.root;
+    h.n_mat = S.n_mat;
+    h.n_bands = S.n_bands;
+    memcpy(h.bounds_lo, S.bounds_lo, 12);
+    memcpy(h.bounds_hi, S.bounds_hi, 12);
+    h.eta = sc->cp.eta;
+    h.area_ref = sc->cp.area_ref;
+    h.hc_frac = sc->cp.hc_frac;
+    h.samples_per_vertex = sc->cp.samples_per_vertex;
+    h.dither = sc->cp.dither;
+    h.budget = sc->cp.budget;
+    h.seed = sc->cp.seed;
+    memcpy(o, &h, sizeof(h));
+    size_t at = pad8(sizeof(BlobHeader));
+    memcpy(o + at, S.band_hz.data(), (size_t)S.n_bands * 4);
+    at += pad8((size_t)S.n_bands * 4);
+    for (const std::vector<float>* v : {&S.k_band, &S.beta_band, &S.diff_band}) {
+        memcpy(o + at, v->data(), nb * 4);
+        at += pad8(nb * 4);
+    }
+    CKC(c, cudaStreamSynchronize(c->stream), "scene_serialize sync");  // earlier work may still write the scene
+    for (const auto& a : arrays) {
+        const uint64_t n = a.second;
+        memcpy(o + at, &n, 8);
+        at += 8;
+        if (n) CKC(c, cudaMemcpy(o + at, a.first->p, n, cudaMemcpyDeviceToHost), "scene_serialize copy");
+        at += pad8(n);
+    }
+    h.checksum = fnv1a(o + pad8(sizeof(BlobHeader)), total - pad8(sizeof(BlobHeader)));
+    memcpy(o, &h, sizeof(h));
+    *bytes = total;
+    return ST_OK;
+}
+
+st_status st_scene_deserialize(st_ctx* c, const void* buf, size_t bytes, st_scene** out) {
+    if (!c || !buf || !out) return ST_ERR_ARG;
+    *out = nullptr;
+    const char* in = static_cast<const char*>(buf);
+    BlobHeader h;
+    if (bytes < sizeof(h)) return fail(c, ST_ERR_ARG, "scene_deserialize: blob too short");
+    memcpy(&h, in, sizeof(h));
+    if (h.magic != kBlobMagic || h.version != kBlobVersion)
+        return fail(c, ST_ERR_ARG, "scene_deserialize: not a scene blob of this format version");
+    if (h.n_verts <= 0 || h.n_tris <= 0 || h.n_tris >= (1ll << 28) || h.n_verts >= (1ll << 31) || h.n_obj < 1 ||
+        h.n_obj > (1 << 24) || h.n_mat < 1 || h.n_mat > 255 || h.n_bands < 1 || h.n_bands > 64 || h.n_nodes < 0 ||
+        h.n_nodes >= h.n_tris + 1 || h.total_samples < 0)
+        return fail(c, ST_ERR_ARG, "scene_deserialize: sizes out of range");
+    // the whole blob is checked before anything reaches the device: its contents index device arrays
+    if (bytes < pad8(sizeof(BlobHeader)) || fnv1a(in + pad8(sizeof(BlobHeader)), bytes - pad8(sizeof(BlobHeader))) !=
+                                                 h.checksum)
+        return fail(c, ST_ERR_ARG, "scene_deserialize: checksum mismatch (truncated or modified blob)");
+    enter(c);
+    st_scene* sc = new st_scene();
+    sc->ctx = c;
+    SceneDev& S = sc->S;
+    S.n_verts = h.n_verts;
+    S.n_tris = h.n_tris;
+    S.n_nodes = h.n_nodes;
+    S.total_samples = h.total_samples;
+    S.n_obj = h.n_obj;
+    S.root = h.root;
+    S.n_mat = h.n_mat;
+    S.n_bands = h.n_bands;
+    memcpy(S.bounds_lo, h.bounds_lo, 12);
+    memcpy(S.bounds_hi, h.bounds_hi, 12);
+    const size_t nb = (size_t)h.n_mat * h.n_bands;
+    size_t at = pad8(sizeof(BlobHeader));
+    auto fail_free = [&](st_status code, const char* msg) {
+        scene_free(sc);
+        return fail(c, code, msg);
+    };
+    if (at + pad8((size_t)h.n_bands * 4) + 3 * pad8(nb * 4) > bytes)
+        return fail_free(ST_ERR_ARG, "scene_deserialize: blob too short");
+    S.band_hz.assign(reinterpret_cast<const float*>(in + at), reinterpret_cast<const float*>(in + at) + h.n_bands);
+    at += pad8((size_t)h.n_bands * 4);
+    for (std::vector<float>* v : {&S.k_band, &S.beta_band, &S.diff_band}) {
+        v->assign(reinterpret_cast<const float*>(in + at), reinterpret_cast<const float*>(in + at) + nb);
+        at += pad8(nb * 4);
+    }
+    for (const auto& a : scene_arrays(S)) {
+        uint64_t n = 0;
+        if (at + 8 > bytes) return fail_free(ST_ERR_ARG, "scene_deserialize: blob too short");
+        memcpy(&n, in + at, 8);
+        at += 8;
+        // every array has exactly the size the header's counts give it
+        if (n != a.second || n > bytes - at) return fail_free(ST_ERR_ARG, "scene_deserialize: array size mismatch");
+        if (n) {
+            cudaError_t e = grow(*a.first, n);
+            if (e == cudaSuccess) e = cudaMemcpy(a.first->p, in + at, n, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                scene_free(sc);
+                return cuda_fail(c, e, "scene_deserialize copy");
+            }
+        }
+        at += pad8(n);
+    }
+    S.built = true;
+    S.bvh_ready = true;
+    sc->cp = CurvParamsDev{h.eta, h.area_ref, h.hc_frac, h.dither, h.samples_per_vertex, h.budget, h.seed};
+    sc->has_materials = true;
+    sc->precomputed = true;
+    sc->version = g_scene_version++;
+    c->scenes.push_back(sc);
+    *out = sc;
+    return ST_OK;
+}
+
 // ---- entry points with NVTX ranges and ST_LOG lines around the implementations above
 st_status st_simulate(st_ctx* c, st_scene* sc, const st_sim_params* params, void* spectra_out, st_stats* stats) {
     NvtxRange range("st_simulate");

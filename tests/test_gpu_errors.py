@@ -204,3 +204,55 @@ def test_log_levels(tmp_path):
     assert any("error" in l and "simulate" in l for l in out["1"]) and not any("simulate: " in l and "rays" in l
                                                                               for l in out["1"])
     assert any("precompute:" in l for l in out["2"]) and any("rays x" in l for l in out["2"])
+
+
+def test_scene_checkpoint_resume(st):
+    """A precomputed scene serialised to a host blob and restored in another context (no precompute)
+    gives the same path records, diffraction samples, curvature and spectra bit for bit; a truncated, a
+    modified and a foreign blob are refused on the host; instanced and unprecomputed scenes are refused."""
+    import ctypes as C
+    wl = synth.clutter(seed=41, target_tris=6000, n_rays=4000, bounces=3, n_mics=8, n_bins=64)
+    ctx = st.Context(0)
+    sc = st.from_workload(ctx, wl, st.curv_params(sample_budget=30_000))
+    p = st.sim_params(max_bounces=wl.bounces, max_distance=wl.max_distance)
+    S0 = ctx.simulate(sc, p).cpu().numpy()
+    P0, D0 = ctx.paths(wl.bounces), ctx.diffraction()
+    G0 = sc.curvature()
+    blob = sc.serialize()
+    ctx2 = st.Context(0)
+    sc2 = st.Scene.deserialize(ctx2, blob)
+    ctx2.set_frequencies(wl.n_bins, wl.f_lo, wl.f_hi)
+    ctx2.set_emitter(wl.emitter, wl.emitter_quat, wl.dirs, None, wl.fov_half)
+    ctx2.set_receivers(wl.mics)
+    S1 = ctx2.simulate(sc2, p).cpu().numpy()
+    assert np.array_equal(S0, S1)
+    P1, D1 = ctx2.paths(wl.bounces), ctx2.diffraction()
+    for k in P0:
+        assert np.array_equal(P0[k], P1[k]), k
+    for a, b in zip(D0, D1):
+        assert np.array_equal(a, b)
+    for a, b in zip(G0, sc2.curvature()):
+        assert np.array_equal(a, b)
+    assert sc2.serialize() == blob
+    # the restored scene refits like the original
+    v = sc.geometry()[0] + np.float32(0.01)
+    sc.update_vertices(v)
+    sc2.update_vertices(v)
+    assert np.array_equal(ctx.simulate(sc, p).cpu().numpy(), ctx2.simulate(sc2, p).cpu().numpy())
+    L = st.load()
+    h = C.c_void_p()
+    bad = bytearray(blob)
+    bad[len(bad) // 2] ^= 1
+    for b in (blob[: len(blob) - 8], bytes(bad), b"XXXX" + blob[4:]):
+        buf = C.create_string_buffer(bytes(b), len(b))
+        assert L.st_scene_deserialize(ctx2.h, buf, len(b), C.byref(h)) == st.ST_ERR_ARG
+    n = C.c_size_t(16)
+    small = C.create_string_buffer(16)
+    assert L.st_scene_serialize(sc.h, small, C.byref(n)) == st.ST_ERR_ARG and n.value == len(blob)
+    raw = st.Scene(ctx, wl.verts, wl.tris, wl.tri_mat, wl.tri_obj)
+    assert L.st_scene_serialize(raw.h, None, C.byref(n)) == st.ST_ERR_STATE
+    fo = synth.instanced_forest(seed=609, n_inst=4, n_rays=64, n_mics=2, n_bins=8)
+    inst = st.Scene.from_instances(ctx, fo.protos, fo.inst_proto, fo.inst_xform)
+    inst.set_materials(fo.base.band_hz, fo.base.k_band, fo.base.beta_band, fo.base.diff_band)
+    inst.precompute()
+    assert L.st_scene_serialize(inst.h, None, C.byref(n)) == st.ST_ERR_STATE
