@@ -121,6 +121,10 @@ void st_curv_params_default(st_curv_params* p);
 void st_sim_params_default(st_sim_params* p);
 /* Static name of a status code ("unknown status" for a value outside the list above). */
 const char* st_status_string(st_status s);
+/* 1 in the bounds-checked build (compiled with ST_CHECKS: indices read from device data -- tree references,
+ * leaf, triangle and material ids -- are checked before they index an array; a failed check skips the access
+ * and the call returns ST_ERR_CUDA), 0 otherwise. */
+int32_t st_checked_build(void);
 /* Message of the last failing call on ctx (owned by ctx, valid until the next call). */
 const char* st_last_error(const st_ctx* ctx);
 

@@ -8,7 +8,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libsonotrace.so")
+# ST_CHECKS=1 in the environment loads the bounds-checked build (build(checks=True)) instead
+LIB_PATH = os.path.join(HERE, "_build_checks" if os.environ.get("ST_CHECKS") == "1" else "_build", "libsonotrace.so")
 
 P = C.c_void_p
 I32, I64, U32, U64, F32, F64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float, C.c_double
@@ -62,6 +63,7 @@ SIGNATURES = {
     "st_curv_params_default": (None, [P]),
     "st_sim_params_default": (None, [P]),
     "st_status_string": (C.c_char_p, [I32]),
+    "st_checked_build": (I32, []),
     "st_last_error": (C.c_char_p, [P]),
     "st_create": (I32, [P, I32, P]),
     "st_destroy": (I32, [P]),

@@ -14,6 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsonotrace.so")
+# the bounds-checked build (-DST_CHECKS: indices read from device data are checked before use, a failed
+# check is reported as ST_ERR_CUDA); same sources, its own output folder
+OUT_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(OUT_CHECKS, "libsonotrace.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -48,16 +52,18 @@ def _sources_newer(target: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
-    if not force and not _sources_newer(LIB):
-        return LIB
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, checks: bool = False) -> str:
+    out, lib = (OUT_CHECKS, LIB_CHECKS) if checks else (OUT, LIB)
+    os.makedirs(out, exist_ok=True)
+    if not force and not _sources_newer(lib):
+        return lib
     cc = nvcc()
+    extra = ["-DST_CHECKS"] if checks else []
 
     def compile_one(unit):
         src = os.path.join(CSRC, unit)
-        obj = os.path.join(OUT, unit.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *COMMON, *UNITS[unit], "-c", src, "-o", obj]
+        obj = os.path.join(out, unit.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *COMMON, *extra, *UNITS[unit], "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -69,7 +75,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     with cf.ThreadPoolExecutor(max_workers=jobs or len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"]
     if verbose:
@@ -77,9 +83,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checks="--checks" in sys.argv))

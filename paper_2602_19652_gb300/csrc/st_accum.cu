@@ -437,7 +437,8 @@ __global__ void k_gather_spec(const GatherArgs g, float* px, float* py, float* p
         uint32_t lo = 0, hi = 0;
         int matj = 0;
         for (int q = 0; q <= j; ++q) {
-            const uint32_t mq = (uint32_t)g.tri_mat[g.rec_tri[ray * g.B + q]] & 255u;
+            uint32_t mq = (uint32_t)g.tri_mat[g.rec_tri[ray * g.B + q]] & 255u;
+            ST_CHECK_OR((int)mq < g.n_mat, g.chk, mq = 0);
             if (q < 4) lo |= mq << (8 * q); else hi |= mq << (8 * (q - 4));
             matj = (int)mq;
         }
@@ -469,7 +470,9 @@ __global__ void k_gather_diff(const GatherArgs g, float* px, float* py, float* p
         const ff r = dist_ff(ox, oy, oz, g.s[0], g.s[1], g.s[2]);
         rhi[c] = r.hi;
         rlo[c] = r.lo;
-        meta[c] = ((uint32_t)g.tri_mat[g.cand_tri[i]] & 255u) << 8;
+        uint32_t mi = (uint32_t)g.tri_mat[g.cand_tri[i]] & 255u;
+        ST_CHECK_OR((int)mi < g.n_mat, g.chk, mi = 0);
+        meta[c] = mi << 8;
         if (g.has_etab) {
             const float vx = ox - g.s[0], vy = oy - g.s[1], vz = oz - g.s[2];
             const float cth = (g.fwd[0] * vx + g.fwd[1] * vy + g.fwd[2] * vz) / r.hi;
@@ -556,7 +559,8 @@ __global__ void k_gather_spec_batch(const BatchArgs a, const uint32_t* idx, cons
         uint32_t lo = 0, hi = 0;
         int matj = 0;
         for (int q = 0; q <= j; ++q) {
-            const uint32_t mq = (uint32_t)b.tri_mat[a.rec_tri[b.rec_off + ray * b.B + q]] & 255u;
+            uint32_t mq = (uint32_t)b.tri_mat[a.rec_tri[b.rec_off + ray * b.B + q]] & 255u;
+            ST_CHECK_OR((int)mq < b.n_mat, a.flags, mq = 0);
             if (q < 4) lo |= mq << (8 * q); else hi |= mq << (8 * (q - 4));
             matj = (int)mq;
         }
@@ -591,7 +595,9 @@ __global__ void k_gather_diff_batch(const BatchArgs a, const uint32_t* idx, cons
         const ff r = dist_ff(ox, oy, oz, b.s[0], b.s[1], b.s[2]);
         rhi[c] = r.hi;
         rlo[c] = r.lo;
-        meta[c] = ((uint32_t)b.tri_mat[a.cand_tri[i]] & 255u) << 8;
+        uint32_t mi = (uint32_t)b.tri_mat[a.cand_tri[i]] & 255u;
+        ST_CHECK_OR((int)mi < b.n_mat, a.flags, mi = 0);
+        meta[c] = mi << 8;
         if (b.etab) {
             const float vx = ox - b.s[0], vy = oy - b.s[1], vz = oz - b.s[2];
             const float cth = (b.fwd[0] * vx + b.fwd[1] * vy + b.fwd[2] * vz) / r.hi;

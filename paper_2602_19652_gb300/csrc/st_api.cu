@@ -224,7 +224,13 @@ static void scene_trav_args(A& a, const SceneDev& S) {
     a.tri_v = ptr<float4>(S.tri_v);
     a.root = S.root;
     a.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
+    a.chk[0] = S.n_nodes > 0 ? S.n_nodes : 1;  // (a scene of one leaf keeps one node allocated)
+    a.chk[1] = S.n_tris;
+    a.chk[5] = S.n_tris;
     if (S.two_level) {
+        a.chk[2] = std::max<int64_t>(S.blas_n_nodes, 1);
+        a.chk[3] = S.inst ? S.inst->ptoff_h.back() : 0;
+        a.chk[4] = S.inst ? S.inst->n_inst : 0;
         const int64_t n_inst = S.inst ? S.inst->n_inst : 0;
         a.bnodes = ptr<float4>(S.blas_nodes);
         a.btri = ptr<float4>(S.blas_tri);
@@ -300,6 +306,14 @@ void st_sim_params_default(st_sim_params* p) {
     p->seed = 0;
     p->pose_index = 0;
     p->los_mode = ST_LOS_REFERENCE;
+}
+
+int32_t st_checked_build(void) {
+#ifdef ST_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 const char* st_status_string(st_status s) {
@@ -1091,6 +1105,8 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
     memcpy(ga.s, c->s, 12);
     ga.idx = ptr<uint32_t>(c->sidx);
     ga.rec_mask = per_mic ? ptr<uint64_t>(c->rec_mask) : nullptr;
+    ga.n_mat = S.n_mat;
+    ga.chk = ptr<uint32_t>(c->flags);
     auto set_paths = [&](AccumArgs& x, PathList& PL) {
         x.px = ptr<float>(PL.px);
         x.py = ptr<float>(PL.py);
@@ -1261,7 +1277,16 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
         }
         stats->terms = ((int64_t)((n_accum & 1) ? h[2] : 0) + (int64_t)((n_accum & 2) ? h[3] : 0)) * M * F;
         if (fl & kFlagBadTree) return fail(c, ST_ERR_CUDA, "malformed BVH: traversal exceeded the node count");
+        if (fl & kFlagCheck) return fail(c, ST_ERR_CUDA, "a bounds check of the checked build failed");
     }
+#ifdef ST_CHECKS
+    {  // the checked build reads the flags after every simulate
+        uint32_t fl = 0;
+        CKC(c, cudaMemcpyAsync(&fl, c->flags.p, 4, cudaMemcpyDeviceToHost, s), "checks");
+        CKC(c, cudaStreamSynchronize(s), "checks sync");
+        if (fl & kFlagCheck) return fail(c, ST_ERR_CUDA, "a bounds check of the checked build failed");
+    }
+#endif
     return ST_OK;
 }
 
@@ -2075,6 +2100,9 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
         d.root = S.root;
         d.max_iter = (int32_t)std::min<int64_t>(2 * S.n_tris + 8, (int64_t)1 << 30);
         d.n_obj = S.n_obj;
+        d.n_mat = S.n_mat;
+        d.chk_nodes = S.n_nodes > 0 ? S.n_nodes : 1;
+        d.chk_tris = S.n_tris;
         d.cos_fov = J.fov_half_rad >= (float)M_PI ? -2.0f : (float)cos((double)J.fov_half_rad);
         d.s = J.emitter;
         d.q = J.emitter_quat;
@@ -2134,6 +2162,7 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     uint32_t fl = 0;
     CKC(c, cudaMemcpy(&fl, B.flags.p, 4, cudaMemcpyDeviceToHost), "batch flags");
     if (fl & kFlagBadTree) return fail(c, ST_ERR_CUDA, "malformed BVH: traversal exceeded the node count");
+    if (fl & kFlagCheck) return fail(c, ST_ERR_CUDA, "a bounds check of the checked build failed");
     CKC(c, cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal), "batch capture");
     cudaError_t ie = batch_issue(c, B, jobs, p, tn, ms);
     cudaGraph_t g = nullptr;

@@ -22,6 +22,15 @@ namespace {
 
 using namespace trv;
 
+// a job's scene as the traversal sees it
+__device__ __forceinline__ Trav job_trav(const JobDev& b, const BatchArgs& a) {
+    Trav T{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
+    T.chk[0] = b.chk_nodes;
+    T.chk[1] = b.chk_tris;
+    T.chk[5] = b.chk_tris;
+    return T;
+}
+
 // per job: receiver reference point (float64 sum of the microphones in order / M) and forward axis
 __global__ void k_batch_prep(const JobDev* J, int n_jobs) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -70,7 +79,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_closest_batch(const BatchArgs
                 g = batch_ray(a, j, idx, &job);
                 const JobDev& b = a.jobs[job];
                 if (j < b.B) {
-                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
+                    T = job_trav(b, a);
                     f3 o, d;
                     int32_t prev;
                     if (j == 0) {
@@ -122,6 +131,7 @@ __global__ void k_shade_batch(const BatchArgs a, int j, int64_t n_first) {
         warp_count(a.queries + 0);
         const int32_t tri = a.hit_tri[g];
         if (tri < 0) continue;
+        ST_CHECK_OR(tri < b.chk_tris, a.flags, continue);
         warp_count(a.queries + 1);
         const float t = a.hit_t[g];
         const int64_t local = g - b.ray_off;
@@ -218,7 +228,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_batch(const BatchArgs
                 if (!(tmax > a.t_min)) {
                     out[id] = 1;
                 } else {
-                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
+                    T = job_trav(b, a);
                     trav_init(S, T, o, u, excl[id], a.t_min, tmax);
                     live = true;
                 }
@@ -271,7 +281,7 @@ __global__ void __launch_bounds__(kTravBlock, 8) k_visible_mics_batch(const Batc
                     atomicOr(reinterpret_cast<unsigned long long*>(&a.rec_mask[id]), 1ull << m);
                     a.rec_los[id] = 1;
                 } else {
-                    T = Trav{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
+                    T = job_trav(b, a);
                     trav_init(S, T, o, u, a.rec_tri[id], a.t_min, tmax);
                     live = true;
                 }
@@ -323,7 +333,8 @@ __global__ void __launch_bounds__(128, 8) k_diffraction_batch(const BatchArgs a)
             const int64_t mid = l + ((h - l) >> 1);
             if (b.cdf[mid] > target) h = mid; else l = mid + 1;
         }
-        const int32_t t = b.mesh_tris[l];
+        int32_t t = b.mesh_tris[l];
+        ST_CHECK_OR(t >= 0 && t < b.chk_tris, a.flags, t = 0);
         float ba = (float)(x[2] >> 8) * (1.0f / 16777216.0f);
         float bb = (float)(x[3] >> 8) * (1.0f / 16777216.0f);
         const float sum = ba + bb;
@@ -381,7 +392,7 @@ __global__ void k_direct_batch(const BatchArgs a) {
         const int job = find_job(a.mic_offs, a.n_jobs, g);
         const JobDev& b = a.jobs[job];
         const int m = (int)(g - b.mic_off);
-        const Trav T{b.nodes, b.tri_v, b.root, b.max_iter, nullptr, a.stack_limit};
+        const Trav T = job_trav(b, a);
         warp_count(a.queries + 1);
         a.dvis[g] = visible(T, f3{b.s[0], b.s[1], b.s[2]}, f3{b.mics[3 * m], b.mics[3 * m + 1], b.mics[3 * m + 2]},
                             -1, a.t_min, a.los_eps, a.flags)

@@ -23,6 +23,25 @@ constexpr uint32_t kFlagStackOverflow = 1u;  // (unused: a traversal that would 
 constexpr uint32_t kFlagBadIndex = 2u;
 constexpr uint32_t kFlagBadVertex = 4u;
 constexpr uint32_t kFlagBadTree = 8u;
+constexpr uint32_t kFlagCheck = 16u;  // a bounds check of the checked build failed (the access was skipped)
+
+// Bounds-checked build (-DST_CHECKS, `build(checks=True)`): indices read from device data (tree references,
+// leaf and triangle ids, materials) are checked before they index an array; a failed check sets kFlagCheck
+// in the launch's flags word, skips the access and takes `action`, and the call returns ST_ERR_CUDA.  In
+// the normal build the checks compile to nothing.
+#ifdef ST_CHECKS
+#define ST_CHECK_OR(cond, flags, action)                   \
+    do {                                                   \
+        if (!(cond)) {                                     \
+            if (flags) atomicOr((flags), kFlagCheck);      \
+            action;                                        \
+        }                                                  \
+    } while (0)
+#else
+#define ST_CHECK_OR(cond, flags, action) \
+    do {                                 \
+    } while (0)
+#endif
 
 // ------------------------------------------------------------------ device buffers
 struct DevBuf {
@@ -161,6 +180,9 @@ struct TraceArgs {
     const float4* btri = nullptr;
     const float4* inst = nullptr;
     const int32_t* tinst = nullptr;
+    // array sizes the checked build compares indices with: wide nodes, leaf-order triangles, prototype nodes,
+    // prototype triangles, instances, world triangles
+    int64_t chk[6] = {0, 0, 0, 0, 0, 0};
     const float* nrm;
     // rays
     float s[3];
@@ -221,6 +243,9 @@ struct DiffArgs {
     const float4* btri = nullptr;
     const float4* inst = nullptr;
     const int32_t* tinst = nullptr;
+    // array sizes the checked build compares indices with: wide nodes, leaf-order triangles, prototype nodes,
+    // prototype triangles, instances, world triangles
+    int64_t chk[6] = {0, 0, 0, 0, 0, 0};
     const float* nrm;
     const float* verts;
     const int32_t* tris;
@@ -265,6 +290,9 @@ struct DirectArgs {
     const float4* btri = nullptr;
     const float4* inst = nullptr;
     const int32_t* tinst = nullptr;
+    // array sizes the checked build compares indices with: wide nodes, leaf-order triangles, prototype nodes,
+    // prototype triangles, instances, world triangles
+    int64_t chk[6] = {0, 0, 0, 0, 0, 0};
     float s[3];
     const float* mics;
     int32_t M;
@@ -362,6 +390,8 @@ struct GatherArgs {
     const uint32_t* count;
     PathList* out;
     const uint64_t* rec_mask;  // optional: per-microphone visibility of the records, copied to out->mask
+    int32_t n_mat = 256;       // checked build: materials of the scene
+    uint32_t* chk = nullptr;   // checked build: flags word
 };
 cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s);
 // Stable sort of the compacted specular indices idx[0 .. cap) by emitter-table row (entries past *g.count
@@ -389,6 +419,8 @@ struct JobDev {
     const uint64_t* cdf;
     const int64_t* sample_off;
     int32_t root, max_iter, n_obj;
+    int32_t n_mat;          // checked build: materials of the scene
+    int64_t chk_nodes, chk_tris;  // checked build: wide nodes and triangles of the scene (see Trav::chk)
     float cos_fov;          // <= -1: field of view off
     // sensor inputs (the caller's device memory, read at run time)
     const float* s;

@@ -37,6 +37,7 @@ __host__ __device__ __forceinline__ Trav trav_of(const A& a) {
     T.btri = a.btri;
     T.inst = a.inst;
     T.tinst = a.tinst;
+    for (int k = 0; k < 6; ++k) T.chk[k] = a.chk[k];
     return T;
 }
 
@@ -101,6 +102,7 @@ __global__ void k_shade(const TraceArgs a, int j, int64_t n_first) {
         warp_count(a.queries + 0);
         const int32_t tri = a.hit_tri[ray];
         if (tri < 0) continue;
+        ST_CHECK_OR(tri < a.chk[5], a.flags, continue);
         const float t = a.hit_t[ray];
         f3 o, d;
         double r;
@@ -306,7 +308,8 @@ __global__ void __launch_bounds__(128, 8) k_diffraction(const DiffArgs a) {
             const int64_t mid = l + ((h - l) >> 1);
             if (a.cdf[mid] > target) h = mid; else l = mid + 1;
         }
-        const int32_t t = a.mesh_tris[l];
+        int32_t t = a.mesh_tris[l];
+        ST_CHECK_OR(t >= 0 && t < a.chk[5], a.flags, t = 0);
         float ba = (float)(x[2] >> 8) * (1.0f / 16777216.0f);
         float bb = (float)(x[3] >> 8) * (1.0f / 16777216.0f);
         const float sum = ba + bb;

@@ -28,6 +28,9 @@ struct Trav {
     const float4* __restrict__ btri = nullptr;
     const float4* __restrict__ inst = nullptr;
     const int32_t* __restrict__ tinst = nullptr;
+    // checked build: sizes of nodes, leaf-order triangles, prototype nodes, prototype triangles, instances,
+    // world triangles (see ST_CHECK_OR)
+    int64_t chk[6] = {0, 0, 0, 0, 0, 0};
 };
 
 __device__ __forceinline__ float safe_inv(float d) {
@@ -119,6 +122,7 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* sta
         return true;
     }
     if (S.ref >= 0) {
+        ST_CHECK_OR(S.ref < T.chk[0], flags, return true);
         // 4-wide node: children's bounds as lo.x, hi.x, lo.y, hi.y, lo.z, hi.z rows, then the refs
         const float4* nd = T.nodes + 8 * (size_t)S.ref;
         const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
@@ -198,6 +202,7 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravState& S, int2* sta
     } else {
         // one triangle of a leaf per step, so lanes in leaves and lanes in inner nodes of the same warp stay
         // in step
+        ST_CHECK_OR((int64_t)((~S.ref) >> 3) + ((~S.ref) & 7) < T.chk[1], flags, return true);
         if (leaf_step<AnyHit>(T, S, 1)) return true;
         if (S.ref < 0) return false;
         if (S.sp < 0) {  // restart walk: back to the node that holds the leaf
@@ -350,6 +355,7 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravStateTL& S, int2* s
     }
     const bool in = S.inst >= 0;
     if (S.ref >= 0) {
+        ST_CHECK_OR(S.ref < (in ? T.chk[2] : T.chk[0]), flags, return true);
         const float4* nd = (in ? T.bnodes : T.nodes) + 8 * (size_t)S.ref;
         const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
         const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
@@ -414,6 +420,7 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravStateTL& S, int2* s
             return false;
         }
     } else if (in) {
+        ST_CHECK_OR((int64_t)((~S.ref) >> 3) + ((~S.ref) & 7) < T.chk[3], flags, return true);
         if (leaf_step_tl<AnyHit>(T, S, 1)) return true;
         if (S.ref < 0) return false;
         if (S.sp < 0) {
@@ -426,7 +433,9 @@ __device__ __forceinline__ bool trav_step(const Trav& T, TravStateTL& S, int2* s
         const int32_t code = ~S.ref;
         const int k = code >> 3, rest = code & 7;
         const int32_t cont = rest > 0 ? ~(((k + 1) << 3) | (rest - 1)) : 1;
+        ST_CHECK_OR((int64_t)k + rest < T.chk[4], flags, return true);
         const int32_t i = __ldg(T.tinst + k);
+        ST_CHECK_OR(i >= 0 && i < T.chk[4], flags, return true);
         const float4* r = T.inst + 8 * (size_t)i;
         const float4 blo = __ldg(r + 6), bhi = __ldg(r + 7);
         ++S.n_nodes;

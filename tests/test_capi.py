@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "sonotrace.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:st_status|void|const char\*)\s+(st_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:st_status|void|const char\*|int32_t)\s+(st_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 

@@ -31,8 +31,9 @@ def run():
     g = ctx.paths(wl.bounces)
     gd = ctx.diffraction()
     gv = ctx.direct_visibility()
-    ms = np.array([0, 13, 31], np.int32)
-    ks = np.array([0, 1, 200, 377, 511], np.int32)
+    # microphones across the pair and tile boundaries, bins at the edges of bin tiles and chain runs
+    ms = np.array([0, 5, 13, 16, 17, 31], np.int32)
+    ks = np.array([0, 1, 15, 16, 127, 128, 200, 255, 256, 377, 500, 511], np.int32)
     o = oracle.simulate(wl, ms=ms, ks=ks)
     return dict(wl=wl, S=S, stats=stats, g=g, gd=gd, gv=gv, o=o, ms=ms, ks=ks)
 
@@ -83,7 +84,7 @@ def veg():
     g = ctx.paths(wl.bounces)
     gd = ctx.diffraction()
     ms = np.array([0, 1], np.int32)
-    ks = np.array([0, 1, 333, 700, 1023], np.int32)
+    ks = np.array([0, 1, 15, 16, 255, 256, 333, 511, 512, 700, 1000, 1023], np.int32)
     o = oracle.simulate(wl, ms=ms, ks=ks)
     return dict(wl=wl, S=S, stats=stats, g=g, gd=gd, o=o, ms=ms, ks=ks)
 
