@@ -51,12 +51,23 @@ def accum_sources_sha16():
     return h.hexdigest()[:16]
 
 
-def accum_roofline(stats_list, n_sm, sm_mhz, peak_src, kernel="k_accum (spectrum accumulator)", traffic=None):
+TENSOR_FLOPS_PER_TERM = 24  # k_accum_diff_mma: a complex multiply-add per term as four real products of bf16
+# high/low parts, three each (hi*hi + hi*lo + lo*hi): 4 x 3 x 2 flops
+
+
+def accum_roofline(stats_list, n_sm, sm_mhz, peak_src, kernel="k_accum (spectrum accumulator)", traffic=None,
+                   only_specular=False):
     """FP32 roofline of the accumulator launches of the given simulate steps: 10 flops per (path, mic, bin)
-    term over the launches' device time, against 128 FP32 lanes x 2 x the SM clock per SM."""
-    acc_ms = sum(s.ms_accum_kernel for s in stats_list)
-    launches = sum(s.accum_launches for s in stats_list)
-    terms = sum(s.terms for s in stats_list)
+    term over the launches' device time, against 128 FP32 lanes x 2 x the SM clock per SM.  only_specular:
+    the specular launch alone (the diffraction launch then runs on the tensor cores, tensor_roofline)."""
+    if only_specular:
+        acc_ms = sum(s.ms_accum_specular for s in stats_list)
+        launches = sum(1 for s in stats_list if s.terms_specular > 0)
+        terms = sum(s.terms_specular for s in stats_list)
+    else:
+        acc_ms = sum(s.ms_accum_kernel for s in stats_list)
+        launches = sum(s.accum_launches for s in stats_list)
+        terms = sum(s.terms for s in stats_list)
     peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = FLOPS_PER_TERM * terms / (acc_ms / 1e3) / 1e12 if acc_ms > 0 else 0.0
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -64,6 +75,22 @@ def accum_roofline(stats_list, n_sm, sm_mhz, peak_src, kernel="k_accum (spectrum
             "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max SM clock, {peak_src})",
             "work": f"{FLOPS_PER_TERM} FP32 flops per (path, mic, bin) term, {terms / max(launches, 1):.3e} "
                     f"terms per launch", "ms_per_launch": acc_ms / max(launches, 1), "traffic": traffic}
+
+
+def tensor_roofline(stats_list, peaks, peak_src):
+    """bf16 tensor roofline of the diffraction accumulator on the tensor cores (k_accum_diff_mma): 24 flops
+    per (path, mic, bin) term over the launch's device time, against the measured bf16 dense rate."""
+    ms = sum(s.ms_accum_diffraction for s in stats_list)
+    terms = sum(s.terms_diffraction for s in stats_list)
+    launches = sum(1 for s in stats_list if s.terms_diffraction > 0)
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = TENSOR_FLOPS_PER_TERM * terms / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    return {"bound": "tensor", "kernel": "k_accum_diff_mma (diffraction accumulator, mma.sync bf16)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": f"bf16 dense, burst ({peak_src})",
+            "work": f"{TENSOR_FLOPS_PER_TERM} bf16 tensor flops per (path, mic, bin) term, "
+                    f"{terms / max(launches, 1):.3e} terms per launch", "ms_per_launch": ms / max(launches, 1),
+            "traffic": None}
 
 
 def e2e_simulate(st, ctx, sc, wl, params, n_steps):
@@ -807,6 +834,11 @@ def compact_line(d):
                       "step": c["step"], "l2": "flushed (256 MiB write)", "parallelism": c["parallelism"]}
     line["roofline"] = {"bound": rf["bound"], "kernel": rf["kernel"].split(" ")[0], "achieved": _r(rf["achieved"]),
                         "peak": _r(rf["peak"]), "unit": rf["unit"], "frac": _r(rf["frac"]), "traffic": rf["traffic"]}
+    rd = d.get("roofline_diffraction")
+    if rd:
+        line["roofline_diffraction"] = {"bound": rd["bound"], "kernel": rd["kernel"].split(" ")[0],
+                                        "achieved": _r(rd["achieved"]), "peak": _r(rd["peak"]), "unit": rd["unit"],
+                                        "frac": _r(rd["frac"], 4)}
     cb = d.get("cpu_baseline")
     if cb:
         line["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"],
@@ -931,7 +963,11 @@ def main():
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     traffic = ACCUM_TRAFFIC["bytes_per_launch"] if ACCUM_TRAFFIC["sources_sha16"] == accum_sources_sha16() else None
-    roofline = accum_roofline(st_list, n_sm, sm_mhz, peak_src, traffic=traffic)
+    tensor_diff = all(s.diffraction_tensor for s in st_list)
+    roofline = accum_roofline(st_list, n_sm, sm_mhz, peak_src, traffic=None if tensor_diff else traffic,
+                              kernel="k_accum (specular accumulator)" if tensor_diff else
+                              "k_accum (spectrum accumulator)", only_specular=tensor_diff)
+    roofline_diffraction = tensor_roofline(st_list, peaks, peak_src) if tensor_diff else None
 
     # ---- end to end through the C ABI with host buffers
     if world > 1:
@@ -997,7 +1033,8 @@ def main():
                          "diffraction_kept": s0.candidates_kept, "terms": s0.terms,
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
                          "ms_accumulate": s0.ms_accumulate},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "adjoint": adjoint,
+            "roofline": roofline, "roofline_diffraction": roofline_diffraction, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "adjoint": adjoint,
             "traversal": traversal, "signal": signal, "scene_update": scene_update, "batched": batched, "batched_directional": batched_dir,
             "vegetation": vegetation, "receiver_test_per_mic": per_mic, "emitters": emitters,
             "instances": instances,

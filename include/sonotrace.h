@@ -114,6 +114,11 @@ typedef struct st_stats {
     int64_t visits[4];          /* with ST_COUNT_VISITS=1: BVH nodes and triangles visited by closest-hit
                                    queries, then by any-hit queries (0 otherwise) */
     int64_t stack_restarts;     /* traversal queries that outgrew their stack and restarted from the root */
+    float ms_accum_specular;    /* device time of the specular accumulator launch, ms */
+    float ms_accum_diffraction; /* device time of the diffraction accumulator launch, ms */
+    int64_t terms_specular;     /* (path, microphone, bin) terms of the specular launch */
+    int64_t terms_diffraction;  /* ... of the diffraction launch */
+    int32_t diffraction_tensor; /* 1: the diffraction launch ran on the tensor cores (k_accum_diff_mma) */
 } st_stats;
 
 /* Fill a parameter block with the library defaults (every field; the caller owns the block). */

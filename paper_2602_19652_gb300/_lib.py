@@ -43,7 +43,9 @@ class Stats(C.Structure):
                 ("visible_records", I64), ("candidates", I64), ("candidates_kept", I64), ("terms", I64),
                 ("ms_trace", F32), ("ms_diffraction", F32), ("ms_accumulate", F32), ("ms_total", F32),
                 ("ms_accum_kernel", F32), ("accum_launches", I32), ("kernel_launches", I64),
-                ("visits", I64 * 4), ("stack_restarts", I64)]
+                ("visits", I64 * 4), ("stack_restarts", I64), ("ms_accum_specular", F32),
+                ("ms_accum_diffraction", F32), ("terms_specular", I64), ("terms_diffraction", I64),
+                ("diffraction_tensor", I32)]
 
 
 class Job(C.Structure):

@@ -31,6 +31,7 @@ UNITS = {
     "st_trace.cu": ["-fmad=false"],
     "st_batch.cu": ["-fmad=false"],
     "st_accum.cu": [],
+    "st_accum_mma.cu": [],
     "st_accum_narrow.cu": [],
     "st_adjoint.cu": [],
     "st_noalloc.cu": [],

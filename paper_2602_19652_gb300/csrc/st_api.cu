@@ -110,6 +110,7 @@ struct st_ctx {
     // last simulate parameters (for the adjoint)
     st_sim_params last_params;
     int32_t last_chunks_spec = 0, last_chunks_diff = 0;
+    DevBuf mat_off, mat_scr;  // diffraction paths by material (tensor-core accumulation)
     float last_fwd[3] = {1, 0, 0};
     bool count_visits = false;  // ST_COUNT_VISITS=1 in the environment: node/triangle visit counters
     st_tune tune{0, 0, 0, 0};   // launch shapes (st_autotune); 0 = default
@@ -360,7 +361,7 @@ st_status st_destroy(st_ctx* c) {
     for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->th_keys, &c->th_scr, &c->vs_keys, &c->vs_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
                       &c->st_d[2], &c->st_r, &c->st_prev, &c->q0, &c->q1, &c->counts, &c->queries, &c->flags, &c->R, &c->rec_tri,
                       &c->rec_p, &c->rec_d, &c->rec_r, &c->rec_los, &c->sflags, &c->sscan, &c->sidx, &c->scratch,
-                      &c->cand_tri, &c->cand_p, &c->keep, &c->dvis, &c->partial, &c->host_out, &c->tables.lk,
+                      &c->cand_tri, &c->cand_p, &c->keep, &c->dvis, &c->partial, &c->host_out, &c->mat_off, &c->mat_scr, &c->tables.lk,
                       &c->tables.g2, &c->tables.lid, &c->tables.qhi, &c->tables.qlo})
         release(*b);
     for (PathList* P : {&c->paths, &c->paths_diff})
@@ -911,8 +912,26 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
     }
     const int32_t chunks_spec =
         accum_chunks(NB, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb, c->tune.bins_per_thread);
+    // diffraction on the tensor cores when the per-bin factor depends on material and bin only
+    bool diff_mma = false;
+    {
+        AccumArgs probe{};
+        probe.kind = 1;
+        probe.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
+        probe.mic_tab = c->mic_nb > 0 ? ptr<float>(c->mic_tab) : nullptr;
+        probe.M = M;
+        probe.F = F;
+        probe.n_mat_tab = S.n_mat;
+        diff_mma = K > 0 && diffraction_mma_applies(probe);
+    }
     const int32_t chunks_diff =
-        accum_chunks(K, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb, c->tune.bins_per_thread);
+        diff_mma ? diffraction_mma_chunks(K, M, F, S.n_mat)
+                 : accum_chunks(K, M, F, S.n_mat, c->mic_nb, c->tune.mic_pairs_per_cta, c->tune.smem_kb,
+                                c->tune.bins_per_thread);
+    if (diff_mma) {
+        CKC(c, grow(c->mat_off, (size_t)(S.n_mat + 1) * 4), "alloc");
+        CKC(c, grow(c->mat_scr, material_order_scratch(K)), "alloc");
+    }
     const int32_t chunks = std::max(chunks_spec, chunks_diff);
     CKC(c, grow(c->partial, (size_t)chunks * M * F * 8), "alloc");
 
@@ -1161,6 +1180,10 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
             "compact");
         ga.count = cnt + 3;
         ga.out = &c->paths_diff;
+        if (diff_mma)  // path list grouped by material (stable: within a material the compaction order)
+            CKC(c, material_order(cnt + 3, K, ptr<int32_t>(c->cand_tri), ptr<int32_t>(S.tri_mat), S.n_mat,
+                                  ptr<uint32_t>(c->sidx), ptr<uint32_t>(c->mat_off), c->mat_scr.p, s),
+                "material order");
         CKC(c, gather_diffraction(ga, s), "gather");
         AccumArgs x = aa;
         x.kind = 1;
@@ -1169,7 +1192,10 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
         set_paths(x, c->paths_diff);
         x.n_chunks = chunks_diff;
         if (stats) CKC(c, cudaEventRecord(c->ev[6], s), "event");
-        CKC(c, accumulate(x, s), "accumulate diffraction");
+        if (diff_mma)
+            CKC(c, accumulate_diffraction_mma(x, ptr<uint32_t>(c->mat_off), s), "accumulate diffraction");
+        else
+            CKC(c, accumulate(x, s), "accumulate diffraction");
         if (stats) CKC(c, cudaEventRecord(c->ev[7], s), "event");
         n_accum += 2;
         CKC(c, reduce_partials(ptr<float2>(c->partial), chunks_diff, MF, out + MF, s), "reduce");
@@ -1268,14 +1294,19 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
         if (n_accum & 1) {
             cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
             stats->ms_accum_kernel += ms;
+            stats->ms_accum_specular = ms;
             stats->accum_launches++;
         }
         if (n_accum & 2) {
             cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]);
             stats->ms_accum_kernel += ms;
+            stats->ms_accum_diffraction = ms;
             stats->accum_launches++;
         }
-        stats->terms = ((int64_t)((n_accum & 1) ? h[2] : 0) + (int64_t)((n_accum & 2) ? h[3] : 0)) * M * F;
+        stats->terms_specular = (int64_t)((n_accum & 1) ? h[2] : 0) * M * F;
+        stats->terms_diffraction = (int64_t)((n_accum & 2) ? h[3] : 0) * M * F;
+        stats->terms = stats->terms_specular + stats->terms_diffraction;
+        stats->diffraction_tensor = diff_mma ? 1 : 0;
         if (fl & kFlagBadTree) return fail(c, ST_ERR_CUDA, "malformed BVH: traversal exceeded the node count");
         if (fl & kFlagCheck) return fail(c, ST_ERR_CUDA, "a bounds check of the checked build failed");
     }

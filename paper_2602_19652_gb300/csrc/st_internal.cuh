@@ -372,6 +372,15 @@ cudaError_t ray_directions(int kind, int64_t n, float* out, DevBuf& scratch, cud
 cudaError_t signal_response(const float2* S, int n_comp, int M, int F, double f_lo, double f_hi, double fs,
                             int n_samples, const float* window, const float* call, int call_len, int per_comp,
                             float2* E_buf, float2* G_buf, float* out, cudaStream_t s);
+// diffraction accumulation on the tensor cores (st_accum_mma.cu): omni emitter and receivers, paths grouped
+// by material (material_order sorts the compacted candidate indices and writes the groups' offsets
+// mat_off [n_mat + 1] on the device)
+bool diffraction_mma_applies(const AccumArgs& a);
+int32_t diffraction_mma_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat);
+size_t material_order_scratch(int64_t cap);
+cudaError_t material_order(const uint32_t* count, int64_t cap, const int32_t* cand_tri, const int32_t* tri_mat,
+                           int n_mat, uint32_t* idx, uint32_t* mat_off, void* scratch, cudaStream_t s);
+cudaError_t accumulate_diffraction_mma(const AccumArgs& a, const uint32_t* mat_off, cudaStream_t s);
 // narrow receiver arrays (one microphone pair): a separate accumulator kernel
 bool narrow_accum(int32_t M);
 int32_t narrow_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb);
