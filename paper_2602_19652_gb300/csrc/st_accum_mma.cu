@@ -47,9 +47,10 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
                  : "r"(addr));
 }
 
-// D += A B: m16n8k16, bf16 inputs, float32 accumulation
+// D += A B: m16n8k16, bf16 inputs, float32 accumulation (registers only: not volatile, so that the compiler
+// interleaves products on independent accumulators)
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
         "{%0, %1, %2, %3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -168,18 +169,20 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
                 const float a32 = ex2(rh * (a.atm2_step * 32.0f));
                 w32 = make_float2(a32 * c, a32 * s);
             }
-            // U row: z (W^32)^k1, k1 = 0 .. 15, parts re hi, re lo, im hi, im lo
+            // U row: z (W^32)^k1, k1 = 0 .. 15, parts re hi, re lo, im hi, im lo (even and odd k1 as two
+            // independent chains of step W^64)
             uint32_t* ur = reinterpret_cast<uint32_t*>(Us + (((size_t)ml * 4) * kMmaPaths + p) * kURow);
             const size_t upart = (size_t)kMmaPaths * kURow / 2;  // words between parts
+            const float2 w64 = cmul(w32, w32);
+            float2 zo = cmul(z, w32);
 #pragma unroll
             for (int j = 0; j < kK1 / 8; ++j) {
                 uint32_t rh4[4], rl4[4], ih4[4], il4[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float2 u0 = z;
-                    z = cmul(z, w32);
-                    const float2 u1 = z;
-                    z = cmul(z, w32);
+                    const float2 u0 = z, u1 = zo;
+                    z = cmul(z, w64);
+                    zo = cmul(zo, w64);
                     split2(u0.x, u1.x, rh4[e], rl4[e]);
                     split2(u0.y, u1.y, ih4[e], il4[e]);
                 }
@@ -191,18 +194,24 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
             // V row: W^k2, k2 = 0 .. 31 (zero for an invalid path or microphone)
             uint32_t* vr = reinterpret_cast<uint32_t*>(Vs + (((size_t)ml * 4) * kMmaPaths + p) * kVRow);
             const size_t vpart = (size_t)kMmaPaths * kVRow / 2;
-            float2 v = (pq[p] && m < a.M) ? make_float2(1.0f, 0.0f) : make_float2(0.0f, 0.0f);
+            // (four independent chains of step W^4: k2 = 4 e + c)
+            float2 vc[4];
+            vc[0] = (pq[p] && m < a.M) ? make_float2(1.0f, 0.0f) : make_float2(0.0f, 0.0f);
+            vc[1] = cmul(vc[0], w1);
+            vc[2] = cmul(vc[1], w1);
+            vc[3] = cmul(vc[2], w1);
+            const float2 w4 = cmul(cmul(w1, w1), cmul(w1, w1));
 #pragma unroll
             for (int j = 0; j < kK2 / 8; ++j) {
                 uint32_t rh4[4], rl4[4], ih4[4], il4[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float2 v0 = v;
-                    v = cmul(v, w1);
-                    const float2 v1 = v;
-                    v = cmul(v, w1);
-                    split2(v0.x, v1.x, rh4[e], rl4[e]);
-                    split2(v0.y, v1.y, ih4[e], il4[e]);
+                for (int e2 = 0; e2 < 2; ++e2) {
+                    split2(vc[0].x, vc[1].x, rh4[2 * e2], rl4[2 * e2]);
+                    split2(vc[0].y, vc[1].y, ih4[2 * e2], il4[2 * e2]);
+                    split2(vc[2].x, vc[3].x, rh4[2 * e2 + 1], rl4[2 * e2 + 1]);
+                    split2(vc[2].y, vc[3].y, ih4[2 * e2 + 1], il4[2 * e2 + 1]);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) vc[c] = cmul(vc[c], w4);
                 }
                 reinterpret_cast<uint4*>(vr + 0 * vpart)[j] = make_uint4(rh4[0], rh4[1], rh4[2], rh4[3]);
                 reinterpret_cast<uint4*>(vr + 1 * vpart)[j] = make_uint4(rl4[0], rl4[1], rl4[2], rl4[3]);
@@ -235,37 +244,41 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
                     nI[1][e] = A[3][e] ^ 0x80008000u;
                 }
                 const int pb = ks * 16 + rr + (mi & 1) * 8;
+                // B fragments (16 paths x 8 k2) of the four n-blocks, from V rows [path][k2]: Bf[part][nb][0..1]
+                uint32_t Bf[4][4][2];
 #pragma unroll
                 for (int nb2 = 0; nb2 < 2; ++nb2) {
-                    // B fragments (16 paths x 8 k2) of n-blocks 2 nb2 and 2 nb2 + 1, from V rows [path][k2]
-                    uint32_t B[4][4];
                     const int cb = nb2 * 16 + (mi >> 1) * 8;
 #pragma unroll
                     for (int part = 0; part < 4; ++part)
-                        ldsm_x4_t(smem_u32(Vw + ((size_t)part * kMmaPaths + pb) * kVRow + cb), B[part][0], B[part][1],
-                                  B[part][2], B[part][3]);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int nb = 2 * nb2 + h;
-                        const uint32_t vrh0 = B[0][2 * h], vrh1 = B[0][2 * h + 1], vrl0 = B[1][2 * h],
-                                       vrl1 = B[1][2 * h + 1], vih0 = B[2][2 * h], vih1 = B[2][2 * h + 1],
-                                       vil0 = B[3][2 * h], vil1 = B[3][2 * h + 1];
-                        // real: Ur Vr - Ui Vi
-                        mma_bf16(Tr[nb], A[0], vrh0, vrh1);
-                        mma_bf16(Tr[nb], A[0], vrl0, vrl1);
-                        mma_bf16(Tr[nb], A[1], vrh0, vrh1);
-                        mma_bf16(Tr[nb], nI[0], vih0, vih1);
-                        mma_bf16(Tr[nb], nI[0], vil0, vil1);
-                        mma_bf16(Tr[nb], nI[1], vih0, vih1);
-                        // imaginary: Ur Vi + Ui Vr
-                        mma_bf16(Ti[nb], A[0], vih0, vih1);
-                        mma_bf16(Ti[nb], A[0], vil0, vil1);
-                        mma_bf16(Ti[nb], A[1], vih0, vih1);
-                        mma_bf16(Ti[nb], A[2], vrh0, vrh1);
-                        mma_bf16(Ti[nb], A[2], vrl0, vrl1);
-                        mma_bf16(Ti[nb], A[3], vrh0, vrh1);
-                    }
+                        ldsm_x4_t(smem_u32(Vw + ((size_t)part * kMmaPaths + pb) * kVRow + cb), Bf[part][2 * nb2][0],
+                                  Bf[part][2 * nb2][1], Bf[part][2 * nb2 + 1][0], Bf[part][2 * nb2 + 1][1]);
                 }
+                // real: Ur Vr - Ui Vi; imaginary: Ur Vi + Ui Vr -- each product over the four n-blocks in turn
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Tr[nb], A[0], Bf[0][nb][0], Bf[0][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Ti[nb], A[0], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Tr[nb], A[0], Bf[1][nb][0], Bf[1][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Ti[nb], A[0], Bf[3][nb][0], Bf[3][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Tr[nb], A[1], Bf[0][nb][0], Bf[0][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Ti[nb], A[1], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Tr[nb], nI[0], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Ti[nb], A[2], Bf[0][nb][0], Bf[0][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Tr[nb], nI[0], Bf[3][nb][0], Bf[3][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Ti[nb], A[2], Bf[1][nb][0], Bf[1][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Tr[nb], nI[1], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) mma_bf16(Ti[nb], A[3], Bf[0][nb][0], Bf[0][nb][1]);
             }
         }
     }
@@ -280,6 +293,314 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
                 const int k = kb + kK2 * (g + 8 * (i >> 1)) + 8 * nb + 2 * t4 + (i & 1);
                 if (k < a.F) out[k] = make_float2(Sr[nb][i], Si[nb][i]);
             }
+    }
+}
+
+// ---------------------------------------------------------------- the diffraction adjoint (positions)
+// The reverse pass needs per (path, microphone) C0 = sum_k c_k z_k and C1 = sum_k (k - kb) c_k z_k with
+// c_k = conj(G_k) E_q[k] (G: dL/dS of the diffraction component, E_q: the material's factor).  With
+// z_k = z0 (W^32)^k1 W^k2 (k - kb = 32 k1 + k2):
+//     C0 = z0 sum_k1 (W^32)^k1 Y[k1],                 Y[k1]  = sum_k2 W^k2 c[k1][k2]
+//     C1 = z0 sum_k1 (W^32)^k1 (32 k1 Y[k1] + Y'[k1]), Y'[k1] = sum_k2 W^k2 k2 c[k1][k2]
+// so for the paths of one material and one microphone [Y | Y'] = V (P x 32) times B (32 x 32) with
+// B[k2][k1] = c[k1][k2] and B[k2][16 + k1] = k2 c[k1][k2]: the gradient is the operand shared by all paths,
+// rebuilt when the material changes.  Per tile each warp multiplies its microphone's V by its B on the tensor
+// cores (bf16 high and low parts as in the forward), then finishes C0 and C1 with the 16-term sums above
+// (float32, the powers (W^32)^k1 kept from the tile's producer), forms dL/dr = Re(D0 C0 + D1 C1) and adds
+// dL/dr times d r / d m and d r / d s to its microphone and emitter gradient registers.
+constexpr int kBRow = 40;  // bf16 per B row: 32 k2 + 8
+constexpr size_t kAdjV = (size_t)kMmaMics * 4 * kMmaPaths * kVRow * 2;
+constexpr size_t kAdjB = (size_t)kMmaMics * 4 * 32 * kBRow * 2;
+constexpr size_t kAdjU = (size_t)kMmaMics * kMmaPaths * kK1 * 8;
+constexpr size_t kAdjPM = (size_t)kMmaMics * kMmaPaths * 8 * 4;
+constexpr size_t kAdjSmem = kAdjV + kAdjB + kAdjU + kAdjPM + kMmaPaths * 8 * 4 + kMmaPaths * 4 + kMmaMics * 4 * 4;
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const AccumArgs a, const AdjointArgs j,
+                                                                      const uint32_t* mat_off, int n_mb, int n_bb) {
+    extern __shared__ float4 smem4[];
+    char* base = reinterpret_cast<char*>(smem4);
+    __nv_bfloat16* Vs = reinterpret_cast<__nv_bfloat16*>(base);                 // [mic][part][path][kVRow]
+    __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + kAdjV);         // [mic][part][n][kBRow]
+    float2* Up = reinterpret_cast<float2*>(base + kAdjV + kAdjB);               // [mic][path][16]: (W^32)^k1
+    float* pm = reinterpret_cast<float*>(base + kAdjV + kAdjB + kAdjU);         // [mic][path][8]
+    float* pd = pm + (size_t)kMmaMics * kMmaPaths * 8;                          // [path][8]
+    int* pq = reinterpret_cast<int*>(pd + kMmaPaths * 8);                       // [path] valid
+    float* ered = reinterpret_cast<float*>(pq + kMmaPaths);                     // [mic][4] emitter sums
+
+    const int mb = blockIdx.x % n_mb, bb = blockIdx.x / n_mb;
+    const int mic0 = mb * kMmaMics, kb = bb * kMmaBins;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int n_mat = a.n_mat_tab;
+    const int m_w = mic0 + warp;
+
+    int64_t n_tiles = 0;
+    for (int q = 0; q < n_mat; ++q) n_tiles += ((int64_t)mat_off[q + 1] - mat_off[q] + kMmaPaths - 1) / kMmaPaths;
+    const int64_t per = (n_tiles + a.n_chunks - 1) / a.n_chunks;
+    const int64_t t0 = (int64_t)blockIdx.y * per, t1 = min(n_tiles, t0 + per);
+
+    // dL/dr = Re(D0 C0 + D1 C1): D0 = -2/r - a(kb) + j w(kb), D1 = -a_step + j w_step
+    const float akb = j.a_0 + j.a_step * (float)kb, wkb = j.w_0 + j.w_step * (float)kb;
+    float gmx = 0.0f, gmy = 0.0f, gmz = 0.0f, gex = 0.0f, gey = 0.0f, gez = 0.0f;
+    int q_cur = -1;
+    const int kq = min(kb, a.F - 1);
+    const ff qk{a.qhi[kq], a.qlo[kq]};
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const MTile T = tile_at(mat_off, n_mat, tile);
+        __syncthreads();  // the previous tile's epilogue has read the path data and the per-(path, mic) values
+        if (tid < kMmaPaths) {
+            const bool ok = tid < T.n;
+            const int64_t i = T.first + tid;
+            pq[tid] = ok ? 1 : 0;
+            float* d = pd + tid * 8;
+            d[0] = ok ? a.px[i] : 0.0f;
+            d[1] = ok ? a.py[i] : 0.0f;
+            d[2] = ok ? a.pz[i] : 0.0f;
+            d[3] = ok ? a.rhi[i] : 1.0f;
+            d[4] = ok ? a.rlo[i] : 0.0f;
+            // d r / d s = -unit(o - s) (the emitter-to-point length is r hi + r lo)
+            const float iv = 1.0f / d[3];
+            d[5] = -((d[0] - j.s[0]) * iv);
+            d[6] = -((d[1] - j.s[1]) * iv);
+            d[7] = -((d[2] - j.s[2]) * iv);
+        }
+        if (T.q != q_cur) {
+            // B of the four microphones for the new material: rows n < 16 c[n][k2], rows 16 + n k2 c[n][k2]
+            for (int e = tid; e < kMmaMics * kK1 * kK2; e += blockDim.x) {
+                const int ml = e / (kK1 * kK2), rem = e - ml * kK1 * kK2, k1 = rem / kK2, k2 = rem - k1 * kK2;
+                const int m = mic0 + ml, k = kb + kK2 * k1 + k2;
+                float cr = 0.0f, ci = 0.0f;
+                if (m < a.M && k < a.F) {
+                    const float2 G = j.G[(int64_t)m * a.F + k];
+                    const float E = ex2(__ldg(a.lid + (int64_t)T.q * a.F + k));
+                    cr = G.x * E;  // conj(G) E
+                    ci = -G.y * E;
+                }
+                const float cw[2][2] = {{cr, ci}, {(float)k2 * cr, (float)k2 * ci}};
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int n = half * kK1 + k1;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const __nv_bfloat16 h = __float2bfloat16_rn(cw[half][c]);
+                        const __nv_bfloat16 l = __float2bfloat16_rn(cw[half][c] - __bfloat162float(h));
+                        Bs[(((size_t)ml * 4 + 2 * c) * 32 + n) * kBRow + k2] = h;
+                        Bs[(((size_t)ml * 4 + 2 * c + 1) * 32 + n) * kBRow + k2] = l;
+                    }
+                }
+            }
+            q_cur = T.q;
+        }
+        __syncthreads();
+        // per (path, microphone): V row, the powers (W^32)^k1, z0, D0's real part and d r / d m
+        {
+            const int p = tid % kMmaPaths, ml = tid / kMmaPaths, m = mic0 + ml;
+            float2 z = make_float2(0.0f, 0.0f), w1 = make_float2(0.0f, 0.0f), w32 = make_float2(0.0f, 0.0f);
+            float* o = pm + ((size_t)ml * kMmaPaths + p) * 8;
+            const bool ok = pq[p] && m < a.M;
+            if (ok) {
+                const float* d = pd + p * 8;
+                const float mx = a.mics[3 * m], my = a.mics[3 * m + 1], mz = a.mics[3 * m + 2];
+                const ff dist = dist_ff(mx, my, mz, d[0], d[1], d[2]);
+                const ff r = ff_add(ff{d[3], d[4]}, dist);
+                const float rh = r.hi;
+                const float L0 = -2.0f * log2_ff(r) + rh * (a.atm2_0 + a.atm2_step * (float)kb);
+                float s, c;
+                sincospif(2.0f * ff_frac(ff_mul(r, qk)), &s, &c);
+                const float A0 = ex2(L0);
+                z = make_float2(A0 * c, A0 * s);
+                sincospif(2.0f * ff_frac(ff_mul(r, ff{a.dq_hi, a.dq_lo})), &s, &c);
+                const float a1 = ex2(rh * a.atm2_step);
+                w1 = make_float2(a1 * c, a1 * s);
+                sincospif(2.0f * ff_frac(ff_mul(r, ff{a.dq_hi * 32.0f, a.dq_lo * 32.0f})), &s, &c);
+                const float a32 = ex2(rh * (a.atm2_step * 32.0f));
+                w32 = make_float2(a32 * c, a32 * s);
+                const float inv = 1.0f / dist.hi;
+                o[0] = z.x;
+                o[1] = z.y;
+                o[2] = -2.0f / rh - akb;
+                o[3] = (mx - d[0]) * inv;  // d r / d m = unit(m - P)
+                o[4] = (my - d[1]) * inv;
+                o[5] = (mz - d[2]) * inv;
+                o[6] = 1.0f;
+            } else {
+                o[0] = o[1] = o[2] = o[3] = o[4] = o[5] = o[6] = 0.0f;
+            }
+            float2* up = Up + ((size_t)ml * kMmaPaths + p) * kK1;
+            float2 ue = make_float2(1.0f, 0.0f), uo = w32;
+            const float2 w64 = cmul(w32, w32);
+#pragma unroll
+            for (int k1 = 0; k1 < kK1; k1 += 2) {
+                reinterpret_cast<float4*>(up)[k1 / 2] = make_float4(ue.x, ue.y, uo.x, uo.y);
+                ue = cmul(ue, w64);
+                uo = cmul(uo, w64);
+            }
+            uint32_t* vr = reinterpret_cast<uint32_t*>(Vs + (((size_t)ml * 4) * kMmaPaths + p) * kVRow);
+            const size_t vpart = (size_t)kMmaPaths * kVRow / 2;
+            float2 vc[4];
+            vc[0] = ok ? make_float2(1.0f, 0.0f) : make_float2(0.0f, 0.0f);
+            vc[1] = cmul(vc[0], w1);
+            vc[2] = cmul(vc[1], w1);
+            vc[3] = cmul(vc[2], w1);
+            const float2 w4 = cmul(cmul(w1, w1), cmul(w1, w1));
+#pragma unroll
+            for (int jj = 0; jj < kK2 / 8; ++jj) {
+                uint32_t rh4[4], rl4[4], ih4[4], il4[4];
+#pragma unroll
+                for (int e2 = 0; e2 < 2; ++e2) {
+                    split2(vc[0].x, vc[1].x, rh4[2 * e2], rl4[2 * e2]);
+                    split2(vc[0].y, vc[1].y, ih4[2 * e2], il4[2 * e2]);
+                    split2(vc[2].x, vc[3].x, rh4[2 * e2 + 1], rl4[2 * e2 + 1]);
+                    split2(vc[2].y, vc[3].y, ih4[2 * e2 + 1], il4[2 * e2 + 1]);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) vc[c] = cmul(vc[c], w4);
+                }
+                reinterpret_cast<uint4*>(vr + 0 * vpart)[jj] = make_uint4(rh4[0], rh4[1], rh4[2], rh4[3]);
+                reinterpret_cast<uint4*>(vr + 1 * vpart)[jj] = make_uint4(rl4[0], rl4[1], rl4[2], rl4[3]);
+                reinterpret_cast<uint4*>(vr + 2 * vpart)[jj] = make_uint4(ih4[0], ih4[1], ih4[2], ih4[3]);
+                reinterpret_cast<uint4*>(vr + 3 * vpart)[jj] = make_uint4(il4[0], il4[1], il4[2], il4[3]);
+            }
+        }
+        __syncthreads();
+        if (m_w < a.M) {
+            const __nv_bfloat16* Vw = Vs + (size_t)warp * 4 * kMmaPaths * kVRow;
+            const __nv_bfloat16* Bw = Bs + (size_t)warp * 4 * 32 * kBRow;
+            const int mi = lane >> 3, rr = lane & 7;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                // [Y | Y'] rows of paths 16 mt .. 16 mt + 15: fragment element i of n-block nb is
+                // (path 16 mt + g + 8 (i >> 1), column 8 nb + 2 t + (i & 1))
+                float Yr[4][4], Yi[4][4];
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) Yr[nb][i] = Yi[nb][i] = 0.0f;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    uint32_t A[4][4];
+                    const int pa = 16 * mt + rr + (mi & 1) * 8, ca = 16 * ks + (mi >> 1) * 8;
+#pragma unroll
+                    for (int part = 0; part < 4; ++part)
+                        ldsm_x4(smem_u32(Vw + ((size_t)part * kMmaPaths + pa) * kVRow + ca), A[part][0], A[part][1],
+                                A[part][2], A[part][3]);
+                    uint32_t nI[2][4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        nI[0][e] = A[2][e] ^ 0x80008000u;
+                        nI[1][e] = A[3][e] ^ 0x80008000u;
+                    }
+                    uint32_t Bf[4][4][2];  // [part][n-block][reg]
+#pragma unroll
+                    for (int nb2 = 0; nb2 < 2; ++nb2) {
+                        const int nrow = 16 * nb2 + rr + (mi >> 1) * 8, cb = 16 * ks + (mi & 1) * 8;
+#pragma unroll
+                        for (int part = 0; part < 4; ++part)
+                            ldsm_x4(smem_u32(Bw + ((size_t)part * 32 + nrow) * kBRow + cb), Bf[part][2 * nb2][0],
+                                    Bf[part][2 * nb2][1], Bf[part][2 * nb2 + 1][0], Bf[part][2 * nb2 + 1][1]);
+                    }
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yr[nb], A[0], Bf[0][nb][0], Bf[0][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yi[nb], A[0], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yr[nb], A[0], Bf[1][nb][0], Bf[1][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yi[nb], A[0], Bf[3][nb][0], Bf[3][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yr[nb], A[1], Bf[0][nb][0], Bf[0][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yi[nb], A[1], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yr[nb], nI[0], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yi[nb], A[2], Bf[0][nb][0], Bf[0][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yr[nb], nI[0], Bf[3][nb][0], Bf[3][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yi[nb], A[2], Bf[1][nb][0], Bf[1][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yr[nb], nI[1], Bf[2][nb][0], Bf[2][nb][1]);
+#pragma unroll
+                    for (int nb = 0; nb < 4; ++nb) mma_bf16(Yi[nb], A[3], Bf[0][nb][0], Bf[0][nb][1]);
+                }
+                // C0 and C1 of the two paths of this thread (rows g and g + 8 of the m-tile): this lane's k1
+                // are 2 t, 2 t + 1 (n-block 0) and 8 + 2 t, 9 + 2 t (n-block 1); Y' in n-blocks 2 and 3
+#pragma unroll
+                for (int hp = 0; hp < 2; ++hp) {
+                    const int p = 16 * mt + g + 8 * hp;
+                    const float2* up = Up + ((size_t)warp * kMmaPaths + p) * kK1;
+                    float s0r = 0.0f, s0i = 0.0f, s1r = 0.0f, s1i = 0.0f;
+#pragma unroll
+                    for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const int i = 2 * hp + c, k1 = 8 * nb + 2 * t4 + c;
+                            const float2 w = up[k1];
+                            const float yr = Yr[nb][i], yi = Yi[nb][i];
+                            const float xr = 32.0f * (float)k1 * yr + Yr[nb + 2][i];
+                            const float xi = 32.0f * (float)k1 * yi + Yi[nb + 2][i];
+                            s0r += w.x * yr - w.y * yi;
+                            s0i += w.x * yi + w.y * yr;
+                            s1r += w.x * xr - w.y * xi;
+                            s1i += w.x * xi + w.y * xr;
+                        }
+#pragma unroll
+                    for (int o = 1; o <= 2; o <<= 1) {
+                        s0r += __shfl_xor_sync(0xffffffffu, s0r, o);
+                        s0i += __shfl_xor_sync(0xffffffffu, s0i, o);
+                        s1r += __shfl_xor_sync(0xffffffffu, s1r, o);
+                        s1i += __shfl_xor_sync(0xffffffffu, s1i, o);
+                    }
+                    const float* q = pm + ((size_t)warp * kMmaPaths + p) * 8;
+                    if (t4 == 0 && q[6] != 0.0f) {
+                        const float zr = q[0], zi = q[1];
+                        const float c0r = zr * s0r - zi * s0i, c0i = zr * s0i + zi * s0r;
+                        const float c1r = zr * s1r - zi * s1i, c1i = zr * s1i + zi * s1r;
+                        const float dl = q[2] * c0r - wkb * c0i - j.a_step * c1r - j.w_step * c1i;
+                        gmx += dl * q[3];
+                        gmy += dl * q[4];
+                        gmz += dl * q[5];
+                        const float* d = pd + p * 8;
+                        gex += dl * d[5];
+                        gey += dl * d[6];
+                        gez += dl * d[7];
+                    }
+                }
+            }
+        }
+    }
+    // the warp's sums (lanes with t = 0 hold them), in a fixed order
+#pragma unroll
+    for (int o = 4; o <= 16; o <<= 1) {
+        gmx += __shfl_xor_sync(0xffffffffu, gmx, o);
+        gmy += __shfl_xor_sync(0xffffffffu, gmy, o);
+        gmz += __shfl_xor_sync(0xffffffffu, gmz, o);
+        gex += __shfl_xor_sync(0xffffffffu, gex, o);
+        gey += __shfl_xor_sync(0xffffffffu, gey, o);
+        gez += __shfl_xor_sync(0xffffffffu, gez, o);
+    }
+    if (lane == 0) {
+        if (m_w < a.M) {
+            float* o = j.mic_part + ((size_t)(blockIdx.y * n_bb + bb) * a.M + m_w) * 3;
+            o[0] = gmx;
+            o[1] = gmy;
+            o[2] = gmz;
+        }
+        ered[warp * 4 + 0] = gex;
+        ered[warp * 4 + 1] = gey;
+        ered[warp * 4 + 2] = gez;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float acc = 0.0f;
+        for (int w = 0; w < kMmaMics; ++w) acc += ered[w * 4 + tid];
+        j.emit_part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 3 + tid] = acc;
     }
 }
 
@@ -340,6 +661,28 @@ cudaError_t material_order(const uint32_t* count, int64_t cap, const int32_t* ca
     if ((e = radix_sort_u64(keys, idx, cap, 9, sort_scr, s)) != cudaSuccess) return e;  // stable
     note_launch();
     k_mat_offsets<<<(n_mat + 1 + 127) / 128, 128, 0, s>>>(keys, count, n_mat, mat_off);
+    return cudaGetLastError();
+}
+
+void adjoint_diffraction_mma_shape(int32_t M, int32_t F, int32_t* n_mb, int32_t* n_bb) {
+    *n_mb = (M + kMmaMics - 1) / kMmaMics;
+    *n_bb = (F + kMmaBins - 1) / kMmaBins;
+}
+
+cudaError_t adjoint_diffraction_mma(const AccumArgs& a, const AdjointArgs& j, const uint32_t* mat_off,
+                                    cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_adjoint_diff_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int32_t n_mb, n_bb;
+    adjoint_diffraction_mma_shape(a.M, a.F, &n_mb, &n_bb);
+    dim3 grid((unsigned)(n_mb * n_bb), (unsigned)a.n_chunks);
+    note_launch();
+    k_adjoint_diff_mma<<<grid, kMmaMics * 32, kAdjSmem, s>>>(a, j, mat_off, n_mb, n_bb);
     return cudaGetLastError();
 }
 

@@ -111,6 +111,7 @@ struct st_ctx {
     st_sim_params last_params;
     int32_t last_chunks_spec = 0, last_chunks_diff = 0;
     DevBuf mat_off, mat_scr;  // diffraction paths by material (tensor-core accumulation)
+    bool last_diff_mma = false;  // the last simulate's diffraction list is in material order (mat_off valid)
     float last_fwd[3] = {1, 0, 0};
     bool count_visits = false;  // ST_COUNT_VISITS=1 in the environment: node/triangle visit counters
     st_tune tune{0, 0, 0, 0};   // launch shapes (st_autotune); 0 = default
@@ -1259,6 +1260,7 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
     c->last_fwd[1] = fwd[1];
     c->last_fwd[2] = fwd[2];
     c->last_chunks_diff = chunks_diff;
+    c->last_diff_mma = diff_mma;
     c->has_last = true;
 
     // device-side error flags are checked whenever the caller synchronises through stats
@@ -1461,10 +1463,15 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         return (int32_t)std::max<int64_t>(1, std::min<int64_t>(std::max(152 * 2 / ctas_, 1), (tiles + 7) / 8));
     };
     const int32_t chunks = chunks_for(g, c->last_N * c->last_B);
-    const int32_t chunks_d = chunks_for(gd, c->last_K);
+    // diffraction on the tensor cores when the forward put its paths in material order
+    const bool diff_mma = c->last_diff_mma && c->last_K > 0;
+    int32_t dm_mb = 0, dm_bb = 0;
+    adjoint_diffraction_mma_shape(M, F, &dm_mb, &dm_bb);
+    const int32_t chunks_d = diff_mma ? diffraction_mma_chunks(c->last_K, M, F, T.n_mat) : chunks_for(gd, c->last_K);
     const int ctas = g.n_mb * g.n_bb;
     const int spec_mic_slices = chunks * g.n_bb, spec_emit_slices = chunks * ctas;
-    const int diff_mic_slices = chunks_d * gd.n_bb, diff_emit_slices = chunks_d * gd.n_mb * gd.n_bb;
+    const int diff_mic_slices = chunks_d * (diff_mma ? dm_bb : gd.n_bb);
+    const int diff_emit_slices = chunks_d * (diff_mma ? dm_mb * dm_bb : gd.n_mb * gd.n_bb);
     const int mic_slices = spec_mic_slices + diff_mic_slices + 1;     // specular, diffraction, direct
     const int emit_slices = spec_emit_slices + diff_emit_slices + M;  // direct: one slice per microphone
     CKC(c, grow(c->adj_v, (size_t)chunks * g.n_mb * 4 * F * 4), "alloc");
@@ -1573,7 +1580,10 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         jj.v_part = ptr<float>(c->adj_v);
         jj.mic_part = micp + (size_t)spec_mic_slices * M * 3;
         jj.emit_part = emitp + (size_t)spec_emit_slices * 3;
-        CKC(c, adjoint_launch(x, jj, gd, s), "adjoint diffraction");
+        if (diff_mma)
+            CKC(c, adjoint_diffraction_mma(x, jj, ptr<uint32_t>(c->mat_off), s), "adjoint diffraction");
+        else
+            CKC(c, adjoint_launch(x, jj, gd, s), "adjoint diffraction");
     }
     // ---- direct path
     if (want_pos && (p.components & ST_COMP_DIRECT)) {

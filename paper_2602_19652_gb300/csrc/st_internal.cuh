@@ -381,6 +381,12 @@ size_t material_order_scratch(int64_t cap);
 cudaError_t material_order(const uint32_t* count, int64_t cap, const int32_t* cand_tri, const int32_t* tri_mat,
                            int n_mat, uint32_t* idx, uint32_t* mat_off, void* scratch, cudaStream_t s);
 cudaError_t accumulate_diffraction_mma(const AccumArgs& a, const uint32_t* mat_off, cudaStream_t s);
+struct AdjointArgs;
+// the diffraction adjoint's position gradients on the tensor cores (same path order and chunking as the
+// forward); its CTA grid: n_mb microphone blocks x n_bb bin blocks per chunk
+void adjoint_diffraction_mma_shape(int32_t M, int32_t F, int32_t* n_mb, int32_t* n_bb);
+cudaError_t adjoint_diffraction_mma(const AccumArgs& a, const AdjointArgs& j, const uint32_t* mat_off,
+                                    cudaStream_t s);
 // narrow receiver arrays (one microphone pair): a separate accumulator kernel
 bool narrow_accum(int32_t M);
 int32_t narrow_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, int32_t dir_nb);
