@@ -311,8 +311,12 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
 constexpr int kBRow = 40;  // bf16 per B row: 32 k2 + 8
 constexpr size_t kAdjV = (size_t)kMmaMics * 4 * kMmaPaths * kVRow * 2;
 constexpr size_t kAdjB = (size_t)kMmaMics * 4 * 32 * kBRow * 2;
-constexpr size_t kAdjU = (size_t)kMmaMics * kMmaPaths * kK1 * 8;
-constexpr size_t kAdjPM = (size_t)kMmaMics * kMmaPaths * 8 * 4;
+// per-path rows of the epilogue's operands, padded against bank conflicts: the lanes of a quad read one path,
+// eight paths at once
+constexpr int kUpRow = kK1 + 1;  // float2 per (W^32)^k1 row
+constexpr int kPmRow = 9;        // floats per (path, microphone) record
+constexpr size_t kAdjU = (size_t)kMmaMics * kMmaPaths * kUpRow * 8;
+constexpr size_t kAdjPM = (size_t)kMmaMics * kMmaPaths * kPmRow * 4;
 constexpr size_t kAdjSmem = kAdjV + kAdjB + kAdjU + kAdjPM + kMmaPaths * 8 * 4 + kMmaPaths * 4 + kMmaMics * 4 * 4;
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
@@ -327,9 +331,9 @@ __global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const Acc
     char* base = reinterpret_cast<char*>(smem4);
     __nv_bfloat16* Vs = reinterpret_cast<__nv_bfloat16*>(base);                 // [mic][part][path][kVRow]
     __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + kAdjV);         // [mic][part][n][kBRow]
-    float2* Up = reinterpret_cast<float2*>(base + kAdjV + kAdjB);               // [mic][path][16]: (W^32)^k1
-    float* pm = reinterpret_cast<float*>(base + kAdjV + kAdjB + kAdjU);         // [mic][path][8]
-    float* pd = pm + (size_t)kMmaMics * kMmaPaths * 8;                          // [path][8]
+    float2* Up = reinterpret_cast<float2*>(base + kAdjV + kAdjB);               // [mic][path][kUpRow]: (W^32)^k1
+    float* pm = reinterpret_cast<float*>(base + kAdjV + kAdjB + kAdjU);         // [mic][path][kPmRow]
+    float* pd = pm + (size_t)kMmaMics * kMmaPaths * kPmRow;                     // [path][8]
     int* pq = reinterpret_cast<int*>(pd + kMmaPaths * 8);                       // [path] valid
     float* ered = reinterpret_cast<float*>(pq + kMmaPaths);                     // [mic][4] emitter sums
 
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const Acc
         {
             const int p = tid % kMmaPaths, ml = tid / kMmaPaths, m = mic0 + ml;
             float2 z = make_float2(0.0f, 0.0f), w1 = make_float2(0.0f, 0.0f), w32 = make_float2(0.0f, 0.0f);
-            float* o = pm + ((size_t)ml * kMmaPaths + p) * 8;
+            float* o = pm + ((size_t)ml * kMmaPaths + p) * kPmRow;
             const bool ok = pq[p] && m < a.M;
             if (ok) {
                 const float* d = pd + p * 8;
@@ -432,12 +436,13 @@ __global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const Acc
             } else {
                 o[0] = o[1] = o[2] = o[3] = o[4] = o[5] = o[6] = 0.0f;
             }
-            float2* up = Up + ((size_t)ml * kMmaPaths + p) * kK1;
+            float2* up = Up + ((size_t)ml * kMmaPaths + p) * kUpRow;
             float2 ue = make_float2(1.0f, 0.0f), uo = w32;
             const float2 w64 = cmul(w32, w32);
 #pragma unroll
             for (int k1 = 0; k1 < kK1; k1 += 2) {
-                reinterpret_cast<float4*>(up)[k1 / 2] = make_float4(ue.x, ue.y, uo.x, uo.y);
+                up[k1] = ue;
+                up[k1 + 1] = uo;
                 ue = cmul(ue, w64);
                 uo = cmul(uo, w64);
             }
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const Acc
 #pragma unroll
                 for (int hp = 0; hp < 2; ++hp) {
                     const int p = 16 * mt + g + 8 * hp;
-                    const float2* up = Up + ((size_t)warp * kMmaPaths + p) * kK1;
+                    const float2* up = Up + ((size_t)warp * kMmaPaths + p) * kUpRow;
                     float s0r = 0.0f, s0i = 0.0f, s1r = 0.0f, s1i = 0.0f;
 #pragma unroll
                     for (int nb = 0; nb < 2; ++nb)
@@ -557,7 +562,7 @@ __global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const Acc
                         s1r += __shfl_xor_sync(0xffffffffu, s1r, o);
                         s1i += __shfl_xor_sync(0xffffffffu, s1i, o);
                     }
-                    const float* q = pm + ((size_t)warp * kMmaPaths + p) * 8;
+                    const float* q = pm + ((size_t)warp * kMmaPaths + p) * kPmRow;
                     if (t4 == 0 && q[6] != 0.0f) {
                         const float zr = q[0], zi = q[1];
                         const float c0r = zr * s0r - zi * s0i, c0i = zr * s0i + zi * s0r;
