@@ -588,6 +588,7 @@ struct AccumTask {
     acc::Geom g;
     float2* out;
     int64_t item0, out0;
+    const uint32_t* mat_off;  // tensor-core diffraction task: first path of each material, then the end
 };
 // fills t->a, t->g and t->out (the general accumulator's tile shape, 16 bins per thread, omni receivers)
 cudaError_t accum_task(const AccumArgs& a, float2* out, AccumTask* t);
@@ -597,5 +598,15 @@ cudaError_t accumulate_queue(int kind, const AccumTask* tasks, int32_t n_tasks, 
                              unsigned long long* counter, cudaStream_t s);
 // fixed-order sums of the tasks' chunk partials into their outputs (outputs numbered from 0 over the tasks)
 cudaError_t reduce_tasks(const AccumTask* tasks, int32_t n_tasks, int64_t n_out, cudaStream_t s);
+// Batched tensor-core diffraction (st_accum_mma.cu).  batch_material_order sorts the compacted candidate
+// indices by (job, material) -- stable, jobs stay contiguous, the material only for jobs with diff_mma set --
+// and writes each such job's material offsets mat_off[j * kMatStride + q] (q = 0 .. n_mat; scratch:
+// material_order_scratch(cap) bytes).  diffraction_mma_task fills a task (its tile geometry: n_mb, n_bb,
+// smem) whose items the queue launch runs, one CTA per item.
+cudaError_t batch_material_order(const BatchArgs& a, const uint32_t* count, int64_t cap, uint32_t* idx,
+                                 uint32_t* mat_off, void* scratch, cudaStream_t s);
+void diffraction_mma_task(const AccumArgs& a, const uint32_t* mat_off, float2* out, AccumTask* t);
+cudaError_t accumulate_diffraction_mma_queue(const AccumTask* tasks, int32_t n_tasks, int64_t n_items,
+                                             cudaStream_t s);
 
 }  // namespace st

@@ -85,16 +85,14 @@ __device__ __forceinline__ MTile tile_at(const uint32_t* mat_off, int n_mat, int
     return MTile{-1, 0, 0};
 }
 
-__global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const AccumArgs a, const uint32_t* mat_off,
-                                                                    int n_mb) {
-    extern __shared__ float4 smem4[];
-    char* base = reinterpret_cast<char*>(smem4);
+// One CTA's work: microphone block mb, bin block bb, chunk `chunk` of a.n_chunks (its share of the tiles)
+__device__ __forceinline__ void diff_mma_cta(const AccumArgs& a, const uint32_t* mat_off, int mb, int bb, int chunk,
+                                             char* base) {
     __nv_bfloat16* Us = reinterpret_cast<__nv_bfloat16*>(base);            // [mic][part][path][kURow]
     __nv_bfloat16* Vs = reinterpret_cast<__nv_bfloat16*>(base + kUBytes);  // [mic][part][path][kVRow]
     float* pd = reinterpret_cast<float*>(base + kUBytes + kVBytes);        // [path][8]: point, r hi, r lo
     int* pq = reinterpret_cast<int*>(pd + kMmaPaths * 8);                  // [path] valid
 
-    const int mb = blockIdx.x % n_mb, bb = blockIdx.x / n_mb;
     const int mic0 = mb * kMmaMics, kb = bb * kMmaBins;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_mat = a.n_mat_tab;
@@ -102,7 +100,7 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
     int64_t n_tiles = 0;
     for (int q = 0; q < n_mat; ++q) n_tiles += ((int64_t)mat_off[q + 1] - mat_off[q] + kMmaPaths - 1) / kMmaPaths;
     const int64_t per = (n_tiles + a.n_chunks - 1) / a.n_chunks;
-    const int64_t t0 = (int64_t)blockIdx.y * per, t1 = min(n_tiles, t0 + per);
+    const int64_t t0 = (int64_t)chunk * per, t1 = min(n_tiles, t0 + per);
 
     // this warp's accumulators: T (current material) and S (spectrum), fragment layout of m16n8 blocks:
     // element i of n-block nb is (k1 = g + 8 (i >> 1), k2 = 8 nb + 2 t + (i & 1))
@@ -285,7 +283,7 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
     flush();
     // this chunk's partial spectrum of the warp's microphone
     if (m_w < a.M) {
-        float2* out = a.partial + ((size_t)blockIdx.y * a.M + m_w) * a.F;
+        float2* out = a.partial + ((size_t)chunk * a.M + m_w) * a.F;
 #pragma unroll
         for (int nb = 0; nb < 4; ++nb)
 #pragma unroll
@@ -294,6 +292,29 @@ __global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const Accum
                 if (k < a.F) out[k] = make_float2(Sr[nb][i], Si[nb][i]);
             }
     }
+}
+
+__global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma(const AccumArgs a, const uint32_t* mat_off,
+                                                                    int n_mb) {
+    extern __shared__ float4 smem4[];
+    diff_mma_cta(a, mat_off, blockIdx.x % n_mb, blockIdx.x / n_mb, blockIdx.y, reinterpret_cast<char*>(smem4));
+}
+
+// The diffraction tasks of a batch (one per job, each with its material offsets): CTA i runs item i of the
+// table, items numbered as in the single-job grid (microphone block fastest, then bin block, then chunk).
+__global__ void __launch_bounds__(kMmaMics * 32, 3) k_accum_diff_mma_queue(const AccumTask* tasks, int32_t n_tasks) {
+    extern __shared__ float4 smem4[];
+    const int64_t it = blockIdx.x;
+    int lo = 0, hi = n_tasks - 1;  // last task whose first item is <= it
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].item0 <= it) lo = mid; else hi = mid - 1;
+    }
+    const AccumTask& T = tasks[lo];
+    const int n_mb = T.g.n_mb, nxy = n_mb * T.g.n_bb;
+    const int local = (int)(it - T.item0);
+    diff_mma_cta(T.a, T.mat_off, (local % nxy) % n_mb, (local % nxy) / n_mb, local / nxy,
+                 reinterpret_cast<char*>(smem4));
 }
 
 // ---------------------------------------------------------------- the diffraction adjoint (positions)
@@ -635,6 +656,42 @@ __global__ void k_mat_offsets(const uint64_t* keys, const uint32_t* count, int n
     off[q] = (uint32_t)lo;
 }
 
+// Batched form: key (job, material) of every compacted diffraction candidate, the material only for the jobs
+// accumulated on the tensor cores (0 for the others, whose order then stays the compaction order); past the
+// count a key above every job
+__global__ void k_mat_keys_batch(const BatchArgs a, const uint32_t* idx, const uint32_t* count, int64_t cap,
+                                 uint64_t* keys) {
+    const int64_t n = *count;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cap; c += (int64_t)gridDim.x * blockDim.x) {
+        if (c >= n) {
+            keys[c] = (uint64_t)a.n_jobs << 8;
+            continue;
+        }
+        const int64_t i = idx[c];
+        const int job = find_job(a.samp_offs, a.n_jobs, i);
+        const JobDev& b = a.jobs[job];
+        const uint32_t q = b.diff_mma ? ((uint32_t)b.tri_mat[a.cand_tri[i]] & 255u) : 0u;
+        keys[c] = ((uint64_t)job << 8) | q;
+    }
+}
+
+// per tensor-core job j: first position of each of its materials and its end, off[j * kMatStride + q]
+__global__ void k_mat_offsets_batch(const BatchArgs a, const uint64_t* keys, const uint32_t* count, uint32_t* off) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)a.n_jobs * kMatStride) return;
+    const int j = (int)(t / kMatStride), q = (int)(t % kMatStride);
+    const JobDev& b = a.jobs[j];
+    if (!b.diff_mma || q > b.n_mat) return;
+    const uint64_t key = ((uint64_t)j << 8) | (uint64_t)q;  // q = n_mat: the first key past the job's materials
+    int64_t lo = 0, hi = *count;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    off[t] = (uint32_t)lo;
+}
+
 }  // namespace
 
 bool diffraction_mma_applies(const AccumArgs& a) {
@@ -688,6 +745,49 @@ cudaError_t adjoint_diffraction_mma(const AccumArgs& a, const AdjointArgs& j, co
     dim3 grid((unsigned)(n_mb * n_bb), (unsigned)a.n_chunks);
     note_launch();
     k_adjoint_diff_mma<<<grid, kMmaMics * 32, kAdjSmem, s>>>(a, j, mat_off, n_mb, n_bb);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_material_order(const BatchArgs& a, const uint32_t* count, int64_t cap, uint32_t* idx,
+                                 uint32_t* mat_off, void* scratch, cudaStream_t s) {
+    if (cap <= 0) return cudaSuccess;
+    uint64_t* keys = static_cast<uint64_t*>(scratch);
+    void* sort_scr = static_cast<char*>(scratch) + (size_t)cap * 8;
+    note_launch();
+    k_mat_keys_batch<<<grid_for(cap, 256), 256, 0, s>>>(a, idx, count, cap, keys);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int bits = 8;
+    while (((int64_t)1 << (bits - 8)) <= a.n_jobs) ++bits;  // job indices 0 .. n_jobs (the sentinel)
+    if ((e = radix_sort_u64(keys, idx, cap, bits, sort_scr, s)) != cudaSuccess) return e;  // stable
+    const int64_t nt = (int64_t)a.n_jobs * kMatStride;
+    note_launch();
+    k_mat_offsets_batch<<<grid_for(nt, 256), 256, 0, s>>>(a, keys, count, mat_off);
+    return cudaGetLastError();
+}
+
+void diffraction_mma_task(const AccumArgs& a, const uint32_t* mat_off, float2* out, AccumTask* t) {
+    t->a = a;
+    t->g = acc::Geom{};
+    t->g.n_mb = (a.M + kMmaMics - 1) / kMmaMics;
+    t->g.n_bb = (a.F + kMmaBins - 1) / kMmaBins;
+    t->g.smem = kMmaSmem;
+    t->out = out;
+    t->mat_off = mat_off;
+}
+
+cudaError_t accumulate_diffraction_mma_queue(const AccumTask* tasks, int32_t n_tasks, int64_t n_items,
+                                             cudaStream_t s) {
+    if (n_tasks <= 0 || n_items <= 0) return cudaSuccess;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_accum_diff_mma_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMmaSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    note_launch();
+    k_accum_diff_mma_queue<<<(unsigned)n_items, kMmaMics * 32, kMmaSmem, s>>>(tasks, n_tasks);
     return cudaGetLastError();
 }
 

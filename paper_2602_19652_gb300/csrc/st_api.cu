@@ -148,6 +148,12 @@ struct BatchState {
     DevBuf tasks, part_all, qctr;
     int32_t n_tasks_spec = 0, n_tasks_diff = 0;
     int64_t items_spec = 0, items_diff = 0, n_out = 0;
+    // diffraction on the tensor cores (jobs with diff_mma): their tasks follow the diffraction ones in the table;
+    // the compacted candidates are sorted by (job, material) and mat_off holds each such job's groups
+    int32_t n_tasks_mma = 0;
+    int64_t items_mma = 0;
+    bool any_mma = false;
+    DevBuf mat_off, mat_scr;
     size_t smem_spec = 0, smem_diff = 0;
     PathList spec, diff;
     int64_t N_total = 0, R_total = 0, K_total = 0, M_total = 0, MF_total = 0;
@@ -1691,7 +1697,7 @@ void batch_release(BatchState& B) {
                       &B.hit_t, &B.vis_q, &B.los_q, &B.rec_mask, &B.vis_qm})
         release(*b);
     release(B.narrow_partial);
-    for (DevBuf* d : {&B.tasks, &B.part_all, &B.qctr}) release(*d);
+    for (DevBuf* d : {&B.tasks, &B.part_all, &B.qctr, &B.mat_off, &B.mat_scr}) release(*d);
     for (auto& T : B.tables)
         for (DevBuf* b : {&T.lk, &T.g2, &T.lid, &T.qhi, &T.qlo, &T.bw, &T.band, &T.kband, &T.bband}) release(*b);
     for (PathList* P : {&B.spec, &B.diff})
@@ -1773,7 +1779,7 @@ AccumArgs batch_accum_args(BatchState& B, const st_job* jobs, int j, int kind, c
 cudaError_t batch_tasks(st_ctx* c, BatchState& B, const st_job* jobs, const st_sim_params& p, const st_tune& tn,
                         cudaStream_t s) {
     (void)c;
-    std::vector<AccumTask> spec, diff;
+    std::vector<AccumTask> spec, diff, mma;
     B.narrow_jobs.clear();
     for (int j = 0; j < B.n_jobs; ++j) {
         const JobDev& jd = B.jobs[j];
@@ -1788,7 +1794,12 @@ cudaError_t batch_tasks(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
             accum_task(batch_accum_args(B, jobs, j, 0, p, tn), out, &t);
             spec.push_back(t);
         }
-        if (jd.K > 0) {
+        if (jd.K > 0 && jd.diff_mma) {
+            AccumTask t{};
+            diffraction_mma_task(batch_accum_args(B, jobs, j, 1, p, tn), ptr<uint32_t>(B.mat_off) + (size_t)j * kMatStride,
+                                 out + MF, &t);
+            mma.push_back(t);
+        } else if (jd.K > 0) {
             AccumTask t{};
             accum_task(batch_accum_args(B, jobs, j, 1, p, tn), out + MF, &t);
             diff.push_back(t);
@@ -1796,17 +1807,20 @@ cudaError_t batch_tasks(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     }
     B.n_tasks_spec = (int32_t)spec.size();
     B.n_tasks_diff = (int32_t)diff.size();
+    B.n_tasks_mma = (int32_t)mma.size();
     std::vector<AccumTask> all(spec);
     all.insert(all.end(), diff.begin(), diff.end());
+    all.insert(all.end(), mma.begin(), mma.end());
     size_t part = 0;
     int64_t out0 = 0;
-    B.items_spec = B.items_diff = 0;
+    B.items_spec = B.items_diff = B.items_mma = 0;
     B.smem_spec = B.smem_diff = 0;
+    size_t smem_mma = 0;
     for (size_t i = 0; i < all.size(); ++i) {
         AccumTask& t = all[i];
-        const bool is_spec = i < spec.size();
-        int64_t& items = is_spec ? B.items_spec : B.items_diff;
-        size_t& sm = is_spec ? B.smem_spec : B.smem_diff;
+        const int cls = i < spec.size() ? 0 : (i < spec.size() + diff.size() ? 1 : 2);
+        int64_t& items = cls == 0 ? B.items_spec : (cls == 1 ? B.items_diff : B.items_mma);
+        size_t& sm = cls == 0 ? B.smem_spec : (cls == 1 ? B.smem_diff : smem_mma);
         t.item0 = items;
         items += (int64_t)t.g.n_mb * t.g.n_bb * t.a.n_chunks;
         sm = std::max(sm, t.g.smem);
@@ -1923,6 +1937,8 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
         CB(flags_from_u8(a.keep, B.K_total, fl, s));
         CB(exclusive_scan_u32(fl, sc, B.K_total, cnt + 3, B.scratch.p, s));
         CB(compact_indices(fl, sc, B.K_total, ix, s));
+        if (B.any_mma)  // tensor-core jobs' paths grouped by material (stable; jobs stay in place)
+            CB(batch_material_order(a, cnt + 3, B.K_total, ix, ptr<uint32_t>(B.mat_off), B.mat_scr.p, s));
         CB(batch_gather_diff(a, ix, cnt + 3, B.diff, s));
     }
     if (spec || B.K_total > 0)
@@ -1933,7 +1949,9 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
         unsigned long long* qc = ptr<unsigned long long>(B.qctr);
         if (spec) CB(accumulate_queue(0, tk, B.n_tasks_spec, B.items_spec, B.smem_spec, qc, s));
         if (B.K_total > 0) CB(accumulate_queue(1, tk + B.n_tasks_spec, B.n_tasks_diff, B.items_diff, B.smem_diff, qc + 1, s));
-        if (spec || B.K_total > 0) CB(reduce_tasks(tk, B.n_tasks_spec + B.n_tasks_diff, B.n_out, s));
+        if (B.K_total > 0)
+            CB(accumulate_diffraction_mma_queue(tk + B.n_tasks_spec + B.n_tasks_diff, B.n_tasks_mma, B.items_mma, s));
+        if (spec || B.K_total > 0) CB(reduce_tasks(tk, B.n_tasks_spec + B.n_tasks_diff + B.n_tasks_mma, B.n_out, s));
         for (const int j : B.narrow_jobs) {
             const JobDev& jd = B.jobs[j];
             const int64_t MF = (int64_t)jd.M * jd.F;
@@ -1942,7 +1960,10 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
                 if (kind == 0 ? !(spec && jd.N > 0) : jd.K <= 0) continue;
                 AccumArgs y = batch_accum_args(B, jobs, j, kind, p, tn);
                 y.partial = ptr<float2>(B.narrow_partial);
-                CB(accumulate(y, s));
+                if (kind == 1 && jd.diff_mma)
+                    CB(accumulate_diffraction_mma(y, ptr<uint32_t>(B.mat_off) + (size_t)j * kMatStride, s));
+                else
+                    CB(accumulate(y, s));
                 CB(reduce_partials(y.partial, y.n_chunks, MF, out + kind * MF, s));
             }
         }
@@ -2036,6 +2057,7 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     batch_release(B);
     B = BatchState();
     B.n_jobs = n_jobs;
+    B.any_mma = false;
     B.tables.resize(n_jobs);
     B.jobs.resize(n_jobs);
     B.chunks_spec.resize(n_jobs);
@@ -2181,13 +2203,30 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
         // chunks that would fill it alone (fewer partial spectra to sum)
         const int nb = big_job(d) ? 1 : kBatchChunkDiv;
         const int dir_nb = J.mic_tables ? S.n_bands : 0;
+        {
+            AccumArgs probe{};
+            probe.kind = 1;
+            probe.M = d.M;
+            probe.F = d.F;
+            probe.n_mat_tab = S.n_mat;
+            probe.etab = d.etab;
+            probe.mic_tab = d.mic_tab;
+            d.diff_mma = d.K > 0 && diffraction_mma_applies(probe) ? 1 : 0;
+        }
+        B.any_mma = B.any_mma || d.diff_mma;
         B.chunks_spec[j] =
             std::max(1, accum_chunks(d.N * d.B, d.M, d.F, S.n_mat, dir_nb, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
-        B.chunks_diff[j] = std::max(1, accum_chunks(d.K, d.M, d.F, S.n_mat, dir_nb, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
+        B.chunks_diff[j] =
+            d.diff_mma ? std::max(1, diffraction_mma_chunks(d.K, d.M, d.F, S.n_mat) / nb)
+                       : std::max(1, accum_chunks(d.K, d.M, d.F, S.n_mat, dir_nb, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
         if (solo_accum(d))
             narrow_part = std::max(narrow_part, (size_t)std::max(B.chunks_spec[j], B.chunks_diff[j]) * d.M * d.F * 8);
     }
     CKC(c, grow(B.narrow_partial, narrow_part), "batch alloc");
+    if (B.any_mma) {
+        CKC(c, grow(B.mat_off, (size_t)n_jobs * kMatStride * 4), "batch alloc");
+        CKC(c, grow(B.mat_scr, material_order_scratch(B.K_total)), "batch alloc");
+    }
     CKC(c, batch_tasks(c, B, jobs, p, tn, s), "batch tasks");
     CKC(c, grow(B.jobs_dev, sizeof(JobDev) * (size_t)n_jobs), "batch alloc");
     CKC(c, cudaMemcpyAsync(B.jobs_dev.p, B.jobs.data(), sizeof(JobDev) * (size_t)n_jobs, cudaMemcpyHostToDevice, s),

@@ -434,7 +434,8 @@ struct JobDev {
     const uint64_t* cdf;
     const int64_t* sample_off;
     int32_t root, max_iter, n_obj;
-    int32_t n_mat;          // checked build: materials of the scene
+    int32_t n_mat;          // materials of the scene
+    int32_t diff_mma;       // diffraction accumulated on the tensor cores (paths grouped by material)
     int64_t chk_nodes, chk_tris;  // checked build: wide nodes and triangles of the scene (see Trav::chk)
     float cos_fov;          // <= -1: field of view off
     // sensor inputs (the caller's device memory, read at run time)
@@ -463,6 +464,9 @@ struct JobDev {
     double f_lo, df;
     float2* out;            // spectra [3][M][F]
 };
+
+// entries per job of a batch's material offsets (materials 0 .. 254 and the end)
+constexpr int kMatStride = 256;
 
 struct BatchArgs {
     const JobDev* jobs;

@@ -318,3 +318,39 @@ def test_batch_directivity(st):
     half = [o.cpu().numpy().copy() for o in ctx.simulate_batch(jobs, p)]
     for c in range(3):
         assert rel_l2(half[1][c], 0.5 * outs[1][c]) <= 1e-6
+
+
+def test_batch_tensor_diffraction(st):
+    """Diffraction paths of omni jobs with three or more microphones and 128 or more bins are accumulated on
+    the tensor cores in the batch too (the candidates sorted by job and material): jobs spanning several
+    microphone and bin blocks with ragged tails, and one job of a million paths accumulated on its own,
+    against the single-pose path and, for two jobs, the oracle."""
+    import oracle
+    ctx = st.Context(0)
+    scenes, jobs0, wl_jobs0 = make_case(st, ctx, seed=21, n_scenes=2, poses=3)
+    rng = np.random.default_rng(2121)
+    shapes = [(3, 128), (5, 700), (12, 513), (4, 300), (9, 1100), (7, 256)]
+    jobs, wl_jobs = [], []
+    for i, (job, wj) in enumerate(zip(jobs0, wl_jobs0)):
+        M, F = shapes[i % len(shapes)]
+        mics = (wj.emitter + rng.uniform(-0.3, 0.3, size=(M, 3))).astype(np.float32)
+        n = 262_144 if i == 1 else wj.dirs.shape[0]
+        bounces = 4 if i == 1 else wj.bounces
+        w = dataclasses.replace(wj, mics=mics, n_bins=F, dirs=synth.fibonacci_directions(n), bounces=bounces)
+        jobs.append(st.BatchJob(job.scene, w.emitter, w.emitter_quat, w.dirs, w.mics, F, w.f_lo, w.f_hi, bounces,
+                                pose_index=job.job.pose_index, fov_half=w.fov_half))
+        wl_jobs.append(w)
+    p = st.sim_params(max_distance=60.0)
+    outs = [o.cpu().numpy() for o in ctx.simulate_batch(jobs, p)]
+    n_diff = 0
+    for j, (job, wj) in enumerate(zip(jobs, wl_jobs)):
+        ref = single(st, ctx, job.scene, wj, job.job.pose_index)
+        for c in range(3):
+            assert rel_l2(outs[j][c], ref[c]) <= TOL_SINGLE, (j, c, rel_l2(outs[j][c], ref[c]))
+        n_diff += int(np.abs(outs[j][1]).sum() > 0)
+    assert n_diff >= len(jobs) - 1
+    for j in (0, 2):
+        wj = wl_jobs[j]
+        o = oracle.simulate(wj, curv=dict(budget=50_000), pose=jobs[j].job.pose_index)
+        for c in range(3):
+            assert rel_l2(outs[j][c], o["spectra"][c]) <= TOL, (j, c, rel_l2(outs[j][c], o["spectra"][c]))
