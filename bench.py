@@ -761,6 +761,9 @@ def run_case(st, torch, case: str, reps: int):
     if case == "batched_bat":
         print(json.dumps(measure_batched_directional(st, torch)))
         return
+    if case == "batched":
+        print(json.dumps(measure_batched(st, torch)))
+        return
     if case == "emitters":
         wl = synth.clutter(seed=202)
         ctx = st.Context(dev)
@@ -894,7 +897,8 @@ def main():
     ap.add_argument("--no-emitters", action="store_true", help="skip the several-emitters timing")
     ap.add_argument("--no-instances", action="store_true", help="skip the instanced-forest timing")
     ap.add_argument("--case", default=None,
-                    choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow", "emitters", "instances", "batched_bat"],
+                    choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow", "emitters", "instances", "batched_bat",
+                             "batched"],
                     help="run a small case of one kernel family a few times and exit (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
