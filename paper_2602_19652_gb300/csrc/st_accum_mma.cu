@@ -14,8 +14,10 @@
 // bf16 pairs x = hi + lo (16 significant bits); each warp then multiplies its microphone's tile with
 // mma.sync (bf16 inputs, float32 accumulation), hi*hi + hi*lo + lo*hi for each of the four real products
 // of the complex one (the dropped lo*lo is below 2^-16 of a product; relative L2 error of the spectra
-// a few 1e-6).  When the material changes, and at the end, a warp adds E_q[k] times its accumulators to
-// its spectrum registers.  Results are in fixed order for a given launch shape.
+// a few 1e-6).  When the material changes, every kFlushTiles tiles, and at the end, a warp adds E_q[k] times
+// its accumulators to its spectrum registers (float32 fma, rounded to nearest: the tensor cores' own float32
+// accumulation is not, and its error would grow with the tiles summed into one accumulator).  Results are in
+// fixed order for a given launch shape.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -33,6 +35,7 @@ using namespace acc;
 constexpr int kMmaMics = 4;     // microphones (warps) per CTA
 constexpr int kMmaPaths = 32;   // paths per tile
 constexpr int kK1 = 16, kK2 = 32, kMmaBins = kK1 * kK2;
+constexpr int kFlushTiles = 4;  // tiles summed into the matrix-product accumulators between flushes
 constexpr int kURow = 24;       // bf16 per U row (16 + 8 padding: conflict-free ldmatrix rows)
 constexpr int kVRow = 40;       // bf16 per V row (32 + 8)
 constexpr size_t kUBytes = (size_t)kMmaMics * 4 * kMmaPaths * kURow * 2;
@@ -111,7 +114,7 @@ __device__ __forceinline__ void diff_mma_cta(const AccumArgs& a, const uint32_t*
         for (int i = 0; i < 4; ++i) Tr[nb][i] = Ti[nb][i] = Sr[nb][i] = Si[nb][i] = 0.0f;
     const int g = lane >> 2, t4 = lane & 3;
     const int m_w = mic0 + warp;
-    int q_cur = -1;
+    int q_cur = -1, n_acc = 0;
 
     auto flush = [&]() {
         if (q_cur < 0) return;
@@ -219,10 +222,15 @@ __device__ __forceinline__ void diff_mma_cta(const AccumArgs& a, const uint32_t*
         }
         __syncthreads();
         if (m_w < a.M) {
-            if (T.q != q_cur) {
+            // the accumulators go into the spectrum registers when the material changes, and at least every
+            // kFlushTiles tiles: the tensor cores' float32 accumulation does not round to nearest, so its error
+            // grows with the number of products summed into one accumulator; the spectrum sums round to nearest
+            if (T.q != q_cur || n_acc == kFlushTiles) {
                 flush();
                 q_cur = T.q;
+                n_acc = 0;
             }
+            ++n_acc;
             const __nv_bfloat16* Uw = Us + (size_t)warp * 4 * kMmaPaths * kURow;
             const __nv_bfloat16* Vw = Vs + (size_t)warp * 4 * kMmaPaths * kVRow;
             const int mi = lane >> 3, rr = lane & 7;

@@ -354,3 +354,31 @@ def test_batch_tensor_diffraction(st):
         o = oracle.simulate(wj, curv=dict(budget=50_000), pose=jobs[j].job.pose_index)
         for c in range(3):
             assert rel_l2(outs[j][c], o["spectra"][c]) <= TOL, (j, c, rel_l2(outs[j][c], o["spectra"][c]))
+
+
+def test_batch_tensor_diffraction_long_accumulation(st):
+    """A job whose diffraction accumulation runs as few chunks of many tiles (62 microphones x 1902 bins,
+    about 25k kept samples, in a batch): the matrix-product accumulators are flushed into the spectrum
+    registers every few tiles, so the error stays at the level of a single chunk's, well inside the
+    spectra tolerance, against the oracle's float64 diffraction spectrum."""
+    import oracle
+    wls, specs = synth.batched_poses(seed=505)
+    sp = specs[233]
+    wl = wls[sp["scene"]]
+    rng = np.random.default_rng(7)
+    q = unit_quat(rng)
+    wj = dataclasses.replace(wl, emitter=sp["emitter"], emitter_quat=q, dirs=synth.fibonacci_directions(1000),
+                             mics=sp["mics"], n_bins=sp["n_bins"], bounces=sp["bounces"], max_distance=60.0,
+                             diffraction=True, fov_half=math.pi)
+    assert len(wj.mics) >= 32 and wj.n_bins > 1024
+    ctx = st.Context(0)
+    sc = st.Scene(ctx, wj.verts, wj.tris, wj.tri_mat, wj.tri_obj)
+    sc.set_materials(wj.band_hz, wj.k_band, wj.beta_band, wj.diff_band)
+    sc.precompute(st.curv_params(sample_budget=65536))
+    job = st.BatchJob(sc, wj.emitter, wj.emitter_quat, wj.dirs, wj.mics, wj.n_bins, wj.f_lo, wj.f_hi, wj.bounces,
+                      pose_index=sp["pose_index"])
+    out = ctx.simulate_batch([job], st.sim_params(max_distance=60.0))[0].cpu().numpy()
+    o = oracle.simulate(wj, curv=dict(budget=65536), pose=sp["pose_index"], components=2)
+    assert np.abs(o["spectra"][1]).sum() > 0
+    err = rel_l2(out[1], o["spectra"][1])
+    assert err <= 3e-5, err
