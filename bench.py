@@ -34,18 +34,21 @@ import synth  # noqa: E402
 METRIC = "Mrays/s (closest + any-hit segments/s; spectra <=1e-4 rel-L2 vs oracle)"
 UNIT = "Mrays/s"
 FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by-complex multiply-accumulate (4)
-# dram__bytes_read.sum + dram__bytes_write.sum per k_accum launch on the clutter workload, from an ncu capture
-# (the diffraction launch at full size, the specular launch on 200k rays scaled by the visible records: the path
-# list is read once), with the hash of the accumulator's sources it was taken on: the bench reports it only while
-# the sources still hash to that value (else null, until the kernel is captured again)
-ACCUM_TRAFFIC = {"sources_sha16": "a3c4ee20590f299a", "bytes_per_launch": 38.7e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch on the clutter workload, from an ncu capture, with the
+# hash of the kernel's sources it was taken on: the bench reports it only while the sources still hash to that
+# value (else null, until the kernel is captured again).  Specular k_accum: captured on 200k rays (7.97 MB read,
+# 0.02 MB written, 163,228 visible records) and scaled to the full-size launch by the visible records (816,192:
+# the path list is read once).  k_accum_diff_mma: the full-size diffraction set (21.36 MB read, 0.07 MB written).
+ACCUM_TRAFFIC = {"sources_sha16": "31519aade733eafa", "specular_bytes_per_launch": 39.9e6}
 ACCUM_SOURCES = ("st_accum.cu", "st_accum_dev.cuh", "st_internal.cuh")
+DIFF_MMA_TRAFFIC = {"sources_sha16": "b3aa22910b479813", "bytes_per_launch": 21.4e6}
+DIFF_MMA_SOURCES = ("st_accum_mma.cu", "st_accum_dev.cuh", "st_internal.cuh")
 
 
-def accum_sources_sha16():
+def accum_sources_sha16(files=ACCUM_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for f in ACCUM_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2602_19652_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -90,7 +93,8 @@ def tensor_roofline(stats_list, peaks, peak_src):
             "peak_source": f"bf16 dense, burst ({peak_src})",
             "work": f"{TENSOR_FLOPS_PER_TERM} bf16 tensor flops per (path, mic, bin) term, "
                     f"{terms / max(launches, 1):.3e} terms per launch", "ms_per_launch": ms / max(launches, 1),
-            "traffic": None}
+            "traffic": DIFF_MMA_TRAFFIC["bytes_per_launch"]
+            if DIFF_MMA_TRAFFIC["sources_sha16"] == accum_sources_sha16(DIFF_MMA_SOURCES) else None}
 
 
 def e2e_simulate(st, ctx, sc, wl, params, n_steps):
@@ -841,7 +845,7 @@ def compact_line(d):
     if rd:
         line["roofline_diffraction"] = {"bound": rd["bound"], "kernel": rd["kernel"].split(" ")[0],
                                         "achieved": _r(rd["achieved"]), "peak": _r(rd["peak"]), "unit": rd["unit"],
-                                        "frac": _r(rd["frac"], 4)}
+                                        "frac": _r(rd["frac"], 4), "traffic": rd["traffic"]}
     cb = d.get("cpu_baseline")
     if cb:
         line["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"],
@@ -966,9 +970,10 @@ def main():
     clocks = clk.summary()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    traffic = ACCUM_TRAFFIC["bytes_per_launch"] if ACCUM_TRAFFIC["sources_sha16"] == accum_sources_sha16() else None
     tensor_diff = all(s.diffraction_tensor for s in st_list)
-    roofline = accum_roofline(st_list, n_sm, sm_mhz, peak_src, traffic=None if tensor_diff else traffic,
+    traffic = (ACCUM_TRAFFIC["specular_bytes_per_launch"]
+               if tensor_diff and ACCUM_TRAFFIC["sources_sha16"] == accum_sources_sha16() else None)
+    roofline = accum_roofline(st_list, n_sm, sm_mhz, peak_src, traffic=traffic,
                               kernel="k_accum (specular accumulator)" if tensor_diff else
                               "k_accum (spectrum accumulator)", only_specular=tensor_diff)
     roofline_diffraction = tensor_roofline(st_list, peaks, peak_src) if tensor_diff else None

@@ -354,41 +354,70 @@ __global__ void k_hc_vertices(int64_t nv, const int32_t* canon, const uint32_t* 
     }
 }
 
-// Single block: empty meshes get no samples, the total is capped by the budget, offsets scanned.
-__global__ void k_sample_counts(int32_t n_obj, const uint32_t* mesh_off, const uint64_t* cdf,
-                                unsigned long long* ns, int64_t budget, int64_t* n_samples, int64_t* sample_off) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long total = 0;
-    for (int32_t m = 0; m < n_obj; ++m) {
-        uint32_t a = mesh_off[m], b = mesh_off[m + 1];
-        if (b <= a || cdf[b - 1] == 0) ns[m] = 0;
-        total += ns[m];
-    }
-    int64_t acc = 0;
-    for (int32_t m = 0; m < n_obj; ++m) {
-        unsigned long long n = ns[m];
-        if (budget >= 0 && total > (unsigned long long)budget) {
-            // (n * budget) / total without overflow: n <= total and budget < 2^63
-            unsigned long long hi = __umul64hi(n, (unsigned long long)budget);
-            unsigned long long lo = n * (unsigned long long)budget;
-            // 128-by-64 division by long division on 64-bit halves
-            unsigned long long q = 0, r = 0;
-            for (int bit = 127; bit >= 0; --bit) {
-                unsigned long long b = bit >= 64 ? (hi >> (bit - 64)) & 1ull : (lo >> bit) & 1ull;
-                unsigned long long top = r >> 63;
-                r = (r << 1) | b;
-                if (top || r >= total) {
-                    r -= total;
-                    if (bit < 64) q |= 1ull << bit;
-                }
-            }
-            n = q;
+// (n * budget) / total without overflow (n <= total, budget < 2^63): 128-by-64 long division on 64-bit halves
+__device__ __forceinline__ unsigned long long scaled_count(unsigned long long n, unsigned long long budget,
+                                                           unsigned long long total) {
+    const unsigned long long hi = __umul64hi(n, budget), lo = n * budget;
+    unsigned long long q = 0, r = 0;
+    for (int bit = 127; bit >= 0; --bit) {
+        const unsigned long long b = bit >= 64 ? (hi >> (bit - 64)) & 1ull : (lo >> bit) & 1ull;
+        const unsigned long long top = r >> 63;
+        r = (r << 1) | b;
+        if (top || r >= total) {
+            r -= total;
+            if (bit < 64) q |= 1ull << bit;
         }
-        n_samples[m] = (int64_t)n;
-        sample_off[m] = acc;
-        acc += (int64_t)n;
     }
-    sample_off[n_obj] = acc;
+    return q;
+}
+
+// One block: empty meshes get no samples, the total is capped by the budget, offsets scanned.  Each thread takes
+// the meshes tid, tid + kScThreads, ...; integer sums, so the result does not depend on the order.
+constexpr int kScThreads = 1024;
+__global__ void __launch_bounds__(kScThreads) k_sample_counts(int32_t n_obj, const uint32_t* mesh_off,
+                                                              const uint64_t* cdf, unsigned long long* ns,
+                                                              int64_t budget, int64_t* n_samples, int64_t* sample_off) {
+    __shared__ unsigned long long wsum[kScThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long part = 0;
+    for (int32_t m = tid; m < n_obj; m += kScThreads) {
+        const uint32_t a = mesh_off[m], b = mesh_off[m + 1];
+        if (b <= a || cdf[b - 1] == 0) ns[m] = 0;
+        part += ns[m];
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) wsum[warp] = part;
+    __syncthreads();
+    unsigned long long total = 0;
+    for (int w = 0; w < kScThreads / 32; ++w) total += wsum[w];
+    __syncthreads();  // wsum is reused by the scans below
+    const bool cap = budget >= 0 && total > (unsigned long long)budget;
+    int64_t carry = 0;
+    for (int32_t base = 0; base < n_obj; base += kScThreads) {
+        const int32_t m = base + tid;
+        unsigned long long n = m < n_obj ? ns[m] : 0ull;
+        if (m < n_obj && cap) n = scaled_count(n, (unsigned long long)budget, total);
+        // exclusive scan over the block: within the warp, then over the warp totals
+        unsigned long long x = n;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        unsigned long long before = 0, chunk = 0;
+        for (int w = 0; w < kScThreads / 32; ++w) {
+            if (w < warp) before += wsum[w];
+            chunk += wsum[w];
+        }
+        if (m < n_obj) {
+            n_samples[m] = (int64_t)n;
+            sample_off[m] = carry + (int64_t)(before + x - n);
+        }
+        carry += (int64_t)chunk;
+        __syncthreads();  // wsum is rewritten by the next chunk
+    }
+    if (tid == 0) sample_off[n_obj] = carry;
 }
 
 // ---------------------------------------------------------------- LBVH
@@ -852,7 +881,7 @@ cudaError_t scene_build(SceneDev& S, const CurvParamsDev& cp, cudaStream_t s, bo
         CK(grow(S.n_samples, (size_t)(n_obj + 1) * 8));
         CK(grow(S.sample_off, (size_t)(n_obj + 1) * 8));
         note_launch();
-        k_sample_counts<<<1, 1, 0, s>>>(n_obj, ptr<uint32_t>(moff), ptr<uint64_t>(S.cdf), ptr<unsigned long long>(nsu),
+        k_sample_counts<<<1, kScThreads, 0, s>>>(n_obj, ptr<uint32_t>(moff), ptr<uint64_t>(S.cdf), ptr<unsigned long long>(nsu),
                                         cp.budget, ptr<int64_t>(S.n_samples), ptr<int64_t>(S.sample_off));
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&S.total_samples, ptr<int64_t>(S.sample_off) + n_obj, 8, cudaMemcpyDeviceToHost, s));
