@@ -86,8 +86,10 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     int* pvb = reinterpret_cast<int*>(pdb + 3 * PT * 12);
     // (16-byte aligned: each path's 12 floats are read as three float4)
     float* pjb = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(pvb + 3 * PT) + 15) & ~uintptr_t(15));
+    // (specular) per path of a tile: how often each of the launch's kNV materials occurs in its reflection chain
+    float4* pcb = reinterpret_cast<float4*>(pjb + (EMIT ? 3 * PT * 12 : 0));
     float* mt = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(pjb + (EMIT ? 3 * PT * 12 : 0)) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(pcb + (KIND == 0 ? 3 * PT : 0)) + 15) & ~uintptr_t(15));
 
     const int mb = blockIdx.x % g.n_mb, bb = blockIdx.x / g.n_mb;
     const int mic0 = mb * g.MP, kb = bb * KB;
@@ -109,6 +111,31 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                 dst[e] = rel < count ? a.jac[rel * 12 + e % 12] : 0.0f;
             }
         }
+    };
+
+    // material counts of one tile's paths (slot of its path data), one thread per path
+    auto chain_counts = [&](const float* pd, const int* pv, float4* dst) {
+        if (KIND == 0 && j.do_k)
+            for (int p = threadIdx.x; p < PT; p += blockDim.x) {
+                float cnt[kNV] = {0.f, 0.f, 0.f, 0.f};
+                if (pv[p]) {
+                    const uint32_t meta = __float_as_uint(pd[p * 12 + 8]);
+                    const int len = meta & 15, matj = (meta >> 8) & 255;
+                    const uint32_t c0 = __float_as_uint(pd[p * 12 + 9]), c1 = __float_as_uint(pd[p * 12 + 10]);
+                    if (a.reflection_mode == 1 || j.do_beta) {  // one material: the last hit's
+                        const int q = matj - j.mat_base;
+                        for (int u = 0; u < kNV; ++u)
+                            if (q == u) cnt[u] = 1.0f;
+                    } else {
+                        for (int q = 0; q < len; ++q) {
+                            const int mq = ((q < 4 ? (c0 >> (8 * q)) : (c1 >> (8 * (q - 4)))) & 255) - j.mat_base;
+                            for (int u = 0; u < kNV; ++u)
+                                if (mq == u) cnt[u] += 1.0f;
+                        }
+                    }
+                }
+                dst[p] = make_float4(cnt[0], cnt[1], cnt[2], cnt[3]);
+            }
     };
 
     // G of the thread's two microphones and KT bins, packed over the microphones
@@ -172,6 +199,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         cp_async_wait_all();
         __syncthreads();
         produce<KT, KIND, 1>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, j.s, t0 * PT);
+        chain_counts(pdb, pvb, pcb);
         __syncthreads();
     }
     for (int64_t tile = t0; tile < t1; ++tile) {
@@ -190,6 +218,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             const int nb = (int)((tile + 1 - t0) % 3);
             produce<KT, KIND, 1>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, j.s,
                                  (tile + 1) * PT);
+            chain_counts(pdb + nb * PT * 12, pvb + nb * PT, pcb + nb * PT);
         }
         for (int p = 0; p < PT; ++p) {
             const ulonglong2 z0 = C.za[((size_t)p * NS + s) * TP + tp];
@@ -312,23 +341,8 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             // reflection-coefficient sums for the materials of the path's chain
             if constexpr (KIND == 0) if (j.do_k && pv[p]) {
                 rs_reduce<TPL>(y, tp, wm);
-                const uint32_t meta = __float_as_uint(pd[p * 12 + 8]);
-                const int len = meta & 15, matj = (meta >> 8) & 255;
-                const uint32_t c0 = __float_as_uint(pd[p * 12 + 9]), c1 = __float_as_uint(pd[p * 12 + 10]);
-                float cnt[kNV] = {0.f, 0.f, 0.f, 0.f};
-                if (a.reflection_mode == 1 || j.do_beta) {  // one material: the last hit's
-                    const int q = matj - j.mat_base;
-#pragma unroll
-                    for (int u = 0; u < kNV; ++u)
-                        if (q == u) cnt[u] = 1.0f;
-                } else {
-                    for (int q = 0; q < len; ++q) {
-                        const int mq = ((q < 4 ? (c0 >> (8 * q)) : (c1 >> (8 * (q - 4)))) & 255) - j.mat_base;
-#pragma unroll
-                        for (int u = 0; u < kNV; ++u)
-                            if (mq == u) cnt[u] += 1.0f;
-                    }
-                }
+                const float4 c4 = pcb[pb * PT + p];  // the chain's material counts, from the producer
+                const float cnt[kNV] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
                 for (int u = 0; u < kNV; ++u)
 #pragma unroll
@@ -607,7 +621,7 @@ cudaError_t launch_adjoint(const AccumArgs& a, const AdjointArgs& j, const Geom&
         attr_set = true;
     }
     dim3 grid((unsigned)(g.n_mb * g.n_bb), (unsigned)a.n_chunks);
-    const size_t smem = g.smem + (EMIT ? (size_t)3 * g.PT * 12 * 4 + 16 : 0);
+    const size_t smem = g.smem + (EMIT ? (size_t)3 * g.PT * 12 * 4 + 16 : 0) + (KIND == 0 ? (size_t)3 * g.PT * 16 + 16 : 0);
     note_launch();
     k_adjoint<KT, KIND, TPL, EMIT><<<grid, g.TP * g.NS, smem, s>>>(a, j, g);
     return cudaGetLastError();
