@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
 #pragma unroll
         for (int v = 0; v < VR; ++v) V[q][v] = 0.0f;
     // position gradients of the thread's two microphones (and the emitter, diffraction), packed
-    u64 dmx = 0ull, dmy = 0ull, dmz = 0ull, dex = 0ull, dey = 0ull, dez = 0ull;
-    // diffraction: the emitter direction is the same for both microphones of a pair, so the emitter gradient
-    // is summed over the pair first (three scalar registers instead of three packed pairs)
+    u64 dmx = 0ull, dmy = 0ull, dmz = 0ull;
+    // emitter gradient: its factors (the direction -unit(o - s) of a diffraction path, the chain jacobian of a
+    // specular one) are the same for both microphones of a pair, so it is summed over the pair first (three
+    // scalar registers instead of three packed pairs)
     float esx = 0.0f, esy = 0.0f, esz = 0.0f;
     // d ln T / dr at this subtile's first bin, without the -2/r spreading term: (-a, w); per bin: (-a_step, w_step)
     const float kbs = (float)(kb + s * KT);
@@ -307,18 +308,20 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                     const float4 j0 = *reinterpret_cast<const float4*>(jp);      // J00 J01 J02 J10
                     const float4 j1 = *reinterpret_cast<const float4*>(jp + 4);  // J11 J12 J20 J21
                     const float4 j2 = *reinterpret_cast<const float4*>(jp + 8);  // J22 drx dry drz
-                    dex = ffma2(pk2(j2.y, j2.y), dl, dex);
-                    dex = ffma2(pk2(-j0.x, -j0.x), gx, dex);
-                    dex = ffma2(pk2(-j0.w, -j0.w), gy, dex);
-                    dex = ffma2(pk2(-j1.z, -j1.z), gz, dex);
-                    dey = ffma2(pk2(j2.z, j2.z), dl, dey);
-                    dey = ffma2(pk2(-j0.y, -j0.y), gx, dey);
-                    dey = ffma2(pk2(-j1.x, -j1.x), gy, dey);
-                    dey = ffma2(pk2(-j1.w, -j1.w), gz, dey);
-                    dez = ffma2(pk2(j2.w, j2.w), dl, dez);
-                    dez = ffma2(pk2(-j0.z, -j0.z), gx, dez);
-                    dez = ffma2(pk2(-j1.y, -j1.y), gy, dez);
-                    dez = ffma2(pk2(-j2.x, -j2.x), gz, dez);
+                    const float2 dl2 = up2(dl), gx2 = up2(gx), gy2 = up2(gy), gz2 = up2(gz);
+                    const float sl = dl2.x + dl2.y, sx = gx2.x + gx2.y, sy = gy2.x + gy2.y, sz = gz2.x + gz2.y;
+                    esx = fmaf(j2.y, sl, esx);
+                    esx = fmaf(-j0.x, sx, esx);
+                    esx = fmaf(-j0.w, sy, esx);
+                    esx = fmaf(-j1.z, sz, esx);
+                    esy = fmaf(j2.z, sl, esy);
+                    esy = fmaf(-j0.y, sx, esy);
+                    esy = fmaf(-j1.x, sy, esy);
+                    esy = fmaf(-j1.w, sz, esy);
+                    esz = fmaf(j2.w, sl, esz);
+                    esz = fmaf(-j0.z, sx, esz);
+                    esz = fmaf(-j1.y, sy, esz);
+                    esz = fmaf(-j2.x, sz, esz);
                 } else {
                     dmx = ffma2(dl, ad[0], dmx);
                     dmy = ffma2(dl, ad[1], dmy);
@@ -363,10 +366,9 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             float* o = red + (size_t)tid * 6;
             o[0] = x.x; o[1] = y2.x; o[2] = z.x;
             o[3] = x.y; o[4] = y2.y; o[5] = z.y;
-            const float2 ex = up2(dex), ey = up2(dey), ez = up2(dez);
-            rede[tid * 3 + 0] = KIND == 1 ? esx : ex.x + ex.y;
-            rede[tid * 3 + 1] = KIND == 1 ? esy : ey.x + ey.y;
-            rede[tid * 3 + 2] = KIND == 1 ? esz : ez.x + ez.y;
+            rede[tid * 3 + 0] = esx;
+            rede[tid * 3 + 1] = esy;
+            rede[tid * 3 + 2] = esz;
         }
         __syncthreads();
         if (tid < g.MP && mic0 + tid < a.M) {  // microphone mic0 + tid: fixed-order sum over the subtiles
