@@ -995,10 +995,22 @@ def main():
             dist.destroy_process_group()
         return
 
+    # each stage's own device time, with the stages issued in order on one stream (in the timed steps the
+    # diffraction stage and the direct path run on a side stream beside the trace); the traversal fetch
+    # rates divide by these
+    ctx.set_stage_overlap(False)
+    serial = []
+    for i in range(3):
+        flush.fill_(i & 255)
+        serial.append(step()[1])
+    torch.cuda.synchronize()
+    ctx.set_stage_overlap(True)
+    stages_serial = {k: float(np.median([getattr(s, k) for s in serial]))
+                     for k in ("ms_trace", "ms_diffraction", "ms_accumulate", "ms_total")}
     signal = measure_signal(st, torch, ctx, out, wl)
     scene_update = measure_scene_update(st, torch, ctx, sc, wl)
-    traversal = measure_traversal(st, torch, wl, float(np.median([s.ms_trace for s in st_list])),
-                                  float(np.median([s.ms_diffraction for s in st_list])), peaks["hbm_gbs"])
+    traversal = measure_traversal(st, torch, wl, stages_serial["ms_trace"], stages_serial["ms_diffraction"],
+                                  peaks["hbm_gbs"])
     adjoint = None
     if not args.no_adjoint:
         adjoint = {"gradient workload (shoebox, 4 materials x 16 bands, 32 mics, 128 bins, 10k rays x 3)":
@@ -1041,7 +1053,10 @@ def main():
                          "visible_records": s0.visible_records, "diffraction_candidates": s0.candidates,
                          "diffraction_kept": s0.candidates_kept, "terms": s0.terms,
                          "ms_trace": s0.ms_trace, "ms_diffraction": s0.ms_diffraction,
-                         "ms_accumulate": s0.ms_accumulate},
+                         "ms_accumulate": s0.ms_accumulate,
+                         "stages": "diffraction stage and direct path on a side stream beside the trace; the "
+                                   "specular accumulation after both"},
+            "stages_serial": stages_serial,
             "roofline": roofline, "roofline_diffraction": roofline_diffraction, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "adjoint": adjoint,
             "traversal": traversal, "signal": signal, "scene_update": scene_update, "batched": batched, "batched_directional": batched_dir,

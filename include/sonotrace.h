@@ -105,8 +105,11 @@ typedef struct st_stats {
     int64_t candidates_kept;    /* diffraction samples passing the filters */
     int64_t terms;              /* (path, microphone, bin) terms accumulated */
     float ms_trace;             /* device time of ray generation + bounces, ms */
-    float ms_diffraction;       /* device time of sampling + filters, ms */
-    float ms_accumulate;        /* device time of spectrum accumulation, ms */
+    float ms_diffraction;       /* device time of sampling + filters, ms (with the stage overlap of
+                                   st_set_stage_overlap on, this runs beside the trace, so the stage times
+                                   overlap) */
+    float ms_accumulate;        /* device time of spectrum accumulation, ms (from the end of the trace; with
+                                   the overlap on it includes the wait for the diffraction stage) */
     float ms_total;             /* device time of the whole call, ms */
     float ms_accum_kernel;      /* device time of the accumulator kernel launches alone, ms */
     int32_t accum_launches;     /* number of accumulator kernel launches */
@@ -354,6 +357,14 @@ st_status st_simulate_batch(st_ctx* ctx, int32_t n_jobs, const st_job* jobs, con
 /* Sets the context's launch shapes (as st_autotune does); later st_simulate calls use them.  ST_ERR_ARG for
  * a null pointer or a value outside the ranges above. */
 st_status st_set_tune(st_ctx* ctx, const st_tune* tune);
+/* Stage overlap of st_simulate (on by default): the diffraction stage (sampling, filters and line of
+ * sight of Sec. III-D, then its accumulation, Eq. 7-8) and the direct path (Eq. 11-12) run on a side
+ * stream of the context while the specular paths are traced (Algorithm 1) on the context's stream;
+ * the specular accumulation (Eq. 2-4) starts once both are done.  The stages share no buffer, so the
+ * results are identical either way.  0 issues every stage on the context's stream in the order trace,
+ * diffraction, accumulation (stage times that do not overlap).  The side stream is created on the
+ * first overlapped call.  ST_ERR_ARG for a null context. */
+st_status st_set_stage_overlap(st_ctx* ctx, int32_t on);
 /* Times candidate launch shapes on one sample job through the single-pose path and writes the
  * fastest to *out (also kept as the context's default for st_simulate).  Replaces the context's
  * emitter, receivers and frequency grid with the sample job's (omni).  Synchronises. */

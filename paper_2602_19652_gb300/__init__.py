@@ -266,6 +266,11 @@ class Context:
         t = Tune(rays_per_block, mic_pairs_per_cta, smem_kb, stack_depth, refill_lanes, bins_per_thread)
         self._check(self.L.st_set_tune(self.h, C.byref(t)))
 
+    def set_stage_overlap(self, on: bool):
+        """Diffraction stage and direct path beside the trace on a side stream (default), or every stage in
+        order on the context's stream (stage times that do not overlap); the results are the same."""
+        self._check(self.L.st_set_stage_overlap(self.h, 1 if on else 0))
+
     def autotune(self, job: "BatchJob", params: SimParams | None = None) -> Tune:
         t = Tune()
         self._check(self.L.st_autotune(self.h, C.byref(job.job), None if params is None else C.byref(params),

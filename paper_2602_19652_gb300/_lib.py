@@ -99,6 +99,7 @@ SIGNATURES = {
     "st_impulse_response": (I32, [P, P, I32, I32, I32, F64, F64, F64, I32, P, P, I32, I32, P]),
     "st_set_frequency_grid": (I32, [P, I32, P]),
     "st_set_tune": (I32, [P, P]),
+    "st_set_stage_overlap": (I32, [P, I32]),
     "st_inject_alloc_failure": (None, [I64]),
     "st_accumulate_specular_noalloc": (I32, [P, P, P, P, P, I64, I32, P, I64, P, I32, I32, F64, F64, I32, I32, P, P, P,
                                              P, P, P]),

@@ -123,6 +123,12 @@ struct st_ctx {
     DevBuf hit_tri, hit_t, vis_q, los_q, trav_cnt;
     DevBuf rec_mask;                 // per-microphone receiver test: visible microphones of each record  // lane-refill traversal: closest hits, query queues, counters
     cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // stage overlap: the diffraction stage and the direct path of a simulate run on a side stream while
+    // the specular paths are traced (own copies of the buffers both would otherwise share)
+    bool overlap = true;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    DevBuf los_keys, los_scr, dflags, dscan, didx, dscratch, dpartial;
 };
 
 // Buffers and the recorded graph of the last batch structure.
@@ -160,6 +166,12 @@ struct BatchState {
     cudaStream_t main = nullptr;     // the batch runs here (capturable even when the context's stream is
                                      // the legacy default stream), ordered after/before the context's stream
     std::vector<cudaEvent_t> events;    // context -> main, main -> context
+    // stage overlap (as in st_simulate): diffraction, its compaction and the direct visibility on a side
+    // branch beside the trace; own scan scratch for the candidates
+    bool overlap = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    DevBuf dscratch;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -364,6 +376,7 @@ st_status st_destroy(st_ctx* c) {
     if (!c) return ST_ERR_ARG;
     enter(c);
     cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     for (DevBuf* b : {&c->mic_q, &c->mic_tab, &c->tables.bw}) release(*b);
     for (DevBuf* b : {&c->dirs, &c->etab, &c->perm, &c->ord_keys, &c->ord_scr, &c->th_keys, &c->th_scr, &c->vs_keys, &c->vs_scr, &c->mics, &c->st_o[0], &c->st_o[1], &c->st_o[2], &c->st_d[0], &c->st_d[1],
                       &c->st_d[2], &c->st_r, &c->st_prev, &c->q0, &c->q1, &c->counts, &c->queries, &c->flags, &c->R, &c->rec_tri,
@@ -382,12 +395,22 @@ st_status st_destroy(st_ctx* c) {
         release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (DevBuf* b : {&c->los_keys, &c->los_scr, &c->dflags, &c->dscan, &c->didx, &c->dscratch, &c->dpartial}) release(*b);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->batch) {
         batch_release_public(*c->batch);
         delete c->batch;
     }
     for (st_scene* sc : c->scenes) scene_free(sc);
     delete c;
+    return ST_OK;
+}
+
+st_status st_set_stage_overlap(st_ctx* c, int32_t on) {
+    if (!c) return ST_ERR_ARG;
+    c->overlap = on != 0;
     return ST_OK;
 }
 
@@ -897,10 +920,13 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
     // Scenes whose hierarchy and triangles are well beyond L2 trace their visibility queries in the Morton
     // order of the hit points (all go to one point, so neighbours in that order share most nodes)
     const bool vsort = S.n_tris >= kVisSortTris && N > 1 && !per_mic;
-    if (vsort || K > 1) {  // (the line-of-sight queue of the diffraction candidates is sorted likewise)
-        const int64_t nk = std::max<int64_t>(vsort ? N : 1, K);
-        CKC(c, grow(c->vs_keys, (size_t)nk * 8), "alloc");
-        CKC(c, grow(c->vs_scr, sort_scratch_bytes(nk)), "alloc");
+    if (vsort) {
+        CKC(c, grow(c->vs_keys, (size_t)N * 8), "alloc");
+        CKC(c, grow(c->vs_scr, sort_scratch_bytes(N)), "alloc");
+    }
+    if (K > 1) {  // the line-of-sight queue of the diffraction candidates is sorted likewise (own buffers)
+        CKC(c, grow(c->los_keys, (size_t)K * 8), "alloc");
+        CKC(c, grow(c->los_scr, sort_scratch_bytes(K)), "alloc");
     }
     if (c->n_theta > 0 && NB > 1) {  // emitter-table row order of the specular path list
         CKC(c, grow(c->th_keys, (size_t)NB * 8), "alloc");
@@ -939,8 +965,14 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
         CKC(c, grow(c->mat_off, (size_t)(S.n_mat + 1) * 4), "alloc");
         CKC(c, grow(c->mat_scr, material_order_scratch(K)), "alloc");
     }
-    const int32_t chunks = std::max(chunks_spec, chunks_diff);
-    CKC(c, grow(c->partial, (size_t)chunks * M * F * 8), "alloc");
+    CKC(c, grow(c->partial, (size_t)chunks_spec * M * F * 8), "alloc");
+    if (K > 0) {  // the diffraction stage's compaction and partial spectra (it may run beside the specular one)
+        CKC(c, grow(c->dflags, (size_t)K * 4), "alloc");
+        CKC(c, grow(c->dscan, (size_t)K * 4), "alloc");
+        CKC(c, grow(c->didx, (size_t)K * 4), "alloc");
+        CKC(c, grow(c->dscratch, scan_scratch_bytes(K)), "alloc");
+        CKC(c, grow(c->dpartial, (size_t)chunks_diff * M * F * 8), "alloc");
+    }
 
     float2* out = static_cast<float2*>(spectra_out);
     const int64_t MF = (int64_t)M * F;
@@ -972,108 +1004,147 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
         fwd[2] = (vz + q[0] * tz) + c2z;
     }
 
-    // ---- Algorithm 1
-    if (p.components & ST_COMP_SPECULAR && N > 0) {
-        NvtxRange range("st_simulate: trace");
-        TraceArgs ta{};
-        scene_trav_args(ta, S);
-        ta.visits = c->count_visits ? qctr + 2 : nullptr;
-        ta.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
-        ta.restarts = qctr + 6;
-        ta.refill = c->tune.refill_lanes;
-        ta.nrm = ptr<float>(S.nrm);
-        memcpy(ta.s, c->s, 12);
-        memcpy(ta.q, c->q, 16);
-        ta.R = ptr<float>(c->R);
-        ta.dirs = ptr<float>(c->dirs);
-        ta.perm = ptr<uint32_t>(c->perm);
-        ta.N = N;
-        ta.B = B;
-        ta.r_max = p.max_distance;
-        ta.t_min = p.t_min;
-        ta.los_eps = p.los_eps;
-        ta.ox = ptr<float>(c->st_o[0]);
-        ta.oy = ptr<float>(c->st_o[1]);
-        ta.oz = ptr<float>(c->st_o[2]);
-        ta.dx = ptr<float>(c->st_d[0]);
-        ta.dy = ptr<float>(c->st_d[1]);
-        ta.dz = ptr<float>(c->st_d[2]);
-        ta.racc = ptr<double>(c->st_r);
-        ta.prev = ptr<int32_t>(c->st_prev);
-        ta.q_in = ptr<uint32_t>(c->q0);
-        ta.q_out = ptr<uint32_t>(c->q1);
-        ta.n_in = cnt + 0;
-        ta.n_out = cnt + 1;
-        ta.rec_tri = ptr<int32_t>(c->rec_tri);
-        ta.rec_p = ptr<float>(c->rec_p);
-        ta.rec_d = ptr<float>(c->rec_d);
-        ta.rec_r = ptr<double>(c->rec_r);
-        ta.rec_los = ptr<uint8_t>(c->rec_los);
-        ta.flags = ptr<uint32_t>(c->flags);
-        ta.queries = qctr;
-        ta.hit_tri = ptr<int32_t>(c->hit_tri);
-        ta.hit_t = ptr<float>(c->hit_t);
-        ta.vis_q = ptr<uint32_t>(c->vis_q);
-        ta.vis_n = ptr<uint32_t>(c->trav_cnt);
-        ta.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 16);
-        ta.rec_mask = per_mic ? ptr<uint64_t>(c->rec_mask) : nullptr;
-        ta.mics = ptr<float>(c->mics);
-        ta.M = M;
-        ta.sort_keys = vsort ? ptr<uint64_t>(c->vs_keys) : nullptr;
-        ta.sort_scr = vsort ? c->vs_scr.p : nullptr;
-        for (int k = 0; k < 3; ++k) {
-            const float ext = S.bounds_hi[k] - S.bounds_lo[k];
-            ta.blo[k] = S.bounds_lo[k];
-            ta.bscale[k] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+    // ---- stage overlap: the diffraction stage (sampling and line of sight, Sec. III-D; its accumulation)
+    // and the direct path run on the context's side stream while the specular paths are traced on the
+    // context's stream, filling the traversal launches' tails; the specular accumulation waits for both
+    // and runs alone.  The stages share no buffer (the diffraction stage has its own sort, compaction and
+    // partial-spectra buffers) and no result depends on the order (fixed-order sums, compaction by scan).
+    const bool overlap = c->overlap && (p.components & ST_COMP_SPECULAR) && N > 0 &&
+                         (K > 0 || (p.components & ST_COMP_DIRECT));
+    cudaStream_t s2 = s;
+    bool joined = false;
+    if (overlap) {
+        if (!c->side) {
+            CKC(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+            CKC(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
+            CKC(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
         }
-        CKC(c, trace_rays(ta, s, c->tune.rays_per_block > 0 ? c->tune.rays_per_block : 128), "trace");
+        CKC(c, cudaEventRecord(c->ev_fork, s), "fork");
+        CKC(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+        s2 = c->side;
     }
-    if (stats) CKC(c, cudaEventRecord(c->ev[1], s), "event");
+    // a call that fails between the fork and the join still orders the side stream's work before the
+    // context stream's next work
+    struct JoinGuard {
+        st_ctx* c;
+        cudaStream_t s;
+        const bool& active;
+        const bool& done;
+        ~JoinGuard() {
+            if (active && !done) {
+                cudaEventRecord(c->ev_join, c->side);
+                cudaStreamWaitEvent(s, c->ev_join, 0);
+            }
+        }
+    } join_guard{c, s, overlap, joined};
 
-    // ---- diffraction (Sec. III-D)
-    if (K > 0) {
-        NvtxRange range("st_simulate: diffraction sampling");
-        DiffArgs da{};
-        scene_trav_args(da, S);
-        da.visits = c->count_visits ? qctr + 2 : nullptr;
-        da.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
-        da.restarts = qctr + 6;
-        da.refill = c->tune.refill_lanes;
-        da.nrm = ptr<float>(S.nrm);
-        da.verts = ptr<float>(S.verts);
-        da.tris = ptr<int32_t>(S.tris);
-        da.n_obj = S.n_obj;
-        da.mesh_tris = ptr<int32_t>(S.mesh_tris);
-        da.mesh_off = ptr<int64_t>(S.mesh_off);
-        da.cdf = ptr<uint64_t>(S.cdf);
-        da.sample_off = ptr<int64_t>(S.sample_off);
-        da.K = K;
-        da.seed = p.seed;
-        da.pose = p.pose_index;
-        memcpy(da.s, c->s, 12);
-        memcpy(da.fwd, fwd, 12);
-        da.cos_fov = c->fov_half >= (float)M_PI ? -2.0f : (float)cos((double)c->fov_half);
-        da.cos_inc = (float)cos((double)p.theta_inc_rad);
-        da.t_min = p.t_min;
-        da.los_eps = p.los_eps;
-        da.cand_tri = ptr<int32_t>(c->cand_tri);
-        da.cand_p = ptr<float>(c->cand_p);
-        da.keep = ptr<uint8_t>(c->keep);
-        da.flags = ptr<uint32_t>(c->flags);
-        da.queries = qctr;
-        da.los_q = ptr<uint32_t>(c->los_q);
-        da.los_n = ptr<uint32_t>(c->trav_cnt) + 1;
-        da.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 32);
-        da.sort_keys = K > 1 ? ptr<uint64_t>(c->vs_keys) : nullptr;
-        da.sort_scr = K > 1 ? c->vs_scr.p : nullptr;
-        for (int k = 0; k < 3; ++k) {
-            const float ext = S.bounds_hi[k] - S.bounds_lo[k];
-            da.blo[k] = S.bounds_lo[k];
-            da.bscale[k] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+    auto stage_trace = [&]() -> st_status {
+        // ---- Algorithm 1
+        if (p.components & ST_COMP_SPECULAR && N > 0) {
+            NvtxRange range("st_simulate: trace");
+            TraceArgs ta{};
+            scene_trav_args(ta, S);
+            ta.visits = c->count_visits ? qctr + 2 : nullptr;
+            ta.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
+            ta.restarts = qctr + 6;
+            ta.refill = c->tune.refill_lanes;
+            ta.nrm = ptr<float>(S.nrm);
+            memcpy(ta.s, c->s, 12);
+            memcpy(ta.q, c->q, 16);
+            ta.R = ptr<float>(c->R);
+            ta.dirs = ptr<float>(c->dirs);
+            ta.perm = ptr<uint32_t>(c->perm);
+            ta.N = N;
+            ta.B = B;
+            ta.r_max = p.max_distance;
+            ta.t_min = p.t_min;
+            ta.los_eps = p.los_eps;
+            ta.ox = ptr<float>(c->st_o[0]);
+            ta.oy = ptr<float>(c->st_o[1]);
+            ta.oz = ptr<float>(c->st_o[2]);
+            ta.dx = ptr<float>(c->st_d[0]);
+            ta.dy = ptr<float>(c->st_d[1]);
+            ta.dz = ptr<float>(c->st_d[2]);
+            ta.racc = ptr<double>(c->st_r);
+            ta.prev = ptr<int32_t>(c->st_prev);
+            ta.q_in = ptr<uint32_t>(c->q0);
+            ta.q_out = ptr<uint32_t>(c->q1);
+            ta.n_in = cnt + 0;
+            ta.n_out = cnt + 1;
+            ta.rec_tri = ptr<int32_t>(c->rec_tri);
+            ta.rec_p = ptr<float>(c->rec_p);
+            ta.rec_d = ptr<float>(c->rec_d);
+            ta.rec_r = ptr<double>(c->rec_r);
+            ta.rec_los = ptr<uint8_t>(c->rec_los);
+            ta.flags = ptr<uint32_t>(c->flags);
+            ta.queries = qctr;
+            ta.hit_tri = ptr<int32_t>(c->hit_tri);
+            ta.hit_t = ptr<float>(c->hit_t);
+            ta.vis_q = ptr<uint32_t>(c->vis_q);
+            ta.vis_n = ptr<uint32_t>(c->trav_cnt);
+            ta.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 16);
+            ta.rec_mask = per_mic ? ptr<uint64_t>(c->rec_mask) : nullptr;
+            ta.mics = ptr<float>(c->mics);
+            ta.M = M;
+            ta.sort_keys = vsort ? ptr<uint64_t>(c->vs_keys) : nullptr;
+            ta.sort_scr = vsort ? c->vs_scr.p : nullptr;
+            for (int k = 0; k < 3; ++k) {
+                const float ext = S.bounds_hi[k] - S.bounds_lo[k];
+                ta.blo[k] = S.bounds_lo[k];
+                ta.bscale[k] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+            }
+            CKC(c, trace_rays(ta, s, c->tune.rays_per_block > 0 ? c->tune.rays_per_block : 128), "trace");
         }
-        CKC(c, diffraction_sample(da, s), "diffraction");
-    }
-    if (stats) CKC(c, cudaEventRecord(c->ev[2], s), "event");
+        return ST_OK;
+    };
+    auto stage_diffraction = [&]() -> st_status {
+        // ---- diffraction (Sec. III-D)
+        if (K > 0) {
+            NvtxRange range("st_simulate: diffraction sampling");
+            DiffArgs da{};
+            scene_trav_args(da, S);
+            da.visits = c->count_visits ? qctr + 2 : nullptr;
+            da.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
+            da.restarts = qctr + 6;
+            da.refill = c->tune.refill_lanes;
+            da.nrm = ptr<float>(S.nrm);
+            da.verts = ptr<float>(S.verts);
+            da.tris = ptr<int32_t>(S.tris);
+            da.n_obj = S.n_obj;
+            da.mesh_tris = ptr<int32_t>(S.mesh_tris);
+            da.mesh_off = ptr<int64_t>(S.mesh_off);
+            da.cdf = ptr<uint64_t>(S.cdf);
+            da.sample_off = ptr<int64_t>(S.sample_off);
+            da.K = K;
+            da.seed = p.seed;
+            da.pose = p.pose_index;
+            memcpy(da.s, c->s, 12);
+            memcpy(da.fwd, fwd, 12);
+            da.cos_fov = c->fov_half >= (float)M_PI ? -2.0f : (float)cos((double)c->fov_half);
+            da.cos_inc = (float)cos((double)p.theta_inc_rad);
+            da.t_min = p.t_min;
+            da.los_eps = p.los_eps;
+            da.cand_tri = ptr<int32_t>(c->cand_tri);
+            da.cand_p = ptr<float>(c->cand_p);
+            da.keep = ptr<uint8_t>(c->keep);
+            da.flags = ptr<uint32_t>(c->flags);
+            da.queries = qctr;
+            da.los_q = ptr<uint32_t>(c->los_q);
+            da.los_n = ptr<uint32_t>(c->trav_cnt) + 1;
+            da.ctr = reinterpret_cast<unsigned long long*>(ptr<char>(c->trav_cnt) + 32);
+            da.sort_keys = K > 1 ? ptr<uint64_t>(c->los_keys) : nullptr;
+            da.sort_scr = K > 1 ? c->los_scr.p : nullptr;
+            for (int k = 0; k < 3; ++k) {
+                const float ext = S.bounds_hi[k] - S.bounds_lo[k];
+                da.blo[k] = S.bounds_lo[k];
+                da.bscale[k] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+            }
+            if (stats) CKC(c, cudaEventRecord(c->ev[8], s2), "event");
+            CKC(c, diffraction_sample(da, s2), "diffraction");
+            if (stats) CKC(c, cudaEventRecord(c->ev[9], s2), "event");
+        }
+        return ST_OK;
+    };
 
     const float inv_dtheta = c->n_theta > 1 ? (float)((c->n_theta - 1) / M_PI) : 0.0f;
     const double l2_10_over_20 = log2(10.0) / 20.0;
@@ -1149,107 +1220,148 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
     };
 
     int n_accum = 0;  // bit 0: specular launch issued, bit 1: diffraction launch issued
-    // ---- specular accumulation (Eq. 2-4)
-    if (p.components & ST_COMP_SPECULAR && NB > 0) {
-        NvtxRange range("st_simulate: specular accumulation");
-        CKC(c, flags_visible_records(ptr<int32_t>(c->rec_tri), ptr<uint8_t>(c->rec_los), NB, ptr<uint32_t>(c->sflags), s),
-            "flags");
-        CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, cnt + 2, c->scratch.p, s),
-            "scan");
-        CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, ptr<uint32_t>(c->sidx), s),
-            "compact");
-        ga.count = cnt + 2;
-        ga.out = &c->paths;
-        if (ga.has_etab && NB > 1) {  // paths in emitter-table row order: a tile's paths share table rows
-            CKC(c, theta_order(ga, NB, ptr<uint32_t>(c->sidx), ptr<uint64_t>(c->th_keys), c->th_scr.p, s), "order");
+    auto stage_specular = [&]() -> st_status {
+        // ---- specular accumulation (Eq. 2-4)
+        if (p.components & ST_COMP_SPECULAR && NB > 0) {
+            NvtxRange range("st_simulate: specular accumulation");
+            CKC(c, flags_visible_records(ptr<int32_t>(c->rec_tri), ptr<uint8_t>(c->rec_los), NB, ptr<uint32_t>(c->sflags), s),
+                "flags");
+            CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, cnt + 2, c->scratch.p, s),
+                "scan");
+            CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, ptr<uint32_t>(c->sidx), s),
+                "compact");
+            ga.count = cnt + 2;
+            ga.out = &c->paths;
+            if (ga.has_etab && NB > 1) {  // paths in emitter-table row order: a tile's paths share table rows
+                CKC(c, theta_order(ga, NB, ptr<uint32_t>(c->sidx), ptr<uint64_t>(c->th_keys), c->th_scr.p, s), "order");
+            }
+            CKC(c, gather_specular(ga, s), "gather");
+            AccumArgs x = aa;
+            x.kind = 0;
+            x.n_paths = NB;
+            x.d_count = cnt + 2;
+            set_paths(x, c->paths);
+            x.mask = per_mic ? ptr<uint64_t>(c->paths.mask) : nullptr;
+            x.n_chunks = chunks_spec;
+            // the side stream's stages end before the accumulation starts, so that it runs alone
+            if (overlap) {
+                CKC(c, cudaEventRecord(c->ev_join, s2), "join");
+                CKC(c, cudaStreamWaitEvent(s, c->ev_join, 0), "join");
+                joined = true;
+            }
+            if (stats) CKC(c, cudaEventRecord(c->ev[4], s), "event");
+            CKC(c, accumulate(x, s), "accumulate specular");
+            if (stats) CKC(c, cudaEventRecord(c->ev[5], s), "event");
+            n_accum++;
+            CKC(c, reduce_partials(ptr<float2>(c->partial), chunks_spec, MF, out, s), "reduce");
         }
-        CKC(c, gather_specular(ga, s), "gather");
-        AccumArgs x = aa;
-        x.kind = 0;
-        x.n_paths = NB;
-        x.d_count = cnt + 2;
-        set_paths(x, c->paths);
-        x.mask = per_mic ? ptr<uint64_t>(c->paths.mask) : nullptr;
-        x.n_chunks = chunks_spec;
-        if (stats) CKC(c, cudaEventRecord(c->ev[4], s), "event");
-        CKC(c, accumulate(x, s), "accumulate specular");
-        if (stats) CKC(c, cudaEventRecord(c->ev[5], s), "event");
-        n_accum++;
-        CKC(c, reduce_partials(ptr<float2>(c->partial), chunks_spec, MF, out, s), "reduce");
-    }
-    // ---- diffraction accumulation (Eq. 7-8)
-    if (K > 0) {
-        NvtxRange range("st_simulate: diffraction accumulation");
-        CKC(c, flags_from_u8(ptr<uint8_t>(c->keep), K, ptr<uint32_t>(c->sflags), s), "flags");
-        CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), K, cnt + 3, c->scratch.p, s),
-            "scan");
-        CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), K, ptr<uint32_t>(c->sidx), s),
-            "compact");
-        ga.count = cnt + 3;
-        ga.out = &c->paths_diff;
-        if (diff_mma)  // path list grouped by material (stable: within a material the compaction order)
-            CKC(c, material_order(cnt + 3, K, ptr<int32_t>(c->cand_tri), ptr<int32_t>(S.tri_mat), S.n_mat,
-                                  ptr<uint32_t>(c->sidx), ptr<uint32_t>(c->mat_off), c->mat_scr.p, s),
-                "material order");
-        CKC(c, gather_diffraction(ga, s), "gather");
-        AccumArgs x = aa;
-        x.kind = 1;
-        x.n_paths = K;
-        x.d_count = cnt + 3;
-        set_paths(x, c->paths_diff);
-        x.n_chunks = chunks_diff;
-        if (stats) CKC(c, cudaEventRecord(c->ev[6], s), "event");
-        if (diff_mma)
-            CKC(c, accumulate_diffraction_mma(x, ptr<uint32_t>(c->mat_off), s), "accumulate diffraction");
-        else
-            CKC(c, accumulate(x, s), "accumulate diffraction");
-        if (stats) CKC(c, cudaEventRecord(c->ev[7], s), "event");
-        n_accum += 2;
-        CKC(c, reduce_partials(ptr<float2>(c->partial), chunks_diff, MF, out + MF, s), "reduce");
-    }
-    // ---- direct path (Eq. 11-12)
-    if (p.components & ST_COMP_DIRECT) {
-        NvtxRange range("st_simulate: direct path");
-        DirectArgs dv{};
-        scene_trav_args(dv, S);
-        dv.visits = c->count_visits ? qctr + 2 : nullptr;
-        dv.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
-        dv.restarts = qctr + 6;
-        dv.refill = c->tune.refill_lanes;
-        memcpy(dv.s, c->s, 12);
-        dv.mics = ptr<float>(c->mics);
-        dv.M = M;
-        dv.t_min = p.t_min;
-        dv.los_eps = p.los_eps;
-        dv.vis = ptr<uint8_t>(c->dvis);
-        dv.flags = ptr<uint32_t>(c->flags);
-        dv.queries = qctr;
-        CKC(c, direct_visibility(dv, s), "direct visibility");
-        DirectAccumArgs da{};
-        memcpy(da.s, c->s, 12);
-        da.mics = ptr<float>(c->mics);
-        da.M = M;
-        da.F = F;
-        da.vis = ptr<uint8_t>(c->dvis);
-        da.f_lo = c->f_lo;
-        da.df = T.df;
-        da.c = p.c;
-        da.a0 = p.alpha0_db_m;
-        da.a1 = p.alpha1_db_m_khz;
-        da.gain = p.direct_gain;
-        da.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
-        da.n_theta = c->n_theta;
-        memcpy(da.fwd, fwd, 12);
-        da.mic_tab = c->mic_nb > 0 ? ptr<float>(c->mic_tab) : nullptr;
-        da.mic_q = (c->mic_nb > 0 && c->has_mic_q) ? ptr<float>(c->mic_q) : nullptr;
-        da.n_el = c->n_el;
-        da.n_az = c->n_az;
-        da.n_bands = S.n_bands;
-        da.bw = ptr<float2>(T.bw);
-        da.out = out + 2 * MF;
-        CKC(c, accumulate_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), s), "direct");
+        return ST_OK;
+    };
+    auto stage_diffraction_accumulation = [&]() -> st_status {
+        // ---- diffraction accumulation (Eq. 7-8)
+        if (K > 0) {
+            NvtxRange range("st_simulate: diffraction accumulation");
+            CKC(c, flags_from_u8(ptr<uint8_t>(c->keep), K, ptr<uint32_t>(c->dflags), s2), "flags");
+            CKC(c, exclusive_scan_u32(ptr<uint32_t>(c->dflags), ptr<uint32_t>(c->dscan), K, cnt + 3, c->dscratch.p, s2),
+                "scan");
+            CKC(c, compact_indices(ptr<uint32_t>(c->dflags), ptr<uint32_t>(c->dscan), K, ptr<uint32_t>(c->didx), s2),
+                "compact");
+            GatherArgs gd = ga;
+            gd.idx = ptr<uint32_t>(c->didx);
+            gd.count = cnt + 3;
+            gd.out = &c->paths_diff;
+            if (diff_mma)  // path list grouped by material (stable: within a material the compaction order)
+                CKC(c, material_order(cnt + 3, K, ptr<int32_t>(c->cand_tri), ptr<int32_t>(S.tri_mat), S.n_mat,
+                                      ptr<uint32_t>(c->didx), ptr<uint32_t>(c->mat_off), c->mat_scr.p, s2),
+                    "material order");
+            CKC(c, gather_diffraction(gd, s2), "gather");
+            AccumArgs x = aa;
+            x.kind = 1;
+            x.n_paths = K;
+            x.d_count = cnt + 3;
+            set_paths(x, c->paths_diff);
+            x.n_chunks = chunks_diff;
+            x.partial = ptr<float2>(c->dpartial);
+            if (stats) CKC(c, cudaEventRecord(c->ev[6], s2), "event");
+            if (diff_mma)
+                CKC(c, accumulate_diffraction_mma(x, ptr<uint32_t>(c->mat_off), s2), "accumulate diffraction");
+            else
+                CKC(c, accumulate(x, s2), "accumulate diffraction");
+            if (stats) CKC(c, cudaEventRecord(c->ev[7], s2), "event");
+            n_accum += 2;
+            CKC(c, reduce_partials(ptr<float2>(c->dpartial), chunks_diff, MF, out + MF, s2), "reduce");
+        }
+        return ST_OK;
+    };
+    auto stage_direct = [&]() -> st_status {
+        // ---- direct path (Eq. 11-12)
+        if (p.components & ST_COMP_DIRECT) {
+            NvtxRange range("st_simulate: direct path");
+            DirectArgs dv{};
+            scene_trav_args(dv, S);
+            dv.visits = c->count_visits ? qctr + 2 : nullptr;
+            dv.stack_limit = c->tune.stack_depth > 0 ? std::min(c->tune.stack_depth, kStack) : kStack;
+            dv.restarts = qctr + 6;
+            dv.refill = c->tune.refill_lanes;
+            memcpy(dv.s, c->s, 12);
+            dv.mics = ptr<float>(c->mics);
+            dv.M = M;
+            dv.t_min = p.t_min;
+            dv.los_eps = p.los_eps;
+            dv.vis = ptr<uint8_t>(c->dvis);
+            dv.flags = ptr<uint32_t>(c->flags);
+            dv.queries = qctr;
+            CKC(c, direct_visibility(dv, s2), "direct visibility");
+            DirectAccumArgs da{};
+            memcpy(da.s, c->s, 12);
+            da.mics = ptr<float>(c->mics);
+            da.M = M;
+            da.F = F;
+            da.vis = ptr<uint8_t>(c->dvis);
+            da.f_lo = c->f_lo;
+            da.df = T.df;
+            da.c = p.c;
+            da.a0 = p.alpha0_db_m;
+            da.a1 = p.alpha1_db_m_khz;
+            da.gain = p.direct_gain;
+            da.etab = c->n_theta > 0 ? ptr<float>(c->etab) : nullptr;
+            da.n_theta = c->n_theta;
+            memcpy(da.fwd, fwd, 12);
+            da.mic_tab = c->mic_nb > 0 ? ptr<float>(c->mic_tab) : nullptr;
+            da.mic_q = (c->mic_nb > 0 && c->has_mic_q) ? ptr<float>(c->mic_q) : nullptr;
+            da.n_el = c->n_el;
+            da.n_az = c->n_az;
+            da.n_bands = S.n_bands;
+            da.bw = ptr<float2>(T.bw);
+            da.out = out + 2 * MF;
+            CKC(c, accumulate_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), s2), "direct");
+        } else {
+            CKC(c, cudaMemsetAsync(c->dvis.p, 0, (size_t)M, s2), "memset");
+        }
+        return ST_OK;
+    };
+
+    if (overlap) {  // side stream: diffraction, its accumulation, the direct path; context stream: the trace
+        st_status r = stage_diffraction();
+        if (r == ST_OK) r = stage_diffraction_accumulation();
+        if (r == ST_OK) r = stage_direct();
+        if (r == ST_OK) r = stage_trace();
+        if (r == ST_OK && stats) r = cudaEventRecord(c->ev[1], s) == cudaSuccess ? ST_OK : fail(c, ST_ERR_CUDA, "event");
+        if (r == ST_OK) r = stage_specular();
+        if (r == ST_OK && !joined) {
+            CKC(c, cudaEventRecord(c->ev_join, s2), "join");
+            CKC(c, cudaStreamWaitEvent(s, c->ev_join, 0), "join");
+            joined = true;
+        }
+        if (r != ST_OK) return r;
     } else {
-        CKC(c, cudaMemsetAsync(c->dvis.p, 0, (size_t)M, s), "memset");
+        st_status r = stage_trace();
+        if (r == ST_OK && stats) r = cudaEventRecord(c->ev[1], s) == cudaSuccess ? ST_OK : fail(c, ST_ERR_CUDA, "event");
+        if (r == ST_OK) r = stage_diffraction();
+        if (r == ST_OK) r = stage_specular();
+        if (r == ST_OK) r = stage_diffraction_accumulation();
+        if (r == ST_OK) r = stage_direct();
+        if (r != ST_OK) return r;
     }
     if (stats) CKC(c, cudaEventRecord(c->ev[3], s), "event");
 
@@ -1288,11 +1400,16 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
         stats->candidates = K;
         stats->candidates_kept = h[3];
         float ms;
+        // with the stage overlap the diffraction stage runs beside the trace, and the accumulation stage (from
+        // the end of the trace) includes the wait for the side stream
         cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
         stats->ms_trace = ms;
-        cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
-        stats->ms_diffraction = ms;
-        cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+        stats->ms_diffraction = 0.0f;
+        if (K > 0) {
+            cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]);
+            stats->ms_diffraction = ms;
+        }
+        cudaEventElapsedTime(&ms, (K > 0 && !overlap) ? c->ev[9] : c->ev[1], c->ev[3]);
         stats->ms_accumulate = ms;
         cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);
         stats->ms_total = ms;
@@ -1708,6 +1825,12 @@ void batch_release(BatchState& B) {
     if (B.main) cudaStreamDestroy(B.main);
     B.main = nullptr;
     B.events.clear();
+    release(B.dscratch);
+    if (B.ev_fork) cudaEventDestroy(B.ev_fork);
+    if (B.ev_join) cudaEventDestroy(B.ev_join);
+    if (B.side) cudaStreamDestroy(B.side);
+    B.ev_fork = B.ev_join = nullptr;
+    B.side = nullptr;
 }
 
 // Jobs accumulated one after the other by the single-pose path's launch (not through the work queue): one
@@ -1919,31 +2042,55 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     for (int j = 0; j < n; ++j) CB(cudaMemsetAsync(jobs[j].spectra_out, 0, (size_t)3 * jobs[j].n_mics * jobs[j].n_bins * 8, s));
     CB(batch_prep(a.jobs, n, s));
     const bool spec = (p.components & ST_COMP_SPECULAR) && B.N_total > 0;
-    if (spec) CB(batch_trace(a, B.max_b, B.N_total, tn.rays_per_block > 0 ? tn.rays_per_block : 128, s));
-    if (B.K_total > 0) CB(batch_diffraction(a, s));
-    if (p.components & ST_COMP_DIRECT) CB(batch_direct(a, s));
-    // compaction of visible records and kept candidates over all jobs; per-job ranges
-    if (spec) {
-        CB(flags_visible_records(a.rec_tri, a.rec_los, B.R_total, ptr<uint32_t>(B.sflags), s));
-        CB(exclusive_scan_u32(ptr<uint32_t>(B.sflags), ptr<uint32_t>(B.sscan), B.R_total, cnt + 2, B.scratch.p, s));
-        CB(compact_indices(ptr<uint32_t>(B.sflags), ptr<uint32_t>(B.sscan), B.R_total, ptr<uint32_t>(B.sidx), s));
-        CB(batch_gather_spec(a, ptr<uint32_t>(B.sidx), cnt + 2, B.spec, s));
-    }
+    const bool direct = (p.components & ST_COMP_DIRECT) != 0;
     const int64_t Koff = std::max<int64_t>(B.R_total, 1);  // candidate scan follows the record scan
-    if (B.K_total > 0) {
-        uint32_t* fl = ptr<uint32_t>(B.sflags) + Koff;
-        uint32_t* sc = ptr<uint32_t>(B.sscan) + Koff;
-        uint32_t* ix = ptr<uint32_t>(B.sidx) + Koff;
-        CB(flags_from_u8(a.keep, B.K_total, fl, s));
-        CB(exclusive_scan_u32(fl, sc, B.K_total, cnt + 3, B.scratch.p, s));
-        CB(compact_indices(fl, sc, B.K_total, ix, s));
-        if (B.any_mma)  // tensor-core jobs' paths grouped by material (stable; jobs stay in place)
-            CB(batch_material_order(a, cnt + 3, B.K_total, ix, ptr<uint32_t>(B.mat_off), B.mat_scr.p, s));
-        CB(batch_gather_diff(a, ix, cnt + 3, B.diff, s));
+    // the trace and the compaction of its visible records
+    auto issue_trace = [&](cudaStream_t st_) -> cudaError_t {
+        cudaError_t e;
+        if (spec) {
+            CB(batch_trace(a, B.max_b, B.N_total, tn.rays_per_block > 0 ? tn.rays_per_block : 128, st_));
+            CB(flags_visible_records(a.rec_tri, a.rec_los, B.R_total, ptr<uint32_t>(B.sflags), st_));
+            CB(exclusive_scan_u32(ptr<uint32_t>(B.sflags), ptr<uint32_t>(B.sscan), B.R_total, cnt + 2, B.scratch.p,
+                                  st_));
+            CB(compact_indices(ptr<uint32_t>(B.sflags), ptr<uint32_t>(B.sscan), B.R_total, ptr<uint32_t>(B.sidx), st_));
+            CB(batch_gather_spec(a, ptr<uint32_t>(B.sidx), cnt + 2, B.spec, st_));
+        }
+        return cudaSuccess;
+    };
+    // diffraction sampling and filters, the compaction of kept candidates, the direct visibility
+    auto issue_diffraction = [&](cudaStream_t st_) -> cudaError_t {
+        cudaError_t e;
+        if (B.K_total > 0) {
+            CB(batch_diffraction(a, st_));
+            uint32_t* fl = ptr<uint32_t>(B.sflags) + Koff;
+            uint32_t* sc = ptr<uint32_t>(B.sscan) + Koff;
+            uint32_t* ix = ptr<uint32_t>(B.sidx) + Koff;
+            CB(flags_from_u8(a.keep, B.K_total, fl, st_));
+            CB(exclusive_scan_u32(fl, sc, B.K_total, cnt + 3, B.dscratch.p, st_));
+            CB(compact_indices(fl, sc, B.K_total, ix, st_));
+            if (B.any_mma)  // tensor-core jobs' paths grouped by material (stable; jobs stay in place)
+                CB(batch_material_order(a, cnt + 3, B.K_total, ix, ptr<uint32_t>(B.mat_off), B.mat_scr.p, st_));
+            CB(batch_gather_diff(a, ix, cnt + 3, B.diff, st_));
+        }
+        if (direct) CB(batch_direct(a, st_));
+        return cudaSuccess;
+    };
+    if (B.overlap && spec && (B.K_total > 0 || direct)) {  // a side branch beside the trace, joined before the ranges
+        CB(cudaEventRecord(B.ev_fork, s));
+        CB(cudaStreamWaitEvent(B.side, B.ev_fork, 0));
+        const cudaError_t e1 = issue_diffraction(B.side);
+        const cudaError_t e2 = e1 == cudaSuccess ? issue_trace(s) : cudaSuccess;
+        CB(cudaEventRecord(B.ev_join, B.side));
+        CB(cudaStreamWaitEvent(s, B.ev_join, 0));
+        CB(e1);
+        CB(e2);
+    } else {
+        CB(issue_trace(s));
+        CB(issue_diffraction(s));
     }
     if (spec || B.K_total > 0)
         CB(batch_ranges(a, ptr<uint32_t>(B.sscan), cnt + 2, ptr<uint32_t>(B.sscan) + Koff, cnt + 3, s));
-    if (p.components & ST_COMP_DIRECT) CB(batch_direct_accum(a, s));
+    if (direct) CB(batch_direct_accum(a, s));
     {  // every job's accumulation: two persistent launches over (job, tile) items, one reduction
         const AccumTask* tk = ptr<AccumTask>(B.tasks);
         unsigned long long* qc = ptr<unsigned long long>(B.qctr);
@@ -2044,6 +2191,8 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     const int32_t ti[6] = {tn.rays_per_block, tn.mic_pairs_per_cta, tn.smem_kb, tn.stack_depth, tn.refill_lanes,
                            tn.bins_per_thread};
     key = fnv(key, ti, sizeof(ti));
+    const int32_t ov = c->overlap ? 1 : 0;
+    key = fnv(key, &ov, sizeof(ov));
     if (B.valid && B.key == key && B.exec) {
         const int ne = (int)B.events.size();
         CKC(c, cudaEventRecord(B.events[ne - 2], s), "batch order");
@@ -2128,7 +2277,8 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     CKC(c, grow(B.sflags, (size_t)(R1 + K1) * 4), "batch alloc");
     CKC(c, grow(B.sscan, (size_t)(R1 + K1) * 4), "batch alloc");
     CKC(c, grow(B.sidx, (size_t)(R1 + K1) * 4), "batch alloc");
-    CKC(c, grow(B.scratch, scan_scratch_bytes(std::max(R1, K1))), "batch alloc");
+    CKC(c, grow(B.scratch, scan_scratch_bytes(R1)), "batch alloc");
+    CKC(c, grow(B.dscratch, scan_scratch_bytes(K1)), "batch alloc");
     for (PathList* P : {&B.spec, &B.diff}) {
         const int64_t nP = P == &B.spec ? R1 : K1;
         for (DevBuf* b : {&P->px, &P->py, &P->pz, &P->dx, &P->dy, &P->dz, &P->rhi, &P->rlo, &P->chain_lo, &P->chain_hi,
@@ -2234,6 +2384,10 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     B.events.resize(2);  // context -> batch stream, batch stream -> context
     for (auto& ev : B.events) CKC(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch events");
     CKC(c, cudaStreamCreateWithFlags(&B.main, cudaStreamNonBlocking), "batch streams");
+    CKC(c, cudaStreamCreateWithFlags(&B.side, cudaStreamNonBlocking), "batch streams");
+    CKC(c, cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming), "batch events");
+    CKC(c, cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming), "batch events");
+    B.overlap = c->overlap;
     CKC(c, cudaStreamSynchronize(s), "batch setup");
     // ---- eager run (also sets kernel attributes), then record the graph for later calls
     cudaStream_t ms = B.main;
@@ -2285,6 +2439,8 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
     DevBuf out_buf;
     CKC(c, grow(out_buf, (size_t)3 * J->n_mics * J->n_bins * 8), "autotune alloc");
     const st_tune saved = c->tune;
+    const bool saved_overlap = c->overlap;
+    c->overlap = false;  // each stage timed on its own
     const int rpb[3] = {64, 128, 256};
     const int tiles[5][2] = {{16, 96}, {8, 96}, {16, 64}, {4, 96}, {16, 128}};
     const int kts[2] = {16, 8};
@@ -2320,6 +2476,7 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
                 r = st_simulate(c, J->scene, &p, out_buf.p, &st);
                 if (r != ST_OK) {
                     c->tune = saved;
+                    c->overlap = saved_overlap;
                     release(out_buf);
                     return r;
                 }
@@ -2334,6 +2491,7 @@ st_status st_autotune(st_ctx* c, const st_job* J, const st_sim_params* params, s
         best = winner;
     }
     release(out_buf);
+    c->overlap = saved_overlap;
     c->tune = best;
     *out = best;
     return ST_OK;
