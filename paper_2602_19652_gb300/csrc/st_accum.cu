@@ -795,6 +795,42 @@ cudaError_t theta_order(const GatherArgs& g, int64_t cap, uint32_t* idx, uint64_
     return radix_sort_u64(keys, idx, cap, 16, scratch, s);  // stable: equal rows keep the compaction order
 }
 
+// Key of a compacted specular path for chain order: the counts of materials 0..3 in its reflection chain in
+// base 9 (cumulative reflection), or its last hit's material (last-hit reflection); entries past *g.count last.
+__global__ void k_chain_keys(const GatherArgs g, int64_t cap, int last_only, uint64_t* keys) {
+    const int64_t n = *g.count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cap; c += stride) {
+        uint64_t key = 0x3fffu;
+        if (c < n) {
+            const int64_t id = g.idx[c];
+            const int64_t ray = id / g.B;
+            const int j = (int)(id % g.B);
+            if (last_only) {
+                key = (uint64_t)((uint32_t)g.tri_mat[g.rec_tri[id]] & 255u);
+            } else {
+                int cnt[4] = {0, 0, 0, 0};
+                for (int q = 0; q <= j; ++q) {
+                    const int mq = g.tri_mat[g.rec_tri[ray * g.B + q]];
+                    if (mq >= 0 && mq < 4) cnt[mq]++;
+                }
+                key = (uint64_t)(((cnt[3] * 9 + cnt[2]) * 9 + cnt[1]) * 9 + cnt[0]);
+            }
+        }
+        keys[c] = key;
+    }
+}
+
+cudaError_t chain_order(const GatherArgs& g, int64_t cap, int last_only, uint32_t* idx, uint64_t* keys, void* scratch,
+                        cudaStream_t s) {
+    if (cap <= 1) return cudaSuccess;
+    note_launch();
+    k_chain_keys<<<grid_for(cap, 256), 256, 0, s>>>(g, cap, last_only, keys);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return radix_sort_u64(keys, idx, cap, 14, scratch, s);  // stable: equal chains keep the compaction order
+}
+
 cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s) {
     PathList& P = *g.out;
     note_launch();

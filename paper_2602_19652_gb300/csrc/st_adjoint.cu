@@ -88,8 +88,10 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     float* pjb = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(pvb + 3 * PT) + 15) & ~uintptr_t(15));
     // (specular) per path of a tile: how often each of the launch's kNV materials occurs in its reflection chain
     float4* pcb = reinterpret_cast<float4*>(pjb + (EMIT ? 3 * PT * 12 : 0));
+    // (specular) and one integer signature of those counts per path (-1: no path), compared between neighbours
+    int* psg = reinterpret_cast<int*>(pcb + (KIND == 0 ? 3 * PT : 0));
     float* mt = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(pcb + (KIND == 0 ? 3 * PT : 0)) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(psg + (KIND == 0 ? 3 * PT : 0)) + 15) & ~uintptr_t(15));
 
     const int mb = blockIdx.x % g.n_mb, bb = blockIdx.x / g.n_mb;
     const int mic0 = mb * g.MP, kb = bb * KB;
@@ -103,6 +105,10 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     const int64_t n_tiles = (count + PT - 1) / PT;
     const int64_t per = (n_tiles + a.n_chunks - 1) / a.n_chunks;
     const int64_t t0 = (int64_t)blockIdx.y * per, t1 = min(n_tiles, t0 + per);
+    // the emitter variant always computes positions and never lobe widths (constants there, so that the term
+    // loop carries no select between the two reflection sums)
+    const bool do_pos = EMIT ? true : j.do_pos != 0;
+    const bool do_beta = EMIT ? false : j.do_beta != 0;
     // chain jacobians of one tile's paths (EMIT), next to their path data
     auto load_jac = [&](int64_t pbase, float* dst) {
         if (EMIT) {
@@ -114,15 +120,16 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     };
 
     // material counts of one tile's paths (slot of its path data), one thread per path
-    auto chain_counts = [&](const float* pd, const int* pv, float4* dst) {
+    auto chain_counts = [&](const float* pd, const int* pv, float4* dst, int* sig) {
         if (KIND == 0 && j.do_k)
             for (int p = threadIdx.x; p < PT; p += blockDim.x) {
                 float cnt[kNV] = {0.f, 0.f, 0.f, 0.f};
+                int code = -1;
                 if (pv[p]) {
                     const uint32_t meta = __float_as_uint(pd[p * 12 + 8]);
                     const int len = meta & 15, matj = (meta >> 8) & 255;
                     const uint32_t c0 = __float_as_uint(pd[p * 12 + 9]), c1 = __float_as_uint(pd[p * 12 + 10]);
-                    if (a.reflection_mode == 1 || j.do_beta) {  // one material: the last hit's
+                    if (a.reflection_mode == 1 || do_beta) {  // one material: the last hit's
                         const int q = matj - j.mat_base;
                         for (int u = 0; u < kNV; ++u)
                             if (q == u) cnt[u] = 1.0f;
@@ -133,8 +140,11 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                                 if (mq == u) cnt[u] += 1.0f;
                         }
                     }
+                    code = 0;  // counts of at most 8 hits: base 9
+                    for (int u = kNV - 1; u >= 0; --u) code = code * 9 + (int)cnt[u];
                 }
                 dst[p] = make_float4(cnt[0], cnt[1], cnt[2], cnt[3]);
+                sig[p] = code;
             }
     };
 
@@ -160,6 +170,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     for (int q = 0; q < kNV; ++q)
 #pragma unroll
         for (int v = 0; v < VR; ++v) V[q][v] = 0.0f;
+
     // position gradients of the thread's two microphones (and the emitter, diffraction), packed
     u64 dmx = 0ull, dmy = 0ull, dmz = 0ull;
     // emitter gradient: its factors (the direction -unit(o - s) of a diffraction path, the chain jacobian of a
@@ -200,7 +211,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
         cp_async_wait_all();
         __syncthreads();
         produce<KT, KIND, 1>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, j.s, t0 * PT);
-        chain_counts(pdb, pvb, pcb);
+        chain_counts(pdb, pvb, pcb, psg);
         __syncthreads();
     }
     for (int64_t tile = t0; tile < t1; ++tile) {
@@ -219,8 +230,13 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             const int nb = (int)((tile + 1 - t0) % 3);
             produce<KT, KIND, 1>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, j.s,
                                  (tile + 1) * PT);
-            chain_counts(pdb + nb * PT * 12, pvb + nb * PT, pcb + nb * PT);
+            chain_counts(pdb + nb * PT * 12, pvb + nb * PT, pcb + nb * PT, psg + nb * PT);
         }
+        // per-bin values of the current run of paths with equal material counts (specular; flushed by the
+        // tile's last path at the latest, so that they are not live across the producer phase)
+        float Y[KT];
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) Y[kk] = 0.0f;
         for (int p = 0; p < PT; ++p) {
             const ulonglong2 z0 = C.za[((size_t)p * NS + s) * TP + tp];
             const u64* w = C.wst + (size_t)p * 4 * TP + tp;  // component-major: conflict-free 64-bit loads
@@ -231,7 +247,6 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
             cmul2(orr, oi, w1r, w1i, fmul2(w1i, pk2(-1.0f, -1.0f)));
             u64 c0r = 0ull, c0i = 0ull, qr = 0ull, qi = 0ull, cg = 0ull;
             u64 c1r = 0ull, c1i = 0ull;  // diffraction: C1 = sum_kk kk conj(G) T directly
-            float y[KT];
             const float2 ngv = up2(ng);  // -gamma^2 of the two microphones (lobe sums)
             const float2* trow = reinterpret_cast<const float2*>(C.tab) + (size_t)p * KB + s;
             // diffraction with the material table read directly: row offset left by the producer in ngp
@@ -280,11 +295,11 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                     qi = fadd2(qi, c0i);
                     if (KIND == 0) cg = ffma2(pk2(t.y, t.y), wr, cg);
                     const float2 wr2 = up2(wr);
-                    y[kk] = j.do_beta ? fmaf(wr2.x, ngv.x, wr2.y * ngv.y) : wr2.x + wr2.y;
+                    Y[kk] += do_beta ? fmaf(wr2.x, ngv.x, wr2.y * ngv.y) : wr2.x + wr2.y;
                     if (kk & 1) cmul2(orr, oi, w2r, w2i, nw2i); else cmul2(er, ei, w2r, w2i, nw2i);
                 }
             }
-            if (j.do_pos) {
+            if (do_pos) {
                 const u64* ad = C.adj + ((size_t)p * TP + tp) * 7;
                 // C1 relative to the subtile's first bin
                 const u64 q1r = KIND == 1 ? c1r : fsub2(fmul2(pk2((float)KT, (float)KT), c0r), qr);
@@ -341,15 +356,22 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
                     esz = fmaf(dsum, up2(ad[5]).x, esz);
                 }
             }
-            // reflection-coefficient sums for the materials of the path's chain
-            if constexpr (KIND == 0) if (j.do_k && pv[p]) {
-                rs_reduce<TPL>(y, tp, wm);
-                const float4 c4 = pcb[pb * PT + p];  // the chain's material counts, from the producer
-                const float cnt[kNV] = {c4.x, c4.y, c4.z, c4.w};
+            // reflection-coefficient sums for the materials of the path's chain: V += cnt (x) Y.  Consecutive
+            // paths with the same material counts (the backward orders its path list by them) share one
+            // reduce-scatter: Y sums their per-bin values until the counts change or the tile ends (the
+            // decision is the same for every thread of the CTA).  An invalid path adds zeros to Y.
+            if constexpr (KIND == 0) if (j.do_k) {
+                if (p == PT - 1 || psg[pb * PT + p] != psg[pb * PT + p + 1]) {
+                    rs_reduce<TPL>(Y, tp, wm);
+                    const float4 c4 = pcb[pb * PT + p];  // the chain's material counts, from the producer
+                    const float cnt[kNV] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-                for (int u = 0; u < kNV; ++u)
+                    for (int u = 0; u < kNV; ++u)
 #pragma unroll
-                    for (int v = 0; v < VR; ++v) V[u][v] = fmaf(cnt[u], y[v], V[u][v]);
+                        for (int v = 0; v < VR; ++v) V[u][v] = fmaf(cnt[u], Y[v], V[u][v]);
+#pragma unroll
+                    for (int kk = 0; kk < KT; ++kk) Y[kk] = 0.0f;
+                }
             }
         }
         cp_async_wait_all();
@@ -357,7 +379,7 @@ __global__ void __launch_bounds__(256, (KIND == 1 || TPL >= 3) ? 2 : 1)
     }
     // ---- outputs of this CTA (shared memory reused)
     const int cta = blockIdx.y * gridDim.x + blockIdx.x;
-    if (j.do_pos) {
+    if (do_pos) {
         float* red = reinterpret_cast<float*>(smem4);  // [NS][TP][2][3] microphones, then [nthr][3] emitter
         float* rede = red + (size_t)nthr * 6;
         __syncthreads();
@@ -623,7 +645,8 @@ cudaError_t launch_adjoint(const AccumArgs& a, const AdjointArgs& j, const Geom&
         attr_set = true;
     }
     dim3 grid((unsigned)(g.n_mb * g.n_bb), (unsigned)a.n_chunks);
-    const size_t smem = g.smem + (EMIT ? (size_t)3 * g.PT * 12 * 4 + 16 : 0) + (KIND == 0 ? (size_t)3 * g.PT * 16 + 16 : 0);
+    const size_t smem =
+        g.smem + (EMIT ? (size_t)3 * g.PT * 12 * 4 + 16 : 0) + (KIND == 0 ? (size_t)3 * g.PT * (16 + 4) + 16 : 0);
     note_launch();
     k_adjoint<KT, KIND, TPL, EMIT><<<grid, g.TP * g.NS, smem, s>>>(a, j, g);
     return cudaGetLastError();

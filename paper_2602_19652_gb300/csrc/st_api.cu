@@ -129,6 +129,9 @@ struct st_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DevBuf los_keys, los_scr, dflags, dscan, didx, dscratch, dpartial;
+    // backward: the specular path list of the last simulate put in chain order (keys and sort scratch)
+    bool paths_chain_order = false;
+    DevBuf ck_keys, ck_scr;
 };
 
 // Buffers and the recorded graph of the last batch structure.
@@ -395,7 +398,9 @@ st_status st_destroy(st_ctx* c) {
         release(*b);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
-    for (DevBuf* b : {&c->los_keys, &c->los_scr, &c->dflags, &c->dscan, &c->didx, &c->dscratch, &c->dpartial}) release(*b);
+    for (DevBuf* b : {&c->los_keys, &c->los_scr, &c->dflags, &c->dscan, &c->didx, &c->dscratch, &c->dpartial,
+                      &c->ck_keys, &c->ck_scr})
+        release(*b);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -1380,6 +1385,7 @@ static st_status simulate_impl(st_ctx* c, st_scene* sc, const st_sim_params* par
     c->last_chunks_diff = chunks_diff;
     c->last_diff_mma = diff_mma;
     c->has_last = true;
+    c->paths_chain_order = false;
 
     // device-side error flags are checked whenever the caller synchronises through stats
     if (stats) {
@@ -1629,10 +1635,9 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         x.n_chunks = chunks;
         set_paths(x, c->paths);
         x.mask = spec_mask;
-        if (grad_emitter) {
-            // the emitter moves the hit points: chain jacobians of the visible records, in the order of
-            // the path list (the compaction of the last simulate, repeated)
-            const int64_t NB = c->last_N * c->last_B;
+        const int64_t NB = c->last_N * c->last_B;
+        if (!c->paths_chain_order || grad_emitter) {
+            // the compaction of the last simulate, repeated: the visible records in the order of its path list
             CKC(c, flags_visible_records(ptr<int32_t>(c->rec_tri), ptr<uint8_t>(c->rec_los), NB,
                                          ptr<uint32_t>(c->sflags), s),
                 "flags");
@@ -1640,6 +1645,44 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
                 "scan");
             CKC(c, compact_indices(ptr<uint32_t>(c->sflags), ptr<uint32_t>(c->sscan), NB, ptr<uint32_t>(c->sidx), s),
                 "compact");
+        }
+        if (c->n_theta == 0 && NB > 1) {
+            // chain order (omni emitter; with an emitter table the list keeps its table-row order): paths with
+            // equal material counts next to each other, so that the adjoint reduces their reflection sums once
+            // per run; the path list is gathered again in that order (once per simulate) and the chain
+            // jacobians follow it
+            GatherArgs ga{};
+            ga.N = c->last_N;
+            ga.B = c->last_B;
+            ga.rec_tri = ptr<int32_t>(c->rec_tri);
+            ga.rec_p = ptr<float>(c->rec_p);
+            ga.rec_d = ptr<float>(c->rec_d);
+            ga.rec_r = ptr<double>(c->rec_r);
+            ga.rec_los = ptr<uint8_t>(c->rec_los);
+            ga.tri_mat = ptr<int32_t>(S.tri_mat);
+            ga.dirs = ptr<float>(c->dirs);
+            memcpy(ga.q, c->q, 16);
+            memcpy(ga.fwd, c->last_fwd, 12);
+            ga.has_etab = false;
+            ga.idx = ptr<uint32_t>(c->sidx);
+            ga.count = cnt + 2;
+            ga.out = &c->paths;
+            ga.rec_mask = spec_mask ? ptr<uint64_t>(c->rec_mask) : nullptr;
+            ga.n_mat = S.n_mat;
+            ga.chk = ptr<uint32_t>(c->flags);
+            if (!c->paths_chain_order || grad_emitter) {  // (the sort is stable: the same order every time)
+                CKC(c, grow(c->ck_keys, (size_t)NB * 8), "alloc");
+                CKC(c, grow(c->ck_scr, sort_scratch_bytes(NB)), "alloc");
+                CKC(c, chain_order(ga, NB, p.reflection_mode == 1 ? 1 : 0, ptr<uint32_t>(c->sidx),
+                                   ptr<uint64_t>(c->ck_keys), c->ck_scr.p, s),
+                    "chain order");
+            }
+            if (!c->paths_chain_order) CKC(c, gather_specular(ga, s), "gather");
+            c->paths_chain_order = true;
+        }
+        if (grad_emitter) {
+            // the emitter moves the hit points: chain jacobians of the visible records, in the order of
+            // the path list
             CKC(c, grow(c->adj_jac, (size_t)NB * 48), "alloc");
             CKC(c, chain_jacobians(ptr<uint32_t>(c->sidx), cnt + 2, NB, c->last_B, ptr<int32_t>(c->rec_tri),
                                    ptr<float>(c->rec_d), ptr<float>(S.nrm), ptr<float>(c->dirs), c->q,

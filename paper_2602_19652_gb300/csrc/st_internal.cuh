@@ -413,6 +413,11 @@ cudaError_t gather_specular(const GatherArgs& g, cudaStream_t s);
 // last); keys [cap] and scratch (sort_scratch_bytes(cap)) are the caller's.
 cudaError_t theta_order(const GatherArgs& g, int64_t cap, uint32_t* idx, uint64_t* keys, void* scratch,
                         cudaStream_t s);
+// Stable sort of the compacted specular indices idx[0 .. cap) by the material counts of their reflection chains
+// (materials 0..3; last_only: by the last hit's material), entries past *g.count last: the adjoint forms its
+// reflection sums once per run of equal counts.  keys [cap] and scratch (sort_scratch_bytes(cap)) are the caller's.
+cudaError_t chain_order(const GatherArgs& g, int64_t cap, int last_only, uint32_t* idx, uint64_t* keys, void* scratch,
+                        cudaStream_t s);
 cudaError_t gather_diffraction(const GatherArgs& g, cudaStream_t s);
 cudaError_t flags_visible_records(const int32_t* rec_tri, const uint8_t* rec_los, int64_t n, uint32_t* flags,
                                   cudaStream_t s);
