@@ -68,6 +68,16 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// Two phasor chains at once, as (re, re) and (im, im) pairs: (zr, zi) *= (wr, wi) with the rounding of cmul
+// (re = fma(zr, wr, -(zi wi)), im = fma(zr, wi, zi wr)), so the pairs hold exactly the scalar chains' values;
+// nwi = -wi
+__device__ __forceinline__ void cmul2_as_scalar(u64& zr, u64& zi, u64 wr, u64 wi, u64 nwi) {
+    const u64 tn = fmul2(zi, nwi), t2 = fmul2(zi, wr);
+    const u64 r = ffma2(zr, wr, tn);
+    zi = ffma2(zr, wi, t2);
+    zr = r;
+}
+
 // tile of the material-ordered path list: material q, first path and path count
 struct MTile {
     int q;
@@ -175,17 +185,19 @@ __device__ __forceinline__ void diff_mma_cta(const AccumArgs& a, const uint32_t*
             uint32_t* ur = reinterpret_cast<uint32_t*>(Us + (((size_t)ml * 4) * kMmaPaths + p) * kURow);
             const size_t upart = (size_t)kMmaPaths * kURow / 2;  // words between parts
             const float2 w64 = cmul(w32, w32);
-            float2 zo = cmul(z, w32);
+            const float2 zo = cmul(z, w32);
+            // the even and odd chains as one packed pair
+            u64 ur2 = pk2(z.x, zo.x), ui2 = pk2(z.y, zo.y);
+            const u64 w64r = pk2(w64.x, w64.x), w64i = pk2(w64.y, w64.y), nw64i = pk2(-w64.y, -w64.y);
 #pragma unroll
             for (int j = 0; j < kK1 / 8; ++j) {
                 uint32_t rh4[4], rl4[4], ih4[4], il4[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float2 u0 = z, u1 = zo;
-                    z = cmul(z, w64);
-                    zo = cmul(zo, w64);
-                    split2(u0.x, u1.x, rh4[e], rl4[e]);
-                    split2(u0.y, u1.y, ih4[e], il4[e]);
+                    const float2 ur = up2(ur2), ui = up2(ui2);
+                    cmul2_as_scalar(ur2, ui2, w64r, w64i, nw64i);
+                    split2(ur.x, ur.y, rh4[e], rl4[e]);
+                    split2(ui.x, ui.y, ih4[e], il4[e]);
                 }
                 reinterpret_cast<uint4*>(ur + 0 * upart)[j] = make_uint4(rh4[0], rh4[1], rh4[2], rh4[3]);
                 reinterpret_cast<uint4*>(ur + 1 * upart)[j] = make_uint4(rl4[0], rl4[1], rl4[2], rl4[3]);
@@ -202,17 +214,22 @@ __device__ __forceinline__ void diff_mma_cta(const AccumArgs& a, const uint32_t*
             vc[2] = cmul(vc[1], w1);
             vc[3] = cmul(vc[2], w1);
             const float2 w4 = cmul(cmul(w1, w1), cmul(w1, w1));
+            // chains 0, 1 and chains 2, 3 as two packed pairs
+            u64 r01 = pk2(vc[0].x, vc[1].x), i01 = pk2(vc[0].y, vc[1].y);
+            u64 r23 = pk2(vc[2].x, vc[3].x), i23 = pk2(vc[2].y, vc[3].y);
+            const u64 w4r = pk2(w4.x, w4.x), w4i = pk2(w4.y, w4.y), nw4i = pk2(-w4.y, -w4.y);
 #pragma unroll
             for (int j = 0; j < kK2 / 8; ++j) {
                 uint32_t rh4[4], rl4[4], ih4[4], il4[4];
 #pragma unroll
                 for (int e2 = 0; e2 < 2; ++e2) {
-                    split2(vc[0].x, vc[1].x, rh4[2 * e2], rl4[2 * e2]);
-                    split2(vc[0].y, vc[1].y, ih4[2 * e2], il4[2 * e2]);
-                    split2(vc[2].x, vc[3].x, rh4[2 * e2 + 1], rl4[2 * e2 + 1]);
-                    split2(vc[2].y, vc[3].y, ih4[2 * e2 + 1], il4[2 * e2 + 1]);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) vc[c] = cmul(vc[c], w4);
+                    const float2 a01 = up2(r01), b01 = up2(i01), a23 = up2(r23), b23 = up2(i23);
+                    split2(a01.x, a01.y, rh4[2 * e2], rl4[2 * e2]);
+                    split2(b01.x, b01.y, ih4[2 * e2], il4[2 * e2]);
+                    split2(a23.x, a23.y, rh4[2 * e2 + 1], rl4[2 * e2 + 1]);
+                    split2(b23.x, b23.y, ih4[2 * e2 + 1], il4[2 * e2 + 1]);
+                    cmul2_as_scalar(r01, i01, w4r, w4i, nw4i);
+                    cmul2_as_scalar(r23, i23, w4r, w4i, nw4i);
                 }
                 reinterpret_cast<uint4*>(vr + 0 * vpart)[j] = make_uint4(rh4[0], rh4[1], rh4[2], rh4[3]);
                 reinterpret_cast<uint4*>(vr + 1 * vpart)[j] = make_uint4(rl4[0], rl4[1], rl4[2], rl4[3]);
@@ -466,14 +483,16 @@ __global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const Acc
                 o[0] = o[1] = o[2] = o[3] = o[4] = o[5] = o[6] = 0.0f;
             }
             float2* up = Up + ((size_t)ml * kMmaPaths + p) * kUpRow;
-            float2 ue = make_float2(1.0f, 0.0f), uo = w32;
             const float2 w64 = cmul(w32, w32);
+            // the even and odd powers as one packed pair
+            u64 ur2 = pk2(1.0f, w32.x), ui2 = pk2(0.0f, w32.y);
+            const u64 w64r = pk2(w64.x, w64.x), w64i = pk2(w64.y, w64.y), nw64i = pk2(-w64.y, -w64.y);
 #pragma unroll
             for (int k1 = 0; k1 < kK1; k1 += 2) {
-                up[k1] = ue;
-                up[k1 + 1] = uo;
-                ue = cmul(ue, w64);
-                uo = cmul(uo, w64);
+                const float2 ur = up2(ur2), ui = up2(ui2);
+                up[k1] = make_float2(ur.x, ui.x);
+                up[k1 + 1] = make_float2(ur.y, ui.y);
+                cmul2_as_scalar(ur2, ui2, w64r, w64i, nw64i);
             }
             uint32_t* vr = reinterpret_cast<uint32_t*>(Vs + (((size_t)ml * 4) * kMmaPaths + p) * kVRow);
             const size_t vpart = (size_t)kMmaPaths * kVRow / 2;
@@ -483,17 +502,22 @@ __global__ void __launch_bounds__(kMmaMics * 32, 2) k_adjoint_diff_mma(const Acc
             vc[2] = cmul(vc[1], w1);
             vc[3] = cmul(vc[2], w1);
             const float2 w4 = cmul(cmul(w1, w1), cmul(w1, w1));
+            // chains 0, 1 and chains 2, 3 as two packed pairs
+            u64 r01 = pk2(vc[0].x, vc[1].x), i01 = pk2(vc[0].y, vc[1].y);
+            u64 r23 = pk2(vc[2].x, vc[3].x), i23 = pk2(vc[2].y, vc[3].y);
+            const u64 w4r = pk2(w4.x, w4.x), w4i = pk2(w4.y, w4.y), nw4i = pk2(-w4.y, -w4.y);
 #pragma unroll
             for (int jj = 0; jj < kK2 / 8; ++jj) {
                 uint32_t rh4[4], rl4[4], ih4[4], il4[4];
 #pragma unroll
                 for (int e2 = 0; e2 < 2; ++e2) {
-                    split2(vc[0].x, vc[1].x, rh4[2 * e2], rl4[2 * e2]);
-                    split2(vc[0].y, vc[1].y, ih4[2 * e2], il4[2 * e2]);
-                    split2(vc[2].x, vc[3].x, rh4[2 * e2 + 1], rl4[2 * e2 + 1]);
-                    split2(vc[2].y, vc[3].y, ih4[2 * e2 + 1], il4[2 * e2 + 1]);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) vc[c] = cmul(vc[c], w4);
+                    const float2 a01 = up2(r01), b01 = up2(i01), a23 = up2(r23), b23 = up2(i23);
+                    split2(a01.x, a01.y, rh4[2 * e2], rl4[2 * e2]);
+                    split2(b01.x, b01.y, ih4[2 * e2], il4[2 * e2]);
+                    split2(a23.x, a23.y, rh4[2 * e2 + 1], rl4[2 * e2 + 1]);
+                    split2(b23.x, b23.y, ih4[2 * e2 + 1], il4[2 * e2 + 1]);
+                    cmul2_as_scalar(r01, i01, w4r, w4i, nw4i);
+                    cmul2_as_scalar(r23, i23, w4r, w4i, nw4i);
                 }
                 reinterpret_cast<uint4*>(vr + 0 * vpart)[jj] = make_uint4(rh4[0], rh4[1], rh4[2], rh4[3]);
                 reinterpret_cast<uint4*>(vr + 1 * vpart)[jj] = make_uint4(rl4[0], rl4[1], rl4[2], rl4[3]);
