@@ -514,7 +514,7 @@ Geom accum_geom(const AccumArgs& a, int kind, int kt, int dir) {
     const bool direct_mat = kind == 1 && !a.etab;
     const int tp = a.tile_tp > 0 ? a.tile_tp : (direct_mat && !g_tile_env_set ? std::max(1, g_tile_tp / 2) : g_tile_tp);
     const size_t budget = a.tile_kb > 0 ? (size_t)a.tile_kb * 1024 : g_tile_budget;
-    return make_geom(a.M, a.F, kt, a.n_mat_tab, tp, budget, dir ? a.n_bands_tab : 0, direct_mat);
+    return make_geom(a.M, a.F, kt, a.n_mat_tab, tp, budget, dir ? a.n_bands_tab : 0, direct_mat, 1);
 }
 
 template <int KT, int KIND, int DIR>
@@ -616,7 +616,7 @@ int32_t accum_chunks(int64_t n_paths_hint, int32_t M, int32_t F, int32_t n_mat, 
     read_tile_env();
     const int tp = tile_tp > 0 ? tile_tp : g_tile_tp;
     const size_t budget = tile_kb > 0 ? (size_t)tile_kb * 1024 : g_tile_budget;
-    const Geom g = make_geom(M, F, dir_nb ? 16 : (tile_kt > 0 ? tile_kt : g_tile_kt), n_mat, tp, budget, dir_nb);
+    const Geom g = make_geom(M, F, dir_nb ? 16 : (tile_kt > 0 ? tile_kt : g_tile_kt), n_mat, tp, budget, dir_nb, 0, 1);
     const int ctas_per_chunk = g.n_mb * g.n_bb;
     const int threads = g.TP * g.NS;
     int resident = std::max(1, std::min(2048 / std::max(threads, 32), (int)((220 * 1024) / std::max<size_t>(g.smem, 1))));

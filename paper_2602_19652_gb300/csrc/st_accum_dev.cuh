@@ -549,8 +549,11 @@ __device__ __forceinline__ void produce(const AccumArgs& a, const Geom& g, const
 
 
 // tp_max: mic pairs per CTA at most; budget: shared-memory bytes per CTA
+// balance: the microphone pairs spread evenly over the microphone blocks with the bin tiling unchanged (40
+// microphones: two blocks of 10 pairs instead of 16 + 4; the CTA then has fewer threads, and where it runs as
+// 256 threads the spare ones are whole idle warps rather than pairs that compute zeros)
 inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t budget = 96 * 1024, int dir_nb = 0,
-                      int mat_direct = 0) {
+                      int mat_direct = 0, int balance = 0) {
     Geom g;
     g.NB = dir_nb;
     g.ADJ = 0;
@@ -559,6 +562,10 @@ inline Geom make_geom(int M, int F, int KT, int n_mat, int tp_max = 8, size_t bu
     g.TP = std::max(1, std::min(pairs, tp_max));
     g.NS = std::max(1, std::min(ns_need, 256 / g.TP));
     g.TP = std::max(1, std::min(pairs, 256 / g.NS));
+    if (balance) {
+        const int nb = (pairs + g.TP - 1) / g.TP;
+        g.TP = (pairs + nb - 1) / nb;
+    }
     g.MP = 2 * g.TP;
     g.KB = g.NS * KT;
     g.n_mb = (M + g.MP - 1) / g.MP;
