@@ -89,7 +89,7 @@ __global__ void k_tables(int32_t F, int32_t n_mat, int32_t n_bands, const float*
 // One CTA of the accumulation: microphone block bx % n_mb, bin block bx / n_mb, chunk by of the path list.
 // Threads past TP * NS (a block larger than the tile, as in the persistent batched launch) take part in
 // the loads, the producer and the barriers only.
-template <int KT, int KIND, int DIR>
+template <int KT, int KIND, int DIR, int SPLIT = 0>
 __device__ __forceinline__ void accum_cta(const AccumArgs& a, const Geom& g, int bx, int by, float4* smem4) {
     static_assert((KT & (KT - 1)) == 0 && KT >= 2, "KT must be a power of two");
     const int PT = g.PT, NS = g.NS, TP = g.TP, KB = g.KB, MP = g.MP;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void accum_cta(const AccumArgs& a, const Geom& g, int
         load_paths<KIND>(a, PT, t0 * PT, count, pdb, pvb);
         if (t0 + 1 < t1) load_paths<KIND>(a, PT, (t0 + 1) * PT, count, pdb + PT * 12, pvb + PT);
         __syncthreads();
-        produce<KT, KIND>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, nullptr, pb0 + t0 * PT);
+        produce<KT, KIND, 0, SPLIT>(a, g, B0, pdb, pvb, mt, mic0, kb, invNS, invKB, nullptr, pb0 + t0 * PT);
         __syncthreads();
     }
     // software pipeline: consume tile t from buffer b while producing tile t+1 into buffer b^1
@@ -158,7 +158,7 @@ __device__ __forceinline__ void accum_cta(const AccumArgs& a, const Geom& g, int
         if (tile + 2 < t1) load_paths_cp<KIND>(a, PT, (tile + 2) * PT, count, pdb + b * PT * 12, pvb + b * PT);
         if (tile + 1 < t1) {
             const int nb = b ^ 1;  // path data of tile+1 sits in pd buffer nb
-            produce<KT, KIND>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, nullptr,
+            produce<KT, KIND, 0, SPLIT>(a, g, Pn, pdb + nb * PT * 12, pvb + nb * PT, mt, mic0, kb, invNS, invKB, nullptr,
                               pb0 + (tile + 1) * PT);
         }
         for (int p = 0; p < (cons ? PT : 0); ++p) {
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256, 2) k_accum_queue(const AccumTask* tasks, 
         if (it >= n_items) break;
         const int nxy = T.g.n_mb * T.g.n_bb;
         const int local = (int)(it - T.item0);
-        accum_cta<16, KIND, 0>(T.a, T.g, local % nxy, local / nxy, smem4);
+        accum_cta<16, KIND, 0, 1>(T.a, T.g, local % nxy, local / nxy, smem4);
         __syncthreads();  // shared memory is reused by the next item
     }
 }
