@@ -38,10 +38,10 @@ FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by
 # hash of the kernel's sources it was taken on: the bench reports it only while the sources still hash to that
 # value (else null, until the kernel is captured again).  Specular k_accum: captured on 200k rays (7.98 MB read,
 # 0.02 MB written, 163,228 visible records) and scaled to the full-size launch by the visible records (816,192:
-# the path list is read once).  k_accum_diff_mma: the full-size diffraction set (21.36 MB read, 0.0003 MB written).
-ACCUM_TRAFFIC = {"sources_sha16": "090273bb11206453", "specular_bytes_per_launch": 39.9e6}
+# the path list is read once).  k_accum_diff_mma: the full-size diffraction set (21.4 MB read, 0.003 MB written).
+ACCUM_TRAFFIC = {"sources_sha16": "3dfb4d8787f86c0b", "specular_bytes_per_launch": 39.9e6}
 ACCUM_SOURCES = ("st_accum.cu", "st_accum_dev.cuh", "st_internal.cuh")
-DIFF_MMA_TRAFFIC = {"sources_sha16": "d1e4b7d40dcc11ca", "bytes_per_launch": 21.4e6}
+DIFF_MMA_TRAFFIC = {"sources_sha16": "1bb994d2be487f37", "bytes_per_launch": 21.4e6}
 DIFF_MMA_SOURCES = ("st_accum_mma.cu", "st_accum_dev.cuh", "st_internal.cuh")
 
 
