@@ -2392,9 +2392,10 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
         d.f_lo = J.f_lo;
         d.df = B.tables[j].df;
         d.out = static_cast<float2*>(J.spectra_out);
-        // chunks: the jobs share the GPU, so each job's accumulation is split into about an eighth of the
-        // chunks that would fill it alone (fewer partial spectra to sum)
-        const int nb = big_job(d) ? 1 : kBatchChunkDiv;
+        // chunks: the jobs of the work queue share the GPU, so each one's accumulation is split into about an
+        // eighth of the chunks that would fill it alone (fewer partial spectra to sum); a job accumulated on its
+        // own (one microphone pair, receiver tables, a million paths or more) runs alone and takes them all
+        const int nb = solo_accum(d) ? 1 : kBatchChunkDiv;
         const int dir_nb = J.mic_tables ? S.n_bands : 0;
         {
             AccumArgs probe{};
