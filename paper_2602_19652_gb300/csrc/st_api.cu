@@ -150,7 +150,8 @@ struct BatchState {
     DevBuf rec_mask, vis_qm;              // per-microphone receiver test
     bool per_mic = false;
     int64_t Q_total = 0;                  // per-microphone visibility queries a bounce, at most
-    DevBuf narrow_partial;  // chunk partials of the one-pair jobs (accumulated one after the other)
+    DevBuf narrow_partial;  // chunk partials of the jobs accumulated on their own, one slice per branch
+    size_t narrow_slice = 0;  // bytes of one branch's slice
     // persistent accumulation: one task per (job, path kind) -- the specular tasks, then the diffraction ones
     // -- their chunk partials, the work-item counter, item counts and the largest tile's shared memory
     std::vector<int32_t> narrow_jobs;  // jobs accumulated on their own (one microphone pair, or receiver tables)
@@ -175,6 +176,9 @@ struct BatchState {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DevBuf dscratch;
+    // the jobs accumulated on their own run on kSoloBranches graph branches beside the work-queue launches
+    cudaStream_t branch[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t br_fork = nullptr, br_join[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -1869,6 +1873,14 @@ void batch_release(BatchState& B) {
     B.main = nullptr;
     B.events.clear();
     release(B.dscratch);
+    for (int k = 0; k < 4; ++k) {
+        if (B.branch[k]) cudaStreamDestroy(B.branch[k]);
+        if (B.br_join[k]) cudaEventDestroy(B.br_join[k]);
+        B.branch[k] = nullptr;
+        B.br_join[k] = nullptr;
+    }
+    if (B.br_fork) cudaEventDestroy(B.br_fork);
+    B.br_fork = nullptr;
     if (B.ev_fork) cudaEventDestroy(B.ev_fork);
     if (B.ev_join) cudaEventDestroy(B.ev_join);
     if (B.side) cudaStreamDestroy(B.side);
@@ -2134,29 +2146,58 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
     if (spec || B.K_total > 0)
         CB(batch_ranges(a, ptr<uint32_t>(B.sscan), cnt + 2, ptr<uint32_t>(B.sscan) + Koff, cnt + 3, s));
     if (direct) CB(batch_direct_accum(a, s));
-    {  // every job's accumulation: two persistent launches over (job, tile) items, one reduction
+    {  // every job's accumulation: two persistent launches over (job, tile) items, one reduction; the jobs
+       // accumulated on their own on branches beside them (job i on branch i mod the branch count, each
+       // branch with its own slice of partial spectra), joined at the end
+        const int nbr = B.overlap && B.narrow_jobs.size() > 1 ? (int)std::min<size_t>(4, B.narrow_jobs.size()) : 0;
+        if (nbr > 0) {
+            CB(cudaEventRecord(B.br_fork, s));
+            for (int k = 0; k < nbr; ++k) CB(cudaStreamWaitEvent(B.branch[k], B.br_fork, 0));
+        }
+        auto solo = [&]() -> cudaError_t {
+            cudaError_t e;
+            for (size_t i = 0; i < B.narrow_jobs.size(); ++i) {
+                const int j = B.narrow_jobs[i];
+                const int br = nbr > 0 ? (int)(i % nbr) : 0;
+                cudaStream_t sj = nbr > 0 ? B.branch[br] : s;
+                const JobDev& jd = B.jobs[j];
+                const int64_t MF = (int64_t)jd.M * jd.F;
+                float2* out = static_cast<float2*>(jobs[j].spectra_out);
+                for (int kind = 0; kind < 2; ++kind) {
+                    if (kind == 0 ? !(spec && jd.N > 0) : jd.K <= 0) continue;
+                    AccumArgs y = batch_accum_args(B, jobs, j, kind, p, tn);
+                    y.partial = reinterpret_cast<float2*>(static_cast<char*>(B.narrow_partial.p) + (size_t)br * B.narrow_slice);
+                    if (kind == 1 && jd.diff_mma)
+                        CB(accumulate_diffraction_mma(y, ptr<uint32_t>(B.mat_off) + (size_t)j * kMatStride, sj));
+                    else
+                        CB(accumulate(y, sj));
+                    CB(reduce_partials(y.partial, y.n_chunks, MF, out + kind * MF, sj));
+                }
+            }
+            return cudaSuccess;
+        };
         const AccumTask* tk = ptr<AccumTask>(B.tasks);
         unsigned long long* qc = ptr<unsigned long long>(B.qctr);
-        if (spec) CB(accumulate_queue(0, tk, B.n_tasks_spec, B.items_spec, B.smem_spec, qc, s));
-        if (B.K_total > 0) CB(accumulate_queue(1, tk + B.n_tasks_spec, B.n_tasks_diff, B.items_diff, B.smem_diff, qc + 1, s));
-        if (B.K_total > 0)
-            CB(accumulate_diffraction_mma_queue(tk + B.n_tasks_spec + B.n_tasks_diff, B.n_tasks_mma, B.items_mma, s));
-        if (spec || B.K_total > 0) CB(reduce_tasks(tk, B.n_tasks_spec + B.n_tasks_diff + B.n_tasks_mma, B.n_out, s));
-        for (const int j : B.narrow_jobs) {
-            const JobDev& jd = B.jobs[j];
-            const int64_t MF = (int64_t)jd.M * jd.F;
-            float2* out = static_cast<float2*>(jobs[j].spectra_out);
-            for (int kind = 0; kind < 2; ++kind) {
-                if (kind == 0 ? !(spec && jd.N > 0) : jd.K <= 0) continue;
-                AccumArgs y = batch_accum_args(B, jobs, j, kind, p, tn);
-                y.partial = ptr<float2>(B.narrow_partial);
-                if (kind == 1 && jd.diff_mma)
-                    CB(accumulate_diffraction_mma(y, ptr<uint32_t>(B.mat_off) + (size_t)j * kMatStride, s));
-                else
-                    CB(accumulate(y, s));
-                CB(reduce_partials(y.partial, y.n_chunks, MF, out + kind * MF, s));
-            }
+        cudaError_t eq = cudaSuccess;
+        auto queue = [&]() -> cudaError_t {
+            cudaError_t e;
+            if (spec) CB(accumulate_queue(0, tk, B.n_tasks_spec, B.items_spec, B.smem_spec, qc, s));
+            if (B.K_total > 0)
+                CB(accumulate_queue(1, tk + B.n_tasks_spec, B.n_tasks_diff, B.items_diff, B.smem_diff, qc + 1, s));
+            if (B.K_total > 0)
+                CB(accumulate_diffraction_mma_queue(tk + B.n_tasks_spec + B.n_tasks_diff, B.n_tasks_mma, B.items_mma, s));
+            if (spec || B.K_total > 0)
+                CB(reduce_tasks(tk, B.n_tasks_spec + B.n_tasks_diff + B.n_tasks_mma, B.n_out, s));
+            return cudaSuccess;
+        };
+        const cudaError_t es = solo();  // (issued first: the branches start beside the queue launches)
+        if (es == cudaSuccess) eq = queue();
+        for (int k = 0; k < nbr; ++k) {  // joined whatever happened, so that nothing is left unordered
+            cudaEventRecord(B.br_join[k], B.branch[k]);
+            cudaStreamWaitEvent(s, B.br_join[k], 0);
         }
+        CB(es);
+        CB(eq);
     }
 #undef CB
     return cudaSuccess;
@@ -2416,7 +2457,8 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
         if (solo_accum(d))
             narrow_part = std::max(narrow_part, (size_t)std::max(B.chunks_spec[j], B.chunks_diff[j]) * d.M * d.F * 8);
     }
-    CKC(c, grow(B.narrow_partial, narrow_part), "batch alloc");
+    B.narrow_slice = (narrow_part + 255) & ~(size_t)255;
+    CKC(c, grow(B.narrow_partial, 4 * B.narrow_slice), "batch alloc");
     if (B.any_mma) {
         CKC(c, grow(B.mat_off, (size_t)n_jobs * kMatStride * 4), "batch alloc");
         CKC(c, grow(B.mat_scr, material_order_scratch(B.K_total)), "batch alloc");
@@ -2431,6 +2473,11 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     CKC(c, cudaStreamCreateWithFlags(&B.side, cudaStreamNonBlocking), "batch streams");
     CKC(c, cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming), "batch events");
     CKC(c, cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming), "batch events");
+    CKC(c, cudaEventCreateWithFlags(&B.br_fork, cudaEventDisableTiming), "batch events");
+    for (int k = 0; k < 4; ++k) {
+        CKC(c, cudaStreamCreateWithFlags(&B.branch[k], cudaStreamNonBlocking), "batch streams");
+        CKC(c, cudaEventCreateWithFlags(&B.br_join[k], cudaEventDisableTiming), "batch events");
+    }
     B.overlap = c->overlap;
     CKC(c, cudaStreamSynchronize(s), "batch setup");
     // ---- eager run (also sets kernel attributes), then record the graph for later calls
