@@ -696,14 +696,25 @@ __global__ void k_mat_keys_batch(const BatchArgs a, const uint32_t* idx, const u
     const int64_t n = *count;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cap; c += (int64_t)gridDim.x * blockDim.x) {
         if (c >= n) {
-            keys[c] = (uint64_t)a.n_jobs << 8;
+            keys[c] = (uint64_t)a.n_jobs << 16;
             continue;
         }
         const int64_t i = idx[c];
         const int job = find_job(a.samp_offs, a.n_jobs, i);
         const JobDev& b = a.jobs[job];
-        const uint32_t q = b.diff_mma ? ((uint32_t)b.tri_mat[a.cand_tri[i]] & 255u) : 0u;
-        keys[c] = ((uint64_t)job << 8) | q;
+        uint32_t q = 0u;
+        if (b.diff_mma) {
+            q = (uint32_t)b.tri_mat[a.cand_tri[i]] & 255u;
+        } else if (b.etab) {
+            // emitter-table row of the candidate (the gather's coordinate, floored): a tile's paths then read the
+            // same one or two table rows, which stay in L1
+            const float ox = a.cand_p[3 * i], oy = a.cand_p[3 * i + 1], oz = a.cand_p[3 * i + 2];
+            const float vx = ox - b.s[0], vy = oy - b.s[1], vz = oz - b.s[2];
+            const ff r = dist_ff(ox, oy, oz, b.s[0], b.s[1], b.s[2]);
+            const float cth = (b.fwd[0] * vx + b.fwd[1] * vy + b.fwd[2] * vz) / r.hi;
+            q = (uint32_t)min((int)(acosf(fminf(1.0f, fmaxf(-1.0f, cth))) * b.inv_dtheta), 0xfffe);
+        }
+        keys[c] = ((uint64_t)job << 16) | q;
     }
 }
 
@@ -714,7 +725,7 @@ __global__ void k_mat_offsets_batch(const BatchArgs a, const uint64_t* keys, con
     const int j = (int)(t / kMatStride), q = (int)(t % kMatStride);
     const JobDev& b = a.jobs[j];
     if (!b.diff_mma || q > b.n_mat) return;
-    const uint64_t key = ((uint64_t)j << 8) | (uint64_t)q;  // q = n_mat: the first key past the job's materials
+    const uint64_t key = ((uint64_t)j << 16) | (uint64_t)q;  // q = n_mat: the first key past the job's materials
     int64_t lo = 0, hi = *count;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
@@ -780,6 +791,8 @@ cudaError_t adjoint_diffraction_mma(const AccumArgs& a, const AdjointArgs& j, co
     return cudaGetLastError();
 }
 
+// (jobs with an emitter table and no tensor-core diffraction are keyed by the emitter-table row of each
+// candidate instead of its material, so that their accumulator reads few table rows per tile)
 cudaError_t batch_material_order(const BatchArgs& a, const uint32_t* count, int64_t cap, uint32_t* idx,
                                  uint32_t* mat_off, void* scratch, cudaStream_t s) {
     if (cap <= 0) return cudaSuccess;
@@ -789,8 +802,8 @@ cudaError_t batch_material_order(const BatchArgs& a, const uint32_t* count, int6
     k_mat_keys_batch<<<grid_for(cap, 256), 256, 0, s>>>(a, idx, count, cap, keys);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int bits = 8;
-    while (((int64_t)1 << (bits - 8)) <= a.n_jobs) ++bits;  // job indices 0 .. n_jobs (the sentinel)
+    int bits = 16;
+    while (((int64_t)1 << (bits - 16)) <= a.n_jobs) ++bits;  // job indices 0 .. n_jobs (the sentinel)
     if ((e = radix_sort_u64(keys, idx, cap, bits, sort_scr, s)) != cudaSuccess) return e;  // stable
     const int64_t nt = (int64_t)a.n_jobs * kMatStride;
     note_launch();

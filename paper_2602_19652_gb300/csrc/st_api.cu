@@ -163,6 +163,7 @@ struct BatchState {
     int32_t n_tasks_mma = 0;
     int64_t items_mma = 0;
     bool any_mma = false;
+    bool any_table_order = false;  // some job's diffraction paths go in emitter-table row order (its table)
     DevBuf mat_off, mat_scr;
     size_t smem_spec = 0, smem_diff = 0;
     PathList spec, diff;
@@ -2123,7 +2124,8 @@ cudaError_t batch_issue(st_ctx* c, BatchState& B, const st_job* jobs, const st_s
             CB(flags_from_u8(a.keep, B.K_total, fl, st_));
             CB(exclusive_scan_u32(fl, sc, B.K_total, cnt + 3, B.dscratch.p, st_));
             CB(compact_indices(fl, sc, B.K_total, ix, st_));
-            if (B.any_mma)  // tensor-core jobs' paths grouped by material (stable; jobs stay in place)
+            if (B.any_mma || B.any_table_order)  // tensor-core jobs' paths grouped by material, jobs with an
+                                                 // emitter table's by table row (stable; jobs stay in place)
                 CB(batch_material_order(a, cnt + 3, B.K_total, ix, ptr<uint32_t>(B.mat_off), B.mat_scr.p, st_));
             CB(batch_gather_diff(a, ix, cnt + 3, B.diff, st_));
         }
@@ -2291,6 +2293,7 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     B = BatchState();
     B.n_jobs = n_jobs;
     B.any_mma = false;
+    B.any_table_order = false;
     B.tables.resize(n_jobs);
     B.jobs.resize(n_jobs);
     B.chunks_spec.resize(n_jobs);
@@ -2449,6 +2452,7 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
             d.diff_mma = d.K > 0 && diffraction_mma_applies(probe) ? 1 : 0;
         }
         B.any_mma = B.any_mma || d.diff_mma;
+        B.any_table_order = B.any_table_order || (d.etab != nullptr && d.K > 0 && !d.diff_mma);
         B.chunks_spec[j] =
             std::max(1, accum_chunks(d.N * d.B, d.M, d.F, S.n_mat, dir_nb, tn.mic_pairs_per_cta, tn.smem_kb) / nb);
         B.chunks_diff[j] =
@@ -2459,7 +2463,7 @@ static st_status simulate_batch_impl(st_ctx* c, int32_t n_jobs, const st_job* jo
     }
     B.narrow_slice = (narrow_part + 255) & ~(size_t)255;
     CKC(c, grow(B.narrow_partial, 4 * B.narrow_slice), "batch alloc");
-    if (B.any_mma) {
+    if (B.any_mma || B.any_table_order) {
         CKC(c, grow(B.mat_off, (size_t)n_jobs * kMatStride * 4), "batch alloc");
         CKC(c, grow(B.mat_scr, material_order_scratch(B.K_total)), "batch alloc");
     }
