@@ -41,7 +41,7 @@ FLOPS_PER_TERM = 10  # per (path, mic, bin) term: complex rotation (6) + real-by
 # the path list is read once).  k_accum_diff_mma: the full-size diffraction set (21.4 MB read, 0.003 MB written).
 ACCUM_TRAFFIC = {"sources_sha16": "3dfb4d8787f86c0b", "specular_bytes_per_launch": 39.9e6}
 ACCUM_SOURCES = ("st_accum.cu", "st_accum_dev.cuh", "st_internal.cuh")
-DIFF_MMA_TRAFFIC = {"sources_sha16": "1bb994d2be487f37", "bytes_per_launch": 21.4e6}
+DIFF_MMA_TRAFFIC = {"sources_sha16": "3bad1f7281ffc9cd", "bytes_per_launch": 21.4e6}
 DIFF_MMA_SOURCES = ("st_accum_mma.cu", "st_accum_dev.cuh", "st_internal.cuh")
 
 
