@@ -54,3 +54,4 @@ def test_host_only_calls(lib):
     assert L.st_simulate(None, None, None, None, None) == -1
     assert L.st_get_receiver_masks(None, None, 0) == -1
     assert L.st_set_frequencies(None, 4, 1.0, 2.0) == -1
+    assert L.st_set_stage_overlap(None, 1) == -1
