@@ -297,7 +297,8 @@ def measure_adjoint(st, torch, wl, steps: int = 5):
     return {"fwd_ms": f, "bwd_ms": b, "bwd_over_fwd": b / f}
 
 
-def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 65536, reps: int = 3):
+def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 65536, reps: int = 3,
+                    plain_arm: bool = True):
     """Batched form against plain per-pose calls on the pose-sweep workload: 256 sensor poses over 16
     procedural scenes (triangle counts log-uniform 10k-2M, 1-4 materials), 2-64 mics, 256-2048 bins,
     1-5 bounces per pose, diffraction on.  Both arms use the autotuned launch shapes; both are timed
@@ -346,6 +347,8 @@ def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 
     ctx.simulate_batch(jobs, p, tune)
     batched_ms = timed(lambda: ctx.simulate_batch(jobs, p, tune))
     batched_out = [j.out.clone() for j in jobs]
+    if not plain_arm:  # (profiling case: the batched arm alone)
+        return {"batched_ms": batched_ms}
 
     # plain: one st_simulate per pose (sensor inputs already on the device)
     plain_out = [torch.empty_like(j.out) for j in jobs]
@@ -381,7 +384,8 @@ def measure_batched(st, torch, rays_per_pose: int = 32768, sample_budget: int = 
             "max_rel_l2_batched_vs_plain": err, "first_call_s": first_call_s}
 
 
-def measure_batched_directional(st, torch, n_poses: int = 64, rays_per_pose: int = 32768, reps: int = 3):
+def measure_batched_directional(st, torch, n_poses: int = 64, rays_per_pose: int = 32768, reps: int = 3,
+                                plain_arm: bool = True):
     """Batched form against plain per-pose calls on bat poses with directivity (Sec. III-F): a 200k-triangle
     leaf-disc scene, n_poses head poses near the centre (random headings; the ears at +-1 cm across the
     head, oriented with it), the piston emitter table and two ear tables, 1024 bins 20-120 kHz, 4 bounces,
@@ -435,6 +439,8 @@ def measure_batched_directional(st, torch, n_poses: int = 64, rays_per_pose: int
     ctx.simulate_batch(jobs, p)
     batched_ms = timed(lambda: ctx.simulate_batch(jobs, p))
     batched_out = [j.out.clone() for j in jobs]
+    if not plain_arm:  # (profiling case: the batched arm alone)
+        return {"batched_ms": batched_ms}
     plain_out = [torch.empty_like(j.out) for j in jobs]
     pp = [st.sim_params(max_distance=wl.max_distance, max_bounces=wl.bounces, pose_index=i) for i in range(n_poses)]
     ctx.set_frequencies(wl.n_bins, wl.f_lo, wl.f_hi)
@@ -768,6 +774,12 @@ def run_case(st, torch, case: str, reps: int):
     if case == "batched":
         print(json.dumps(measure_batched(st, torch)))
         return
+    if case == "batched_bat_only":  # the batched arm alone (launch lists)
+        print(json.dumps(measure_batched_directional(st, torch, plain_arm=False)))
+        return
+    if case == "batched_only":
+        print(json.dumps(measure_batched(st, torch, plain_arm=False)))
+        return
     if case == "emitters":
         wl = synth.clutter(seed=202)
         ctx = st.Context(dev)
@@ -902,7 +914,7 @@ def main():
     ap.add_argument("--no-instances", action="store_true", help="skip the instanced-forest timing")
     ap.add_argument("--case", default=None,
                     choices=["accum", "adjoint", "trace", "trace_per_mic", "narrow", "emitters", "instances", "batched_bat",
-                             "batched"],
+                             "batched", "batched_bat_only", "batched_only"],
                     help="run a small case of one kernel family a few times and exit (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
