@@ -1632,6 +1632,76 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
         x.meta = ptr<uint32_t>(PL.meta);
         x.dep = ptr<float>(PL.dep);
     };
+    // The diffraction and direct-path adjoints (positions) share nothing with the specular part but G and the
+    // zeroed gradient slices, each writing its own: with the stage overlap they run on the context's side
+    // stream beside the specular part's preparation and adjoint, joined before the position sums.
+    const bool side_pos = c->overlap && c->side && want_pos &&
+                          (c->last_K > 0 || (p.components & ST_COMP_DIRECT)) &&
+                          (p.components & ST_COMP_SPECULAR) && c->last_N > 0;
+    cudaStream_t s2 = s;
+    bool joined = false;
+    if (side_pos) {
+        CKC(c, cudaEventRecord(c->ev_fork, s), "fork");
+        CKC(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+        s2 = c->side;
+    }
+    struct JoinGuard {
+        st_ctx* c;
+        cudaStream_t s;
+        const bool& active;
+        const bool& done;
+        ~JoinGuard() {
+            if (active && !done) {
+                cudaEventRecord(c->ev_join, c->side);
+                cudaStreamWaitEvent(s, c->ev_join, 0);
+            }
+        }
+    } join_guard{c, s, side_pos, joined};
+    auto positions_beside = [&]() -> st_status {
+        // ---- diffraction: positions
+        if (want_pos && c->last_K > 0) {
+            AccumArgs x = aa;
+            x.kind = 1;
+            x.d_count = cnt + 3;
+            x.n_chunks = chunks_d;
+            set_paths(x, c->paths_diff);
+            AdjointArgs jj = ja;
+            jj.G = G + MF;
+            jj.do_pos = 1;
+            jj.do_k = 0;
+            jj.v_part = ptr<float>(c->adj_v);
+            jj.mic_part = micp + (size_t)spec_mic_slices * M * 3;
+            jj.emit_part = emitp + (size_t)spec_emit_slices * 3;
+            if (diff_mma)
+                CKC(c, adjoint_diffraction_mma(x, jj, ptr<uint32_t>(c->mat_off), s2), "adjoint diffraction");
+            else
+                CKC(c, adjoint_launch(x, jj, gd, s2), "adjoint diffraction");
+        }
+        // ---- direct path
+        if (want_pos && (p.components & ST_COMP_DIRECT)) {
+            DirectAccumArgs da{};
+            memcpy(da.s, c->s, 12);
+            da.mics = ptr<float>(c->mics);
+            da.M = M;
+            da.F = F;
+            da.vis = ptr<uint8_t>(c->dvis);
+            da.f_lo = c->f_lo;
+            da.df = T.df;
+            da.c = p.c;
+            da.a0 = p.alpha0_db_m;
+            da.a1 = p.alpha1_db_m_khz;
+            da.gain = p.direct_gain;
+            CKC(c, adjoint_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), G + 2 * MF,
+                                  micp + (size_t)(spec_mic_slices + diff_mic_slices) * M * 3,
+                                  emitp + (size_t)(spec_emit_slices + diff_emit_slices) * 3, s2),
+                "adjoint direct");
+        }
+        return ST_OK;
+    };
+    if (side_pos) {
+        const st_status r = positions_beside();
+        if (r != ST_OK) return r;
+    }
     // ---- specular: reflection sums in batches of four materials, positions with the first batch
     if ((p.components & ST_COMP_SPECULAR) && c->last_N > 0 && (grad_k || want_pos)) {
         AccumArgs x = aa;
@@ -1737,43 +1807,13 @@ static st_status backward_impl(st_ctx* c, st_scene* sc, const void* grad_spectra
                 "adjoint dbeta");
         }
     }
-    // ---- diffraction: positions
-    if (want_pos && c->last_K > 0) {
-        AccumArgs x = aa;
-        x.kind = 1;
-        x.d_count = cnt + 3;
-        x.n_chunks = chunks_d;
-        set_paths(x, c->paths_diff);
-        AdjointArgs jj = ja;
-        jj.G = G + MF;
-        jj.do_pos = 1;
-        jj.do_k = 0;
-        jj.v_part = ptr<float>(c->adj_v);
-        jj.mic_part = micp + (size_t)spec_mic_slices * M * 3;
-        jj.emit_part = emitp + (size_t)spec_emit_slices * 3;
-        if (diff_mma)
-            CKC(c, adjoint_diffraction_mma(x, jj, ptr<uint32_t>(c->mat_off), s), "adjoint diffraction");
-        else
-            CKC(c, adjoint_launch(x, jj, gd, s), "adjoint diffraction");
-    }
-    // ---- direct path
-    if (want_pos && (p.components & ST_COMP_DIRECT)) {
-        DirectAccumArgs da{};
-        memcpy(da.s, c->s, 12);
-        da.mics = ptr<float>(c->mics);
-        da.M = M;
-        da.F = F;
-        da.vis = ptr<uint8_t>(c->dvis);
-        da.f_lo = c->f_lo;
-        da.df = T.df;
-        da.c = p.c;
-        da.a0 = p.alpha0_db_m;
-        da.a1 = p.alpha1_db_m_khz;
-        da.gain = p.direct_gain;
-        CKC(c, adjoint_direct(da, ptr<float>(T.qhi), ptr<float>(T.qlo), G + 2 * MF,
-                              micp + (size_t)(spec_mic_slices + diff_mic_slices) * M * 3,
-                              emitp + (size_t)(spec_emit_slices + diff_emit_slices) * 3, s),
-            "adjoint direct");
+    if (!side_pos) {
+        const st_status r = positions_beside();
+        if (r != ST_OK) return r;
+    } else {
+        CKC(c, cudaEventRecord(c->ev_join, s2), "join");
+        CKC(c, cudaStreamWaitEvent(s, c->ev_join, 0), "join");
+        joined = true;
     }
     if (want_pos)
         CKC(c, adjoint_pos(micp, mic_slices, emitp, emit_slices, M, grad_mic, grad_emitter, s), "adjoint reduce");
