@@ -295,12 +295,18 @@ st_status st_get_direct_visibility(st_ctx* ctx, uint8_t* vis, int32_t mem);
  * After a simulate with ST_LOS_PER_MIC each specular path reaches only the microphones of its mask here too.
  * Needs omni receivers; position gradients also need an omni emitter (ST_ERR_ARG otherwise).  scene must be the one of the
  * last simulate, unchanged since (ST_ERR_STATE otherwise).  Deterministic: every sum runs in a fixed
- * order.  Stream-ordered; allocates reduction buffers on first use. */
+ * order.  Stream-ordered; allocates reduction buffers on first use.  The first call after a simulate (omni
+ * emitter) puts that simulate's internal specular path list in reflection-chain order, so that the reflection
+ * sums are formed once per run of paths with equal material counts; later calls find it so, and repeated calls
+ * give identical gradients.  With the stage overlap (st_set_stage_overlap) the diffraction and direct-path
+ * adjoints run on the context's side stream beside the specular one. */
 st_status st_backward(st_ctx* ctx, st_scene* scene, const void* grad_spectra, float* grad_k, float* grad_mic,
                       float* grad_emitter);
 /* Adjoint with respect to the lobe widths: grad_beta [n_mat][n_bands] device float32, the gradient of
  * the loss through the specular lobe exp(-gamma^2 / (2 beta^2)) of each path's last hit (the lobe
- * exponent interpolated between bands through 1 / (2 beta^2)).  Same conditions as st_backward. */
+ * exponent interpolated between bands through 1 / (2 beta^2)).  Same conditions as st_backward.  Its
+ * float32 sums follow the path list's order, so a call before and a call after st_backward (which orders
+ * the list by reflection chain) can differ in the last bits. */
 st_status st_backward_beta(st_ctx* ctx, st_scene* scene, const void* grad_spectra, float* grad_beta);
 
 /* Batched form: many poses (over one or more precomputed scenes) simulated together.  Every stage
