@@ -43,6 +43,12 @@ ACCUM_TRAFFIC = {"sources_sha16": "3dfb4d8787f86c0b", "specular_bytes_per_launch
 ACCUM_SOURCES = ("st_accum.cu", "st_accum_dev.cuh", "st_internal.cuh")
 DIFF_MMA_TRAFFIC = {"sources_sha16": "3bad1f7281ffc9cd", "bytes_per_launch": 21.4e6}
 DIFF_MMA_SOURCES = ("st_accum_mma.cu", "st_accum_dev.cuh", "st_internal.cuh")
+# k_accum_narrow on the vegetation workload (two launches a step, specular and diffraction): captured on 500k
+# rays (specular 51.75 MB read + 0.14 MB written for 871,268 visible records; diffraction 11.04 MB read for the
+# full-size set of 222,807 kept samples), the specular launch scaled to the full-size 6,971,043 records (the
+# path list is read once: 414.2 MB), averaged over the step's two launches.
+NARROW_TRAFFIC = {"sources_sha16": "90bea9bb00972dd0", "bytes_per_launch": 212.6e6}
+NARROW_SOURCES = ("st_accum_narrow.cu", "st_accum_dev.cuh", "st_internal.cuh")
 
 
 def accum_sources_sha16(files=ACCUM_SOURCES):
@@ -606,7 +612,8 @@ def measure_instances(st, torch, n_inst: int = 8000, n_rays: int = 1_000_000, re
     return res
 
 
-def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: int = 0, roofline=None, e2e=False):
+def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: int = 0, roofline=None, e2e=False,
+                     traffic=None):
     """Device time of one simulate on another workload (scene prebuilt, L2 flushed before each step);
     los_mode 1: the receiver test of every hit made per microphone.  roofline = (n_sm, sm_mhz, peak_src):
     also the accumulator's FP32 roofline; e2e: also the end-to-end rate through host buffers."""
@@ -641,7 +648,7 @@ def measure_workload(st, torch, wl, steps: int = 3, warmup: int = 2, los_mode: i
     if roofline is not None:
         n_sm, sm_mhz, peak_src = roofline
         kern = "k_accum_narrow (one microphone pair)" if len(wl.mics) <= 2 else "k_accum (spectrum accumulator)"
-        res["roofline"] = accum_roofline(all_stats, n_sm, sm_mhz, peak_src, kernel=kern)
+        res["roofline"] = accum_roofline(all_stats, n_sm, sm_mhz, peak_src, kernel=kern, traffic=traffic)
     if e2e:
         n = max(3, steps)
         dt, h2d, d2h = e2e_simulate(st, ctx, sc, wl, p, n)
@@ -1035,8 +1042,10 @@ def main():
         batched_dir = measure_batched_directional(st, torch)
     vegetation = None
     if not args.no_vegetation and args.workload != "vegetation":
+        veg_traffic = (NARROW_TRAFFIC["bytes_per_launch"]
+                       if NARROW_TRAFFIC["sources_sha16"] == accum_sources_sha16(NARROW_SOURCES) else None)
         vegetation = measure_workload(st, torch, synth.vegetation(seed=303), roofline=(n_sm, sm_mhz, peak_src),
-                                      e2e=True)
+                                      e2e=True, traffic=veg_traffic)
     per_mic = None
     if not args.no_per_mic and len(wl.mics) <= 64:
         per_mic = measure_workload(st, torch, wl, los_mode=st.ST_LOS_PER_MIC)
